@@ -1,0 +1,845 @@
+/*
+ * pa_oracle.c -- plain FP64 CPU oracle of the Plastic Arbor time-step loop.
+ *
+ * TEST INFRASTRUCTURE.  Used only by tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py.  It shares no code, header, table
+ * or constant generator with the CUDA engine; it is written to be read against
+ * the paper (arXiv 2411.16445) line by line, not to be fast.
+ *
+ * What one step k (t_k = k*dt -> t_{k+1}) computes, in this order:
+ *   1. events at t_k: synaptic pre events due at step k (spikes delivered after
+ *      their integer delay), independent Poisson pre events, the delayed
+ *      presynaptic calcium contributions (t_c,delay of Eqs.
+ *      ca_model_graupner_brunel / ca_for_stc_model, the second target of the
+ *      round_robin_halt policy), then the POST_EVENT hook for cells that spiked
+ *      in step k-1 (Sec. "Spike-time detection to simplify computation").
+ *   2. membrane currents at V^k, linearised into the matrix: every current here
+ *      is linear in V for fixed gates/conductances, so i = g (V - E) enters as
+ *      diagonal g and right-hand side g E.
+ *   3. backward-Euler step of the cable equation (Eq. cable) on each cell's
+ *      tree, solved by Hines elimination -> V^{k+1}.
+ *   4. state updates: HH gates by exponential integration at V^{k+1}; synaptic
+ *      conductance and calcium decay; forward-Euler steps of the plasticity
+ *      ODEs (Eqs. weight_graupner_brunel, early_phase_weight,
+ *      late_phase_weight, prp_single_comp) evaluated with the post-event state
+ *      of step k; STDP traces decay (Eqs. stdp_ode_1-2).
+ *   5. threshold detection at the soma CV: a spike in step k iff
+ *      V^k < theta <= V^{k+1}.
+ *
+ * Readings where the paper is silent are listed in the repository's design
+ * notes; the ones that fix arithmetic are repeated next to the code.
+ * Parity: the HH channel kinetics are "parity unpinned" beyond the textbook
+ * resting potential and firing-rate checks of the test-suite; every other
+ * function here is pinned by a closed form, a brute-force or library solve, or
+ * an invariant (tests/test_oracle_pins.py).
+ */
+#define _GNU_SOURCE
+#include "pa_oracle.h"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+static __thread char g_err[512];
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+const char* orc_last_error(void) { return g_err; }
+
+/* ------------------------------------------------------------------------ */
+/* exp(x) used by the HH kinetics.  Both the oracle and the engine define the
+ * model's exponential as this function so that FP64 results can agree to the
+ * last bit (a reading: the paper fixes no exp).  Method: Cody-Waite argument
+ * reduction x = k ln2 + r, |r| <= ln2/2, with ln2 split into a 32-bit head
+ * (the double nearest ln2 with its low 21 mantissa bits cleared) and a tail,
+ * then the degree-13 Taylor polynomial sum r^j/j! by Horner's rule with fused
+ * multiply-adds, then scaling by 2^k.  Truncation error < r^14/14! < 5e-18. */
+static const double kLn2Hi = 6.93147180369123816490e-01;  /* 0x1.62e42feep-1     */
+static const double kLn2Lo = 1.9082149292705877e-10;      /* ln2 - kLn2Hi         */
+static const double kInvLn2 = 1.4426950408889634;         /* nearest double 1/ln2 */
+static const double kInvFact[14] = {
+    1.0, 1.0, 0.5, 0.16666666666666666, 0.041666666666666664, 0.008333333333333333,
+    0.001388888888888889, 0.0001984126984126984, 2.48015873015873e-05,
+    2.7557319223985893e-06, 2.755731922398589e-07, 2.505210838544172e-08,
+    2.08767569878681e-09, 1.6059043836821613e-10};
+
+double orc_exp(double x) {
+  if (x != x) return x;
+  if (x > 709.0) return HUGE_VAL;
+  if (x < -708.0) return 0.0;
+  double kd = nearbyint(x * kInvLn2);
+  double r = (x - kd * kLn2Hi) - kd * kLn2Lo;
+  double p = kInvFact[13];
+  for (int j = 12; j >= 0; --j) p = fma(p, r, kInvFact[j]);
+  int64_t k = (int64_t)kd;
+  uint64_t bits = (uint64_t)(k + 1023) << 52;
+  double scale;
+  memcpy(&scale, &bits, sizeof scale);
+  return p * scale;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hodgkin-Huxley rate functions (HodgkinHuxley1952, used on the soma of the
+ * paper's simple-branchy cells): textbook form with resting potential -65 mV,
+ * temperature factor 1 (6.3 C).  vtrap removes the 0/0 of alpha_m, alpha_n. */
+static double vtrap(double x, double y) {
+  double u = x / y;
+  if (fabs(u) < 1e-6) return y * (1.0 - 0.5 * u);
+  return x / (orc_exp(u) - 1.0);
+}
+
+void orc_hh_rates(double v, double* am, double* bm, double* ah, double* bh, double* an,
+                  double* bn) {
+  *am = 0.1 * vtrap(-(v + 40.0), 10.0);
+  *bm = 4.0 * orc_exp(-(v + 65.0) / 18.0);
+  *ah = 0.07 * orc_exp(-(v + 65.0) / 20.0);
+  *bh = 1.0 / (orc_exp(-(v + 35.0) / 10.0) + 1.0);
+  *an = 0.01 * vtrap(-(v + 55.0), 10.0);
+  *bn = 0.125 * orc_exp(-(v + 65.0) / 80.0);
+}
+
+/* exponential (cnexp) integration of dx/dt = a (1 - x) - b x over dt */
+static double cnexp_gate(double x, double a, double b, double dt) {
+  double s = a + b;
+  double xinf = a / s;
+  return xinf + (x - xinf) * orc_exp(-dt * s);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hines elimination for a tree with parent[i] < i (textbook; Hines 1984):
+ * for i = n-1 .. 1:  r_i = 1/d_i, f_i = a_i r_i, x'_i = b_i r_i,
+ *                    d_p -= f_i a_i,  b_p -= a_i x'_i     (p = parent[i])
+ * then x_0 = b_0 / d_0 and, for i = 1 .. n-1, x_i = x'_i - f_i x_{p}.
+ * a_i is the (symmetric) off-diagonal entry between i and parent[i].
+ * d and b are modified in place; f and xp are scratch of length n. */
+static void hines(int64_t n, const int32_t* parent, double* d, const double* a, double* b,
+                  double* f, double* xp, double* x) {
+  for (int64_t i = n - 1; i >= 1; --i) {
+    int32_t p = parent[i];
+    double r = 1.0 / d[i];
+    f[i] = a[i] * r;
+    xp[i] = b[i] * r;
+    d[p] = fma(-f[i], a[i], d[p]);
+    b[p] = fma(-a[i], xp[i], b[p]);
+  }
+  x[0] = b[0] * (1.0 / d[0]);
+  for (int64_t i = 1; i < n; ++i) x[i] = fma(-f[i], x[parent[i]], xp[i]);
+}
+
+int orc_hines_solve(int32_t n, const int32_t* parent, const double* d, const double* a,
+                    const double* b, double* x) {
+  if (n <= 0) return -1;
+  double* dd = (double*)malloc(sizeof(double) * 4 * (size_t)n);
+  if (!dd) return -2;
+  double* bb = dd + n;
+  double* f = bb + n;
+  double* xp = f + n;
+  memcpy(dd, d, sizeof(double) * n);
+  memcpy(bb, b, sizeof(double) * n);
+  hines(n, parent, dd, a, bb, f, xp, x);
+  free(dd);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Threefry-4x64-12 counter-based generator (Salmon et al. 2011, the generator
+ * named in Sec. "Computation with stochastic differential equations"):
+ * Threefish-256 rotation schedule, key parity constant 0x1BD11BDAA9FC1A22,
+ * key injection after every fourth round.  Used here for Poisson drive. */
+static uint64_t rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+void orc_threefry4x64_12(const uint64_t ctr[4], const uint64_t key[4], uint64_t out[4]) {
+  static const int rot[8][2] = {{14, 16}, {52, 57}, {23, 40}, {5, 37},
+                                {25, 33}, {46, 12}, {58, 22}, {32, 32}};
+  uint64_t ks[5];
+  ks[4] = 0x1BD11BDAA9FC1A22ULL;
+  for (int i = 0; i < 4; ++i) {
+    ks[i] = key[i];
+    ks[4] ^= key[i];
+  }
+  uint64_t x0 = ctr[0] + ks[0], x1 = ctr[1] + ks[1], x2 = ctr[2] + ks[2], x3 = ctr[3] + ks[3];
+  for (int r = 0; r < 12; ++r) {
+    const int* rc = rot[r % 8];
+    if ((r & 1) == 0) {
+      x0 += x1; x1 = rotl64(x1, rc[0]); x1 ^= x0;
+      x2 += x3; x3 = rotl64(x3, rc[1]); x3 ^= x2;
+    } else {
+      x0 += x3; x3 = rotl64(x3, rc[0]); x3 ^= x0;
+      x2 += x1; x1 = rotl64(x1, rc[1]); x1 ^= x2;
+    }
+    if ((r & 3) == 3) {
+      int s = (r >> 2) + 1;
+      x0 += ks[s % 5];
+      x1 += ks[(s + 1) % 5];
+      x2 += ks[(s + 2) % 5];
+      x3 += ks[(s + 3) % 5] + (uint64_t)s;
+    }
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Uniform 32-bit word for Poisson stream `stream` at step `step`: one
+ * Threefry call (key = seed, counter = {stream, step/8, 1, 0}) serves eight
+ * consecutive steps; word j = step mod 8 is 32-bit half (j mod 2) of output
+ * word j/2, low half first. */
+uint32_t orc_poisson_u32(uint64_t seed, uint64_t stream, int64_t step) {
+  uint64_t key[4] = {seed, 0, 0, 0};
+  uint64_t ctr[4] = {stream, (uint64_t)step >> 3, 1, 0};
+  uint64_t out[4];
+  orc_threefry4x64_12(ctr, key, out);
+  int j = (int)(step & 7);
+  uint64_t w = out[j >> 1];
+  return (j & 1) ? (uint32_t)(w >> 32) : (uint32_t)w;
+}
+
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t syn;
+  int32_t type; /* 0: pre (conductance) event, 1: delayed calcium event */
+} orc_ev;
+typedef struct {
+  orc_ev* v;
+  int64_t n, cap;
+} orc_bucket;
+
+typedef struct {
+  int32_t kind;
+  double p[20];
+  /* derived per-dt constants */
+  double decay_g, decay_c, decay_pre, decay_post;
+  double rate_w, rate_h, rate_z, rate_p;
+  int64_t dc_steps;
+} orc_mech;
+
+struct orc_model {
+  double dt;
+  uint64_t seed;
+  int64_t step;
+  int32_t n_cells;
+  int64_t n_cv;
+  int64_t* cv_off;
+  int32_t* parent; /* cell-local */
+  double *cap, *cdt, *gax, *a, *gpas, *em_pas;
+  int32_t* cv_mech; /* mechanism index of the CV's density mechanism */
+  double *gna_a, *gk_a, *gl_a;
+  double *V, *m, *h, *n;
+  double *gs, *es, *d, *b, *f, *xp, *xnew;
+  double* istep;
+  int64_t *k_on, *k_off;
+  double *thresh, *p;
+  int32_t *spiked_prev, *spk_flag, *cell_stc_mech;
+  double* spk_t;
+  int32_t n_mech;
+  orc_mech* mech;
+  int64_t n_syn;
+  int32_t *syn_cell, *syn_mech, *syn_src;
+  int64_t* syn_cv; /* global CV index */
+  double* syn_weight;
+  int64_t* syn_D;
+  uint32_t* syn_thr;
+  double *g, *c, *w, *hs, *z, *apre, *apost;
+  int64_t *cell_syn_off, *cell_syn;
+  int64_t *out_off, *out_syn;
+  int64_t *poisson_syn, n_poisson;
+  int64_t R;
+  orc_bucket* q;
+  int64_t n_spk, cap_spk;
+  int32_t* spk_gid;
+  int64_t* spk_step;
+  double* spk_time;
+  int32_t n_probe;
+  int64_t* probe_cv;
+  double* probes;
+  int64_t n_samples, cap_samples;
+  int replay;
+  int64_t n_rep, rep_pos;
+  int32_t* rep_gid;
+  int64_t* rep_step;
+};
+
+static int is_point(int32_t k) {
+  return k == ORC_MECH_EXPSYN || k == ORC_MECH_GB || k == ORC_MECH_STC || k == ORC_MECH_STDP;
+}
+static int n_params_of(int32_t k) {
+  switch (k) {
+    case ORC_MECH_PAS: return 2;
+    case ORC_MECH_HH: return 6;
+    case ORC_MECH_EXPSYN: return 2;
+    case ORC_MECH_GB: return 13;
+    case ORC_MECH_STC: return 18;
+    case ORC_MECH_STDP: return 8;
+  }
+  return -1;
+}
+
+static void push_ev(orc_bucket* bk, int32_t syn, int32_t type) {
+  if (bk->n == bk->cap) {
+    bk->cap = bk->cap ? 2 * bk->cap : 64;
+    bk->v = (orc_ev*)realloc(bk->v, sizeof(orc_ev) * (size_t)bk->cap);
+  }
+  bk->v[bk->n].syn = syn;
+  bk->v[bk->n].type = type;
+  bk->n++;
+}
+
+#define ALLOC(ptr, n) ((ptr) = calloc((size_t)((n) > 0 ? (n) : 1), sizeof(*(ptr))))
+
+static orc_model* g_sort_model;
+static int cmp_syn(const void* x, const void* y) {
+  int64_t i = *(const int64_t*)x, j = *(const int64_t*)y;
+  const orc_model* M = g_sort_model;
+  if (M->syn_mech[i] != M->syn_mech[j]) return M->syn_mech[i] < M->syn_mech[j] ? -1 : 1;
+  if (M->syn_cv[i] != M->syn_cv[j]) return M->syn_cv[i] < M->syn_cv[j] ? -1 : 1;
+  return i < j ? -1 : (i > j);
+}
+
+void orc_free(orc_model* M) {
+  if (!M) return;
+  void* ptrs[] = {M->cv_off, M->parent, M->cap, M->cdt, M->gax, M->a, M->gpas, M->em_pas,
+                  M->cv_mech, M->gna_a, M->gk_a, M->gl_a, M->V, M->m, M->h, M->n, M->gs,
+                  M->es, M->d, M->b, M->f, M->xp, M->xnew, M->istep, M->k_on, M->k_off,
+                  M->thresh, M->p, M->spiked_prev, M->spk_flag, M->cell_stc_mech, M->spk_t,
+                  M->mech, M->syn_cell, M->syn_mech, M->syn_src, M->syn_cv, M->syn_weight,
+                  M->syn_D, M->syn_thr, M->g, M->c, M->w, M->hs, M->z, M->apre, M->apost,
+                  M->cell_syn_off, M->cell_syn, M->out_off, M->out_syn, M->poisson_syn,
+                  M->spk_gid, M->spk_step, M->spk_time, M->probe_cv, M->probes, M->rep_gid,
+                  M->rep_step};
+  for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
+  if (M->q) {
+    for (int64_t i = 0; i < M->R; ++i) free(M->q[i].v);
+    free(M->q);
+  }
+  free(M);
+}
+
+int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_soma_mech,
+              const int32_t* cell_dend_mech, const double* cell_cm, const double* cell_ra,
+              const double* cell_istep, const double* cell_ton, const double* cell_toff,
+              const double* cell_vinit, const double* cell_thresh,
+              int32_t n_morph, const int32_t* morph_ncv, const int32_t* morph_off,
+              const int32_t* parent, const double* length_um, const double* diam_um,
+              const int32_t* region,
+              int32_t n_mech, const int32_t* mech_kind, const int32_t* mech_off,
+              const double* mech_params,
+              int64_t n_conn, const int32_t* conn_src, const int32_t* conn_dst,
+              const int32_t* conn_cv, const int32_t* conn_mech, const double* conn_weight,
+              const double* conn_delay, const double* conn_rate,
+              double dt, uint64_t seed, int32_t n_probe, const int32_t* probe_gid,
+              const int32_t* probe_cv, orc_model** out) {
+  *out = NULL;
+  if (!(dt > 0)) return fail(-1, "dt must be positive");
+  if (n_cells < 0 || n_morph < 0 || n_mech < 0 || n_conn < 0)
+    return fail(-1, "negative count");
+  orc_model* M = (orc_model*)calloc(1, sizeof *M);
+  M->dt = dt;
+  M->seed = seed;
+  M->n_cells = n_cells;
+  M->n_mech = n_mech;
+  ALLOC(M->mech, n_mech);
+  for (int32_t j = 0; j < n_mech; ++j) {
+    int np = n_params_of(mech_kind[j]);
+    if (np < 0) { orc_free(M); return fail(-1, "mechanism %d: unknown kind %d", j, mech_kind[j]); }
+    orc_mech* mc = &M->mech[j];
+    mc->kind = mech_kind[j];
+    for (int i = 0; i < np; ++i) mc->p[i] = mech_params[mech_off[j] + i];
+    /* per-dt constants: exact exponential decay of the linear ODEs
+       (g' = -g/tau, c' = -c/tau_c, a' = -a/tau) and forward-Euler rates */
+    if (is_point(mc->kind)) mc->decay_g = exp(-dt / mc->p[0]);
+    if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC) {
+      mc->decay_c = exp(-dt / mc->p[2]);
+      double tcd = mc->kind == ORC_MECH_GB ? mc->p[11] : mc->p[17];
+      mc->dc_steps = llround(tcd / dt);
+      if (mc->dc_steps < 0) { orc_free(M); return fail(-1, "negative t_c_delay"); }
+    }
+    if (mc->kind == ORC_MECH_GB) mc->rate_w = dt / mc->p[9];
+    if (mc->kind == ORC_MECH_STC) {
+      mc->rate_h = dt / mc->p[9];
+      mc->rate_z = dt / mc->p[10];
+      mc->rate_p = dt / mc->p[11];
+    }
+    if (mc->kind == ORC_MECH_STDP) {
+      mc->decay_pre = exp(-dt / mc->p[2]);
+      mc->decay_post = exp(-dt / mc->p[3]);
+    }
+  }
+  /* CV layout: cell-major */
+  ALLOC(M->cv_off, n_cells + 1);
+  for (int32_t c = 0; c < n_cells; ++c) {
+    int32_t mo = cell_morph[c];
+    if (mo < 0 || mo >= n_morph) { orc_free(M); return fail(-1, "cell %d: bad morphology", c); }
+    if (morph_ncv[mo] < 1) { orc_free(M); return fail(-1, "morphology %d: no CV", mo); }
+    M->cv_off[c + 1] = M->cv_off[c] + morph_ncv[mo];
+  }
+  int64_t N = M->n_cv = M->cv_off[n_cells];
+  ALLOC(M->parent, N); ALLOC(M->cap, N); ALLOC(M->cdt, N); ALLOC(M->gax, N);
+  ALLOC(M->a, N); ALLOC(M->gpas, N); ALLOC(M->em_pas, N); ALLOC(M->cv_mech, N);
+  ALLOC(M->gna_a, N); ALLOC(M->gk_a, N); ALLOC(M->gl_a, N);
+  ALLOC(M->V, N); ALLOC(M->m, N); ALLOC(M->h, N); ALLOC(M->n, N);
+  ALLOC(M->gs, N); ALLOC(M->es, N); ALLOC(M->d, N); ALLOC(M->b, N);
+  ALLOC(M->f, N); ALLOC(M->xp, N); ALLOC(M->xnew, N);
+  ALLOC(M->istep, n_cells); ALLOC(M->k_on, n_cells); ALLOC(M->k_off, n_cells);
+  ALLOC(M->thresh, n_cells); ALLOC(M->p, n_cells); ALLOC(M->spiked_prev, n_cells);
+  ALLOC(M->spk_flag, n_cells); ALLOC(M->spk_t, n_cells); ALLOC(M->cell_stc_mech, n_cells);
+  double* rhalf = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+  for (int32_t c = 0; c < n_cells; ++c) {
+    int32_t mo = cell_morph[c];
+    int64_t n = morph_ncv[mo], base = M->cv_off[c], mb = morph_off[mo];
+    int32_t ms = cell_soma_mech[c], md = cell_dend_mech[c];
+    if (ms < 0 || ms >= n_mech || md < 0 || md >= n_mech ||
+        (M->mech[ms].kind != ORC_MECH_PAS && M->mech[ms].kind != ORC_MECH_HH) ||
+        (M->mech[md].kind != ORC_MECH_PAS && M->mech[md].kind != ORC_MECH_HH)) {
+      free(rhalf); orc_free(M);
+      return fail(-1, "cell %d: soma/dendrite mechanism must be pas or hh", c);
+    }
+    double cm = cell_cm[c], ra = cell_ra[c];
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t pi = parent[mb + i];
+      if ((i == 0 && pi != -1) || (i > 0 && (pi < 0 || pi >= i))) {
+        free(rhalf); orc_free(M);
+        return fail(-1, "morphology %d: parent[%lld] invalid", mo, (long long)i);
+      }
+      double L = length_um[mb + i], dia = diam_um[mb + i];
+      if (!(L > 0) || !(dia > 0)) {
+        free(rhalf); orc_free(M);
+        return fail(-1, "morphology %d: non-positive length/diameter", mo);
+      }
+      /* a CV is a cylinder; area pi d L [um2]; C = cm A 1e-5 [nF];
+         half-cylinder axial resistance Ra (L/2) / (pi r^2) 1e-2 [Mohm] */
+      double r = 0.5 * dia;
+      double A = (M_PI * dia) * L;
+      M->parent[base + i] = pi;
+      M->cap[base + i] = (cm * A) * 1e-5;
+      M->cdt[base + i] = M->cap[base + i] / dt;
+      rhalf[base + i] = ((ra * (0.5 * L)) / (M_PI * (r * r))) * 1e-2;
+      int32_t mj = region[mb + i] == 0 ? ms : md;
+      M->cv_mech[base + i] = mj;
+      const orc_mech* mc = &M->mech[mj];
+      if (mc->kind == ORC_MECH_PAS) {
+        M->gpas[base + i] = (mc->p[0] * A) * 1e-2; /* S/cm2 * um2 -> uS */
+        M->em_pas[base + i] = M->gpas[base + i] * mc->p[1];
+      } else {
+        M->gna_a[base + i] = (mc->p[0] * A) * 1e-2;
+        M->gk_a[base + i] = (mc->p[1] * A) * 1e-2;
+        M->gl_a[base + i] = (mc->p[2] * A) * 1e-2;
+      }
+    }
+    /* axial conductances: two half-cylinders in series between i and parent */
+    for (int64_t i = 1; i < n; ++i) {
+      int64_t p = base + M->parent[base + i];
+      double gi = 1.0 / (rhalf[base + i] + rhalf[p]);
+      M->a[base + i] = -gi;
+      M->gax[base + i] += gi;
+      M->gax[p] += gi;
+    }
+    double v0 = cell_vinit[c];
+    for (int64_t i = 0; i < n; ++i) {
+      M->V[base + i] = v0;
+      if (M->mech[M->cv_mech[base + i]].kind == ORC_MECH_HH) {
+        double am, bm, ah, bh, an, bn;
+        orc_hh_rates(v0, &am, &bm, &ah, &bh, &an, &bn);
+        M->m[base + i] = am / (am + bm);
+        M->h[base + i] = ah / (ah + bh);
+        M->n[base + i] = an / (an + bn);
+      }
+    }
+    M->istep[c] = cell_istep[c];
+    M->k_on[c] = llround(cell_ton[c] / dt);
+    M->k_off[c] = cell_toff[c] > 1e15 ? INT64_MAX : llround(cell_toff[c] / dt);
+    M->thresh[c] = cell_thresh[c];
+    M->cell_stc_mech[c] = -1;
+  }
+  free(rhalf);
+  /* synapses, one per connection, in connection order */
+  M->n_syn = n_conn;
+  ALLOC(M->syn_cell, n_conn); ALLOC(M->syn_mech, n_conn); ALLOC(M->syn_src, n_conn);
+  ALLOC(M->syn_cv, n_conn); ALLOC(M->syn_weight, n_conn); ALLOC(M->syn_D, n_conn);
+  ALLOC(M->syn_thr, n_conn); ALLOC(M->g, n_conn); ALLOC(M->c, n_conn); ALLOC(M->w, n_conn);
+  ALLOC(M->hs, n_conn); ALLOC(M->z, n_conn); ALLOC(M->apre, n_conn); ALLOC(M->apost, n_conn);
+  ALLOC(M->poisson_syn, n_conn);
+  int64_t maxdelay = 1;
+  ALLOC(M->out_off, n_cells + 1);
+  for (int64_t s = 0; s < n_conn; ++s) {
+    int32_t dst = conn_dst[s], mj = conn_mech[s], src = conn_src[s];
+    if (dst < 0 || dst >= n_cells) { orc_free(M); return fail(-1, "connection %lld: bad dst", (long long)s); }
+    int64_t ncv = M->cv_off[dst + 1] - M->cv_off[dst];
+    if (conn_cv[s] < 0 || conn_cv[s] >= ncv) { orc_free(M); return fail(-1, "connection %lld: bad cv", (long long)s); }
+    if (mj < 0 || mj >= n_mech || !is_point(M->mech[mj].kind)) {
+      orc_free(M); return fail(-1, "connection %lld: mechanism must be a synapse", (long long)s);
+    }
+    const orc_mech* mc = &M->mech[mj];
+    M->syn_cell[s] = dst;
+    M->syn_mech[s] = mj;
+    M->syn_src[s] = src;
+    M->syn_cv[s] = M->cv_off[dst] + conn_cv[s];
+    M->syn_weight[s] = conn_weight[s];
+    if (src == ORC_SRC_POISSON) {
+      double x = ((conn_rate[s] * dt) * 1e-3) * 4294967296.0;
+      if (!(x >= 0) || x >= 4294967296.0) { orc_free(M); return fail(-1, "connection %lld: rate*dt out of range", (long long)s); }
+      M->syn_thr[s] = (uint32_t)floor(x);
+      M->syn_D[s] = 0;
+      M->poisson_syn[M->n_poisson++] = s;
+    } else {
+      if (src < 0 || src >= n_cells) { orc_free(M); return fail(-1, "connection %lld: bad src", (long long)s); }
+      M->syn_D[s] = llround(conn_delay[s] / dt);
+      if (M->syn_D[s] < 1) { orc_free(M); return fail(-1, "connection %lld: delay below one step", (long long)s); }
+      M->out_off[src + 1]++;
+    }
+    int64_t tot = M->syn_D[s] + ((mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC) ? mc->dc_steps : 0);
+    if (tot > maxdelay) maxdelay = tot;
+    /* initial synapse state (readings): GB w = w0; STC h = h0, z = 0, p = 0;
+       STDP w = w0; all conductances, calcium and traces start at zero */
+    if (mc->kind == ORC_MECH_GB) M->w[s] = mc->p[12];
+    if (mc->kind == ORC_MECH_STC) {
+      M->hs[s] = mc->p[12];
+      if (M->cell_stc_mech[dst] >= 0 && M->cell_stc_mech[dst] != mj) {
+        orc_free(M); return fail(-1, "cell %d: STC synapses must share one mechanism", dst);
+      }
+      M->cell_stc_mech[dst] = mj;
+    }
+    if (mc->kind == ORC_MECH_STDP) M->w[s] = mc->p[6];
+  }
+  for (int32_t c = 0; c < n_cells; ++c) M->out_off[c + 1] += M->out_off[c];
+  ALLOC(M->out_syn, M->out_off[n_cells]);
+  {
+    int64_t* fill = (int64_t*)calloc((size_t)n_cells + 1, sizeof(int64_t));
+    for (int64_t s = 0; s < n_conn; ++s) {
+      if (conn_src[s] == ORC_SRC_POISSON) continue;
+      int32_t src = conn_src[s];
+      M->out_syn[M->out_off[src] + fill[src]++] = s;
+    }
+    free(fill);
+  }
+  /* canonical synapse order of each cell: (mechanism, CV, connection) */
+  ALLOC(M->cell_syn_off, n_cells + 1);
+  for (int64_t s = 0; s < n_conn; ++s) M->cell_syn_off[M->syn_cell[s] + 1]++;
+  for (int32_t c = 0; c < n_cells; ++c) M->cell_syn_off[c + 1] += M->cell_syn_off[c];
+  ALLOC(M->cell_syn, n_conn);
+  {
+    int64_t* fill = (int64_t*)calloc((size_t)n_cells + 1, sizeof(int64_t));
+    for (int64_t s = 0; s < n_conn; ++s) {
+      int32_t c = M->syn_cell[s];
+      M->cell_syn[M->cell_syn_off[c] + fill[c]++] = s;
+    }
+    free(fill);
+  }
+  g_sort_model = M;
+  for (int32_t c = 0; c < n_cells; ++c)
+    qsort(M->cell_syn + M->cell_syn_off[c], (size_t)(M->cell_syn_off[c + 1] - M->cell_syn_off[c]),
+          sizeof(int64_t), cmp_syn);
+  M->R = maxdelay + 2;
+  M->q = (orc_bucket*)calloc((size_t)M->R, sizeof(orc_bucket));
+  M->n_probe = n_probe;
+  ALLOC(M->probe_cv, n_probe);
+  for (int32_t i = 0; i < n_probe; ++i) {
+    int32_t gid = probe_gid[i];
+    if (gid < 0 || gid >= n_cells || probe_cv[i] < 0 ||
+        probe_cv[i] >= M->cv_off[gid + 1] - M->cv_off[gid]) {
+      orc_free(M); return fail(-1, "probe %d: bad location", i);
+    }
+    M->probe_cv[i] = M->cv_off[gid] + probe_cv[i];
+  }
+  *out = M;
+  return 0;
+}
+
+int orc_set_replay(orc_model* M, int64_t n, const int32_t* gid, const int64_t* step) {
+  free(M->rep_gid);
+  free(M->rep_step);
+  ALLOC(M->rep_gid, n);
+  ALLOC(M->rep_step, n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (i > 0 && step[i] < step[i - 1]) return fail(-1, "replay spikes must be sorted by step");
+    M->rep_gid[i] = gid[i];
+    M->rep_step[i] = step[i];
+  }
+  M->n_rep = n;
+  M->rep_pos = 0;
+  M->replay = 1;
+  while (M->rep_pos < n && M->rep_step[M->rep_pos] < M->step) M->rep_pos++;
+  return 0;
+}
+
+/* pre event on synapse s (conductance jump; STDP pre update, Eqs.
+   stdp_ode_1 and stdp_ode_3 with the conductance contribution clipped at w_max) */
+static void pre_event(orc_model* M, int64_t s) {
+  const orc_mech* mc = &M->mech[M->syn_mech[s]];
+  switch (mc->kind) {
+    case ORC_MECH_EXPSYN:
+    case ORC_MECH_GB:
+      M->g[s] += M->syn_weight[s];
+      break;
+    case ORC_MECH_STC: {
+      /* Eq. total_syn_weight: w = h + h0 z, as a multiple of its baseline h0 */
+      double h0 = mc->p[12];
+      M->g[s] += M->syn_weight[s] * ((M->hs[s] + h0 * M->z[s]) / h0);
+      break;
+    }
+    case ORC_MECH_STDP: {
+      double wc = M->w[s];
+      if (wc < 0.0) wc = 0.0;
+      if (wc > mc->p[7]) wc = mc->p[7];
+      M->g[s] += M->syn_weight[s] * wc;
+      M->apre[s] += mc->p[4];
+      M->w[s] += M->apost[s];
+      break;
+    }
+  }
+}
+
+/* delayed presynaptic calcium jump c_pre (Eq. ca_model_graupner_brunel) */
+static void ca_event(orc_model* M, int64_t s) {
+  const orc_mech* mc = &M->mech[M->syn_mech[s]];
+  if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC) M->c[s] += mc->p[3];
+}
+
+/* POST_EVENT -- postsynaptic calcium jump c_post; STDP post update
+   (Eqs. stdp_ode_2 and stdp_ode_3) */
+static void post_event(orc_model* M, int64_t s) {
+  const orc_mech* mc = &M->mech[M->syn_mech[s]];
+  if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC) M->c[s] += mc->p[4];
+  if (mc->kind == ORC_MECH_STDP) {
+    M->apost[s] += mc->p[5];
+    M->w[s] += M->apre[s];
+  }
+}
+
+static void queue_spike_events(orc_model* M, int32_t gid, int64_t k) {
+  for (int64_t e = M->out_off[gid]; e < M->out_off[gid + 1]; ++e) {
+    int64_t s = M->out_syn[e];
+    const orc_mech* mc = &M->mech[M->syn_mech[s]];
+    push_ev(&M->q[(k + M->syn_D[s]) % M->R], (int32_t)s, 0);
+    if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC)
+      push_ev(&M->q[(k + M->syn_D[s] + mc->dc_steps) % M->R], (int32_t)s, 1);
+  }
+}
+
+/* steps 2-5 for one cell */
+static void cell_step(orc_model* M, int32_t c, int64_t k) {
+  const double dt = M->dt;
+  int64_t base = M->cv_off[c], n = M->cv_off[c + 1] - base;
+  const int32_t* par = M->parent + base;
+  double *V = M->V + base, *gs = M->gs + base, *es = M->es + base;
+  double *d = M->d + base, *b = M->b + base;
+  for (int64_t i = 0; i < n; ++i) { gs[i] = 0.0; es[i] = 0.0; }
+  /* synaptic conductances summed per CV in the cell's canonical order */
+  for (int64_t j = M->cell_syn_off[c]; j < M->cell_syn_off[c + 1]; ++j) {
+    int64_t s = M->cell_syn[j];
+    int64_t i = M->syn_cv[s] - base;
+    double E = M->mech[M->syn_mech[s]].p[1];
+    gs[i] = gs[i] + M->g[s];
+    es[i] = es[i] + M->g[s] * E;
+  }
+  double iinj = (k >= M->k_on[c] && k < M->k_off[c]) ? M->istep[c] : 0.0;
+  /* backward-Euler matrix: (C/dt + sum g_axial + g_m) V^{k+1} - sum g_axial V_nb^{k+1}
+     = C/dt V^k + sum g E + I_inj */
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t gi = base + i;
+    const orc_mech* mc = &M->mech[M->cv_mech[gi]];
+    double gm, em;
+    if (mc->kind == ORC_MECH_PAS) {
+      gm = M->gpas[gi];
+      em = M->em_pas[gi];
+    } else {
+      double mv = M->m[gi], hv = M->h[gi], nv = M->n[gi];
+      double gna = M->gna_a[gi] * (((mv * mv) * mv) * hv);
+      double gk = M->gk_a[gi] * (((nv * nv) * nv) * nv);
+      gm = (gna + gk) + M->gl_a[gi];
+      em = ((gna * mc->p[3]) + (gk * mc->p[4])) + (M->gl_a[gi] * mc->p[5]);
+    }
+    d[i] = ((M->cdt[gi] + M->gax[gi]) + gm) + gs[i];
+    b[i] = (fma(M->cdt[gi], V[i], em) + (i == 0 ? iinj : 0.0)) + es[i];
+  }
+  double v0_old = V[0];
+  double* xnew = M->xnew + base;
+  hines(n, par, d, M->a + base, b, M->f + base, M->xp + base, xnew);
+  for (int64_t i = 0; i < n; ++i) V[i] = xnew[i];
+  /* HH gates at V^{k+1} */
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t gi = base + i;
+    if (M->mech[M->cv_mech[gi]].kind != ORC_MECH_HH) continue;
+    double am, bm, ah, bh, an, bn;
+    orc_hh_rates(V[i], &am, &bm, &ah, &bh, &an, &bn);
+    M->m[gi] = cnexp_gate(M->m[gi], am, bm, dt);
+    M->h[gi] = cnexp_gate(M->h[gi], ah, bh, dt);
+    M->n[gi] = cnexp_gate(M->n[gi], an, bn, dt);
+  }
+  /* synapse state updates with the post-event values of step k */
+  double S = 0.0, pk = M->p[c];
+  for (int64_t j = M->cell_syn_off[c]; j < M->cell_syn_off[c + 1]; ++j) {
+    int64_t s = M->cell_syn[j];
+    const orc_mech* mc = &M->mech[M->syn_mech[s]];
+    const double* q = mc->p;
+    M->g[s] = M->g[s] * mc->decay_g;
+    if (mc->kind == ORC_MECH_GB) {
+      /* Eq. weight_graupner_brunel (sigma_pl = 0), forward Euler */
+      double w = M->w[s], cc = M->c[s];
+      double A = (w * (1.0 - w)) * (q[10] - w);
+      double P = (cc > q[5]) ? q[7] * (1.0 - w) : 0.0;
+      double D = (cc > q[6]) ? q[8] * w : 0.0;
+      M->w[s] = w + mc->rate_w * ((P - A) - D);
+      M->c[s] = cc * mc->decay_c;
+    } else if (mc->kind == ORC_MECH_STC) {
+      double h = M->hs[s], z = M->z[s], cc = M->c[s], h0 = q[12];
+      S = S + fabs(h - h0);
+      /* Eq. late_phase_weight with the cell's PRP p^k */
+      double T1 = ((h - h0) > q[13]) ? (pk * q[16]) * (1.0 - z) : 0.0;
+      double T2 = ((h0 - h) > q[13]) ? (pk * q[16]) * (z + 0.5) : 0.0;
+      M->z[s] = z + mc->rate_z * (T1 - T2);
+      /* Eq. early_phase_weight (sigma_pl = 0), 10 mV potentiation ceiling */
+      double P = (cc > q[5]) ? q[7] * (10.0 - h) : 0.0;
+      double D = (cc > q[6]) ? q[8] * h : 0.0;
+      M->hs[s] = h + mc->rate_h * ((0.1 * (h0 - h) + P) - D);
+      M->c[s] = cc * mc->decay_c;
+    } else if (mc->kind == ORC_MECH_STDP) {
+      M->apre[s] = M->apre[s] * mc->decay_pre;
+      M->apost[s] = M->apost[s] * mc->decay_post;
+    }
+  }
+  if (M->cell_stc_mech[c] >= 0) {
+    /* Eq. prp_single_comp: synthesis while the summed early-phase change
+       exceeds theta_pro */
+    const orc_mech* mc = &M->mech[M->cell_stc_mech[c]];
+    double qs = (S > mc->p[14]) ? mc->p[15] : 0.0;
+    M->p[c] = pk + mc->rate_p * (qs - pk);
+  }
+  /* threshold detection at the soma CV with linear interpolation of the time */
+  double th = M->thresh[c];
+  M->spk_flag[c] = 0;
+  if (v0_old < th && V[0] >= th) {
+    M->spk_flag[c] = 1;
+    M->spk_t[c] = (double)k * dt + dt * ((th - v0_old) / (V[0] - v0_old));
+  }
+}
+
+int orc_run(orc_model* M, int64_t n_steps) {
+  for (int64_t it = 0; it < n_steps; ++it) {
+    int64_t k = M->step;
+    orc_bucket* bk = &M->q[k % M->R];
+    for (int64_t e = 0; e < bk->n; ++e)
+      if (bk->v[e].type == 0) pre_event(M, bk->v[e].syn);
+    for (int64_t i = 0; i < M->n_poisson; ++i) {
+      int64_t s = M->poisson_syn[i];
+      if (orc_poisson_u32(M->seed, (uint64_t)s, k) < M->syn_thr[s]) {
+        const orc_mech* mc = &M->mech[M->syn_mech[s]];
+        pre_event(M, s);
+        if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC)
+          push_ev(&M->q[(k + mc->dc_steps) % M->R], (int32_t)s, 1);
+      }
+    }
+    for (int64_t e = 0; e < bk->n; ++e)
+      if (bk->v[e].type == 1) ca_event(M, bk->v[e].syn);
+    bk->n = 0;
+    for (int32_t c = 0; c < M->n_cells; ++c) {
+      if (!M->spiked_prev[c]) continue;
+      for (int64_t j = M->cell_syn_off[c]; j < M->cell_syn_off[c + 1]; ++j)
+        post_event(M, M->cell_syn[j]);
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int32_t c = 0; c < M->n_cells; ++c) cell_step(M, c, k);
+    for (int32_t c = 0; c < M->n_cells; ++c) {
+      if (M->spk_flag[c]) {
+        if (M->n_spk == M->cap_spk) {
+          M->cap_spk = M->cap_spk ? 2 * M->cap_spk : 1024;
+          M->spk_gid = (int32_t*)realloc(M->spk_gid, sizeof(int32_t) * (size_t)M->cap_spk);
+          M->spk_step = (int64_t*)realloc(M->spk_step, sizeof(int64_t) * (size_t)M->cap_spk);
+          M->spk_time = (double*)realloc(M->spk_time, sizeof(double) * (size_t)M->cap_spk);
+        }
+        M->spk_gid[M->n_spk] = c;
+        M->spk_step[M->n_spk] = k;
+        M->spk_time[M->n_spk] = M->spk_t[c];
+        M->n_spk++;
+      }
+    }
+    if (!M->replay) {
+      for (int32_t c = 0; c < M->n_cells; ++c) {
+        M->spiked_prev[c] = M->spk_flag[c];
+        if (M->spk_flag[c]) queue_spike_events(M, c, k);
+      }
+    } else {
+      for (int32_t c = 0; c < M->n_cells; ++c) M->spiked_prev[c] = 0;
+      while (M->rep_pos < M->n_rep && M->rep_step[M->rep_pos] == k) {
+        int32_t gid = M->rep_gid[M->rep_pos++];
+        if (gid < 0 || gid >= M->n_cells) continue;
+        M->spiked_prev[gid] = 1;
+        queue_spike_events(M, gid, k);
+      }
+    }
+    if (M->n_probe > 0) {
+      if (M->n_samples == M->cap_samples) {
+        M->cap_samples = M->cap_samples ? 2 * M->cap_samples : 1024;
+        M->probes = (double*)realloc(M->probes, sizeof(double) * (size_t)M->cap_samples * (size_t)M->n_probe);
+      }
+      for (int32_t i = 0; i < M->n_probe; ++i)
+        M->probes[M->n_samples * M->n_probe + i] = M->V[M->probe_cv[i]];
+      M->n_samples++;
+    }
+    M->step++;
+  }
+  return 0;
+}
+
+int64_t orc_step_count(const orc_model* M) { return M->step; }
+int64_t orc_n_spikes(const orc_model* M) { return M->n_spk; }
+void orc_get_spikes(const orc_model* M, int32_t* gid, int64_t* step, double* t) {
+  for (int64_t i = 0; i < M->n_spk; ++i) {
+    if (gid) gid[i] = M->spk_gid[i];
+    if (step) step[i] = M->spk_step[i];
+    if (t) t[i] = M->spk_time[i];
+  }
+}
+int64_t orc_n_cv(const orc_model* M) { return M->n_cv; }
+void orc_get_v(const orc_model* M, double* out) { memcpy(out, M->V, sizeof(double) * (size_t)M->n_cv); }
+int64_t orc_n_probe_samples(const orc_model* M) { return M->n_samples; }
+void orc_get_probes(const orc_model* M, double* out) {
+  if (M->n_samples * M->n_probe > 0)
+    memcpy(out, M->probes, sizeof(double) * (size_t)(M->n_samples * M->n_probe));
+}
+void orc_get_syn(const orc_model* M, int32_t field, double* out) {
+  for (int64_t s = 0; s < M->n_syn; ++s) {
+    const orc_mech* mc = &M->mech[M->syn_mech[s]];
+    double v = 0.0;
+    switch (field) {
+      case ORC_SYN_G: v = M->g[s]; break;
+      case ORC_SYN_C: v = M->c[s]; break;
+      case ORC_SYN_W: v = M->w[s]; break;
+      case ORC_SYN_H: v = M->hs[s]; break;
+      case ORC_SYN_Z: v = M->z[s]; break;
+      case ORC_SYN_APRE: v = M->apre[s]; break;
+      case ORC_SYN_APOST: v = M->apost[s]; break;
+      case ORC_SYN_WEIGHT_TOTAL:
+        if (mc->kind == ORC_MECH_STC) v = M->hs[s] + mc->p[12] * M->z[s];
+        else if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STDP) v = M->w[s];
+        else v = M->syn_weight[s];
+        break;
+    }
+    out[s] = v;
+  }
+}
+void orc_get_cell_p(const orc_model* M, double* out) {
+  memcpy(out, M->p, sizeof(double) * (size_t)M->n_cells);
+}
+void orc_get_gates(const orc_model* M, double* out) {
+  for (int32_t c = 0; c < M->n_cells; ++c) {
+    int64_t gi = M->cv_off[c];
+    out[3 * c] = M->m[gi];
+    out[3 * c + 1] = M->h[gi];
+    out[3 * c + 2] = M->n[gi];
+  }
+}
+void orc_get_cv_geometry(const orc_model* M, double* cap_nF, double* gpas_uS, double* a_uS) {
+  for (int64_t i = 0; i < M->n_cv; ++i) {
+    if (cap_nF) cap_nF[i] = M->cap[i];
+    if (gpas_uS) gpas_uS[i] = M->gpas[i];
+    if (a_uS) a_uS[i] = M->a[i];
+  }
+}

@@ -1,0 +1,385 @@
+"""Seeded synthetic inputs: morphologies, cells, mechanism tables, connections.
+
+This module only *describes* networks (shapes, parameter tables, random
+connectivity).  It holds none of the simulated method's arithmetic, so both the
+CUDA engine and the CPU oracle can be fed from it.  The workloads follow the
+configurations the engine is measured on, with the paper's parameter tables
+(Tables 3 and 5) and the readings listed in the design notes where the
+configurations are silent.
+
+Units: mV, ms, um, uS (weights), nA, S/cm2, uF/cm2, ohm cm.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+# Mechanism kinds (descriptor format shared by the engine's C-ABI and the oracle).
+PAS, HH, EXPSYN, GB, STC, STDP = 1, 2, 10, 11, 12, 13
+SRC_POISSON = -1
+NEVER = 1e300  # t_off meaning "never switched off"
+
+MASTER_SEED = 20241125
+
+
+def config_seed(name: str, master: int = MASTER_SEED) -> int:
+    """Per-workload seed: an FNV-style integer hash of the workload name and the master seed."""
+    h = master & 0xFFFFFFFFFFFFFFFF
+    for ch in name.encode():
+        h = ((h ^ ch) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+# --------------------------------------------------------------------------
+# parameter tables
+def hh_params(gnabar=0.12, gkbar=0.036, gl=3e-4, ena=50.0, ek=-77.0, el=-54.4):
+    return np.array([gnabar, gkbar, gl, ena, ek, el])
+
+
+def pas_params(g=3e-5, e=-54.4):
+    return np.array([g, e])
+
+
+def expsyn_params(tau=5.0, e=0.0):
+    return np.array([tau, e])
+
+
+def gb_params(tau=5.0, e=0.0, tau_c=20.0, c_pre=1.0, c_post=2.0, theta_p=1.3, theta_d=1.0,
+              gamma_p=725.0, gamma_d=331.0, tau_w=346.0e3, w_star=0.5, t_c_delay=13.7, w0=0.0):
+    """Graupner-Brunel calcium rule (Eqs. weight_graupner_brunel, ca_model_graupner_brunel).
+    Defaults: the single-neuron workload's constants; w_star and t_c_delay from Table 3."""
+    return np.array([tau, e, tau_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_w,
+                     w_star, t_c_delay, w0])
+
+
+def stc_params(tau=5.0, e=0.0, tau_c=48.8, c_pre=0.6, c_post=0.1655, theta_p=3.0, theta_d=1.2,
+               gamma_p=1645.6, gamma_d=313.1, tau_h=688.4e3, tau_z=3600.0e3, tau_p=3600.0e3,
+               h0=4.20075, theta_tag=0.840149, theta_pro=2.10037, p_max=10.0, f_int=0.1,
+               t_c_delay=18.8):
+    """Tagging-and-capture rule (Eqs. total_syn_weight .. prp_single_comp), Table 5 with
+    the in-vivo calcium contributions used for networks."""
+    return np.array([tau, e, tau_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_h,
+                     tau_z, tau_p, h0, theta_tag, theta_pro, p_max, f_int, t_c_delay])
+
+
+def stdp_params(tau=5.0, e=0.0, tau_pre=16.8, tau_post=33.7, a_pre=0.01, a_post=-0.012,
+                w0=0.5, w_max=1.0):
+    """Pair STDP (Eqs. stdp_ode_1-3); w dimensionless, conductance weight*clip(w, 0, w_max)."""
+    return np.array([tau, e, tau_pre, tau_post, a_pre, a_post, w0, w_max])
+
+
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Morphology:
+    parent: np.ndarray   # int32, parent[0] = -1, parent[i] < i
+    length: np.ndarray   # float64 um
+    diam: np.ndarray     # float64 um
+    region: np.ndarray   # int32: 0 soma, 1 dendrite
+
+    @property
+    def n_cv(self) -> int:
+        return int(self.parent.shape[0])
+
+    def is_chain(self) -> bool:
+        return bool(np.all(self.parent[1:] == np.arange(self.n_cv - 1)))
+
+
+@dataclasses.dataclass
+class Network:
+    dt: float
+    seed: int
+    mech_kind: np.ndarray                  # int32 [M]
+    mech_params: List[np.ndarray]
+    morphs: List[Morphology]
+    cell_morph: np.ndarray                 # int32 [N]
+    cell_soma_mech: np.ndarray
+    cell_dend_mech: np.ndarray
+    cell_cm: np.ndarray                    # float64 [N]
+    cell_ra: np.ndarray
+    cell_istep: np.ndarray
+    cell_ton: np.ndarray
+    cell_toff: np.ndarray
+    cell_vinit: np.ndarray
+    cell_thresh: np.ndarray
+    conn_src: np.ndarray                   # int32 [C]
+    conn_dst: np.ndarray
+    conn_cv: np.ndarray
+    conn_mech: np.ndarray
+    conn_weight: np.ndarray                # float64 [C]
+    conn_delay: np.ndarray
+    conn_rate: np.ndarray
+    name: str = "custom"
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cell_morph.shape[0])
+
+    @property
+    def n_conn(self) -> int:
+        return int(self.conn_src.shape[0])
+
+    def cell_ncv(self) -> np.ndarray:
+        sizes = np.array([m.n_cv for m in self.morphs], dtype=np.int64)
+        return sizes[self.cell_morph]
+
+    @property
+    def n_cv(self) -> int:
+        return int(self.cell_ncv().sum())
+
+    def packed_morphs(self):
+        ncv = np.array([m.n_cv for m in self.morphs], dtype=np.int32)
+        off = np.zeros(len(self.morphs), dtype=np.int32)
+        if len(self.morphs) > 1:
+            off[1:] = np.cumsum(ncv[:-1])
+
+        def cat(f, dt_):
+            if not self.morphs:
+                return np.zeros(0, dt_)
+            return np.concatenate([getattr(m, f) for m in self.morphs]).astype(dt_)
+
+        return (ncv, off, cat("parent", np.int32), cat("length", np.float64),
+                cat("diam", np.float64), cat("region", np.int32))
+
+    def packed_mechs(self):
+        off = np.zeros(len(self.mech_params), dtype=np.int32)
+        sizes = [len(p) for p in self.mech_params]
+        if len(sizes) > 1:
+            off[1:] = np.cumsum(sizes[:-1])
+        params = (np.concatenate(self.mech_params).astype(np.float64)
+                  if self.mech_params else np.zeros(0))
+        return self.mech_kind.astype(np.int32), off, params
+
+
+class _Builder:
+    """Accumulates mechanisms, morphologies, cells and connections."""
+
+    def __init__(self, dt: float, seed: int, name: str):
+        self.dt, self.seed, self.name = dt, seed, name
+        self.mk, self.mp, self.morphs = [], [], []
+        self.cells = {k: [] for k in ("morph", "soma", "dend", "cm", "ra", "istep", "ton", "toff",
+                                      "vinit", "thresh")}
+        self.conn = {k: [] for k in ("src", "dst", "cv", "mech", "w", "delay", "rate")}
+
+    def mech(self, kind: int, params) -> int:
+        self.mk.append(kind)
+        self.mp.append(np.asarray(params, dtype=np.float64))
+        return len(self.mk) - 1
+
+    def morph(self, m: Morphology) -> int:
+        self.morphs.append(m)
+        return len(self.morphs) - 1
+
+    def cells_add(self, n, morph, soma, dend, cm=1.0, ra=100.0, istep=0.0, ton=0.0, toff=NEVER,
+                  vinit=-65.0, thresh=-10.0) -> np.ndarray:
+        start = len(self.cells["morph"])
+        for k, v in (("morph", morph), ("soma", soma), ("dend", dend), ("cm", cm), ("ra", ra),
+                     ("istep", istep), ("ton", ton), ("toff", toff), ("vinit", vinit),
+                     ("thresh", thresh)):
+            self.cells[k].extend(np.broadcast_to(np.asarray(v), (n,)).tolist())
+        return np.arange(start, start + n)
+
+    def connect(self, src, dst, cv, mech, w, delay=0.0, rate=0.0) -> None:
+        n = len(np.atleast_1d(dst))
+        for k, v in (("src", src), ("dst", dst), ("cv", cv), ("mech", mech), ("w", w),
+                     ("delay", delay), ("rate", rate)):
+            self.conn[k].extend(np.broadcast_to(np.asarray(v), (n,)).tolist())
+
+    def build(self) -> Network:
+        c, k = self.cells, self.conn
+        i32 = lambda x: np.asarray(x, dtype=np.int32)
+        f64 = lambda x: np.asarray(x, dtype=np.float64)
+        return Network(
+            dt=self.dt, seed=self.seed, mech_kind=i32(self.mk), mech_params=self.mp,
+            morphs=self.morphs, cell_morph=i32(c["morph"]), cell_soma_mech=i32(c["soma"]),
+            cell_dend_mech=i32(c["dend"]), cell_cm=f64(c["cm"]), cell_ra=f64(c["ra"]),
+            cell_istep=f64(c["istep"]), cell_ton=f64(c["ton"]), cell_toff=f64(c["toff"]),
+            cell_vinit=f64(c["vinit"]), cell_thresh=f64(c["thresh"]), conn_src=i32(k["src"]),
+            conn_dst=i32(k["dst"]), conn_cv=i32(k["cv"]), conn_mech=i32(k["mech"]),
+            conn_weight=f64(k["w"]), conn_delay=f64(k["delay"]), conn_rate=f64(k["rate"]),
+            name=self.name)
+
+
+# --------------------------------------------------------------------------
+# morphologies
+def ball_and_stick(soma_diam=20.0, dend_len=500.0, dend_diam=1.0, n_dend=64) -> Morphology:
+    """Soma: one cylinder with length = diameter (lateral area of the sphere).
+    Dendrite: n_dend equal cylinders in a chain from the soma."""
+    n = 1 + n_dend
+    parent = np.arange(-1, n - 1, dtype=np.int32)
+    length = np.full(n, dend_len / max(n_dend, 1))
+    diam = np.full(n, dend_diam)
+    length[0], diam[0] = soma_diam, soma_diam
+    region = np.ones(n, dtype=np.int32)
+    region[0] = 0
+    return Morphology(parent, length, diam, region)
+
+
+def soma_only(diam=20.0) -> Morphology:
+    return Morphology(np.array([-1], np.int32), np.array([diam]), np.array([diam]),
+                      np.array([0], np.int32))
+
+
+def random_binary_tree(rng: np.random.Generator, n_dend: int, soma_diam=20.0,
+                       branch_len=(20.0, 100.0), max_cv_len=20.0, diam_root=2.0,
+                       diam_tip=0.5) -> Morphology:
+    """Random binary dendritic tree of exactly n_dend CVs on a soma CV.
+
+    Grows branches from the soma by splitting a uniformly chosen open tip into
+    two child branches; each branch has a length ~ U(branch_len) discretised
+    into CVs of at most max_cv_len; growth stops at n_dend CVs (the last branch
+    is truncated).  Diameters taper linearly with branch order from diam_root
+    (order 0) to diam_tip (deepest order).  CVs are numbered depth-first so
+    parent[i] < i."""
+    branches = []  # (parent_branch, order, n_cv, cv_len)
+    remaining = n_dend
+    tips = []
+
+    def new_branch(pb, order):
+        nonlocal remaining
+        L = rng.uniform(*branch_len)
+        full = max(1, int(math.ceil(L / max_cv_len)))
+        ncv = min(full, remaining)
+        branches.append((pb, order, ncv, L / full))
+        remaining -= ncv
+        tips.append(len(branches) - 1)
+
+    new_branch(-1, 0)
+    while remaining > 0:
+        t = tips.pop(int(rng.integers(len(tips))))
+        new_branch(t, branches[t][1] + 1)
+        if remaining > 0:
+            new_branch(t, branches[t][1] + 1)
+    max_order = max(b[1] for b in branches)
+    children = [[] for _ in branches]
+    for i, b in enumerate(branches):
+        if b[0] >= 0:
+            children[b[0]].append(i)
+    parent, length, diam = [-1], [soma_diam], [soma_diam]
+    stack = [(0, 0)]  # (branch, parent CV)
+    while stack:
+        bi, pcv = stack.pop()
+        _, order, ncv, cvl = branches[bi]
+        dia = diam_root + (diam_tip - diam_root) * (order / max_order if max_order else 0.0)
+        for j in range(ncv):
+            parent.append(pcv if j == 0 else len(parent) - 1)
+            length.append(cvl)
+            diam.append(dia)
+        last = len(parent) - 1
+        for ch in reversed(children[bi]):
+            stack.append((ch, last))
+    region = np.ones(len(parent), dtype=np.int32)
+    region[0] = 0
+    return Morphology(np.asarray(parent, np.int32), np.asarray(length), np.asarray(diam), region)
+
+
+# --------------------------------------------------------------------------
+# workloads
+def single_neuron(dt: float = 0.025, seed: Optional[int] = None, w_syn: float = 1e-3) -> Network:
+    """Plain FP64 single ball-and-stick neuron with one calcium-plastic synapse at the
+    dendrite midpoint, 10 Hz Poisson input and a 0.5 nA somatic step."""
+    b = _Builder(dt, config_seed("single_neuron") if seed is None else seed, "single_neuron")
+    hh = b.mech(HH, hh_params())
+    pas = b.mech(PAS, pas_params(3e-5, -54.4))
+    gb = b.mech(GB, gb_params())
+    m = b.morph(ball_and_stick(20.0, 500.0, 1.0, 64))
+    b.cells_add(1, m, hh, pas, istep=0.5)
+    b.connect(SRC_POISSON, 0, 1 + 64 // 2, gb, w_syn, rate=10.0)
+    return b.build()
+
+
+def recurrent_stc(n_exc=1600, n_inh=400, p=0.1, dt=0.2, seed=None, w_bg=1e-3,
+                  bg_rate=5.0) -> Network:
+    """Plain FP64 recurrent network: HH ball-and-stick cells with an 8-CV 200 um
+    dendrite; Erdos-Renyi connectivity without self-loops; 3 ms delays; weights
+    1 nS * U(0.9, 1.1); E->E synapses follow the tagging-and-capture rule; all
+    other synapses are static; every cell receives 5 Hz Poisson background."""
+    name = "recurrent_stc"
+    b = _Builder(dt, config_seed(name) if seed is None else seed, name)
+    rng = np.random.default_rng(b.seed)
+    hh = b.mech(HH, hh_params())
+    pas = b.mech(PAS, pas_params(3e-5, -54.4))
+    exc = b.mech(EXPSYN, expsyn_params(5.0, 0.0))
+    inh = b.mech(EXPSYN, expsyn_params(5.0, -80.0))
+    stc = b.mech(STC, stc_params())
+    m = b.morph(ball_and_stick(20.0, 200.0, 1.0, 8))
+    n = n_exc + n_inh
+    b.cells_add(n, m, hh, pas)
+    adj = rng.random((n, n)) < p
+    np.fill_diagonal(adj, False)
+    src, dst = np.nonzero(adj)  # row-major: sorted by source
+    w = 1e-3 * rng.uniform(0.9, 1.1, size=src.shape[0])
+    e_src = src < n_exc
+    mech = np.where(e_src, np.where(dst < n_exc, stc, exc), inh)
+    cv = np.where(e_src, rng.integers(1, 9, size=src.shape[0]), 0)
+    b.connect(src, dst, cv, mech, w, delay=3.0)
+    b.connect(SRC_POISSON, np.arange(n), 0, exc, w_bg, rate=bg_rate)
+    return b.build()
+
+
+def morphology_sweep(n_nets=64, cells_per_net=500, p=0.1, dt=0.2, seed=None,
+                     w_syn=1e-3, drive_hz=10.0) -> Network:
+    """Many independent networks built like the single-neuron workload: per network a
+    dendrite length L ~ U(100, 800) um with 4 + round(60 (L - 100) / 700) CVs and a
+    diameter ~ U(0.5, 2) um; recurrent p, 3 ms delays, calcium-plastic synapses,
+    10 Hz Poisson drive on the midpoint synapse and the 0.5 nA somatic step."""
+    name = "morphology_sweep"
+    b = _Builder(dt, config_seed(name) if seed is None else seed, name)
+    rng = np.random.default_rng(b.seed)
+    hh = b.mech(HH, hh_params())
+    pas = b.mech(PAS, pas_params(3e-5, -54.4))
+    gb = b.mech(GB, gb_params())
+    for _ in range(n_nets):
+        L = rng.uniform(100.0, 800.0)
+        nd = 4 + int(round(60.0 * (L - 100.0) / 700.0))
+        dia = rng.uniform(0.5, 2.0)
+        m = b.morph(ball_and_stick(20.0, L, dia, nd))
+        cells = b.cells_add(cells_per_net, m, hh, pas, istep=0.5)
+        adj = rng.random((cells_per_net, cells_per_net)) < p
+        np.fill_diagonal(adj, False)
+        s, d = np.nonzero(adj)
+        b.connect(cells[s], cells[d], rng.integers(1, nd + 1, size=s.shape[0]), gb, w_syn,
+                  delay=3.0)
+        b.connect(SRC_POISSON, cells, 1 + nd // 2, gb, w_syn, rate=drive_hz)
+    return b.build()
+
+
+def large_stdp(n_cells=100_000, fan_in=100, dt=0.025, seed=None, n_dend=(50, 500),
+               w_syn=1e-3, w_drive=0.05, drive_hz=2.0, delay_ms=(1.0, 5.0),
+               n_shapes: Optional[int] = None) -> Network:
+    """Large network of HH-soma cells on random binary dendritic trees of 50-500
+    dendritic CVs; fixed fan-in of `fan_in` uniform random presynaptic cells per
+    cell with pair-STDP synapses on uniform random dendritic CVs and delays of
+    1-5 ms; every cell also receives a 2 Hz Poisson drive on a static somatic
+    synapse.  n_shapes, if given, draws that many tree shapes and assigns them
+    to cells uniformly (a cheaper generator for very large networks)."""
+    name = "large_stdp"
+    b = _Builder(dt, config_seed(name) if seed is None else seed, name)
+    rng = np.random.default_rng(b.seed)
+    hh = b.mech(HH, hh_params())
+    pas = b.mech(PAS, pas_params(3e-5, -54.4))
+    stdp = b.mech(STDP, stdp_params())
+    drive = b.mech(EXPSYN, expsyn_params(5.0, 0.0))
+    n_trees = n_cells if n_shapes is None else n_shapes
+    tree_sizes = rng.integers(n_dend[0], n_dend[1] + 1, size=n_trees)
+    for t in range(n_trees):
+        b.morph(random_binary_tree(rng, int(tree_sizes[t])))
+    morph_ids = np.arange(n_cells) if n_shapes is None else rng.integers(0, n_trees, n_cells)
+    sizes = tree_sizes[morph_ids]
+    cells = np.arange(n_cells)
+    b.cells["morph"].extend(morph_ids.tolist())
+    for k, v in (("soma", hh), ("dend", pas), ("cm", 1.0), ("ra", 100.0), ("istep", 0.0),
+                 ("ton", 0.0), ("toff", NEVER), ("vinit", -65.0), ("thresh", -10.0)):
+        b.cells[k].extend([v] * n_cells)
+    src = rng.integers(0, n_cells - 1, size=(n_cells, fan_in))
+    src = (src + (src >= cells[:, None])).reshape(-1)   # no self-connections
+    dst = np.repeat(cells, fan_in)
+    cv = 1 + (rng.random(dst.shape[0]) * sizes[dst]).astype(np.int64)
+    steps = rng.integers(int(round(delay_ms[0] / dt)), int(round(delay_ms[1] / dt)) + 1,
+                         size=dst.shape[0])
+    order = np.argsort(src, kind="stable")
+    b.connect(src[order], dst[order], cv[order], stdp, w_syn, delay=steps[order] * dt)
+    b.connect(SRC_POISSON, cells, 0, drive, w_drive, rate=drive_hz)
+    return b.build()
