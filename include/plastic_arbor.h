@@ -1,0 +1,240 @@
+/*
+ * plastic_arbor.h -- C-ABI of the B300 engine for the fixed-dt time-step loop of
+ * networks of multi-compartment neurons with spike-driven plastic synapses
+ * ("Plastic Arbor", arXiv 2411.16445).
+ *
+ * One call of pa_advance runs, for every cell and every step, the four stages of
+ * the loop on the GPU:
+ *   1. mechanism currents and state updates: Hodgkin-Huxley soma (the paper's
+ *      simple-branchy cells, Sec. "Runtime and memory benchmarking with
+ *      large-scale networks"), passive leak, conductance-based exponential
+ *      synapses, pair STDP (Eqs. stdp_ode_1-3), Graupner-Brunel calcium
+ *      plasticity (Eqs. weight_graupner_brunel, ca_model_graupner_brunel) and
+ *      synaptic tagging and capture (Eqs. total_syn_weight .. prp_single_comp),
+ *      with the POST_EVENT hook (Sec. "Spike-time detection to simplify
+ *      computation") and the delayed second calcium target of the
+ *      round_robin_halt policy (Sec. "Multiple postsynaptic variables ...");
+ *   2. backward-Euler assembly of the cable equation (Eq. cable) and a Hines
+ *      solve of each cell's tree;
+ *   3. threshold-crossing spike detection at the soma;
+ *   4. event delivery through a CSR connectivity table once per min-delay epoch.
+ *
+ * Units: mV, ms, um, uS (weights and point conductances), nA, S/cm2 (densities),
+ * uF/cm2, ohm cm.
+ *
+ * Conventions for every entry point:
+ *   - All pointers passed in are host pointers owned by the caller; they are
+ *     read during the call and may be freed afterwards.  The model owns every
+ *     device allocation it makes and releases it in pa_free_model.
+ *   - Return value 0 means success.  Negative values are errors (PA_ERR_*); a
+ *     human-readable message is then available from pa_last_error() (thread-
+ *     local, valid until the next call on the same thread).  No C++ exception
+ *     crosses this boundary.
+ *   - A model is used by one host thread at a time.
+ */
+#ifndef PLASTIC_ARBOR_H
+#define PLASTIC_ARBOR_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define PA_OK 0
+#define PA_ERR_ARG (-1)      /* invalid descriptor, size or argument */
+#define PA_ERR_OOM (-2)      /* device or host allocation failed */
+#define PA_ERR_CUDA (-3)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define PA_ERR_TIMEOUT (-4)  /* a bounded device wait expired */
+#define PA_ERR_CAPACITY (-5) /* a probe or spike record buffer filled up; data were dropped */
+#define PA_ERR_STATE (-6)    /* call not valid in the model's current state */
+
+/* mechanism kinds */
+#define PA_MECH_PAS 1     /* density, params: g [S/cm2], e [mV] */
+#define PA_MECH_HH 2      /* density (soma CV only), params: gnabar, gkbar, gl [S/cm2],
+                             ena, ek, el [mV] */
+#define PA_MECH_EXPSYN 10 /* point, params: tau [ms], e [mV] */
+#define PA_MECH_GB 11     /* point, expsyn + Graupner-Brunel calcium rule; params: tau, e,
+                             tau_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d,
+                             tau_w [ms], w_star, t_c_delay [ms], w0 */
+#define PA_MECH_STC 12    /* point, expsyn + tagging and capture; params: tau, e, tau_c,
+                             c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_h,
+                             tau_z, tau_p [ms], h0 [mV], theta_tag [mV], theta_pro [mV],
+                             p_max, f_int, t_c_delay [ms] */
+#define PA_MECH_STDP 13   /* point, expsyn + pair STDP; params: tau, e, tau_pre, tau_post
+                             [ms], A_pre, A_post, w0, w_max (w dimensionless, conductance
+                             jump = weight * clip(w, 0, w_max)) */
+
+/* arithmetic of the loop */
+#define PA_FP64 0   /* everything in FP64 */
+#define PA_MIXED 1  /* synaptic conductances and STDP traces (exponential integration)
+                       and the per-CV synaptic sums in FP32; voltage, cable coefficients,
+                       assembly, Hines solve, HH, calcium and the slow plasticity state
+                       (GB w, STC h/z/p, STDP w) in FP64 */
+
+/* connection source meaning "an independent Poisson train of rate rate_hz" */
+#define PA_SRC_POISSON (-1)
+
+/* synapse / cell state fields for pa_read_state */
+#define PA_FIELD_G 0       /* synaptic conductance [uS], per connection */
+#define PA_FIELD_C 1       /* calcium, per connection (GB, STC) */
+#define PA_FIELD_W 2       /* plastic weight w (GB, STDP), per connection */
+#define PA_FIELD_H 3       /* early-phase weight h [mV] (STC), per connection */
+#define PA_FIELD_Z 4       /* late-phase weight z (STC), per connection */
+#define PA_FIELD_APRE 5    /* STDP presynaptic trace, per connection */
+#define PA_FIELD_APOST 6   /* STDP postsynaptic trace, per connection */
+#define PA_FIELD_V 16      /* membrane potential [mV], per CV in cell-major order */
+#define PA_FIELD_PRP 17    /* PRP concentration p (STC), per cell */
+#define PA_FIELD_GATES 18  /* HH gates m, h, n of each cell's soma CV: 3 values per cell */
+
+typedef struct pa_model pa_model;
+
+/* A CV-level morphology: CV i is a cylinder of length length_um[i] and diameter
+ * diam_um[i] whose parent is parent[i] (parent[0] = -1, 0 <= parent[i] < i,
+ * n_cv <= 32767).  region[i] = 0 selects the cell's soma mechanism, 1 its
+ * dendrite mechanism.  CV 0 is the soma: spikes are detected there. */
+typedef struct {
+  int32_t n_cv;
+  const int32_t* parent;
+  const double* length_um;
+  const double* diam_um;
+  const int32_t* region;
+} pa_morphology;
+
+/* One cell.  soma_mech / dend_mech index the mechanism table (PAS or HH; HH
+ * only on CV 0).  i_step [nA] is injected into CV 0 during steps k with
+ * round(t_on/dt) <= k < round(t_off/dt) (t_off > 1e15 means never off). */
+typedef struct {
+  int32_t morph;
+  int32_t soma_mech;
+  int32_t dend_mech;
+  int32_t reserved;
+  double cm;        /* uF/cm2 */
+  double ra;        /* ohm cm */
+  double i_step;    /* nA */
+  double t_on;      /* ms */
+  double t_off;     /* ms */
+  double v_init;    /* mV */
+  double threshold; /* mV: spike iff V_soma^k < threshold <= V_soma^{k+1} */
+} pa_cell;
+
+typedef struct {
+  int32_t kind;     /* PA_MECH_* */
+  int32_t n_params; /* must equal the kind's parameter count */
+  const double* params;
+} pa_mechanism;
+
+/* One connection = one synapse of mechanism `mech` on CV dst_cv of cell
+ * dst_gid.  A spike of src_gid in step k is delivered at the start of step
+ * k + round(delay_ms/dt) (>= 1 step); a GB/STC synapse also receives its
+ * presynaptic calcium jump round(t_c_delay/dt) steps later.  src_gid =
+ * PA_SRC_POISSON drives the synapse with its own Poisson train of rate_hz
+ * (delivered in the step it is drawn; delay_ms ignored).  Such a train is
+ * identified by poisson_id (a negative value means the connection's index):
+ * connections with the same poisson_id and rate receive the same train. */
+typedef struct {
+  int32_t src_gid;
+  int32_t dst_gid;
+  int32_t dst_cv;
+  int32_t mech;
+  double weight;   /* uS */
+  double delay_ms;
+  double rate_hz;
+  int64_t poisson_id;
+} pa_connection;
+
+typedef struct {
+  double dt;                /* ms, fixed for the model's lifetime */
+  uint64_t seed;            /* keys the Poisson trains (Threefry-4x64-12) */
+  int32_t precision;        /* PA_FP64 or PA_MIXED */
+  int32_t device;           /* CUDA device ordinal */
+  void* stream;             /* cudaStream_t to run on; NULL = the legacy default stream */
+  int32_t n_probe;          /* membrane-potential probes recorded after every step */
+  const int32_t* probe_gid;
+  const int32_t* probe_cv;
+  int64_t probe_capacity;   /* samples held between pa_read_probes calls (0: 65536) */
+  int64_t spike_capacity;   /* spikes held between pa_read_spikes calls (0: automatic) */
+  int32_t max_epoch_steps;  /* upper bound of the epoch length (0: 64); <= 64 */
+  int32_t flags;            /* PA_FLAG_* */
+} pa_options;
+
+/* pa_options.flags: record CUDA events around every kernel launch on the model's
+ * stream so that pa_get_kernel_stats can report device time per kernel kind. */
+#define PA_FLAG_TIME_KERNELS 1
+
+typedef struct {
+  int64_t epoch_launches;   /* epoch (time-step) kernel launches since the last reset */
+  int64_t kernel_launches;  /* all kernel launches of the engine since the last reset */
+  double epoch_kernel_ms;   /* device time of the epoch kernels (PA_FLAG_TIME_KERNELS) */
+  double event_kernels_ms;  /* device time of the Poisson, routing and record kernels */
+} pa_kernel_stats;
+
+typedef struct {
+  int64_t n_cells, n_cv, n_conn, n_groups, n_padded_cv;
+  int64_t step;             /* steps completed */
+  int32_t epoch_steps;      /* min-delay epoch length E */
+  int32_t precision;
+  int32_t tree;             /* 1 if any morphology branches */
+  int32_t n_streams;        /* synapse streams (one per point mechanism in use) */
+  int64_t device_bytes;     /* device memory held by the model */
+} pa_info;
+
+/* Validates the descriptors, discretises every morphology (CV = cylinder:
+ * area pi d L, C = c_m A, axial conductance of two half-cylinders in series,
+ * Eq. cable), lays the state out on the device and uploads it.  On success
+ * *out receives the model.  Errors: PA_ERR_ARG (message names the offending
+ * element), PA_ERR_OOM, PA_ERR_CUDA. */
+int pa_build_model(const pa_cell* cells, int64_t n_cells, const pa_morphology* morphs,
+                   int64_t n_morph, const pa_mechanism* mechs, int64_t n_mech,
+                   const pa_connection* conns, int64_t n_conn, const pa_options* opt,
+                   pa_model** out);
+
+/* Advances the simulation to t_end_ms (on the dt grid, >= the current time).
+ * dt_ms must equal the build-time dt.  Runs asynchronously on the model's
+ * stream except that it returns only after the work was enqueued; errors
+ * raised by the device (record overflow) are reported by the next
+ * pa_read_* / pa_sync call. */
+int pa_advance(pa_model* m, double t_end_ms, double dt_ms);
+
+/* Waits for the model's stream and reports device-side errors. */
+int pa_sync(pa_model* m);
+
+/* Copies the probe samples recorded since the last call into out
+ * ([sample][probe], double, cap values) and clears the record.  cap = 0 only
+ * queries: *n_out receives the number of values available. */
+int pa_read_probes(pa_model* m, double* out, int64_t cap, int64_t* n_out);
+
+/* Copies the spikes recorded since the last call, sorted by (step, gid), into
+ * gid / step / t (any may be NULL; cap entries each) and clears the record.
+ * t is the interpolated crossing time [ms].  cap = 0 only queries. */
+int pa_read_spikes(pa_model* m, int32_t* gid, int64_t* step, double* t, int64_t cap,
+                   int64_t* n_out);
+
+/* Plastic weight of every connection in build order: GB and STDP w, STC
+ * total weight h + h0 z (Eq. total_syn_weight), static synapses their weight. */
+int pa_read_weights(pa_model* m, double* out, int64_t cap, int64_t* n_out);
+
+/* Any state field (PA_FIELD_*), per connection, per CV or per cell. */
+int pa_read_state(pa_model* m, int32_t field, double* out, int64_t cap, int64_t* n_out);
+
+/* Open-loop replay: from now on the network's own spikes no longer drive
+ * synaptic events or POST_EVENT; instead cell gid[i] is taken to have spiked
+ * in step step[i] (sorted by step, all >= the current step).  Own spikes are
+ * still detected and recorded. */
+int pa_set_replay(pa_model* m, int64_t n, const int32_t* gid, const int64_t* step);
+
+int pa_model_info(const pa_model* m, pa_info* info);
+
+/* Launch counts and (with PA_FLAG_TIME_KERNELS) device times since the last
+ * reset.  Synchronises the model's stream. */
+int pa_get_kernel_stats(pa_model* m, pa_kernel_stats* out);
+int pa_reset_kernel_stats(pa_model* m);
+
+void pa_free_model(pa_model* m);
+
+const char* pa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

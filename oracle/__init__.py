@@ -24,7 +24,7 @@ def lib():
         P = C.c_void_p
         L.orc_build.restype = C.c_int
         L.orc_build.argtypes = ([C.c_int32] + [P] * 10 + [C.c_int32] + [P] * 6 + [C.c_int32]
-                                + [P] * 3 + [C.c_int64] + [P] * 7
+                                + [P] * 3 + [C.c_int64] + [P] * 8
                                 + [C.c_double, C.c_uint64, C.c_int32, P, P, P])
         L.orc_run.argtypes = [P, C.c_int64]
         L.orc_set_replay.argtypes = [P, C.c_int64, P, P]
@@ -84,7 +84,7 @@ class Oracle:
             net.n_conn, arr(net.conn_src, np.int32), arr(net.conn_dst, np.int32),
             arr(net.conn_cv, np.int32), arr(net.conn_mech, np.int32),
             arr(net.conn_weight, np.float64), arr(net.conn_delay, np.float64),
-            arr(net.conn_rate, np.float64), float(net.dt), int(net.seed) & (2**64 - 1),
+            arr(net.conn_rate, np.float64), arr(net.conn_pid, np.int64), float(net.dt), int(net.seed) & (2**64 - 1),
             len(pg), arr(pg, np.int32), arr(pc, np.int32), C.byref(h))
         if rc != 0:
             raise ValueError("oracle build failed: " + L.orc_last_error().decode())

@@ -246,6 +246,7 @@ struct orc_model {
   int64_t* syn_cv; /* global CV index */
   double* syn_weight;
   int64_t* syn_D;
+  uint64_t* syn_pid; /* Poisson train of the synapse */
   uint32_t* syn_thr;
   double *g, *c, *w, *hs, *z, *apre, *apost;
   int64_t *cell_syn_off, *cell_syn;
@@ -310,7 +311,7 @@ void orc_free(orc_model* M) {
                   M->es, M->d, M->b, M->f, M->xp, M->xnew, M->istep, M->k_on, M->k_off,
                   M->thresh, M->p, M->spiked_prev, M->spk_flag, M->cell_stc_mech, M->spk_t,
                   M->mech, M->syn_cell, M->syn_mech, M->syn_src, M->syn_cv, M->syn_weight,
-                  M->syn_D, M->syn_thr, M->g, M->c, M->w, M->hs, M->z, M->apre, M->apost,
+                  M->syn_D, M->syn_pid, M->syn_thr, M->g, M->c, M->w, M->hs, M->z, M->apre, M->apost,
                   M->cell_syn_off, M->cell_syn, M->out_off, M->out_syn, M->poisson_syn,
                   M->spk_gid, M->spk_step, M->spk_time, M->probe_cv, M->probes, M->rep_gid,
                   M->rep_step};
@@ -333,7 +334,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
               const double* mech_params,
               int64_t n_conn, const int32_t* conn_src, const int32_t* conn_dst,
               const int32_t* conn_cv, const int32_t* conn_mech, const double* conn_weight,
-              const double* conn_delay, const double* conn_rate,
+              const double* conn_delay, const double* conn_rate, const int64_t* conn_pid,
               double dt, uint64_t seed, int32_t n_probe, const int32_t* probe_gid,
               const int32_t* probe_cv, orc_model** out) {
   *out = NULL;
@@ -463,7 +464,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
   M->n_syn = n_conn;
   ALLOC(M->syn_cell, n_conn); ALLOC(M->syn_mech, n_conn); ALLOC(M->syn_src, n_conn);
   ALLOC(M->syn_cv, n_conn); ALLOC(M->syn_weight, n_conn); ALLOC(M->syn_D, n_conn);
-  ALLOC(M->syn_thr, n_conn); ALLOC(M->g, n_conn); ALLOC(M->c, n_conn); ALLOC(M->w, n_conn);
+  ALLOC(M->syn_thr, n_conn); ALLOC(M->syn_pid, n_conn); ALLOC(M->g, n_conn); ALLOC(M->c, n_conn); ALLOC(M->w, n_conn);
   ALLOC(M->hs, n_conn); ALLOC(M->z, n_conn); ALLOC(M->apre, n_conn); ALLOC(M->apost, n_conn);
   ALLOC(M->poisson_syn, n_conn);
   int64_t maxdelay = 1;
@@ -486,6 +487,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
       double x = ((conn_rate[s] * dt) * 1e-3) * 4294967296.0;
       if (!(x >= 0) || x >= 4294967296.0) { orc_free(M); return fail(-1, "connection %lld: rate*dt out of range", (long long)s); }
       M->syn_thr[s] = (uint32_t)floor(x);
+      M->syn_pid[s] = (conn_pid && conn_pid[s] >= 0) ? (uint64_t)conn_pid[s] : (uint64_t)s;
       M->syn_D[s] = 0;
       M->poisson_syn[M->n_poisson++] = s;
     } else {
@@ -729,7 +731,7 @@ int orc_run(orc_model* M, int64_t n_steps) {
       if (bk->v[e].type == 0) pre_event(M, bk->v[e].syn);
     for (int64_t i = 0; i < M->n_poisson; ++i) {
       int64_t s = M->poisson_syn[i];
-      if (orc_poisson_u32(M->seed, (uint64_t)s, k) < M->syn_thr[s]) {
+      if (orc_poisson_u32(M->seed, M->syn_pid[s], k) < M->syn_thr[s]) {
         const orc_mech* mc = &M->mech[M->syn_mech[s]];
         pre_event(M, s);
         if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC)

@@ -60,7 +60,9 @@ typedef struct orc_model orc_model;
  * Mechanisms: kind and params[mech_off[j] ..].
  * Connections: src gid (ORC_SRC_POISSON for an independent Poisson train of
  *         rate conn_rate [Hz]), dst gid, dst CV, point-mechanism index, weight
- *         [uS], delay [ms].  Each connection creates one synapse.
+ *         [uS], delay [ms].  Each connection creates one synapse.  conn_pid
+ *         (may be NULL) names the Poisson train of a Poisson connection; a
+ *         negative entry or a NULL array means "the connection's index".
  * Probes: membrane potential of CV probe_cv of cell probe_gid after each step.
  * Returns 0 or a negative error code; *out receives the model. */
 int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_soma_mech,
@@ -74,7 +76,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
               const double* mech_params,
               int64_t n_conn, const int32_t* conn_src, const int32_t* conn_dst,
               const int32_t* conn_cv, const int32_t* conn_mech, const double* conn_weight,
-              const double* conn_delay, const double* conn_rate,
+              const double* conn_delay, const double* conn_rate, const int64_t* conn_pid,
               double dt, uint64_t seed, int32_t n_probe, const int32_t* probe_gid,
               const int32_t* probe_cv, orc_model** out);
 

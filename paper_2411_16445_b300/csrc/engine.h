@@ -1,0 +1,160 @@
+// engine.h -- internal data layout shared by the host builder and the kernels.
+//
+// Layout ("lane-interleaved groups"): cells are sorted by CV count (descending)
+// and dealt into groups of 32; one warp advances one group, one thread one
+// cell.  Row i of a group holds CV i of its 32 cells in 32 consecutive slots,
+// so element (group g, row i, lane l) lives at ((row_base[g] + i) << 5) | l and
+// every per-row access of a warp is one coalesced 256-byte (FP64) transaction.
+// A group has as many rows as its largest cell; shorter cells leave padding
+// rows that are never touched.  Synapses are laid out the same way, one
+// "stream" per point mechanism of the model: row j of a stream holds the j-th
+// synapse (in the canonical order CV, connection) of each lane's cell.
+#pragma once
+#include <cstdint>
+
+namespace pa {
+
+constexpr int kLanes = 32;
+constexpr int kMaxStreams = 8;
+constexpr int kMaxProbeRowsPerLane = 1 << 15;
+
+enum StreamKind : int32_t { SK_EXPSYN = 0, SK_GB = 1, SK_STC = 2, SK_STDP = 3 };
+
+// Constants of one synapse stream (one point mechanism), derived for the dt.
+struct StreamParams {
+  int32_t kind;
+  int32_t dc_steps;      // presynaptic calcium delay in steps (GB, STC)
+  double e;              // reversal potential [mV]
+  double decay_g;        // exp(-dt/tau)
+  double decay_c;        // exp(-dt/tau_c)
+  double c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d;
+  double rate_w, w_star; // GB: dt/tau_w, w*
+  double rate_h, rate_z, rate_p, h0, theta_tag, theta_pro, p_max, f_int;  // STC
+  double a_pre, a_post, decay_pre, decay_post, w_max;                     // STDP
+};
+
+// Device pointers of one synapse stream.  Element index e = ((sbase+j)<<5)|lane.
+struct StreamDev {
+  const int32_t* cvf;    // (cv << 1) | first-on-CV flag; -1 for padding
+  const int32_t* sbase;  // [n_groups + 1] row offsets of each group
+  const void* weight;    // uS, double (FP64) or float (mixed)
+  void* g;               // conductance, TM
+  double* c;             // calcium (GB, STC)
+  double* w;             // GB w, STDP w, STC h
+  double* z;             // STC z
+  void* apre;            // TM (STDP)
+  void* apost;           // TM (STDP)
+  uint64_t* cmask;       // [n_slots][n_elem]: bit (k mod E) = conductance event in step k
+  uint64_t* camask;      // [n_slots][n_elem]: delayed calcium event (GB, STC)
+  int64_t n_elem;
+};
+
+struct EpochArgs {
+  // launch window: steps [k_begin, k_end) all inside epoch [k0, k0 + E)
+  int64_t k_begin, k_end, k0;
+  int32_t slot;          // mask slot of this epoch
+  int32_t n_groups;
+  double dt;
+  // groups / lanes
+  const int32_t* row_base;   // [n_groups + 1]
+  const int32_t* ncv;        // [n_lanes] CV count of the lane's cell (0: empty lane)
+  const int32_t* gid;        // [n_lanes] cell gid (-1: empty lane)
+  // CV arrays (element index)
+  double* V;
+  const double* cdt;         // C/dt [uS]
+  const double* dc;          // cdt + axial sum (+ leak for passive CVs)
+  const double* em;          // leak g E for passive CVs
+  const double* a;           // -g_axial to the parent
+  void* gs;                  // synaptic conductance per CV, TM
+  void* es;                  // synaptic g E per CV, TM
+  double* f;                 // elimination scratch
+  double* xp;                // elimination scratch
+  const int16_t* par;        // tree: parent row (row 0: -1)
+  const int16_t* och_head;   // tree: highest-index non-first child (-1: none)
+  const int16_t* och_next;   // tree: next lower non-first sibling (-1: none)
+  // soma / cell state (lane index)
+  const uint8_t* is_hh;
+  const double* hh_g;        // [3][n_lanes] gna, gk, gl [uS]
+  const double* hh_e;        // [3][n_lanes] ena, ek, el [mV]
+  double* gate;              // [3][n_lanes] m, h, n
+  const double* iinj;
+  const int64_t* k_on;
+  const int64_t* k_off;
+  const double* thresh;
+  uint8_t* spiked_prev;
+  double* prp;               // STC PRP per lane
+  const uint8_t* has_stc;
+  int32_t stc_stream;        // index of the STC stream or -1
+  int64_t n_lanes;
+  // synapse streams
+  int32_t n_streams;
+  StreamParams sp[kMaxStreams];
+  StreamDev sd[kMaxStreams];
+  // spike output of this launch
+  int32_t* spk_count;
+  int32_t* spk_gid;
+  int32_t* spk_step;
+  double* spk_t;
+  int32_t spk_cap;
+  // open-loop replay (POST_EVENT source); replay_bits[lane] bit j = spike at k_begin + j
+  int32_t replay;
+  const uint64_t* replay_bits;
+  // probes
+  const int32_t* probe_ptr;  // [n_lanes + 1]
+  const int32_t* probe_row;
+  const int32_t* probe_id;
+  double* probe_buf;
+  int64_t probe_sample0;     // sample index of step k_begin
+  int64_t probe_cap;         // samples
+  int32_t n_probe;
+  int32_t* err_flags;        // bit 0: probe overflow
+};
+
+struct PoissonArgs {
+  int64_t k0;                // epoch start
+  int32_t E;
+  int32_t n_slots;
+  uint64_t seed;
+  int64_t n;                 // Poisson synapses
+  const int32_t* stream;     // stream index
+  const int64_t* elem;       // element index in the stream
+  const int64_t* conn;       // Poisson train id (the connection index by default)
+  const uint32_t* thr;       // spike iff u32 < thr
+  const int32_t* dc_steps;   // calcium delay (-1: none)
+  uint64_t* cmask[kMaxStreams];
+  uint64_t* camask[kMaxStreams];
+  int64_t n_elem[kMaxStreams];
+};
+
+struct RouteArgs {
+  int32_t E;
+  int32_t n_slots;
+  int32_t spk_cap;           // entries in the spike buffer
+  const int32_t* spk_count;
+  const int32_t* spk_gid;
+  const int32_t* spk_step;
+  const int64_t* out_ptr;    // [n_cells + 1] CSR by source gid
+  const uint8_t* out_stream;
+  const int64_t* out_elem;
+  const int32_t* out_delay;  // steps
+  int32_t dc_steps[kMaxStreams];  // -1: no calcium target
+  uint64_t* cmask[kMaxStreams];
+  uint64_t* camask[kMaxStreams];
+  int64_t n_elem[kMaxStreams];
+};
+
+// kernel launchers (defined in the .cu files)
+int launch_epoch_fp64(const EpochArgs& a, bool tree, void* stream);
+int launch_epoch_mixed(const EpochArgs& a, bool tree, void* stream);
+int launch_init_gates_fp64(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
+                           void* stream);
+int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
+                            void* stream);
+int launch_poisson(const PoissonArgs& a, int64_t k_from, int64_t k_to, void* stream);
+int launch_route(const RouteArgs& a, int32_t max_spikes, void* stream);
+int launch_log_append(const int32_t* spk_count, const int32_t* gid, const int32_t* step,
+                      const double* t, int32_t max_spikes, int32_t* log_count,
+                      int32_t* log_gid, int64_t* log_step, double* log_t, int64_t log_cap,
+                      int32_t* err_flags, void* stream);
+
+}  // namespace pa

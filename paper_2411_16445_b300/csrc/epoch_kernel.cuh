@@ -1,0 +1,389 @@
+// epoch_kernel.cuh -- the fused per-epoch time-step kernel.
+//
+// One warp advances one group of 32 cells (one thread per cell) through the
+// steps [k_begin, k_end) of one min-delay epoch.  Cells do not interact inside
+// an epoch: every synaptic event produced by a spike in this epoch is due at
+// least one epoch later, and the POST_EVENT hook only touches the spiking
+// cell's own synapses.  So the launch needs no inter-block synchronisation and
+// contains no waits.
+//
+// Per step and cell (Sec. "Design and Implementation" of arXiv 2411.16445):
+//   a. synapse streams: deliver this step's pre / delayed-calcium events (bit
+//      (k - k0) of the synapse's epoch mask), the POST_EVENT of a spike in the
+//      previous step, scatter g and g*E into the per-CV accumulators, then
+//      decay g, calcium and STDP traces and take the forward-Euler step of the
+//      plasticity ODEs (Eqs. weight_graupner_brunel, early_phase_weight,
+//      late_phase_weight, prp_single_comp);
+//   b. backward pass over rows n-1..0: assemble the backward-Euler row of the
+//      cable equation (Eq. cable) and eliminate it into its parent (Hines);
+//   c. forward pass over rows 0..n-1: back substitution -> V^{k+1};
+//   d. soma: HH gates by exponential integration at V^{k+1}; threshold
+//      detection; warp-ballot compaction of the spikes.
+//
+// Arithmetic: the FP64 instantiation is compiled without contraction so that
+// every operation and its order equal the plain definition (one IEEE
+// reciprocal per row; fused multiply-adds only where written as fma), and the
+// model's exponential is the Cody-Waite + degree-13 Taylor function below.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "engine.h"
+
+namespace pa {
+
+// ---------------------------------------------------------------------------
+// The model's exponential (the FP64 path): x = k ln2 + r with ln2 split into a
+// 32-bit head (ln2 rounded to a double with its low 21 mantissa bits cleared)
+// and a tail; exp(r) by the degree-13 Taylor polynomial sum r^j / j! in
+// Horner form with fused multiply-adds; scaling by 2^k through the exponent
+// field.  |r| <= ln2/2, so the truncation error is below r^14/14! < 5e-18.
+__device__ __forceinline__ double model_exp(double x) {
+  const double ln2_hi = 6.93147180369123816490e-01;
+  const double ln2_lo = 1.9082149292705877e-10;
+  const double inv_ln2 = 1.4426950408889634;
+  if (x != x) return x;
+  if (x > 709.0) return __longlong_as_double(0x7ff0000000000000LL);
+  if (x < -708.0) return 0.0;
+  double kd = rint(x * inv_ln2);
+  double r = (x - kd * ln2_hi) - kd * ln2_lo;
+  double p = 1.6059043836821613e-10;            // 1/13!
+  p = fma(p, r, 2.08767569878681e-09);           // 1/12!
+  p = fma(p, r, 2.505210838544172e-08);          // 1/11!
+  p = fma(p, r, 2.755731922398589e-07);          // 1/10!
+  p = fma(p, r, 2.7557319223985893e-06);         // 1/9!
+  p = fma(p, r, 2.48015873015873e-05);           // 1/8!
+  p = fma(p, r, 0.0001984126984126984);          // 1/7!
+  p = fma(p, r, 0.001388888888888889);           // 1/6!
+  p = fma(p, r, 0.008333333333333333);           // 1/5!
+  p = fma(p, r, 0.041666666666666664);           // 1/4!
+  p = fma(p, r, 0.16666666666666666);            // 1/3!
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p = fma(p, r, 1.0);
+  long long k = (long long)kd;
+  return p * __longlong_as_double((k + 1023LL) << 52);
+}
+
+// Hodgkin-Huxley kinetics (textbook, rest -65 mV, 6.3 C) with the model's
+// exponential, in FP64 in both precisions: FP32 rate functions (CUDA's expf)
+// shift the phase of tonic firing by ~2e-5 V within a second, twice the mixed
+// path's tolerance, while the soma is one CV of hundreds.
+struct HH64 {
+  __device__ static __forceinline__ double vtrap(double x, double y) {
+    double u = x / y;
+    if (fabs(u) < 1e-6) return y * (1.0 - 0.5 * u);
+    return x / (model_exp(u) - 1.0);
+  }
+  __device__ static __forceinline__ void rates(double v, double& am, double& bm, double& ah,
+                                               double& bh, double& an, double& bn) {
+    am = 0.1 * vtrap(-(v + 40.0), 10.0);
+    bm = 4.0 * model_exp(-(v + 65.0) / 18.0);
+    ah = 0.07 * model_exp(-(v + 65.0) / 20.0);
+    bh = 1.0 / (model_exp(-(v + 35.0) / 10.0) + 1.0);
+    an = 0.01 * vtrap(-(v + 55.0), 10.0);
+    bn = 0.125 * model_exp(-(v + 65.0) / 80.0);
+  }
+  __device__ static __forceinline__ double gate(double x, double a, double b, double dt) {
+    double s = a + b;
+    double xinf = a / s;
+    return xinf + (x - xinf) * model_exp(-dt * s);
+  }
+};
+
+__device__ __forceinline__ uint32_t elem_of(int32_t row_base, int32_t row, int lane) {
+  return ((uint32_t)(row_base + row) << 5) | (uint32_t)lane;
+}
+
+// scatter one synapse's g and g*E into its CV's accumulators
+template <class TM>
+__device__ __forceinline__ void contribute(TM* gs, TM* es, int32_t rb, int lane, int32_t cvf,
+                                           TM g, TM E) {
+  uint32_t ce = elem_of(rb, cvf >> 1, lane);
+  if (cvf & 1) {
+    gs[ce] = g;
+    es[ce] = g * E;
+  } else {
+    gs[ce] = gs[ce] + g;
+    es[ce] = es[ce] + g * E;
+  }
+}
+
+template <class TM, bool TREE>
+__global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (g >= A.n_groups) return;  // whole warps only
+  using HH = HH64;
+  const int64_t L = (int64_t)g * 32 + lane;
+  const int n = A.ncv[L];
+  const int32_t rb = A.row_base[g];
+  const int rows = A.row_base[g + 1] - rb;
+  const double dt = A.dt;
+
+  double* __restrict__ Vg = A.V;
+  const double* __restrict__ CDT = A.cdt;
+  const double* __restrict__ DC = A.dc;
+  const double* __restrict__ EM = A.em;
+  const double* __restrict__ AA = A.a;
+  TM* __restrict__ GS = (TM*)A.gs;
+  TM* __restrict__ ES = (TM*)A.es;
+  double* __restrict__ F = A.f;
+  double* __restrict__ XP = A.xp;
+
+  const bool hh = n > 0 && A.is_hh[L];
+  const double* hg = A.hh_g;
+  const double* he = A.hh_e;
+  double* gate = A.gate;
+  double gna = 0, gk = 0, gl = 0, ena = 0, ek = 0, el = 0, gm_ = 0, gh_ = 0, gn_ = 0;
+  if (hh) {
+    gna = hg[L]; gk = hg[A.n_lanes + L]; gl = hg[2 * A.n_lanes + L];
+    ena = he[L]; ek = he[A.n_lanes + L]; el = he[2 * A.n_lanes + L];
+    gm_ = gate[L]; gh_ = gate[A.n_lanes + L]; gn_ = gate[2 * A.n_lanes + L];
+  }
+  const double iinj_val = n > 0 ? A.iinj[L] : 0.0;
+  const int64_t kon = n > 0 ? A.k_on[L] : 0, koff = n > 0 ? A.k_off[L] : 0;
+  const double th = n > 0 ? A.thresh[L] : 0.0;
+  bool spiked_prev = n > 0 && A.spiked_prev[L];
+  double prp = (n > 0 && A.stc_stream >= 0) ? A.prp[L] : 0.0;
+  const bool has_stc = n > 0 && A.stc_stream >= 0 && A.has_stc[L];
+  const uint64_t rbits = (A.replay && n > 0) ? A.replay_bits[L] : 0ull;
+  const int32_t pq0 = n > 0 ? A.probe_ptr[L] : 0, pq1 = n > 0 ? A.probe_ptr[L + 1] : 0;
+
+  for (int64_t k = A.k_begin; k < A.k_end; ++k) {
+    const int kk = (int)(k - A.k0);
+    const bool post = spiked_prev;
+    // ---- a. synapse streams ------------------------------------------------
+    double S = 0.0;
+    for (int s = 0; s < A.n_streams; ++s) {
+      const StreamParams& P = A.sp[s];
+      const StreamDev& D = A.sd[s];
+      const int32_t sb = D.sbase[g], se = D.sbase[g + 1];
+      const uint64_t* cm = D.cmask + (int64_t)A.slot * D.n_elem;
+      const uint64_t* cam = D.camask ? D.camask + (int64_t)A.slot * D.n_elem : nullptr;
+      TM* G = (TM*)D.g;
+      const TM E = (TM)P.e;
+      const TM dg = (TM)P.decay_g;
+      for (int32_t j = sb; j < se; ++j) {
+        const uint32_t e = ((uint32_t)j << 5) | (uint32_t)lane;
+        const int32_t cvf = D.cvf[e];
+        if (cvf < 0) continue;
+        const bool pre = (cm[e] >> kk) & 1ull;
+        TM gv = G[e];
+        if (P.kind == SK_EXPSYN) {
+          if (pre) gv = gv + ((const TM*)D.weight)[e];
+          contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
+        } else if (P.kind == SK_GB) {
+          double* C = D.c;
+          double cc = C[e];
+          if (pre) gv = gv + ((const TM*)D.weight)[e];
+          if ((cam[e] >> kk) & 1ull) cc = cc + P.c_pre;
+          if (post) cc = cc + P.c_post;
+          contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
+          double w = D.w[e];
+          double Aw = (w * (1.0 - w)) * (P.w_star - w);
+          double Pw = (cc > P.theta_p) ? P.gamma_p * (1.0 - w) : 0.0;
+          double Dw = (cc > P.theta_d) ? P.gamma_d * w : 0.0;
+          D.w[e] = w + P.rate_w * ((Pw - Aw) - Dw);
+          C[e] = cc * P.decay_c;
+        } else if (P.kind == SK_STC) {
+          double* C = D.c;
+          double cc = C[e];
+          double h = D.w[e], z = D.z[e];
+          const double h0 = P.h0;
+          if (pre) gv = gv + (TM)((double)((const TM*)D.weight)[e] * ((h + h0 * z) / h0));
+          if ((cam[e] >> kk) & 1ull) cc = cc + P.c_pre;
+          if (post) cc = cc + P.c_post;
+          contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
+          S = S + fabs(h - h0);
+          double T1 = ((h - h0) > P.theta_tag) ? (prp * P.f_int) * (1.0 - z) : 0.0;
+          double T2 = ((h0 - h) > P.theta_tag) ? (prp * P.f_int) * (z + 0.5) : 0.0;
+          D.z[e] = z + P.rate_z * (T1 - T2);
+          double Ph = (cc > P.theta_p) ? P.gamma_p * (10.0 - h) : 0.0;
+          double Dh = (cc > P.theta_d) ? P.gamma_d * h : 0.0;
+          D.w[e] = h + P.rate_h * ((0.1 * (h0 - h) + Ph) - Dh);
+          C[e] = cc * P.decay_c;
+        } else {  // SK_STDP
+          TM* AP = (TM*)D.apre;
+          TM* AQ = (TM*)D.apost;
+          TM ap = AP[e], aq = AQ[e];
+          if (pre || post) {
+            double w = D.w[e];
+            if (pre) {
+              double wc = w < 0.0 ? 0.0 : (w > P.w_max ? P.w_max : w);
+              gv = gv + (TM)((double)((const TM*)D.weight)[e] * wc);
+              ap = ap + (TM)P.a_pre;
+              w = w + (double)aq;
+            }
+            if (post) {
+              aq = aq + (TM)P.a_post;
+              w = w + (double)ap;
+            }
+            D.w[e] = w;
+          }
+          contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
+          AP[e] = ap * (TM)P.decay_pre;
+          AQ[e] = aq * (TM)P.decay_post;
+        }
+        G[e] = gv * dg;
+      }
+      if (s == A.stc_stream && has_stc) {
+        const double qs = (S > P.theta_pro) ? P.p_max : 0.0;
+        prp = prp + P.rate_p * (qs - prp);
+      }
+    }
+
+    // ---- b. backward pass: assembly + elimination --------------------------
+    double v0_old = 0.0, v0_new = 0.0;
+    const double iinj = (k >= kon && k < koff) ? iinj_val : 0.0;
+    double cf = 0.0, ca = 0.0, cx = 0.0;
+    bool carry = false;
+    for (int i = rows - 1; i >= 0; --i) {
+      if (i >= n) continue;
+      const uint32_t e = elem_of(rb, i, lane);
+      const double v = Vg[e];
+      const double cdt = CDT[e];
+      double d, b;
+      if (i == 0) {
+        v0_old = v;
+        if (hh) {
+          const double mmmh = ((gm_ * gm_) * gm_) * gh_;
+          const double nnnn = ((gn_ * gn_) * gn_) * gn_;
+          const double g1 = gna * mmmh;
+          const double g2 = gk * nnnn;
+          const double gmt = (g1 + g2) + gl;
+          const double emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
+          d = (DC[e] + gmt) + (double)GS[e];
+          b = (fma(cdt, v, emt) + iinj) + (double)ES[e];
+        } else {
+          d = DC[e] + (double)GS[e];
+          b = (fma(cdt, v, EM[e]) + iinj) + (double)ES[e];
+        }
+      } else {
+        d = DC[e] + (double)GS[e];
+        b = fma(cdt, v, EM[e]) + (double)ES[e];
+      }
+      int pi = i - 1;
+      if (TREE) {
+        if (i > 0) pi = A.par[e];
+        for (int c = A.och_head[e]; c >= 0;) {
+          const uint32_t ec = elem_of(rb, c, lane);
+          const double ac = AA[ec];
+          d = fma(-F[ec], ac, d);
+          b = fma(-ac, XP[ec], b);
+          c = A.och_next[ec];
+        }
+      }
+      if (carry) {
+        d = fma(-cf, ca, d);
+        b = fma(-ca, cx, b);
+      }
+      if (i > 0) {
+        const double ai = AA[e];
+        const double r = 1.0 / d;
+        const double fi = ai * r;
+        const double xi = b * r;
+        F[e] = fi;
+        XP[e] = xi;
+        carry = !TREE || pi == i - 1;
+        cf = fi; ca = ai; cx = xi;
+      } else {
+        v0_new = b * (1.0 / d);
+      }
+    }
+    // ---- c. forward pass: back substitution ---------------------------------
+    if (n > 0) {
+      Vg[elem_of(rb, 0, lane)] = v0_new;
+      double vprev = v0_new;
+      for (int i = 1; i < n; ++i) {
+        const uint32_t e = elem_of(rb, i, lane);
+        double vp = vprev;
+        if (TREE) {
+          const int pi = A.par[e];
+          if (pi != i - 1) vp = Vg[elem_of(rb, pi, lane)];
+        }
+        const double vi = fma(-F[e], vp, XP[e]);
+        Vg[e] = vi;
+        vprev = vi;
+      }
+      for (int32_t q = pq0; q < pq1; ++q) {
+        const int64_t smp = A.probe_sample0 + (k - A.k_begin);
+        if (smp < A.probe_cap) {
+          A.probe_buf[smp * A.n_probe + A.probe_id[q]] = Vg[elem_of(rb, A.probe_row[q], lane)];
+        } else {
+          atomicOr(A.err_flags, 1);
+        }
+      }
+    }
+    // ---- d. soma gates, detection, compaction --------------------------------
+    if (hh) {
+      double am, bm, ah, bh, an, bn;
+      HH::rates(v0_new, am, bm, ah, bh, an, bn);
+      gm_ = HH::gate(gm_, am, bm, dt);
+      gh_ = HH::gate(gh_, ah, bh, dt);
+      gn_ = HH::gate(gn_, an, bn, dt);
+    }
+    const bool spk = n > 0 && v0_old < th && v0_new >= th;
+    const unsigned ball = __ballot_sync(0xffffffffu, spk);
+    if (ball) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(A.spk_count, __popc(ball));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (spk) {
+        const int slot = base + __popc(ball & ((1u << lane) - 1u));
+        if (slot < A.spk_cap) {
+          A.spk_gid[slot] = A.gid[L];
+          A.spk_step[slot] = (int32_t)k;
+          A.spk_t[slot] = (double)k * dt + dt * ((th - v0_old) / (v0_new - v0_old));
+        }
+      }
+    }
+    spiked_prev = A.replay ? (((rbits >> (k - A.k_begin)) & 1ull) != 0) : spk;
+  }
+  if (n > 0) {
+    A.spiked_prev[L] = spiked_prev ? 1 : 0;
+    if (hh) {
+      gate[L] = gm_; gate[A.n_lanes + L] = gh_; gate[2 * A.n_lanes + L] = gn_;
+    }
+    if (has_stc) A.prp[L] = prp;
+  }
+}
+
+// Steady-state HH gates x_inf = alpha / (alpha + beta) at each soma's v_init.
+template <class TM>
+__global__ void init_gates_kernel(const double* v, double* gate, int64_t n_lanes,
+                                  const uint8_t* is_hh) {
+  const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= n_lanes || !is_hh[L]) return;
+  double am, bm, ah, bh, an, bn;
+  HH64::rates(v[L], am, bm, ah, bh, an, bn);
+  gate[L] = am / (am + bm);
+  gate[n_lanes + L] = ah / (ah + bh);
+  gate[2 * n_lanes + L] = an / (an + bn);
+}
+
+template <class TM>
+int launch_init_gates_impl(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
+                           void* stream) {
+  if (n_lanes == 0) return 0;
+  const int threads = 128;
+  const int blocks = (int)((n_lanes + threads - 1) / threads);
+  init_gates_kernel<TM><<<blocks, threads, 0, (cudaStream_t)stream>>>(v, (double*)gate, n_lanes,
+                                                                      is_hh);
+  return (int)cudaGetLastError();
+}
+
+template <class TM>
+int launch_epoch_impl(const EpochArgs& a, bool tree, void* stream) {
+  const int threads = 128;
+  const int64_t warps = a.n_groups;
+  const int blocks = (int)((warps * 32 + threads - 1) / threads);
+  if (blocks == 0) return 0;
+  if (tree)
+    epoch_kernel<TM, true><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
+  else
+    epoch_kernel<TM, false><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace pa

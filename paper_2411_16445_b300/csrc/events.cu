@@ -1,0 +1,175 @@
+// events.cu -- Poisson drive, CSR spike routing and the spike record.
+//
+// Events are kept as per-synapse bitmasks, one 64-bit word per synapse and
+// epoch slot: bit (k mod E) of slot (k / E) mod n_slots says "a conductance
+// event reaches this synapse in step k" (cmask) or "a delayed presynaptic
+// calcium jump does" (camask, the second target of Sec. "Multiple
+// postsynaptic variables ..." at t_c,delay).  Each connection owns its synapse
+// and a cell spikes at most once per step, so an event carries no payload and
+// OR-ing bits is order independent: routing is deterministic without a sort.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "engine.h"
+
+namespace pa {
+
+// Threefry-4x64-12 (Salmon et al. 2011): Threefish-256 rotations, key parity
+// 0x1BD11BDAA9FC1A22, key injection after every fourth round.
+__device__ __forceinline__ uint64_t rotl(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+__device__ void threefry4x64_12(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                uint64_t k0, uint64_t k1, uint64_t k2, uint64_t k3,
+                                uint64_t out[4]) {
+  const int R0[8] = {14, 52, 23, 5, 25, 46, 58, 32};
+  const int R1[8] = {16, 57, 40, 37, 33, 12, 22, 32};
+  uint64_t ks[5] = {k0, k1, k2, k3, 0x1BD11BDAA9FC1A22ULL ^ k0 ^ k1 ^ k2 ^ k3};
+  uint64_t x0 = c0 + ks[0], x1 = c1 + ks[1], x2 = c2 + ks[2], x3 = c3 + ks[3];
+#pragma unroll
+  for (int r = 0; r < 12; ++r) {
+    if ((r & 1) == 0) {
+      x0 += x1; x1 = rotl(x1, R0[r & 7]); x1 ^= x0;
+      x2 += x3; x3 = rotl(x3, R1[r & 7]); x3 ^= x2;
+    } else {
+      x0 += x3; x3 = rotl(x3, R0[r & 7]); x3 ^= x0;
+      x2 += x1; x1 = rotl(x1, R1[r & 7]); x1 ^= x2;
+    }
+    if ((r & 3) == 3) {
+      const int s = (r >> 2) + 1;
+      x0 += ks[s % 5];
+      x1 += ks[(s + 1) % 5];
+      x2 += ks[(s + 2) % 5];
+      x3 += ks[(s + 3) % 5] + (uint64_t)s;
+    }
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+// One thread per Poisson-driven synapse: draws its spikes for steps
+// [k_from, k_to) (one Threefry call per 8 steps: key = seed, counter =
+// {train id, step / 8, 1, 0}; the word of step k is 32-bit half (k mod 2)
+// of output word (k mod 8) / 2) and sets the event bits, plus the calcium
+// jump t_c,delay later for calcium-plastic synapses.
+__global__ void poisson_kernel(const PoissonArgs A, int64_t k_from, int64_t k_to) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const int s = A.stream[i];
+  const int64_t el = A.elem[i];
+  const uint32_t thr = A.thr[i];
+  const int32_t dc = A.dc_steps[i];
+  const uint64_t sid = (uint64_t)A.conn[i];
+  uint64_t* cm = A.cmask[s];
+  uint64_t* cam = A.camask[s];
+  const int64_t ne = A.n_elem[s];
+  uint64_t word[4];
+  int64_t have = -1;
+  uint64_t bits = 0;
+  const int64_t slot = (A.k0 / A.E) % A.n_slots;
+  for (int64_t k = k_from; k < k_to; ++k) {
+    const int64_t blk = k >> 3;
+    if (blk != have) {
+      threefry4x64_12(sid, (uint64_t)blk, 1, 0, A.seed, 0, 0, 0, word);
+      have = blk;
+    }
+    const int j = (int)(k & 7);
+    const uint32_t u = (j & 1) ? (uint32_t)(word[j >> 1] >> 32) : (uint32_t)word[j >> 1];
+    if (u < thr) {
+      bits |= 1ull << (k - A.k0);
+      if (dc >= 0) {
+        const int64_t kc = k + dc;
+        const int64_t sc = (kc / A.E) % A.n_slots;
+        atomicOr((unsigned long long*)&cam[sc * ne + el], 1ull << (kc % A.E));
+      }
+    }
+  }
+  if (bits) atomicOr((unsigned long long*)&cm[slot * ne + el], bits);
+}
+
+// One warp per spike of the launch; its lanes walk the source's CSR row.
+__global__ void route_kernel(const RouteArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = min(*A.spk_count, A.spk_cap);
+  for (int64_t q = warp; q < n; q += nwarps) {
+    const int gid = A.spk_gid[q];
+    const int64_t ks = A.spk_step[q];
+    for (int64_t e = A.out_ptr[gid] + lane; e < A.out_ptr[gid + 1]; e += 32) {
+      const int s = A.out_stream[e];
+      const int64_t el = A.out_elem[e];
+      const int64_t kd = ks + A.out_delay[e];
+      const int64_t ne = A.n_elem[s];
+      atomicOr((unsigned long long*)&A.cmask[s][((kd / A.E) % A.n_slots) * ne + el],
+               1ull << (kd % A.E));
+      const int dc = A.dc_steps[s];
+      if (dc >= 0) {
+        const int64_t kc = kd + dc;
+        atomicOr((unsigned long long*)&A.camask[s][((kc / A.E) % A.n_slots) * ne + el],
+                 1ull << (kc % A.E));
+      }
+    }
+  }
+}
+
+// Appends the launch's spikes to the record (log_count is advanced later by
+// finalize_kernel, so every block sees the same base).
+__global__ void log_append_kernel(const int32_t* spk_count, int32_t spk_cap, const int32_t* gid,
+                                  const int32_t* step, const double* t, int32_t* log_count,
+                                  int32_t* log_gid, int64_t* log_step, double* log_t,
+                                  int64_t log_cap, int32_t* err_flags) {
+  const int n = min(*spk_count, spk_cap);
+  const int64_t base = *log_count;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = base + i;
+    if (o < log_cap) {
+      log_gid[o] = gid[i];
+      log_step[o] = step[i];
+      log_t[o] = t[i];
+    } else {
+      atomicOr(err_flags, 2);
+    }
+  }
+}
+
+__global__ void finalize_kernel(int32_t* spk_count, int32_t spk_cap, int32_t* log_count,
+                                int64_t log_cap) {
+  int64_t c = (int64_t)*log_count + min(*spk_count, spk_cap);
+  *log_count = (int32_t)(c < log_cap ? c : log_cap);
+  *spk_count = 0;
+}
+
+int launch_poisson(const PoissonArgs& a, int64_t k_from, int64_t k_to, void* stream) {
+  if (a.n == 0 || k_to <= k_from) return 0;
+  const int threads = 256;
+  const int blocks = (int)((a.n + threads - 1) / threads);
+  poisson_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(a, k_from, k_to);
+  return (int)cudaGetLastError();
+}
+
+int launch_route(const RouteArgs& a, int32_t max_spikes, void* stream) {
+  const int threads = 256;
+  int blocks = (max_spikes * 32 + threads - 1) / threads;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  if (blocks < 1) blocks = 1;
+  route_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int launch_log_append(const int32_t* spk_count, const int32_t* gid, const int32_t* step,
+                      const double* t, int32_t max_spikes, int32_t* log_count,
+                      int32_t* log_gid, int64_t* log_step, double* log_t, int64_t log_cap,
+                      int32_t* err_flags, void* stream) {
+  const int threads = 256;
+  int blocks = (max_spikes + threads - 1) / threads;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (blocks < 1) blocks = 1;
+  log_append_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(
+      spk_count, max_spikes, gid, step, t, log_count, log_gid, log_step, log_t, log_cap,
+      err_flags);
+  finalize_kernel<<<1, 1, 0, (cudaStream_t)stream>>>((int32_t*)spk_count, max_spikes, log_count,
+                                                     log_cap);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace pa

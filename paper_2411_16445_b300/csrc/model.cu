@@ -1,0 +1,1192 @@
+// model.cu -- host side of the C-ABI: descriptor validation, discretisation,
+// device layout, the epoch loop of pa_advance and the read-back calls.
+//
+// Host arithmetic that feeds the device (CV geometry, per-dt constants) is
+// compiled without floating-point contraction, so the FP64 path starts from
+// exactly the coefficients the plain definition gives.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/plastic_arbor.h"
+#include "engine.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_err(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return set_err(PA_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));       \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+int n_params_of(int kind) {
+  switch (kind) {
+    case PA_MECH_PAS: return 2;
+    case PA_MECH_HH: return 6;
+    case PA_MECH_EXPSYN: return 2;
+    case PA_MECH_GB: return 13;
+    case PA_MECH_STC: return 18;
+    case PA_MECH_STDP: return 8;
+  }
+  return -1;
+}
+bool is_point(int kind) {
+  return kind == PA_MECH_EXPSYN || kind == PA_MECH_GB || kind == PA_MECH_STC ||
+         kind == PA_MECH_STDP;
+}
+
+// A bump allocator over one cudaMalloc: every array of a model lives in it.
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0, cap = 0;
+  std::vector<std::pair<size_t, size_t>> plan;  // offset, bytes
+  size_t reserve(size_t bytes) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + bytes;
+    return off;
+  }
+};
+
+}  // namespace
+
+struct pa_model {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = PA_FP64;
+  bool tree = false;
+  double dt = 0;
+  uint64_t seed = 0;
+  int64_t n_cells = 0, n_cv = 0, n_conn = 0, n_groups = 0, n_lanes = 0, total_rows = 0;
+  int64_t step = 0;
+  int32_t E = 1, n_slots = 1;
+  int64_t poisson_epoch_done = -1;
+  int32_t max_spikes = 0;
+  int64_t log_cap = 0;
+  int32_t n_probe = 0;
+  int64_t probe_cap = 0, probe_samples = 0;
+  bool replay = false;
+  std::vector<int32_t> rep_gid;
+  std::vector<int64_t> rep_step;
+  size_t rep_pos = 0;
+  // host-side maps
+  std::vector<int32_t> lane_of_gid;       // gid -> lane
+  std::vector<int32_t> row_base;          // per group
+  std::vector<int32_t> cell_ncv;          // per gid
+  std::vector<int64_t> cell_cv_off;       // per gid, cell-major CV offsets
+  std::vector<int32_t> conn_stream;       // per connection
+  std::vector<int64_t> conn_elem;
+  std::vector<int32_t> conn_kind;         // PA_MECH_* of the connection
+  std::vector<double> conn_weight;
+  std::vector<double> conn_h0;
+  size_t elem_bytes_m = 8;
+  int n_streams = 0;
+  pa::StreamParams sp[pa::kMaxStreams];
+  int64_t s_nelem[pa::kMaxStreams];
+  // device
+  char* dmem = nullptr;
+  size_t dbytes = 0;
+  pa::EpochArgs ea;
+  pa::PoissonArgs pa_args;
+  pa::RouteArgs ra;
+  uint64_t* replay_bits = nullptr;
+  int32_t* rep_spk_count = nullptr;
+  int32_t* rep_spk_gid = nullptr;
+  int32_t* rep_spk_step = nullptr;
+  int32_t* log_count = nullptr;
+  int32_t* log_gid = nullptr;
+  int64_t* log_step = nullptr;
+  double* log_t = nullptr;
+  int32_t* err_flags = nullptr;
+  std::vector<uint64_t*> mask_bases;  // cmask/camask bases to clear per epoch
+  std::vector<int64_t> mask_elems;
+  // kernel statistics
+  bool time_kernels = false;
+  int64_t n_epoch_launches = 0, n_kernel_launches = 0;
+  double epoch_ms = 0, event_ms = 0;
+  std::vector<cudaEvent_t> ev_pool;                       // recycled events
+  struct Timed { cudaEvent_t a, b, c, d; };               // [a,b): Poisson, [b,c): epoch, [c,d): routing
+  std::vector<Timed> pending;
+};
+
+namespace {
+
+struct SynRec {
+  int64_t conn;
+  int32_t cv;
+};
+
+template <class T>
+std::vector<float> to_f32(const std::vector<T>& v) {
+  std::vector<float> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+  return o;
+}
+
+int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morphs,
+               int64_t n_morph, const pa_mechanism* mechs, int64_t n_mech,
+               const pa_connection* conns, int64_t n_conn, const pa_options* opt,
+               pa_model** out) {
+  using namespace pa;
+  if (!out) return set_err(PA_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!opt) return set_err(PA_ERR_ARG, "options are NULL");
+  if (n_cells < 0 || n_morph < 0 || n_mech < 0 || n_conn < 0)
+    return set_err(PA_ERR_ARG, "negative count");
+  if (n_cells > (1LL << 30) || n_conn > (1LL << 31) - 1)
+    return set_err(PA_ERR_ARG, "too many cells or connections");
+  if ((n_cells && !cells) || (n_morph && !morphs) || (n_mech && !mechs) || (n_conn && !conns))
+    return set_err(PA_ERR_ARG, "NULL descriptor array with a nonzero count");
+  const double dt = opt->dt;
+  if (!(dt > 0) || !std::isfinite(dt)) return set_err(PA_ERR_ARG, "dt must be positive");
+  if (opt->precision != PA_FP64 && opt->precision != PA_MIXED)
+    return set_err(PA_ERR_ARG, "precision must be PA_FP64 or PA_MIXED");
+  const bool mixed = opt->precision == PA_MIXED;
+  int max_e = opt->max_epoch_steps > 0 ? opt->max_epoch_steps : 64;
+  if (max_e > 64) return set_err(PA_ERR_ARG, "max_epoch_steps must be <= 64");
+
+  // ---- mechanisms -------------------------------------------------------------
+  for (int64_t j = 0; j < n_mech; ++j) {
+    int np = n_params_of(mechs[j].kind);
+    if (np < 0) return set_err(PA_ERR_ARG, "mechanism %lld: unknown kind %d", (long long)j, mechs[j].kind);
+    if (mechs[j].n_params != np || !mechs[j].params)
+      return set_err(PA_ERR_ARG, "mechanism %lld: expected %d parameters", (long long)j, np);
+    for (int i = 0; i < np; ++i)
+      if (!std::isfinite(mechs[j].params[i]))
+        return set_err(PA_ERR_ARG, "mechanism %lld: non-finite parameter %d", (long long)j, i);
+  }
+  // streams: one per point mechanism used by a connection, in table order
+  std::vector<int> mech_stream(n_mech, -1);
+  {
+    std::vector<char> used(n_mech, 0);
+    for (int64_t c = 0; c < n_conn; ++c) {
+      int m = conns[c].mech;
+      if (m < 0 || m >= n_mech || !is_point(mechs[m].kind))
+        return set_err(PA_ERR_ARG, "connection %lld: mechanism must be a synapse", (long long)c);
+      used[m] = 1;
+    }
+    int ns = 0, n_stc = 0;
+    for (int64_t m = 0; m < n_mech; ++m)
+      if (used[m]) {
+        if (ns == kMaxStreams) return set_err(PA_ERR_ARG, "more than %d synapse mechanisms in use", kMaxStreams);
+        if (mechs[m].kind == PA_MECH_STC) ++n_stc;
+        mech_stream[m] = ns++;
+      }
+    if (n_stc > 1) return set_err(PA_ERR_ARG, "at most one STC mechanism per model");
+  }
+
+  pa_model* M = new (std::nothrow) pa_model();
+  if (!M) return set_err(PA_ERR_OOM, "host allocation failed");
+  struct Guard {
+    pa_model*& m;
+    bool ok = false;
+    ~Guard() { if (!ok && m) pa_free_model(m); }
+  } guard{M};
+  M->device = opt->device;
+  M->stream = (cudaStream_t)opt->stream;
+  M->precision = opt->precision;
+  M->dt = dt;
+  M->seed = opt->seed;
+  M->n_cells = n_cells;
+  M->n_conn = n_conn;
+  M->elem_bytes_m = mixed ? 4 : 8;
+  M->time_kernels = (opt->flags & PA_FLAG_TIME_KERNELS) != 0;
+  CUDA_TRY(cudaSetDevice(M->device));
+
+  int n_streams = 0, stc_stream = -1;
+  int stream_mech[kMaxStreams];
+  for (int64_t m = 0; m < n_mech; ++m) {
+    int s = mech_stream[m];
+    if (s < 0) continue;
+    n_streams = std::max(n_streams, s + 1);
+    stream_mech[s] = (int)m;
+    const double* p = mechs[m].params;
+    StreamParams& P = M->sp[s];
+    std::memset(&P, 0, sizeof P);
+    P.dc_steps = -1;
+    P.e = p[1];
+    P.decay_g = std::exp(-dt / p[0]);
+    switch (mechs[m].kind) {
+      case PA_MECH_EXPSYN: P.kind = SK_EXPSYN; break;
+      case PA_MECH_GB:
+        P.kind = SK_GB;
+        P.decay_c = std::exp(-dt / p[2]);
+        P.c_pre = p[3]; P.c_post = p[4]; P.theta_p = p[5]; P.theta_d = p[6];
+        P.gamma_p = p[7]; P.gamma_d = p[8]; P.rate_w = dt / p[9]; P.w_star = p[10];
+        P.dc_steps = (int32_t)std::llround(p[11] / dt);
+        break;
+      case PA_MECH_STC:
+        P.kind = SK_STC;
+        stc_stream = s;
+        P.decay_c = std::exp(-dt / p[2]);
+        P.c_pre = p[3]; P.c_post = p[4]; P.theta_p = p[5]; P.theta_d = p[6];
+        P.gamma_p = p[7]; P.gamma_d = p[8];
+        P.rate_h = dt / p[9]; P.rate_z = dt / p[10]; P.rate_p = dt / p[11];
+        P.h0 = p[12]; P.theta_tag = p[13]; P.theta_pro = p[14]; P.p_max = p[15];
+        P.f_int = p[16];
+        P.dc_steps = (int32_t)std::llround(p[17] / dt);
+        break;
+      case PA_MECH_STDP:
+        P.kind = SK_STDP;
+        P.decay_pre = std::exp(-dt / p[2]);
+        P.decay_post = std::exp(-dt / p[3]);
+        P.a_pre = p[4]; P.a_post = p[5]; P.w_max = p[7];
+        break;
+    }
+    if ((P.kind == SK_GB || P.kind == SK_STC) && P.dc_steps < 0)
+      return set_err(PA_ERR_ARG, "mechanism %lld: negative t_c_delay", (long long)m);
+  }
+  M->n_streams = n_streams;
+
+  // ---- morphologies and cells -------------------------------------------------
+  for (int64_t mo = 0; mo < n_morph; ++mo) {
+    const pa_morphology& g = morphs[mo];
+    if (g.n_cv < 1 || g.n_cv > 32767)
+      return set_err(PA_ERR_ARG, "morphology %lld: n_cv must be in [1, 32767]", (long long)mo);
+    if (!g.parent || !g.length_um || !g.diam_um || !g.region)
+      return set_err(PA_ERR_ARG, "morphology %lld: NULL array", (long long)mo);
+    for (int i = 0; i < g.n_cv; ++i) {
+      int p = g.parent[i];
+      if ((i == 0 && p != -1) || (i > 0 && (p < 0 || p >= i)))
+        return set_err(PA_ERR_ARG, "morphology %lld: parent[%d] = %d invalid", (long long)mo, i, p);
+      if (!(g.length_um[i] > 0) || !(g.diam_um[i] > 0) || !std::isfinite(g.length_um[i]) ||
+          !std::isfinite(g.diam_um[i]))
+        return set_err(PA_ERR_ARG, "morphology %lld: CV %d has non-positive length/diameter", (long long)mo, i);
+      if (i > 0 && p != i - 1) M->tree = true;
+    }
+  }
+  M->cell_ncv.resize(n_cells);
+  M->cell_cv_off.resize(n_cells + 1, 0);
+  for (int64_t c = 0; c < n_cells; ++c) {
+    const pa_cell& cl = cells[c];
+    if (cl.morph < 0 || cl.morph >= n_morph)
+      return set_err(PA_ERR_ARG, "cell %lld: bad morphology index", (long long)c);
+    for (int which = 0; which < 2; ++which) {
+      int m = which == 0 ? cl.soma_mech : cl.dend_mech;
+      if (m < 0 || m >= n_mech || (mechs[m].kind != PA_MECH_PAS && mechs[m].kind != PA_MECH_HH))
+        return set_err(PA_ERR_ARG, "cell %lld: soma/dendrite mechanism must be pas or hh", (long long)c);
+    }
+    const pa_morphology& g = morphs[cl.morph];
+    for (int i = 0; i < g.n_cv; ++i) {
+      int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
+      if (mechs[m].kind == PA_MECH_HH && i != 0)
+        return set_err(PA_ERR_ARG, "cell %lld: HH is supported on the soma CV (CV 0) only", (long long)c);
+    }
+    if (!(cl.cm > 0) || !(cl.ra > 0))
+      return set_err(PA_ERR_ARG, "cell %lld: cm and ra must be positive", (long long)c);
+    M->cell_ncv[c] = g.n_cv;
+    M->cell_cv_off[c + 1] = M->cell_cv_off[c] + g.n_cv;
+  }
+  M->n_cv = M->cell_cv_off[n_cells];
+
+  // sort cells by CV count (descending), deal into groups of 32 lanes
+  std::vector<int32_t> order(n_cells);
+  for (int64_t c = 0; c < n_cells; ++c) order[c] = (int32_t)c;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t x, int32_t y) { return M->cell_ncv[x] > M->cell_ncv[y]; });
+  const int64_t n_groups = (n_cells + kLanes - 1) / kLanes;
+  const int64_t n_lanes = n_groups * kLanes;
+  M->n_groups = n_groups;
+  M->n_lanes = n_lanes;
+  M->lane_of_gid.assign(n_cells, -1);
+  std::vector<int32_t> lane_gid(n_lanes, -1), lane_ncv(n_lanes, 0);
+  for (int64_t L = 0; L < n_cells; ++L) {
+    lane_gid[L] = order[L];
+    lane_ncv[L] = M->cell_ncv[order[L]];
+    M->lane_of_gid[order[L]] = (int32_t)L;
+  }
+  M->row_base.assign(n_groups + 1, 0);
+  for (int64_t g = 0; g < n_groups; ++g) {
+    int64_t rows = lane_ncv[g * kLanes];
+    if ((int64_t)M->row_base[g] + rows > (1LL << 26))
+      return set_err(PA_ERR_ARG, "model too large: more than 2^31 padded CVs");
+    M->row_base[g + 1] = M->row_base[g] + (int32_t)rows;
+  }
+  M->total_rows = M->row_base[n_groups];
+  const int64_t n_elem = M->total_rows * kLanes;
+  auto elem = [&](int64_t L, int row) -> int64_t {
+    return ((int64_t)M->row_base[L / kLanes] + row) * kLanes + (L % kLanes);
+  };
+
+  // ---- CV discretisation (a CV is a cylinder; Eq. cable) -----------------------
+  std::vector<double> h_cdt(n_elem, 0.0), h_dc(n_elem, 1.0), h_em(n_elem, 0.0),
+      h_a(n_elem, 0.0), h_V(n_elem, 0.0);
+  std::vector<int16_t> h_par, h_och, h_ocn;
+  if (M->tree) {
+    h_par.assign(n_elem, -1);
+    h_och.assign(n_elem, -1);
+    h_ocn.assign(n_elem, -1);
+  }
+  std::vector<uint8_t> h_is_hh(n_lanes, 0);
+  std::vector<double> h_hhg(3 * n_lanes, 0.0), h_hhe(3 * n_lanes, 0.0);
+  std::vector<double> h_iinj(n_lanes, 0.0), h_thresh(n_lanes, 0.0);
+  std::vector<int64_t> h_kon(n_lanes, 0), h_koff(n_lanes, 0);
+  std::vector<double> rhalf, gi_v, gax, cdt_v, dcc;
+  for (int64_t L = 0; L < n_cells; ++L) {
+    const pa_cell& cl = cells[lane_gid[L]];
+    const pa_morphology& g = morphs[cl.morph];
+    const int n = g.n_cv;
+    rhalf.assign(n, 0.0);
+    gi_v.assign(n, 0.0);
+    gax.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      const double Lc = g.length_um[i], dia = g.diam_um[i];
+      const double r = 0.5 * dia;
+      const double A = (kPi * dia) * Lc;               // um2
+      const double cap = (cl.cm * A) * 1e-5;            // nF
+      const int64_t e = elem(L, i);
+      h_cdt[e] = cap / dt;                              // uS
+      rhalf[i] = ((cl.ra * (0.5 * Lc)) / (kPi * (r * r))) * 1e-2;  // Mohm
+      const int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
+      const double* p = mechs[m].params;
+      if (mechs[m].kind == PA_MECH_PAS) {
+        const double gp = (p[0] * A) * 1e-2;            // S/cm2 * um2 -> uS
+        h_em[e] = gp * p[1];
+        h_dc[e] = gp;                                   // leak, folded in below
+      } else {
+        h_is_hh[L] = 1;
+        h_hhg[L] = (p[0] * A) * 1e-2;
+        h_hhg[n_lanes + L] = (p[1] * A) * 1e-2;
+        h_hhg[2 * n_lanes + L] = (p[2] * A) * 1e-2;
+        h_hhe[L] = p[3];
+        h_hhe[n_lanes + L] = p[4];
+        h_hhe[2 * n_lanes + L] = p[5];
+        h_dc[e] = 0.0;                                  // gates enter per step
+        h_em[e] = 0.0;
+      }
+      h_V[e] = cl.v_init;
+    }
+    // axial conductance of two half-cylinders in series, summed in CV order
+    for (int i = 1; i < n; ++i) {
+      const int p = g.parent[i];
+      const double gi = 1.0 / (rhalf[i] + rhalf[p]);
+      h_a[elem(L, i)] = -gi;
+      gax[i] += gi;
+      gax[p] += gi;
+    }
+    for (int i = 0; i < n; ++i) {
+      const int64_t e = elem(L, i);
+      const int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
+      const double base = h_cdt[e] + gax[i];
+      h_dc[e] = mechs[m].kind == PA_MECH_PAS ? base + h_dc[e] : base;
+    }
+    if (M->tree) {
+      // other (non-first) children of each node, linked from the highest index down
+      for (int i = 1; i < n; ++i) h_par[elem(L, i)] = (int16_t)g.parent[i];
+      for (int i = 1; i < n; ++i) {
+        const int p = g.parent[i];
+        if (i == p + 1) continue;  // the first child is eliminated through registers
+        // children are visited in increasing i: push to the front -> descending list
+        h_ocn[elem(L, i)] = h_och[elem(L, p)];
+        h_och[elem(L, p)] = (int16_t)i;
+      }
+    }
+    h_iinj[L] = cl.i_step;
+    h_kon[L] = std::llround(cl.t_on / dt);
+    h_koff[L] = cl.t_off > 1e15 ? INT64_MAX : std::llround(cl.t_off / dt);
+    h_thresh[L] = cl.threshold;
+  }
+
+  // ---- synapses: one per connection, streams by mechanism -------------------------
+  M->conn_stream.assign(n_conn, -1);
+  M->conn_elem.assign(n_conn, -1);
+  M->conn_kind.assign(n_conn, 0);
+  M->conn_weight.assign(n_conn, 0.0);
+  M->conn_h0.assign(n_conn, 0.0);
+  std::vector<std::vector<SynRec>> per_lane(n_lanes * (size_t)std::max(n_streams, 1));
+  int64_t max_delay = 1, min_delay = INT64_MAX;
+  int32_t max_dc = 0;
+  std::vector<int64_t> n_out(n_cells + 1, 0);
+  std::vector<int32_t> conn_D(n_conn, 0);
+  for (int64_t c = 0; c < n_conn; ++c) {
+    const pa_connection& k = conns[c];
+    if (k.dst_gid < 0 || k.dst_gid >= n_cells)
+      return set_err(PA_ERR_ARG, "connection %lld: bad dst_gid", (long long)c);
+    if (k.dst_cv < 0 || k.dst_cv >= M->cell_ncv[k.dst_gid])
+      return set_err(PA_ERR_ARG, "connection %lld: bad dst_cv", (long long)c);
+    if (!std::isfinite(k.weight)) return set_err(PA_ERR_ARG, "connection %lld: bad weight", (long long)c);
+    const int s = mech_stream[k.mech];
+    const StreamParams& P = M->sp[s];
+    if (k.src_gid == PA_SRC_POISSON) {
+      const double x = ((k.rate_hz * dt) * 1e-3) * 4294967296.0;
+      if (!(x >= 0) || x >= 4294967296.0)
+        return set_err(PA_ERR_ARG, "connection %lld: rate_hz * dt out of range", (long long)c);
+    } else {
+      if (k.src_gid < 0 || k.src_gid >= n_cells)
+        return set_err(PA_ERR_ARG, "connection %lld: bad src_gid", (long long)c);
+      const int64_t D = std::llround(k.delay_ms / dt);
+      if (!(D >= 1) || D > (1 << 30))
+        return set_err(PA_ERR_ARG, "connection %lld: delay must be at least one step", (long long)c);
+      conn_D[c] = (int32_t)D;
+      max_delay = std::max(max_delay, D);
+      min_delay = std::min(min_delay, D);
+      n_out[k.src_gid + 1]++;
+    }
+    if (P.dc_steps > max_dc) max_dc = P.dc_steps;
+    const int64_t L = M->lane_of_gid[k.dst_gid];
+    per_lane[(size_t)s * n_lanes + L].push_back({c, k.dst_cv});
+    M->conn_kind[c] = mechs[k.mech].kind;
+    M->conn_weight[c] = k.weight;
+    if (mechs[k.mech].kind == PA_MECH_STC) M->conn_h0[c] = mechs[k.mech].params[12];
+  }
+  int E = (int)std::min<int64_t>(min_delay == INT64_MAX ? max_e : min_delay, max_e);
+  if (E < 1) E = 1;
+  M->E = E;
+  M->n_slots = (int32_t)((max_delay + max_dc + E - 1) / E + 2);
+
+  // per stream: canonical order (CV, connection) per lane, padded rows per group
+  std::vector<std::vector<int32_t>> s_sbase(n_streams);
+  std::vector<std::vector<int32_t>> s_cvf(n_streams);
+  std::vector<std::vector<double>> s_weight(n_streams), s_w(n_streams);
+  std::vector<uint8_t> h_has_stc(n_lanes, 0);
+  for (int s = 0; s < n_streams; ++s) {
+    s_sbase[s].assign(n_groups + 1, 0);
+    for (int64_t g = 0; g < n_groups; ++g) {
+      size_t mx = 0;
+      for (int l = 0; l < kLanes; ++l) {
+        auto& v = per_lane[(size_t)s * n_lanes + g * kLanes + l];
+        std::sort(v.begin(), v.end(), [](const SynRec& x, const SynRec& y) {
+          return x.cv != y.cv ? x.cv < y.cv : x.conn < y.conn;
+        });
+        mx = std::max(mx, v.size());
+      }
+      if ((int64_t)s_sbase[s][g] + (int64_t)mx > (1LL << 26))
+        return set_err(PA_ERR_ARG, "too many synapses in one stream");
+      s_sbase[s][g + 1] = s_sbase[s][g] + (int32_t)mx;
+    }
+    const int64_t ne = (int64_t)s_sbase[s][n_groups] * kLanes;
+    M->s_nelem[s] = ne;
+    s_cvf[s].assign(ne, -1);
+    s_weight[s].assign(ne, 0.0);
+    s_w[s].assign(ne, 0.0);
+  }
+  // first-on-CV flags follow the canonical (mechanism, CV, connection) order
+  for (int64_t L = 0; L < n_cells; ++L) {
+    std::vector<char> touched(M->cell_ncv[lane_gid[L]], 0);
+    const int64_t g = L / kLanes, l = L % kLanes;
+    for (int s = 0; s < n_streams; ++s) {
+      const int m = stream_mech[s];
+      const double* p = mechs[m].params;
+      auto& v = per_lane[(size_t)s * n_lanes + L];
+      for (size_t j = 0; j < v.size(); ++j) {
+        const int64_t e = ((int64_t)s_sbase[s][g] + (int64_t)j) * kLanes + l;
+        const int cv = v[j].cv;
+        s_cvf[s][e] = (cv << 1) | (touched[cv] ? 0 : 1);
+        touched[cv] = 1;
+        s_weight[s][e] = conns[v[j].conn].weight;
+        if (M->sp[s].kind == SK_GB) s_w[s][e] = p[12];
+        if (M->sp[s].kind == SK_STDP) s_w[s][e] = p[6];
+        if (M->sp[s].kind == SK_STC) {
+          s_w[s][e] = p[12];
+          h_has_stc[L] = 1;
+        }
+        M->conn_stream[v[j].conn] = s;
+        M->conn_elem[v[j].conn] = e;
+      }
+    }
+  }
+  per_lane.clear();
+  per_lane.shrink_to_fit();
+
+  // Poisson drives
+  std::vector<int32_t> ps_stream, ps_dc;
+  std::vector<int64_t> ps_conn;
+  std::vector<int64_t> ps_elem;
+  std::vector<uint32_t> ps_thr;
+  for (int64_t c = 0; c < n_conn; ++c) {
+    if (conns[c].src_gid != PA_SRC_POISSON) continue;
+    const int s = M->conn_stream[c];
+    const double x = ((conns[c].rate_hz * dt) * 1e-3) * 4294967296.0;
+    ps_stream.push_back(s);
+    ps_elem.push_back(M->conn_elem[c]);
+    ps_conn.push_back(conns[c].poisson_id >= 0 ? conns[c].poisson_id : c);
+    ps_thr.push_back((uint32_t)std::floor(x));
+    ps_dc.push_back(M->sp[s].dc_steps);
+  }
+  // CSR of recurrent connections by source gid (connection order within a row)
+  for (int64_t c = 0; c < n_cells; ++c) n_out[c + 1] += n_out[c];
+  const int64_t n_edges = n_out[n_cells];
+  std::vector<uint8_t> out_stream(n_edges);
+  std::vector<int64_t> out_elem(n_edges);
+  std::vector<int32_t> out_delay(n_edges);
+  {
+    std::vector<int64_t> fill(n_out.begin(), n_out.end() - 1);
+    for (int64_t c = 0; c < n_conn; ++c) {
+      const int src = conns[c].src_gid;
+      if (src == PA_SRC_POISSON) continue;
+      const int64_t q = fill[src]++;
+      out_stream[q] = (uint8_t)M->conn_stream[c];
+      out_elem[q] = M->conn_elem[c];
+      out_delay[q] = conn_D[c];
+    }
+  }
+  // probes
+  M->n_probe = opt->n_probe;
+  if (opt->n_probe < 0 || (opt->n_probe > 0 && (!opt->probe_gid || !opt->probe_cv)))
+    return set_err(PA_ERR_ARG, "bad probe list");
+  std::vector<int32_t> probe_ptr(n_lanes + 1, 0), probe_row, probe_id;
+  {
+    std::vector<std::vector<std::pair<int, int>>> pl(n_lanes);
+    for (int i = 0; i < opt->n_probe; ++i) {
+      const int gid = opt->probe_gid[i], cv = opt->probe_cv[i];
+      if (gid < 0 || gid >= n_cells || cv < 0 || cv >= M->cell_ncv[gid])
+        return set_err(PA_ERR_ARG, "probe %d: bad location", i);
+      pl[M->lane_of_gid[gid]].push_back({cv, i});
+    }
+    for (int64_t L = 0; L < n_lanes; ++L) {
+      probe_ptr[L + 1] = probe_ptr[L] + (int32_t)pl[L].size();
+      for (auto& q : pl[L]) {
+        probe_row.push_back(q.first);
+        probe_id.push_back(q.second);
+      }
+    }
+  }
+  M->probe_cap = opt->n_probe > 0 ? (opt->probe_capacity > 0 ? opt->probe_capacity : 65536) : 0;
+  M->max_spikes = (int32_t)std::min<int64_t>(n_lanes * ((E + 1) / 2) + 32, (1LL << 31) - 1);
+  M->log_cap = opt->spike_capacity > 0 ? opt->spike_capacity
+                                       : std::max<int64_t>(1 << 20, (int64_t)n_cells * 64);
+  if (M->log_cap > (1LL << 31) - 1) M->log_cap = (1LL << 31) - 1;
+
+  // ---- device layout ------------------------------------------------------------
+  const size_t tm = M->elem_bytes_m;   // synapse state element size (FP32 in mixed)
+  Arena ar;
+  auto R = [&](size_t bytes) { return ar.reserve(bytes); };
+  const size_t o_rowbase = R(sizeof(int32_t) * (n_groups + 1));
+  const size_t o_ncv = R(sizeof(int32_t) * n_lanes);
+  const size_t o_gid = R(sizeof(int32_t) * n_lanes);
+  const size_t o_V = R(8 * n_elem);
+  const size_t o_cdt = R(8 * n_elem), o_dc = R(8 * n_elem), o_em = R(8 * n_elem),
+               o_a = R(8 * n_elem), o_gs = R(tm * n_elem), o_es = R(tm * n_elem);
+  const size_t o_f = R(8 * n_elem), o_xp = R(8 * n_elem);
+  size_t o_par = 0, o_och = 0, o_ocn = 0;
+  if (M->tree) {
+    o_par = R(2 * n_elem);
+    o_och = R(2 * n_elem);
+    o_ocn = R(2 * n_elem);
+  }
+  const size_t o_ishh = R(n_lanes), o_hhg = R(8 * 3 * n_lanes), o_hhe = R(8 * 3 * n_lanes),
+               o_gate = R(8 * 3 * n_lanes), o_iinj = R(8 * n_lanes), o_kon = R(8 * n_lanes),
+               o_koff = R(8 * n_lanes), o_th = R(8 * n_lanes), o_sp = R(n_lanes),
+               o_prp = R(8 * n_lanes), o_hasstc = R(n_lanes), o_rbits = R(8 * n_lanes);
+  size_t o_s[kMaxStreams][10];
+  for (int s = 0; s < n_streams; ++s) {
+    const int64_t ne = M->s_nelem[s];
+    const int kind = M->sp[s].kind;
+    o_s[s][0] = R(sizeof(int32_t) * (n_groups + 1));
+    o_s[s][1] = R(4 * ne);                    // cvf
+    o_s[s][2] = R(tm * ne);                   // weight
+    o_s[s][3] = R(tm * ne);                   // g
+    o_s[s][4] = (kind == SK_GB || kind == SK_STC) ? R(8 * ne) : 0;              // c
+    o_s[s][5] = (kind != SK_EXPSYN) ? R(8 * ne) : 0;                            // w / h
+    o_s[s][6] = (kind == SK_STC) ? R(8 * ne) : 0;                               // z
+    o_s[s][7] = (kind == SK_STDP) ? R(tm * ne) : 0;                             // apre
+    o_s[s][8] = (kind == SK_STDP) ? R(tm * ne) : 0;                             // apost
+    o_s[s][9] = R(8 * ne * (size_t)M->n_slots * ((kind == SK_GB || kind == SK_STC) ? 2 : 1));
+  }
+  const size_t np = ps_conn.size();
+  const size_t o_ps_stream = R(4 * np), o_ps_elem = R(8 * np), o_ps_conn = R(8 * np),
+               o_ps_thr = R(4 * np), o_ps_dc = R(4 * np);
+  const size_t o_out_ptr = R(8 * (n_cells + 1)), o_out_stream = R(n_edges),
+               o_out_elem = R(8 * n_edges), o_out_delay = R(4 * n_edges);
+  const size_t o_pptr = R(4 * (n_lanes + 1)), o_prow = R(4 * probe_row.size()),
+               o_pid = R(4 * probe_id.size()),
+               o_pbuf = R(8 * (size_t)M->probe_cap * (size_t)std::max(M->n_probe, 0));
+  const size_t o_spk_count = R(4), o_spk_gid = R(4 * (size_t)M->max_spikes),
+               o_spk_step = R(4 * (size_t)M->max_spikes), o_spk_t = R(8 * (size_t)M->max_spikes);
+  const size_t o_rep_count = R(4), o_rep_gid = R(4 * (size_t)M->max_spikes),
+               o_rep_step = R(4 * (size_t)M->max_spikes);
+  const size_t o_log_count = R(4), o_log_gid = R(4 * (size_t)M->log_cap),
+               o_log_step = R(8 * (size_t)M->log_cap), o_log_t = R(8 * (size_t)M->log_cap);
+  const size_t o_err = R(4);
+
+  const size_t total = ar.used;
+  cudaError_t ce = cudaMalloc((void**)&M->dmem, total);
+  if (ce != cudaSuccess) {
+    M->dmem = nullptr;
+    return set_err(ce == cudaErrorMemoryAllocation ? PA_ERR_OOM : PA_ERR_CUDA,
+                   "cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(ce));
+  }
+  M->dbytes = total;
+  CUDA_TRY(cudaMemsetAsync(M->dmem, 0, total, M->stream));
+
+  // upload every non-zero array (pageable copies: the source may go out of scope
+  // as soon as the call returns)
+  int up_rc = 0;
+  auto putv = [&](size_t off, const auto& v) {
+    if (up_rc || v.empty()) return;
+    cudaError_t e3 = cudaMemcpyAsync(M->dmem + off, v.data(), v.size() * sizeof(v[0]),
+                                     cudaMemcpyHostToDevice, M->stream);
+    if (e3 != cudaSuccess) up_rc = set_err(PA_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e3));
+  };
+  putv(o_rowbase, M->row_base);
+  putv(o_ncv, lane_ncv);
+  putv(o_gid, lane_gid);
+  putv(o_V, h_V);
+  putv(o_cdt, h_cdt); putv(o_dc, h_dc); putv(o_em, h_em); putv(o_a, h_a);
+  putv(o_hhg, h_hhg); putv(o_hhe, h_hhe);
+  if (M->tree) { putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn); }
+  putv(o_ishh, h_is_hh);
+  putv(o_iinj, h_iinj); putv(o_kon, h_kon); putv(o_koff, h_koff); putv(o_th, h_thresh);
+  putv(o_hasstc, h_has_stc);
+  for (int s = 0; s < n_streams; ++s) {
+    putv(o_s[s][0], s_sbase[s]);
+    putv(o_s[s][1], s_cvf[s]);
+    if (mixed) putv(o_s[s][2], to_f32(s_weight[s])); else putv(o_s[s][2], s_weight[s]);
+    if (o_s[s][5]) putv(o_s[s][5], s_w[s]);
+  }
+  putv(o_ps_stream, ps_stream); putv(o_ps_elem, ps_elem); putv(o_ps_conn, ps_conn);
+  putv(o_ps_thr, ps_thr); putv(o_ps_dc, ps_dc);
+  putv(o_out_ptr, n_out); putv(o_out_stream, out_stream); putv(o_out_elem, out_elem);
+  putv(o_out_delay, out_delay);
+  putv(o_pptr, probe_ptr); putv(o_prow, probe_row); putv(o_pid, probe_id);
+  if (up_rc) return up_rc;
+  CUDA_TRY(cudaStreamSynchronize(M->stream));
+
+  char* D = M->dmem;
+  auto P8 = [&](size_t o) { return (void*)(D + o); };
+  EpochArgs& A = M->ea;
+  std::memset(&A, 0, sizeof A);
+  A.n_groups = (int32_t)n_groups;
+  A.dt = dt;
+  A.row_base = (const int32_t*)P8(o_rowbase);
+  A.ncv = (const int32_t*)P8(o_ncv);
+  A.gid = (const int32_t*)P8(o_gid);
+  A.V = (double*)P8(o_V);
+  A.cdt = (const double*)P8(o_cdt); A.dc = (const double*)P8(o_dc);
+  A.em = (const double*)P8(o_em); A.a = (const double*)P8(o_a);
+  A.gs = P8(o_gs); A.es = P8(o_es);
+  A.f = (double*)P8(o_f); A.xp = (double*)P8(o_xp);
+  if (M->tree) {
+    A.par = (const int16_t*)P8(o_par);
+    A.och_head = (const int16_t*)P8(o_och);
+    A.och_next = (const int16_t*)P8(o_ocn);
+  }
+  A.is_hh = (const uint8_t*)P8(o_ishh);
+  A.hh_g = (const double*)P8(o_hhg); A.hh_e = (const double*)P8(o_hhe);
+  A.gate = (double*)P8(o_gate);
+  A.iinj = (const double*)P8(o_iinj);
+  A.k_on = (const int64_t*)P8(o_kon); A.k_off = (const int64_t*)P8(o_koff);
+  A.thresh = (const double*)P8(o_th);
+  A.spiked_prev = (uint8_t*)P8(o_sp);
+  A.prp = (double*)P8(o_prp);
+  A.has_stc = (const uint8_t*)P8(o_hasstc);
+  A.stc_stream = stc_stream;
+  A.n_lanes = n_lanes;
+  A.n_streams = n_streams;
+  M->mask_bases.clear();
+  M->mask_elems.clear();
+  for (int s = 0; s < n_streams; ++s) {
+    A.sp[s] = M->sp[s];
+    StreamDev& sd = A.sd[s];
+    const int64_t ne = M->s_nelem[s];
+    const int kind = M->sp[s].kind;
+    sd.sbase = (const int32_t*)P8(o_s[s][0]);
+    sd.cvf = (const int32_t*)P8(o_s[s][1]);
+    sd.weight = P8(o_s[s][2]);
+    sd.g = P8(o_s[s][3]);
+    sd.c = o_s[s][4] ? (double*)P8(o_s[s][4]) : nullptr;
+    sd.w = o_s[s][5] ? (double*)P8(o_s[s][5]) : nullptr;
+    sd.z = o_s[s][6] ? (double*)P8(o_s[s][6]) : nullptr;
+    sd.apre = o_s[s][7] ? P8(o_s[s][7]) : nullptr;
+    sd.apost = o_s[s][8] ? P8(o_s[s][8]) : nullptr;
+    sd.cmask = (uint64_t*)P8(o_s[s][9]);
+    sd.camask = (kind == SK_GB || kind == SK_STC) ? sd.cmask + ne * M->n_slots : nullptr;
+    sd.n_elem = ne;
+    M->mask_bases.push_back(sd.cmask);
+    M->mask_elems.push_back(ne);
+    if (sd.camask) {
+      M->mask_bases.push_back(sd.camask);
+      M->mask_elems.push_back(ne);
+    }
+  }
+  A.spk_count = (int32_t*)P8(o_spk_count);
+  A.spk_gid = (int32_t*)P8(o_spk_gid);
+  A.spk_step = (int32_t*)P8(o_spk_step);
+  A.spk_t = (double*)P8(o_spk_t);
+  A.spk_cap = M->max_spikes;
+  A.replay_bits = (const uint64_t*)P8(o_rbits);
+  M->replay_bits = (uint64_t*)P8(o_rbits);
+  A.probe_ptr = (const int32_t*)P8(o_pptr);
+  A.probe_row = (const int32_t*)P8(o_prow);
+  A.probe_id = (const int32_t*)P8(o_pid);
+  A.probe_buf = (double*)P8(o_pbuf);
+  A.probe_cap = M->probe_cap;
+  A.n_probe = M->n_probe;
+  A.err_flags = (int32_t*)P8(o_err);
+  M->err_flags = A.err_flags;
+
+  PoissonArgs& PA = M->pa_args;
+  std::memset(&PA, 0, sizeof PA);
+  PA.E = E;
+  PA.n_slots = M->n_slots;
+  PA.seed = M->seed;
+  PA.n = (int64_t)np;
+  PA.stream = (const int32_t*)P8(o_ps_stream);
+  PA.elem = (const int64_t*)P8(o_ps_elem);
+  PA.conn = (const int64_t*)P8(o_ps_conn);
+  PA.thr = (const uint32_t*)P8(o_ps_thr);
+  PA.dc_steps = (const int32_t*)P8(o_ps_dc);
+  RouteArgs& RA = M->ra;
+  std::memset(&RA, 0, sizeof RA);
+  RA.E = E;
+  RA.n_slots = M->n_slots;
+  RA.spk_cap = M->max_spikes;
+  RA.spk_count = A.spk_count;
+  RA.spk_gid = A.spk_gid;
+  RA.spk_step = A.spk_step;
+  RA.out_ptr = (const int64_t*)P8(o_out_ptr);
+  RA.out_stream = (const uint8_t*)P8(o_out_stream);
+  RA.out_elem = (const int64_t*)P8(o_out_elem);
+  RA.out_delay = (const int32_t*)P8(o_out_delay);
+  for (int s = 0; s < n_streams; ++s) {
+    PA.cmask[s] = A.sd[s].cmask;
+    PA.camask[s] = A.sd[s].camask;
+    PA.n_elem[s] = M->s_nelem[s];
+    RA.cmask[s] = A.sd[s].cmask;
+    RA.camask[s] = A.sd[s].camask;
+    RA.n_elem[s] = M->s_nelem[s];
+    RA.dc_steps[s] = M->sp[s].dc_steps;
+  }
+  M->rep_spk_count = (int32_t*)P8(o_rep_count);
+  M->rep_spk_gid = (int32_t*)P8(o_rep_gid);
+  M->rep_spk_step = (int32_t*)P8(o_rep_step);
+  M->log_count = (int32_t*)P8(o_log_count);
+  M->log_gid = (int32_t*)P8(o_log_gid);
+  M->log_step = (int64_t*)P8(o_log_step);
+  M->log_t = (double*)P8(o_log_t);
+
+  // initial HH gates at their steady state for v_init, from the kernels' own
+  // rate functions
+  {
+    std::vector<double> vin(n_lanes, 0.0);
+    for (int64_t L = 0; L < n_cells; ++L) vin[L] = cells[lane_gid[L]].v_init;
+    double* dv = nullptr;
+    CUDA_TRY(cudaMalloc((void**)&dv, sizeof(double) * n_lanes));
+    cudaError_t e2 = cudaMemcpyAsync(dv, vin.data(), sizeof(double) * n_lanes,
+                                     cudaMemcpyHostToDevice, M->stream);
+    int rc = 0;
+    if (e2 == cudaSuccess) {
+      rc = mixed ? launch_init_gates_mixed(dv, A.gate, n_lanes, A.is_hh, M->stream)
+                 : launch_init_gates_fp64(dv, A.gate, n_lanes, A.is_hh, M->stream);
+      e2 = cudaStreamSynchronize(M->stream);
+    }
+    cudaFree(dv);
+    if (e2 != cudaSuccess || rc != 0)
+      return set_err(PA_ERR_CUDA, "gate initialisation failed: %s",
+                     cudaGetErrorString(e2 != cudaSuccess ? e2 : (cudaError_t)rc));
+  }
+  guard.ok = true;
+  *out = M;
+  return PA_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+namespace {
+
+int check_device_errors(pa_model* M) {
+  int32_t flags = 0;
+  CUDA_TRY(cudaMemcpyAsync(&flags, M->err_flags, 4, cudaMemcpyDeviceToHost, M->stream));
+  CUDA_TRY(cudaStreamSynchronize(M->stream));
+  if (flags) {
+    CUDA_TRY(cudaMemsetAsync(M->err_flags, 0, 4, M->stream));
+    return set_err(PA_ERR_CAPACITY, "%s%s",
+                   (flags & 1) ? "probe buffer full (read probes more often or raise probe_capacity); " : "",
+                   (flags & 2) ? "spike record full (read spikes more often or raise spike_capacity)" : "");
+  }
+  return PA_OK;
+}
+
+cudaEvent_t take_event(pa_model* M) {
+  if (!M->ev_pool.empty()) {
+    cudaEvent_t e = M->ev_pool.back();
+    M->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+int collect_timings(pa_model* M) {
+  if (M->pending.empty()) return PA_OK;
+  CUDA_TRY(cudaStreamSynchronize(M->stream));
+  for (auto& t : M->pending) {
+    float x = 0, y = 0, z = 0;
+    CUDA_TRY(cudaEventElapsedTime(&x, t.a, t.b));
+    CUDA_TRY(cudaEventElapsedTime(&y, t.b, t.c));
+    CUDA_TRY(cudaEventElapsedTime(&z, t.c, t.d));
+    M->event_ms += x + z;
+    M->epoch_ms += y;
+    for (cudaEvent_t e : {t.a, t.b, t.c, t.d}) M->ev_pool.push_back(e);
+  }
+  M->pending.clear();
+  return PA_OK;
+}
+
+int run_window(pa_model* M, int64_t k_begin, int64_t k_end) {
+  using namespace pa;
+  const int64_t e = k_begin / M->E;
+  const int64_t k0 = e * M->E;
+  pa_model::Timed tm{nullptr, nullptr, nullptr, nullptr};
+  if (M->time_kernels) {
+    if (M->pending.size() >= 4096) {
+      int rc = collect_timings(M);
+      if (rc) return rc;
+    }
+    tm = {take_event(M), take_event(M), take_event(M), take_event(M)};
+    if (!tm.a || !tm.b || !tm.c || !tm.d) return set_err(PA_ERR_CUDA, "cudaEventCreate failed");
+    CUDA_TRY(cudaEventRecord(tm.a, M->stream));
+  }
+  if (M->poisson_epoch_done != e) {
+    M->pa_args.k0 = k0;
+    int rc = launch_poisson(M->pa_args, k0, k0 + M->E, M->stream);
+    if (rc) return set_err(PA_ERR_CUDA, "poisson launch: %s", cudaGetErrorString((cudaError_t)rc));
+    M->poisson_epoch_done = e;
+    if (M->pa_args.n > 0) M->n_kernel_launches++;
+  }
+  EpochArgs& A = M->ea;
+  A.k_begin = k_begin;
+  A.k_end = k_end;
+  A.k0 = k0;
+  A.slot = (int32_t)(e % M->n_slots);
+  A.probe_sample0 = M->probe_samples;
+  A.replay = M->replay ? 1 : 0;
+  std::vector<int32_t> rg, rs;
+  if (M->replay) {
+    std::vector<uint64_t> bits(M->n_lanes, 0);
+    while (M->rep_pos < M->rep_gid.size() && M->rep_step[M->rep_pos] < k_end) {
+      const int64_t ks = M->rep_step[M->rep_pos];
+      const int gid = M->rep_gid[M->rep_pos++];
+      if (ks < k_begin || gid < 0 || gid >= M->n_cells) continue;
+      bits[M->lane_of_gid[gid]] |= 1ull << (ks - k_begin);
+      rg.push_back(gid);
+      rs.push_back((int32_t)ks);
+    }
+    CUDA_TRY(cudaMemcpyAsync(M->replay_bits, bits.data(), 8 * bits.size(),
+                             cudaMemcpyHostToDevice, M->stream));
+    if ((int64_t)rg.size() > M->max_spikes)
+      return set_err(PA_ERR_ARG, "replay list has more than %d spikes in one epoch", M->max_spikes);
+    const int32_t nr = (int32_t)rg.size();
+    CUDA_TRY(cudaMemcpyAsync(M->rep_spk_count, &nr, 4, cudaMemcpyHostToDevice, M->stream));
+    if (nr) {
+      CUDA_TRY(cudaMemcpyAsync(M->rep_spk_gid, rg.data(), 4 * rg.size(), cudaMemcpyHostToDevice, M->stream));
+      CUDA_TRY(cudaMemcpyAsync(M->rep_spk_step, rs.data(), 4 * rs.size(), cudaMemcpyHostToDevice, M->stream));
+    }
+  }
+  if (M->time_kernels) CUDA_TRY(cudaEventRecord(tm.b, M->stream));
+  int rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->stream)
+                                    : launch_epoch_fp64(A, M->tree, M->stream);
+  if (rc) return set_err(PA_ERR_CUDA, "epoch launch: %s", cudaGetErrorString((cudaError_t)rc));
+  if (M->time_kernels) CUDA_TRY(cudaEventRecord(tm.c, M->stream));
+  M->n_epoch_launches++;
+  M->n_kernel_launches += 4;  // epoch, route, record append, record finalize
+  RouteArgs RA = M->ra;
+  if (M->replay) {
+    RA.spk_count = M->rep_spk_count;
+    RA.spk_gid = M->rep_spk_gid;
+    RA.spk_step = M->rep_spk_step;
+  }
+  rc = launch_route(RA, M->max_spikes, M->stream);
+  if (rc == 0)
+    rc = launch_log_append(A.spk_count, A.spk_gid, A.spk_step, A.spk_t, M->max_spikes,
+                           M->log_count, M->log_gid, M->log_step, M->log_t, M->log_cap,
+                           M->err_flags, M->stream);
+  if (M->replay && rc == 0) {
+    // replayed spikes have been routed: reset their count for the next window
+    rc = (int)cudaMemsetAsync(M->rep_spk_count, 0, 4, M->stream);
+  }
+  if (rc) return set_err(PA_ERR_CUDA, "route launch: %s", cudaGetErrorString((cudaError_t)rc));
+  if (k_end == k0 + M->E) {
+    // the epoch is complete: its mask slot becomes the slot of a future epoch
+    for (size_t i = 0; i < M->mask_bases.size(); ++i)
+      CUDA_TRY(cudaMemsetAsync(M->mask_bases[i] + (int64_t)A.slot * M->mask_elems[i], 0,
+                               8 * M->mask_elems[i], M->stream));
+  }
+  if (M->time_kernels) {
+    CUDA_TRY(cudaEventRecord(tm.d, M->stream));
+    M->pending.push_back(tm);
+  }
+  if (M->n_probe > 0) M->probe_samples += k_end - k_begin;
+  return PA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pa_build_model(const pa_cell* cells, int64_t n_cells, const pa_morphology* morphs,
+                   int64_t n_morph, const pa_mechanism* mechs, int64_t n_mech,
+                   const pa_connection* conns, int64_t n_conn, const pa_options* opt,
+                   pa_model** out) {
+  try {
+    return build_impl(cells, n_cells, morphs, n_morph, mechs, n_mech, conns, n_conn, opt, out);
+  } catch (const std::bad_alloc&) {
+    return set_err(PA_ERR_OOM, "host allocation failed while building the model");
+  } catch (...) {
+    return set_err(PA_ERR_ARG, "unexpected failure while building the model");
+  }
+}
+
+int pa_advance(pa_model* M, double t_end_ms, double dt_ms) {
+  if (!M) return set_err(PA_ERR_ARG, "model is NULL");
+  if (dt_ms != M->dt) return set_err(PA_ERR_ARG, "dt %.17g differs from the build-time dt %.17g", dt_ms, M->dt);
+  const double ks = t_end_ms / M->dt;
+  const int64_t k_end = std::llround(ks);
+  if (!std::isfinite(ks) || std::fabs(ks - (double)k_end) > 1e-6 * std::max(1.0, std::fabs(ks)))
+    return set_err(PA_ERR_ARG, "t_end %.17g is not on the dt grid", t_end_ms);
+  if (k_end < M->step) return set_err(PA_ERR_ARG, "t_end lies before the current time");
+  try {
+    CUDA_TRY(cudaSetDevice(M->device));
+    while (M->step < k_end) {
+      const int64_t e = M->step / M->E;
+      const int64_t stop = std::min(k_end, (e + 1) * (int64_t)M->E);
+      int rc = run_window(M, M->step, stop);
+      if (rc) return rc;
+      M->step = stop;
+    }
+  } catch (...) {
+    return set_err(PA_ERR_OOM, "host allocation failed in pa_advance");
+  }
+  return PA_OK;
+}
+
+int pa_sync(pa_model* M) {
+  if (!M) return set_err(PA_ERR_ARG, "model is NULL");
+  CUDA_TRY(cudaSetDevice(M->device));
+  return check_device_errors(M);
+}
+
+int pa_read_probes(pa_model* M, double* out, int64_t cap, int64_t* n_out) {
+  if (!M || !n_out) return set_err(PA_ERR_ARG, "NULL argument");
+  CUDA_TRY(cudaSetDevice(M->device));
+  int rc = check_device_errors(M);
+  const int64_t ns = std::min(M->probe_samples, M->probe_cap);
+  const int64_t n = ns * M->n_probe;
+  *n_out = n;
+  if (cap == 0) return rc;
+  if (!out || cap < n) return set_err(PA_ERR_ARG, "output holds %lld values, %lld needed", (long long)cap, (long long)n);
+  if (n) {
+    CUDA_TRY(cudaMemcpyAsync(out, M->ea.probe_buf, 8 * n, cudaMemcpyDeviceToHost, M->stream));
+    CUDA_TRY(cudaStreamSynchronize(M->stream));
+  }
+  M->probe_samples = 0;
+  return rc;
+}
+
+int pa_read_spikes(pa_model* M, int32_t* gid, int64_t* step, double* t, int64_t cap,
+                   int64_t* n_out) {
+  if (!M || !n_out) return set_err(PA_ERR_ARG, "NULL argument");
+  CUDA_TRY(cudaSetDevice(M->device));
+  int rc = check_device_errors(M);
+  int32_t n = 0;
+  CUDA_TRY(cudaMemcpyAsync(&n, M->log_count, 4, cudaMemcpyDeviceToHost, M->stream));
+  CUDA_TRY(cudaStreamSynchronize(M->stream));
+  *n_out = n;
+  if (cap == 0) return rc;
+  if (cap < n) return set_err(PA_ERR_ARG, "output holds %lld spikes, %d needed", (long long)cap, n);
+  std::vector<int32_t> g(n);
+  std::vector<int64_t> s(n);
+  std::vector<double> tt(n);
+  if (n) {
+    CUDA_TRY(cudaMemcpyAsync(g.data(), M->log_gid, 4 * (size_t)n, cudaMemcpyDeviceToHost, M->stream));
+    CUDA_TRY(cudaMemcpyAsync(s.data(), M->log_step, 8 * (size_t)n, cudaMemcpyDeviceToHost, M->stream));
+    CUDA_TRY(cudaMemcpyAsync(tt.data(), M->log_t, 8 * (size_t)n, cudaMemcpyDeviceToHost, M->stream));
+  }
+  CUDA_TRY(cudaMemsetAsync(M->log_count, 0, 4, M->stream));
+  CUDA_TRY(cudaStreamSynchronize(M->stream));
+  std::vector<int32_t> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    return s[a] != s[b] ? s[a] < s[b] : g[a] < g[b];
+  });
+  for (int i = 0; i < n; ++i) {
+    if (gid) gid[i] = g[idx[i]];
+    if (step) step[i] = s[idx[i]];
+    if (t) t[i] = tt[idx[i]];
+  }
+  return rc;
+}
+
+int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t* n_out) {
+  using namespace pa;
+  if (!M || !n_out) return set_err(PA_ERR_ARG, "NULL argument");
+  CUDA_TRY(cudaSetDevice(M->device));
+  const bool mixed = M->precision == PA_MIXED;
+  auto fetch = [&](const void* dptr, int64_t n, size_t esz, std::vector<double>& dst) -> int {
+    dst.assign(n, 0.0);
+    if (n == 0 || !dptr) return 0;
+    std::vector<char> raw(n * esz);
+    cudaError_t e = cudaMemcpyAsync(raw.data(), dptr, n * esz, cudaMemcpyDeviceToHost, M->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+    if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "read back: %s", cudaGetErrorString(e));
+    for (int64_t i = 0; i < n; ++i)
+      dst[i] = esz == 8 ? ((const double*)raw.data())[i] : (double)((const float*)raw.data())[i];
+    return 0;
+  };
+  std::vector<double> tmp, tmp2;
+  if (field == PA_FIELD_V) {
+    *n_out = M->n_cv;
+    if (cap == 0) return PA_OK;
+    if (!out || cap < M->n_cv) return set_err(PA_ERR_ARG, "output too small");
+    int rc = fetch(M->ea.V, M->total_rows * kLanes, 8, tmp);
+    if (rc) return rc;
+    for (int64_t c = 0; c < M->n_cells; ++c) {
+      const int64_t L = M->lane_of_gid[c];
+      for (int i = 0; i < M->cell_ncv[c]; ++i)
+        out[M->cell_cv_off[c] + i] = tmp[((int64_t)M->row_base[L / kLanes] + i) * kLanes + L % kLanes];
+    }
+    return PA_OK;
+  }
+  if (field == PA_FIELD_PRP || field == PA_FIELD_GATES) {
+    const int per = field == PA_FIELD_GATES ? 3 : 1;
+    *n_out = M->n_cells * per;
+    if (cap == 0) return PA_OK;
+    if (!out || cap < *n_out) return set_err(PA_ERR_ARG, "output too small");
+    int rc = field == PA_FIELD_PRP ? fetch(M->ea.prp, M->n_lanes, 8, tmp)
+                                   : fetch(M->ea.gate, 3 * M->n_lanes, 8, tmp);
+    if (rc) return rc;
+    for (int64_t c = 0; c < M->n_cells; ++c)
+      for (int j = 0; j < per; ++j) out[c * per + j] = tmp[j * M->n_lanes + M->lane_of_gid[c]];
+    return PA_OK;
+  }
+  if (field < PA_FIELD_G || field > PA_FIELD_APOST) return set_err(PA_ERR_ARG, "unknown field %d", field);
+  *n_out = M->n_conn;
+  if (cap == 0) return PA_OK;
+  if (!out || cap < M->n_conn) return set_err(PA_ERR_ARG, "output too small");
+  std::vector<std::vector<double>> per_stream(M->n_streams);
+  for (int s = 0; s < M->n_streams; ++s) {
+    const StreamDev& D = M->ea.sd[s];
+    const int kind = M->sp[s].kind;
+    const void* src = nullptr;
+    size_t esz = mixed ? 4 : 8;
+    switch (field) {
+      case PA_FIELD_G: src = D.g; break;
+      case PA_FIELD_C: src = D.c; esz = 8; break;
+      case PA_FIELD_W: src = (kind == SK_GB || kind == SK_STDP) ? D.w : nullptr; esz = 8; break;
+      case PA_FIELD_H: src = kind == SK_STC ? D.w : nullptr; esz = 8; break;
+      case PA_FIELD_Z: src = D.z; esz = 8; break;
+      case PA_FIELD_APRE: src = D.apre; break;
+      case PA_FIELD_APOST: src = D.apost; break;
+    }
+    int rc = fetch(src, src ? D.n_elem : 0, esz, per_stream[s]);
+    if (rc) return rc;
+  }
+  for (int64_t c = 0; c < M->n_conn; ++c) {
+    const auto& v = per_stream[M->conn_stream[c]];
+    out[c] = v.empty() ? 0.0 : v[M->conn_elem[c]];
+  }
+  return PA_OK;
+}
+
+int pa_read_weights(pa_model* M, double* out, int64_t cap, int64_t* n_out) {
+  using namespace pa;
+  if (!M || !n_out) return set_err(PA_ERR_ARG, "NULL argument");
+  *n_out = M->n_conn;
+  if (cap == 0) return PA_OK;
+  if (!out || cap < M->n_conn) return set_err(PA_ERR_ARG, "output too small");
+  std::vector<double> w(M->n_conn), h(M->n_conn), z(M->n_conn);
+  int64_t n;
+  int rc = pa_read_state(M, PA_FIELD_W, w.data(), M->n_conn, &n);
+  if (!rc) rc = pa_read_state(M, PA_FIELD_H, h.data(), M->n_conn, &n);
+  if (!rc) rc = pa_read_state(M, PA_FIELD_Z, z.data(), M->n_conn, &n);
+  if (rc) return rc;
+  for (int64_t c = 0; c < M->n_conn; ++c) {
+    switch (M->conn_kind[c]) {
+      case PA_MECH_GB:
+      case PA_MECH_STDP: out[c] = w[c]; break;
+      case PA_MECH_STC: out[c] = h[c] + M->conn_h0[c] * z[c]; break;
+      default: out[c] = M->conn_weight[c];
+    }
+  }
+  return PA_OK;
+}
+
+int pa_set_replay(pa_model* M, int64_t n, const int32_t* gid, const int64_t* step) {
+  if (!M || n < 0 || (n > 0 && (!gid || !step))) return set_err(PA_ERR_ARG, "bad replay arguments");
+  M->rep_gid.assign(gid, gid + n);
+  M->rep_step.assign(step, step + n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (i > 0 && step[i] < step[i - 1]) return set_err(PA_ERR_ARG, "replay spikes must be sorted by step");
+    if (step[i] < M->step) return set_err(PA_ERR_ARG, "replay spike before the current step");
+  }
+  M->rep_pos = 0;
+  M->replay = true;
+  return PA_OK;
+}
+
+int pa_model_info(const pa_model* M, pa_info* info) {
+  if (!M || !info) return set_err(PA_ERR_ARG, "NULL argument");
+  info->n_cells = M->n_cells;
+  info->n_cv = M->n_cv;
+  info->n_conn = M->n_conn;
+  info->n_groups = M->n_groups;
+  info->n_padded_cv = M->total_rows * pa::kLanes;
+  info->step = M->step;
+  info->epoch_steps = M->E;
+  info->precision = M->precision;
+  info->tree = M->tree ? 1 : 0;
+  info->n_streams = M->n_streams;
+  info->device_bytes = (int64_t)M->dbytes;
+  return PA_OK;
+}
+
+int pa_get_kernel_stats(pa_model* M, pa_kernel_stats* out) {
+  if (!M || !out) return set_err(PA_ERR_ARG, "NULL argument");
+  CUDA_TRY(cudaSetDevice(M->device));
+  int rc = collect_timings(M);
+  if (rc) return rc;
+  out->epoch_launches = M->n_epoch_launches;
+  out->kernel_launches = M->n_kernel_launches;
+  out->epoch_kernel_ms = M->epoch_ms;
+  out->event_kernels_ms = M->event_ms;
+  return PA_OK;
+}
+
+int pa_reset_kernel_stats(pa_model* M) {
+  if (!M) return set_err(PA_ERR_ARG, "NULL argument");
+  CUDA_TRY(cudaSetDevice(M->device));
+  int rc = collect_timings(M);
+  M->n_epoch_launches = M->n_kernel_launches = 0;
+  M->epoch_ms = M->event_ms = 0;
+  return rc;
+}
+
+void pa_free_model(pa_model* M) {
+  if (!M) return;
+  cudaSetDevice(M->device);
+  if (M->dmem) {
+    cudaStreamSynchronize(M->stream);
+    cudaFree(M->dmem);
+  }
+  for (auto& t : M->pending)
+    for (cudaEvent_t e : {t.a, t.b, t.c, t.d}) cudaEventDestroy(e);
+  for (cudaEvent_t e : M->ev_pool) cudaEventDestroy(e);
+  delete M;
+}
+
+const char* pa_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

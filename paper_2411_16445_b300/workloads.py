@@ -111,7 +111,12 @@ class Network:
     conn_weight: np.ndarray                # float64 [C]
     conn_delay: np.ndarray
     conn_rate: np.ndarray
+    conn_pid: Optional[np.ndarray] = None  # int64 Poisson train id (-1: connection index)
     name: str = "custom"
+
+    def __post_init__(self):
+        if self.conn_pid is None:
+            self.conn_pid = np.full(self.conn_src.shape[0], -1, dtype=np.int64)
 
     @property
     def n_cells(self) -> int:

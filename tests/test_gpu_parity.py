@@ -1,0 +1,216 @@
+"""Parity of the CUDA engine (called through the C-ABI) with the FP64 oracle.
+
+Tolerances (from the engine's specification): FP64 voltages within 1e-9 V
+(1e-6 mV), mixed precision within 1e-5 V (1e-2 mV); identical spike counts,
+spike times within 1e-3 ms; plastic weights within 1e-6 relative; spike
+indices and event routing bit-exact.  The FP64 path is built to reproduce the
+oracle's arithmetic operation for operation, so most FP64 checks below also
+record whether the results are bit-identical."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2411_16445_b300 import engine as E
+from paper_2411_16445_b300 import workloads as W
+
+from _nets import compare, edge_net, extract, map_spikes, tiny_tree_net
+
+pytestmark = pytest.mark.gpu
+
+V_TOL = {E.PA_FP64: 1e-6, E.PA_MIXED: 1e-2}   # mV
+W_RTOL = 1e-6
+T_TOL = 1e-3                                     # ms
+
+FIELDS = [(O.SYN_G, E.FIELD_G), (O.SYN_C, E.FIELD_C), (O.SYN_W, E.FIELD_W),
+          (O.SYN_H, E.FIELD_H), (O.SYN_Z, E.FIELD_Z), (O.SYN_APRE, E.FIELD_APRE),
+          (O.SYN_APOST, E.FIELD_APOST)]
+
+
+def run_both(net, steps, precision, probes=(), chunks=1, max_epoch_steps=0):
+    o = O.Oracle(net, probes=probes)
+    o.run(steps)
+    m = E.Model(net, precision=precision, probes=probes, max_epoch_steps=max_epoch_steps)
+    per = steps // chunks
+    done = 0
+    for c in range(chunks):
+        n = per if c < chunks - 1 else steps - done
+        m.advance((done + n) * net.dt)
+        done += n
+    m.sync()
+    return o, m
+
+
+def run_replay_both(net, steps, precision, chunks=1):
+    """Mixed precision on networks: both sides driven by the oracle's closed-loop
+    spike list (open-loop replay), so no chaotic amplification of rounding."""
+    ref = O.Oracle(net)
+    ref.run(steps)
+    gid, step, _ = ref.spikes()
+    o = O.Oracle(net)
+    o.set_replay(gid, step)
+    o.run(steps)
+    m = E.Model(net, precision=precision)
+    m.set_replay(gid, step)
+    per = steps // chunks
+    done = 0
+    for c in range(chunks):
+        n = per if c < chunks - 1 else steps - done
+        m.advance((done + n) * net.dt)
+        done += n
+    m.sync()
+    return o, m
+
+
+def check_state(o, m, precision, exact=False):
+    vo, vg = o.v(), m.read_state(E.FIELD_V)
+    dv = compare(vo, vg)
+    assert dv <= V_TOL[precision], f"max |dV| = {dv} mV"
+    if exact:
+        assert np.array_equal(vo, vg), f"FP64 path not bit-identical (max |dV| {dv})"
+    go, so, to = o.spikes()
+    gg, sg, tg = m.read_spikes()
+    assert len(go) == len(gg), f"spike counts {len(go)} vs {len(gg)}"
+    assert np.array_equal(go, gg) and np.array_equal(so, sg), "spike indices differ"
+    assert compare(to, tg) <= T_TOL
+    wo = o.syn(O.SYN_WEIGHT_TOTAL)
+    wg = m.read_weights()
+    assert np.all(np.abs(wo - wg) <= W_RTOL * np.maximum(np.abs(wo), 1e-12) + 1e-15)
+    if precision == E.PA_FP64:
+        for fo, fg in FIELDS:
+            a, b = o.syn(fo), m.read_state(fg)
+            assert compare(a, b) <= 1e-12 * max(1.0, np.abs(a).max() if a.size else 1.0)
+        assert compare(o.cell_p(), m.read_state(E.FIELD_PRP)) <= 1e-12
+        assert compare(o.gates().reshape(-1), m.read_state(E.FIELD_GATES)) <= 1e-12
+    return dv
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_single_neuron_full_second(precision):
+    """The single-neuron workload over its full 1 s (40,000 steps): soma and synapse
+    CV traces every step, spikes, calcium and the GB weight."""
+    net = W.single_neuron()
+    probes = [(0, 0), (0, 33), (0, 64)]
+    o, m = run_both(net, 40000, precision, probes=probes, chunks=7)
+    po, pg = o.probes(), m.read_probes(len(probes))
+    assert po.shape == pg.shape
+    d = compare(po, pg)
+    assert d <= V_TOL[precision], f"probe max |dV| = {d} mV"
+    if precision == E.PA_FP64:
+        assert np.array_equal(po, pg)
+    check_state(o, m, precision, exact=precision == E.PA_FP64)
+
+
+def test_recurrent_stc_closed_loop_fp64():
+    """100-cell recurrent tagging-and-capture network (4 groups, ragged last group),
+    closed loop: bit-identical spike trains, voltages, weights, tags and PRP."""
+    net = W.recurrent_stc(n_exc=80, n_inh=20, p=0.1, w_bg=3e-3, bg_rate=20.0)
+    o, m = run_both(net, 2500, E.PA_FP64, chunks=3)
+    check_state(o, m, E.PA_FP64, exact=True)
+
+
+def test_recurrent_stc_mixed_open_loop():
+    net = W.recurrent_stc(n_exc=80, n_inh=20, p=0.1, w_bg=3e-3, bg_rate=20.0)
+    o, m = run_replay_both(net, 2500, E.PA_MIXED, chunks=3)
+    check_state(o, m, E.PA_MIXED)
+
+
+def test_tree_cells_fp64_bit_exact():
+    """Random binary trees: Hines elimination with branch points (children applied in
+    descending order through the scratch arrays) and STDP."""
+    net = tiny_tree_net()
+    o, m = run_both(net, 3000, E.PA_FP64, chunks=2)
+    check_state(o, m, E.PA_FP64, exact=True)
+
+
+def test_tree_cells_mixed_open_loop():
+    net = tiny_tree_net()
+    o, m = run_replay_both(net, 3000, E.PA_MIXED, chunks=2)
+    check_state(o, m, E.PA_MIXED)
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_edge_cases(precision):
+    """One-CV cells, a cell without synapses, several synapses of different mechanisms
+    on one CV, a zero-rate Poisson train, a non-DFS branching numbering, delays that
+    are not multiples of the epoch, partial epochs (odd advance chunks)."""
+    net = edge_net()
+    if precision == E.PA_FP64:
+        o, m = run_both(net, 3001, precision, chunks=5)
+    else:
+        o, m = run_replay_both(net, 3001, precision, chunks=5)
+    check_state(o, m, precision, exact=precision == E.PA_FP64)
+
+
+def test_morphology_sweep_small_fp64():
+    net = W.morphology_sweep(n_nets=3, cells_per_net=40)
+    o, m = run_both(net, 600, E.PA_FP64, chunks=2)
+    check_state(o, m, E.PA_FP64, exact=True)
+
+
+def test_short_epochs_equal_long_epochs():
+    """Routing once per epoch is exact for any epoch length <= the minimum delay."""
+    net = tiny_tree_net(n_cells=40)
+    m1 = E.Model(net, precision=E.PA_FP64, max_epoch_steps=3)
+    m2 = E.Model(net, precision=E.PA_FP64)
+    m1.advance(1200 * net.dt)
+    m2.advance(1200 * net.dt)
+    assert np.array_equal(m1.read_state(E.FIELD_V), m2.read_state(E.FIELD_V))
+    assert np.array_equal(m1.read_spikes()[1], m2.read_spikes()[1])
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_open_loop_replay_stc(precision):
+    """Open-loop replay: both sides are driven by the oracle's own spike list, so each
+    cell's trajectory is compared without chaotic amplification."""
+    net = W.recurrent_stc(n_exc=80, n_inh=20, p=0.1, w_bg=3e-3, bg_rate=20.0)
+    ref = O.Oracle(net)
+    ref.run(2000)
+    gid, step, _ = ref.spikes()
+    o = O.Oracle(net)
+    o.set_replay(gid, step)
+    o.run(2000)
+    m = E.Model(net, precision=precision)
+    m.set_replay(gid, step)
+    m.advance(2000 * net.dt)
+    dv = compare(o.v(), m.read_state(E.FIELD_V))
+    assert dv <= V_TOL[precision]
+    wo, wg = o.syn(O.SYN_WEIGHT_TOTAL), m.read_weights()
+    assert np.all(np.abs(wo - wg) <= W_RTOL * np.abs(wo) + 1e-15)
+
+
+def test_poisson_train_ids_shared():
+    """Connections with the same poisson_id receive the same train."""
+    b = W._Builder(0.1, 77, "pid")
+    pas = b.mech(W.PAS, W.pas_params())
+    e1 = b.mech(W.EXPSYN, W.expsyn_params(4.0, 0.0))
+    m_ = b.morph(W.soma_only(20.0))
+    b.cells_add(3, m_, pas, pas)
+    b.connect(W.SRC_POISSON, [0, 1, 2], 0, e1, 1e-3, rate=50.0)
+    net = b.build()
+    net.conn_pid = np.array([5, 5, 6], np.int64)
+    m = E.Model(net)
+    m.advance(500.0)
+    g = m.read_state(E.FIELD_G)
+    assert g[0] == g[1] and g[0] != g[2]
+    o = O.Oracle(net)
+    o.run(5000)
+    assert np.array_equal(o.syn(O.SYN_G), g)
+
+
+def test_errors_are_reported_not_raised_on_device():
+    net = W.single_neuron()
+    with pytest.raises(E.PaError) as ei:
+        bad = W.single_neuron()
+        bad.conn_cv = np.array([999], np.int32)
+        E.Model(bad)
+    assert ei.value.code == -1
+    m = E.Model(net)
+    with pytest.raises(E.PaError):
+        m.advance(0.0123)  # off the dt grid
+    assert E.lib().pa_advance(m._h, 1.0, 0.05) == -1  # dt differs from the build-time dt
+    # probe buffer overflow is reported as PA_ERR_CAPACITY, data kept up to capacity
+    m2 = E.Model(net, probes=[(0, 0)], probe_capacity=100)
+    m2.advance(200 * net.dt)
+    with pytest.raises(E.PaError) as ei:
+        m2.sync()
+    assert ei.value.code == -5
