@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark of the plastic multi-compartment time-step loop on B300.
+
+Workload: the large mixed-precision network -- 100,000 HH-soma cells on random
+binary dendritic trees of 51-501 CVs (each cell's tree drawn from a seeded pool
+of 4,096 random trees), 10^7 pair-STDP synapses (fan-in 100, delays 1-5 ms),
+2 Hz Poisson drive, dt = 0.025 ms.  One benchmark step is one min-delay epoch
+(40 time steps = 1 ms) of the whole loop: Poisson drive, synaptic and
+mechanism updates, cable assembly + Hines solve, detection, CSR routing.
+
+value = compartment-updates/s (CU/s = CVs x time steps / device time) of the
+mixed-precision path; the FP64 path is timed on the same GPU and reported
+beside it.  All inputs are synthetic and resident in HBM before timing; the
+working set (several GB) is far larger than the 126 MB L2, so no L2 flush is
+needed between steps.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compartment-updates/s, mixed vs FP64 plain, same GPU; serving p50/p99 latency"
+UNIT = "CU/s"
+HBM_PEAK_GBS = 6470.8          # measured copy bandwidth of this machine's B300 (STREAM-style)
+N_SM = 148
+DFMA_PER_SM_CLK = 2            # FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal @ 2.03 GHz)
+RCP64_DFMA_EQ = 465.0 / 71.0   # measured: FP64 FMA 465 G/s vs FP64 reciprocal 71 G/s on B300
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--cells", type=int, default=100_000)
+    p.add_argument("--shapes", type=int, default=4096)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    return p.parse_args()
+
+
+def workload(n_cells, n_shapes, seed_offset=0):
+    from paper_2411_16445_b300 import workloads as W
+    net = W.large_stdp(n_cells=n_cells, n_shapes=n_shapes)
+    if seed_offset:
+        net.seed = (net.seed + 0x9E3779B97F4A7C15 * seed_offset) & (2**64 - 1)
+    return net
+
+
+def net_stats(net):
+    ncv = net.cell_ncv()
+    kinds = net.mech_kind[net.conn_mech]
+    return {
+        "n_cells": int(net.n_cells),
+        "n_cv": int(ncv.sum()),
+        "n_syn": int(net.n_conn),
+        "n_stdp": int(np.sum(kinds == 13)),
+        "n_expsyn": int(np.sum(kinds == 10)),
+        "tree": any(not m.is_chain() for m in net.morphs),
+    }
+
+
+def per_cu_model(st, mixed):
+    """Algorithmic work of one compartment-update, amortising soma and synapse work.
+    Bytes: state that must stream every step (V read+write, four FP64 cable
+    coefficients C/dt, diagonal, leak E term, axial coupling; 2-byte parent index
+    on trees) plus per-synapse state read+write, CV index and event word.
+    FP64 ops in FMA-equivalents: the Hines row (b assembly, two synaptic sums,
+    two child-contribution FMAs, f and x' products, back-substitution FMA, one
+    reciprocal costed at its measured issue cost), HH per soma, FP64 synapse ops."""
+    ts = 4 if mixed else 8
+    cv_bytes = 16 + 32 + (2 if st["tree"] else 0)
+    stdp_bytes = 2 * ts * 3 + 8 + 4 + 8          # g, apre, apost r/w; w touched on events only
+    exp_bytes = 2 * ts + 4 + 8
+    syn_bytes = st["n_stdp"] * stdp_bytes + st["n_expsyn"] * exp_bytes
+    bytes_per_cu = cv_bytes + syn_bytes / st["n_cv"]
+    solve = 8 + RCP64_DFMA_EQ + (2 if mixed else 0)   # mixed: two FP32->FP64 sum conversions
+    hh = 153 + 6 * RCP64_DFMA_EQ + 20                  # 9 model exps, 6 divisions, currents
+    syn = 0 if mixed else (st["n_stdp"] * 6 + st["n_expsyn"] * 4)
+    fp64_per_cu = solve + (hh * st["n_cells"] + syn) / st["n_cv"]
+    return bytes_per_cu, fp64_per_cu
+
+
+class ClockSampler:
+    def __init__(self, device):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device)],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def time_gpu(net, precision, steps, warmup, device, stream_barrier):
+    import torch
+    from paper_2411_16445_b300 import engine as E
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream(device)
+    t0 = time.perf_counter()
+    m = E.Model(net, precision=precision, device=device, stream=E.C.c_void_p(stream.cuda_stream),
+                flags=E.FLAG_TIME_KERNELS)
+    setup_s = time.perf_counter() - t0
+    info = m.info()
+    E_steps = info.epoch_steps
+    m.advance(warmup * E_steps * net.dt)
+    m.sync()
+    m.read_spikes()
+    m.reset_kernel_stats()
+    stream_barrier()
+    torch.cuda.synchronize(device)
+    sampler = ClockSampler(device)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    m.advance((warmup + steps) * E_steps * net.dt)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize(device)
+    clocks = sampler.stop()
+    stream_barrier()
+    ms = ev0.elapsed_time(ev1)
+    m.sync()
+    ks = m.kernel_stats()
+    gid, _, _ = m.read_spikes()
+    res = {"ms": ms, "epoch_steps": E_steps, "n_cv": info.n_cv, "setup_s": setup_s,
+           "epoch_kernel_ms": ks.epoch_kernel_ms, "event_kernels_ms": ks.event_kernels_ms,
+           "epoch_launches": ks.epoch_launches, "kernel_launches": ks.kernel_launches,
+           "spikes": int(len(gid)), "device_bytes": info.device_bytes, "clocks": clocks}
+    m.close()
+    return res
+
+
+def time_e2e(net, precision, steps, device):
+    """The user's end-to-end path through the C-ABI: descriptors from host memory
+    uploaded by pa_build_model, pa_advance one epoch at a time with the epoch's
+    spikes read back to the host each time, final weights read back."""
+    import torch
+    from paper_2411_16445_b300 import engine as E
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    m = E.Model(net, precision=precision, device=device)
+    info = m.info()
+    h2d = info.device_bytes
+    spikes = 0
+    for s in range(steps):
+        m.advance((s + 1) * info.epoch_steps * net.dt)
+        g, _, _ = m.read_spikes()
+        spikes += len(g)
+    w = m.read_weights()
+    torch.cuda.synchronize(device)
+    t = time.perf_counter() - t0
+    m.close()
+    cu = info.n_cv * info.epoch_steps * steps
+    d2h = spikes * (4 + 8 + 8) + w.nbytes
+    return {"value": cu / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d / steps),
+            "d2h_bytes_per_step": int(d2h / steps), "wall_s": t,
+            "note": "includes pa_build_model (host descriptors -> HBM) and per-epoch spike read-back"}
+
+
+def oracle_sample(n_cells, n_shapes, budget_s=15.0, max_steps=4000, warm=2):
+    """The FP64 CPU oracle on a bounded sample of the workload: the same generator
+    at n_cells cells, timed over whole steps until the CPU budget is spent."""
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle as O
+    net = workload(n_cells, n_shapes)
+    o = O.Oracle(net)
+    o.run(warm)
+    n_cv = net.n_cv
+    done, t = 0, 0.0
+    chunk = 5
+    while t < budget_s and done < max_steps:
+        t0 = time.perf_counter()
+        o.run(chunk)
+        t += time.perf_counter() - t0
+        done += chunk
+    return {"value": n_cv * done / t, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle", "sample": f"{n_cells} cells ({n_cv} CVs, {net.n_conn} synapses) of "
+            f"the same generator, {done} time steps, FP64, OpenMP over cells", "seconds": t}
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle as O
+    n_cells = min(args.cells, 4096)
+    net = workload(n_cells, min(args.shapes, n_cells))
+    o = O.Oracle(net)
+    steps_per_sample = 4
+    o.run(args.warmup * steps_per_sample)
+    t0 = time.perf_counter()
+    o.run(args.steps * steps_per_sample)
+    t = time.perf_counter() - t0
+    val = net.n_cv * steps_per_sample * args.steps / t
+    sample = (f"each step: {steps_per_sample} time steps of {n_cells} cells ({net.n_cv} CVs) "
+              f"of the large STDP network generator, FP64 oracle, OpenMP over cells")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "large_stdp", "n_cells": n_cells, "dt_ms": net.dt,
+                       "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+        def barrier():
+            dist.barrier()
+    else:
+        def barrier():
+            pass
+    device = local
+    net = workload(args.cells, args.shapes, seed_offset=rank)
+    st = net_stats(net)
+    runs = {}
+    precs = {"mixed": 1, "fp64": 0}
+    order = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    for name in order:
+        runs[name] = time_gpu(net, precs[name], args.steps, args.warmup, device, barrier)
+    head = order[0]
+    r = runs[head]
+    ms = r["ms"]
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=f"cuda:{device}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cu_per_rank = r["n_cv"] * r["epoch_steps"] * args.steps
+    value = cu_per_rank * ws / (ms * 1e-3)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    def roofline(run, mixed):
+        bpc, fpc = per_cu_model(st, mixed)
+        cu_launch = run["n_cv"] * run["epoch_steps"]
+        t_launch = run["epoch_kernel_ms"] / max(run["epoch_launches"], 1) * 1e-3
+        clk = (run["clocks"] or {}).get("sm_mhz") or 2032.0
+        peak_tflops = N_SM * DFMA_PER_SM_CLK * 2 * clk * 1e6 / 1e12
+        ach_tflops = 2 * fpc * cu_launch / t_launch / 1e12
+        ach_gbs = bpc * cu_launch / t_launch / 1e9
+        return {"bound": "alu", "achieved": ach_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": ach_tflops / peak_tflops, "traffic": None,
+                "kernel": "epoch_kernel", "fp64_fma_eq_per_cu": fpc,
+                "peak_note": f"FP64: {N_SM} SMs x {DFMA_PER_SM_CLK} FMA/clk x 2 flop at the median "
+                             f"SM clock under load ({clk:.0f} MHz); a reciprocal costs "
+                             f"{RCP64_DFMA_EQ:.2f} FMA-equivalents (measured)",
+                "hbm": {"achieved": ach_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                        "frac": ach_gbs / HBM_PEAK_GBS, "algorithmic_bytes_per_cu": bpc,
+                        "peak_note": "measured copy bandwidth"}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 solve + f32 synapses" if head == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "large_stdp", "n_cells": st["n_cells"], "n_cv": st["n_cv"],
+                   "n_synapses": st["n_syn"], "dt_ms": net.dt,
+                   "epoch_steps": r["epoch_steps"], "step": "one min-delay epoch",
+                   "precision": head, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (working set "
+                         f"{r['device_bytes'] / 1e9:.1f} GB vs 126 MB L2)"},
+        "roofline": roofline(r, head == "mixed"),
+        "gpu_launches": r["kernel_launches"],
+        "clocks": r["clocks"],
+        "setup_s": r["setup_s"],
+    }
+    for name, run in runs.items():
+        line[name] = {"value": run["n_cv"] * run["epoch_steps"] * args.steps / (run["ms"] * 1e-3),
+                      "ms_per_step": run["ms"] / args.steps,
+                      "epoch_kernel_ms_per_step": run["epoch_kernel_ms"] / max(run["epoch_launches"], 1),
+                      "event_kernels_ms_per_step": run["event_kernels_ms"] / max(run["epoch_launches"], 1),
+                      "spikes": run["spikes"], "roofline": roofline(run, name == "mixed")}
+    if "mixed" in runs and "fp64" in runs:
+        line["mixed_over_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
+    if not args.no_e2e:
+        line["e2e"] = time_e2e(net, precs[head], args.steps, device)
+    if not args.no_cpu and ws == 1:
+        line["cpu_baseline"] = oracle_sample(min(args.cells, 2048), min(args.shapes, 2048))
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -159,14 +159,20 @@ class Network:
 
 
 class _Builder:
-    """Accumulates mechanisms, morphologies, cells and connections."""
+    """Accumulates mechanisms, morphologies, cells and connections (numpy chunks)."""
+
+    _CELL = (("morph", np.int32), ("soma", np.int32), ("dend", np.int32), ("cm", np.float64),
+             ("ra", np.float64), ("istep", np.float64), ("ton", np.float64),
+             ("toff", np.float64), ("vinit", np.float64), ("thresh", np.float64))
+    _CONN = (("src", np.int32), ("dst", np.int32), ("cv", np.int32), ("mech", np.int32),
+             ("w", np.float64), ("delay", np.float64), ("rate", np.float64))
 
     def __init__(self, dt: float, seed: int, name: str):
         self.dt, self.seed, self.name = dt, seed, name
         self.mk, self.mp, self.morphs = [], [], []
-        self.cells = {k: [] for k in ("morph", "soma", "dend", "cm", "ra", "istep", "ton", "toff",
-                                      "vinit", "thresh")}
-        self.conn = {k: [] for k in ("src", "dst", "cv", "mech", "w", "delay", "rate")}
+        self.cells = {k: [] for k, _ in self._CELL}
+        self.conn = {k: [] for k, _ in self._CONN}
+        self.n_cells = 0
 
     def mech(self, kind: int, params) -> int:
         self.mk.append(kind)
@@ -179,32 +185,34 @@ class _Builder:
 
     def cells_add(self, n, morph, soma, dend, cm=1.0, ra=100.0, istep=0.0, ton=0.0, toff=NEVER,
                   vinit=-65.0, thresh=-10.0) -> np.ndarray:
-        start = len(self.cells["morph"])
-        for k, v in (("morph", morph), ("soma", soma), ("dend", dend), ("cm", cm), ("ra", ra),
-                     ("istep", istep), ("ton", ton), ("toff", toff), ("vinit", vinit),
-                     ("thresh", thresh)):
-            self.cells[k].extend(np.broadcast_to(np.asarray(v), (n,)).tolist())
+        start = self.n_cells
+        vals = dict(morph=morph, soma=soma, dend=dend, cm=cm, ra=ra, istep=istep, ton=ton,
+                    toff=toff, vinit=vinit, thresh=thresh)
+        for k, dt_ in self._CELL:
+            self.cells[k].append(np.broadcast_to(np.asarray(vals[k], dtype=dt_), (n,)).copy())
+        self.n_cells += n
         return np.arange(start, start + n)
 
     def connect(self, src, dst, cv, mech, w, delay=0.0, rate=0.0) -> None:
         n = len(np.atleast_1d(dst))
-        for k, v in (("src", src), ("dst", dst), ("cv", cv), ("mech", mech), ("w", w),
-                     ("delay", delay), ("rate", rate)):
-            self.conn[k].extend(np.broadcast_to(np.asarray(v), (n,)).tolist())
+        vals = dict(src=src, dst=dst, cv=cv, mech=mech, w=w, delay=delay, rate=rate)
+        for k, dt_ in self._CONN:
+            self.conn[k].append(np.broadcast_to(np.asarray(vals[k], dtype=dt_), (n,)).copy())
 
     def build(self) -> Network:
-        c, k = self.cells, self.conn
-        i32 = lambda x: np.asarray(x, dtype=np.int32)
-        f64 = lambda x: np.asarray(x, dtype=np.float64)
+        def cat(d, k, dt_):
+            return np.concatenate(d[k]).astype(dt_) if d[k] else np.zeros(0, dt_)
+
+        c = {k: cat(self.cells, k, t) for k, t in self._CELL}
+        k = {kk: cat(self.conn, kk, t) for kk, t in self._CONN}
         return Network(
-            dt=self.dt, seed=self.seed, mech_kind=i32(self.mk), mech_params=self.mp,
-            morphs=self.morphs, cell_morph=i32(c["morph"]), cell_soma_mech=i32(c["soma"]),
-            cell_dend_mech=i32(c["dend"]), cell_cm=f64(c["cm"]), cell_ra=f64(c["ra"]),
-            cell_istep=f64(c["istep"]), cell_ton=f64(c["ton"]), cell_toff=f64(c["toff"]),
-            cell_vinit=f64(c["vinit"]), cell_thresh=f64(c["thresh"]), conn_src=i32(k["src"]),
-            conn_dst=i32(k["dst"]), conn_cv=i32(k["cv"]), conn_mech=i32(k["mech"]),
-            conn_weight=f64(k["w"]), conn_delay=f64(k["delay"]), conn_rate=f64(k["rate"]),
-            name=self.name)
+            dt=self.dt, seed=self.seed, mech_kind=np.asarray(self.mk, np.int32),
+            mech_params=self.mp, morphs=self.morphs, cell_morph=c["morph"],
+            cell_soma_mech=c["soma"], cell_dend_mech=c["dend"], cell_cm=c["cm"],
+            cell_ra=c["ra"], cell_istep=c["istep"], cell_ton=c["ton"], cell_toff=c["toff"],
+            cell_vinit=c["vinit"], cell_thresh=c["thresh"], conn_src=k["src"],
+            conn_dst=k["dst"], conn_cv=k["cv"], conn_mech=k["mech"], conn_weight=k["w"],
+            conn_delay=k["delay"], conn_rate=k["rate"], name=self.name)
 
 
 # --------------------------------------------------------------------------
@@ -373,11 +381,7 @@ def large_stdp(n_cells=100_000, fan_in=100, dt=0.025, seed=None, n_dend=(50, 500
         b.morph(random_binary_tree(rng, int(tree_sizes[t])))
     morph_ids = np.arange(n_cells) if n_shapes is None else rng.integers(0, n_trees, n_cells)
     sizes = tree_sizes[morph_ids]
-    cells = np.arange(n_cells)
-    b.cells["morph"].extend(morph_ids.tolist())
-    for k, v in (("soma", hh), ("dend", pas), ("cm", 1.0), ("ra", 100.0), ("istep", 0.0),
-                 ("ton", 0.0), ("toff", NEVER), ("vinit", -65.0), ("thresh", -10.0)):
-        b.cells[k].extend([v] * n_cells)
+    cells = b.cells_add(n_cells, morph_ids, hh, pas)
     src = rng.integers(0, n_cells - 1, size=(n_cells, fan_in))
     src = (src + (src >= cells[:, None])).reshape(-1)   # no self-connections
     dst = np.repeat(cells, fan_in)
