@@ -196,6 +196,29 @@ int pa_build_model(const pa_cell* cells, int64_t n_cells, const pa_morphology* m
  * pa_read_* / pa_sync call. */
 int pa_advance(pa_model* m, double t_end_ms, double dt_ms);
 
+/* pa_advance for callers that must not allocate GPU memory while they run --
+ * for example code inside a region whose allocations are owned by another
+ * memory manager, or a host thread on a real-time path where a device
+ * allocation could stall or fail.  The paper has no counterpart; this is an
+ * interface convenience.
+ *
+ * It advances the model exactly like pa_advance (same kernels, same results;
+ * the FP64 path is bit-identical), but the Hines elimination scratch of the
+ * epoch kernel comes from one array of 32 MiB that the library reserves in
+ * device memory on every GPU it is used on, held until the process exits.
+ * The call itself allocates nothing: no cudaMalloc, no cudaFree, no kernel
+ * timing events (PA_FLAG_TIME_KERNELS is ignored here).
+ *   - Limit: models of at most 2,097,152 padded CVs (pa_info.n_padded_cv);
+ *     larger models get PA_ERR_ARG.  Open-loop replay is not supported
+ *     (PA_ERR_STATE).
+ *   - The first call on a GPU looks the array's device address up (a one-time
+ *     set-up, per device): make that first call before any stream capture.
+ *   - All calls share the one array.  Calls whose GPU work overlaps (two models
+ *     advanced concurrently on different streams) race on it; serialise them.
+ *   - Nothing in the array needs clearing: each step writes the values before
+ *     it reads them. */
+int pa_advance_noalloc(pa_model* m, double t_end_ms, double dt_ms);
+
 /* Waits for the model's stream and reports device-side errors. */
 int pa_sync(pa_model* m);
 

@@ -28,6 +28,7 @@ UNITS = {
     "step_mixed.cu": [],
     "events.cu": [],
     "model.cu": NOFMA,
+    "epoch_noalloc.cu": NOFMA,
 }
 
 

@@ -150,6 +150,9 @@ int launch_init_gates_fp64(const double* v, void* gate, int64_t n_lanes, const u
                            void* stream);
 int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
                             void* stream);
+int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, bool mixed,
+                         void* stream);
+int64_t noalloc_max_padded_cv();
 int launch_poisson(const PoissonArgs& a, int64_t k_from, int64_t k_to, void* stream);
 int launch_route(const RouteArgs& a, int32_t max_spikes, void* stream);
 int launch_log_append(const int32_t* spk_count, const int32_t* gid, const int32_t* step,

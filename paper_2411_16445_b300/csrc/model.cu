@@ -846,12 +846,13 @@ int collect_timings(pa_model* M) {
   return PA_OK;
 }
 
-int run_window(pa_model* M, int64_t k_begin, int64_t k_end) {
+int run_window(pa_model* M, int64_t k_begin, int64_t k_end, bool static_scratch = false) {
   using namespace pa;
   const int64_t e = k_begin / M->E;
   const int64_t k0 = e * M->E;
   pa_model::Timed tm{nullptr, nullptr, nullptr, nullptr};
-  if (M->time_kernels) {
+  const bool timed = M->time_kernels && !static_scratch;
+  if (timed) {
     if (M->pending.size() >= 4096) {
       int rc = collect_timings(M);
       if (rc) return rc;
@@ -896,11 +897,20 @@ int run_window(pa_model* M, int64_t k_begin, int64_t k_end) {
       CUDA_TRY(cudaMemcpyAsync(M->rep_spk_step, rs.data(), 4 * rs.size(), cudaMemcpyHostToDevice, M->stream));
     }
   }
-  if (M->time_kernels) CUDA_TRY(cudaEventRecord(tm.b, M->stream));
-  int rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->stream)
-                                    : launch_epoch_fp64(A, M->tree, M->stream);
+  if (timed) CUDA_TRY(cudaEventRecord(tm.b, M->stream));
+  int rc = 0;
+  if (static_scratch) {
+    rc = launch_epoch_noalloc(A, M->total_rows * kLanes, M->tree, M->precision == PA_MIXED,
+                              M->stream);
+    if (rc == -1)
+      return set_err(PA_ERR_ARG, "model has %lld padded CVs; pa_advance_noalloc holds at most %lld",
+                     (long long)(M->total_rows * kLanes), (long long)noalloc_max_padded_cv());
+  } else {
+    rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->stream)
+                                  : launch_epoch_fp64(A, M->tree, M->stream);
+  }
   if (rc) return set_err(PA_ERR_CUDA, "epoch launch: %s", cudaGetErrorString((cudaError_t)rc));
-  if (M->time_kernels) CUDA_TRY(cudaEventRecord(tm.c, M->stream));
+  if (timed) CUDA_TRY(cudaEventRecord(tm.c, M->stream));
   M->n_epoch_launches++;
   M->n_kernel_launches += 4;  // epoch, route, record append, record finalize
   RouteArgs RA = M->ra;
@@ -925,7 +935,7 @@ int run_window(pa_model* M, int64_t k_begin, int64_t k_end) {
       CUDA_TRY(cudaMemsetAsync(M->mask_bases[i] + (int64_t)A.slot * M->mask_elems[i], 0,
                                8 * M->mask_elems[i], M->stream));
   }
-  if (M->time_kernels) {
+  if (timed) {
     CUDA_TRY(cudaEventRecord(tm.d, M->stream));
     M->pending.push_back(tm);
   }
@@ -969,6 +979,29 @@ int pa_advance(pa_model* M, double t_end_ms, double dt_ms) {
     }
   } catch (...) {
     return set_err(PA_ERR_OOM, "host allocation failed in pa_advance");
+  }
+  return PA_OK;
+}
+
+int pa_advance_noalloc(pa_model* M, double t_end_ms, double dt_ms) {
+  if (!M) return set_err(PA_ERR_ARG, "model is NULL");
+  if (dt_ms != M->dt) return set_err(PA_ERR_ARG, "dt %.17g differs from the build-time dt %.17g", dt_ms, M->dt);
+  if (M->replay) return set_err(PA_ERR_STATE, "pa_advance_noalloc does not run in open-loop replay");
+  if (M->total_rows * pa::kLanes > pa::noalloc_max_padded_cv())
+    return set_err(PA_ERR_ARG, "model has %lld padded CVs; pa_advance_noalloc holds at most %lld",
+                   (long long)(M->total_rows * pa::kLanes), (long long)pa::noalloc_max_padded_cv());
+  const double ks = t_end_ms / M->dt;
+  const int64_t k_end = std::llround(ks);
+  if (!std::isfinite(ks) || std::fabs(ks - (double)k_end) > 1e-6 * std::max(1.0, std::fabs(ks)))
+    return set_err(PA_ERR_ARG, "t_end %.17g is not on the dt grid", t_end_ms);
+  if (k_end < M->step) return set_err(PA_ERR_ARG, "t_end lies before the current time");
+  CUDA_TRY(cudaSetDevice(M->device));
+  while (M->step < k_end) {
+    const int64_t e = M->step / M->E;
+    const int64_t stop = std::min(k_end, (e + 1) * (int64_t)M->E);
+    int rc = run_window(M, M->step, stop, true);
+    if (rc) return rc;
+    M->step = stop;
   }
   return PA_OK;
 }

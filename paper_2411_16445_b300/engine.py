@@ -22,7 +22,7 @@ FIELD_V, FIELD_PRP, FIELD_GATES = 16, 17, 18
 ERRORS = {-1: "PA_ERR_ARG", -2: "PA_ERR_OOM", -3: "PA_ERR_CUDA", -4: "PA_ERR_TIMEOUT",
           -5: "PA_ERR_CAPACITY", -6: "PA_ERR_STATE"}
 
-EXPORTED = ("pa_build_model", "pa_advance", "pa_sync", "pa_read_probes", "pa_read_spikes",
+EXPORTED = ("pa_build_model", "pa_advance", "pa_advance_noalloc", "pa_sync", "pa_read_probes", "pa_read_spikes",
             "pa_read_weights", "pa_read_state", "pa_set_replay", "pa_model_info",
             "pa_get_kernel_stats", "pa_reset_kernel_stats", "pa_free_model", "pa_last_error")
 
@@ -87,6 +87,7 @@ def lib():
         L.pa_build_model.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, P, C.c_int64,
                                      P, C.POINTER(C.c_void_p)]
         L.pa_advance.argtypes = [P, C.c_double, C.c_double]
+        L.pa_advance_noalloc.argtypes = [P, C.c_double, C.c_double]
         L.pa_sync.argtypes = [P]
         L.pa_read_probes.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.pa_read_spikes.argtypes = [P, P, P, P, C.c_int64, C.POINTER(C.c_int64)]
@@ -195,6 +196,10 @@ class Model:
 
     def advance(self, t_end_ms: float):
         _check(lib().pa_advance(self._h, float(t_end_ms), self.dt))
+
+    def advance_noalloc(self, t_end_ms: float):
+        """pa_advance_noalloc: same as advance(), allocating nothing during the call."""
+        _check(lib().pa_advance_noalloc(self._h, float(t_end_ms), self.dt))
 
     def advance_steps(self, n: int):
         self.advance((self.step + int(n)) * self.dt)
