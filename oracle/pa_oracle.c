@@ -22,7 +22,10 @@
  *      conductance and calcium decay; forward-Euler steps of the plasticity
  *      ODEs (Eqs. weight_graupner_brunel, early_phase_weight,
  *      late_phase_weight, prp_single_comp) evaluated with the post-event state
- *      of step k; STDP traces decay (Eqs. stdp_ode_1-2).
+ *      of step k.  The STDP traces (Eqs. stdp_ode_1-2) decay exponentially
+ *      between spikes; they are kept as (value, step of the last jump) and
+ *      evaluated in closed form, a(t_k) = a_last exp(-(k - k_last) dt / tau),
+ *      when an event needs them.
  *   5. threshold detection at the soma CV: a spike in step k iff
  *      V^k < theta <= V^{k+1}.
  *
@@ -216,7 +219,7 @@ typedef struct {
   int32_t kind;
   double p[20];
   /* derived per-dt constants */
-  double decay_g, decay_c, decay_pre, decay_post;
+  double decay_g, decay_c;
   double rate_w, rate_h, rate_z, rate_p;
   int64_t dc_steps;
 } orc_mech;
@@ -249,6 +252,7 @@ struct orc_model {
   uint64_t* syn_pid; /* Poisson train of the synapse */
   uint32_t* syn_thr;
   double *g, *c, *w, *hs, *z, *apre, *apost;
+  int64_t *apre_k, *apost_k; /* step of the traces' last jump */
   int64_t *cell_syn_off, *cell_syn;
   int64_t *out_off, *out_syn;
   int64_t *poisson_syn, n_poisson;
@@ -311,7 +315,7 @@ void orc_free(orc_model* M) {
                   M->es, M->d, M->b, M->f, M->xp, M->xnew, M->istep, M->k_on, M->k_off,
                   M->thresh, M->p, M->spiked_prev, M->spk_flag, M->cell_stc_mech, M->spk_t,
                   M->mech, M->syn_cell, M->syn_mech, M->syn_src, M->syn_cv, M->syn_weight,
-                  M->syn_D, M->syn_pid, M->syn_thr, M->g, M->c, M->w, M->hs, M->z, M->apre, M->apost,
+                  M->syn_D, M->syn_pid, M->syn_thr, M->g, M->c, M->w, M->hs, M->z, M->apre, M->apost, M->apre_k, M->apost_k,
                   M->cell_syn_off, M->cell_syn, M->out_off, M->out_syn, M->poisson_syn,
                   M->spk_gid, M->spk_step, M->spk_time, M->probe_cv, M->probes, M->rep_gid,
                   M->rep_step};
@@ -368,10 +372,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
       mc->rate_z = dt / mc->p[10];
       mc->rate_p = dt / mc->p[11];
     }
-    if (mc->kind == ORC_MECH_STDP) {
-      mc->decay_pre = exp(-dt / mc->p[2]);
-      mc->decay_post = exp(-dt / mc->p[3]);
-    }
+
   }
   /* CV layout: cell-major */
   ALLOC(M->cv_off, n_cells + 1);
@@ -466,6 +467,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
   ALLOC(M->syn_cv, n_conn); ALLOC(M->syn_weight, n_conn); ALLOC(M->syn_D, n_conn);
   ALLOC(M->syn_thr, n_conn); ALLOC(M->syn_pid, n_conn); ALLOC(M->g, n_conn); ALLOC(M->c, n_conn); ALLOC(M->w, n_conn);
   ALLOC(M->hs, n_conn); ALLOC(M->z, n_conn); ALLOC(M->apre, n_conn); ALLOC(M->apost, n_conn);
+  ALLOC(M->apre_k, n_conn); ALLOC(M->apost_k, n_conn);
   ALLOC(M->poisson_syn, n_conn);
   int64_t maxdelay = 1;
   ALLOC(M->out_off, n_cells + 1);
@@ -571,9 +573,15 @@ int orc_set_replay(orc_model* M, int64_t n, const int32_t* gid, const int64_t* s
   return 0;
 }
 
-/* pre event on synapse s (conductance jump; STDP pre update, Eqs.
+/* STDP trace value at step k: exact decay since its last jump (Eqs. stdp_ode_1-2
+   without spikes in between) */
+static double trace_at(double a, int64_t k_last, int64_t k, double dt, double tau) {
+  return a * orc_exp(-((double)(k - k_last) * dt) / tau);
+}
+
+/* pre event on synapse s in step k (conductance jump; STDP pre update, Eqs.
    stdp_ode_1 and stdp_ode_3 with the conductance contribution clipped at w_max) */
-static void pre_event(orc_model* M, int64_t s) {
+static void pre_event(orc_model* M, int64_t s, int64_t k) {
   const orc_mech* mc = &M->mech[M->syn_mech[s]];
   switch (mc->kind) {
     case ORC_MECH_EXPSYN:
@@ -591,8 +599,9 @@ static void pre_event(orc_model* M, int64_t s) {
       if (wc < 0.0) wc = 0.0;
       if (wc > mc->p[7]) wc = mc->p[7];
       M->g[s] += M->syn_weight[s] * wc;
-      M->apre[s] += mc->p[4];
-      M->w[s] += M->apost[s];
+      M->apre[s] = trace_at(M->apre[s], M->apre_k[s], k, M->dt, mc->p[2]) + mc->p[4];
+      M->apre_k[s] = k;
+      M->w[s] += trace_at(M->apost[s], M->apost_k[s], k, M->dt, mc->p[3]);
       break;
     }
   }
@@ -604,14 +613,15 @@ static void ca_event(orc_model* M, int64_t s) {
   if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC) M->c[s] += mc->p[3];
 }
 
-/* POST_EVENT -- postsynaptic calcium jump c_post; STDP post update
+/* POST_EVENT in step k -- postsynaptic calcium jump c_post; STDP post update
    (Eqs. stdp_ode_2 and stdp_ode_3) */
-static void post_event(orc_model* M, int64_t s) {
+static void post_event(orc_model* M, int64_t s, int64_t k) {
   const orc_mech* mc = &M->mech[M->syn_mech[s]];
   if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC) M->c[s] += mc->p[4];
   if (mc->kind == ORC_MECH_STDP) {
-    M->apost[s] += mc->p[5];
-    M->w[s] += M->apre[s];
+    M->apost[s] = trace_at(M->apost[s], M->apost_k[s], k, M->dt, mc->p[3]) + mc->p[5];
+    M->apost_k[s] = k;
+    M->w[s] += trace_at(M->apre[s], M->apre_k[s], k, M->dt, mc->p[2]);
   }
 }
 
@@ -702,9 +712,6 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
       double D = (cc > q[6]) ? q[8] * h : 0.0;
       M->hs[s] = h + mc->rate_h * ((0.1 * (h0 - h) + P) - D);
       M->c[s] = cc * mc->decay_c;
-    } else if (mc->kind == ORC_MECH_STDP) {
-      M->apre[s] = M->apre[s] * mc->decay_pre;
-      M->apost[s] = M->apost[s] * mc->decay_post;
     }
   }
   if (M->cell_stc_mech[c] >= 0) {
@@ -728,12 +735,12 @@ int orc_run(orc_model* M, int64_t n_steps) {
     int64_t k = M->step;
     orc_bucket* bk = &M->q[k % M->R];
     for (int64_t e = 0; e < bk->n; ++e)
-      if (bk->v[e].type == 0) pre_event(M, bk->v[e].syn);
+      if (bk->v[e].type == 0) pre_event(M, bk->v[e].syn, k);
     for (int64_t i = 0; i < M->n_poisson; ++i) {
       int64_t s = M->poisson_syn[i];
       if (orc_poisson_u32(M->seed, M->syn_pid[s], k) < M->syn_thr[s]) {
         const orc_mech* mc = &M->mech[M->syn_mech[s]];
-        pre_event(M, s);
+        pre_event(M, s, k);
         if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC)
           push_ev(&M->q[(k + mc->dc_steps) % M->R], (int32_t)s, 1);
       }
@@ -744,7 +751,7 @@ int orc_run(orc_model* M, int64_t n_steps) {
     for (int32_t c = 0; c < M->n_cells; ++c) {
       if (!M->spiked_prev[c]) continue;
       for (int64_t j = M->cell_syn_off[c]; j < M->cell_syn_off[c + 1]; ++j)
-        post_event(M, M->cell_syn[j]);
+        post_event(M, M->cell_syn[j], k);
     }
 #pragma omp parallel for schedule(dynamic, 16)
     for (int32_t c = 0; c < M->n_cells; ++c) cell_step(M, c, k);
@@ -816,8 +823,12 @@ void orc_get_syn(const orc_model* M, int32_t field, double* out) {
       case ORC_SYN_W: v = M->w[s]; break;
       case ORC_SYN_H: v = M->hs[s]; break;
       case ORC_SYN_Z: v = M->z[s]; break;
-      case ORC_SYN_APRE: v = M->apre[s]; break;
-      case ORC_SYN_APOST: v = M->apost[s]; break;
+      case ORC_SYN_APRE:
+        v = mc->kind == ORC_MECH_STDP ? trace_at(M->apre[s], M->apre_k[s], M->step, M->dt, mc->p[2]) : 0.0;
+        break;
+      case ORC_SYN_APOST:
+        v = mc->kind == ORC_MECH_STDP ? trace_at(M->apost[s], M->apost_k[s], M->step, M->dt, mc->p[3]) : 0.0;
+        break;
       case ORC_SYN_WEIGHT_TOTAL:
         if (mc->kind == ORC_MECH_STC) v = M->hs[s] + mc->p[12] * M->z[s];
         else if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STDP) v = M->w[s];

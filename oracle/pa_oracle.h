@@ -41,7 +41,8 @@ enum {
   ORC_MECH_STDP = 13   /* params: tau, e, tau_pre, tau_post, A_pre, A_post, w0, w_max */
 };
 
-/* per-connection synapse state fields readable with orc_get_syn */
+/* per-connection synapse state fields readable with orc_get_syn (STDP traces:
+   their value at the current step) */
 enum {
   ORC_SYN_G = 0, ORC_SYN_C = 1, ORC_SYN_W = 2, ORC_SYN_H = 3, ORC_SYN_Z = 4,
   ORC_SYN_APRE = 5, ORC_SYN_APOST = 6, ORC_SYN_WEIGHT_TOTAL = 7

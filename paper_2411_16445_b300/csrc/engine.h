@@ -30,7 +30,7 @@ struct StreamParams {
   double c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d;
   double rate_w, w_star; // GB: dt/tau_w, w*
   double rate_h, rate_z, rate_p, h0, theta_tag, theta_pro, p_max, f_int;  // STC
-  double a_pre, a_post, decay_pre, decay_post, w_max;                     // STDP
+  double a_pre, a_post, tau_pre, tau_post, w_max;                         // STDP
 };
 
 // Device pointers of one synapse stream.  Element index e = ((sbase+j)<<5)|lane.
@@ -42,8 +42,10 @@ struct StreamDev {
   double* c;             // calcium (GB, STC)
   double* w;             // GB w, STDP w, STC h
   double* z;             // STC z
-  void* apre;            // TM (STDP)
+  void* apre;            // TM (STDP): trace value right after its last jump
   void* apost;           // TM (STDP)
+  int32_t* kpre;         // step of the last jump of apre (STDP)
+  int32_t* kpost;        // step of the last jump of apost (STDP)
   uint64_t* cmask;       // [n_slots][n_elem]: bit (k mod E) = conductance event in step k
   uint64_t* camask;      // [n_slots][n_elem]: delayed calcium event (GB, STC)
   int64_t n_elem;
@@ -107,7 +109,8 @@ struct EpochArgs {
   int64_t probe_sample0;     // sample index of step k_begin
   int64_t probe_cap;         // samples
   int32_t n_probe;
-  int32_t* err_flags;        // bit 0: probe overflow
+  int32_t* err_flags;        // bit 0: probe overflow, bit 1: spike record full,
+                             // bit 2: a bounded wait expired
 };
 
 struct PoissonArgs {

@@ -95,6 +95,86 @@ __device__ __forceinline__ uint32_t elem_of(int32_t row_base, int32_t row, int l
   return ((uint32_t)(row_base + row) << 5) | (uint32_t)lane;
 }
 
+
+// ---------------------------------------------------------------------------
+// Bulk TMA row staging.  Each warp owns a ring of kStages shared-memory stages;
+// one elected lane issues one-dimensional bulk copies (cp.async.bulk, TMA) of
+// the next chunk of rows of every array the pass reads -- a group's rows are
+// contiguous in HBM, 32 lanes per row -- and arms the stage's mbarrier with the
+// byte count; all lanes wait on the barrier (bounded) before reading.
+constexpr int kStages = 2;
+constexpr int kRowsBack = 4;    // rows per chunk in the backward pass
+constexpr int kRowsFwd = 12;    // rows per chunk in the forward pass
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false if the phase did not complete within kSpinLimit polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// generic-proxy global writes of this thread become visible to later TMA reads
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// generic-proxy shared reads of this thread are ordered before later TMA writes
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shared-memory layout of one warp's stages for a given precision / tree flag.
+template <class TM, bool TREE>
+struct Stage {
+  // bytes per row (32 lanes) of each staged array
+  static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(TM), kI = TREE ? 32 * 2 : 0;
+  // backward pass: V, C/dt, diagonal, leak E term, axial coupling, synaptic sums, tree rows
+  static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oDC = oCDT + kRowsBack * kD,
+                       oEM = oDC + kRowsBack * kD, oA = oEM + kRowsBack * kD,
+                       oGS = oA + kRowsBack * kD, oES = oGS + kRowsBack * kM,
+                       oPAR = oES + kRowsBack * kM, oOCH = oPAR + kRowsBack * kI,
+                       kBackBytes = oOCH + kRowsBack * kI;
+  static constexpr int kBackRow = 5 * kD + 2 * kM + 2 * kI;
+  // forward pass: f, x', tree parent rows
+  static constexpr int fF = 0, fXP = fF + kRowsFwd * kD, fPAR = fXP + kRowsFwd * kD,
+                       kFwdBytes = fPAR + kRowsFwd * kI;
+  static constexpr int kFwdRow = 2 * kD + kI;
+  static constexpr int kBytes = (kBackBytes > kFwdBytes ? kBackBytes : kFwdBytes);
+  static constexpr int kWarpBytes = kStages * kBytes + 64;  // + mbarriers
+};
+
 // scatter one synapse's g and g*E into its CV's accumulators
 template <class TM>
 __device__ __forceinline__ void contribute(TM* gs, TM* es, int32_t rb, int lane, int32_t cvf,
@@ -111,9 +191,20 @@ __device__ __forceinline__ void contribute(TM* gs, TM* es, int32_t rb, int lane,
 
 template <class TM, bool TREE>
 __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
+  using ST = Stage<TM, TREE>;
+  extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   if (g >= A.n_groups) return;  // whole warps only
+  char* wbuf = smem_raw + (threadIdx.x >> 5) * ST::kWarpBytes;
+  uint64_t* bar = (uint64_t*)(wbuf + kStages * ST::kBytes);
+  if (lane == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  uint32_t phase = 0;  // expected parity of each stage's barrier
+  bool failed = false;
   using HH = HH64;
   const int64_t L = (int64_t)g * 32 + lane;
   const int n = A.ncv[L];
@@ -203,27 +294,30 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
           double Dh = (cc > P.theta_d) ? P.gamma_d * h : 0.0;
           D.w[e] = h + P.rate_h * ((0.1 * (h0 - h) + Ph) - Dh);
           C[e] = cc * P.decay_c;
-        } else {  // SK_STDP
-          TM* AP = (TM*)D.apre;
-          TM* AQ = (TM*)D.apost;
-          TM ap = AP[e], aq = AQ[e];
+        } else {  // SK_STDP: traces evaluated in closed form at events only
           if (pre || post) {
+            TM* AP = (TM*)D.apre;
+            TM* AQ = (TM*)D.apost;
             double w = D.w[e];
+            double ap = (double)AP[e] * model_exp(-((double)(k - D.kpre[e]) * dt) / P.tau_pre);
+            double aq = (double)AQ[e] * model_exp(-((double)(k - D.kpost[e]) * dt) / P.tau_post);
             if (pre) {
               double wc = w < 0.0 ? 0.0 : (w > P.w_max ? P.w_max : w);
               gv = gv + (TM)((double)((const TM*)D.weight)[e] * wc);
-              ap = ap + (TM)P.a_pre;
-              w = w + (double)aq;
+              ap = ap + P.a_pre;
+              w = w + aq;
+              AP[e] = (TM)ap;
+              D.kpre[e] = (int32_t)k;
             }
             if (post) {
-              aq = aq + (TM)P.a_post;
-              w = w + (double)ap;
+              aq = aq + P.a_post;
+              w = w + ap;
+              AQ[e] = (TM)aq;
+              D.kpost[e] = (int32_t)k;
             }
             D.w[e] = w;
           }
           contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
-          AP[e] = ap * (TM)P.decay_pre;
-          AQ[e] = aq * (TM)P.decay_post;
         }
         G[e] = gv * dg;
       }
@@ -234,78 +328,167 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
     }
 
     // ---- b. backward pass: assembly + elimination --------------------------
+    // rows n-1 .. 0, staged from HBM in chunks of kRowsBack rows
     double v0_old = 0.0, v0_new = 0.0;
     const double iinj = (k >= kon && k < koff) ? iinj_val : 0.0;
-    double cf = 0.0, ca = 0.0, cx = 0.0;
-    bool carry = false;
-    for (int i = rows - 1; i >= 0; --i) {
-      if (i >= n) continue;
-      const uint32_t e = elem_of(rb, i, lane);
-      const double v = Vg[e];
-      const double cdt = CDT[e];
-      double d, b;
-      if (i == 0) {
-        v0_old = v;
-        if (hh) {
-          const double mmmh = ((gm_ * gm_) * gm_) * gh_;
-          const double nnnn = ((gn_ * gn_) * gn_) * gn_;
-          const double g1 = gna * mmmh;
-          const double g2 = gk * nnnn;
-          const double gmt = (g1 + g2) + gl;
-          const double emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
-          d = (DC[e] + gmt) + (double)GS[e];
-          b = (fma(cdt, v, emt) + iinj) + (double)ES[e];
-        } else {
-          d = DC[e] + (double)GS[e];
-          b = (fma(cdt, v, EM[e]) + iinj) + (double)ES[e];
+    fence_async_global();  // this step's V and synaptic sums, written by plain stores
+    __syncwarp();
+    {
+      const int nc = (rows + kRowsBack - 1) / kRowsBack;
+      auto issue = [&](int c) {
+        const int s = c % kStages;
+        const int hi = rows - kRowsBack * c, lo = hi > kRowsBack ? hi - kRowsBack : 0;
+        const uint32_t cnt = (uint32_t)(hi - lo);
+        if (lane == 0) {
+          char* st = wbuf + s * ST::kBytes;
+          const size_t r0 = (size_t)(rb + lo);
+          mbar_expect_tx(&bar[s], cnt * ST::kBackRow);
+          bulk_load(st + ST::oV, Vg + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::oCDT, CDT + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::oDC, DC + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::oEM, EM + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::oA, AA + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kM, &bar[s]);
+          bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kM, &bar[s]);
+          if (TREE) {
+            bulk_load(st + ST::oPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
+            bulk_load(st + ST::oOCH, A.och_head + r0 * 32, cnt * ST::kI, &bar[s]);
+          }
         }
-      } else {
-        d = DC[e] + (double)GS[e];
-        b = fma(cdt, v, EM[e]) + (double)ES[e];
-      }
-      int pi = i - 1;
-      if (TREE) {
-        if (i > 0) pi = A.par[e];
-        for (int c = A.och_head[e]; c >= 0;) {
-          const uint32_t ec = elem_of(rb, c, lane);
-          const double ac = AA[ec];
-          d = fma(-F[ec], ac, d);
-          b = fma(-ac, XP[ec], b);
-          c = A.och_next[ec];
+      };
+      for (int c = 0; c < kStages - 1 && c < nc; ++c) issue(c);
+      double cf = 0.0, ca = 0.0, cx = 0.0;
+      bool carry = false;
+      for (int c = 0; c < nc; ++c) {
+        if (c + kStages - 1 < nc) {
+          fence_async_shared();  // reads of the stage about to be refilled are done
+          __syncwarp();
+          issue(c + kStages - 1);
         }
-      }
-      if (carry) {
-        d = fma(-cf, ca, d);
-        b = fma(-ca, cx, b);
-      }
-      if (i > 0) {
-        const double ai = AA[e];
-        const double r = 1.0 / d;
-        const double fi = ai * r;
-        const double xi = b * r;
-        F[e] = fi;
-        XP[e] = xi;
-        carry = !TREE || pi == i - 1;
-        cf = fi; ca = ai; cx = xi;
-      } else {
-        v0_new = b * (1.0 / d);
+        const int s = c % kStages;
+        if (!mbar_wait(&bar[s], (phase >> s) & 1u)) failed = true;
+        phase ^= 1u << s;
+        if (__any_sync(0xffffffffu, failed)) break;
+        const char* st = wbuf + s * ST::kBytes;
+        const int hi = rows - kRowsBack * c, lo = hi > kRowsBack ? hi - kRowsBack : 0;
+        for (int i = hi - 1; i >= lo; --i) {
+          if (i >= n) continue;
+          const int r = (i - lo) * 32 + lane;
+          const uint32_t e = elem_of(rb, i, lane);
+          const double v = ((const double*)(st + ST::oV))[r];
+          const double cdt = ((const double*)(st + ST::oCDT))[r];
+          const double dcv = ((const double*)(st + ST::oDC))[r];
+          const double gsv = (double)((const TM*)(st + ST::oGS))[r];
+          const double esv = (double)((const TM*)(st + ST::oES))[r];
+          double d, b;
+          if (i == 0) {
+            v0_old = v;
+            if (hh) {
+              const double mmmh = ((gm_ * gm_) * gm_) * gh_;
+              const double nnnn = ((gn_ * gn_) * gn_) * gn_;
+              const double g1 = gna * mmmh;
+              const double g2 = gk * nnnn;
+              const double gmt = (g1 + g2) + gl;
+              const double emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
+              d = (dcv + gmt) + gsv;
+              b = (fma(cdt, v, emt) + iinj) + esv;
+            } else {
+              d = dcv + gsv;
+              b = (fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + iinj) + esv;
+            }
+          } else {
+            d = dcv + gsv;
+            b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + esv;
+          }
+          int pi = i - 1;
+          if (TREE) {
+            if (i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
+            for (int ch = ((const int16_t*)(st + ST::oOCH))[r]; ch >= 0;) {
+              const uint32_t ec = elem_of(rb, ch, lane);
+              const double ac = AA[ec];
+              d = fma(-F[ec], ac, d);
+              b = fma(-ac, XP[ec], b);
+              ch = A.och_next[ec];
+            }
+          }
+          if (carry) {
+            d = fma(-cf, ca, d);
+            b = fma(-ca, cx, b);
+          }
+          if (i > 0) {
+            const double ai = ((const double*)(st + ST::oA))[r];
+            const double rr = 1.0 / d;
+            const double fi = ai * rr;
+            const double xi = b * rr;
+            F[e] = fi;
+            XP[e] = xi;
+            carry = !TREE || pi == i - 1;
+            cf = fi; ca = ai; cx = xi;
+          } else {
+            v0_new = b * (1.0 / d);
+          }
+        }
       }
     }
-    // ---- c. forward pass: back substitution ---------------------------------
-    if (n > 0) {
-      Vg[elem_of(rb, 0, lane)] = v0_new;
-      double vprev = v0_new;
-      for (int i = 1; i < n; ++i) {
-        const uint32_t e = elem_of(rb, i, lane);
-        double vp = vprev;
-        if (TREE) {
-          const int pi = A.par[e];
-          if (pi != i - 1) vp = Vg[elem_of(rb, pi, lane)];
+    // ---- c. forward pass: back substitution, rows 0 .. n-1 ------------------
+    fence_async_global();  // f and x' of this step, written by plain stores
+    __syncwarp();
+    if (!__any_sync(0xffffffffu, failed)) {
+      const int nc = (rows + kRowsFwd - 1) / kRowsFwd;
+      auto issue = [&](int c) {
+        const int s = c % kStages;
+        const int lo = kRowsFwd * c, hi = lo + kRowsFwd < rows ? lo + kRowsFwd : rows;
+        const uint32_t cnt = (uint32_t)(hi - lo);
+        if (lane == 0) {
+          char* st = wbuf + s * ST::kBytes;
+          const size_t r0 = (size_t)(rb + lo);
+          mbar_expect_tx(&bar[s], cnt * ST::kFwdRow);
+          bulk_load(st + ST::fF, F + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::fXP, XP + r0 * 32, cnt * ST::kD, &bar[s]);
+          if (TREE) bulk_load(st + ST::fPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
         }
-        const double vi = fma(-F[e], vp, XP[e]);
-        Vg[e] = vi;
-        vprev = vi;
+      };
+      fence_async_shared();
+      __syncwarp();
+      for (int c = 0; c < kStages - 1 && c < nc; ++c) issue(c);
+      if (n > 0) Vg[elem_of(rb, 0, lane)] = v0_new;
+      double vprev = v0_new;
+      for (int c = 0; c < nc; ++c) {
+        if (c + kStages - 1 < nc) {
+          fence_async_shared();
+          __syncwarp();
+          issue(c + kStages - 1);
+        }
+        const int s = c % kStages;
+        if (!mbar_wait(&bar[s], (phase >> s) & 1u)) failed = true;
+        phase ^= 1u << s;
+        if (__any_sync(0xffffffffu, failed)) break;
+        const char* st = wbuf + s * ST::kBytes;
+        const int lo = kRowsFwd * c, hi = lo + kRowsFwd < rows ? lo + kRowsFwd : rows;
+        for (int i = lo > 1 ? lo : 1; i < hi; ++i) {
+          if (i >= n) break;
+          const int r = (i - lo) * 32 + lane;
+          double vp = vprev;
+          if (TREE) {
+            const int pi = ((const int16_t*)(st + ST::fPAR))[r];
+            if (pi != i - 1) vp = Vg[elem_of(rb, pi, lane)];
+          }
+          const double vi = fma(-((const double*)(st + ST::fF))[r], vp,
+                                ((const double*)(st + ST::fXP))[r]);
+          Vg[elem_of(rb, i, lane)] = vi;
+          vprev = vi;
+        }
       }
+      fence_async_shared();
+      __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, failed)) {
+      // a stage never arrived: report and drain every copy still in flight
+      if (lane == 0) atomicOr(A.err_flags, 4);
+      for (int s = 0; s < kStages; ++s) mbar_wait(&bar[s], (phase >> s) & 1u);
+      return;
+    }
+    if (n > 0) {
       for (int32_t q = pq0; q < pq1; ++q) {
         const int64_t smp = A.probe_sample0 + (k - A.k_begin);
         if (smp < A.probe_cap) {
@@ -373,17 +556,23 @@ int launch_init_gates_impl(const double* v, void* gate, int64_t n_lanes, const u
   return (int)cudaGetLastError();
 }
 
-template <class TM>
-int launch_epoch_impl(const EpochArgs& a, bool tree, void* stream) {
+template <class TM, bool TREE>
+int launch_epoch_t(const EpochArgs& a, void* stream) {
   const int threads = 128;
   const int64_t warps = a.n_groups;
   const int blocks = (int)((warps * 32 + threads - 1) / threads);
   if (blocks == 0) return 0;
-  if (tree)
-    epoch_kernel<TM, true><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
-  else
-    epoch_kernel<TM, false><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
+  const int smem = (threads / 32) * Stage<TM, TREE>::kWarpBytes;
+  cudaError_t e = cudaFuncSetAttribute(epoch_kernel<TM, TREE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return (int)e;
+  epoch_kernel<TM, TREE><<<blocks, threads, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
+}
+
+template <class TM>
+int launch_epoch_impl(const EpochArgs& a, bool tree, void* stream) {
+  return tree ? launch_epoch_t<TM, true>(a, stream) : launch_epoch_t<TM, false>(a, stream);
 }
 
 }  // namespace pa

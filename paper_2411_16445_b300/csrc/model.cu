@@ -249,8 +249,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         break;
       case PA_MECH_STDP:
         P.kind = SK_STDP;
-        P.decay_pre = std::exp(-dt / p[2]);
-        P.decay_post = std::exp(-dt / p[3]);
+        P.tau_pre = p[2];
+        P.tau_post = p[3];
         P.a_pre = p[4]; P.a_post = p[5]; P.w_max = p[7];
         break;
     }
@@ -589,7 +589,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
                o_gate = R(8 * 3 * n_lanes), o_iinj = R(8 * n_lanes), o_kon = R(8 * n_lanes),
                o_koff = R(8 * n_lanes), o_th = R(8 * n_lanes), o_sp = R(n_lanes),
                o_prp = R(8 * n_lanes), o_hasstc = R(n_lanes), o_rbits = R(8 * n_lanes);
-  size_t o_s[kMaxStreams][10];
+  size_t o_s[kMaxStreams][11];
   for (int s = 0; s < n_streams; ++s) {
     const int64_t ne = M->s_nelem[s];
     const int kind = M->sp[s].kind;
@@ -602,6 +602,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     o_s[s][6] = (kind == SK_STC) ? R(8 * ne) : 0;                               // z
     o_s[s][7] = (kind == SK_STDP) ? R(tm * ne) : 0;                             // apre
     o_s[s][8] = (kind == SK_STDP) ? R(tm * ne) : 0;                             // apost
+    o_s[s][10] = (kind == SK_STDP) ? R(8 * ne) : 0;                             // kpre, kpost
     o_s[s][9] = R(8 * ne * (size_t)M->n_slots * ((kind == SK_GB || kind == SK_STC) ? 2 : 1));
   }
   const size_t np = ps_conn.size();
@@ -710,6 +711,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     sd.z = o_s[s][6] ? (double*)P8(o_s[s][6]) : nullptr;
     sd.apre = o_s[s][7] ? P8(o_s[s][7]) : nullptr;
     sd.apost = o_s[s][8] ? P8(o_s[s][8]) : nullptr;
+    sd.kpre = o_s[s][10] ? (int32_t*)P8(o_s[s][10]) : nullptr;
+    sd.kpost = o_s[s][10] ? (int32_t*)P8(o_s[s][10]) + ne : nullptr;
     sd.cmask = (uint64_t*)P8(o_s[s][9]);
     sd.camask = (kind == SK_GB || kind == SK_STC) ? sd.cmask + ne * M->n_slots : nullptr;
     sd.n_elem = ne;
@@ -812,6 +815,8 @@ int check_device_errors(pa_model* M) {
   CUDA_TRY(cudaStreamSynchronize(M->stream));
   if (flags) {
     CUDA_TRY(cudaMemsetAsync(M->err_flags, 0, 4, M->stream));
+    if (flags & 4)
+      return set_err(PA_ERR_TIMEOUT, "a bounded device wait expired (row staging); results invalid");
     return set_err(PA_ERR_CAPACITY, "%s%s",
                    (flags & 1) ? "probe buffer full (read probes more often or raise probe_capacity); " : "",
                    (flags & 2) ? "spike record full (read spikes more often or raise spike_capacity)" : "");
@@ -1127,9 +1132,27 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
     int rc = fetch(src, src ? D.n_elem : 0, esz, per_stream[s]);
     if (rc) return rc;
   }
+  // STDP traces are stored as (value after the last jump, step of that jump)
+  std::vector<std::vector<double>> kstep(M->n_streams);
+  if (field == PA_FIELD_APRE || field == PA_FIELD_APOST) {
+    for (int s = 0; s < M->n_streams; ++s) {
+      const StreamDev& D = M->ea.sd[s];
+      if (M->sp[s].kind != SK_STDP) continue;
+      std::vector<int32_t> ks(D.n_elem);
+      const int32_t* src = field == PA_FIELD_APRE ? D.kpre : D.kpost;
+      CUDA_TRY(cudaMemcpyAsync(ks.data(), src, 4 * D.n_elem, cudaMemcpyDeviceToHost, M->stream));
+      CUDA_TRY(cudaStreamSynchronize(M->stream));
+      kstep[s].assign(ks.begin(), ks.end());
+    }
+  }
   for (int64_t c = 0; c < M->n_conn; ++c) {
-    const auto& v = per_stream[M->conn_stream[c]];
+    const int s = M->conn_stream[c];
+    const auto& v = per_stream[s];
     out[c] = v.empty() ? 0.0 : v[M->conn_elem[c]];
+    if (!kstep[s].empty()) {
+      const double tau = field == PA_FIELD_APRE ? M->sp[s].tau_pre : M->sp[s].tau_post;
+      out[c] *= std::exp(-((double)(M->step - (int64_t)kstep[s][M->conn_elem[c]]) * M->dt) / tau);
+    }
   }
   return PA_OK;
 }
