@@ -75,23 +75,27 @@ def net_stats(net):
     }
 
 
-def per_cu_model(st, mixed):
+def per_cu_model(st, mixed, static_frac):
     """Algorithmic work of one compartment-update, amortising soma and synapse work.
     Bytes: state that must stream every step (V read+write, four FP64 cable
-    coefficients C/dt, diagonal, leak E term, axial coupling; 2-byte parent index
-    on trees) plus per-synapse state read+write, CV index and event word.
-    FP64 ops in FMA-equivalents: the Hines row (b assembly, two synaptic sums,
-    two child-contribution FMAs, f and x' products, back-substitution FMA, one
-    reciprocal costed at its measured issue cost), HH per soma, FP64 synapse ops."""
+    coefficients: C/dt, diagonal, leak E term, axial coupling; 2-byte parent
+    index on trees) plus per-synapse state read+write (conductance; the STDP
+    traces are touched only at events), CV index and event word.
+    FP64 ops in FMA-equivalents: a row with a time-varying diagonal costs the b
+    assembly, two synaptic sums, two child-contribution FMAs, the f and x'
+    products, the back-substitution FMA and one reciprocal at its measured issue
+    cost; a static row (constant diagonal, reciprocal precomputed) costs the b
+    assembly, one child FMA, the x' product and the back-substitution FMA.  Plus
+    HH per soma and, on the FP64 path, the synapse ops."""
     ts = 4 if mixed else 8
     cv_bytes = 16 + 32 + (2 if st["tree"] else 0)
-    stdp_bytes = 2 * ts * 3 + 8 + 4 + 8          # g, apre, apost r/w; w touched on events only
+    stdp_bytes = 2 * ts + 4 + 8
     exp_bytes = 2 * ts + 4 + 8
     syn_bytes = st["n_stdp"] * stdp_bytes + st["n_expsyn"] * exp_bytes
     bytes_per_cu = cv_bytes + syn_bytes / st["n_cv"]
-    solve = 8 + RCP64_DFMA_EQ + (2 if mixed else 0)   # mixed: two FP32->FP64 sum conversions
+    solve = (1 - static_frac) * (8 + RCP64_DFMA_EQ) + static_frac * 4
     hh = 153 + 6 * RCP64_DFMA_EQ + 20                  # 9 model exps, 6 divisions, currents
-    syn = 0 if mixed else (st["n_stdp"] * 6 + st["n_expsyn"] * 4)
+    syn = 0 if mixed else (st["n_stdp"] * 3 + st["n_expsyn"] * 3)
     fp64_per_cu = solve + (hh * st["n_cells"] + syn) / st["n_cv"]
     return bytes_per_cu, fp64_per_cu
 
@@ -151,9 +155,10 @@ def time_gpu(net, precision, steps, warmup, device, stream_barrier):
     stream = torch.cuda.current_stream(device)
     t0 = time.perf_counter()
     m = E.Model(net, precision=precision, device=device, stream=E.C.c_void_p(stream.cuda_stream),
-                flags=E.FLAG_TIME_KERNELS)
+                flags=E.FLAG_TIME_KERNELS | E.FLAG_AUTOTUNE)
     setup_s = time.perf_counter() - t0
     info = m.info()
+    shape, trial_ms = m.tuning()
     E_steps = info.epoch_steps
     m.advance(warmup * E_steps * net.dt)
     m.sync()
@@ -176,9 +181,11 @@ def time_gpu(net, precision, steps, warmup, device, stream_barrier):
     ks = m.kernel_stats()
     gid, _, _ = m.read_spikes()
     res = {"ms": ms, "epoch_steps": E_steps, "n_cv": info.n_cv, "setup_s": setup_s,
+           "static_frac": info.n_static_cv / max(info.n_cv, 1),
            "epoch_kernel_ms": ks.epoch_kernel_ms, "event_kernels_ms": ks.event_kernels_ms,
            "epoch_launches": ks.epoch_launches, "kernel_launches": ks.kernel_launches,
-           "spikes": int(len(gid)), "device_bytes": info.device_bytes, "clocks": clocks}
+           "spikes": int(len(gid)), "device_bytes": info.device_bytes, "clocks": clocks,
+           "shape": shape, "shape_trial_ms": [round(float(x), 3) for x in trial_ms]}
     m.close()
     return res
 
@@ -191,7 +198,7 @@ def time_e2e(net, precision, steps, device):
     from paper_2411_16445_b300 import engine as E
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
-    m = E.Model(net, precision=precision, device=device)
+    m = E.Model(net, precision=precision, device=device, flags=E.FLAG_AUTOTUNE)
     info = m.info()
     h2d = info.device_bytes
     spikes = 0
@@ -303,7 +310,7 @@ def main():
         return
 
     def roofline(run, mixed):
-        bpc, fpc = per_cu_model(st, mixed)
+        bpc, fpc = per_cu_model(st, mixed, run["static_frac"])
         cu_launch = run["n_cv"] * run["epoch_steps"]
         t_launch = run["epoch_kernel_ms"] / max(run["epoch_launches"], 1) * 1e-3
         clk = (run["clocks"] or {}).get("sm_mhz") or 2032.0
@@ -342,7 +349,9 @@ def main():
                       "ms_per_step": run["ms"] / args.steps,
                       "epoch_kernel_ms_per_step": run["epoch_kernel_ms"] / max(run["epoch_launches"], 1),
                       "event_kernels_ms_per_step": run["event_kernels_ms"] / max(run["epoch_launches"], 1),
-                      "spikes": run["spikes"], "roofline": roofline(run, name == "mixed")}
+                      "spikes": run["spikes"], "kernel_shape": run["shape"],
+                      "shape_trial_ms": run["shape_trial_ms"],
+                      "roofline": roofline(run, name == "mixed")}
     if "mixed" in runs and "fp64" in runs:
         line["mixed_over_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
     if not args.no_e2e:

@@ -161,6 +161,15 @@ typedef struct {
 /* pa_options.flags: record CUDA events around every kernel launch on the model's
  * stream so that pa_get_kernel_stats can report device time per kernel kind. */
 #define PA_FLAG_TIME_KERNELS 1
+/* pa_options.flags: at build time, time every compiled shape of the epoch kernel
+ * (rows per TMA chunk, warps per block, register budget) on the model's first
+ * epoch and keep the fastest.  The model's state is snapshot and restored
+ * around the trials (needs a second copy of the model's device memory for the
+ * duration of the build; without room for it the default shape is kept). */
+#define PA_FLAG_AUTOTUNE 2
+/* pa_options.flags: force epoch-kernel shape s (0 <= s < PA_N_SHAPES) */
+#define PA_FLAG_SHAPE(s) ((((s) + 1) & 0xF) << 8)
+#define PA_N_SHAPES 5
 
 typedef struct {
   int64_t epoch_launches;   /* epoch (time-step) kernel launches since the last reset */
@@ -176,7 +185,11 @@ typedef struct {
   int32_t precision;
   int32_t tree;             /* 1 if any morphology branches */
   int32_t n_streams;        /* synapse streams (one per point mechanism in use) */
+  int32_t shape;            /* epoch-kernel shape in use */
+  int32_t reserved;
   int64_t device_bytes;     /* device memory held by the model */
+  int64_t n_static_cv;      /* CVs whose subtree carries no synapse: their eliminated
+                               diagonal is constant, its reciprocal precomputed */
 } pa_info;
 
 /* Validates the descriptors, discretises every morphology (CV = cylinder:
@@ -247,6 +260,10 @@ int pa_read_state(pa_model* m, int32_t field, double* out, int64_t cap, int64_t*
 int pa_set_replay(pa_model* m, int64_t n, const int32_t* gid, const int64_t* step);
 
 int pa_model_info(const pa_model* m, pa_info* info);
+
+/* The epoch-kernel shape in use and, if the model was autotuned, the trial time
+ * [ms] of each shape (cap entries of trial_ms; 0 for untried shapes). */
+int pa_get_tuning(const pa_model* m, int32_t* shape, double* trial_ms, int32_t cap);
 
 /* Launch counts and (with PA_FLAG_TIME_KERNELS) device times since the last
  * reset.  Synchronises the model's stream. */

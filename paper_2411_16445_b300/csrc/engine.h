@@ -147,14 +147,15 @@ struct RouteArgs {
 };
 
 // kernel launchers (defined in the .cu files)
-int launch_epoch_fp64(const EpochArgs& a, bool tree, void* stream);
-int launch_epoch_mixed(const EpochArgs& a, bool tree, void* stream);
+constexpr int kNumShapes = 5;  // kernel shapes (see launch_epoch_shape)
+int launch_epoch_fp64(const EpochArgs& a, bool tree, int shape, void* stream);
+int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream);
 int launch_init_gates_fp64(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
                            void* stream);
 int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
                             void* stream);
 int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, bool mixed,
-                         void* stream);
+                         int shape, void* stream);
 int64_t noalloc_max_padded_cv();
 int launch_poisson(const PoissonArgs& a, int64_t k_from, int64_t k_to, void* stream);
 int launch_route(const RouteArgs& a, int32_t max_spikes, void* stream);

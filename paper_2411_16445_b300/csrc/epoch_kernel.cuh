@@ -98,13 +98,13 @@ __device__ __forceinline__ uint32_t elem_of(int32_t row_base, int32_t row, int l
 
 // ---------------------------------------------------------------------------
 // Bulk TMA row staging.  Each warp owns a ring of kStages shared-memory stages;
+// the chunk sizes (rows per copy in the backward and forward passes) and the
+// register budget form the kernel's "shape", chosen per model (autotuned);
 // one elected lane issues one-dimensional bulk copies (cp.async.bulk, TMA) of
 // the next chunk of rows of every array the pass reads -- a group's rows are
 // contiguous in HBM, 32 lanes per row -- and arms the stage's mbarrier with the
 // byte count; all lanes wait on the barrier (bounded) before reading.
 constexpr int kStages = 2;
-constexpr int kRowsBack = 4;    // rows per chunk in the backward pass
-constexpr int kRowsFwd = 12;    // rows per chunk in the forward pass
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -156,7 +156,7 @@ __device__ __forceinline__ void fence_async_shared() {
 }
 
 // Shared-memory layout of one warp's stages for a given precision / tree flag.
-template <class TM, bool TREE>
+template <class TM, bool TREE, int kRowsBack, int kRowsFwd>
 struct Stage {
   // bytes per row (32 lanes) of each staged array
   static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(TM), kI = TREE ? 32 * 2 : 0;
@@ -175,23 +175,36 @@ struct Stage {
   static constexpr int kWarpBytes = kStages * kBytes + 64;  // + mbarriers
 };
 
-// scatter one synapse's g and g*E into its CV's accumulators
+// Per-CV synaptic sums over one run of same-CV synapses of a stream, in the
+// canonical order: the run starts from 0 (first synapse on the CV) or from the
+// sums left by an earlier stream, and is stored when it ends.
+// cvf = (cv << 3) | first-on-CV (1) | run start (2) | run end (4).
 template <class TM>
-__device__ __forceinline__ void contribute(TM* gs, TM* es, int32_t rb, int lane, int32_t cvf,
-                                           TM g, TM E) {
-  uint32_t ce = elem_of(rb, cvf >> 1, lane);
-  if (cvf & 1) {
-    gs[ce] = g;
-    es[ce] = g * E;
+__device__ __forceinline__ void run_sum(TM* gs, TM* es, int32_t rb, int lane, int32_t cvf, TM g,
+                                        TM E, TM& accg, TM& acce) {
+  if (cvf & 2) {
+    if (cvf & 1) {
+      accg = g;
+      acce = g * E;
+    } else {
+      const uint32_t ce = elem_of(rb, cvf >> 3, lane);
+      accg = gs[ce] + g;
+      acce = es[ce] + g * E;
+    }
   } else {
-    gs[ce] = gs[ce] + g;
-    es[ce] = es[ce] + g * E;
+    accg = accg + g;
+    acce = acce + g * E;
+  }
+  if (cvf & 4) {
+    const uint32_t ce = elem_of(rb, cvf >> 3, lane);
+    gs[ce] = accg;
+    es[ce] = acce;
   }
 }
 
-template <class TM, bool TREE>
-__global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
-  using ST = Stage<TM, TREE>;
+template <class TM, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const EpochArgs A) {
+  using ST = Stage<TM, TREE, kRowsBack, kRowsFwd>;
   extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -223,13 +236,9 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
   double* __restrict__ XP = A.xp;
 
   const bool hh = n > 0 && A.is_hh[L];
-  const double* hg = A.hh_g;
-  const double* he = A.hh_e;
   double* gate = A.gate;
-  double gna = 0, gk = 0, gl = 0, ena = 0, ek = 0, el = 0, gm_ = 0, gh_ = 0, gn_ = 0;
+  double gm_ = 0, gh_ = 0, gn_ = 0;
   if (hh) {
-    gna = hg[L]; gk = hg[A.n_lanes + L]; gl = hg[2 * A.n_lanes + L];
-    ena = he[L]; ek = he[A.n_lanes + L]; el = he[2 * A.n_lanes + L];
     gm_ = gate[L]; gh_ = gate[A.n_lanes + L]; gn_ = gate[2 * A.n_lanes + L];
   }
   const double iinj_val = n > 0 ? A.iinj[L] : 0.0;
@@ -241,97 +250,154 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
   const uint64_t rbits = (A.replay && n > 0) ? A.replay_bits[L] : 0ull;
   const int32_t pq0 = n > 0 ? A.probe_ptr[L] : 0, pq1 = n > 0 ? A.probe_ptr[L + 1] : 0;
 
-  for (int64_t k = A.k_begin; k < A.k_end; ++k) {
+  for (int64_t k = A.k_begin; k < A.k_end && !failed; ++k) {
     const int kk = (int)(k - A.k0);
     const bool post = spiked_prev;
-    // ---- a. synapse streams ------------------------------------------------
+    // ---- a. synapse streams, rows staged by TMA ------------------------------
+    fence_async_global();  // last step's synapse state and V, written by plain stores
+    __syncwarp();
     double S = 0.0;
-    for (int s = 0; s < A.n_streams; ++s) {
+    for (int s = 0; s < A.n_streams && !failed; ++s) {
       const StreamParams& P = A.sp[s];
       const StreamDev& D = A.sd[s];
-      const int32_t sb = D.sbase[g], se = D.sbase[g + 1];
-      const uint64_t* cm = D.cmask + (int64_t)A.slot * D.n_elem;
-      const uint64_t* cam = D.camask ? D.camask + (int64_t)A.slot * D.n_elem : nullptr;
+      const int32_t sb = D.sbase[g], nrow = D.sbase[g + 1] - sb;
+      const bool calc = P.kind == SK_GB || P.kind == SK_STC;
+      const bool stc = P.kind == SK_STC;
+      constexpr int szm = 32 * (int)sizeof(TM);
+      const int rowb = 128 + 256 + szm + (calc ? 768 : 0) + (stc ? 256 : 0);
+      int RS = ST::kBytes / rowb;
+      if (RS > 16) RS = 16;
+      const int o_cm = RS * 128, o_g = o_cm + RS * 256, o_cam = o_g + RS * szm,
+                o_c = o_cam + RS * 256, o_w = o_c + RS * 256, o_z = o_w + RS * 256;
+      const int nc = (nrow + RS - 1) / RS;
+      const uint64_t* cmg = D.cmask + (int64_t)A.slot * D.n_elem;
+      const uint64_t* camg = calc ? D.camask + (int64_t)A.slot * D.n_elem : nullptr;
       TM* G = (TM*)D.g;
       const TM E = (TM)P.e;
       const TM dg = (TM)P.decay_g;
-      for (int32_t j = sb; j < se; ++j) {
-        const uint32_t e = ((uint32_t)j << 5) | (uint32_t)lane;
-        const int32_t cvf = D.cvf[e];
-        if (cvf < 0) continue;
-        const bool pre = (cm[e] >> kk) & 1ull;
-        TM gv = G[e];
-        if (P.kind == SK_EXPSYN) {
-          if (pre) gv = gv + ((const TM*)D.weight)[e];
-          contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
-        } else if (P.kind == SK_GB) {
-          double* C = D.c;
-          double cc = C[e];
-          if (pre) gv = gv + ((const TM*)D.weight)[e];
-          if ((cam[e] >> kk) & 1ull) cc = cc + P.c_pre;
-          if (post) cc = cc + P.c_post;
-          contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
-          double w = D.w[e];
-          double Aw = (w * (1.0 - w)) * (P.w_star - w);
-          double Pw = (cc > P.theta_p) ? P.gamma_p * (1.0 - w) : 0.0;
-          double Dw = (cc > P.theta_d) ? P.gamma_d * w : 0.0;
-          D.w[e] = w + P.rate_w * ((Pw - Aw) - Dw);
-          C[e] = cc * P.decay_c;
-        } else if (P.kind == SK_STC) {
-          double* C = D.c;
-          double cc = C[e];
-          double h = D.w[e], z = D.z[e];
-          const double h0 = P.h0;
-          if (pre) gv = gv + (TM)((double)((const TM*)D.weight)[e] * ((h + h0 * z) / h0));
-          if ((cam[e] >> kk) & 1ull) cc = cc + P.c_pre;
-          if (post) cc = cc + P.c_post;
-          contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
-          S = S + fabs(h - h0);
-          double T1 = ((h - h0) > P.theta_tag) ? (prp * P.f_int) * (1.0 - z) : 0.0;
-          double T2 = ((h0 - h) > P.theta_tag) ? (prp * P.f_int) * (z + 0.5) : 0.0;
-          D.z[e] = z + P.rate_z * (T1 - T2);
-          double Ph = (cc > P.theta_p) ? P.gamma_p * (10.0 - h) : 0.0;
-          double Dh = (cc > P.theta_d) ? P.gamma_d * h : 0.0;
-          D.w[e] = h + P.rate_h * ((0.1 * (h0 - h) + Ph) - Dh);
-          C[e] = cc * P.decay_c;
-        } else {  // SK_STDP: traces evaluated in closed form at events only
-          if (pre || post) {
-            TM* AP = (TM*)D.apre;
-            TM* AQ = (TM*)D.apost;
-            double w = D.w[e];
-            double ap = (double)AP[e] * model_exp(-((double)(k - D.kpre[e]) * dt) / P.tau_pre);
-            double aq = (double)AQ[e] * model_exp(-((double)(k - D.kpost[e]) * dt) / P.tau_post);
-            if (pre) {
-              double wc = w < 0.0 ? 0.0 : (w > P.w_max ? P.w_max : w);
-              gv = gv + (TM)((double)((const TM*)D.weight)[e] * wc);
-              ap = ap + P.a_pre;
-              w = w + aq;
-              AP[e] = (TM)ap;
-              D.kpre[e] = (int32_t)k;
-            }
-            if (post) {
-              aq = aq + P.a_post;
-              w = w + ap;
-              AQ[e] = (TM)aq;
-              D.kpost[e] = (int32_t)k;
-            }
-            D.w[e] = w;
+      auto issue = [&](int c) {
+        const int si = c % kStages;
+        const int lo = c * RS, cnt = nrow - lo < RS ? nrow - lo : RS;
+        if (lane == 0) {
+          char* st = wbuf + si * ST::kBytes;
+          const size_t r0 = (size_t)(sb + lo) * 32;
+          mbar_expect_tx(&bar[si], (uint32_t)(cnt * rowb));
+          bulk_load(st, D.cvf + r0, cnt * 128, &bar[si]);
+          bulk_load(st + o_cm, cmg + r0, cnt * 256, &bar[si]);
+          bulk_load(st + o_g, (const TM*)D.g + r0, cnt * szm, &bar[si]);
+          if (calc) {
+            bulk_load(st + o_cam, camg + r0, cnt * 256, &bar[si]);
+            bulk_load(st + o_c, D.c + r0, cnt * 256, &bar[si]);
+            bulk_load(st + o_w, D.w + r0, cnt * 256, &bar[si]);
           }
-          contribute<TM>(GS, ES, rb, lane, cvf, gv, E);
+          if (stc) bulk_load(st + o_z, D.z + r0, cnt * 256, &bar[si]);
         }
-        G[e] = gv * dg;
+      };
+      if (nc > 0) {
+        fence_async_shared();  // lanes are done reading the stages about to be refilled
+        __syncwarp();
+        issue(0);
+      }
+      TM accg = 0, acce = 0;
+      for (int c = 0; c < nc; ++c) {
+        if (c + 1 < nc) {
+          fence_async_shared();
+          __syncwarp();
+          issue(c + 1);
+        }
+        const int si = c % kStages;
+        if (!mbar_wait(&bar[si], (phase >> si) & 1u)) failed = true;
+        phase ^= 1u << si;
+        if (__any_sync(0xffffffffu, failed)) {
+          failed = true;
+          break;
+        }
+        const char* st = wbuf + si * ST::kBytes;
+        const int lo = c * RS, cnt = nrow - lo < RS ? nrow - lo : RS;
+        for (int jj = 0; jj < cnt; ++jj) {
+          const int r = jj * 32 + lane;
+          const int32_t cvf = ((const int32_t*)st)[r];
+          if (cvf < 0) continue;
+          const uint32_t e = ((uint32_t)(sb + lo + jj) << 5) | (uint32_t)lane;
+          const bool pre = (((const uint64_t*)(st + o_cm))[r] >> kk) & 1ull;
+          TM gv = ((const TM*)(st + o_g))[r];
+          if (P.kind == SK_EXPSYN) {
+            if (pre) gv = gv + ((const TM*)D.weight)[e];
+            run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
+          } else if (P.kind == SK_GB) {
+            double cc = ((const double*)(st + o_c))[r];
+            if (pre) gv = gv + ((const TM*)D.weight)[e];
+            if ((((const uint64_t*)(st + o_cam))[r] >> kk) & 1ull) cc = cc + P.c_pre;
+            if (post) cc = cc + P.c_post;
+            run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
+            const double w = ((const double*)(st + o_w))[r];
+            const double Aw = (w * (1.0 - w)) * (P.w_star - w);
+            const double Pw = (cc > P.theta_p) ? P.gamma_p * (1.0 - w) : 0.0;
+            const double Dw = (cc > P.theta_d) ? P.gamma_d * w : 0.0;
+            D.w[e] = w + P.rate_w * ((Pw - Aw) - Dw);
+            D.c[e] = cc * P.decay_c;
+          } else if (P.kind == SK_STC) {
+            double cc = ((const double*)(st + o_c))[r];
+            const double h = ((const double*)(st + o_w))[r], z = ((const double*)(st + o_z))[r];
+            const double h0 = P.h0;
+            if (pre) gv = gv + (TM)((double)((const TM*)D.weight)[e] * ((h + h0 * z) / h0));
+            if ((((const uint64_t*)(st + o_cam))[r] >> kk) & 1ull) cc = cc + P.c_pre;
+            if (post) cc = cc + P.c_post;
+            run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
+            S = S + fabs(h - h0);
+            const double T1 = ((h - h0) > P.theta_tag) ? (prp * P.f_int) * (1.0 - z) : 0.0;
+            const double T2 = ((h0 - h) > P.theta_tag) ? (prp * P.f_int) * (z + 0.5) : 0.0;
+            D.z[e] = z + P.rate_z * (T1 - T2);
+            const double Ph = (cc > P.theta_p) ? P.gamma_p * (10.0 - h) : 0.0;
+            const double Dh = (cc > P.theta_d) ? P.gamma_d * h : 0.0;
+            D.w[e] = h + P.rate_h * ((0.1 * (h0 - h) + Ph) - Dh);
+            D.c[e] = cc * P.decay_c;
+          } else {  // SK_STDP: traces evaluated in closed form at events only
+            if (pre || post) {
+              TM* AP = (TM*)D.apre;
+              TM* AQ = (TM*)D.apost;
+              double w = D.w[e];
+              double ap = (double)AP[e] * model_exp(-((double)(k - D.kpre[e]) * dt) / P.tau_pre);
+              double aq = (double)AQ[e] * model_exp(-((double)(k - D.kpost[e]) * dt) / P.tau_post);
+              if (pre) {
+                const double wc = w < 0.0 ? 0.0 : (w > P.w_max ? P.w_max : w);
+                gv = gv + (TM)((double)((const TM*)D.weight)[e] * wc);
+                ap = ap + P.a_pre;
+                w = w + aq;
+                AP[e] = (TM)ap;
+                D.kpre[e] = (int32_t)k;
+              }
+              if (post) {
+                aq = aq + P.a_post;
+                w = w + ap;
+                AQ[e] = (TM)aq;
+                D.kpost[e] = (int32_t)k;
+              }
+              D.w[e] = w;
+            }
+            run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
+          }
+          G[e] = gv * dg;
+        }
       }
       if (s == A.stc_stream && has_stc) {
         const double qs = (S > P.theta_pro) ? P.p_max : 0.0;
         prp = prp + P.rate_p * (qs - prp);
       }
     }
+    if (__any_sync(0xffffffffu, failed)) {
+      failed = true;
+      break;
+    }
 
-    // ---- b. backward pass: assembly + elimination --------------------------
-    // rows n-1 .. 0, staged from HBM in chunks of kRowsBack rows
+    // ---- b. backward pass: assembly + elimination ----------------------------
+    // rows n-1 .. 0, staged from HBM in chunks of kRowsBack rows.  A row whose
+    // subtree carries no synapse has a constant eliminated diagonal: its
+    // reciprocal was computed once at build time (stored negated in the diagonal
+    // constant), so only its right-hand side is eliminated.
     double v0_old = 0.0, v0_new = 0.0;
     const double iinj = (k >= kon && k < koff) ? iinj_val : 0.0;
-    fence_async_global();  // this step's V and synaptic sums, written by plain stores
+    fence_async_global();  // this step's synaptic sums, written by plain stores
     __syncwarp();
     {
       const int nc = (rows + kRowsBack - 1) / kRowsBack;
@@ -356,6 +422,8 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
           }
         }
       };
+      fence_async_shared();
+      __syncwarp();
       for (int c = 0; c < kStages - 1 && c < nc; ++c) issue(c);
       double cf = 0.0, ca = 0.0, cx = 0.0;
       bool carry = false;
@@ -368,7 +436,10 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
         const int s = c % kStages;
         if (!mbar_wait(&bar[s], (phase >> s) & 1u)) failed = true;
         phase ^= 1u << s;
-        if (__any_sync(0xffffffffu, failed)) break;
+        if (__any_sync(0xffffffffu, failed)) {
+          failed = true;
+          break;
+        }
         const char* st = wbuf + s * ST::kBytes;
         const int hi = rows - kRowsBack * c, lo = hi > kRowsBack ? hi - kRowsBack : 0;
         for (int i = hi - 1; i >= lo; --i) {
@@ -378,12 +449,40 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
           const double v = ((const double*)(st + ST::oV))[r];
           const double cdt = ((const double*)(st + ST::oCDT))[r];
           const double dcv = ((const double*)(st + ST::oDC))[r];
+          int pi = i - 1;
+          if (TREE && i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
+          if (dcv < 0.0) {
+            // static row (never the soma): right-hand side only
+            double b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]);
+            if (TREE) {
+              for (int ch = ((const int16_t*)(st + ST::oOCH))[r]; ch >= 0;) {
+                const uint32_t ec = elem_of(rb, ch, lane);
+                b = fma(-AA[ec], XP[ec], b);
+                ch = A.och_next[ec];
+              }
+            }
+            if (carry) b = fma(-ca, cx, b);
+            const double ai = ((const double*)(st + ST::oA))[r];
+            const double rr = -dcv;
+            const double fi = ai * rr;
+            const double xi = b * rr;
+            F[e] = fi;
+            XP[e] = xi;
+            carry = !TREE || pi == i - 1;
+            cf = fi; ca = ai; cx = xi;
+            continue;
+          }
           const double gsv = (double)((const TM*)(st + ST::oGS))[r];
           const double esv = (double)((const TM*)(st + ST::oES))[r];
           double d, b;
           if (i == 0) {
             v0_old = v;
             if (hh) {
+              // per-soma constants are reloaded here rather than kept live
+              const double gna = __ldg(&A.hh_g[L]), gk = __ldg(&A.hh_g[A.n_lanes + L]),
+                           gl = __ldg(&A.hh_g[2 * A.n_lanes + L]);
+              const double ena = __ldg(&A.hh_e[L]), ek = __ldg(&A.hh_e[A.n_lanes + L]),
+                           el = __ldg(&A.hh_e[2 * A.n_lanes + L]);
               const double mmmh = ((gm_ * gm_) * gm_) * gh_;
               const double nnnn = ((gn_ * gn_) * gn_) * gn_;
               const double g1 = gna * mmmh;
@@ -400,9 +499,7 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
             d = dcv + gsv;
             b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + esv;
           }
-          int pi = i - 1;
           if (TREE) {
-            if (i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
             for (int ch = ((const int16_t*)(st + ST::oOCH))[r]; ch >= 0;) {
               const uint32_t ec = elem_of(rb, ch, lane);
               const double ac = AA[ec];
@@ -430,10 +527,14 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
         }
       }
     }
+    if (__any_sync(0xffffffffu, failed)) {
+      failed = true;
+      break;
+    }
     // ---- c. forward pass: back substitution, rows 0 .. n-1 ------------------
     fence_async_global();  // f and x' of this step, written by plain stores
     __syncwarp();
-    if (!__any_sync(0xffffffffu, failed)) {
+    {
       const int nc = (rows + kRowsFwd - 1) / kRowsFwd;
       auto issue = [&](int c) {
         const int s = c % kStages;
@@ -462,7 +563,10 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
         const int s = c % kStages;
         if (!mbar_wait(&bar[s], (phase >> s) & 1u)) failed = true;
         phase ^= 1u << s;
-        if (__any_sync(0xffffffffu, failed)) break;
+        if (__any_sync(0xffffffffu, failed)) {
+          failed = true;
+          break;
+        }
         const char* st = wbuf + s * ST::kBytes;
         const int lo = kRowsFwd * c, hi = lo + kRowsFwd < rows ? lo + kRowsFwd : rows;
         for (int i = lo > 1 ? lo : 1; i < hi; ++i) {
@@ -479,14 +583,10 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
           vprev = vi;
         }
       }
-      fence_async_shared();
-      __syncwarp();
     }
     if (__any_sync(0xffffffffu, failed)) {
-      // a stage never arrived: report and drain every copy still in flight
-      if (lane == 0) atomicOr(A.err_flags, 4);
-      for (int s = 0; s < kStages; ++s) mbar_wait(&bar[s], (phase >> s) & 1u);
-      return;
+      failed = true;
+      break;
     }
     if (n > 0) {
       for (int32_t q = pq0; q < pq1; ++q) {
@@ -523,6 +623,12 @@ __global__ void __launch_bounds__(128) epoch_kernel(const EpochArgs A) {
     }
     spiked_prev = A.replay ? (((rbits >> (k - A.k_begin)) & 1ull) != 0) : spk;
   }
+  if (failed) {
+    // a stage never arrived: report it and drain every copy still in flight
+    if (lane == 0) atomicOr(A.err_flags, 4);
+    for (int s = 0; s < kStages; ++s) mbar_wait(&bar[s], (phase >> s) & 1u);
+    return;
+  }
   if (n > 0) {
     A.spiked_prev[L] = spiked_prev ? 1 : 0;
     if (hh) {
@@ -556,23 +662,47 @@ int launch_init_gates_impl(const double* v, void* gate, int64_t n_lanes, const u
   return (int)cudaGetLastError();
 }
 
-template <class TM, bool TREE>
+template <class TM, bool TREE, int RB, int RF, int WPB, int MB>
 int launch_epoch_t(const EpochArgs& a, void* stream) {
-  const int threads = 128;
+  constexpr int warps_per_block = WPB;
+  const int threads = 32 * warps_per_block;
   const int64_t warps = a.n_groups;
   const int blocks = (int)((warps * 32 + threads - 1) / threads);
   if (blocks == 0) return 0;
-  const int smem = (threads / 32) * Stage<TM, TREE>::kWarpBytes;
-  cudaError_t e = cudaFuncSetAttribute(epoch_kernel<TM, TREE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int smem = warps_per_block * Stage<TM, TREE, RB, RF>::kWarpBytes;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
-  epoch_kernel<TM, TREE><<<blocks, threads, smem, (cudaStream_t)stream>>>(a);
+  static bool attr_set[64] = {false};  // per device; setting it twice is harmless
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    e = cudaFuncSetAttribute(epoch_kernel<TM, TREE, RB, RF, 32 * WPB, MB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  epoch_kernel<TM, TREE, RB, RF, 32 * WPB, MB><<<blocks, threads, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 
+// Kernel shapes: rows per TMA chunk (backward, forward), warps per block and
+// minimum resident blocks per SM (which sets the register budget).  Shape 0 is
+// the default; the autotuner times all of them on the model and keeps the
+// fastest.
+template <class TM, bool TREE>
+int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
+  switch (shape) {
+    case 1: return launch_epoch_t<TM, TREE, 2, 8, 4, 4>(a, stream);
+    case 2: return launch_epoch_t<TM, TREE, 3, 8, 2, 7>(a, stream);
+    case 3: return launch_epoch_t<TM, TREE, 2, 8, 2, 8>(a, stream);
+    case 4: return launch_epoch_t<TM, TREE, 4, 12, 1, 12>(a, stream);
+    default: return launch_epoch_t<TM, TREE, 4, 12, 4, 3>(a, stream);
+  }
+}
+
 template <class TM>
-int launch_epoch_impl(const EpochArgs& a, bool tree, void* stream) {
-  return tree ? launch_epoch_t<TM, true>(a, stream) : launch_epoch_t<TM, false>(a, stream);
+int launch_epoch_impl(const EpochArgs& a, bool tree, int shape, void* stream) {
+  return tree ? launch_epoch_shape<TM, true>(a, shape, stream)
+              : launch_epoch_shape<TM, false>(a, shape, stream);
 }
 
 }  // namespace pa

@@ -31,7 +31,7 @@ int64_t noalloc_max_padded_cv() { return kNoallocMaxPaddedCV; }
 
 // Returns 0 or a cudaError_t value; -1 if the model is larger than the array.
 int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, bool mixed,
-                         void* stream) {
+                         int shape, void* stream) {
   if (n_padded_cv > kNoallocMaxPaddedCV) return -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -48,8 +48,8 @@ int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, boo
   EpochArgs b = a;
   b.f = g_scratch_dev_ptr[dev];
   b.xp = g_scratch_dev_ptr[dev] + n_padded_cv;
-  return mixed ? launch_epoch_impl<float>(b, tree, stream)
-               : launch_epoch_impl<double>(b, tree, stream);
+  return mixed ? launch_epoch_impl<float>(b, tree, shape, stream)
+               : launch_epoch_impl<double>(b, tree, shape, stream);
 }
 
 }  // namespace pa

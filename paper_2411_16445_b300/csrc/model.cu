@@ -123,6 +123,9 @@ struct pa_model {
   std::vector<int64_t> mask_elems;
   // kernel statistics
   bool time_kernels = false;
+  int64_t n_static_cv = 0;
+  int shape = 0;
+  float tune_ms[pa::kNumShapes] = {0};
   int64_t n_epoch_launches = 0, n_kernel_launches = 0;
   double epoch_ms = 0, event_ms = 0;
   std::vector<cudaEvent_t> ev_pool;                       // recycled events
@@ -142,6 +145,70 @@ std::vector<float> to_f32(const std::vector<T>& v) {
   std::vector<float> o(v.size());
   for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
   return o;
+}
+
+// Times every epoch-kernel shape on the model's first epoch and keeps the fastest.
+// The whole device arena is copied aside first and restored after each trial,
+// so the trials leave no trace in the model's state.
+int autotune(pa_model* M) {
+  using namespace pa;
+  char* snap = nullptr;
+  if (cudaMalloc((void**)&snap, M->dbytes) != cudaSuccess) {
+    cudaGetLastError();
+    return PA_OK;  // no room for a snapshot: keep the default shape
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = PA_OK;
+  float best = 1e30f;
+  int best_shape = M->shape;
+  auto fail = [&](cudaError_t e) {
+    rc = set_err(PA_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // the first epoch's Poisson drive, so the trials see realistic events
+  if (e == cudaSuccess) {
+    M->pa_args.k0 = 0;
+    e = (cudaError_t)launch_poisson(M->pa_args, 0, M->E, M->stream);
+    M->poisson_epoch_done = 0;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(snap, M->dmem, M->dbytes, cudaMemcpyDeviceToDevice, M->stream);
+  EpochArgs A = M->ea;
+  A.k_begin = 0;
+  A.k_end = M->E;
+  A.k0 = 0;
+  A.slot = 0;
+  A.probe_sample0 = 0;
+  A.replay = 0;
+  for (int s = 0; s < kNumShapes && e == cudaSuccess; ++s) {
+    float best_s = 1e30f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, M->stream);
+      if (e == cudaSuccess)
+        e = (cudaError_t)(M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, s, M->stream)
+                                                   : launch_epoch_fp64(A, M->tree, s, M->stream));
+      if (e == cudaSuccess) e = cudaEventRecord(e1, M->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best_s) best_s = ms;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(M->dmem, snap, M->dbytes, cudaMemcpyDeviceToDevice, M->stream);
+    }
+    M->tune_ms[s] = best_s;
+    if (best_s < best) {
+      best = best_s;
+      best_shape = s;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+  if (e != cudaSuccess) fail(e);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(snap);
+  if (rc == PA_OK) M->shape = best_shape;
+  return rc;
 }
 
 int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morphs,
@@ -212,6 +279,11 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   M->n_conn = n_conn;
   M->elem_bytes_m = mixed ? 4 : 8;
   M->time_kernels = (opt->flags & PA_FLAG_TIME_KERNELS) != 0;
+  {
+    const int forced = ((opt->flags >> 8) & 0xF) - 1;
+    if (forced >= pa::kNumShapes) return set_err(PA_ERR_ARG, "shape %d out of range", forced);
+    if (forced >= 0) M->shape = forced;
+  }
   CUDA_TRY(cudaSetDevice(M->device));
 
   int n_streams = 0, stc_stream = -1;
@@ -481,9 +553,13 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     s_weight[s].assign(ne, 0.0);
     s_w[s].assign(ne, 0.0);
   }
-  // first-on-CV flags follow the canonical (mechanism, CV, connection) order
+  // Per-CV synaptic sums are accumulated in registers over each run of same-CV
+  // synapses of a stream (canonical order: mechanism, CV, connection).  Flags:
+  // bit 0 "first on this CV over all streams" (the run starts from 0), bit 1 "run
+  // starts", bit 2 "run ends" (store the sums).  cvf = (cv << 3) | flags.
   for (int64_t L = 0; L < n_cells; ++L) {
-    std::vector<char> touched(M->cell_ncv[lane_gid[L]], 0);
+    const int ncell = M->cell_ncv[lane_gid[L]];
+    std::vector<char> touched(ncell, 0);
     const int64_t g = L / kLanes, l = L % kLanes;
     for (int s = 0; s < n_streams; ++s) {
       const int m = stream_mech[s];
@@ -492,7 +568,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       for (size_t j = 0; j < v.size(); ++j) {
         const int64_t e = ((int64_t)s_sbase[s][g] + (int64_t)j) * kLanes + l;
         const int cv = v[j].cv;
-        s_cvf[s][e] = (cv << 1) | (touched[cv] ? 0 : 1);
+        const bool start = j == 0 || v[j - 1].cv != cv;
+        const bool end = j + 1 == v.size() || v[j + 1].cv != cv;
+        const bool first = !touched[cv];
+        s_cvf[s][e] = (cv << 3) | (first ? 1 : 0) | (start ? 2 : 0) | (end ? 4 : 0);
         touched[cv] = 1;
         s_weight[s][e] = conns[v[j].conn].weight;
         if (M->sp[s].kind == SK_GB) s_w[s][e] = p[12];
@@ -504,6 +583,35 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         M->conn_stream[v[j].conn] = s;
         M->conn_elem[v[j].conn] = e;
       }
+    }
+    // Static rows: a row whose subtree carries no synapse (and is not the soma)
+    // has the same eliminated diagonal in every step, so its reciprocal is computed
+    // here once, with the kernel's own operations in the kernel's order (children
+    // above the first child in descending order, then the first child), and stored
+    // negated in place of the diagonal constant (which is positive for every row).
+    const pa_morphology& gm = morphs[cells[lane_gid[L]].morph];
+    std::vector<char> dyn(ncell, 0);
+    for (int i = 0; i < ncell; ++i) dyn[i] = touched[i] || i == 0;
+    for (int i = ncell - 1; i >= 1; --i)
+      if (dyn[i]) dyn[gm.parent[i]] = 1;
+    std::vector<double> fst(ncell, 0.0);
+    std::vector<std::vector<int>> kids(ncell);
+    for (int i = 1; i < ncell; ++i) kids[gm.parent[i]].push_back(i);
+    for (int i = ncell - 1; i >= 1; --i) {
+      if (dyn[i]) continue;
+      const int64_t e = elem(L, i);
+      double d = h_dc[e] + 0.0;
+      const auto& ks = kids[i];
+      for (int q = (int)ks.size() - 1; q >= 0; --q) {
+        const int c = ks[q];
+        if (c == i + 1) continue;
+        d = std::fma(-fst[c], h_a[elem(L, c)], d);
+      }
+      if (i + 1 < ncell && gm.parent[i + 1] == i) d = std::fma(-fst[i + 1], h_a[elem(L, i + 1)], d);
+      const double r = 1.0 / d;
+      fst[i] = h_a[e] * r;
+      h_dc[e] = -r;
+      M->n_static_cv++;
     }
   }
   per_lane.clear();
@@ -799,6 +907,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       return set_err(PA_ERR_CUDA, "gate initialisation failed: %s",
                      cudaGetErrorString(e2 != cudaSuccess ? e2 : (cudaError_t)rc));
   }
+  if ((opt->flags & PA_FLAG_AUTOTUNE) && ((opt->flags >> 8) & 0xF) == 0) {
+    int rc = autotune(M);
+    if (rc) return rc;
+  }
   guard.ok = true;
   *out = M;
   return PA_OK;
@@ -906,13 +1018,13 @@ int run_window(pa_model* M, int64_t k_begin, int64_t k_end, bool static_scratch 
   int rc = 0;
   if (static_scratch) {
     rc = launch_epoch_noalloc(A, M->total_rows * kLanes, M->tree, M->precision == PA_MIXED,
-                              M->stream);
+                              M->shape, M->stream);
     if (rc == -1)
       return set_err(PA_ERR_ARG, "model has %lld padded CVs; pa_advance_noalloc holds at most %lld",
                      (long long)(M->total_rows * kLanes), (long long)noalloc_max_padded_cv());
   } else {
-    rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->stream)
-                                  : launch_epoch_fp64(A, M->tree, M->stream);
+    rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->shape, M->stream)
+                                  : launch_epoch_fp64(A, M->tree, M->shape, M->stream);
   }
   if (rc) return set_err(PA_ERR_CUDA, "epoch launch: %s", cudaGetErrorString((cudaError_t)rc));
   if (timed) CUDA_TRY(cudaEventRecord(tm.c, M->stream));
@@ -1205,7 +1317,17 @@ int pa_model_info(const pa_model* M, pa_info* info) {
   info->precision = M->precision;
   info->tree = M->tree ? 1 : 0;
   info->n_streams = M->n_streams;
+  info->shape = M->shape;
+  info->reserved = 0;
   info->device_bytes = (int64_t)M->dbytes;
+  info->n_static_cv = M->n_static_cv;
+  return PA_OK;
+}
+
+int pa_get_tuning(const pa_model* M, int32_t* shape, double* trial_ms, int32_t cap) {
+  if (!M) return set_err(PA_ERR_ARG, "model is NULL");
+  if (shape) *shape = M->shape;
+  for (int32_t s = 0; trial_ms && s < cap && s < pa::kNumShapes; ++s) trial_ms[s] = M->tune_ms[s];
   return PA_OK;
 }
 

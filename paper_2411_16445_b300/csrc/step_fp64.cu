@@ -4,8 +4,8 @@
 #include "epoch_kernel.cuh"
 
 namespace pa {
-int launch_epoch_fp64(const EpochArgs& a, bool tree, void* stream) {
-  return launch_epoch_impl<double>(a, tree, stream);
+int launch_epoch_fp64(const EpochArgs& a, bool tree, int shape, void* stream) {
+  return launch_epoch_impl<double>(a, tree, shape, stream);
 }
 int launch_init_gates_fp64(const double* v, void* gate, int64_t n_lanes,
                            const uint8_t* is_hh, void* stream) {

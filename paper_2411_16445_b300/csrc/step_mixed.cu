@@ -5,8 +5,8 @@
 #include "epoch_kernel.cuh"
 
 namespace pa {
-int launch_epoch_mixed(const EpochArgs& a, bool tree, void* stream) {
-  return launch_epoch_impl<float>(a, tree, stream);
+int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream) {
+  return launch_epoch_impl<float>(a, tree, shape, stream);
 }
 int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes,
                            const uint8_t* is_hh, void* stream) {

@@ -24,7 +24,8 @@ ERRORS = {-1: "PA_ERR_ARG", -2: "PA_ERR_OOM", -3: "PA_ERR_CUDA", -4: "PA_ERR_TIM
 
 EXPORTED = ("pa_build_model", "pa_advance", "pa_advance_noalloc", "pa_sync", "pa_read_probes", "pa_read_spikes",
             "pa_read_weights", "pa_read_state", "pa_set_replay", "pa_model_info",
-            "pa_get_kernel_stats", "pa_reset_kernel_stats", "pa_free_model", "pa_last_error")
+            "pa_get_kernel_stats", "pa_reset_kernel_stats", "pa_get_tuning", "pa_free_model",
+            "pa_last_error")
 
 
 class PaError(RuntimeError):
@@ -56,13 +57,21 @@ class KernelStats(C.Structure):
 
 
 FLAG_TIME_KERNELS = 1
+FLAG_AUTOTUNE = 2
+N_SHAPES = 5
+
+
+def flag_shape(s: int) -> int:
+    """pa_options.flags value forcing epoch-kernel shape s."""
+    return ((s + 1) & 0xF) << 8
 
 
 class Info(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_cv", C.c_int64), ("n_conn", C.c_int64),
                 ("n_groups", C.c_int64), ("n_padded_cv", C.c_int64), ("step", C.c_int64),
                 ("epoch_steps", C.c_int32), ("precision", C.c_int32), ("tree", C.c_int32),
-                ("n_streams", C.c_int32), ("device_bytes", C.c_int64)]
+                ("n_streams", C.c_int32), ("shape", C.c_int32), ("reserved", C.c_int32),
+                ("device_bytes", C.c_int64), ("n_static_cv", C.c_int64)]
 
 
 CELL_DTYPE = np.dtype([("morph", "<i4"), ("soma_mech", "<i4"), ("dend_mech", "<i4"),
@@ -97,6 +106,7 @@ def lib():
         L.pa_model_info.argtypes = [P, C.POINTER(Info)]
         L.pa_get_kernel_stats.argtypes = [P, C.POINTER(KernelStats)]
         L.pa_reset_kernel_stats.argtypes = [P]
+        L.pa_get_tuning.argtypes = [P, C.POINTER(C.c_int32), P, C.c_int32]
         L.pa_free_model.argtypes = [P]
         L.pa_free_model.restype = None
         L.pa_last_error.restype = C.c_char_p
@@ -243,6 +253,13 @@ class Model:
         ks = KernelStats()
         _check(lib().pa_get_kernel_stats(self._h, C.byref(ks)))
         return ks
+
+    def tuning(self):
+        """(shape in use, trial time in ms of each shape; zeros unless autotuned)"""
+        s = C.c_int32()
+        ms = np.zeros(N_SHAPES)
+        _check(lib().pa_get_tuning(self._h, C.byref(s), _ptr(ms), N_SHAPES))
+        return int(s.value), ms
 
     def reset_kernel_stats(self):
         _check(lib().pa_reset_kernel_stats(self._h))

@@ -392,3 +392,51 @@ def large_stdp(n_cells=100_000, fan_in=100, dt=0.025, seed=None, n_dend=(50, 500
     b.connect(src[order], dst[order], cv[order], stdp, w_syn, delay=steps[order] * dt)
     b.connect(SRC_POISSON, cells, 0, drive, w_drive, rate=drive_hz)
     return b.build()
+
+
+def serving_job(n_cells: int, long_dendrite: bool, dend_len_um: float, dend_diam_um: float,
+                seed: int, dt: float = 0.2, fan_in: int = 50, w_syn: float = 1e-3,
+                w_bg: float = 3e-3, bg_rate: float = 20.0) -> Network:
+    """One serving job: n_cells HH ball-and-stick cells (a 64-CV dendrite like the
+    single-neuron workload, or an 8-CV one like the recurrent network) with the
+    job's dendritic length and diameter (a parameter sweep), random recurrent
+    connectivity of fan-in min(fan_in, n_cells - 1) with 3 ms delays and pair-STDP
+    synapses, and Poisson background on a somatic synapse."""
+    b = _Builder(dt, seed, "serving_job")
+    rng = np.random.default_rng(seed)
+    hh = b.mech(HH, hh_params())
+    pas = b.mech(PAS, pas_params(3e-5, -54.4))
+    bg = b.mech(EXPSYN, expsyn_params(5.0, 0.0))
+    stdp = b.mech(STDP, stdp_params())
+    nd = 64 if long_dendrite else 8
+    m = b.morph(ball_and_stick(20.0, dend_len_um, dend_diam_um, nd))
+    cells = b.cells_add(n_cells, m, hh, pas)
+    k = min(fan_in, n_cells - 1)
+    if k > 0:
+        src = rng.integers(0, n_cells - 1, size=(n_cells, k))
+        src = (src + (src >= cells[:, None])).reshape(-1)
+        dst = np.repeat(cells, k)
+        b.connect(src, dst, rng.integers(1, nd + 1, size=dst.shape[0]), stdp, w_syn, delay=3.0)
+    b.connect(SRC_POISSON, cells, 0, bg, w_bg, rate=bg_rate)
+    return b.build()
+
+
+def serving_trace(n_jobs: int = 2000, rate_hz: float = 20.0, seed: Optional[int] = None,
+                  sizes=(1, 20000), durations_s=(0.1, 10.0), dt: float = 0.2):
+    """Poisson arrivals of serving jobs: sizes log-uniform in `sizes` cells, durations
+    log-uniform in `durations_s` simulated seconds, 64-CV and 8-CV morphologies 50/50,
+    dendrite length U(100, 800) um and diameter U(0.5, 2) um per job."""
+    rng = np.random.default_rng(config_seed("serving") if seed is None else seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_jobs))
+    lo, hi = np.log(sizes[0]), np.log(sizes[1])
+    n = np.floor(np.exp(rng.uniform(lo, np.log(sizes[1] + 1), size=n_jobs))).astype(int)
+    n = np.clip(n, sizes[0], sizes[1])
+    dur = np.exp(rng.uniform(np.log(durations_s[0]), np.log(durations_s[1]), size=n_jobs))
+    long_d = rng.random(n_jobs) < 0.5
+    L = rng.uniform(100.0, 800.0, size=n_jobs)
+    d = rng.uniform(0.5, 2.0, size=n_jobs)
+    seeds = rng.integers(0, 2**62, size=n_jobs)
+    return [dict(job_id=i, arrival_s=float(t[i]), n_cells=int(n[i]), long_dendrite=bool(long_d[i]),
+                 dend_len_um=float(L[i]), dend_diam_um=float(d[i]),
+                 duration_ms=float(round(dur[i] * 1000.0 / dt) * dt), seed=int(seeds[i]), dt=dt)
+            for i in range(n_jobs)]

@@ -230,3 +230,25 @@ def test_errors_are_reported_not_raised_on_device():
     with pytest.raises(E.PaError) as ei:
         m2.sync()
     assert ei.value.code == -5
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_every_kernel_shape_gives_identical_results(precision):
+    """The compiled kernel shapes (TMA chunk sizes, warps per block, register budget)
+    change scheduling only: every shape gives bit-identical results, and an
+    autotuned model equals an untuned one."""
+    net = tiny_tree_net(n_cells=70)
+    ref = None
+    for s in range(E.N_SHAPES):
+        m = E.Model(net, precision=precision, flags=E.flag_shape(s))
+        assert m.info().shape == s
+        m.advance(800 * net.dt)
+        v, sp = m.read_state(E.FIELD_V), m.read_spikes()[1]
+        if ref is None:
+            ref = (v, sp)
+        assert np.array_equal(v, ref[0]) and np.array_equal(sp, ref[1])
+    m = E.Model(net, precision=precision, flags=E.FLAG_AUTOTUNE)
+    shape, ms = m.tuning()
+    assert 0 <= shape < E.N_SHAPES and np.all(ms > 0) and ms[shape] == ms.min()
+    m.advance(800 * net.dt)
+    assert np.array_equal(m.read_state(E.FIELD_V), ref[0])
