@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    p.add_argument("--shape", type=int, default=-1,
+                   help="force this epoch-kernel shape instead of autotuning")
     return p.parse_args()
 
 
@@ -65,38 +67,45 @@ def workload(n_cells, n_shapes, seed_offset=0):
 def net_stats(net):
     ncv = net.cell_ncv()
     kinds = net.mech_kind[net.conn_mech]
+    # rows that carry a first child (i + 1 with parent i) and non-first children
+    first = np.array([int(np.sum(m.parent[1:] == np.arange(m.n_cv - 1))) for m in net.morphs])
+    other = np.array([m.n_cv - 1 for m in net.morphs]) - first
+    per_cell = np.bincount(net.cell_morph, minlength=len(net.morphs))
     return {
         "n_cells": int(net.n_cells),
         "n_cv": int(ncv.sum()),
         "n_syn": int(net.n_conn),
         "n_stdp": int(np.sum(kinds == 13)),
         "n_expsyn": int(np.sum(kinds == 10)),
+        "n_first": int(np.dot(per_cell, first)),
+        "n_other": int(np.dot(per_cell, other)),
         "tree": any(not m.is_chain() for m in net.morphs),
     }
 
 
-def per_cu_model(st, mixed, static_frac):
+def per_cu_model(st, mixed):
     """Algorithmic work of one compartment-update, amortising soma and synapse work.
     Bytes: state that must stream every step (V read+write, four FP64 cable
     coefficients: C/dt, diagonal, leak E term, axial coupling; 2-byte parent
     index on trees) plus per-synapse state read+write (conductance; the STDP
     traces are touched only at events), CV index and event word.
-    FP64 ops in FMA-equivalents: a row with a time-varying diagonal costs the b
-    assembly, two synaptic sums, two child-contribution FMAs, the f and x'
-    products, the back-substitution FMA and one reciprocal at its measured issue
-    cost; a static row (constant diagonal, reciprocal precomputed) costs the b
-    assembly, one child FMA, the x' product and the back-substitution FMA.  Plus
-    HH per soma and, on the FP64 path, the synapse ops."""
+    FP64 ops (FMA, multiply or add; the FP64 pipe's work): per row the diagonal
+    and right-hand-side assembly (3: d + g_syn, C/dt V + E-term, + gE_syn), the
+    f and x' products (2) and the back substitution (1); two FMAs per child
+    eliminated into its parent (carried first child or other child); HH per
+    soma; on the FP64 path the synapse ops (decay, two sums, g E).  The row
+    reciprocal runs on the integer pipes (correctly rounded, about forty
+    integer ops) and is not counted."""
     ts = 4 if mixed else 8
     cv_bytes = 16 + 32 + (2 if st["tree"] else 0)
     stdp_bytes = 2 * ts + 4 + 8
     exp_bytes = 2 * ts + 4 + 8
     syn_bytes = st["n_stdp"] * stdp_bytes + st["n_expsyn"] * exp_bytes
     bytes_per_cu = cv_bytes + syn_bytes / st["n_cv"]
-    solve = (1 - static_frac) * (8 + RCP64_DFMA_EQ) + static_frac * 4
+    solve = 6 * st["n_cv"] + 2 * (st["n_first"] + st["n_other"])
     hh = 153 + 6 * RCP64_DFMA_EQ + 20                  # 9 model exps, 6 divisions, currents
-    syn = 0 if mixed else (st["n_stdp"] * 3 + st["n_expsyn"] * 3)
-    fp64_per_cu = solve + (hh * st["n_cells"] + syn) / st["n_cv"]
+    syn = 0 if mixed else 4 * (st["n_stdp"] + st["n_expsyn"])
+    fp64_per_cu = (solve + hh * st["n_cells"] + syn) / st["n_cv"]
     return bytes_per_cu, fp64_per_cu
 
 
@@ -148,14 +157,21 @@ def dist_setup():
     return ws, rank, local
 
 
-def time_gpu(net, precision, steps, warmup, device, stream_barrier):
+def model_flags(args):
+    from paper_2411_16445_b300 import engine as E
+    f = E.FLAG_TIME_KERNELS
+    f |= E.flag_shape(args.shape) if args.shape >= 0 else E.FLAG_AUTOTUNE
+    return f
+
+
+def time_gpu(net, precision, steps, warmup, device, stream_barrier, flags):
     import torch
     from paper_2411_16445_b300 import engine as E
     torch.cuda.set_device(device)
     stream = torch.cuda.current_stream(device)
     t0 = time.perf_counter()
     m = E.Model(net, precision=precision, device=device, stream=E.C.c_void_p(stream.cuda_stream),
-                flags=E.FLAG_TIME_KERNELS | E.FLAG_AUTOTUNE)
+                flags=flags)
     setup_s = time.perf_counter() - t0
     info = m.info()
     shape, trial_ms = m.tuning()
@@ -181,7 +197,6 @@ def time_gpu(net, precision, steps, warmup, device, stream_barrier):
     ks = m.kernel_stats()
     gid, _, _ = m.read_spikes()
     res = {"ms": ms, "epoch_steps": E_steps, "n_cv": info.n_cv, "setup_s": setup_s,
-           "static_frac": info.n_static_cv / max(info.n_cv, 1),
            "epoch_kernel_ms": ks.epoch_kernel_ms, "event_kernels_ms": ks.event_kernels_ms,
            "epoch_launches": ks.epoch_launches, "kernel_launches": ks.kernel_launches,
            "spikes": int(len(gid)), "device_bytes": info.device_bytes, "clocks": clocks,
@@ -293,7 +308,8 @@ def main():
     precs = {"mixed": 1, "fp64": 0}
     order = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
     for name in order:
-        runs[name] = time_gpu(net, precs[name], args.steps, args.warmup, device, barrier)
+        runs[name] = time_gpu(net, precs[name], args.steps, args.warmup, device, barrier,
+                              model_flags(args))
     head = order[0]
     r = runs[head]
     ms = r["ms"]
@@ -310,7 +326,7 @@ def main():
         return
 
     def roofline(run, mixed):
-        bpc, fpc = per_cu_model(st, mixed, run["static_frac"])
+        bpc, fpc = per_cu_model(st, mixed)
         cu_launch = run["n_cv"] * run["epoch_steps"]
         t_launch = run["epoch_kernel_ms"] / max(run["epoch_launches"], 1) * 1e-3
         clk = (run["clocks"] or {}).get("sm_mhz") or 2032.0
@@ -319,10 +335,11 @@ def main():
         ach_gbs = bpc * cu_launch / t_launch / 1e9
         return {"bound": "alu", "achieved": ach_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": ach_tflops / peak_tflops, "traffic": None,
-                "kernel": "epoch_kernel", "fp64_fma_eq_per_cu": fpc,
+                "kernel": "epoch_kernel", "fp64_ops_per_cu": fpc,
                 "peak_note": f"FP64: {N_SM} SMs x {DFMA_PER_SM_CLK} FMA/clk x 2 flop at the median "
-                             f"SM clock under load ({clk:.0f} MHz); a reciprocal costs "
-                             f"{RCP64_DFMA_EQ:.2f} FMA-equivalents (measured)",
+                             f"SM clock under load ({clk:.0f} MHz); HH divisions count "
+                             f"{RCP64_DFMA_EQ:.2f} FMA-equivalents (measured); the solver's "
+                             "row reciprocal runs on the integer pipes",
                 "hbm": {"achieved": ach_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                         "frac": ach_gbs / HBM_PEAK_GBS, "algorithmic_bytes_per_cu": bpc,
                         "peak_note": "measured copy bandwidth"}}

@@ -188,8 +188,7 @@ typedef struct {
   int32_t shape;            /* epoch-kernel shape in use */
   int32_t reserved;
   int64_t device_bytes;     /* device memory held by the model */
-  int64_t n_static_cv;      /* CVs whose subtree carries no synapse: their eliminated
-                               diagonal is constant, its reciprocal precomputed */
+  int64_t n_static_cv;      /* CVs whose subtree carries no synapse (a statistic) */
 } pa_info;
 
 /* Validates the descriptors, discretises every morphology (CV = cylinder:
@@ -271,6 +270,17 @@ int pa_get_kernel_stats(pa_model* m, pa_kernel_stats* out);
 int pa_reset_kernel_stats(pa_model* m);
 
 void pa_free_model(pa_model* m);
+
+/* Self-check of the engine's integer FP64 arithmetic on GPU `device` (no model
+ * needed; the paper has no counterpart).  The solver's row reciprocal 1/d is
+ * computed from integer operations and a single-precision seed, and the mixed
+ * path widens its FP32 synaptic sums to FP64 by moving bit fields; both must
+ * equal the GPU's IEEE operations bit for bit.  Checks every single-precision
+ * seed pattern (2^23 x 8 inputs), n_random random doubles and every float bit
+ * pattern.  out[0] = reciprocal mismatches, out[1] = widening mismatches,
+ * out[2] = cases checked, out[3] = bits of the first mismatching reciprocal
+ * input (0 if none).  Synchronous; allocates 32 bytes of device memory. */
+int pa_check_arith(int32_t device, uint64_t seed, int64_t n_random, int64_t* out);
 
 const char* pa_last_error(void);
 

@@ -29,6 +29,7 @@ UNITS = {
     "events.cu": [],
     "model.cu": NOFMA,
     "epoch_noalloc.cu": NOFMA,
+    "arith_check.cu": NOFMA,
 }
 
 

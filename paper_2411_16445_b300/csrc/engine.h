@@ -157,6 +157,12 @@ int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes, const 
 int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, bool mixed,
                          int shape, void* stream);
 int64_t noalloc_max_padded_cv();
+
+// Device self-check of int_arith.cuh (arith_check.cu): counts into d_out[0]
+// reciprocal mismatches, [1] float-widening mismatches, [2] cases checked,
+// [3] the first mismatching reciprocal input (bits).
+int launch_arith_check(uint64_t seed, int64_t n_random, unsigned long long* d_out, int n_sm,
+                       void* stream);
 int launch_poisson(const PoissonArgs& a, int64_t k_from, int64_t k_to, void* stream);
 int launch_route(const RouteArgs& a, int32_t max_spikes, void* stream);
 int launch_log_append(const int32_t* spk_count, const int32_t* gid, const int32_t* step,

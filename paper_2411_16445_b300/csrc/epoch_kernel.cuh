@@ -21,14 +21,16 @@
 //      detection; warp-ballot compaction of the spikes.
 //
 // Arithmetic: the FP64 instantiation is compiled without contraction so that
-// every operation and its order equal the plain definition (one IEEE
-// reciprocal per row; fused multiply-adds only where written as fma), and the
+// every operation and its order equal the plain definition (one correctly
+// rounded reciprocal per row, computed on the integer pipes by rcp_rn_pos;
+// fused multiply-adds only where written as fma), and the
 // model's exponential is the Cody-Waite + degree-13 Taylor function below.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "engine.h"
+#include "int_arith.cuh"
 
 namespace pa {
 
@@ -160,7 +162,8 @@ template <class TM, bool TREE, int kRowsBack, int kRowsFwd>
 struct Stage {
   // bytes per row (32 lanes) of each staged array
   static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(TM), kI = TREE ? 32 * 2 : 0;
-  // backward pass: V, C/dt, diagonal, leak E term, axial coupling, synaptic sums, tree rows
+  // backward pass: V, C/dt, diagonal, leak E term, axial coupling, synaptic sums,
+  // tree rows (parent, first other child)
   static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oDC = oCDT + kRowsBack * kD,
                        oEM = oDC + kRowsBack * kD, oA = oEM + kRowsBack * kD,
                        oGS = oA + kRowsBack * kD, oES = oGS + kRowsBack * kM,
@@ -391,10 +394,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
     }
 
     // ---- b. backward pass: assembly + elimination ----------------------------
-    // rows n-1 .. 0, staged from HBM in chunks of kRowsBack rows.  A row whose
-    // subtree carries no synapse has a constant eliminated diagonal: its
-    // reciprocal was computed once at build time (stored negated in the diagonal
-    // constant), so only its right-hand side is eliminated.
+    // rows n-1 .. 0, staged from HBM in chunks of kRowsBack rows.  Every row
+    // takes the same operations (the lanes of a warp are different cells, so a
+    // per-row shortcut would run both paths).
     double v0_old = 0.0, v0_new = 0.0;
     const double iinj = (k >= kon && k < koff) ? iinj_val : 0.0;
     fence_async_global();  // this step's synaptic sums, written by plain stores
@@ -451,29 +453,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           const double dcv = ((const double*)(st + ST::oDC))[r];
           int pi = i - 1;
           if (TREE && i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
-          if (dcv < 0.0) {
-            // static row (never the soma): right-hand side only
-            double b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]);
-            if (TREE) {
-              for (int ch = ((const int16_t*)(st + ST::oOCH))[r]; ch >= 0;) {
-                const uint32_t ec = elem_of(rb, ch, lane);
-                b = fma(-AA[ec], XP[ec], b);
-                ch = A.och_next[ec];
-              }
-            }
-            if (carry) b = fma(-ca, cx, b);
-            const double ai = ((const double*)(st + ST::oA))[r];
-            const double rr = -dcv;
-            const double fi = ai * rr;
-            const double xi = b * rr;
-            F[e] = fi;
-            XP[e] = xi;
-            carry = !TREE || pi == i - 1;
-            cf = fi; ca = ai; cx = xi;
-            continue;
-          }
-          const double gsv = (double)((const TM*)(st + ST::oGS))[r];
-          const double esv = (double)((const TM*)(st + ST::oES))[r];
+          const double gsv = widen_f32(((const TM*)(st + ST::oGS))[r]);
+          const double esv = widen_f32(((const TM*)(st + ST::oES))[r]);
           double d, b;
           if (i == 0) {
             v0_old = v;
@@ -500,6 +481,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
             b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + esv;
           }
           if (TREE) {
+            // other children, highest index first, from the scratch arrays
             for (int ch = ((const int16_t*)(st + ST::oOCH))[r]; ch >= 0;) {
               const uint32_t ec = elem_of(rb, ch, lane);
               const double ac = AA[ec];
@@ -514,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           }
           if (i > 0) {
             const double ai = ((const double*)(st + ST::oA))[r];
-            const double rr = 1.0 / d;
+            const double rr = rcp_rn_pos(d);
             const double fi = ai * rr;
             const double xi = b * rr;
             F[e] = fi;
@@ -522,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
             carry = !TREE || pi == i - 1;
             cf = fi; ca = ai; cx = xi;
           } else {
-            v0_new = b * (1.0 / d);
+            v0_new = b * rcp_rn_pos(d);
           }
         }
       }
@@ -691,11 +673,11 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 template <class TM, bool TREE>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   switch (shape) {
-    case 1: return launch_epoch_t<TM, TREE, 2, 8, 4, 4>(a, stream);
-    case 2: return launch_epoch_t<TM, TREE, 3, 8, 2, 7>(a, stream);
-    case 3: return launch_epoch_t<TM, TREE, 2, 8, 2, 8>(a, stream);
-    case 4: return launch_epoch_t<TM, TREE, 4, 12, 1, 12>(a, stream);
-    default: return launch_epoch_t<TM, TREE, 4, 12, 4, 3>(a, stream);
+    case 1: return launch_epoch_t<TM, TREE, 3, 9, 4, 4>(a, stream);   // 16 warps per SM
+    case 2: return launch_epoch_t<TM, TREE, 6, 16, 2, 4>(a, stream);  // 8 warps, long chunks
+    case 3: return launch_epoch_t<TM, TREE, 4, 12, 2, 6>(a, stream);  // 2-warp blocks
+    case 4: return launch_epoch_t<TM, TREE, 4, 12, 1, 12>(a, stream); // 1-warp blocks
+    default: return launch_epoch_t<TM, TREE, 4, 12, 4, 3>(a, stream); // 12 warps per SM
   }
 }
 

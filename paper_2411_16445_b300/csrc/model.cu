@@ -584,35 +584,15 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         M->conn_elem[v[j].conn] = e;
       }
     }
-    // Static rows: a row whose subtree carries no synapse (and is not the soma)
-    // has the same eliminated diagonal in every step, so its reciprocal is computed
-    // here once, with the kernel's own operations in the kernel's order (children
-    // above the first child in descending order, then the first child), and stored
-    // negated in place of the diagonal constant (which is positive for every row).
+    // Rows whose subtree carries no synapse (statistic only: their eliminated
+    // diagonal is constant, but a shortcut for them would split each warp's
+    // rows into two paths, since lanes are different cells).
     const pa_morphology& gm = morphs[cells[lane_gid[L]].morph];
     std::vector<char> dyn(ncell, 0);
     for (int i = 0; i < ncell; ++i) dyn[i] = touched[i] || i == 0;
     for (int i = ncell - 1; i >= 1; --i)
       if (dyn[i]) dyn[gm.parent[i]] = 1;
-    std::vector<double> fst(ncell, 0.0);
-    std::vector<std::vector<int>> kids(ncell);
-    for (int i = 1; i < ncell; ++i) kids[gm.parent[i]].push_back(i);
-    for (int i = ncell - 1; i >= 1; --i) {
-      if (dyn[i]) continue;
-      const int64_t e = elem(L, i);
-      double d = h_dc[e] + 0.0;
-      const auto& ks = kids[i];
-      for (int q = (int)ks.size() - 1; q >= 0; --q) {
-        const int c = ks[q];
-        if (c == i + 1) continue;
-        d = std::fma(-fst[c], h_a[elem(L, c)], d);
-      }
-      if (i + 1 < ncell && gm.parent[i + 1] == i) d = std::fma(-fst[i + 1], h_a[elem(L, i + 1)], d);
-      const double r = 1.0 / d;
-      fst[i] = h_a[e] * r;
-      h_dc[e] = -r;
-      M->n_static_cv++;
-    }
+    for (int i = 1; i < ncell; ++i) M->n_static_cv += dyn[i] ? 0 : 1;
   }
   per_lane.clear();
   per_lane.shrink_to_fit();
@@ -754,7 +734,9 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   putv(o_V, h_V);
   putv(o_cdt, h_cdt); putv(o_dc, h_dc); putv(o_em, h_em); putv(o_a, h_a);
   putv(o_hhg, h_hhg); putv(o_hhe, h_hhe);
-  if (M->tree) { putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn); }
+  if (M->tree) {
+    putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn);
+  }
   putv(o_ishh, h_is_hh);
   putv(o_iinj, h_iinj); putv(o_kon, h_kon); putv(o_koff, h_koff); putv(o_th, h_thresh);
   putv(o_hasstc, h_has_stc);
@@ -1316,9 +1298,9 @@ int pa_model_info(const pa_model* M, pa_info* info) {
   info->epoch_steps = M->E;
   info->precision = M->precision;
   info->tree = M->tree ? 1 : 0;
+  info->reserved = 0;
   info->n_streams = M->n_streams;
   info->shape = M->shape;
-  info->reserved = 0;
   info->device_bytes = (int64_t)M->dbytes;
   info->n_static_cv = M->n_static_cv;
   return PA_OK;
@@ -1350,6 +1332,24 @@ int pa_reset_kernel_stats(pa_model* M) {
   M->n_epoch_launches = M->n_kernel_launches = 0;
   M->epoch_ms = M->event_ms = 0;
   return rc;
+}
+
+int pa_check_arith(int32_t device, uint64_t seed, int64_t n_random, int64_t* out) {
+  if (!out || n_random < 0) return set_err(PA_ERR_ARG, "pa_check_arith: bad arguments");
+  CUDA_TRY(cudaSetDevice(device));
+  int n_sm = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device));
+  unsigned long long* d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, 4 * sizeof(unsigned long long)));
+  unsigned long long h[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemset(d, 0, sizeof h);
+  if (e == cudaSuccess) e = (cudaError_t)pa::launch_arith_check(seed, n_random, d, n_sm, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess)
+    return set_err(PA_ERR_CUDA, "pa_check_arith: %s", cudaGetErrorString(e));
+  for (int i = 0; i < 4; ++i) out[i] = (int64_t)h[i];
+  return PA_OK;
 }
 
 void pa_free_model(pa_model* M) {

@@ -25,7 +25,7 @@ ERRORS = {-1: "PA_ERR_ARG", -2: "PA_ERR_OOM", -3: "PA_ERR_CUDA", -4: "PA_ERR_TIM
 EXPORTED = ("pa_build_model", "pa_advance", "pa_advance_noalloc", "pa_sync", "pa_read_probes", "pa_read_spikes",
             "pa_read_weights", "pa_read_state", "pa_set_replay", "pa_model_info",
             "pa_get_kernel_stats", "pa_reset_kernel_stats", "pa_get_tuning", "pa_free_model",
-            "pa_last_error")
+            "pa_check_arith", "pa_last_error")
 
 
 class PaError(RuntimeError):
@@ -107,6 +107,7 @@ def lib():
         L.pa_get_kernel_stats.argtypes = [P, C.POINTER(KernelStats)]
         L.pa_reset_kernel_stats.argtypes = [P]
         L.pa_get_tuning.argtypes = [P, C.POINTER(C.c_int32), P, C.c_int32]
+        L.pa_check_arith.argtypes = [C.c_int32, C.c_uint64, C.c_int64, P]
         L.pa_free_model.argtypes = [P]
         L.pa_free_model.restype = None
         L.pa_last_error.restype = C.c_char_p
@@ -121,6 +122,15 @@ def _check(rc: int):
 
 def _ptr(a: np.ndarray):
     return C.c_void_p(a.ctypes.data) if a.size else C.c_void_p(0)
+
+
+def check_arith(device: int = 0, seed: int = 1, n_random: int = 1 << 30) -> dict:
+    """pa_check_arith: the integer FP64 reciprocal and float widening against the
+    GPU's IEEE operations; returns the mismatch counts."""
+    out = np.zeros(4, np.int64)
+    _check(lib().pa_check_arith(device, seed, n_random, _ptr(out)))
+    return {"rcp_mismatch": int(out[0]), "widen_mismatch": int(out[1]),
+            "checked": int(out[2]), "first_bad_rcp_bits": int(out[3])}
 
 
 def current_stream_handle(device: int = 0):

@@ -112,6 +112,39 @@ def edge_net(dt=0.1, seed=9):
     return b.build()
 
 
+def caterpillar_net(n_trunk=40, dt=0.025, seed=13):
+    """Cells whose depth-first numbering visits the whole trunk before any side
+    branch (soma, trunk 1..n_trunk, then side CVs n_trunk+1.. of trunk nodes
+    n_trunk..1), so that n_trunk - 1 side branches wait for their parents at
+    once in the elimination, plus cells of the same tree numbered
+    side-branch-first."""
+    b = W._Builder(dt, seed, "caterpillar")
+    hh = b.mech(W.HH, W.hh_params())
+    pas = b.mech(W.PAS, W.pas_params())
+    syn = b.mech(W.EXPSYN, W.expsyn_params(3.0, 0.0))
+    n = 1 + 2 * n_trunk
+    par = np.empty(n, np.int32)
+    par[0] = -1
+    par[1:n_trunk + 1] = np.arange(0, n_trunk)
+    par[n_trunk + 1:] = np.arange(n_trunk, 0, -1)          # side CV of trunk node t
+    diam = np.r_[18.0, np.full(n_trunk, 2.0), np.full(n_trunk, 0.8)]
+    region = np.r_[0, np.ones(n - 1, np.int32)].astype(np.int32)
+    m_deep = b.morph(W.Morphology(par, np.full(n, 12.0), diam, region))
+    # side-branch-first: trunk node t = 2t-1, its side CV 2t
+    par2 = np.empty(n, np.int32)
+    par2[0] = -1
+    for t in range(1, n_trunk + 1):
+        par2[2 * t - 1] = 0 if t == 1 else 2 * t - 3
+        par2[2 * t] = 2 * t - 1
+    diam2 = np.r_[18.0, np.tile([2.0, 0.8], n_trunk)]
+    m_flat = b.morph(W.Morphology(par2, np.full(n, 12.0), diam2, region))
+    b.cells_add(3, m_deep, hh, pas, istep=0.25)
+    b.cells_add(2, m_flat, hh, pas, istep=0.25)
+    rng = np.random.default_rng(seed)
+    b.connect(W.SRC_POISSON, np.arange(5), rng.integers(1, n, 5), syn, 4e-3, rate=60.0)
+    return b.build()
+
+
 def compare(a, b):
     a, b = np.asarray(a), np.asarray(b)
     assert a.shape == b.shape, (a.shape, b.shape)

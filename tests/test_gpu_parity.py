@@ -13,7 +13,7 @@ import oracle as O
 from paper_2411_16445_b300 import engine as E
 from paper_2411_16445_b300 import workloads as W
 
-from _nets import compare, edge_net, extract, map_spikes, tiny_tree_net
+from _nets import caterpillar_net, compare, edge_net, extract, map_spikes, tiny_tree_net
 
 pytestmark = pytest.mark.gpu
 
@@ -252,3 +252,13 @@ def test_every_kernel_shape_gives_identical_results(precision):
     assert 0 <= shape < E.N_SHAPES and np.all(ms > 0) and ms[shape] == ms.min()
     m.advance(800 * net.dt)
     assert np.array_equal(m.read_state(E.FIELD_V), ref[0])
+
+
+def test_trunk_first_and_side_first_numberings():
+    """The same caterpillar tree numbered trunk-first (39 side branches wait for
+    their parents at once in the elimination) and side-branch-first:
+    bit-identical to the oracle."""
+    net = caterpillar_net()
+    o, m = run_both(net, 2000, E.PA_FP64, chunks=2)
+    assert m.info().tree == 1
+    check_state(o, m, E.PA_FP64, exact=True)
