@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    p.add_argument("--serve-jobs", type=int, default=80,
+                   help="serving measurement on this many jobs of the trace (0: skip)")
     p.add_argument("--shape", type=int, default=-1,
                    help="force this epoch-kernel shape instead of autotuning")
     return p.parse_args()
@@ -254,6 +256,51 @@ def oracle_sample(n_cells, n_shapes, budget_s=15.0, max_steps=4000, warm=2):
             f"the same generator, {done} time steps, FP64, OpenMP over cells", "seconds": t}
 
 
+def serving_bench(n_jobs, device):
+    """Continuous-batching server on the first n_jobs of the seeded serving trace
+    (Poisson arrivals at 20 jobs/s, sizes log-uniform 1-20000 cells, durations
+    log-uniform 0.1-10 s, dt 0.2 ms), mixed precision, jobs admitted by HBM
+    budget and advanced together on their own streams.  Baseline: every job
+    alone on the plain FP64 path (build, run, read back), served one at a time
+    in arrival order; its latencies follow from the measured per-job times."""
+    import torch
+    from paper_2411_16445_b300 import engine as E
+    from paper_2411_16445_b300 import serving as S
+    from paper_2411_16445_b300 import workloads as W
+    trace = W.serving_trace()[:n_jobs]
+    srv = S.Server(hbm_budget_bytes=64 << 30, precision=E.PA_MIXED, device=device)
+    out = srv.run(trace)
+    cu = out["cu"]
+    span = trace[-1]["arrival_s"] - trace[0]["arrival_s"]
+    t_alone = []
+    for spec in trace:
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        S.run_alone(spec, precision=E.PA_FP64, device=device)
+        torch.cuda.synchronize(device)
+        t_alone.append(time.perf_counter() - t0)
+    free_at, lat = 0.0, []
+    for spec, t in zip(trace, t_alone):
+        start = max(spec["arrival_s"], free_at)
+        free_at = start + t
+        lat.append(free_at - spec["arrival_s"])
+    lat = np.array(lat)
+    first = trace[0]["arrival_s"]
+    return {"jobs": n_jobs, "precision": "mixed",
+            "sample": f"first {n_jobs} jobs of the 2000-job seeded trace "
+                      f"({span:.1f} s of arrivals at 20 jobs/s)",
+            "p50_s": out["p50_s"], "p99_s": out["p99_s"], "cu": cu,
+            "cu_per_s": out["cu_per_s"], "wall_s": out["wall_s"],
+            "offered_cu_per_s": cu / max(span, 1e-9),
+            "hbm_budget_bytes": 64 << 30,
+            "alone_fp64": {"p50_s": float(np.percentile(lat, 50)),
+                           "p99_s": float(np.percentile(lat, 99)),
+                           "cu_per_s": cu / max(free_at - first, 1e-9),
+                           "busy_s": float(sum(t_alone)),
+                           "note": "each job built, run and read back alone on the FP64 path; "
+                                   "jobs served one at a time in arrival order"}}
+
+
 def reference_arm(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -286,6 +333,8 @@ def reference_arm(args):
 
 def main():
     args = parse()
+    # the serving measurement drives many streams at once
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -373,6 +422,8 @@ def main():
         line["mixed_over_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
     if not args.no_e2e:
         line["e2e"] = time_e2e(net, precs[head], args.steps, device)
+    if args.serve_jobs > 0:
+        line["serving"] = serving_bench(args.serve_jobs, device)
     if not args.no_cpu and ws == 1:
         line["cpu_baseline"] = oracle_sample(min(args.cells, 2048), min(args.shapes, 2048))
     print(json.dumps(line), flush=True)

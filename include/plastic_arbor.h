@@ -170,12 +170,19 @@ typedef struct {
 /* pa_options.flags: force epoch-kernel shape s (0 <= s < PA_N_SHAPES) */
 #define PA_FLAG_SHAPE(s) ((((s) + 1) & 0xF) << 8)
 #define PA_N_SHAPES 5
+/* pa_options.flags: launch every kernel directly.  By default pa_advance runs
+ * each run of whole min-delay epochs as CUDA-graph launches (the epoch's Poisson,
+ * time-step, routing and record kernels captured once, replayed per epoch; 8
+ * epochs per launch where they fit).  Partial epochs, open-loop replay and
+ * PA_FLAG_TIME_KERNELS always launch directly.  Results are identical. */
+#define PA_FLAG_NO_GRAPHS 8
 
 typedef struct {
   int64_t epoch_launches;   /* epoch (time-step) kernel launches since the last reset */
   int64_t kernel_launches;  /* all kernel launches of the engine since the last reset */
   double epoch_kernel_ms;   /* device time of the epoch kernels (PA_FLAG_TIME_KERNELS) */
   double event_kernels_ms;  /* device time of the Poisson, routing and record kernels */
+  int64_t graph_launches;   /* CUDA-graph launches (each runs 1 or 8 whole epochs) */
 } pa_kernel_stats;
 
 typedef struct {

@@ -51,10 +51,22 @@ struct StreamDev {
   int64_t n_elem;
 };
 
+// Device-side position of a graph-launched model: the epoch a captured launch
+// sequence advances (every launch reads it; the sequence's last kernel moves it
+// on by one epoch), so that one captured CUDA graph serves every epoch.
+struct EpochClock {
+  int64_t k0;              // first step of the epoch
+  int64_t probe_sample0;   // probe sample index of step k0
+};
+
 struct EpochArgs {
-  // launch window: steps [k_begin, k_end) all inside epoch [k0, k0 + E)
+  // launch window: steps [k_begin, k_end) all inside epoch [k0, k0 + E); with
+  // `clock` set the window is the whole epoch the clock names instead
   int64_t k_begin, k_end, k0;
   int32_t slot;          // mask slot of this epoch
+  int32_t epoch_len;     // E
+  int32_t n_slots;
+  const EpochClock* clock;
   int32_t n_groups;
   double dt;
   // groups / lanes
@@ -114,7 +126,8 @@ struct EpochArgs {
 };
 
 struct PoissonArgs {
-  int64_t k0;                // epoch start
+  int64_t k0;                // epoch start (ignored with `clock` set)
+  const EpochClock* clock;   // graph launches: the epoch comes from here
   int32_t E;
   int32_t n_slots;
   uint64_t seed;
@@ -154,6 +167,18 @@ int launch_init_gates_fp64(const double* v, void* gate, int64_t n_lanes, const u
                            void* stream);
 int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
                             void* stream);
+// Graph launches: zero the mask slot of the clock's epoch in every mask array,
+// then advance the clock by one epoch (events.cu).
+struct SlotClear {
+  int32_t n;                       // mask arrays
+  int32_t n_slots, E;
+  int32_t probes;                  // advance probe_sample0 too
+  uint64_t* base[2 * kMaxStreams];
+  int64_t elems[2 * kMaxStreams];  // elements per slot
+};
+int launch_clear_and_tick(const SlotClear& c, EpochClock* clock, void* stream);
+int launch_set_clock(EpochClock* clock, int64_t k0, int64_t probe_sample0, void* stream);
+
 int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, bool mixed,
                          int shape, void* stream);
 int64_t noalloc_max_padded_cv();

@@ -253,8 +253,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
   const uint64_t rbits = (A.replay && n > 0) ? A.replay_bits[L] : 0ull;
   const int32_t pq0 = n > 0 ? A.probe_ptr[L] : 0, pq1 = n > 0 ? A.probe_ptr[L + 1] : 0;
 
-  for (int64_t k = A.k_begin; k < A.k_end && !failed; ++k) {
-    const int kk = (int)(k - A.k0);
+  // the launch window: from the arguments, or the whole epoch the clock names
+  int64_t k_begin = A.k_begin, k_end = A.k_end, k0 = A.k0, probe0 = A.probe_sample0;
+  int32_t slot = A.slot;
+  if (A.clock) {
+    k0 = A.clock->k0;
+    k_begin = k0;
+    k_end = k0 + A.epoch_len;
+    probe0 = A.clock->probe_sample0;
+    slot = (int32_t)((k0 / A.epoch_len) % A.n_slots);
+  }
+  for (int64_t k = k_begin; k < k_end && !failed; ++k) {
+    const int kk = (int)(k - k0);
     const bool post = spiked_prev;
     // ---- a. synapse streams, rows staged by TMA ------------------------------
     fence_async_global();  // last step's synapse state and V, written by plain stores
@@ -273,8 +283,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       const int o_cm = RS * 128, o_g = o_cm + RS * 256, o_cam = o_g + RS * szm,
                 o_c = o_cam + RS * 256, o_w = o_c + RS * 256, o_z = o_w + RS * 256;
       const int nc = (nrow + RS - 1) / RS;
-      const uint64_t* cmg = D.cmask + (int64_t)A.slot * D.n_elem;
-      const uint64_t* camg = calc ? D.camask + (int64_t)A.slot * D.n_elem : nullptr;
+      const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
+      const uint64_t* camg = calc ? D.camask + (int64_t)slot * D.n_elem : nullptr;
       TM* G = (TM*)D.g;
       const TM E = (TM)P.e;
       const TM dg = (TM)P.decay_g;
@@ -572,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
     }
     if (n > 0) {
       for (int32_t q = pq0; q < pq1; ++q) {
-        const int64_t smp = A.probe_sample0 + (k - A.k_begin);
+        const int64_t smp = probe0 + (k - k_begin);
         if (smp < A.probe_cap) {
           A.probe_buf[smp * A.n_probe + A.probe_id[q]] = Vg[elem_of(rb, A.probe_row[q], lane)];
         } else {
@@ -603,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
         }
       }
     }
-    spiked_prev = A.replay ? (((rbits >> (k - A.k_begin)) & 1ull) != 0) : spk;
+    spiked_prev = A.replay ? (((rbits >> (k - k_begin)) & 1ull) != 0) : spk;
   }
   if (failed) {
     // a stage never arrived: report it and drain every copy still in flight

@@ -64,7 +64,12 @@ __global__ void poisson_kernel(const PoissonArgs A, int64_t k_from, int64_t k_to
   uint64_t word[4];
   int64_t have = -1;
   uint64_t bits = 0;
-  const int64_t slot = (A.k0 / A.E) % A.n_slots;
+  const int64_t k0 = A.clock ? A.clock->k0 : A.k0;
+  if (A.clock) {
+    k_from = k0;
+    k_to = k0 + A.E;
+  }
+  const int64_t slot = (k0 / A.E) % A.n_slots;
   for (int64_t k = k_from; k < k_to; ++k) {
     const int64_t blk = k >> 3;
     if (blk != have) {
@@ -74,7 +79,7 @@ __global__ void poisson_kernel(const PoissonArgs A, int64_t k_from, int64_t k_to
     const int j = (int)(k & 7);
     const uint32_t u = (j & 1) ? (uint32_t)(word[j >> 1] >> 32) : (uint32_t)word[j >> 1];
     if (u < thr) {
-      bits |= 1ull << (k - A.k0);
+      bits |= 1ull << (k - k0);
       if (dc >= 0) {
         const int64_t kc = k + dc;
         const int64_t sc = (kc / A.E) % A.n_slots;
@@ -137,6 +142,43 @@ __global__ void finalize_kernel(int32_t* spk_count, int32_t spk_cap, int32_t* lo
   int64_t c = (int64_t)*log_count + min(*spk_count, spk_cap);
   *log_count = (int32_t)(c < log_cap ? c : log_cap);
   *spk_count = 0;
+}
+
+// Graph launches: zero the finished epoch's mask slot (the slot is reused for
+// epoch + n_slots; no event of the ring's horizon targets it meanwhile).
+__global__ void clear_slot_kernel(const SlotClear C, const EpochClock* clock) {
+  const int64_t slot = (clock->k0 / C.E) % C.n_slots;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int a = 0; a < C.n; ++a) {
+    uint64_t* p = C.base[a] + slot * C.elems[a];
+    for (int64_t i = tid; i < C.elems[a]; i += nth) p[i] = 0;
+  }
+}
+
+__global__ void tick_kernel(EpochClock* clock, int32_t E, int32_t probes) {
+  clock->k0 += E;
+  if (probes) clock->probe_sample0 += E;
+}
+
+__global__ void set_clock_kernel(EpochClock* clock, int64_t k0, int64_t probe_sample0) {
+  clock->k0 = k0;
+  clock->probe_sample0 = probe_sample0;
+}
+
+int launch_clear_and_tick(const SlotClear& c, EpochClock* clock, void* stream) {
+  int64_t most = 1;
+  for (int a = 0; a < c.n; ++a) most = c.elems[a] > most ? c.elems[a] : most;
+  int blocks = (int)((most + 255) / 256);
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (c.n > 0) clear_slot_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(c, clock);
+  tick_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(clock, c.E, c.probes);
+  return (int)cudaGetLastError();
+}
+
+int launch_set_clock(EpochClock* clock, int64_t k0, int64_t probe_sample0, void* stream) {
+  set_clock_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(clock, k0, probe_sample0);
+  return (int)cudaGetLastError();
 }
 
 int launch_poisson(const PoissonArgs& a, int64_t k_from, int64_t k_to, void* stream) {

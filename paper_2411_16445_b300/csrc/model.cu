@@ -121,6 +121,13 @@ struct pa_model {
   int32_t* err_flags = nullptr;
   std::vector<uint64_t*> mask_bases;  // cmask/camask bases to clear per epoch
   std::vector<int64_t> mask_elems;
+  // CUDA-graph launches of whole epochs (PA_FLAG_NO_GRAPHS turns them off)
+  bool graphs = true;
+  pa::EpochClock* clock = nullptr;          // device
+  pa::SlotClear slot_clear;
+  cudaStream_t cap_stream = nullptr;        // capture only
+  cudaGraphExec_t graph1 = nullptr, graph8 = nullptr;  // 1 and 8 epochs
+  int64_t n_graph_launches = 0;
   // kernel statistics
   bool time_kernels = false;
   int64_t n_static_cv = 0;
@@ -279,6 +286,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   M->n_conn = n_conn;
   M->elem_bytes_m = mixed ? 4 : 8;
   M->time_kernels = (opt->flags & PA_FLAG_TIME_KERNELS) != 0;
+  M->graphs = (opt->flags & PA_FLAG_NO_GRAPHS) == 0;
   {
     const int forced = ((opt->flags >> 8) & 0xF) - 1;
     if (forced >= pa::kNumShapes) return set_err(PA_ERR_ARG, "shape %d out of range", forced);
@@ -708,6 +716,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_log_count = R(4), o_log_gid = R(4 * (size_t)M->log_cap),
                o_log_step = R(8 * (size_t)M->log_cap), o_log_t = R(8 * (size_t)M->log_cap);
   const size_t o_err = R(4);
+  const size_t o_clock = R(sizeof(EpochClock));
 
   const size_t total = ar.used;
   cudaError_t ce = cudaMalloc((void**)&M->dmem, total);
@@ -828,6 +837,19 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   A.n_probe = M->n_probe;
   A.err_flags = (int32_t*)P8(o_err);
   M->err_flags = A.err_flags;
+  A.epoch_len = E;
+  A.n_slots = M->n_slots;
+  A.clock = nullptr;
+  M->clock = (EpochClock*)P8(o_clock);
+  std::memset(&M->slot_clear, 0, sizeof M->slot_clear);
+  M->slot_clear.n = (int32_t)M->mask_bases.size();
+  M->slot_clear.n_slots = M->n_slots;
+  M->slot_clear.E = E;
+  M->slot_clear.probes = M->n_probe > 0 ? 1 : 0;
+  for (size_t i = 0; i < M->mask_bases.size(); ++i) {
+    M->slot_clear.base[i] = M->mask_bases[i];
+    M->slot_clear.elems[i] = M->mask_elems[i];
+  }
 
   PoissonArgs& PA = M->pa_args;
   std::memset(&PA, 0, sizeof PA);
@@ -1042,6 +1064,78 @@ int run_window(pa_model* M, int64_t k_begin, int64_t k_end, bool static_scratch 
   return PA_OK;
 }
 
+// The launch sequence of one whole epoch, every kernel taking its epoch from the
+// device clock, and the clock's advance: what a captured graph holds.
+int enqueue_graph_epoch(pa_model* M, cudaStream_t st) {
+  using namespace pa;
+  int rc = 0;
+  if (M->pa_args.n > 0) {
+    PoissonArgs P = M->pa_args;
+    P.clock = M->clock;
+    rc = launch_poisson(P, 0, M->E, st);
+  }
+  if (rc == 0) {
+    EpochArgs A = M->ea;
+    A.clock = M->clock;
+    A.replay = 0;
+    rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->shape, st)
+                                  : launch_epoch_fp64(A, M->tree, M->shape, st);
+  }
+  if (rc == 0) rc = launch_route(M->ra, M->max_spikes, st);
+  if (rc == 0)
+    rc = launch_log_append(M->ea.spk_count, M->ea.spk_gid, M->ea.spk_step, M->ea.spk_t,
+                           M->max_spikes, M->log_count, M->log_gid, M->log_step, M->log_t,
+                           M->log_cap, M->err_flags, st);
+  if (rc == 0) rc = launch_clear_and_tick(M->slot_clear, M->clock, st);
+  return rc;
+}
+
+int capture_epochs(pa_model* M, int count, cudaGraphExec_t* out) {
+  if (!M->cap_stream)
+    CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaStreamBeginCapture(M->cap_stream, cudaStreamCaptureModeRelaxed));
+  int rc = 0;
+  for (int i = 0; i < count && rc == 0; ++i) rc = enqueue_graph_epoch(M, M->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(M->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return set_err(PA_ERR_CUDA, "graph capture: %s", cudaGetErrorString((cudaError_t)rc));
+  }
+  if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+  return PA_OK;
+}
+
+// n whole epochs from the current step (an epoch start) as graph launches.
+int run_graph_epochs(pa_model* M, int64_t n) {
+  using namespace pa;
+  int rc = launch_set_clock(M->clock, M->step, M->probe_samples, M->stream);
+  if (rc) return set_err(PA_ERR_CUDA, "clock: %s", cudaGetErrorString((cudaError_t)rc));
+  const int per_epoch = (M->pa_args.n > 0 ? 1 : 0) + 4 + (M->slot_clear.n > 0 ? 1 : 0) + 1;
+  while (n > 0) {
+    const int take = n >= 8 ? 8 : 1;
+    cudaGraphExec_t& g = take == 8 ? M->graph8 : M->graph1;
+    if (!g) {
+      rc = capture_epochs(M, take, &g);
+      if (rc) return rc;
+    }
+    CUDA_TRY(cudaGraphLaunch(g, M->stream));
+    ++M->n_graph_launches;
+    for (int i = 0; i < take; ++i) {
+      M->poisson_epoch_done = M->step / M->E;
+      M->step += M->E;
+      if (M->n_probe > 0) M->probe_samples += M->E;
+    }
+    M->n_epoch_launches += take;
+    M->n_kernel_launches += (int64_t)take * per_epoch;
+    n -= take;
+  }
+  return PA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1071,6 +1165,12 @@ int pa_advance(pa_model* M, double t_end_ms, double dt_ms) {
     CUDA_TRY(cudaSetDevice(M->device));
     while (M->step < k_end) {
       const int64_t e = M->step / M->E;
+      const int64_t whole = M->step == e * M->E ? (k_end - M->step) / M->E : 0;
+      if (M->graphs && !M->replay && !M->time_kernels && whole > 0 && M->poisson_epoch_done != e) {
+        int rc = run_graph_epochs(M, whole);
+        if (rc) return rc;
+        continue;
+      }
       const int64_t stop = std::min(k_end, (e + 1) * (int64_t)M->E);
       int rc = run_window(M, M->step, stop);
       if (rc) return rc;
@@ -1322,6 +1422,7 @@ int pa_get_kernel_stats(pa_model* M, pa_kernel_stats* out) {
   out->kernel_launches = M->n_kernel_launches;
   out->epoch_kernel_ms = M->epoch_ms;
   out->event_kernels_ms = M->event_ms;
+  out->graph_launches = M->n_graph_launches;
   return PA_OK;
 }
 
@@ -1329,7 +1430,7 @@ int pa_reset_kernel_stats(pa_model* M) {
   if (!M) return set_err(PA_ERR_ARG, "NULL argument");
   CUDA_TRY(cudaSetDevice(M->device));
   int rc = collect_timings(M);
-  M->n_epoch_launches = M->n_kernel_launches = 0;
+  M->n_epoch_launches = M->n_kernel_launches = M->n_graph_launches = 0;
   M->epoch_ms = M->event_ms = 0;
   return rc;
 }
@@ -1362,6 +1463,9 @@ void pa_free_model(pa_model* M) {
   for (auto& t : M->pending)
     for (cudaEvent_t e : {t.a, t.b, t.c, t.d}) cudaEventDestroy(e);
   for (cudaEvent_t e : M->ev_pool) cudaEventDestroy(e);
+  if (M->graph1) cudaGraphExecDestroy(M->graph1);
+  if (M->graph8) cudaGraphExecDestroy(M->graph8);
+  if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
   delete M;
 }
 

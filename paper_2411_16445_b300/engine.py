@@ -53,11 +53,13 @@ class Options(C.Structure):
 
 class KernelStats(C.Structure):
     _fields_ = [("epoch_launches", C.c_int64), ("kernel_launches", C.c_int64),
-                ("epoch_kernel_ms", C.c_double), ("event_kernels_ms", C.c_double)]
+                ("epoch_kernel_ms", C.c_double), ("event_kernels_ms", C.c_double),
+                ("graph_launches", C.c_int64)]
 
 
 FLAG_TIME_KERNELS = 1
 FLAG_AUTOTUNE = 2
+FLAG_NO_GRAPHS = 8
 N_SHAPES = 5
 
 

@@ -8,6 +8,13 @@ jobs overlap on the device.  A finished job's spikes and weights are read back
 and its memory freed, which makes room for waiting jobs.  Latency is measured
 from a job's arrival to the moment its results are on the host.
 
+Quanta are whole 8-epoch CUDA-graph launches, more of them for a small job
+(about `quantum_cu` compartment-updates per quantum; measured on the serving
+trace, one launch per quantum for all but the smallest jobs keeps the large
+jobs' kernels interleaved best).  Many jobs means
+many streams: set CUDA_DEVICE_MAX_CONNECTIONS (32) before CUDA is initialised
+so that their launches do not share a few hardware queues.
+
 Jobs never share device state, so a job's results are the same whether it runs
 alone or among others; tests/test_serving.py checks this.
 """
@@ -71,16 +78,23 @@ class _Resident:
         self.reserved = reserved
         self.done_steps = 0
         self.event = None
+        self.gid, self.step = [], []   # spikes drained after each quantum
+        self.epoch_steps = model.info().epoch_steps
+
+    def drain(self):
+        g, st, _ = self.model.read_spikes()
+        self.gid.append(g)
+        self.step.append(st)
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int = 64 << 30, quantum_ms: float = 20.0,
-                 precision: int = E.PA_MIXED, device: int = 0, builders: int = 2,
+    def __init__(self, hbm_budget_bytes: int = 64 << 30, quantum_cu: float = 1e6,
+                 precision: int = E.PA_MIXED, device: int = 0, builders: int = 4,
                  max_resident: int = 512):
         import torch
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
-        self.quantum_ms = quantum_ms
+        self.quantum_cu = quantum_cu
         self.precision = precision
         self.device = device
         self.max_resident = max_resident
@@ -134,17 +148,23 @@ class Server:
             for r in resident:
                 if r.event is not None and not r.event.query():
                     continue
+                if r.event is not None:
+                    r.drain()             # the quantum is complete: stream its spikes out
+                    r.event = None
                 if r.done_steps >= r.steps:
                     finished.append(r)
                     continue
-                q = max(1, int(round(self.quantum_ms / r.model.dt)))
+                # whole 8-epoch graph launches, about quantum_cu compartment-updates
+                blk = 8 * r.epoch_steps
+                q = blk * max(1, min(64, int(self.quantum_cu / (r.n_cv * blk))))
                 r.done_steps = min(r.steps, r.done_steps + q)
                 r.model.advance(r.done_steps * r.model.dt)
                 r.event = torch.cuda.Event()
                 r.event.record(r.stream)
                 progressed = True
             for r in finished:
-                g, st, _ = r.model.read_spikes()
+                r.drain()
+                g, st = np.concatenate(r.gid), np.concatenate(r.step)
                 w = r.model.read_weights()
                 results.append(JobResult(r.spec["job_id"], r.spec["arrival_s"] * time_scale,
                                          r.start_s, now(), r.n_cv, r.steps, len(g),
@@ -171,14 +191,22 @@ def spike_digest(gid, step) -> int:
                       zlib.crc32(np.ascontiguousarray(gid, np.int32).tobytes()))
 
 
-def run_alone(spec, precision=E.PA_FP64, device=0):
-    """One job by itself on the default stream (the comparison path)."""
+def run_alone(spec, precision=E.PA_FP64, device=0, chunk_ms=1000.0):
+    """One job by itself on the default stream (the comparison path); spikes are
+    read back every chunk_ms of simulated time."""
     net = W.serving_job(spec["n_cells"], spec["long_dendrite"], spec["dend_len_um"],
                         spec["dend_diam_um"], spec["seed"], dt=spec["dt"])
     m = E.Model(net, precision=precision, device=device)
     steps = int(round(spec["duration_ms"] / net.dt))
-    m.advance(steps * net.dt)
-    g, s, _ = m.read_spikes()
+    per = max(1, int(round(chunk_ms / net.dt)))
+    gs, ss = [], []
+    done = 0
+    while done < steps:
+        done = min(steps, done + per)
+        m.advance(done * net.dt)
+        g, s, _ = m.read_spikes()
+        gs.append(g)
+        ss.append(s)
     w = m.read_weights()
     m.close()
-    return net.n_cv, steps, g, s, w
+    return net.n_cv, steps, np.concatenate(gs), np.concatenate(ss), w

@@ -33,6 +33,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(E.Mech) == 16
     assert C.sizeof(E.Options) == 80
     assert C.sizeof(E.Info) == 88
+    assert C.sizeof(E.KernelStats) == 40
 
 
 def test_last_error_without_gpu_is_a_string():

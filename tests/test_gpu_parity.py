@@ -262,3 +262,30 @@ def test_trunk_first_and_side_first_numberings():
     o, m = run_both(net, 2000, E.PA_FP64, chunks=2)
     assert m.info().tree == 1
     check_state(o, m, E.PA_FP64, exact=True)
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_graph_launches_equal_direct_launches(precision):
+    """Whole epochs replayed from captured CUDA graphs (epoch taken from the
+    device clock) give bit-identical voltages, probes, spikes and weights to
+    direct launches, across partial epochs, probes, Poisson drive and delayed
+    calcium targets."""
+    net = edge_net()
+    probes = [(3, 0), (5, 4), (6, 2)]
+    runs = []
+    for flags in (E.FLAG_NO_GRAPHS, 0):
+        m = E.Model(net, precision=precision, probes=probes, flags=flags, probe_capacity=1000)
+        steps = 0
+        for n in (7, 160, 1, 333, 96, 15):     # partial and whole epochs
+            steps += n
+            m.advance(steps * net.dt)
+        m.sync()
+        ks = m.kernel_stats()
+        runs.append((m.read_state(E.FIELD_V), m.read_probes(len(probes)), m.read_spikes(),
+                     m.read_weights(), ks.graph_launches))
+        m.close()
+    (va, pa, sa, wa, ga), (vb, pb, sb, wb, gb) = runs
+    assert ga == 0 and gb > 0
+    assert np.array_equal(va, vb) and np.array_equal(pa, pb) and np.array_equal(wa, wb)
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)

@@ -35,7 +35,7 @@ def test_trace_statistics_and_estimates():
 def test_results_alone_equal_results_in_the_mix():
     from paper_2411_16445_b300 import engine as E
     trace = small_trace()
-    srv = S.Server(hbm_budget_bytes=2 << 30, quantum_ms=4.0, precision=E.PA_MIXED)
+    srv = S.Server(hbm_budget_bytes=2 << 30, quantum_cu=1e5, precision=E.PA_MIXED)
     out = srv.run(trace)
     assert len(out["results"]) == len(trace)
     assert out["p50_s"] is not None and out["p99_s"] >= out["p50_s"] > 0
@@ -52,7 +52,7 @@ def test_budget_limits_residency():
     trace = small_trace(8, seed=9)
     biggest = max(S.estimate_spec_bytes(j) for j in trace)
     # a budget for one job at a time still completes every job, one after another
-    srv = S.Server(hbm_budget_bytes=biggest, quantum_ms=10.0, precision=E.PA_MIXED)
+    srv = S.Server(hbm_budget_bytes=biggest, quantum_cu=1e6, precision=E.PA_MIXED)
     out = srv.run(trace)
     assert len(out["results"]) == len(trace)
     starts = sorted((r.start_s, r.done_s) for r in out["results"])
