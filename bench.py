@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched morphology-sweep measurement")
     p.add_argument("--serve-jobs", type=int, default=80,
                    help="serving measurement on this many jobs of the trace (0: skip)")
     p.add_argument("--shape", type=int, default=-1,
@@ -301,6 +303,53 @@ def serving_bench(n_jobs, device):
                                    "jobs served one at a time in arrival order"}}
 
 
+def batched_bench(device, epochs=200, warmup=8):
+    """Many networks in one persistent launch per min-delay epoch: the batched
+    morphology sweep (64 independent 500-cell ball-and-stick networks with
+    4-64-CV dendrites, calcium-plastic synapses, dt 0.2 ms), every epoch a
+    CUDA-graph launch, kernel shape autotuned.  Mixed and FP64; one network
+    alone (same generator, one network) for comparison."""
+    import torch
+    from paper_2411_16445_b300 import engine as E
+    from paper_2411_16445_b300 import workloads as W
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream(device)
+
+    def run(net, prec):
+        m = E.Model(net, precision=prec, device=device, stream=E.C.c_void_p(stream.cuda_stream),
+                    flags=E.FLAG_AUTOTUNE)
+        info = m.info()
+        Es = info.epoch_steps
+        m.advance(warmup * Es * net.dt)
+        m.read_spikes()
+        torch.cuda.synchronize(device)
+        m.reset_kernel_stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m.advance((warmup + epochs) * Es * net.dt)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        ks = m.kernel_stats()
+        m.read_spikes()
+        res = {"cu_per_s": info.n_cv * Es * epochs / (ms * 1e-3), "ms_per_epoch": ms / epochs,
+               "graph_launches": ks.graph_launches, "kernel_launches": ks.kernel_launches,
+               "shape": m.tuning()[0]}
+        m.close()
+        return res, info
+
+    net = W.morphology_sweep()
+    mixed, info = run(net, E.PA_MIXED)
+    fp64, _ = run(net, E.PA_FP64)
+    one, _ = run(W.morphology_sweep(n_nets=1), E.PA_MIXED)
+    return {"workload": "morphology_sweep", "n_networks": 64, "n_cells": info.n_cells,
+            "n_cv": info.n_cv, "dt_ms": net.dt, "epoch_steps": info.epoch_steps,
+            "epochs_timed": epochs, "launch": "one persistent epoch kernel per min-delay epoch "
+            "for all 64 networks, whole epochs as CUDA-graph launches (8 epochs per launch)",
+            "mixed": mixed, "fp64": fp64, "one_network_alone_mixed": one}
+
+
 def reference_arm(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -422,6 +471,8 @@ def main():
         line["mixed_over_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
     if not args.no_e2e:
         line["e2e"] = time_e2e(net, precs[head], args.steps, device)
+    if not args.no_batched:
+        line["batched"] = batched_bench(device)
     if args.serve_jobs > 0:
         line["serving"] = serving_bench(args.serve_jobs, device)
     if not args.no_cpu and ws == 1:
