@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    p.add_argument("--busyring", action="store_true",
+                   help="run the paper's busyring table instead (setup and propagation)")
+    p.add_argument("--busyring-cells", default="1024,16384,32768")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched morphology-sweep measurement")
     p.add_argument("--serve-jobs", type=int, default=80,
@@ -350,6 +353,65 @@ def batched_bench(device, epochs=200, warmup=8):
             "mixed": mixed, "fp64": fp64, "one_network_alone_mixed": one}
 
 
+# The paper's busyring propagation times [s] (Table 8: CPU, Arbor with SIMD on a
+# 64-core Threadripper PRO 5995WX; Table 9: the same with an NVIDIA T1000), keyed
+# by (cells, depth, stdp): (cpu, cpu + gpu).
+PAPER_BUSYRING = {
+    (1024, 0, False): (0.19, 0.30), (1024, 2, False): (0.28, 0.41), (1024, 10, False): (2.48, 2.99),
+    (1024, 0, True): (0.68, 0.78), (1024, 2, True): (0.79, 1.00), (1024, 10, True): (3.01, 3.50),
+    (16384, 0, False): (2.86, 2.81), (16384, 2, False): (4.23, 4.15), (16384, 10, False): (40.72, 40.45),
+    (16384, 0, True): (10.61, 10.44), (16384, 2, True): (12.37, 12.04), (16384, 10, True): (49.90, 49.05),
+    (32768, 0, False): (5.31, 5.30), (32768, 2, False): (7.86, 7.78), (32768, 10, False): (81.09, 80.44),
+    (32768, 0, True): (21.00, 20.47), (32768, 2, True): (24.45, 23.71), (32768, 10, True): (99.60, 97.75),
+}
+
+
+def busyring_bench(device, cells_list, depths, precision_name):
+    """The busyring benchmark at the paper's sizes: 200 ms at dt 0.025 ms, setup
+    (network description -> resident model) and propagation (pa_advance over the
+    whole run, CUDA events on the model's stream) timed separately, as in
+    Tables 8-9; trees from a seeded pool of 4096 shapes above 4096 cells."""
+    import torch
+    from paper_2411_16445_b300 import engine as E
+    from paper_2411_16445_b300 import workloads as W
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream(device)
+    prec = E.PA_MIXED if precision_name == "mixed" else E.PA_FP64
+    rows = []
+    for n in cells_list:
+        for d in depths:
+            for stdp in (False, True):
+                net = W.busyring(n_cells=n, depth=d, stdp=stdp,
+                                 n_shapes=4096 if n > 4096 else None)
+                torch.cuda.synchronize(device)
+                t0 = time.perf_counter()
+                m = E.Model(net, precision=prec, device=device,
+                            stream=E.C.c_void_p(stream.cuda_stream), flags=E.FLAG_AUTOTUNE)
+                torch.cuda.synchronize(device)
+                setup = time.perf_counter() - t0
+                info = m.info()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                steps = int(round(200.0 / net.dt))
+                e0.record(stream)
+                m.advance(steps * net.dt)
+                e1.record(stream)
+                e1.synchronize()
+                prop = e0.elapsed_time(e1) * 1e-3
+                g, _, _ = m.read_spikes()
+                m.close()
+                paper = PAPER_BUSYRING.get((n, d, stdp))
+                rows.append({"cells": n, "depth": d, "stdp": stdp, "n_cv": info.n_cv,
+                             "synapses": net.n_conn, "setup_s": round(setup, 3),
+                             "propagation_s": round(prop, 4),
+                             "cu_per_s": info.n_cv * steps / prop, "spikes": int(len(g)),
+                             "paper_propagation_s_cpu": paper[0] if paper else None,
+                             "paper_propagation_s_cpu_gpu": paper[1] if paper else None,
+                             "speedup_vs_paper_cpu": paper[0] / prop if paper else None})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return rows
+
+
 def reference_arm(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -386,6 +448,16 @@ def main():
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.busyring:
+        cells = [int(x) for x in args.busyring_cells.split(",")]
+        rows = busyring_bench(0, cells, [0, 2, 10], args.precision if args.precision != "both"
+                              else "fp64")
+        print(json.dumps({"benchmark": "busyring", "unit": UNIT, "simulated_ms": 200.0,
+                          "dt_ms": 0.025, "rows": rows,
+                          "paper_hardware": "AMD Threadripper PRO 5995WX (64 cores), "
+                                            "+ NVIDIA T1000 8GB for the cpu_gpu column"}),
+              flush=True)
         return
     import torch
     ws, rank, local = dist_setup()

@@ -359,6 +359,78 @@ def morphology_sweep(n_nets=64, cells_per_net=500, p=0.1, dt=0.2, seed=None,
     return b.build()
 
 
+def simple_branchy(rng: np.random.Generator, depth: int, soma_diam=20.0, cv_len=10.0,
+                   diam=1.0, cvs_per_branch=9, p_fork=0.727) -> Morphology:
+    """Random dendritic tree of the given depth on an HH soma (the busyring
+    `simple-branchy` cell, Sec. "Runtime and memory benchmarking with
+    large-scale networks").  Reading: two primary branches leave the soma; a
+    branch of level l < depth forks into two with probability p_fork; every
+    branch has cvs_per_branch CVs of cv_len um and diameter diam.  The defaults
+    reproduce the mean compartment counts of Table 8 (45.0 per cell at depth 2,
+    1633.5 at depth 10; one CV at depth 0).  Depth-first numbering."""
+    parent, length, dia, region = [-1], [soma_diam], [soma_diam], [0]
+    if depth <= 0:
+        return Morphology(np.array(parent, np.int32), np.array(length), np.array(dia),
+                          np.array(region, np.int32))
+    stack = [(0, 1), (0, 1)]          # (parent CV, level); popped depth-first
+    while stack:
+        pcv, level = stack.pop()
+        prev = pcv
+        for _ in range(cvs_per_branch):
+            parent.append(prev)
+            length.append(cv_len)
+            dia.append(diam)
+            region.append(1)
+            prev = len(parent) - 1
+        if level < depth and rng.random() < p_fork:
+            stack.append((prev, level + 1))
+            stack.append((prev, level + 1))
+    return Morphology(np.array(parent, np.int32), np.array(length), np.array(dia),
+                      np.array(region, np.int32))
+
+
+def busyring(n_cells=1024, depth=2, stdp=False, ring=4, s=1000, dt=0.025, delay_ms=5.0,
+             w_ring=0.5, seed=None, n_shapes: Optional[int] = None) -> Network:
+    """The busyring benchmark (Sec. "Runtime and memory benchmarking with large-scale
+    networks", Table 7): rings of `ring` simple-branchy cells, each cell driving
+    the next through an exponential synapse on the soma (tau 2 ms, E 0 mV,
+    weight w_ring uS, delay 5 ms), so that a spike circulates at
+    1 / (ring * delay); plus s random connections into every cell from random
+    cells, weight 0, delay 5 ms, on uniform random CVs -- exponential synapses,
+    or pair STDP (tau_pre = tau_post = 10 ms, A_pre 0.01, A_post -0.01,
+    w_max 10, w0 0) with `stdp`.  The first cell of every ring is started by a
+    2 nA, 1 ms somatic current step.  Each cell draws its own tree, or, with
+    n_shapes, one of a pool of n_shapes trees (a faster generator for very large
+    networks; the engine does not exploit shared shapes)."""
+    name = f"busyring_d{depth}{'_stdp' if stdp else ''}"
+    b = _Builder(dt, config_seed(name) if seed is None else seed, name)
+    rng = np.random.default_rng(b.seed)
+    hh = b.mech(HH, hh_params())
+    pas = b.mech(PAS, pas_params(3e-5, -65.0))
+    ring_syn = b.mech(EXPSYN, expsyn_params(2.0, 0.0))
+    rand_syn = (b.mech(STDP, stdp_params(2.0, 0.0, 10.0, 10.0, 0.01, -0.01, 0.0, 10.0))
+                if stdp else b.mech(EXPSYN, expsyn_params(2.0, 0.0)))
+    n_trees = n_cells if n_shapes is None else min(n_shapes, n_cells)
+    for _ in range(n_trees):
+        b.morph(simple_branchy(rng, depth))
+    tree_sizes = np.array([m.n_cv for m in b.morphs], np.int64)
+    morph = np.arange(n_cells) if n_shapes is None else rng.integers(0, n_trees, n_cells)
+    sizes = tree_sizes[morph]
+    cells = np.arange(n_cells)
+    first = cells % ring == 0
+    b.cells_add(n_cells, morph, hh, pas, istep=np.where(first, 2.0, 0.0), ton=0.0,
+                toff=np.where(first, 1.0, NEVER))
+    nxt = (cells // ring) * ring + (cells % ring + 1) % ring
+    b.connect(cells, nxt, 0, ring_syn, w_ring, delay=delay_ms)
+    if s > 0:
+        dst = np.repeat(cells, s)
+        src = rng.integers(0, n_cells, size=dst.shape[0])
+        cv = (rng.random(dst.shape[0]) * sizes[dst]).astype(np.int64)
+        order = np.argsort(src, kind="stable")
+        b.connect(src[order], dst[order], cv[order], rand_syn, 0.0, delay=delay_ms)
+    return b.build()
+
+
 def large_stdp(n_cells=100_000, fan_in=100, dt=0.025, seed=None, n_dend=(50, 500),
                w_syn=1e-3, w_drive=0.05, drive_hz=2.0, delay_ms=(1.0, 5.0),
                n_shapes: Optional[int] = None) -> Network:

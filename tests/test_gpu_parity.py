@@ -289,3 +289,15 @@ def test_graph_launches_equal_direct_launches(precision):
     assert np.array_equal(va, vb) and np.array_equal(pa, pb) and np.array_equal(wa, wb)
     for x, y in zip(sa, sb):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("stdp", [False, True])
+def test_busyring_fp64_bit_exact(stdp):
+    """The busyring benchmark network (rings of 4 simple-branchy cells, zero-weight
+    random connections, optionally STDP): FP64 bit-identical to the oracle over
+    40 ms, with the ring's spike circulating."""
+    net = W.busyring(n_cells=48, depth=2, s=100, stdp=stdp)
+    o, m = run_both(net, 1600, E.PA_FP64, chunks=3)
+    go, _, _ = o.spikes()
+    assert len(go) == 48 * 2          # every cell fires once per 20 ms lap
+    check_state(o, m, E.PA_FP64, exact=True)
