@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--busyring", action="store_true",
                    help="run the paper's busyring table instead (setup and propagation)")
     p.add_argument("--busyring-cells", default="1024,16384,32768")
+    p.add_argument("--busyring-depths", default="0,2,10")
+    p.add_argument("--busyring-flags", type=int, default=0,
+                   help="extra pa_options flags for the busyring models (e.g. cell bins)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched morphology-sweep measurement")
     p.add_argument("--serve-jobs", type=int, default=80,
@@ -366,7 +369,7 @@ PAPER_BUSYRING = {
 }
 
 
-def busyring_bench(device, cells_list, depths, precision_name):
+def busyring_bench(device, cells_list, depths, precision_name, extra_flags=0):
     """The busyring benchmark at the paper's sizes: 200 ms at dt 0.025 ms, setup
     (network description -> resident model) and propagation (pa_advance over the
     whole run, CUDA events on the model's stream) timed separately, as in
@@ -386,7 +389,8 @@ def busyring_bench(device, cells_list, depths, precision_name):
                 torch.cuda.synchronize(device)
                 t0 = time.perf_counter()
                 m = E.Model(net, precision=prec, device=device,
-                            stream=E.C.c_void_p(stream.cuda_stream), flags=E.FLAG_AUTOTUNE)
+                            stream=E.C.c_void_p(stream.cuda_stream),
+                            flags=E.FLAG_AUTOTUNE | extra_flags)
                 torch.cuda.synchronize(device)
                 setup = time.perf_counter() - t0
                 info = m.info()
@@ -402,6 +406,7 @@ def busyring_bench(device, cells_list, depths, precision_name):
                 m.close()
                 paper = PAPER_BUSYRING.get((n, d, stdp))
                 rows.append({"cells": n, "depth": d, "stdp": stdp, "n_cv": info.n_cv,
+                             "wide_cells": info.n_wide,
                              "synapses": net.n_conn, "setup_s": round(setup, 3),
                              "propagation_s": round(prop, 4),
                              "cu_per_s": info.n_cv * steps / prop, "spikes": int(len(g)),
@@ -451,8 +456,9 @@ def main():
         return
     if args.busyring:
         cells = [int(x) for x in args.busyring_cells.split(",")]
-        rows = busyring_bench(0, cells, [0, 2, 10], args.precision if args.precision != "both"
-                              else "fp64")
+        rows = busyring_bench(0, cells, [int(x) for x in args.busyring_depths.split(",")],
+                              args.precision if args.precision != "both" else "fp64",
+                              args.busyring_flags)
         print(json.dumps({"benchmark": "busyring", "unit": UNIT, "simulated_ms": 200.0,
                           "dt_ms": 0.025, "rows": rows,
                           "paper_hardware": "AMD Threadripper PRO 5995WX (64 cores), "

@@ -176,6 +176,15 @@ typedef struct {
  * epochs per launch where they fit).  Partial epochs, open-loop replay and
  * PA_FLAG_TIME_KERNELS always launch directly.  Results are identical. */
 #define PA_FLAG_NO_GRAPHS 8
+/* pa_options.flags: cell bins.  A cell runs on one thread of a warp that holds
+ * 32 cells (the narrow bin), or on a whole warp (the wide bin: its synapses
+ * updated 32 at a time, its tree eliminated branch-parallel by levels).  By
+ * default, when the narrow bin alone would leave fewer than 4 warps per SM,
+ * cells with at least 128 CVs in at least 8 branches and at most 2 synapses
+ * per CV are wide.  Both bins give identical results.  NARROW_ONLY / WIDE_ALL
+ * force every cell into one bin. */
+#define PA_FLAG_NARROW_ONLY 16
+#define PA_FLAG_WIDE_ALL 32
 
 typedef struct {
   int64_t epoch_launches;   /* epoch (time-step) kernel launches since the last reset */
@@ -193,7 +202,7 @@ typedef struct {
   int32_t tree;             /* 1 if any morphology branches */
   int32_t n_streams;        /* synapse streams (one per point mechanism in use) */
   int32_t shape;            /* epoch-kernel shape in use */
-  int32_t reserved;
+  int32_t n_wide;           /* cells in the warp-per-cell bin */
   int64_t device_bytes;     /* device memory held by the model */
   int64_t n_static_cv;      /* CVs whose subtree carries no synapse (a statistic) */
 } pa_info;

@@ -59,6 +59,26 @@ struct EpochClock {
   int64_t probe_sample0;   // probe sample index of step k0
 };
 
+// A cell of the wide bin (one warp per cell): its branch list (rows
+// [wbr_s, wbr_e] of each branch, sorted by level) and the level offsets into it.
+struct WideCell {
+  int32_t br0;    // first entry in wbr_s / wbr_e
+  int32_t lvl0;   // first entry in wlvl (n_lvl + 1 offsets, relative to br0)
+  int32_t n_lvl;
+  int32_t pad;
+};
+
+// Cell bins: when the narrow bin alone would give fewer than
+// kWideMaxWarpsPerSM warps per SM, the wide bin takes the cells with at least
+// kWideMinCV CVs in at least kWideMinBranches branches and at most
+// kWideMaxSynPerCV synapses per CV (the per-CV sums are serial runs, so a
+// cell whose synapses crowd onto few CVs gains nothing from a warp); every
+// cell with PA_FLAG_WIDE_ALL.
+constexpr int kWideMinCV = 128;
+constexpr int kWideMinBranches = 8;
+constexpr int kWideMaxSynPerCV = 2;
+constexpr int kWideMaxWarpsPerSM = 4;
+
 struct EpochArgs {
   // launch window: steps [k_begin, k_end) all inside epoch [k0, k0 + E); with
   // `clock` set the window is the whole epoch the clock names instead
@@ -67,7 +87,13 @@ struct EpochArgs {
   int32_t epoch_len;     // E
   int32_t n_slots;
   const EpochClock* clock;
-  int32_t n_groups;
+  int32_t n_groups;      // all groups: narrow [0, n_narrow), then one per wide cell
+  int32_t n_narrow;      // groups of 32 cells, one thread per cell
+  int32_t n_wide;        // wide cells, one warp per cell
+  const WideCell* wcell; // [n_wide]
+  const int32_t* wbr_s;  // branch first row
+  const int32_t* wbr_e;  // branch last row
+  const int32_t* wlvl;   // level offsets
   double dt;
   // groups / lanes
   const int32_t* row_base;   // [n_groups + 1]
@@ -161,8 +187,20 @@ struct RouteArgs {
 
 // kernel launchers (defined in the .cu files)
 constexpr int kNumShapes = 5;  // kernel shapes (see launch_epoch_shape)
-int launch_epoch_fp64(const EpochArgs& a, bool tree, int shape, void* stream);
-int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream);
+// The narrow kernel over groups [0, n_narrow) and the wide kernel.  With
+// `side` (a second stream and two events) and both bins in use, the wide
+// kernel runs on the side stream concurrently with the narrow one (fork and
+// join through the events, so a stream capture records two parallel
+// branches); otherwise one after the other on `stream`.
+struct SideLaunch {
+  void* stream;  // cudaStream_t
+  void* fork;    // cudaEvent_t
+  void* join;    // cudaEvent_t
+};
+int launch_epoch_fp64(const EpochArgs& a, bool tree, int shape, void* stream,
+                      const SideLaunch* side = nullptr);
+int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream,
+                       const SideLaunch* side = nullptr);
 int launch_init_gates_fp64(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
                            void* stream);
 int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,

@@ -178,6 +178,77 @@ struct Stage {
   static constexpr int kWarpBytes = kStages * kBytes + 64;  // + mbarriers
 };
 
+// One synapse's step (rows a1, a2, a4): this step's conductance event, the
+// delayed calcium event and the POST_EVENT of the cell's spike in the previous
+// step, then the plasticity update of its kind (Eqs. weight_graupner_brunel,
+// early_phase_weight, late_phase_weight, stdp_ode_1-3); stores the synapse's
+// plastic state and returns the conductance entering this step's per-CV sums.
+// cc, wv, zv are the synapse's calcium, weight (h for STC) and z as loaded by
+// the caller (only those its kind uses); S accumulates |h - h0| (STC).
+template <class TM>
+__device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev& D, uint32_t e,
+                                         bool pre, bool capre, bool post, TM gv, double cc,
+                                         double wv, double zv, double prp, int64_t k, double dt,
+                                         double& S) {
+  if (P.kind == SK_EXPSYN) {
+    if (pre) gv = gv + ((const TM*)D.weight)[e];
+  } else if (P.kind == SK_GB) {
+    if (pre) gv = gv + ((const TM*)D.weight)[e];
+    if (capre) cc = cc + P.c_pre;
+    if (post) cc = cc + P.c_post;
+    const double w = wv;
+    const double Aw = (w * (1.0 - w)) * (P.w_star - w);
+    const double Pw = (cc > P.theta_p) ? P.gamma_p * (1.0 - w) : 0.0;
+    const double Dw = (cc > P.theta_d) ? P.gamma_d * w : 0.0;
+    D.w[e] = w + P.rate_w * ((Pw - Aw) - Dw);
+    D.c[e] = cc * P.decay_c;
+  } else if (P.kind == SK_STC) {
+    const double h = wv, z = zv;
+    const double h0 = P.h0;
+    if (pre) gv = gv + (TM)((double)((const TM*)D.weight)[e] * ((h + h0 * z) / h0));
+    if (capre) cc = cc + P.c_pre;
+    if (post) cc = cc + P.c_post;
+    S = S + fabs(h - h0);
+    const double T1 = ((h - h0) > P.theta_tag) ? (prp * P.f_int) * (1.0 - z) : 0.0;
+    const double T2 = ((h0 - h) > P.theta_tag) ? (prp * P.f_int) * (z + 0.5) : 0.0;
+    D.z[e] = z + P.rate_z * (T1 - T2);
+    const double Ph = (cc > P.theta_p) ? P.gamma_p * (10.0 - h) : 0.0;
+    const double Dh = (cc > P.theta_d) ? P.gamma_d * h : 0.0;
+    D.w[e] = h + P.rate_h * ((0.1 * (h0 - h) + Ph) - Dh);
+    D.c[e] = cc * P.decay_c;
+  } else if (pre || post) {  // SK_STDP: traces evaluated in closed form at events only
+    TM* AP = (TM*)D.apre;
+    TM* AQ = (TM*)D.apost;
+    double w = D.w[e];
+    double ap = (double)AP[e] * model_exp(-((double)(k - D.kpre[e]) * dt) / P.tau_pre);
+    double aq = (double)AQ[e] * model_exp(-((double)(k - D.kpost[e]) * dt) / P.tau_post);
+    if (pre) {
+      const double wc = w < 0.0 ? 0.0 : (w > P.w_max ? P.w_max : w);
+      gv = gv + (TM)((double)((const TM*)D.weight)[e] * wc);
+      ap = ap + P.a_pre;
+      w = w + aq;
+      AP[e] = (TM)ap;
+      D.kpre[e] = (int32_t)k;
+    }
+    if (post) {
+      aq = aq + P.a_post;
+      w = w + ap;
+      AQ[e] = (TM)aq;
+      D.kpost[e] = (int32_t)k;
+    }
+    D.w[e] = w;
+  }
+  return gv;
+}
+
+// The per-CV synaptic sums are spelled with explicitly rounded operations, never
+// contracted into fused multiply-adds, so that both cell bins (and any compiler
+// schedule) produce the same sums.
+__device__ __forceinline__ float tm_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float tm_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double tm_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double tm_add(double a, double b) { return __dadd_rn(a, b); }
+
 // Per-CV synaptic sums over one run of same-CV synapses of a stream, in the
 // canonical order: the run starts from 0 (first synapse on the CV) or from the
 // sums left by an earlier stream, and is stored when it ends.
@@ -185,18 +256,19 @@ struct Stage {
 template <class TM>
 __device__ __forceinline__ void run_sum(TM* gs, TM* es, int32_t rb, int lane, int32_t cvf, TM g,
                                         TM E, TM& accg, TM& acce) {
+  const TM ge = tm_mul(g, E);
   if (cvf & 2) {
     if (cvf & 1) {
       accg = g;
-      acce = g * E;
+      acce = ge;
     } else {
       const uint32_t ce = elem_of(rb, cvf >> 3, lane);
-      accg = gs[ce] + g;
-      acce = es[ce] + g * E;
+      accg = tm_add(gs[ce], g);
+      acce = tm_add(es[ce], ge);
     }
   } else {
-    accg = accg + g;
-    acce = acce + g * E;
+    accg = tm_add(accg, g);
+    acce = tm_add(acce, ge);
   }
   if (cvf & 4) {
     const uint32_t ce = elem_of(rb, cvf >> 3, lane);
@@ -211,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
   extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  if (g >= A.n_groups) return;  // whole warps only
+  if (g >= A.n_narrow) return;  // whole warps only
   char* wbuf = smem_raw + (threadIdx.x >> 5) * ST::kWarpBytes;
   uint64_t* bar = (uint64_t*)(wbuf + kStages * ST::kBytes);
   if (lane == 0) {
@@ -333,63 +405,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           if (cvf < 0) continue;
           const uint32_t e = ((uint32_t)(sb + lo + jj) << 5) | (uint32_t)lane;
           const bool pre = (((const uint64_t*)(st + o_cm))[r] >> kk) & 1ull;
-          TM gv = ((const TM*)(st + o_g))[r];
-          if (P.kind == SK_EXPSYN) {
-            if (pre) gv = gv + ((const TM*)D.weight)[e];
-            run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
-          } else if (P.kind == SK_GB) {
-            double cc = ((const double*)(st + o_c))[r];
-            if (pre) gv = gv + ((const TM*)D.weight)[e];
-            if ((((const uint64_t*)(st + o_cam))[r] >> kk) & 1ull) cc = cc + P.c_pre;
-            if (post) cc = cc + P.c_post;
-            run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
-            const double w = ((const double*)(st + o_w))[r];
-            const double Aw = (w * (1.0 - w)) * (P.w_star - w);
-            const double Pw = (cc > P.theta_p) ? P.gamma_p * (1.0 - w) : 0.0;
-            const double Dw = (cc > P.theta_d) ? P.gamma_d * w : 0.0;
-            D.w[e] = w + P.rate_w * ((Pw - Aw) - Dw);
-            D.c[e] = cc * P.decay_c;
-          } else if (P.kind == SK_STC) {
-            double cc = ((const double*)(st + o_c))[r];
-            const double h = ((const double*)(st + o_w))[r], z = ((const double*)(st + o_z))[r];
-            const double h0 = P.h0;
-            if (pre) gv = gv + (TM)((double)((const TM*)D.weight)[e] * ((h + h0 * z) / h0));
-            if ((((const uint64_t*)(st + o_cam))[r] >> kk) & 1ull) cc = cc + P.c_pre;
-            if (post) cc = cc + P.c_post;
-            run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
-            S = S + fabs(h - h0);
-            const double T1 = ((h - h0) > P.theta_tag) ? (prp * P.f_int) * (1.0 - z) : 0.0;
-            const double T2 = ((h0 - h) > P.theta_tag) ? (prp * P.f_int) * (z + 0.5) : 0.0;
-            D.z[e] = z + P.rate_z * (T1 - T2);
-            const double Ph = (cc > P.theta_p) ? P.gamma_p * (10.0 - h) : 0.0;
-            const double Dh = (cc > P.theta_d) ? P.gamma_d * h : 0.0;
-            D.w[e] = h + P.rate_h * ((0.1 * (h0 - h) + Ph) - Dh);
-            D.c[e] = cc * P.decay_c;
-          } else {  // SK_STDP: traces evaluated in closed form at events only
-            if (pre || post) {
-              TM* AP = (TM*)D.apre;
-              TM* AQ = (TM*)D.apost;
-              double w = D.w[e];
-              double ap = (double)AP[e] * model_exp(-((double)(k - D.kpre[e]) * dt) / P.tau_pre);
-              double aq = (double)AQ[e] * model_exp(-((double)(k - D.kpost[e]) * dt) / P.tau_post);
-              if (pre) {
-                const double wc = w < 0.0 ? 0.0 : (w > P.w_max ? P.w_max : w);
-                gv = gv + (TM)((double)((const TM*)D.weight)[e] * wc);
-                ap = ap + P.a_pre;
-                w = w + aq;
-                AP[e] = (TM)ap;
-                D.kpre[e] = (int32_t)k;
-              }
-              if (post) {
-                aq = aq + P.a_post;
-                w = w + ap;
-                AQ[e] = (TM)aq;
-                D.kpost[e] = (int32_t)k;
-              }
-              D.w[e] = w;
-            }
-            run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
-          }
+          const bool capre = calc && ((((const uint64_t*)(st + o_cam))[r] >> kk) & 1ull);
+          const double cc = calc ? ((const double*)(st + o_c))[r] : 0.0;
+          const double wv = calc ? ((const double*)(st + o_w))[r] : 0.0;
+          const double zv = stc ? ((const double*)(st + o_z))[r] : 0.0;
+          TM gv = syn_update<TM>(P, D, e, pre, capre, post, ((const TM*)(st + o_g))[r], cc, wv,
+                                 zv, prp, k, dt, S);
+          run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
           G[e] = gv * dg;
         }
       }
@@ -658,7 +680,7 @@ template <class TM, bool TREE, int RB, int RF, int WPB, int MB>
 int launch_epoch_t(const EpochArgs& a, void* stream) {
   constexpr int warps_per_block = WPB;
   const int threads = 32 * warps_per_block;
-  const int64_t warps = a.n_groups;
+  const int64_t warps = a.n_narrow;
   const int blocks = (int)((warps * 32 + threads - 1) / threads);
   if (blocks == 0) return 0;
   const int smem = warps_per_block * Stage<TM, TREE, RB, RF>::kWarpBytes;

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "epoch_kernel.cuh"
+#include "wide_kernel.cuh"
 
 namespace pa {
 
@@ -48,8 +49,10 @@ int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, boo
   EpochArgs b = a;
   b.f = g_scratch_dev_ptr[dev];
   b.xp = g_scratch_dev_ptr[dev] + n_padded_cv;
-  return mixed ? launch_epoch_impl<float>(b, tree, shape, stream)
-               : launch_epoch_impl<double>(b, tree, shape, stream);
+  int rc = mixed ? launch_epoch_impl<float>(b, tree, shape, stream)
+                 : launch_epoch_impl<double>(b, tree, shape, stream);
+  if (rc == 0) rc = mixed ? launch_wide_impl<float>(b, stream) : launch_wide_impl<double>(b, stream);
+  return rc;
 }
 
 }  // namespace pa

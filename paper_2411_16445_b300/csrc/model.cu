@@ -79,6 +79,7 @@ struct pa_model {
   double dt = 0;
   uint64_t seed = 0;
   int64_t n_cells = 0, n_cv = 0, n_conn = 0, n_groups = 0, n_lanes = 0, total_rows = 0;
+  int64_t n_narrow = 0, n_wide = 0;       // groups of the thread- and warp-per-cell bins
   int64_t step = 0;
   int32_t E = 1, n_slots = 1;
   int64_t poisson_epoch_done = -1;
@@ -126,6 +127,9 @@ struct pa_model {
   pa::EpochClock* clock = nullptr;          // device
   pa::SlotClear slot_clear;
   cudaStream_t cap_stream = nullptr;        // capture only
+  cudaStream_t side_stream = nullptr;       // the wide bin, concurrent with the narrow one
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  pa::SideLaunch side{nullptr, nullptr, nullptr};
   cudaGraphExec_t graph1 = nullptr, graph8 = nullptr;  // 1 and 8 epochs
   int64_t n_graph_launches = 0;
   // kernel statistics
@@ -139,6 +143,11 @@ struct pa_model {
   struct Timed { cudaEvent_t a, b, c, d; };               // [a,b): Poisson, [b,c): epoch, [c,d): routing
   std::vector<Timed> pending;
 };
+
+namespace {
+// the side stream of the wide bin, once both bins are in use
+const pa::SideLaunch* side_of(const pa_model* M) { return M->side.stream ? &M->side : nullptr; }
+}  // namespace
 
 namespace {
 
@@ -193,8 +202,8 @@ int autotune(pa_model* M) {
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
       e = cudaEventRecord(e0, M->stream);
       if (e == cudaSuccess)
-        e = (cudaError_t)(M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, s, M->stream)
-                                                   : launch_epoch_fp64(A, M->tree, s, M->stream));
+        e = (cudaError_t)(M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, s, M->stream, side_of(M))
+                                                   : launch_epoch_fp64(A, M->tree, s, M->stream, side_of(M)));
       if (e == cudaSuccess) e = cudaEventRecord(e1, M->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0;
@@ -380,25 +389,61 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   }
   M->n_cv = M->cell_cv_off[n_cells];
 
-  // sort cells by CV count (descending), deal into groups of 32 lanes
-  std::vector<int32_t> order(n_cells);
-  for (int64_t c = 0; c < n_cells; ++c) order[c] = (int32_t)c;
+  // ---- cell bins: thread per cell (narrow) or warp per cell (wide) ----------------
+  if ((opt->flags & PA_FLAG_NARROW_ONLY) && (opt->flags & PA_FLAG_WIDE_ALL))
+    return set_err(PA_ERR_ARG, "PA_FLAG_NARROW_ONLY and PA_FLAG_WIDE_ALL exclude each other");
+  std::vector<char> wide(n_cells, 0);
+  {
+    std::vector<int64_t> cell_syn(n_cells, 0);
+    for (int64_t c = 0; c < n_conn; ++c)
+      if (conns[c].dst_gid >= 0 && conns[c].dst_gid < n_cells) ++cell_syn[conns[c].dst_gid];
+    std::vector<int32_t> morph_branches(n_morph, 0);
+    for (int64_t j = 0; j < n_morph; ++j)
+      for (int i = 0; i < morphs[j].n_cv; ++i)
+        morph_branches[j] += (i == 0 || morphs[j].parent[i] != i - 1) ? 1 : 0;
+    int n_sm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, M->device));
+    const bool few = (n_cells + kLanes - 1) / kLanes < (int64_t)kWideMaxWarpsPerSM * n_sm;
+    for (int64_t c = 0; c < n_cells; ++c)
+      wide[c] = (opt->flags & PA_FLAG_WIDE_ALL) ||
+                (!(opt->flags & PA_FLAG_NARROW_ONLY) && few && M->cell_ncv[c] >= kWideMinCV &&
+                 morph_branches[cells[c].morph] >= kWideMinBranches &&
+                 cell_syn[c] <= (int64_t)kWideMaxSynPerCV * M->cell_ncv[c]);
+  }
+  // narrow cells sorted by CV count (descending) and dealt into groups of 32
+  // lanes; then one group per wide cell (its cell in lane 0, CVs contiguous)
+  std::vector<int32_t> order, order_w;
+  for (int64_t c = 0; c < n_cells; ++c) (wide[c] ? order_w : order).push_back((int32_t)c);
   std::stable_sort(order.begin(), order.end(),
                    [&](int32_t x, int32_t y) { return M->cell_ncv[x] > M->cell_ncv[y]; });
-  const int64_t n_groups = (n_cells + kLanes - 1) / kLanes;
+  std::stable_sort(order_w.begin(), order_w.end(),
+                   [&](int32_t x, int32_t y) { return M->cell_ncv[x] > M->cell_ncv[y]; });
+  const int64_t n_narrow = ((int64_t)order.size() + kLanes - 1) / kLanes;
+  const int64_t n_wide = (int64_t)order_w.size();
+  const int64_t n_groups = n_narrow + n_wide;
   const int64_t n_lanes = n_groups * kLanes;
+  if (n_groups > (1LL << 30)) return set_err(PA_ERR_ARG, "too many cells");
   M->n_groups = n_groups;
+  M->n_narrow = n_narrow;
+  M->n_wide = n_wide;
   M->n_lanes = n_lanes;
   M->lane_of_gid.assign(n_cells, -1);
   std::vector<int32_t> lane_gid(n_lanes, -1), lane_ncv(n_lanes, 0);
-  for (int64_t L = 0; L < n_cells; ++L) {
-    lane_gid[L] = order[L];
-    lane_ncv[L] = M->cell_ncv[order[L]];
-    M->lane_of_gid[order[L]] = (int32_t)L;
+  for (size_t i = 0; i < order.size(); ++i) {
+    lane_gid[i] = order[i];
+    lane_ncv[i] = M->cell_ncv[order[i]];
+    M->lane_of_gid[order[i]] = (int32_t)i;
+  }
+  for (int64_t j = 0; j < n_wide; ++j) {
+    const int64_t L = (n_narrow + j) * kLanes;
+    lane_gid[L] = order_w[j];
+    lane_ncv[L] = M->cell_ncv[order_w[j]];
+    M->lane_of_gid[order_w[j]] = (int32_t)L;
   }
   M->row_base.assign(n_groups + 1, 0);
   for (int64_t g = 0; g < n_groups; ++g) {
-    int64_t rows = lane_ncv[g * kLanes];
+    const int64_t nc = lane_ncv[g * kLanes];
+    const int64_t rows = g < n_narrow ? nc : (nc + kLanes - 1) / kLanes;
     if ((int64_t)M->row_base[g] + rows > (1LL << 26))
       return set_err(PA_ERR_ARG, "model too large: more than 2^31 padded CVs");
     M->row_base[g + 1] = M->row_base[g] + (int32_t)rows;
@@ -406,7 +451,9 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   M->total_rows = M->row_base[n_groups];
   const int64_t n_elem = M->total_rows * kLanes;
   auto elem = [&](int64_t L, int row) -> int64_t {
-    return ((int64_t)M->row_base[L / kLanes] + row) * kLanes + (L % kLanes);
+    const int64_t g = L / kLanes;
+    if (g >= n_narrow) return ((int64_t)M->row_base[g] << 5) + row;
+    return ((int64_t)M->row_base[g] + row) * kLanes + (L % kLanes);
   };
 
   // ---- CV discretisation (a CV is a cylinder; Eq. cable) -----------------------
@@ -423,7 +470,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<double> h_iinj(n_lanes, 0.0), h_thresh(n_lanes, 0.0);
   std::vector<int64_t> h_kon(n_lanes, 0), h_koff(n_lanes, 0);
   std::vector<double> rhalf, gi_v, gax, cdt_v, dcc;
-  for (int64_t L = 0; L < n_cells; ++L) {
+  for (int64_t L = 0; L < n_lanes; ++L) {
+    if (lane_gid[L] < 0) continue;
     const pa_cell& cl = cells[lane_gid[L]];
     const pa_morphology& g = morphs[cl.morph];
     const int n = g.n_cv;
@@ -486,6 +534,51 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     h_kon[L] = std::llround(cl.t_on / dt);
     h_koff[L] = cl.t_off > 1e15 ? INT64_MAX : std::llround(cl.t_off / dt);
     h_thresh[L] = cl.threshold;
+  }
+
+  // ---- branch tables of the wide cells ------------------------------------------
+  // A branch is a maximal run of rows i whose parent is i - 1 (rows are
+  // contiguous).  A branch's level exceeds that of every branch starting at a
+  // child of one of its rows, so a level only needs lower levels eliminated;
+  // the root branch (row 0) is then the only branch of the top level.
+  std::vector<WideCell> h_wcell(n_wide);
+  std::vector<int32_t> h_wbr_s, h_wbr_e, h_wlvl;
+  for (int64_t j = 0; j < n_wide; ++j) {
+    const pa_morphology& gm = morphs[cells[order_w[j]].morph];
+    const int n = gm.n_cv;
+    std::vector<int32_t> bstart, bidx(n);
+    for (int i = 0; i < n; ++i) {
+      if (i == 0 || gm.parent[i] != i - 1) bstart.push_back(i);
+      bidx[i] = (int32_t)bstart.size() - 1;
+    }
+    const int nb = (int)bstart.size();
+    std::vector<int32_t> lvl(nb, 0);
+    for (int i = n - 1; i >= 1; --i) {
+      if (gm.parent[i] == i - 1) continue;
+      int32_t& up = lvl[bidx[gm.parent[i]]];
+      up = std::max(up, lvl[bidx[i]] + 1);
+    }
+    std::vector<int32_t> ordb(nb);
+    for (int b = 0; b < nb; ++b) ordb[b] = b;
+    std::stable_sort(ordb.begin(), ordb.end(), [&](int32_t x, int32_t y) { return lvl[x] < lvl[y]; });
+    const int n_lvl = lvl[0] + 1;
+    if (ordb[nb - 1] != 0 || (nb > 1 && lvl[ordb[nb - 2]] == lvl[0]))
+      return set_err(PA_ERR_ARG, "internal: root branch is not alone on the top level");
+    WideCell& w = h_wcell[j];
+    w.br0 = (int32_t)h_wbr_s.size();
+    w.lvl0 = (int32_t)h_wlvl.size();
+    w.n_lvl = n_lvl;
+    w.pad = 0;
+    int b = 0;
+    for (int lv = 0; lv <= n_lvl; ++lv) {
+      while (b < nb && lvl[ordb[b]] < lv) ++b;
+      h_wlvl.push_back(b);
+    }
+    for (int q = 0; q < nb; ++q) {
+      const int bb = ordb[q];
+      h_wbr_s.push_back(bstart[bb]);
+      h_wbr_e.push_back(bb + 1 < nb ? bstart[bb + 1] - 1 : n - 1);
+    }
   }
 
   // ---- synapses: one per connection, streams by mechanism -------------------------
@@ -551,9 +644,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         });
         mx = std::max(mx, v.size());
       }
-      if ((int64_t)s_sbase[s][g] + (int64_t)mx > (1LL << 26))
+      const int64_t rows = g < n_narrow ? (int64_t)mx : ((int64_t)mx + kLanes - 1) / kLanes;
+      if ((int64_t)s_sbase[s][g] + rows > (1LL << 26))
         return set_err(PA_ERR_ARG, "too many synapses in one stream");
-      s_sbase[s][g + 1] = s_sbase[s][g] + (int32_t)mx;
+      s_sbase[s][g + 1] = s_sbase[s][g] + (int32_t)rows;
     }
     const int64_t ne = (int64_t)s_sbase[s][n_groups] * kLanes;
     M->s_nelem[s] = ne;
@@ -565,7 +659,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // synapses of a stream (canonical order: mechanism, CV, connection).  Flags:
   // bit 0 "first on this CV over all streams" (the run starts from 0), bit 1 "run
   // starts", bit 2 "run ends" (store the sums).  cvf = (cv << 3) | flags.
-  for (int64_t L = 0; L < n_cells; ++L) {
+  for (int64_t L = 0; L < n_lanes; ++L) {
+    if (lane_gid[L] < 0) continue;
     const int ncell = M->cell_ncv[lane_gid[L]];
     std::vector<char> touched(ncell, 0);
     const int64_t g = L / kLanes, l = L % kLanes;
@@ -574,7 +669,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       const double* p = mechs[m].params;
       auto& v = per_lane[(size_t)s * n_lanes + L];
       for (size_t j = 0; j < v.size(); ++j) {
-        const int64_t e = ((int64_t)s_sbase[s][g] + (int64_t)j) * kLanes + l;
+        const int64_t e = g < n_narrow ? ((int64_t)s_sbase[s][g] + (int64_t)j) * kLanes + l
+                                       : ((int64_t)s_sbase[s][g] << 5) + (int64_t)j;
         const int cv = v[j].cv;
         const bool start = j == 0 || v[j - 1].cv != cv;
         const bool end = j + 1 == v.size() || v[j + 1].cv != cv;
@@ -659,7 +755,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     }
   }
   M->probe_cap = opt->n_probe > 0 ? (opt->probe_capacity > 0 ? opt->probe_capacity : 65536) : 0;
-  M->max_spikes = (int32_t)std::min<int64_t>(n_lanes * ((E + 1) / 2) + 32, (1LL << 31) - 1);
+  M->max_spikes = (int32_t)std::min<int64_t>(n_cells * ((E + 1) / 2) + 32, (1LL << 31) - 1);
   M->log_cap = opt->spike_capacity > 0 ? opt->spike_capacity
                                        : std::max<int64_t>(1 << 20, (int64_t)n_cells * 64);
   if (M->log_cap > (1LL << 31) - 1) M->log_cap = (1LL << 31) - 1;
@@ -716,6 +812,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_log_count = R(4), o_log_gid = R(4 * (size_t)M->log_cap),
                o_log_step = R(8 * (size_t)M->log_cap), o_log_t = R(8 * (size_t)M->log_cap);
   const size_t o_err = R(4);
+  const size_t o_wcell = R(sizeof(WideCell) * std::max<int64_t>(n_wide, 1));
+  const size_t o_wbr_s = R(sizeof(int32_t) * std::max<size_t>(h_wbr_s.size(), 1));
+  const size_t o_wbr_e = R(sizeof(int32_t) * std::max<size_t>(h_wbr_e.size(), 1));
+  const size_t o_wlvl = R(sizeof(int32_t) * std::max<size_t>(h_wlvl.size(), 1));
   const size_t o_clock = R(sizeof(EpochClock));
 
   const size_t total = ar.used;
@@ -747,6 +847,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn);
   }
   putv(o_ishh, h_is_hh);
+  putv(o_wcell, h_wcell); putv(o_wbr_s, h_wbr_s); putv(o_wbr_e, h_wbr_e); putv(o_wlvl, h_wlvl);
   putv(o_iinj, h_iinj); putv(o_kon, h_kon); putv(o_koff, h_koff); putv(o_th, h_thresh);
   putv(o_hasstc, h_has_stc);
   for (int s = 0; s < n_streams; ++s) {
@@ -768,6 +869,18 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   EpochArgs& A = M->ea;
   std::memset(&A, 0, sizeof A);
   A.n_groups = (int32_t)n_groups;
+  A.n_narrow = (int32_t)n_narrow;
+  A.n_wide = (int32_t)n_wide;
+  A.wcell = (const WideCell*)P8(o_wcell);
+  A.wbr_s = (const int32_t*)P8(o_wbr_s);
+  A.wbr_e = (const int32_t*)P8(o_wbr_e);
+  A.wlvl = (const int32_t*)P8(o_wlvl);
+  if (n_narrow > 0 && n_wide > 0) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&M->side_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming));
+    M->side = {M->side_stream, M->ev_fork, M->ev_join};
+  }
   A.dt = dt;
   A.row_base = (const int32_t*)P8(o_rowbase);
   A.ncv = (const int32_t*)P8(o_ncv);
@@ -895,7 +1008,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // rate functions
   {
     std::vector<double> vin(n_lanes, 0.0);
-    for (int64_t L = 0; L < n_cells; ++L) vin[L] = cells[lane_gid[L]].v_init;
+    for (int64_t L = 0; L < n_lanes; ++L)
+      if (lane_gid[L] >= 0) vin[L] = cells[lane_gid[L]].v_init;
     double* dv = nullptr;
     CUDA_TRY(cudaMalloc((void**)&dv, sizeof(double) * n_lanes));
     cudaError_t e2 = cudaMemcpyAsync(dv, vin.data(), sizeof(double) * n_lanes,
@@ -1027,8 +1141,8 @@ int run_window(pa_model* M, int64_t k_begin, int64_t k_end, bool static_scratch 
       return set_err(PA_ERR_ARG, "model has %lld padded CVs; pa_advance_noalloc holds at most %lld",
                      (long long)(M->total_rows * kLanes), (long long)noalloc_max_padded_cv());
   } else {
-    rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->shape, M->stream)
-                                  : launch_epoch_fp64(A, M->tree, M->shape, M->stream);
+    rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->shape, M->stream, side_of(M))
+                                  : launch_epoch_fp64(A, M->tree, M->shape, M->stream, side_of(M));
   }
   if (rc) return set_err(PA_ERR_CUDA, "epoch launch: %s", cudaGetErrorString((cudaError_t)rc));
   if (timed) CUDA_TRY(cudaEventRecord(tm.c, M->stream));
@@ -1078,8 +1192,8 @@ int enqueue_graph_epoch(pa_model* M, cudaStream_t st) {
     EpochArgs A = M->ea;
     A.clock = M->clock;
     A.replay = 0;
-    rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->shape, st)
-                                  : launch_epoch_fp64(A, M->tree, M->shape, st);
+    rc = M->precision == PA_MIXED ? launch_epoch_mixed(A, M->tree, M->shape, st, side_of(M))
+                                  : launch_epoch_fp64(A, M->tree, M->shape, st, side_of(M));
   }
   if (rc == 0) rc = launch_route(M->ra, M->max_spikes, st);
   if (rc == 0)
@@ -1286,9 +1400,11 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
     int rc = fetch(M->ea.V, M->total_rows * kLanes, 8, tmp);
     if (rc) return rc;
     for (int64_t c = 0; c < M->n_cells; ++c) {
-      const int64_t L = M->lane_of_gid[c];
+      const int64_t L = M->lane_of_gid[c], g = L / kLanes;
       for (int i = 0; i < M->cell_ncv[c]; ++i)
-        out[M->cell_cv_off[c] + i] = tmp[((int64_t)M->row_base[L / kLanes] + i) * kLanes + L % kLanes];
+        out[M->cell_cv_off[c] + i] =
+            tmp[g < M->n_narrow ? ((int64_t)M->row_base[g] + i) * kLanes + L % kLanes
+                                : ((int64_t)M->row_base[g] << 5) + i];
     }
     return PA_OK;
   }
@@ -1398,7 +1514,7 @@ int pa_model_info(const pa_model* M, pa_info* info) {
   info->epoch_steps = M->E;
   info->precision = M->precision;
   info->tree = M->tree ? 1 : 0;
-  info->reserved = 0;
+  info->n_wide = (int32_t)M->n_wide;
   info->n_streams = M->n_streams;
   info->shape = M->shape;
   info->device_bytes = (int64_t)M->dbytes;
@@ -1466,6 +1582,9 @@ void pa_free_model(pa_model* M) {
   if (M->graph1) cudaGraphExecDestroy(M->graph1);
   if (M->graph8) cudaGraphExecDestroy(M->graph8);
   if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
+  if (M->side_stream) cudaStreamDestroy(M->side_stream);
+  if (M->ev_fork) cudaEventDestroy(M->ev_fork);
+  if (M->ev_join) cudaEventDestroy(M->ev_join);
   delete M;
 }
 

@@ -3,10 +3,11 @@
 // voltage, cable coefficients, assembly, Hines solve, HH, calcium (a threshold
 // variable) and the slow plasticity state in FP64.
 #include "epoch_kernel.cuh"
+#include "wide_kernel.cuh"
 
 namespace pa {
-int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream) {
-  return launch_epoch_impl<float>(a, tree, shape, stream);
+int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream, const SideLaunch* side) {
+  return launch_bins<float>(a, tree, shape, stream, side);
 }
 int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes,
                            const uint8_t* is_hh, void* stream) {

@@ -1,0 +1,340 @@
+// wide_kernel.cuh -- the epoch kernel for the wide cell bin: one warp per cell.
+//
+// A large cell whose own rows and synapses would keep one thread busy for a
+// whole step (thousands of serial rows or synapses) runs on all 32 lanes of a
+// warp.  The cell's CVs are contiguous (element (row_base << 5) + i for CV i),
+// as are its synapses in each stream.
+//
+// Per step, in the same order and with the same operations as the narrow
+// kernel (epoch_kernel.cuh), so that both equal the plain definition:
+//   a. synapse streams: lanes update 32 synapses at a time in parallel
+//      (events, POST_EVENT, plasticity; syn_update); the per-CV sums and the
+//      cell's STC sum S are then folded in canonical synapse order, every lane
+//      reading the 32 values by shuffle, so the sums are the sequential ones;
+//   b. backward pass by branches: a branch is a maximal run of rows i whose
+//      parent is i - 1 (contiguous in the numbering).  Branches are scheduled
+//      by level (a branch's level exceeds that of every branch hanging off
+//      it); the branches of one level run on the lanes in parallel, each
+//      eliminated row by row from its last row to its first, children applied
+//      in descending index order exactly as in the narrow kernel; a warp
+//      barrier separates levels.  The root branch (CV 0, the soma) is the only
+//      branch of the top level and runs on lane 0;
+//   c. forward pass by levels from the root down; a branch starts from its
+//      parent's new voltage (written one level earlier);
+//   d. soma on lane 0: HH gates, detection, spike record.
+#pragma once
+#include "epoch_kernel.cuh"
+
+namespace pa {
+
+template <class TM>
+__global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (w >= A.n_wide) return;  // whole warps only
+  const int g = A.n_narrow + w;
+  const int64_t L = (int64_t)g * 32;  // the cell's lane slot
+  const int n = A.ncv[L];
+  const int64_t e0 = (int64_t)A.row_base[g] << 5;  // element of CV 0
+  const WideCell wc = A.wcell[w];
+  const double dt = A.dt;
+  using HH = HH64;
+
+  double* __restrict__ Vg = A.V;
+  const double* __restrict__ CDT = A.cdt;
+  const double* __restrict__ DC = A.dc;
+  const double* __restrict__ EM = A.em;
+  const double* __restrict__ AA = A.a;
+  TM* __restrict__ GS = (TM*)A.gs;
+  TM* __restrict__ ES = (TM*)A.es;
+  double* __restrict__ F = A.f;
+  double* __restrict__ XP = A.xp;
+  const int16_t* __restrict__ PAR = A.par;
+  const int16_t* __restrict__ OCH = A.och_head;
+  const int16_t* __restrict__ OCN = A.och_next;
+
+  // soma state: lane 0 owns it (every lane keeps prp and the POST_EVENT flag)
+  const bool hh = n > 0 && A.is_hh[L];
+  double gm_ = 0, gh_ = 0, gn_ = 0;
+  if (hh && lane == 0) {
+    gm_ = A.gate[L]; gh_ = A.gate[A.n_lanes + L]; gn_ = A.gate[2 * A.n_lanes + L];
+  }
+  const double iinj_val = n > 0 ? A.iinj[L] : 0.0;
+  const int64_t kon = n > 0 ? A.k_on[L] : 0, koff = n > 0 ? A.k_off[L] : 0;
+  const double th = n > 0 ? A.thresh[L] : 0.0;
+  bool spiked_prev = n > 0 && A.spiked_prev[L];
+  double prp = (n > 0 && A.stc_stream >= 0) ? A.prp[L] : 0.0;
+  const bool has_stc = n > 0 && A.stc_stream >= 0 && A.has_stc[L];
+  const uint64_t rbits = (A.replay && n > 0) ? A.replay_bits[L] : 0ull;
+  const int32_t pq0 = n > 0 ? A.probe_ptr[L] : 0, pq1 = n > 0 ? A.probe_ptr[L + 1] : 0;
+
+  int64_t k_begin = A.k_begin, k_end = A.k_end, k0 = A.k0, probe0 = A.probe_sample0;
+  int32_t slot = A.slot;
+  if (A.clock) {
+    k0 = A.clock->k0;
+    k_begin = k0;
+    k_end = k0 + A.epoch_len;
+    probe0 = A.clock->probe_sample0;
+    slot = (int32_t)((k0 / A.epoch_len) % A.n_slots);
+  }
+  for (int64_t k = k_begin; k < k_end && n > 0; ++k) {
+    const int kk = (int)(k - k0);
+    const bool post = spiked_prev;
+    // ---- a. synapse streams ---------------------------------------------------
+    double S = 0.0;
+    for (int s = 0; s < A.n_streams; ++s) {
+      const StreamParams& P = A.sp[s];
+      const StreamDev& D = A.sd[s];
+      const int32_t sb = D.sbase[g], nrow = D.sbase[g + 1] - sb;
+      const bool calc = P.kind == SK_GB || P.kind == SK_STC;
+      const bool stc = P.kind == SK_STC;
+      const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
+      const uint64_t* camg = calc ? D.camask + (int64_t)slot * D.n_elem : nullptr;
+      TM* G = (TM*)D.g;
+      const TM E = (TM)P.e;
+      const TM dg = (TM)P.decay_g;
+      TM carry_g = 0, carry_e = 0;  // sums of the run crossing into the next row
+      for (int t = 0; t < nrow; ++t) {
+        const uint32_t e = ((uint32_t)(sb + t) << 5) | (uint32_t)lane;
+        const int32_t cvf = D.cvf[e];
+        const bool valid = cvf >= 0;  // padding only after the cell's last synapse
+        TM gv = 0;
+        double sadd = 0.0;
+        if (valid) {
+          const bool pre = (cmg[e] >> kk) & 1ull;
+          const bool capre = calc && ((camg[e] >> kk) & 1ull);
+          const double cc = calc ? D.c[e] : 0.0;
+          const double wv = calc ? D.w[e] : 0.0;
+          const double zv = stc ? D.z[e] : 0.0;
+          gv = syn_update<TM>(P, D, e, pre, capre, post, G[e], cc, wv, zv, prp, k, dt, sadd);
+          G[e] = gv * dg;
+        }
+        // Per-CV sums in canonical order (run_sum's arithmetic): each lane sums
+        // its run from the run's first synapse in this row up to itself, in
+        // order, reading the values by shuffle; a run that crosses rows
+        // continues from the last lane's sums of the previous row.
+        const TM ge = tm_mul(gv, E);
+        const unsigned smask = __ballot_sync(full, valid && (cvf & 2));
+        const unsigned upto = lane == 31 ? full : ((2u << lane) - 1u);
+        const unsigned mm = smask & upto;
+        const int seg0 = mm ? 31 - __clz(mm) : -1;
+        const int src0 = seg0 < 0 ? 0 : seg0;
+        const int len = valid ? lane - src0 + 1 : 0;
+        const int maxlen = (int)__reduce_max_sync(full, (unsigned)len);
+        const int32_t cs = __shfl_sync(full, cvf, src0);
+        TM acc = __shfl_sync(full, gv, src0), ace = __shfl_sync(full, ge, src0);
+        if (seg0 < 0) {
+          acc = tm_add(carry_g, acc);
+          ace = tm_add(carry_e, ace);
+        } else if (valid && !(cs & 1)) {
+          const int64_t cs_e = e0 + (cs >> 3);  // continues the sums of earlier streams
+          acc = tm_add(GS[cs_e], acc);
+          ace = tm_add(ES[cs_e], ace);
+        }
+        for (int it = 1; it < maxlen; ++it) {
+          const int src = src0 + it < 31 ? src0 + it : 31;
+          const TM gi = __shfl_sync(full, gv, src), ei = __shfl_sync(full, ge, src);
+          if (it < len) {
+            acc = tm_add(acc, gi);
+            ace = tm_add(ace, ei);
+          }
+        }
+        if (valid && (cvf & 4)) {
+          GS[e0 + (cvf >> 3)] = acc;
+          ES[e0 + (cvf >> 3)] = ace;
+        }
+        carry_g = __shfl_sync(full, acc, 31);
+        carry_e = __shfl_sync(full, ace, 31);
+        if (stc) {
+          // the cell's S = sum |h - h0| over its STC synapses, in order
+#pragma unroll 1
+          for (int q = 0; q < 32; ++q) {
+            const double sq = __shfl_sync(full, sadd, q);
+            if (__shfl_sync(full, cvf, q) >= 0) S = S + sq;
+          }
+        }
+      }
+      __syncwarp();  // this stream's sums are visible to later streams and the solve
+      if (s == A.stc_stream && has_stc) {
+        const double qs = (S > P.theta_pro) ? P.p_max : 0.0;
+        prp = prp + P.rate_p * (qs - prp);
+      }
+    }
+
+    // ---- b. backward pass by branch levels ---------------------------------------
+    double v0_old = 0.0, v0_new = 0.0;
+    const double iinj = (k >= kon && k < koff) ? iinj_val : 0.0;
+    for (int lv = 0; lv < wc.n_lvl; ++lv) {
+      const int b0 = A.wlvl[wc.lvl0 + lv], b1 = A.wlvl[wc.lvl0 + lv + 1];
+      for (int b = b0 + lane; b < b1; b += 32) {
+        const int bs = A.wbr_s[wc.br0 + b], be = A.wbr_e[wc.br0 + b];
+        double cf = 0.0, ca = 0.0, cx = 0.0;
+        bool carry = false;
+        // one row of lookahead: the next row's values load during this row's
+        // elimination
+        double nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be], nem = EM[e0 + be],
+               na = AA[e0 + be];
+        TM ngs = GS[e0 + be], nes = ES[e0 + be];
+        int noch = PAR ? OCH[e0 + be] : -1;
+        for (int i = be; i >= bs; --i) {
+          const int64_t ei = e0 + i;
+          const double v = nv, cdt = ncdt, dcv = ndc, emv = nem, ai = na;
+          const double gsv = widen_f32(ngs);
+          const double esv = widen_f32(nes);
+          const int och = noch;
+          if (i > bs) {
+            const int64_t en = ei - 1;
+            nv = Vg[en]; ncdt = CDT[en]; ndc = DC[en]; nem = EM[en]; na = AA[en];
+            ngs = GS[en]; nes = ES[en];
+            if (PAR) noch = OCH[en];
+          }
+          double d, bb;
+          if (i == 0) {
+            v0_old = v;
+            if (hh) {
+              const double gna = __ldg(&A.hh_g[L]), gk = __ldg(&A.hh_g[A.n_lanes + L]),
+                           gl = __ldg(&A.hh_g[2 * A.n_lanes + L]);
+              const double ena = __ldg(&A.hh_e[L]), ek = __ldg(&A.hh_e[A.n_lanes + L]),
+                           el = __ldg(&A.hh_e[2 * A.n_lanes + L]);
+              const double mmmh = ((gm_ * gm_) * gm_) * gh_;
+              const double nnnn = ((gn_ * gn_) * gn_) * gn_;
+              const double g1 = gna * mmmh;
+              const double g2 = gk * nnnn;
+              const double gmt = (g1 + g2) + gl;
+              const double emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
+              d = (dcv + gmt) + gsv;
+              bb = (fma(cdt, v, emt) + iinj) + esv;
+            } else {
+              d = dcv + gsv;
+              bb = (fma(cdt, v, emv) + iinj) + esv;
+            }
+          } else {
+            d = dcv + gsv;
+            bb = fma(cdt, v, emv) + esv;
+          }
+          if (PAR) {
+            // other children, highest index first (eliminated at lower levels)
+            for (int ch = och; ch >= 0; ch = OCN[e0 + ch]) {
+              const int64_t ec = e0 + ch;
+              const double ac = AA[ec];
+              d = fma(-F[ec], ac, d);
+              bb = fma(-ac, XP[ec], bb);
+            }
+          }
+          if (carry) {
+            d = fma(-cf, ca, d);
+            bb = fma(-ca, cx, bb);
+          }
+          if (i > 0) {
+            const double rr = rcp_rn_pos(d);
+            const double fi = ai * rr;
+            const double xi = bb * rr;
+            F[ei] = fi;
+            XP[ei] = xi;
+            carry = true;  // row i - 1 of this branch has i as its first child
+            cf = fi; ca = ai; cx = xi;
+          } else {
+            v0_new = bb * rcp_rn_pos(d);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // ---- c. forward pass, root level first ------------------------------------------
+    for (int lv = wc.n_lvl - 1; lv >= 0; --lv) {
+      const int b0 = A.wlvl[wc.lvl0 + lv], b1 = A.wlvl[wc.lvl0 + lv + 1];
+      for (int b = b0 + lane; b < b1; b += 32) {
+        const int bs = A.wbr_s[wc.br0 + b], be = A.wbr_e[wc.br0 + b];
+        double vp;
+        int i = bs;
+        if (bs == 0) {
+          Vg[e0] = v0_new;
+          vp = v0_new;
+          i = 1;
+        } else {
+          vp = Vg[e0 + PAR[e0 + bs]];
+        }
+        double nf = i <= be ? F[e0 + i] : 0.0, nx = i <= be ? XP[e0 + i] : 0.0;
+        for (; i <= be; ++i) {
+          const int64_t ei = e0 + i;
+          const double fi = nf, xi = nx;
+          if (i < be) {
+            nf = F[ei + 1];
+            nx = XP[ei + 1];
+          }
+          const double vi = fma(-fi, vp, xi);
+          Vg[ei] = vi;
+          vp = vi;
+        }
+      }
+      __syncwarp();
+    }
+    for (int32_t q = pq0 + lane; q < pq1; q += 32) {
+      const int64_t smp = probe0 + (k - k_begin);
+      if (smp < A.probe_cap) {
+        A.probe_buf[smp * A.n_probe + A.probe_id[q]] = Vg[e0 + A.probe_row[q]];
+      } else {
+        atomicOr(A.err_flags, 1);
+      }
+    }
+    // ---- d. soma gates, detection (lane 0) -------------------------------------------
+    bool spk = false;
+    if (lane == 0) {
+      if (hh) {
+        double am, bm, ah, bh, an, bn;
+        HH::rates(v0_new, am, bm, ah, bh, an, bn);
+        gm_ = HH::gate(gm_, am, bm, dt);
+        gh_ = HH::gate(gh_, ah, bh, dt);
+        gn_ = HH::gate(gn_, an, bn, dt);
+      }
+      spk = v0_old < th && v0_new >= th;
+      if (spk) {
+        const int slot_ = atomicAdd(A.spk_count, 1);
+        if (slot_ < A.spk_cap) {
+          A.spk_gid[slot_] = A.gid[L];
+          A.spk_step[slot_] = (int32_t)k;
+          A.spk_t[slot_] = (double)k * dt + dt * ((th - v0_old) / (v0_new - v0_old));
+        }
+      }
+    }
+    spk = __shfl_sync(full, spk, 0);
+    spiked_prev = A.replay ? (((rbits >> (k - k_begin)) & 1ull) != 0) : spk;
+  }
+  if (n > 0 && lane == 0) {
+    A.spiked_prev[L] = spiked_prev ? 1 : 0;
+    if (hh) {
+      A.gate[L] = gm_; A.gate[A.n_lanes + L] = gh_; A.gate[2 * A.n_lanes + L] = gn_;
+    }
+    if (has_stc) A.prp[L] = prp;
+  }
+}
+
+template <class TM>
+int launch_wide_impl(const EpochArgs& a, void* stream) {
+  if (a.n_wide <= 0) return 0;
+  const int threads = 128;
+  const int blocks = (int)(((int64_t)a.n_wide * 32 + threads - 1) / threads);
+  wide_kernel<TM><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+// Both cell bins of one epoch (see SideLaunch).
+template <class TM>
+int launch_bins(const EpochArgs& a, bool tree, int shape, void* stream, const SideLaunch* side) {
+  if (side && a.n_narrow > 0 && a.n_wide > 0) {
+    cudaStream_t s0 = (cudaStream_t)stream, s1 = (cudaStream_t)side->stream;
+    cudaError_t e = cudaEventRecord((cudaEvent_t)side->fork, s0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, (cudaEvent_t)side->fork, 0);
+    if (e != cudaSuccess) return (int)e;
+    int rc = launch_epoch_impl<TM>(a, tree, shape, stream);
+    if (rc == 0) rc = launch_wide_impl<TM>(a, side->stream);
+    e = cudaEventRecord((cudaEvent_t)side->join, s1);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, (cudaEvent_t)side->join, 0);
+    return rc ? rc : (int)e;
+  }
+  const int rc = launch_epoch_impl<TM>(a, tree, shape, stream);
+  return rc ? rc : launch_wide_impl<TM>(a, stream);
+}
+
+}  // namespace pa

@@ -60,6 +60,8 @@ class KernelStats(C.Structure):
 FLAG_TIME_KERNELS = 1
 FLAG_AUTOTUNE = 2
 FLAG_NO_GRAPHS = 8
+FLAG_NARROW_ONLY = 16
+FLAG_WIDE_ALL = 32
 N_SHAPES = 5
 
 
@@ -72,7 +74,7 @@ class Info(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_cv", C.c_int64), ("n_conn", C.c_int64),
                 ("n_groups", C.c_int64), ("n_padded_cv", C.c_int64), ("step", C.c_int64),
                 ("epoch_steps", C.c_int32), ("precision", C.c_int32), ("tree", C.c_int32),
-                ("n_streams", C.c_int32), ("shape", C.c_int32), ("reserved", C.c_int32),
+                ("n_streams", C.c_int32), ("shape", C.c_int32), ("n_wide", C.c_int32),
                 ("device_bytes", C.c_int64), ("n_static_cv", C.c_int64)]
 
 

@@ -301,3 +301,61 @@ def test_busyring_fp64_bit_exact(stdp):
     go, _, _ = o.spikes()
     assert len(go) == 48 * 2          # every cell fires once per 20 ms lap
     check_state(o, m, E.PA_FP64, exact=True)
+
+
+def _bin_run(net, precision, flags, probes):
+    m = E.Model(net, precision=precision, probes=probes, flags=flags, probe_capacity=4000)
+    steps = 0
+    for n in (13, 250, 400, 97):              # partial and whole epochs
+        steps += n
+        m.advance(steps * net.dt)
+    m.sync()
+    out = [m.read_state(E.FIELD_V), m.read_probes(len(probes)), m.read_weights(),
+           m.read_state(E.FIELD_G), m.read_state(E.FIELD_GATES), m.read_state(E.FIELD_PRP)]
+    out += list(m.read_spikes())
+    n_wide = m.info().n_wide
+    m.close()
+    return out, n_wide
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+@pytest.mark.parametrize("which", ["trees", "edge", "busyring_stdp", "recurrent_stc"])
+def test_wide_bin_equals_narrow_bin(precision, which):
+    """Cells on a whole warp (synapses 32 at a time with an ordered fold, the tree
+    eliminated branch-parallel by levels) give bit-identical states, probes,
+    spikes and weights to cells on one thread each."""
+    net = {"trees": lambda: tiny_tree_net(n_cells=40),
+           "edge": edge_net,
+           "busyring_stdp": lambda: W.busyring(n_cells=24, depth=3, s=60, stdp=True),
+           "recurrent_stc": lambda: W.recurrent_stc(n_exc=64, n_inh=16)}[which]()
+    ncv = net.cell_ncv()
+    mid = net.n_cells // 2
+    probes = [(0, 0), (net.n_cells - 1, int(ncv[-1]) - 1), (mid, int(ncv[mid]) // 2)]
+    a, na = _bin_run(net, precision, E.FLAG_NARROW_ONLY, probes)
+    b, nb = _bin_run(net, precision, E.FLAG_WIDE_ALL, probes)
+    assert na == 0 and nb == net.n_cells
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_wide_bin_fp64_matches_oracle_and_automatic_bins():
+    """The wide bin against the oracle, bit for bit, on the edge cases (non-DFS
+    numbering, several synapse kinds on one CV, point cells); the automatic rule
+    puts small busyring networks on whole warps and keeps large networks narrow."""
+    net = edge_net()
+    o = O.Oracle(net)
+    o.run(3001)
+    m = E.Model(net, precision=E.PA_FP64, flags=E.FLAG_WIDE_ALL)
+    for n in (1000, 2001, 3001):
+        m.advance(n * net.dt)
+    m.sync()
+    check_state(o, m, E.PA_FP64, exact=True)
+    ring = W.busyring(n_cells=64, depth=10, s=100)
+    ncv = ring.cell_ncv()
+    nsyn = np.bincount(ring.conn_dst, minlength=ring.n_cells)
+    nbr = np.array([1 + int(np.sum(m.parent[1:] != np.arange(m.n_cv - 1))) for m in ring.morphs])
+    want = (ncv >= 128) & (nbr[ring.cell_morph] >= 8) & (nsyn <= 2 * ncv)
+    assert E.Model(ring, precision=E.PA_MIXED).info().n_wide == int(want.sum()) > 32
+    dense = W.busyring(n_cells=64, depth=2, s=100)   # 100 synapses on ~45 CVs: narrow
+    assert E.Model(dense, precision=E.PA_MIXED).info().n_wide == 0
+    assert E.Model(tiny_tree_net(n_cells=40), precision=E.PA_MIXED).info().n_wide == 0
