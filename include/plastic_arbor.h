@@ -181,7 +181,8 @@ typedef struct {
  * updated 32 at a time, its tree eliminated branch-parallel by levels).  By
  * default, when the narrow bin alone would leave fewer than 4 warps per SM,
  * cells with at least 128 CVs in at least 8 branches and at most 2 synapses
- * per CV are wide.  Both bins give identical results.  NARROW_ONLY / WIDE_ALL
+ * per CV are wide; below 1 warp per SM, every cell with at least 128 CVs plus
+ * synapses is.  Both bins give identical results.  NARROW_ONLY / WIDE_ALL
  * force every cell into one bin. */
 #define PA_FLAG_NARROW_ONLY 16
 #define PA_FLAG_WIDE_ALL 32

@@ -68,16 +68,18 @@ struct WideCell {
   int32_t pad;
 };
 
-// Cell bins: when the narrow bin alone would give fewer than
+// Cell bins.  When the narrow bin alone would give fewer than
 // kWideMaxWarpsPerSM warps per SM, the wide bin takes the cells with at least
 // kWideMinCV CVs in at least kWideMinBranches branches and at most
 // kWideMaxSynPerCV synapses per CV (the per-CV sums are serial runs, so a
-// cell whose synapses crowd onto few CVs gains nothing from a warp); every
-// cell with PA_FLAG_WIDE_ALL.
+// cell whose synapses crowd onto few CVs gains less from a warp).  Below one
+// warp per SM the GPU is mostly idle in the narrow bin, and every cell with at
+// least kWideMinWork CVs plus synapses is wide.  PA_FLAG_WIDE_ALL: every cell.
 constexpr int kWideMinCV = 128;
 constexpr int kWideMinBranches = 8;
 constexpr int kWideMaxSynPerCV = 2;
 constexpr int kWideMaxWarpsPerSM = 4;
+constexpr int kWideMinWork = 128;
 
 struct EpochArgs {
   // launch window: steps [k_begin, k_end) all inside epoch [k0, k0 + E); with

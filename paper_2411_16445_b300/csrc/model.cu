@@ -403,12 +403,16 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         morph_branches[j] += (i == 0 || morphs[j].parent[i] != i - 1) ? 1 : 0;
     int n_sm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, M->device));
-    const bool few = (n_cells + kLanes - 1) / kLanes < (int64_t)kWideMaxWarpsPerSM * n_sm;
-    for (int64_t c = 0; c < n_cells; ++c)
+    const int64_t warps = (n_cells + kLanes - 1) / kLanes;
+    const bool few = warps < (int64_t)kWideMaxWarpsPerSM * n_sm, idle = warps < n_sm;
+    for (int64_t c = 0; c < n_cells; ++c) {
+      const bool branched = M->cell_ncv[c] >= kWideMinCV &&
+                            morph_branches[cells[c].morph] >= kWideMinBranches &&
+                            cell_syn[c] <= (int64_t)kWideMaxSynPerCV * M->cell_ncv[c];
+      const bool heavy = M->cell_ncv[c] + cell_syn[c] >= kWideMinWork;
       wide[c] = (opt->flags & PA_FLAG_WIDE_ALL) ||
-                (!(opt->flags & PA_FLAG_NARROW_ONLY) && few && M->cell_ncv[c] >= kWideMinCV &&
-                 morph_branches[cells[c].morph] >= kWideMinBranches &&
-                 cell_syn[c] <= (int64_t)kWideMaxSynPerCV * M->cell_ncv[c]);
+                (!(opt->flags & PA_FLAG_NARROW_ONLY) && ((few && branched) || (idle && heavy)));
+    }
   }
   // narrow cells sorted by CV count (descending) and dealt into groups of 32
   // lanes; then one group per wide cell (its cell in lane 0, CVs contiguous)
@@ -537,24 +541,31 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   }
 
   // ---- branch tables of the wide cells ------------------------------------------
-  // A branch is a maximal run of rows i whose parent is i - 1 (rows are
-  // contiguous).  A branch's level exceeds that of every branch starting at a
-  // child of one of its rows, so a level only needs lower levels eliminated;
-  // the root branch (row 0) is then the only branch of the top level.
+  // A branch is a run of rows i whose parent is i - 1 (rows are contiguous),
+  // cut after every fork.  A branch's level exceeds that of every branch
+  // starting at a child of one of its rows, so a level only needs lower levels
+  // eliminated; the root branch (row 0) is then the only branch of the top
+  // level.
   std::vector<WideCell> h_wcell(n_wide);
   std::vector<int32_t> h_wbr_s, h_wbr_e, h_wlvl;
   for (int64_t j = 0; j < n_wide; ++j) {
     const pa_morphology& gm = morphs[cells[order_w[j]].morph];
     const int n = gm.n_cv;
+    std::vector<int32_t> nchild(n, 0);
+    for (int i = 1; i < n; ++i) ++nchild[gm.parent[i]];
+    // a new branch starts at row 0, at a row whose parent is not the row
+    // before, and after every fork (a row with two or more children)
+    std::vector<char> is_start(n, 0);
     std::vector<int32_t> bstart, bidx(n);
     for (int i = 0; i < n; ++i) {
-      if (i == 0 || gm.parent[i] != i - 1) bstart.push_back(i);
+      is_start[i] = i == 0 || gm.parent[i] != i - 1 || nchild[i - 1] >= 2;
+      if (is_start[i]) bstart.push_back(i);
       bidx[i] = (int32_t)bstart.size() - 1;
     }
     const int nb = (int)bstart.size();
     std::vector<int32_t> lvl(nb, 0);
     for (int i = n - 1; i >= 1; --i) {
-      if (gm.parent[i] == i - 1) continue;
+      if (!is_start[i]) continue;
       int32_t& up = lvl[bidx[gm.parent[i]]];
       up = std::max(up, lvl[bidx[i]] + 1);
     }

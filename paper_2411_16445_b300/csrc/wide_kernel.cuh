@@ -11,8 +11,10 @@
 //      (events, POST_EVENT, plasticity; syn_update); the per-CV sums and the
 //      cell's STC sum S are then folded in canonical synapse order, every lane
 //      reading the 32 values by shuffle, so the sums are the sequential ones;
-//   b. backward pass by branches: a branch is a maximal run of rows i whose
-//      parent is i - 1 (contiguous in the numbering).  Branches are scheduled
+//   b. backward pass by branches: a branch is a run of rows i whose parent is
+//      i - 1 (contiguous in the numbering), cut after every fork; at a fork the
+//      first child's values come from memory like the other children's, applied
+//      last as in the narrow kernel.  Branches are scheduled
 //      by level (a branch's level exceeds that of every branch hanging off
 //      it); the branches of one level run on the lanes in parallel, each
 //      eliminated row by row from its last row to its first, children applied
@@ -225,6 +227,11 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           if (carry) {
             d = fma(-cf, ca, d);
             bb = fma(-ca, cx, bb);
+          } else if (i == be && PAR && i + 1 < n && PAR[ei + 1] == i) {
+            // a fork: the first child starts a branch of a lower level
+            const double ac = AA[ei + 1];
+            d = fma(-F[ei + 1], ac, d);
+            bb = fma(-ac, XP[ei + 1], bb);
           }
           if (i > 0) {
             const double rr = rcp_rn_pos(d);

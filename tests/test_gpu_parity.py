@@ -350,12 +350,15 @@ def test_wide_bin_fp64_matches_oracle_and_automatic_bins():
         m.advance(n * net.dt)
     m.sync()
     check_state(o, m, E.PA_FP64, exact=True)
-    ring = W.busyring(n_cells=64, depth=10, s=100)
+    # between one and four narrow warps per SM: only large branched sparse cells
+    ring = W.busyring(n_cells=6000, depth=10, s=30, n_shapes=256)
     ncv = ring.cell_ncv()
     nsyn = np.bincount(ring.conn_dst, minlength=ring.n_cells)
     nbr = np.array([1 + int(np.sum(m.parent[1:] != np.arange(m.n_cv - 1))) for m in ring.morphs])
     want = (ncv >= 128) & (nbr[ring.cell_morph] >= 8) & (nsyn <= 2 * ncv)
-    assert E.Model(ring, precision=E.PA_MIXED).info().n_wide == int(want.sum()) > 32
-    dense = W.busyring(n_cells=64, depth=2, s=100)   # 100 synapses on ~45 CVs: narrow
-    assert E.Model(dense, precision=E.PA_MIXED).info().n_wide == 0
+    assert E.Model(ring, precision=E.PA_MIXED).info().n_wide == int(want.sum()) > 3000
+    # below one narrow warp per SM, cells with 128+ CVs plus synapses are wide too
+    dense = W.busyring(n_cells=64, depth=2, s=100)
+    heavy = dense.cell_ncv() + np.bincount(dense.conn_dst, minlength=dense.n_cells) >= 128
+    assert E.Model(dense, precision=E.PA_MIXED).info().n_wide == int(heavy.sum())
     assert E.Model(tiny_tree_net(n_cells=40), precision=E.PA_MIXED).info().n_wide == 0
