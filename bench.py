@@ -167,6 +167,21 @@ def dist_setup():
     return ws, rank, local
 
 
+def replica_total(ms_local, cu_per_rank, ws, device=None):
+    """Replicas (one independent network per rank, no data-path collective): the
+    job's time is the slowest rank's, and the job processed ws x cu_per_rank
+    compartment-updates.  Returns (max ms over ranks, whole-job CU/s)."""
+    ms = ms_local
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64,
+                         device=f"cuda:{device}" if device is not None else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, cu_per_rank * ws / (ms * 1e-3)
+
+
 def model_flags(args):
     from paper_2411_16445_b300 import engine as E
     f = E.FLAG_TIME_KERNELS
@@ -489,13 +504,8 @@ def main():
     head = order[0]
     r = runs[head]
     ms = r["ms"]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=f"cuda:{device}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     cu_per_rank = r["n_cv"] * r["epoch_steps"] * args.steps
-    value = cu_per_rank * ws / (ms * 1e-3)
+    ms, value = replica_total(ms, cu_per_rank, ws, device)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
