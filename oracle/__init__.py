@@ -24,7 +24,7 @@ def lib():
         P = C.c_void_p
         L.orc_build.restype = C.c_int
         L.orc_build.argtypes = ([C.c_int32] + [P] * 10 + [C.c_int32] + [P] * 6 + [C.c_int32]
-                                + [P] * 3 + [C.c_int64] + [P] * 8
+                                + [P] * 3 + [C.c_int64] + [C.c_int64] + [P] * 8
                                 + [C.c_double, C.c_uint64, C.c_int32, P, P, P])
         L.orc_run.argtypes = [P, C.c_int64]
         L.orc_set_replay.argtypes = [P, C.c_int64, P, P]
@@ -47,6 +47,12 @@ def lib():
         L.orc_threefry4x64_12.argtypes = [P, P, P]
         L.orc_poisson_u32.restype = C.c_uint32
         L.orc_poisson_u32.argtypes = [C.c_uint64, C.c_uint64, C.c_int64]
+        L.orc_log.restype = C.c_double
+        L.orc_log.argtypes = [C.c_double]
+        L.orc_cis2pi.restype = C.c_double
+        L.orc_cis2pi.argtypes = [C.c_double, C.c_int]
+        L.orc_normal.restype = C.c_double
+        L.orc_normal.argtypes = [C.c_uint64, C.c_uint64, C.c_int64]
         _lib = L
     return _lib
 
@@ -80,7 +86,7 @@ class Oracle:
             arr(net.cell_vinit, np.float64), arr(net.cell_thresh, np.float64),
             len(net.morphs), arr(ncv, np.int32), arr(moff, np.int32), arr(par, np.int32),
             arr(ln, np.float64), arr(dm, np.float64), arr(reg, np.int32),
-            len(mk), arr(mk, np.int32), arr(mo, np.int32), arr(mp, np.float64),
+            len(mk), arr(mk, np.int32), arr(mo, np.int32), arr(mp, np.float64), len(mp),
             net.n_conn, arr(net.conn_src, np.int32), arr(net.conn_dst, np.int32),
             arr(net.conn_cv, np.int32), arr(net.conn_mech, np.int32),
             arr(net.conn_weight, np.float64), arr(net.conn_delay, np.float64),
@@ -185,3 +191,16 @@ def threefry(ctr, key):
 
 def poisson_u32(seed: int, stream: int, step: int) -> int:
     return lib().orc_poisson_u32(seed & (2**64 - 1), stream, step)
+
+
+def log(x: float) -> float:
+    return lib().orc_log(float(x))
+
+
+def cis2pi(v: float, which: int) -> float:
+    """cos(2 pi v) (which = 0) or sin(2 pi v) (which = 1), the model's own."""
+    return lib().orc_cis2pi(float(v), int(which))
+
+
+def normal(seed: int, noise_id: int, step: int) -> float:
+    return lib().orc_normal(seed & (2**64 - 1), noise_id, step)

@@ -206,6 +206,100 @@ uint32_t orc_poisson_u32(uint64_t seed, uint64_t stream, int64_t step) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Plasticity noise (Eqs. plasticity_noise_1, plasticity_noise_2; Sec.
+ * "Computation with stochastic differential equations"): Euler-Maruyama with
+ * Delta W = sqrt(dt) N(0,1), the normal deviates by the Box-Muller method from
+ * Threefry-4x64-12 uniforms.  The model defines its own logarithm and circular
+ * functions (below) so that the deviates are reproducible to the last bit. */
+
+/* Natural logarithm of x > 0 (normal): x = m 2^e with m in [sqrt(1/2), sqrt(2)),
+ * log m = 2 atanh(s), s = (m - 1)/(m + 1), by the odd series
+ * s + s^3/3 + ... + s^23/23 in Horner form with fused multiply-adds (|s| < 0.172,
+ * so the first omitted term is below 2^-60 relative); e ln2 is added with ln2
+ * split into the exponential's 32-bit head and tail.  The coefficients are
+ * 1/k rounded to double. */
+double orc_log(double x) {
+  static const double c[12] = {0.043478260869565216, 0.047619047619047616, 0.05263157894736842,
+                               0.058823529411764705, 0.06666666666666667, 0.07692307692307693,
+                               0.09090909090909091, 0.1111111111111111, 0.14285714285714285,
+                               0.2, 0.3333333333333333, 1.0};
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  int e = (int)((b >> 52) & 0x7ff) - 1022;
+  b = (b & 0x800fffffffffffffULL) | (1022ULL << 52); /* m in [0.5, 1) */
+  double m;
+  memcpy(&m, &b, 8);
+  if (m < 0.70710678118654752440) {
+    m = m * 2.0;
+    e = e - 1;
+  }
+  double s = (m - 1.0) / (m + 1.0);
+  double s2 = s * s;
+  double p = c[0];
+  for (int i = 1; i < 12; ++i) p = fma(p, s2, c[i]);
+  double t = s * p;
+  double lm = t + t;
+  double ed = (double)e;
+  double hi = ed * 6.93147180369123816490e-01;
+  return hi + fma(ed, 1.9082149292705877e-10, lm);
+}
+
+/* cos(2 pi v) (which = 0) or sin(2 pi v) (which = 1) for v in [0, 1): the
+ * quadrant q = rint(4v) and the remainder r = v - q/4 (|r| <= 1/8) are exact
+ * in binary; t = 2 pi r by one rounded product; the Taylor series of sin t
+ * (to t^21) and cos t (to t^22) in Horner form with fused multiply-adds
+ * (|t| <= pi/4); coefficients (-1)^k / n! rounded to double. */
+double orc_cis2pi(double v, int which) {
+  static const double sc[10] = {1.9572941063391263e-20, -8.22063524662433e-18,
+                                2.8114572543455206e-15, -7.647163731819816e-13,
+                                1.6059043836821613e-10, -2.505210838544172e-08,
+                                2.7557319223985893e-06, -0.0001984126984126984,
+                                0.008333333333333333, -0.16666666666666666};
+  static const double cc[11] = {-8.896791392450574e-22, 4.110317623312165e-19,
+                                -1.5619206968586225e-16, 4.779477332387385e-14,
+                                -1.1470745597729725e-11, 2.08767569878681e-09,
+                                -2.755731922398589e-07, 2.48015873015873e-05,
+                                -0.001388888888888889, 0.041666666666666664, -0.5};
+  double q = rint(4.0 * v);
+  double r = v - 0.25 * q;
+  double t = r * 6.283185307179586;
+  double t2 = t * t;
+  int quad = ((int)q) & 3;
+  /* sin(t + quad pi/2) and cos(t + quad pi/2) from sin t and cos t */
+  int want_sin = which ? (quad == 0 || quad == 2) : (quad == 1 || quad == 3);
+  double val;
+  if (want_sin) {
+    double sp = sc[0];
+    for (int i = 1; i < 10; ++i) sp = fma(sp, t2, sc[i]);
+    val = fma(sp * t2, t, t);
+  } else {
+    double cp = cc[0];
+    for (int i = 1; i < 11; ++i) cp = fma(cp, t2, cc[i]);
+    val = fma(cp, t2, 1.0);
+  }
+  /* signs: cos: +cos, -sin, -cos, +sin; sin: +sin, +cos, -sin, -cos */
+  int neg = which ? (quad >= 2) : (quad == 1 || quad == 2);
+  return neg ? -val : val;
+}
+
+/* The normal deviate of noise source `id` at step `step`: one Threefry call
+ * (key = seed, counter = {id, step/4, 2, 0}) serves four consecutive steps;
+ * step mod 4 = 2p + j takes the Box-Muller pair of words 2p and 2p+1 (53-bit
+ * uniforms u1, u2 in [0, 1)): sqrt(-2 log(1 - u1)) times cos (j = 0) or
+ * sin (j = 1) of 2 pi u2. */
+double orc_normal(uint64_t seed, uint64_t id, int64_t step) {
+  uint64_t key[4] = {seed, 0, 0, 0};
+  uint64_t ctr[4] = {id, (uint64_t)step >> 2, 2, 0};
+  uint64_t out[4];
+  orc_threefry4x64_12(ctr, key, out);
+  int j = (int)(step & 3);
+  double u1 = (double)(out[j & 2] >> 11) * 0x1p-53;
+  double u2 = (double)(out[(j & 2) + 1] >> 11) * 0x1p-53;
+  double rad = sqrt(-2.0 * orc_log(1.0 - u1));
+  return rad * orc_cis2pi(u2, j & 1);
+}
+
+/* ------------------------------------------------------------------------ */
 typedef struct {
   int32_t syn;
   int32_t type; /* 0: pre (conductance) event, 1: delayed calcium event */
@@ -222,6 +316,9 @@ typedef struct {
   double decay_g, decay_c;
   double rate_w, rate_h, rate_z, rate_p;
   int64_t dc_steps;
+  double sigma;   /* sigma_pl (GB, STC) */
+  double amp[3];  /* Euler-Maruyama noise amplitude with n of the two thresholds crossed:
+                     sigma_pl sqrt(n dt / tau) for tau = tau_w (GB) or tau_h (STC) */
 } orc_mech;
 
 struct orc_model {
@@ -286,6 +383,11 @@ static int n_params_of(int32_t k) {
   }
   return -1;
 }
+/* GB and STC take an optional trailing sigma_pl (the noise scale; 0 if absent) */
+static int accepts_params(int32_t k, int32_t n) {
+  int np = n_params_of(k);
+  return n == np || ((k == ORC_MECH_GB || k == ORC_MECH_STC) && n == np + 1);
+}
 
 static void push_ev(orc_bucket* bk, int32_t syn, int32_t type) {
   if (bk->n == bk->cap) {
@@ -335,7 +437,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
               const int32_t* parent, const double* length_um, const double* diam_um,
               const int32_t* region,
               int32_t n_mech, const int32_t* mech_kind, const int32_t* mech_off,
-              const double* mech_params,
+              const double* mech_params, int64_t n_mech_params,
               int64_t n_conn, const int32_t* conn_src, const int32_t* conn_dst,
               const int32_t* conn_cv, const int32_t* conn_mech, const double* conn_weight,
               const double* conn_delay, const double* conn_rate, const int64_t* conn_pid,
@@ -354,9 +456,17 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
   for (int32_t j = 0; j < n_mech; ++j) {
     int np = n_params_of(mech_kind[j]);
     if (np < 0) { orc_free(M); return fail(-1, "mechanism %d: unknown kind %d", j, mech_kind[j]); }
+    int64_t given = (j + 1 < n_mech ? (int64_t)mech_off[j + 1] : n_mech_params) - mech_off[j];
+    if (!accepts_params(mech_kind[j], (int32_t)given)) {
+      orc_free(M); return fail(-1, "mechanism %d: %lld parameters", j, (long long)given);
+    }
     orc_mech* mc = &M->mech[j];
     mc->kind = mech_kind[j];
-    for (int i = 0; i < np; ++i) mc->p[i] = mech_params[mech_off[j] + i];
+    for (int i = 0; i < given; ++i) mc->p[i] = mech_params[mech_off[j] + i];
+    mc->sigma = (given > np) ? mc->p[np] : 0.0;
+    if (!(mc->sigma >= 0.0)) { orc_free(M); return fail(-1, "mechanism %d: sigma_pl < 0", j); }
+    for (int n = 0; n < 3; ++n)
+      mc->amp[n] = (given > np) ? mc->sigma * sqrt(((double)n * dt) / mc->p[9]) : 0.0;
     /* per-dt constants: exact exponential decay of the linear ODEs
        (g' = -g/tau, c' = -c/tau_c, a' = -a/tau) and forward-Euler rates */
     if (is_point(mc->kind)) mc->decay_g = exp(-dt / mc->p[0]);
@@ -693,12 +803,17 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
     const double* q = mc->p;
     M->g[s] = M->g[s] * mc->decay_g;
     if (mc->kind == ORC_MECH_GB) {
-      /* Eq. weight_graupner_brunel (sigma_pl = 0), forward Euler */
+      /* Eq. weight_graupner_brunel, forward Euler */
       double w = M->w[s], cc = M->c[s];
       double A = (w * (1.0 - w)) * (q[10] - w);
       double P = (cc > q[5]) ? q[7] * (1.0 - w) : 0.0;
       double D = (cc > q[6]) ? q[8] * w : 0.0;
-      M->w[s] = w + mc->rate_w * ((P - A) - D);
+      double wn = w + mc->rate_w * ((P - A) - D);
+      /* Eq. plasticity_noise_1, Euler-Maruyama: sigma_pl sqrt(n dt / tau_w) N(0,1)
+         with n the number of thresholds the calcium exceeds */
+      int nth = (cc > q[5]) + (cc > q[6]);
+      if (mc->sigma > 0.0 && nth > 0) wn = wn + mc->amp[nth] * orc_normal(M->seed, (uint64_t)s, k);
+      M->w[s] = wn;
       M->c[s] = cc * mc->decay_c;
     } else if (mc->kind == ORC_MECH_STC) {
       double h = M->hs[s], z = M->z[s], cc = M->c[s], h0 = q[12];
@@ -707,10 +822,14 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
       double T1 = ((h - h0) > q[13]) ? (pk * q[16]) * (1.0 - z) : 0.0;
       double T2 = ((h0 - h) > q[13]) ? (pk * q[16]) * (z + 0.5) : 0.0;
       M->z[s] = z + mc->rate_z * (T1 - T2);
-      /* Eq. early_phase_weight (sigma_pl = 0), 10 mV potentiation ceiling */
+      /* Eq. early_phase_weight, 10 mV potentiation ceiling */
       double P = (cc > q[5]) ? q[7] * (10.0 - h) : 0.0;
       double D = (cc > q[6]) ? q[8] * h : 0.0;
-      M->hs[s] = h + mc->rate_h * ((0.1 * (h0 - h) + P) - D);
+      double hn = h + mc->rate_h * ((0.1 * (h0 - h) + P) - D);
+      /* Eq. plasticity_noise_2 with tau_h */
+      int nth = (cc > q[5]) + (cc > q[6]);
+      if (mc->sigma > 0.0 && nth > 0) hn = hn + mc->amp[nth] * orc_normal(M->seed, (uint64_t)s, k);
+      M->hs[s] = hn;
       M->c[s] = cc * mc->decay_c;
     }
   }

@@ -74,7 +74,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
               const int32_t* parent, const double* length_um, const double* diam_um,
               const int32_t* region,
               int32_t n_mech, const int32_t* mech_kind, const int32_t* mech_off,
-              const double* mech_params,
+              const double* mech_params, int64_t n_mech_params,
               int64_t n_conn, const int32_t* conn_src, const int32_t* conn_dst,
               const int32_t* conn_cv, const int32_t* conn_mech, const double* conn_weight,
               const double* conn_delay, const double* conn_rate, const int64_t* conn_pid,
@@ -110,6 +110,11 @@ int orc_hines_solve(int32_t n, const int32_t* parent, const double* d, const dou
                     const double* b, double* x);
 void orc_threefry4x64_12(const uint64_t ctr[4], const uint64_t key[4], uint64_t out[4]);
 uint32_t orc_poisson_u32(uint64_t seed, uint64_t stream, int64_t step);
+/* Plasticity noise: the model's logarithm, cos/sin(2 pi v) (which = 0/1) and the
+ * Box-Muller normal deviate of noise source `id` at step `step`. */
+double orc_log(double x);
+double orc_cis2pi(double v, int which);
+double orc_normal(uint64_t seed, uint64_t id, int64_t step);
 
 #ifdef __cplusplus
 }

@@ -48,21 +48,24 @@ def expsyn_params(tau=5.0, e=0.0):
 
 
 def gb_params(tau=5.0, e=0.0, tau_c=20.0, c_pre=1.0, c_post=2.0, theta_p=1.3, theta_d=1.0,
-              gamma_p=725.0, gamma_d=331.0, tau_w=346.0e3, w_star=0.5, t_c_delay=13.7, w0=0.0):
-    """Graupner-Brunel calcium rule (Eqs. weight_graupner_brunel, ca_model_graupner_brunel).
-    Defaults: the single-neuron workload's constants; w_star and t_c_delay from Table 3."""
+              gamma_p=725.0, gamma_d=331.0, tau_w=346.0e3, w_star=0.5, t_c_delay=13.7, w0=0.0,
+              sigma_pl=0.0):
+    """Graupner-Brunel calcium rule (Eqs. weight_graupner_brunel, ca_model_graupner_brunel,
+    plasticity_noise_1).  Defaults: the single-neuron workload's constants; w_star and
+    t_c_delay from Table 3; sigma_pl = 0 (deterministic; Table 3 gives 2.8248)."""
     return np.array([tau, e, tau_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_w,
-                     w_star, t_c_delay, w0])
+                     w_star, t_c_delay, w0, sigma_pl])
 
 
 def stc_params(tau=5.0, e=0.0, tau_c=48.8, c_pre=0.6, c_post=0.1655, theta_p=3.0, theta_d=1.2,
                gamma_p=1645.6, gamma_d=313.1, tau_h=688.4e3, tau_z=3600.0e3, tau_p=3600.0e3,
                h0=4.20075, theta_tag=0.840149, theta_pro=2.10037, p_max=10.0, f_int=0.1,
-               t_c_delay=18.8):
-    """Tagging-and-capture rule (Eqs. total_syn_weight .. prp_single_comp), Table 5 with
-    the in-vivo calcium contributions used for networks."""
+               t_c_delay=18.8, sigma_pl=0.0):
+    """Tagging-and-capture rule (Eqs. total_syn_weight .. prp_single_comp,
+    plasticity_noise_2), Table 5 with the in-vivo calcium contributions used for
+    networks; sigma_pl = 0 (deterministic; Table 5 gives 2.90436 mV)."""
     return np.array([tau, e, tau_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_h,
-                     tau_z, tau_p, h0, theta_tag, theta_pro, p_max, f_int, t_c_delay])
+                     tau_z, tau_p, h0, theta_tag, theta_pro, p_max, f_int, t_c_delay, sigma_pl])
 
 
 def stdp_params(tau=5.0, e=0.0, tau_pre=16.8, tau_post=33.7, a_pre=0.01, a_post=-0.012,
