@@ -56,11 +56,19 @@ extern "C" {
 #define PA_MECH_EXPSYN 10 /* point, params: tau [ms], e [mV] */
 #define PA_MECH_GB 11     /* point, expsyn + Graupner-Brunel calcium rule; params: tau, e,
                              tau_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d,
-                             tau_w [ms], w_star, t_c_delay [ms], w0 */
+                             tau_w [ms], w_star, t_c_delay [ms], w0 [, sigma_pl] */
 #define PA_MECH_STC 12    /* point, expsyn + tagging and capture; params: tau, e, tau_c,
                              c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_h,
                              tau_z, tau_p [ms], h0 [mV], theta_tag [mV], theta_pro [mV],
-                             p_max, f_int, t_c_delay [ms] */
+                             p_max, f_int, t_c_delay [ms] [, sigma_pl [mV]] */
+/* Plasticity noise (Eqs. plasticity_noise_1-2): with the optional trailing
+ * sigma_pl > 0, each step adds sigma_pl sqrt(n dt / tau) N(0,1) to w (GB,
+ * tau = tau_w) or h (STC, tau = tau_h), n = number of the thresholds theta_p,
+ * theta_d the calcium exceeds (Euler-Maruyama).  N(0,1) of synapse (connection)
+ * c at step k: Box-Muller from Threefry-4x64-12 with key (seed, 0, 0, 0) and
+ * counter (c, k / 4, 2, 0); k mod 4 = 2p + j uses output words 2p, 2p+1 as
+ * 53-bit uniforms u1, u2: sqrt(-2 log(1 - u1)) cos (j = 0) or sin (j = 1) of
+ * 2 pi u2, with the engine's own log, cos and sin (documented in rng.cuh). */
 #define PA_MECH_STDP 13   /* point, expsyn + pair STDP; params: tau, e, tau_pre, tau_post
                              [ms], A_pre, A_post, w0, w_max (w dimensionless, conductance
                              jump = weight * clip(w, 0, w_max)) */

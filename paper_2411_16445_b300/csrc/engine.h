@@ -31,6 +31,8 @@ struct StreamParams {
   double rate_w, w_star; // GB: dt/tau_w, w*
   double rate_h, rate_z, rate_p, h0, theta_tag, theta_pro, p_max, f_int;  // STC
   double a_pre, a_post, tau_pre, tau_post, w_max;                         // STDP
+  double sigma;          // GB, STC: plasticity noise sigma_pl (0: none)
+  double amp[3];         // sigma_pl sqrt(n dt / tau) with n thresholds crossed
 };
 
 // Device pointers of one synapse stream.  Element index e = ((sbase+j)<<5)|lane.
@@ -48,6 +50,7 @@ struct StreamDev {
   int32_t* kpost;        // step of the last jump of apost (STDP)
   uint64_t* cmask;       // [n_slots][n_elem]: bit (k mod E) = conductance event in step k
   uint64_t* camask;      // [n_slots][n_elem]: delayed calcium event (GB, STC)
+  const int32_t* nid;    // noise source of each synapse (its connection index; noisy streams)
   int64_t n_elem;
 };
 
@@ -89,6 +92,7 @@ struct EpochArgs {
   int32_t epoch_len;     // E
   int32_t n_slots;
   const EpochClock* clock;
+  uint64_t seed;         // key of the counter-based generator (plasticity noise)
   int32_t n_groups;      // all groups: narrow [0, n_narrow), then one per wide cell
   int32_t n_narrow;      // groups of 32 cells, one thread per cell
   int32_t n_wide;        // wide cells, one warp per cell

@@ -31,6 +31,7 @@
 
 #include "engine.h"
 #include "int_arith.cuh"
+#include "rng.cuh"
 
 namespace pa {
 
@@ -189,7 +190,7 @@ template <class TM>
 __device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev& D, uint32_t e,
                                          bool pre, bool capre, bool post, TM gv, double cc,
                                          double wv, double zv, double prp, int64_t k, double dt,
-                                         double& S) {
+                                         uint64_t seed, double& S) {
   if (P.kind == SK_EXPSYN) {
     if (pre) gv = gv + ((const TM*)D.weight)[e];
   } else if (P.kind == SK_GB) {
@@ -200,7 +201,12 @@ __device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev&
     const double Aw = (w * (1.0 - w)) * (P.w_star - w);
     const double Pw = (cc > P.theta_p) ? P.gamma_p * (1.0 - w) : 0.0;
     const double Dw = (cc > P.theta_d) ? P.gamma_d * w : 0.0;
-    D.w[e] = w + P.rate_w * ((Pw - Aw) - Dw);
+    double wn = w + P.rate_w * ((Pw - Aw) - Dw);
+    // Eq. plasticity_noise_1, Euler-Maruyama, gated by the thresholds crossed
+    const int nth = (cc > P.theta_p) + (cc > P.theta_d);
+    if (P.sigma > 0.0 && nth > 0)
+      wn = __dadd_rn(wn, __dmul_rn(P.amp[nth], model_normal(seed, (uint64_t)D.nid[e], k)));
+    D.w[e] = wn;
     D.c[e] = cc * P.decay_c;
   } else if (P.kind == SK_STC) {
     const double h = wv, z = zv;
@@ -214,7 +220,12 @@ __device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev&
     D.z[e] = z + P.rate_z * (T1 - T2);
     const double Ph = (cc > P.theta_p) ? P.gamma_p * (10.0 - h) : 0.0;
     const double Dh = (cc > P.theta_d) ? P.gamma_d * h : 0.0;
-    D.w[e] = h + P.rate_h * ((0.1 * (h0 - h) + Ph) - Dh);
+    double hn = h + P.rate_h * ((0.1 * (h0 - h) + Ph) - Dh);
+    // Eq. plasticity_noise_2
+    const int nth = (cc > P.theta_p) + (cc > P.theta_d);
+    if (P.sigma > 0.0 && nth > 0)
+      hn = __dadd_rn(hn, __dmul_rn(P.amp[nth], model_normal(seed, (uint64_t)D.nid[e], k)));
+    D.w[e] = hn;
     D.c[e] = cc * P.decay_c;
   } else if (pre || post) {  // SK_STDP: traces evaluated in closed form at events only
     TM* AP = (TM*)D.apre;
@@ -410,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           const double wv = calc ? ((const double*)(st + o_w))[r] : 0.0;
           const double zv = stc ? ((const double*)(st + o_z))[r] : 0.0;
           TM gv = syn_update<TM>(P, D, e, pre, capre, post, ((const TM*)(st + o_g))[r], cc, wv,
-                                 zv, prp, k, dt, S);
+                                 zv, prp, k, dt, A.seed, S);
           run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
           G[e] = gv * dg;
         }

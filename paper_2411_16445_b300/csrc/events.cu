@@ -11,39 +11,9 @@
 #include <stdint.h>
 
 #include "engine.h"
+#include "rng.cuh"
 
 namespace pa {
-
-// Threefry-4x64-12 (Salmon et al. 2011): Threefish-256 rotations, key parity
-// 0x1BD11BDAA9FC1A22, key injection after every fourth round.
-__device__ __forceinline__ uint64_t rotl(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
-
-__device__ void threefry4x64_12(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                uint64_t k0, uint64_t k1, uint64_t k2, uint64_t k3,
-                                uint64_t out[4]) {
-  const int R0[8] = {14, 52, 23, 5, 25, 46, 58, 32};
-  const int R1[8] = {16, 57, 40, 37, 33, 12, 22, 32};
-  uint64_t ks[5] = {k0, k1, k2, k3, 0x1BD11BDAA9FC1A22ULL ^ k0 ^ k1 ^ k2 ^ k3};
-  uint64_t x0 = c0 + ks[0], x1 = c1 + ks[1], x2 = c2 + ks[2], x3 = c3 + ks[3];
-#pragma unroll
-  for (int r = 0; r < 12; ++r) {
-    if ((r & 1) == 0) {
-      x0 += x1; x1 = rotl(x1, R0[r & 7]); x1 ^= x0;
-      x2 += x3; x3 = rotl(x3, R1[r & 7]); x3 ^= x2;
-    } else {
-      x0 += x3; x3 = rotl(x3, R0[r & 7]); x3 ^= x0;
-      x2 += x1; x1 = rotl(x1, R1[r & 7]); x1 ^= x2;
-    }
-    if ((r & 3) == 3) {
-      const int s = (r >> 2) + 1;
-      x0 += ks[s % 5];
-      x1 += ks[(s + 1) % 5];
-      x2 += ks[(s + 2) % 5];
-      x3 += ks[(s + 3) % 5] + (uint64_t)s;
-    }
-  }
-  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
-}
 
 // One thread per Poisson-driven synapse: draws its spikes for steps
 // [k_from, k_to) (one Threefry call per 8 steps: key = seed, counter =

@@ -52,6 +52,14 @@ int n_params_of(int kind) {
   }
   return -1;
 }
+// Plasticity noise of a GB/STC stream (Eqs. plasticity_noise_1-2): sigma_pl,
+// the optional parameter at index np, and the Euler-Maruyama amplitudes
+// sigma_pl sqrt(n dt / tau) for n = 0, 1, 2 thresholds crossed.
+void set_noise(pa::StreamParams& P, const pa_mechanism& m, int np, double tau, double dt) {
+  P.sigma = m.n_params > np ? m.params[np] : 0.0;
+  for (int n = 0; n < 3; ++n)
+    P.amp[n] = m.n_params > np ? P.sigma * std::sqrt(((double)n * dt) / tau) : 0.0;
+}
 bool is_point(int kind) {
   return kind == PA_MECH_EXPSYN || kind == PA_MECH_GB || kind == PA_MECH_STC ||
          kind == PA_MECH_STDP;
@@ -253,9 +261,14 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   for (int64_t j = 0; j < n_mech; ++j) {
     int np = n_params_of(mechs[j].kind);
     if (np < 0) return set_err(PA_ERR_ARG, "mechanism %lld: unknown kind %d", (long long)j, mechs[j].kind);
-    if (mechs[j].n_params != np || !mechs[j].params)
+    // GB and STC take an optional trailing sigma_pl (plasticity noise; 0 if absent)
+    const bool noisy_kind = mechs[j].kind == PA_MECH_GB || mechs[j].kind == PA_MECH_STC;
+    if (!(mechs[j].n_params == np || (noisy_kind && mechs[j].n_params == np + 1)) ||
+        !mechs[j].params)
       return set_err(PA_ERR_ARG, "mechanism %lld: expected %d parameters", (long long)j, np);
-    for (int i = 0; i < np; ++i)
+    if (mechs[j].n_params > np && !(mechs[j].params[np] >= 0.0))
+      return set_err(PA_ERR_ARG, "mechanism %lld: sigma_pl must be >= 0", (long long)j);
+    for (int i = 0; i < mechs[j].n_params; ++i)
       if (!std::isfinite(mechs[j].params[i]))
         return set_err(PA_ERR_ARG, "mechanism %lld: non-finite parameter %d", (long long)j, i);
   }
@@ -324,6 +337,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         P.c_pre = p[3]; P.c_post = p[4]; P.theta_p = p[5]; P.theta_d = p[6];
         P.gamma_p = p[7]; P.gamma_d = p[8]; P.rate_w = dt / p[9]; P.w_star = p[10];
         P.dc_steps = (int32_t)std::llround(p[11] / dt);
+        set_noise(P, mechs[m], 13, p[9], dt);
         break;
       case PA_MECH_STC:
         P.kind = SK_STC;
@@ -335,6 +349,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         P.h0 = p[12]; P.theta_tag = p[13]; P.theta_pro = p[14]; P.p_max = p[15];
         P.f_int = p[16];
         P.dc_steps = (int32_t)std::llround(p[17] / dt);
+        set_noise(P, mechs[m], 18, p[9], dt);
         break;
       case PA_MECH_STDP:
         P.kind = SK_STDP;
@@ -643,6 +658,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<std::vector<int32_t>> s_sbase(n_streams);
   std::vector<std::vector<int32_t>> s_cvf(n_streams);
   std::vector<std::vector<double>> s_weight(n_streams), s_w(n_streams);
+  std::vector<std::vector<int32_t>> s_nid(n_streams);   // noise source ids (noisy streams)
   std::vector<uint8_t> h_has_stc(n_lanes, 0);
   for (int s = 0; s < n_streams; ++s) {
     s_sbase[s].assign(n_groups + 1, 0);
@@ -665,6 +681,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     s_cvf[s].assign(ne, -1);
     s_weight[s].assign(ne, 0.0);
     s_w[s].assign(ne, 0.0);
+    if (M->sp[s].sigma > 0.0) s_nid[s].assign(ne, 0);
   }
   // Per-CV synaptic sums are accumulated in registers over each run of same-CV
   // synapses of a stream (canonical order: mechanism, CV, connection).  Flags:
@@ -695,6 +712,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
           s_w[s][e] = p[12];
           h_has_stc[L] = 1;
         }
+        if (!s_nid[s].empty()) s_nid[s][e] = (int32_t)v[j].conn;
         M->conn_stream[v[j].conn] = s;
         M->conn_elem[v[j].conn] = e;
       }
@@ -792,7 +810,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
                o_gate = R(8 * 3 * n_lanes), o_iinj = R(8 * n_lanes), o_kon = R(8 * n_lanes),
                o_koff = R(8 * n_lanes), o_th = R(8 * n_lanes), o_sp = R(n_lanes),
                o_prp = R(8 * n_lanes), o_hasstc = R(n_lanes), o_rbits = R(8 * n_lanes);
-  size_t o_s[kMaxStreams][11];
+  size_t o_s[kMaxStreams][12];
   for (int s = 0; s < n_streams; ++s) {
     const int64_t ne = M->s_nelem[s];
     const int kind = M->sp[s].kind;
@@ -807,6 +825,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     o_s[s][8] = (kind == SK_STDP) ? R(tm * ne) : 0;                             // apost
     o_s[s][10] = (kind == SK_STDP) ? R(8 * ne) : 0;                             // kpre, kpost
     o_s[s][9] = R(8 * ne * (size_t)M->n_slots * ((kind == SK_GB || kind == SK_STC) ? 2 : 1));
+    o_s[s][11] = M->sp[s].sigma > 0.0 ? R(4 * ne) : 0;                          // noise ids
   }
   const size_t np = ps_conn.size();
   const size_t o_ps_stream = R(4 * np), o_ps_elem = R(8 * np), o_ps_conn = R(8 * np),
@@ -866,6 +885,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     putv(o_s[s][1], s_cvf[s]);
     if (mixed) putv(o_s[s][2], to_f32(s_weight[s])); else putv(o_s[s][2], s_weight[s]);
     if (o_s[s][5]) putv(o_s[s][5], s_w[s]);
+    if (o_s[s][11]) putv(o_s[s][11], s_nid[s]);
   }
   putv(o_ps_stream, ps_stream); putv(o_ps_elem, ps_elem); putv(o_ps_conn, ps_conn);
   putv(o_ps_thr, ps_thr); putv(o_ps_dc, ps_dc);
@@ -879,6 +899,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   auto P8 = [&](size_t o) { return (void*)(D + o); };
   EpochArgs& A = M->ea;
   std::memset(&A, 0, sizeof A);
+  A.seed = M->seed;
   A.n_groups = (int32_t)n_groups;
   A.n_narrow = (int32_t)n_narrow;
   A.n_wide = (int32_t)n_wide;
@@ -938,6 +959,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     sd.kpost = o_s[s][10] ? (int32_t*)P8(o_s[s][10]) + ne : nullptr;
     sd.cmask = (uint64_t*)P8(o_s[s][9]);
     sd.camask = (kind == SK_GB || kind == SK_STC) ? sd.cmask + ne * M->n_slots : nullptr;
+    sd.nid = o_s[s][11] ? (const int32_t*)P8(o_s[s][11]) : nullptr;
     sd.n_elem = ne;
     M->mask_bases.push_back(sd.cmask);
     M->mask_elems.push_back(ne);

@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           const double cc = calc ? D.c[e] : 0.0;
           const double wv = calc ? D.w[e] : 0.0;
           const double zv = stc ? D.z[e] : 0.0;
-          gv = syn_update<TM>(P, D, e, pre, capre, post, G[e], cc, wv, zv, prp, k, dt, sadd);
+          gv = syn_update<TM>(P, D, e, pre, capre, post, G[e], cc, wv, zv, prp, k, dt, A.seed,
+                              sadd);
           G[e] = gv * dg;
         }
         // Per-CV sums in canonical order (run_sum's arithmetic): each lane sums

@@ -293,13 +293,15 @@ def random_binary_tree(rng: np.random.Generator, n_dend: int, soma_diam=20.0,
 
 # --------------------------------------------------------------------------
 # workloads
-def single_neuron(dt: float = 0.025, seed: Optional[int] = None, w_syn: float = 1e-3) -> Network:
+def single_neuron(dt: float = 0.025, seed: Optional[int] = None, w_syn: float = 1e-3,
+                  sigma_pl: float = 0.0) -> Network:
     """Plain FP64 single ball-and-stick neuron with one calcium-plastic synapse at the
-    dendrite midpoint, 10 Hz Poisson input and a 0.5 nA somatic step."""
+    dendrite midpoint, 10 Hz Poisson input and a 0.5 nA somatic step (sigma_pl:
+    plasticity noise, Table 3's 2.8248 for the noisy variant)."""
     b = _Builder(dt, config_seed("single_neuron") if seed is None else seed, "single_neuron")
     hh = b.mech(HH, hh_params())
     pas = b.mech(PAS, pas_params(3e-5, -54.4))
-    gb = b.mech(GB, gb_params())
+    gb = b.mech(GB, gb_params(sigma_pl=sigma_pl))
     m = b.morph(ball_and_stick(20.0, 500.0, 1.0, 64))
     b.cells_add(1, m, hh, pas, istep=0.5)
     b.connect(SRC_POISSON, 0, 1 + 64 // 2, gb, w_syn, rate=10.0)
@@ -307,7 +309,7 @@ def single_neuron(dt: float = 0.025, seed: Optional[int] = None, w_syn: float = 
 
 
 def recurrent_stc(n_exc=1600, n_inh=400, p=0.1, dt=0.2, seed=None, w_bg=1e-3,
-                  bg_rate=5.0) -> Network:
+                  bg_rate=5.0, sigma_pl=0.0) -> Network:
     """Plain FP64 recurrent network: HH ball-and-stick cells with an 8-CV 200 um
     dendrite; Erdos-Renyi connectivity without self-loops; 3 ms delays; weights
     1 nS * U(0.9, 1.1); E->E synapses follow the tagging-and-capture rule; all
@@ -319,7 +321,7 @@ def recurrent_stc(n_exc=1600, n_inh=400, p=0.1, dt=0.2, seed=None, w_bg=1e-3,
     pas = b.mech(PAS, pas_params(3e-5, -54.4))
     exc = b.mech(EXPSYN, expsyn_params(5.0, 0.0))
     inh = b.mech(EXPSYN, expsyn_params(5.0, -80.0))
-    stc = b.mech(STC, stc_params())
+    stc = b.mech(STC, stc_params(sigma_pl=sigma_pl))
     m = b.morph(ball_and_stick(20.0, 200.0, 1.0, 8))
     n = n_exc + n_inh
     b.cells_add(n, m, hh, pas)

@@ -362,3 +362,34 @@ def test_wide_bin_fp64_matches_oracle_and_automatic_bins():
     heavy = dense.cell_ncv() + np.bincount(dense.conn_dst, minlength=dense.n_cells) >= 128
     assert E.Model(dense, precision=E.PA_MIXED).info().n_wide == int(heavy.sum())
     assert E.Model(tiny_tree_net(n_cells=40), precision=E.PA_MIXED).info().n_wide == 0
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_plasticity_noise_single_neuron(precision):
+    """Graupner-Brunel weight with noise (sigma_pl = 2.8248, Table 3) on the
+    single-neuron workload: the deviates of both sides are the same
+    counter-based draws through the same log/sin/cos, so FP64 is bit-identical
+    and the mixed path stays within its tolerances."""
+    net = W.single_neuron(sigma_pl=2.8248)
+    steps = 8000
+    if precision == E.PA_FP64:
+        o, m = run_both(net, steps, precision, chunks=3)
+    else:
+        o, m = run_replay_both(net, steps, precision, chunks=3)
+    det = O.Oracle(W.single_neuron())
+    det.run(steps)
+    assert not np.array_equal(det.syn(O.SYN_W), o.syn(O.SYN_W))   # the noise acted
+    check_state(o, m, precision, exact=precision == E.PA_FP64)
+
+
+def test_plasticity_noise_recurrent_stc_fp64_closed_loop():
+    """Early-phase weights with noise (sigma_pl = 2.90436 mV, Table 5) in a small
+    recurrent STC network, closed loop: FP64 bit-identical to the oracle, in
+    both cell bins."""
+    net = W.recurrent_stc(n_exc=96, n_inh=24, sigma_pl=2.90436)
+    o, m = run_both(net, 2500, E.PA_FP64, chunks=2)
+    check_state(o, m, E.PA_FP64, exact=True)
+    mw = E.Model(net, precision=E.PA_FP64, flags=E.FLAG_WIDE_ALL)
+    mw.advance(2500 * net.dt)
+    assert np.array_equal(mw.read_state(E.FIELD_H), o.syn(O.SYN_H))
+    assert np.array_equal(mw.read_state(E.FIELD_V), o.v())
