@@ -38,6 +38,10 @@ def lib():
         L.orc_get_cell_p.argtypes = [P, P]
         L.orc_get_gates.argtypes = [P, P]
         L.orc_get_cv_geometry.argtypes = [P, P, P, P]
+        L.orc_fast_forward.argtypes = [P, C.c_int64, C.c_int64]
+        L.orc_set_syn.argtypes = [P, C.c_int32, P]
+        for fn in ("orc_set_v", "orc_set_cell_p", "orc_set_gates"):
+            getattr(L, fn).argtypes = [P, P]
         L.orc_free.argtypes = [P]
         L.orc_last_error.restype = C.c_char_p
         L.orc_exp.restype = C.c_double
@@ -136,6 +140,34 @@ class Oracle:
         out = np.zeros(ns * self.n_probe)
         lib().orc_get_probes(self._h, _p(out))
         return out.reshape(ns, self.n_probe)
+
+    def step_count(self) -> int:
+        return int(lib().orc_step_count(self._h))
+
+    def fast_forward(self, steps: int, n_long: int):
+        """steps of simulated time without spiking and calcium dynamics, the slow
+        plasticity variables in n_long long forward-Euler steps."""
+        if lib().orc_fast_forward(self._h, steps, n_long) != 0:
+            raise ValueError("fast_forward: bad arguments or replay mode")
+
+    def set_syn(self, field: int, values):
+        a = np.ascontiguousarray(values, np.float64)
+        assert a.shape == (self.n_conn,)
+        lib().orc_set_syn(self._h, field, _p(a))
+
+    def set_v(self, values):
+        a = np.ascontiguousarray(values, np.float64)
+        lib().orc_set_v(self._h, _p(a))
+
+    def set_cell_p(self, values):
+        a = np.ascontiguousarray(values, np.float64)
+        assert a.shape == (self.n_cells,)
+        lib().orc_set_cell_p(self._h, _p(a))
+
+    def set_gates(self, values):
+        a = np.ascontiguousarray(values, np.float64).reshape(-1)
+        assert a.shape == (3 * self.n_cells,)
+        lib().orc_set_gates(self._h, _p(a))
 
     def syn(self, field: int):
         out = np.zeros(self.n_conn)

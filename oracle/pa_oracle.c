@@ -916,6 +916,84 @@ int orc_run(orc_model* M, int64_t n_steps) {
   return 0;
 }
 
+/* Fast-forward (the '8h-recall' paradigm, Sec. on the recurrent network with
+ * plastic synapses): K steps of simulated time without spiking and calcium
+ * dynamics.  The membrane state is kept; pending events are dropped; every
+ * conductance and calcium decays by its exact factor exp(-K dt / tau); the slow
+ * plasticity variables take n_long forward-Euler steps of K dt / n_long with
+ * the calcium terms (and so the noise) off, in the order of a full step: per
+ * cell, S from h before the update, then per synapse z (with the cell's p) and
+ * h (relaxation to h0), GB w (its cubic drift), then p.  STDP traces decay
+ * through their closed form as the clock advances by K. */
+int orc_fast_forward(orc_model* M, int64_t K, int64_t n_long) {
+  if (K < 0 || n_long < 1 || M->replay) return -1;
+  const double T = (double)K * M->dt;
+  const double dtl = T / (double)n_long;
+  for (int64_t s = 0; s < M->n_syn; ++s) {
+    const orc_mech* mc = &M->mech[M->syn_mech[s]];
+    M->g[s] = M->g[s] * exp(-T / mc->p[0]);
+    if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC) M->c[s] = M->c[s] * exp(-T / mc->p[2]);
+  }
+  for (int64_t r = 0; r < M->R; ++r) M->q[r].n = 0;
+  for (int32_t c = 0; c < M->n_cells; ++c) M->spiked_prev[c] = 0;
+  for (int64_t it = 0; it < n_long; ++it) {
+    for (int32_t c = 0; c < M->n_cells; ++c) {
+      double S = 0.0, pk = M->p[c];
+      for (int64_t j = M->cell_syn_off[c]; j < M->cell_syn_off[c + 1]; ++j) {
+        int64_t s = M->cell_syn[j];
+        const orc_mech* mc = &M->mech[M->syn_mech[s]];
+        const double* q = mc->p;
+        if (mc->kind == ORC_MECH_GB) {
+          double w = M->w[s];
+          double A = (w * (1.0 - w)) * (q[10] - w);
+          M->w[s] = w + (dtl / q[9]) * (-A);
+        } else if (mc->kind == ORC_MECH_STC) {
+          double h = M->hs[s], z = M->z[s], h0 = q[12];
+          S = S + fabs(h - h0);
+          double T1 = ((h - h0) > q[13]) ? (pk * q[16]) * (1.0 - z) : 0.0;
+          double T2 = ((h0 - h) > q[13]) ? (pk * q[16]) * (z + 0.5) : 0.0;
+          M->z[s] = z + (dtl / q[10]) * (T1 - T2);
+          M->hs[s] = h + (dtl / q[9]) * (0.1 * (h0 - h));
+        }
+      }
+      if (M->cell_stc_mech[c] >= 0) {
+        const orc_mech* mc = &M->mech[M->cell_stc_mech[c]];
+        double qs = (S > mc->p[14]) ? mc->p[15] : 0.0;
+        M->p[c] = pk + (dtl / mc->p[11]) * (qs - pk);
+      }
+    }
+  }
+  M->step += K;
+  return 0;
+}
+
+/* State setters (the inverse of the getters; a model's state swapped in). */
+void orc_set_syn(orc_model* M, int32_t field, const double* in) {
+  for (int64_t s = 0; s < M->n_syn; ++s) {
+    switch (field) {
+      case ORC_SYN_G: M->g[s] = in[s]; break;
+      case ORC_SYN_C: M->c[s] = in[s]; break;
+      case ORC_SYN_W: M->w[s] = in[s]; break;
+      case ORC_SYN_H: M->hs[s] = in[s]; break;
+      case ORC_SYN_Z: M->z[s] = in[s]; break;
+      case ORC_SYN_APRE: M->apre[s] = in[s]; M->apre_k[s] = M->step; break;
+      case ORC_SYN_APOST: M->apost[s] = in[s]; M->apost_k[s] = M->step; break;
+    }
+  }
+}
+void orc_set_v(orc_model* M, const double* in) { memcpy(M->V, in, sizeof(double) * (size_t)M->n_cv); }
+void orc_set_cell_p(orc_model* M, const double* in) {
+  memcpy(M->p, in, sizeof(double) * (size_t)M->n_cells);
+}
+void orc_set_gates(orc_model* M, const double* in) {
+  for (int32_t c = 0; c < M->n_cells; ++c) {
+    int64_t gi = M->cv_off[c];
+    M->m[gi] = in[3 * c];
+    M->h[gi] = in[3 * c + 1];
+    M->n[gi] = in[3 * c + 2];
+  }
+}
+
 int64_t orc_step_count(const orc_model* M) { return M->step; }
 int64_t orc_n_spikes(const orc_model* M) { return M->n_spk; }
 void orc_get_spikes(const orc_model* M, int32_t* gid, int64_t* step, double* t) {

@@ -115,6 +115,12 @@ uint32_t orc_poisson_u32(uint64_t seed, uint64_t stream, int64_t step);
 double orc_log(double x);
 double orc_cis2pi(double v, int which);
 double orc_normal(uint64_t seed, uint64_t id, int64_t step);
+/* Fast-forward K steps with n_long long steps of the slow plasticity variables. */
+int orc_fast_forward(orc_model* M, int64_t K, int64_t n_long);
+void orc_set_syn(orc_model* M, int32_t field, const double* in);
+void orc_set_v(orc_model* M, const double* in);
+void orc_set_cell_p(orc_model* M, const double* in);
+void orc_set_gates(orc_model* M, const double* in);
 
 #ifdef __cplusplus
 }
