@@ -285,6 +285,28 @@ int pa_set_replay(pa_model* m, int64_t n, const int32_t* gid, const int64_t* ste
 
 int pa_model_info(const pa_model* m, pa_info* info);
 
+/* Writes a state field (the inverse of pa_read_state, same layout and count):
+ * per connection for the synapse fields (entries of connections whose kind
+ * lacks the field are ignored; a written STDP trace counts as jumping now),
+ * per CV for PA_FIELD_V, per cell for PA_FIELD_PRP and (3 per cell: m, h, n)
+ * PA_FIELD_GATES.  Swaps a saved state into a model, e.g. one built from an
+ * edited network (the state-saving mechanism of the '8h-recall' paradigm).
+ * Synchronises the model's stream. */
+int pa_write_state(pa_model* m, int32_t field, const double* values, int64_t n);
+
+/* Fast-forward (the '8h-recall' paradigm: phases of slow network dynamics):
+ * advances the model by duration_ms (whole steps) without spiking and calcium
+ * dynamics.  The membrane state is kept, pending events are dropped, every
+ * conductance and calcium decays by exp(-duration / tau), and the slow
+ * plasticity variables take n_long forward-Euler steps of duration / n_long
+ * with the calcium terms (and the noise) off: per cell S = sum |h - h0| (STC,
+ * canonical order) from h before the step, then per synapse z (Eq.
+ * late_phase_weight with the cell's p), h (Eq. early_phase_weight: 0.1 (h0 - h)
+ * / tau_h), GB w (Eq. weight_graupner_brunel: its cubic term), then p (Eq.
+ * prp_single_comp).  STDP traces decay through their closed form.  All state
+ * stays on the device.  Not in open-loop replay. */
+int pa_fast_forward(pa_model* m, double duration_ms, int64_t n_long);
+
 /* The epoch-kernel shape in use and, if the model was autotuned, the trial time
  * [ms] of each shape (cap entries of trial_ms; 0 for untried shapes). */
 int pa_get_tuning(const pa_model* m, int32_t* shape, double* trial_ms, int32_t cap);

@@ -30,6 +30,7 @@ UNITS = {
     "model.cu": NOFMA,
     "epoch_noalloc.cu": NOFMA,
     "arith_check.cu": NOFMA,
+    "fastforward.cu": NOFMA,
 }
 
 

@@ -223,6 +223,16 @@ struct SlotClear {
 int launch_clear_and_tick(const SlotClear& c, EpochClock* clock, void* stream);
 int launch_set_clock(EpochClock* clock, int64_t k0, int64_t probe_sample0, void* stream);
 
+// pa_fast_forward (fastforward.cu): per-stream exact decay factors over the
+// fast-forwarded time and long-step rates dt_long / tau.
+struct FastForward {
+  int64_t n_long;
+  double decay_g[kMaxStreams], decay_c[kMaxStreams];
+  double rate_w[kMaxStreams], rate_h[kMaxStreams], rate_z[kMaxStreams];
+  double rate_p;  // dt_long / tau_p of the STC stream
+};
+int launch_fast_forward(const EpochArgs& a, const FastForward& f, bool mixed, void* stream);
+
 int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, bool mixed,
                          int shape, void* stream);
 int64_t noalloc_max_padded_cv();

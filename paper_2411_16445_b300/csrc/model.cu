@@ -112,6 +112,7 @@ struct pa_model {
   size_t elem_bytes_m = 8;
   int n_streams = 0;
   pa::StreamParams sp[pa::kMaxStreams];
+  std::vector<double> mech_params[pa::kMaxStreams];  // each stream's mechanism parameters
   int64_t s_nelem[pa::kMaxStreams];
   // device
   char* dmem = nullptr;
@@ -323,6 +324,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     if (s < 0) continue;
     n_streams = std::max(n_streams, s + 1);
     stream_mech[s] = (int)m;
+    M->mech_params[s].assign(mechs[m].params, mechs[m].params + mechs[m].n_params);
     const double* p = mechs[m].params;
     StreamParams& P = M->sp[s];
     std::memset(&P, 0, sizeof P);
@@ -1582,6 +1584,121 @@ int pa_reset_kernel_stats(pa_model* M) {
   M->n_epoch_launches = M->n_kernel_launches = M->n_graph_launches = 0;
   M->epoch_ms = M->event_ms = 0;
   return rc;
+}
+
+int pa_fast_forward(pa_model* M, double duration_ms, int64_t n_long) {
+  using namespace pa;
+  if (!M) return set_err(PA_ERR_ARG, "model is NULL");
+  if (M->replay) return set_err(PA_ERR_STATE, "pa_fast_forward does not run in open-loop replay");
+  const double ks = duration_ms / M->dt;
+  const int64_t K = std::llround(ks);
+  if (!std::isfinite(ks) || K < 0 || std::fabs(ks - (double)K) > 1e-6 * std::max(1.0, std::fabs(ks)))
+    return set_err(PA_ERR_ARG, "duration %.17g is not a whole number of steps", duration_ms);
+  if (n_long < 1) return set_err(PA_ERR_ARG, "n_long must be at least 1");
+  CUDA_TRY(cudaSetDevice(M->device));
+  const double T = (double)K * M->dt;
+  const double dtl = T / (double)n_long;
+  FastForward F;
+  std::memset(&F, 0, sizeof F);
+  F.n_long = n_long;
+  for (int s = 0; s < M->n_streams; ++s) {
+    const StreamParams& P = M->sp[s];
+    const double* p = M->mech_params[s].data();
+    F.decay_g[s] = std::exp(-T / p[0]);
+    F.decay_c[s] = (P.kind == SK_GB || P.kind == SK_STC) ? std::exp(-T / p[2]) : 1.0;
+    if (P.kind == SK_GB) F.rate_w[s] = dtl / p[9];
+    if (P.kind == SK_STC) {
+      F.rate_h[s] = dtl / p[9];
+      F.rate_z[s] = dtl / p[10];
+      F.rate_p = dtl / p[11];
+    }
+  }
+  int rc = launch_fast_forward(M->ea, F, M->precision == PA_MIXED, M->stream);
+  if (rc) return set_err(PA_ERR_CUDA, "fast forward: %s", cudaGetErrorString((cudaError_t)rc));
+  // pending events are dropped; no POST_EVENT is due
+  for (size_t i = 0; i < M->mask_bases.size(); ++i)
+    CUDA_TRY(cudaMemsetAsync(M->mask_bases[i], 0, 8 * M->mask_elems[i] * (size_t)M->n_slots,
+                             M->stream));
+  CUDA_TRY(cudaMemsetAsync(M->ea.spiked_prev, 0, M->n_lanes, M->stream));
+  M->step += K;
+  M->poisson_epoch_done = -1;
+  return check_device_errors(M);
+}
+
+int pa_write_state(pa_model* M, int32_t field, const double* in, int64_t n) {
+  using namespace pa;
+  if (!M || (!in && n > 0)) return set_err(PA_ERR_ARG, "NULL argument");
+  CUDA_TRY(cudaSetDevice(M->device));
+  const bool mixed = M->precision == PA_MIXED;
+  // read-modify-write of the device array (padding entries keep their values)
+  auto rmw = [&](void* dptr, int64_t count, size_t esz, auto&& edit) -> int {
+    std::vector<char> raw((size_t)count * esz);
+    cudaError_t e = cudaMemcpyAsync(raw.data(), dptr, raw.size(), cudaMemcpyDeviceToHost, M->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+    if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "write state: %s", cudaGetErrorString(e));
+    edit(raw.data());
+    e = cudaMemcpyAsync(dptr, raw.data(), raw.size(), cudaMemcpyHostToDevice, M->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+    if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "write state: %s", cudaGetErrorString(e));
+    return PA_OK;
+  };
+  if (field == PA_FIELD_V) {
+    if (n != M->n_cv) return set_err(PA_ERR_ARG, "expected %lld values", (long long)M->n_cv);
+    return rmw(M->ea.V, M->total_rows * kLanes, 8, [&](char* raw) {
+      double* v = (double*)raw;
+      for (int64_t c = 0; c < M->n_cells; ++c) {
+        const int64_t L = M->lane_of_gid[c], g = L / kLanes;
+        for (int i = 0; i < M->cell_ncv[c]; ++i)
+          v[g < M->n_narrow ? ((int64_t)M->row_base[g] + i) * kLanes + L % kLanes
+                            : ((int64_t)M->row_base[g] << 5) + i] = in[M->cell_cv_off[c] + i];
+      }
+    });
+  }
+  if (field == PA_FIELD_PRP || field == PA_FIELD_GATES) {
+    const int per = field == PA_FIELD_GATES ? 3 : 1;
+    if (n != M->n_cells * per) return set_err(PA_ERR_ARG, "expected %lld values", (long long)(M->n_cells * per));
+    return rmw(field == PA_FIELD_PRP ? (void*)M->ea.prp : (void*)M->ea.gate, per * M->n_lanes, 8,
+               [&](char* raw) {
+                 double* v = (double*)raw;
+                 for (int64_t c = 0; c < M->n_cells; ++c)
+                   for (int j = 0; j < per; ++j) v[j * M->n_lanes + M->lane_of_gid[c]] = in[c * per + j];
+               });
+  }
+  if (field < PA_FIELD_G || field > PA_FIELD_APOST) return set_err(PA_ERR_ARG, "unknown field %d", field);
+  if (n != M->n_conn) return set_err(PA_ERR_ARG, "expected %lld values", (long long)M->n_conn);
+  for (int s = 0; s < M->n_streams; ++s) {
+    const StreamDev& D = M->ea.sd[s];
+    const int kind = M->sp[s].kind;
+    void* dst = nullptr;
+    bool tm32 = false;
+    switch (field) {
+      case PA_FIELD_G: dst = D.g; tm32 = mixed; break;
+      case PA_FIELD_C: dst = D.c; break;
+      case PA_FIELD_W: dst = (kind == SK_GB || kind == SK_STDP) ? D.w : nullptr; break;
+      case PA_FIELD_H: dst = kind == SK_STC ? D.w : nullptr; break;
+      case PA_FIELD_Z: dst = D.z; break;
+      case PA_FIELD_APRE: dst = D.apre; tm32 = mixed; break;
+      case PA_FIELD_APOST: dst = D.apost; tm32 = mixed; break;
+    }
+    if (!dst) continue;
+    int rc = rmw(dst, D.n_elem, tm32 ? 4 : 8, [&](char* raw) {
+      for (int64_t c = 0; c < M->n_conn; ++c) {
+        if (M->conn_stream[c] != s) continue;
+        const int64_t e = M->conn_elem[c];
+        if (tm32) ((float*)raw)[e] = (float)in[c]; else ((double*)raw)[e] = in[c];
+      }
+    });
+    if (rc) return rc;
+    if ((field == PA_FIELD_APRE || field == PA_FIELD_APOST) && kind == SK_STDP) {
+      // a trace written now: its last jump is the current step
+      rc = rmw(field == PA_FIELD_APRE ? (void*)D.kpre : (void*)D.kpost, D.n_elem, 4, [&](char* raw) {
+        for (int64_t c = 0; c < M->n_conn; ++c)
+          if (M->conn_stream[c] == s) ((int32_t*)raw)[M->conn_elem[c]] = (int32_t)M->step;
+      });
+      if (rc) return rc;
+    }
+  }
+  return PA_OK;
 }
 
 int pa_check_arith(int32_t device, uint64_t seed, int64_t n_random, int64_t* out) {

@@ -25,7 +25,7 @@ ERRORS = {-1: "PA_ERR_ARG", -2: "PA_ERR_OOM", -3: "PA_ERR_CUDA", -4: "PA_ERR_TIM
 EXPORTED = ("pa_build_model", "pa_advance", "pa_advance_noalloc", "pa_sync", "pa_read_probes", "pa_read_spikes",
             "pa_read_weights", "pa_read_state", "pa_set_replay", "pa_model_info",
             "pa_get_kernel_stats", "pa_reset_kernel_stats", "pa_get_tuning", "pa_free_model",
-            "pa_check_arith", "pa_last_error")
+            "pa_check_arith", "pa_write_state", "pa_fast_forward", "pa_last_error")
 
 
 class PaError(RuntimeError):
@@ -112,6 +112,8 @@ def lib():
         L.pa_reset_kernel_stats.argtypes = [P]
         L.pa_get_tuning.argtypes = [P, C.POINTER(C.c_int32), P, C.c_int32]
         L.pa_check_arith.argtypes = [C.c_int32, C.c_uint64, C.c_int64, P]
+        L.pa_write_state.argtypes = [P, C.c_int32, P, C.c_int64]
+        L.pa_fast_forward.argtypes = [P, C.c_double, C.c_int64]
         L.pa_free_model.argtypes = [P]
         L.pa_free_model.restype = None
         L.pa_last_error.restype = C.c_char_p
@@ -262,6 +264,16 @@ class Model:
         out = np.zeros(n.value)
         _check(lib().pa_read_state(self._h, int(field), _ptr(out), n.value, C.byref(n)))
         return out
+
+    def write_state(self, field: int, values) -> None:
+        """pa_write_state: the inverse of read_state (same layout)."""
+        a = np.ascontiguousarray(values, np.float64).reshape(-1)
+        _check(lib().pa_write_state(self._h, int(field), _ptr(a), a.size))
+
+    def fast_forward(self, duration_ms: float, n_long: int) -> None:
+        """pa_fast_forward: duration_ms without spiking and calcium dynamics, the
+        slow plasticity variables in n_long long steps."""
+        _check(lib().pa_fast_forward(self._h, float(duration_ms), int(n_long)))
 
     def kernel_stats(self) -> KernelStats:
         ks = KernelStats()

@@ -393,3 +393,62 @@ def test_plasticity_noise_recurrent_stc_fp64_closed_loop():
     mw.advance(2500 * net.dt)
     assert np.array_equal(mw.read_state(E.FIELD_H), o.syn(O.SYN_H))
     assert np.array_equal(mw.read_state(E.FIELD_V), o.v())
+
+
+def _ff_sequence(model_or_oracle, net, is_oracle):
+    """advance 1000 steps, fast-forward 10 s in 50 long steps, advance 1000 steps"""
+    m = model_or_oracle
+    if is_oracle:
+        m.run(1000)
+        m.fast_forward(int(round(10000.0 / net.dt)), 50)
+        m.run(1000)
+    else:
+        m.advance(1000 * net.dt)
+        m.fast_forward(10000.0, 50)
+        m.advance((2000 + int(round(10000.0 / net.dt))) * net.dt)
+        m.sync()
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_fast_forward_matches_oracle(precision):
+    """Fast-forward of the slow plasticity variables between two stretches of
+    full simulation (the '8h-recall' pattern) on the recurrent STC network with
+    noise, closed loop: FP64 bit-identical to the oracle."""
+    net = W.recurrent_stc(n_exc=96, n_inh=24, sigma_pl=2.90436)
+    o = O.Oracle(net)
+    _ff_sequence(o, net, True)
+    m = E.Model(net, precision=precision)
+    _ff_sequence(m, net, False)
+    if precision == E.PA_FP64:
+        check_state(o, m, precision, exact=True)
+    else:   # mixed: the state after the fast-forward, before chaos sets in
+        assert compare(o.cell_p(), m.read_state(E.FIELD_PRP)) <= 1e-9
+        assert compare(o.syn(O.SYN_Z), m.read_state(E.FIELD_Z)) <= 1e-9
+
+
+def test_state_swap_into_a_new_model():
+    """Save every state field of a model, build a new model of the same network,
+    move its clock to the same step, write the state in: both continue
+    bit-identically (the state-saving mechanism of the '8h-recall' paradigm)."""
+    net = W.recurrent_stc(n_exc=96, n_inh=24, sigma_pl=2.90436)
+    a = E.Model(net, precision=E.PA_FP64)
+    a.advance(1500 * net.dt)
+    a.fast_forward(5000.0, 10)        # no events in flight, no POST_EVENT due
+    fields = [E.FIELD_V, E.FIELD_GATES, E.FIELD_PRP, E.FIELD_G, E.FIELD_C, E.FIELD_W,
+              E.FIELD_H, E.FIELD_Z]
+    saved = {f: a.read_state(f) for f in fields}
+    b = E.Model(net, precision=E.PA_FP64)
+    b.fast_forward(1500 * net.dt + 5000.0, 1)
+    for f in fields:
+        b.write_state(f, saved[f])
+        assert np.array_equal(b.read_state(f), saved[f])
+    t_end = (1500 + int(round(5000.0 / net.dt)) + 1200) * net.dt
+    for m in (a, b):
+        m.advance(t_end)
+    assert np.array_equal(a.read_state(E.FIELD_V), b.read_state(E.FIELD_V))
+    assert np.array_equal(a.read_state(E.FIELD_H), b.read_state(E.FIELD_H))
+    k_swap = 1500 + int(round(5000.0 / net.dt))
+    ga, sa, _ = a.read_spikes()
+    gb, sb, _ = b.read_spikes()
+    after = sa >= k_swap
+    assert len(gb) > 0 and np.array_equal(ga[after], gb) and np.array_equal(sa[after], sb)
