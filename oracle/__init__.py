@@ -36,6 +36,10 @@ def lib():
         L.orc_get_probes.argtypes = [P, P]
         L.orc_get_syn.argtypes = [P, C.c_int32, P]
         L.orc_get_cell_p.argtypes = [P, P]
+        L.orc_get_prp.argtypes = [P, P]
+        L.orc_set_prp.argtypes = [P, P]
+        L.orc_has_diffusion.restype = C.c_int32
+        L.orc_has_diffusion.argtypes = [P, C.c_int32]
         L.orc_get_gates.argtypes = [P, P]
         L.orc_get_cv_geometry.argtypes = [P, P, P, P]
         L.orc_fast_forward.argtypes = [P, C.c_int64, C.c_int64]
@@ -178,6 +182,21 @@ class Oracle:
         out = np.zeros(self.n_cells)
         lib().orc_get_cell_p(self._h, _p(out))
         return out
+
+    def prp(self):
+        """PRP concentration per CV (cell-major) of the cells whose PRP diffuses;
+        0 on every other CV."""
+        out = np.zeros(lib().orc_n_cv(self._h))
+        lib().orc_get_prp(self._h, _p(out))
+        return out
+
+    def set_prp(self, values):
+        a = np.ascontiguousarray(values, np.float64)
+        assert a.shape == (lib().orc_n_cv(self._h),)
+        lib().orc_set_prp(self._h, _p(a))
+
+    def has_diffusion(self, cell: int) -> bool:
+        return bool(lib().orc_has_diffusion(self._h, int(cell)))
 
     def gates(self):
         out = np.zeros(3 * self.n_cells)

@@ -317,6 +317,7 @@ typedef struct {
   double rate_w, rate_h, rate_z, rate_p;
   int64_t dc_steps;
   double sigma;   /* sigma_pl (GB, STC) */
+  double diff_d;  /* STC: PRP diffusivity D_p [um2/ms] (0: one pool per cell) */
   double amp[3];  /* Euler-Maruyama noise amplitude with n of the two thresholds crossed:
                      sigma_pl sqrt(n dt / tau) for tau = tau_w (GB) or tau_h (STC) */
 } orc_mech;
@@ -334,6 +335,11 @@ struct orc_model {
   double *gna_a, *gk_a, *gl_a;
   double *V, *m, *h, *n;
   double *gs, *es, *d, *b, *f, *xp, *xnew;
+  /* PRP diffusion (cells whose STC mechanism has D_p > 0): CV volume [um3],
+     diffusive half-length (L/2)/(pi r^2) [1/um], PRP concentration, the
+     constant backward-Euler matrix (diagonal, coupling to the parent), V/dt */
+  double *vol, *hx, *prp_cv, *prp_d, *prp_a, *prp_vdt, *vtot, *prp_src;
+  int32_t* has_diff;
   double* istep;
   int64_t *k_on, *k_off;
   double *thresh, *p;
@@ -384,9 +390,12 @@ static int n_params_of(int32_t k) {
   return -1;
 }
 /* GB and STC take an optional trailing sigma_pl (the noise scale; 0 if absent) */
+/* GB and STC take an optional trailing sigma_pl; STC then an optional PRP
+ * diffusivity D_p [um2/ms] (Eq. diffusion; 0 or absent: one PRP pool per cell) */
 static int accepts_params(int32_t k, int32_t n) {
   int np = n_params_of(k);
-  return n == np || ((k == ORC_MECH_GB || k == ORC_MECH_STC) && n == np + 1);
+  return n == np || ((k == ORC_MECH_GB || k == ORC_MECH_STC) && n == np + 1) ||
+         (k == ORC_MECH_STC && n == np + 2);
 }
 
 static void push_ev(orc_bucket* bk, int32_t syn, int32_t type) {
@@ -420,7 +429,8 @@ void orc_free(orc_model* M) {
                   M->syn_D, M->syn_pid, M->syn_thr, M->g, M->c, M->w, M->hs, M->z, M->apre, M->apost, M->apre_k, M->apost_k,
                   M->cell_syn_off, M->cell_syn, M->out_off, M->out_syn, M->poisson_syn,
                   M->spk_gid, M->spk_step, M->spk_time, M->probe_cv, M->probes, M->rep_gid,
-                  M->rep_step};
+                  M->rep_step, M->vol, M->hx, M->prp_cv, M->prp_d, M->prp_a, M->prp_vdt,
+                  M->vtot, M->prp_src, M->has_diff};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
   if (M->q) {
     for (int64_t i = 0; i < M->R; ++i) free(M->q[i].v);
@@ -464,6 +474,8 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
     mc->kind = mech_kind[j];
     for (int i = 0; i < given; ++i) mc->p[i] = mech_params[mech_off[j] + i];
     mc->sigma = (given > np) ? mc->p[np] : 0.0;
+    mc->diff_d = (given > np + 1) ? mc->p[np + 1] : 0.0;
+    if (!(mc->diff_d >= 0.0)) { orc_free(M); return fail(-1, "mechanism %d: D_p < 0", j); }
     if (!(mc->sigma >= 0.0)) { orc_free(M); return fail(-1, "mechanism %d: sigma_pl < 0", j); }
     for (int n = 0; n < 3; ++n)
       mc->amp[n] = (given > np) ? mc->sigma * sqrt(((double)n * dt) / mc->p[9]) : 0.0;
@@ -499,6 +511,9 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
   ALLOC(M->V, N); ALLOC(M->m, N); ALLOC(M->h, N); ALLOC(M->n, N);
   ALLOC(M->gs, N); ALLOC(M->es, N); ALLOC(M->d, N); ALLOC(M->b, N);
   ALLOC(M->f, N); ALLOC(M->xp, N); ALLOC(M->xnew, N);
+  ALLOC(M->vol, N); ALLOC(M->hx, N); ALLOC(M->prp_cv, N); ALLOC(M->prp_d, N);
+  ALLOC(M->prp_a, N); ALLOC(M->prp_vdt, N); ALLOC(M->vtot, n_cells); ALLOC(M->has_diff, n_cells);
+  ALLOC(M->prp_src, n_cells);
   ALLOC(M->istep, n_cells); ALLOC(M->k_on, n_cells); ALLOC(M->k_off, n_cells);
   ALLOC(M->thresh, n_cells); ALLOC(M->p, n_cells); ALLOC(M->spiked_prev, n_cells);
   ALLOC(M->spk_flag, n_cells); ALLOC(M->spk_t, n_cells); ALLOC(M->cell_stc_mech, n_cells);
@@ -533,6 +548,8 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
       M->cap[base + i] = (cm * A) * 1e-5;
       M->cdt[base + i] = M->cap[base + i] / dt;
       rhalf[base + i] = ((ra * (0.5 * L)) / (M_PI * (r * r))) * 1e-2;
+      M->vol[base + i] = (M_PI * (r * r)) * L;
+      M->hx[base + i] = (0.5 * L) / (M_PI * (r * r));
       int32_t mj = region[mb + i] == 0 ? ms : md;
       M->cv_mech[base + i] = mj;
       const orc_mech* mc = &M->mech[mj];
@@ -652,6 +669,38 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
           sizeof(int64_t), cmp_syn);
   M->R = maxdelay + 2;
   M->q = (orc_bucket*)calloc((size_t)M->R, sizeof(orc_bucket));
+  /* PRP diffusion (Eq. diffusion with the cable equation's solver): the
+     diffusion part by backward Euler on the cell's tree,
+     V_i (P_i^{k+1} - P*_i)/dt = sum_j gD_ij (P_j^{k+1} - P_i^{k+1}), with gD of
+     two half-cylinders in series, D / ((L_i/2)/(pi r_i^2) + (L_p/2)/(pi r_p^2))
+     [um3/ms]; the matrix is constant: diagonal V_i/dt + sum gD, coupling -gD. */
+  for (int32_t c = 0; c < n_cells; ++c) {
+    int32_t mj = M->cell_stc_mech[c];
+    if (mj < 0 || !(M->mech[mj].diff_d > 0.0)) continue;
+    const double D = M->mech[mj].diff_d;
+    int64_t base = M->cv_off[c], n = M->cv_off[c + 1] - base;
+    for (int64_t i = 0; i < n; ++i) M->xnew[base + i] = 0.0; /* summed couplings */
+    for (int64_t i = 1; i < n; ++i) {
+      int64_t p = base + M->parent[base + i];
+      double gd = D / (M->hx[base + i] + M->hx[p]);
+      M->prp_a[base + i] = -gd;
+      M->xnew[base + i] += gd;
+      M->xnew[p] += gd;
+    }
+    double vt = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      double v = M->vol[base + i];
+      M->prp_vdt[base + i] = v / dt;
+      M->prp_d[base + i] = (v / dt) + M->xnew[base + i];
+      vt = vt + v;
+    }
+    M->vtot[c] = vt;
+    /* synthesis enters the soma CV at p_max V_tot / (V_0 tau_p): the cell's
+       total amount then follows the single pool's equation for the mean
+       concentration (Eq. prp_single_comp) */
+    M->prp_src[c] = vt / M->vol[base];
+    M->has_diff[c] = 1;
+  }
   M->n_probe = n_probe;
   ALLOC(M->probe_cv, n_probe);
   for (int32_t i = 0; i < n_probe; ++i) {
@@ -818,9 +867,11 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
     } else if (mc->kind == ORC_MECH_STC) {
       double h = M->hs[s], z = M->z[s], cc = M->c[s], h0 = q[12];
       S = S + fabs(h - h0);
-      /* Eq. late_phase_weight with the cell's PRP p^k */
-      double T1 = ((h - h0) > q[13]) ? (pk * q[16]) * (1.0 - z) : 0.0;
-      double T2 = ((h0 - h) > q[13]) ? (pk * q[16]) * (z + 0.5) : 0.0;
+      /* Eq. late_phase_weight with the PRP p^k of the cell, or at the synapse's
+         CV when PRP diffuses */
+      double pz = M->has_diff[c] ? M->prp_cv[M->syn_cv[s]] : pk;
+      double T1 = ((h - h0) > q[13]) ? (pz * q[16]) * (1.0 - z) : 0.0;
+      double T2 = ((h0 - h) > q[13]) ? (pz * q[16]) * (z + 0.5) : 0.0;
       M->z[s] = z + mc->rate_z * (T1 - T2);
       /* Eq. early_phase_weight, 10 mV potentiation ceiling */
       double P = (cc > q[5]) ? q[7] * (10.0 - h) : 0.0;
@@ -838,7 +889,23 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
        exceeds theta_pro */
     const orc_mech* mc = &M->mech[M->cell_stc_mech[c]];
     double qs = (S > mc->p[14]) ? mc->p[15] : 0.0;
-    M->p[c] = pk + mc->rate_p * (qs - pk);
+    if (M->has_diff[c]) {
+      /* the reaction as the mechanism's explicit update, P* = P + dt/tau_p
+         (src - P) in every CV (synthesis only at the soma, degradation
+         everywhere), then the diffusion by one backward-Euler solve */
+      double* P = M->prp_cv + base;
+      for (int64_t i = 0; i < n; ++i) {
+        double src = (i == 0) ? qs * M->prp_src[c] : 0.0;
+        double ps = P[i] + mc->rate_p * (src - P[i]);
+        d[i] = M->prp_d[base + i];
+        b[i] = M->prp_vdt[base + i] * ps;
+      }
+      hines(n, par, d, M->prp_a + base, b, M->f + base, M->xp + base, xnew);
+      for (int64_t i = 0; i < n; ++i) P[i] = xnew[i];
+      M->p[c] = P[0];
+    } else {
+      M->p[c] = pk + mc->rate_p * (qs - pk);
+    }
   }
   /* threshold detection at the soma CV with linear interpolation of the time */
   double th = M->thresh[c];
@@ -927,6 +994,8 @@ int orc_run(orc_model* M, int64_t n_steps) {
  * through their closed form as the clock advances by K. */
 int orc_fast_forward(orc_model* M, int64_t K, int64_t n_long) {
   if (K < 0 || n_long < 1 || M->replay) return -1;
+  for (int32_t c = 0; c < M->n_cells; ++c)
+    if (M->has_diff[c]) return -1; /* a long step of the PRP field is not defined */
   const double T = (double)K * M->dt;
   const double dtl = T / (double)n_long;
   for (int64_t s = 0; s < M->n_syn; ++s) {
@@ -982,6 +1051,18 @@ void orc_set_syn(orc_model* M, int32_t field, const double* in) {
   }
 }
 void orc_set_v(orc_model* M, const double* in) { memcpy(M->V, in, sizeof(double) * (size_t)M->n_cv); }
+/* PRP concentration per CV of cells whose PRP diffuses (other CVs: 0) */
+void orc_get_prp(const orc_model* M, double* out) {
+  memcpy(out, M->prp_cv, sizeof(double) * (size_t)M->n_cv);
+}
+void orc_set_prp(orc_model* M, const double* in) {
+  for (int32_t c = 0; c < M->n_cells; ++c) {
+    if (!M->has_diff[c]) continue;
+    for (int64_t i = M->cv_off[c]; i < M->cv_off[c + 1]; ++i) M->prp_cv[i] = in[i];
+    M->p[c] = M->prp_cv[M->cv_off[c]];
+  }
+}
+int32_t orc_has_diffusion(const orc_model* M, int32_t c) { return M->has_diff[c]; }
 void orc_set_cell_p(orc_model* M, const double* in) {
   memcpy(M->p, in, sizeof(double) * (size_t)M->n_cells);
 }

@@ -34,10 +34,13 @@ enum {
   ORC_MECH_HH = 2,     /* params: gnabar, gkbar, gl [S/cm2], ena, ek, el [mV]         */
   ORC_MECH_EXPSYN = 10,/* params: tau [ms], e [mV]                                    */
   ORC_MECH_GB = 11,    /* params: tau, e, tau_c, c_pre, c_post, theta_p, theta_d,
-                          gamma_p, gamma_d, tau_w [ms], w_star, t_c_delay [ms], w0   */
+                          gamma_p, gamma_d, tau_w [ms], w_star, t_c_delay [ms], w0
+                          [, sigma_pl]                                              */
   ORC_MECH_STC = 12,   /* params: tau, e, tau_c, c_pre, c_post, theta_p, theta_d,
                           gamma_p, gamma_d, tau_h, tau_z, tau_p [ms], h0 [mV],
-                          theta_tag [mV], theta_pro [mV], p_max, f_int, t_c_delay    */
+                          theta_tag [mV], theta_pro [mV], p_max, f_int, t_c_delay
+                          [, sigma_pl [, D_p [um2/ms]]]; D_p > 0: the cell's PRP is
+                          a concentration per CV that diffuses (Eq. diffusion)      */
   ORC_MECH_STDP = 13   /* params: tau, e, tau_pre, tau_post, A_pre, A_post, w0, w_max */
 };
 
@@ -96,6 +99,9 @@ int64_t orc_n_probe_samples(const orc_model* m);
 void orc_get_probes(const orc_model* m, double* out);      /* [sample][probe] */
 void orc_get_syn(const orc_model* m, int32_t field, double* out); /* connection order */
 void orc_get_cell_p(const orc_model* m, double* out);      /* PRP per cell */
+void orc_get_prp(const orc_model* m, double* out);  /* PRP per CV of diffusing cells, else 0 */
+void orc_set_prp(orc_model* m, const double* in);   /* per CV; cells without diffusion untouched */
+int32_t orc_has_diffusion(const orc_model* m, int32_t cell);
 void orc_get_gates(const orc_model* m, double* out);       /* m,h,n of each cell's CV 0 */
 void orc_get_cv_geometry(const orc_model* m, double* cap_nF, double* gpas_uS,
                          double* a_uS);                    /* per CV, cell-major */

@@ -60,12 +60,17 @@ def gb_params(tau=5.0, e=0.0, tau_c=20.0, c_pre=1.0, c_post=2.0, theta_p=1.3, th
 def stc_params(tau=5.0, e=0.0, tau_c=48.8, c_pre=0.6, c_post=0.1655, theta_p=3.0, theta_d=1.2,
                gamma_p=1645.6, gamma_d=313.1, tau_h=688.4e3, tau_z=3600.0e3, tau_p=3600.0e3,
                h0=4.20075, theta_tag=0.840149, theta_pro=2.10037, p_max=10.0, f_int=0.1,
-               t_c_delay=18.8, sigma_pl=0.0):
+               t_c_delay=18.8, sigma_pl=0.0, d_p=0.0):
     """Tagging-and-capture rule (Eqs. total_syn_weight .. prp_single_comp,
     plasticity_noise_2), Table 5 with the in-vivo calcium contributions used for
-    networks; sigma_pl = 0 (deterministic; Table 5 gives 2.90436 mV)."""
-    return np.array([tau, e, tau_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_h,
-                     tau_z, tau_p, h0, theta_tag, theta_pro, p_max, f_int, t_c_delay, sigma_pl])
+    networks; sigma_pl = 0 (deterministic; Table 5 gives 2.90436 mV).  d_p > 0
+    [um2/ms] makes the PRP a concentration per CV that diffuses over the cell
+    (Eq. diffusion; 1e-11 m2/s = 1e-2 um2/ms)."""
+    p = [tau, e, tau_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_h,
+         tau_z, tau_p, h0, theta_tag, theta_pro, p_max, f_int, t_c_delay, sigma_pl]
+    if d_p > 0.0:
+        p.append(d_p)
+    return np.array(p)
 
 
 def stdp_params(tau=5.0, e=0.0, tau_pre=16.8, tau_post=33.7, a_pre=0.01, a_post=-0.012,
