@@ -60,7 +60,19 @@ extern "C" {
 #define PA_MECH_STC 12    /* point, expsyn + tagging and capture; params: tau, e, tau_c,
                              c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d, tau_h,
                              tau_z, tau_p [ms], h0 [mV], theta_tag [mV], theta_pro [mV],
-                             p_max, f_int, t_c_delay [ms] [, sigma_pl [mV]] */
+                             p_max, f_int, t_c_delay [ms] [, sigma_pl [mV] [, D_p]] */
+/* PRP diffusion (Eq. diffusion on the cable's tree): with the optional
+ * diffusivity D_p > 0 [um2/ms] (1e-11 m2/s = 1e-2 um2/ms) the PRP of every cell
+ * with STC synapses is a concentration per CV.  Each step, after the synapse
+ * updates (which capture the PRP at their own CV, Eq. late_phase_weight), every
+ * CV takes the explicit reaction step P + dt/tau_p (src - P), src = p_max
+ * V_tot / V_0 at the soma CV while S > theta_pro and 0 elsewhere (so the total
+ * amount follows Eq. prp_single_comp for the mean concentration), then the
+ * field takes one backward-Euler diffusion step, V_i (P_i' - P_i)/dt =
+ * sum_j gD_ij (P_j' - P_i'), gD = D_p / ((L_i/2)/(pi r_i^2) + (L_j/2)/(pi r_j^2))
+ * for adjacent CVs, solved by the same tree elimination as the cable equation.
+ * PA_FIELD_PRP then reads the soma CV's concentration.  Such cells always run
+ * in the narrow bin; pa_fast_forward refuses the model (PA_ERR_STATE). */
 /* Plasticity noise (Eqs. plasticity_noise_1-2): with the optional trailing
  * sigma_pl > 0, each step adds sigma_pl sqrt(n dt / tau) N(0,1) to w (GB,
  * tau = tau_w) or h (STC, tau = tau_h), n = number of the thresholds theta_p,
@@ -94,6 +106,8 @@ extern "C" {
 #define PA_FIELD_V 16      /* membrane potential [mV], per CV in cell-major order */
 #define PA_FIELD_PRP 17    /* PRP concentration p (STC), per cell */
 #define PA_FIELD_GATES 18  /* HH gates m, h, n of each cell's soma CV: 3 values per cell */
+#define PA_FIELD_PRP_CV 19 /* PRP concentration per CV (cell-major) of cells whose PRP
+                              diffuses (STC with D_p > 0); 0 on every other CV */
 
 typedef struct pa_model pa_model;
 
@@ -191,7 +205,8 @@ typedef struct {
  * cells with at least 128 CVs in at least 8 branches and at most 2 synapses
  * per CV are wide; below 1 warp per SM, every cell with at least 128 CVs plus
  * synapses is.  Both bins give identical results.  NARROW_ONLY / WIDE_ALL
- * force every cell into one bin. */
+ * force every cell into one bin, except that a cell whose PRP diffuses is
+ * always narrow. */
 #define PA_FLAG_NARROW_ONLY 16
 #define PA_FLAG_WIDE_ALL 32
 
@@ -288,8 +303,9 @@ int pa_model_info(const pa_model* m, pa_info* info);
 /* Writes a state field (the inverse of pa_read_state, same layout and count):
  * per connection for the synapse fields (entries of connections whose kind
  * lacks the field are ignored; a written STDP trace counts as jumping now),
- * per CV for PA_FIELD_V, per cell for PA_FIELD_PRP and (3 per cell: m, h, n)
- * PA_FIELD_GATES.  Swaps a saved state into a model, e.g. one built from an
+ * per CV for PA_FIELD_V and PA_FIELD_PRP_CV (cells whose PRP diffuses; other
+ * entries ignored), per cell for PA_FIELD_PRP (a diffusing cell's field is set
+ * uniform) and (3 per cell: m, h, n) PA_FIELD_GATES.  Swaps a saved state into a model, e.g. one built from an
  * edited network (the state-saving mechanism of the '8h-recall' paradigm).
  * Synchronises the model's stream. */
 int pa_write_state(pa_model* m, int32_t field, const double* values, int64_t n);

@@ -1063,8 +1063,12 @@ void orc_set_prp(orc_model* M, const double* in) {
   }
 }
 int32_t orc_has_diffusion(const orc_model* M, int32_t c) { return M->has_diff[c]; }
+/* per cell; the field of a cell whose PRP diffuses is set uniform */
 void orc_set_cell_p(orc_model* M, const double* in) {
   memcpy(M->p, in, sizeof(double) * (size_t)M->n_cells);
+  for (int32_t c = 0; c < M->n_cells; ++c)
+    if (M->has_diff[c])
+      for (int64_t i = M->cv_off[c]; i < M->cv_off[c + 1]; ++i) M->prp_cv[i] = in[c];
 }
 void orc_set_gates(orc_model* M, const double* in) {
   for (int32_t c = 0; c < M->n_cells; ++c) {

@@ -131,6 +131,17 @@ struct EpochArgs {
   double* prp;               // STC PRP per lane
   const uint8_t* has_stc;
   int32_t stc_stream;        // index of the STC stream or -1
+  // PRP diffusion (Eq. diffusion; an STC mechanism with D_p > 0, every cell with
+  // STC synapses in the narrow bin): the PRP concentration, the constant
+  // backward-Euler matrix (diagonal V/dt + sum gD, coupling -gD to the parent)
+  // and V/dt per CV in the narrow element layout; per lane the soma's synthesis
+  // scale V_tot / V_0.  prp[] then holds the soma CV's concentration.
+  int32_t prp_diff;
+  double* prp_cv;
+  const double* prp_dg;
+  const double* prp_a;
+  const double* prp_vdt;
+  const double* prp_src;
   int64_t n_lanes;
   // synapse streams
   int32_t n_streams;

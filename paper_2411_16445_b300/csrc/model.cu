@@ -109,6 +109,8 @@ struct pa_model {
   std::vector<int32_t> conn_kind;         // PA_MECH_* of the connection
   std::vector<double> conn_weight;
   std::vector<double> conn_h0;
+  bool prp_diff = false;                  // the STC mechanism's PRP diffuses (D_p > 0)
+  std::vector<uint8_t> cell_diff;         // per gid: the cell's PRP is a field over its CVs
   size_t elem_bytes_m = 8;
   int n_streams = 0;
   pa::StreamParams sp[pa::kMaxStreams];
@@ -262,13 +264,18 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   for (int64_t j = 0; j < n_mech; ++j) {
     int np = n_params_of(mechs[j].kind);
     if (np < 0) return set_err(PA_ERR_ARG, "mechanism %lld: unknown kind %d", (long long)j, mechs[j].kind);
-    // GB and STC take an optional trailing sigma_pl (plasticity noise; 0 if absent)
+    // GB and STC take an optional trailing sigma_pl (plasticity noise; 0 if
+    // absent), STC then an optional PRP diffusivity D_p
     const bool noisy_kind = mechs[j].kind == PA_MECH_GB || mechs[j].kind == PA_MECH_STC;
-    if (!(mechs[j].n_params == np || (noisy_kind && mechs[j].n_params == np + 1)) ||
+    const bool stc_kind = mechs[j].kind == PA_MECH_STC;
+    if (!(mechs[j].n_params == np || (noisy_kind && mechs[j].n_params == np + 1) ||
+          (stc_kind && mechs[j].n_params == np + 2)) ||
         !mechs[j].params)
       return set_err(PA_ERR_ARG, "mechanism %lld: expected %d parameters", (long long)j, np);
     if (mechs[j].n_params > np && !(mechs[j].params[np] >= 0.0))
       return set_err(PA_ERR_ARG, "mechanism %lld: sigma_pl must be >= 0", (long long)j);
+    if (mechs[j].n_params > np + 1 && !(mechs[j].params[np + 1] >= 0.0))
+      return set_err(PA_ERR_ARG, "mechanism %lld: D_p must be >= 0", (long long)j);
     for (int i = 0; i < mechs[j].n_params; ++i)
       if (!std::isfinite(mechs[j].params[i]))
         return set_err(PA_ERR_ARG, "mechanism %lld: non-finite parameter %d", (long long)j, i);
@@ -318,6 +325,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   CUDA_TRY(cudaSetDevice(M->device));
 
   int n_streams = 0, stc_stream = -1;
+  double diff_d = 0.0;  // PRP diffusivity [um2/ms]
   int stream_mech[kMaxStreams];
   for (int64_t m = 0; m < n_mech; ++m) {
     int s = mech_stream[m];
@@ -352,6 +360,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         P.f_int = p[16];
         P.dc_steps = (int32_t)std::llround(p[17] / dt);
         set_noise(P, mechs[m], 18, p[9], dt);
+        if (mechs[m].n_params > 19 && p[19] > 0.0) {
+          M->prp_diff = true;
+          diff_d = p[19];
+        }
         break;
       case PA_MECH_STDP:
         P.kind = SK_STDP;
@@ -410,10 +422,15 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   if ((opt->flags & PA_FLAG_NARROW_ONLY) && (opt->flags & PA_FLAG_WIDE_ALL))
     return set_err(PA_ERR_ARG, "PA_FLAG_NARROW_ONLY and PA_FLAG_WIDE_ALL exclude each other");
   std::vector<char> wide(n_cells, 0);
+  M->cell_diff.assign(n_cells, 0);
   {
     std::vector<int64_t> cell_syn(n_cells, 0);
     for (int64_t c = 0; c < n_conn; ++c)
-      if (conns[c].dst_gid >= 0 && conns[c].dst_gid < n_cells) ++cell_syn[conns[c].dst_gid];
+      if (conns[c].dst_gid >= 0 && conns[c].dst_gid < n_cells) {
+        ++cell_syn[conns[c].dst_gid];
+        if (M->prp_diff && mechs[conns[c].mech].kind == PA_MECH_STC)
+          M->cell_diff[conns[c].dst_gid] = 1;
+      }
     std::vector<int32_t> morph_branches(n_morph, 0);
     for (int64_t j = 0; j < n_morph; ++j)
       for (int i = 0; i < morphs[j].n_cv; ++i)
@@ -427,8 +444,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
                             morph_branches[cells[c].morph] >= kWideMinBranches &&
                             cell_syn[c] <= (int64_t)kWideMaxSynPerCV * M->cell_ncv[c];
       const bool heavy = M->cell_ncv[c] + cell_syn[c] >= kWideMinWork;
-      wide[c] = (opt->flags & PA_FLAG_WIDE_ALL) ||
-                (!(opt->flags & PA_FLAG_NARROW_ONLY) && ((few && branched) || (idle && heavy)));
+      // a diffusing PRP field is solved by the thread-per-cell bin only
+      wide[c] = !M->cell_diff[c] &&
+                ((opt->flags & PA_FLAG_WIDE_ALL) ||
+                 (!(opt->flags & PA_FLAG_NARROW_ONLY) && ((few && branched) || (idle && heavy))));
     }
   }
   // narrow cells sorted by CV count (descending) and dealt into groups of 32
@@ -491,6 +510,13 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<double> h_iinj(n_lanes, 0.0), h_thresh(n_lanes, 0.0);
   std::vector<int64_t> h_kon(n_lanes, 0), h_koff(n_lanes, 0);
   std::vector<double> rhalf, gi_v, gax, cdt_v, dcc;
+  std::vector<double> h_pcv, h_pdg, h_pa, h_pvdt, h_psrc, vol, hx, gdx;
+  if (M->prp_diff) {
+    h_pdg.assign(n_elem, 1.0);
+    h_pa.assign(n_elem, 0.0);
+    h_pvdt.assign(n_elem, 0.0);
+    h_psrc.assign(n_lanes, 0.0);
+  }
   for (int64_t L = 0; L < n_lanes; ++L) {
     if (lane_gid[L] < 0) continue;
     const pa_cell& cl = cells[lane_gid[L]];
@@ -550,6 +576,34 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         h_ocn[elem(L, i)] = h_och[elem(L, p)];
         h_och[elem(L, p)] = (int16_t)i;
       }
+    }
+    if (M->cell_diff[lane_gid[L]]) {
+      // PRP diffusion (Eq. diffusion on the cable's tree): CV volume, the
+      // diffusive conductance of two half-cylinders in series
+      // D / ((L_i/2)/(pi r_i^2) + (L_p/2)/(pi r_p^2)), summed in CV order
+      vol.assign(n, 0.0);
+      hx.assign(n, 0.0);
+      gdx.assign(n, 0.0);
+      for (int i = 0; i < n; ++i) {
+        const double Lc = g.length_um[i], r = 0.5 * g.diam_um[i];
+        vol[i] = (kPi * (r * r)) * Lc;
+        hx[i] = (0.5 * Lc) / (kPi * (r * r));
+      }
+      for (int i = 1; i < n; ++i) {
+        const int p = g.parent[i];
+        const double gd = diff_d / (hx[i] + hx[p]);
+        h_pa[elem(L, i)] = -gd;
+        gdx[i] += gd;
+        gdx[p] += gd;
+      }
+      double vt = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const int64_t e = elem(L, i);
+        h_pvdt[e] = vol[i] / dt;
+        h_pdg[e] = (vol[i] / dt) + gdx[i];
+        vt = vt + vol[i];
+      }
+      h_psrc[L] = vt / vol[0];  // synthesis at the soma: p_max V_tot / (V_0 tau_p)
     }
     h_iinj[L] = cl.i_step;
     h_kon[L] = std::llround(cl.t_on / dt);
@@ -849,6 +903,11 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_wbr_e = R(sizeof(int32_t) * std::max<size_t>(h_wbr_e.size(), 1));
   const size_t o_wlvl = R(sizeof(int32_t) * std::max<size_t>(h_wlvl.size(), 1));
   const size_t o_clock = R(sizeof(EpochClock));
+  size_t o_pcv = 0, o_pdg = 0, o_pa = 0, o_pvdt = 0, o_psrc = 0;
+  if (M->prp_diff) {
+    o_pcv = R(8 * n_elem); o_pdg = R(8 * n_elem); o_pa = R(8 * n_elem);
+    o_pvdt = R(8 * n_elem); o_psrc = R(8 * n_lanes);
+  }
 
   const size_t total = ar.used;
   cudaError_t ce = cudaMalloc((void**)&M->dmem, total);
@@ -882,6 +941,9 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   putv(o_wcell, h_wcell); putv(o_wbr_s, h_wbr_s); putv(o_wbr_e, h_wbr_e); putv(o_wlvl, h_wlvl);
   putv(o_iinj, h_iinj); putv(o_kon, h_kon); putv(o_koff, h_koff); putv(o_th, h_thresh);
   putv(o_hasstc, h_has_stc);
+  if (M->prp_diff) {
+    putv(o_pdg, h_pdg); putv(o_pa, h_pa); putv(o_pvdt, h_pvdt); putv(o_psrc, h_psrc);
+  }
   for (int s = 0; s < n_streams; ++s) {
     putv(o_s[s][0], s_sbase[s]);
     putv(o_s[s][1], s_cvf[s]);
@@ -939,6 +1001,14 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   A.prp = (double*)P8(o_prp);
   A.has_stc = (const uint8_t*)P8(o_hasstc);
   A.stc_stream = stc_stream;
+  if (M->prp_diff) {
+    A.prp_diff = 1;
+    A.prp_cv = (double*)P8(o_pcv);
+    A.prp_dg = (const double*)P8(o_pdg);
+    A.prp_a = (const double*)P8(o_pa);
+    A.prp_vdt = (const double*)P8(o_pvdt);
+    A.prp_src = (const double*)P8(o_psrc);
+  }
   A.n_lanes = n_lanes;
   A.n_streams = n_streams;
   M->mask_bases.clear();
@@ -1443,6 +1513,20 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
     }
     return PA_OK;
   }
+  if (field == PA_FIELD_PRP_CV) {
+    *n_out = M->n_cv;
+    if (cap == 0) return PA_OK;
+    if (!out || cap < M->n_cv) return set_err(PA_ERR_ARG, "output too small");
+    int rc = fetch(M->ea.prp_cv, M->prp_diff ? M->total_rows * kLanes : 0, 8, tmp);
+    if (rc) return rc;
+    for (int64_t c = 0; c < M->n_cells; ++c) {
+      const int64_t L = M->lane_of_gid[c], g = L / kLanes;
+      for (int i = 0; i < M->cell_ncv[c]; ++i)
+        out[M->cell_cv_off[c] + i] =
+            M->cell_diff[c] ? tmp[((int64_t)M->row_base[g] + i) * kLanes + L % kLanes] : 0.0;
+    }
+    return PA_OK;
+  }
   if (field == PA_FIELD_PRP || field == PA_FIELD_GATES) {
     const int per = field == PA_FIELD_GATES ? 3 : 1;
     *n_out = M->n_cells * per;
@@ -1590,6 +1674,8 @@ int pa_fast_forward(pa_model* M, double duration_ms, int64_t n_long) {
   using namespace pa;
   if (!M) return set_err(PA_ERR_ARG, "model is NULL");
   if (M->replay) return set_err(PA_ERR_STATE, "pa_fast_forward does not run in open-loop replay");
+  if (M->prp_diff)
+    return set_err(PA_ERR_STATE, "pa_fast_forward: a diffusing PRP field has no long-step scheme");
   const double ks = duration_ms / M->dt;
   const int64_t K = std::llround(ks);
   if (!std::isfinite(ks) || K < 0 || std::fabs(ks - (double)K) > 1e-6 * std::max(1.0, std::fabs(ks)))
@@ -1651,6 +1737,33 @@ int pa_write_state(pa_model* M, int32_t field, const double* in, int64_t n) {
         for (int i = 0; i < M->cell_ncv[c]; ++i)
           v[g < M->n_narrow ? ((int64_t)M->row_base[g] + i) * kLanes + L % kLanes
                             : ((int64_t)M->row_base[g] << 5) + i] = in[M->cell_cv_off[c] + i];
+      }
+    });
+  }
+  if (field == PA_FIELD_PRP_CV || (field == PA_FIELD_PRP && M->prp_diff)) {
+    // the field of each diffusing cell (PA_FIELD_PRP: uniform at the cell's
+    // value) and the soma value that PA_FIELD_PRP reads back
+    const bool per_cv = field == PA_FIELD_PRP_CV;
+    const int64_t want = per_cv ? M->n_cv : M->n_cells;
+    if (n != want) return set_err(PA_ERR_ARG, "expected %lld values", (long long)want);
+    if (M->prp_diff) {
+      int rc = rmw(M->ea.prp_cv, M->total_rows * kLanes, 8, [&](char* raw) {
+        double* v = (double*)raw;
+        for (int64_t c = 0; c < M->n_cells; ++c) {
+          if (!M->cell_diff[c]) continue;
+          const int64_t L = M->lane_of_gid[c], g = L / kLanes;
+          for (int i = 0; i < M->cell_ncv[c]; ++i)
+            v[((int64_t)M->row_base[g] + i) * kLanes + L % kLanes] =
+                per_cv ? in[M->cell_cv_off[c] + i] : in[c];
+        }
+      });
+      if (rc) return rc;
+    }
+    return rmw(M->ea.prp, M->n_lanes, 8, [&](char* raw) {
+      double* v = (double*)raw;
+      for (int64_t c = 0; c < M->n_cells; ++c) {
+        if (per_cv && !M->cell_diff[c]) continue;
+        v[M->lane_of_gid[c]] = per_cv ? in[M->cell_cv_off[c]] : in[c];
       }
     });
   }

@@ -342,6 +342,78 @@ def recurrent_stc(n_exc=1600, n_inh=400, p=0.1, dt=0.2, seed=None, w_bg=1e-3,
     return b.build()
 
 
+def stc_morpho_cell(large_cell: bool = False, large_dend: bool = False) -> Morphology:
+    """Multi-compartment STC neuron of Table 6 (1 um compartments of one radius,
+    6 or 12 um): the synthesis compartment (CV 0, the soma proper) between two
+    halves of the somatic cylinder (l_soma / 2 each), the apical branch (12.5 or
+    25 um) continuing one half and the basal branch (5 or 10 um) the other: 31
+    or 48 CVs.  Only CV 0 is region 0 (the engine's HH is somatic)."""
+    r = 12.0 if large_cell else 6.0
+    half = int(round((24.0 if large_cell else 12.0) / 2))
+    apical = 25.0 if large_dend else 12.5
+    basal = 10.0 if large_dend else 5.0
+
+    def pieces(total):
+        n = int(np.floor(total))
+        out = [1.0] * n
+        if total - n > 1e-9:
+            out.append(total - n)
+        return out
+
+    lengths = [1.0]
+    parent = [-1]
+    for branch in (apical, basal):
+        prev = 0
+        for ln in [1.0] * half + pieces(branch):
+            parent.append(prev)
+            lengths.append(ln)
+            prev = len(lengths) - 1
+    n = len(lengths)
+    return Morphology(np.asarray(parent, np.int32), np.asarray(lengths),
+                      np.full(n, 2.0 * r), np.r_[0, np.ones(n - 1)].astype(np.int32))
+
+
+def recurrent_stc_morpho(n_exc=160, n_inh=40, p=0.1, dt=0.2, seed=None, d_p=1e-2,
+                         large_cell=False, large_dend=False, w_ext=4e-3, ext_rate=40.0,
+                         n_ext=4, w_rec=2e-3, w_inh=2e-3, sigma_pl=0.0,
+                         tau_p=3600.0e3) -> Network:
+    """Recurrent tagging-and-capture network of multi-compartment neurons
+    (Sec. on memory consolidation in networks of morphological neurons): the
+    excitatory cells have the morphology of stc_morpho_cell and a diffusing PRP
+    (D_p, um2/ms; 1e-2 = 1e-11 m2/s); external Poisson input onto the apical
+    tip, recurrent E->E (STC) synapses onto the basal tip, inhibition onto the
+    soma; inhibitory cells are single-compartment.  HH soma, passive elsewhere;
+    Erdos-Renyi connectivity without self-loops, 3 ms delays."""
+    name = "recurrent_stc_morpho"
+    b = _Builder(dt, config_seed(name) if seed is None else seed, name)
+    rng = np.random.default_rng(b.seed)
+    hh = b.mech(HH, hh_params())
+    pas = b.mech(PAS, pas_params(3e-5, -54.4))
+    exc = b.mech(EXPSYN, expsyn_params(5.0, 0.0))
+    inh = b.mech(EXPSYN, expsyn_params(5.0, -80.0))
+    stc = b.mech(STC, stc_params(sigma_pl=sigma_pl, d_p=d_p, tau_p=tau_p))
+    mo = stc_morpho_cell(large_cell, large_dend)
+    m_e = b.morph(mo)
+    m_i = b.morph(soma_only(12.0))
+    tips = [i for i in range(1, mo.n_cv) if i not in set(mo.parent.tolist())]
+    apical_tip, basal_tip = tips[0], tips[1]
+    b.cells_add(n_exc, m_e, hh, pas)
+    b.cells_add(n_inh, m_i, hh, hh)
+    n = n_exc + n_inh
+    adj = rng.random((n, n)) < p
+    np.fill_diagonal(adj, False)
+    src, dst = np.nonzero(adj)
+    e_src, e_dst = src < n_exc, dst < n_exc
+    mech = np.where(e_src, np.where(e_dst, stc, exc), inh)
+    cv = np.where(e_src & e_dst, basal_tip, 0)
+    w = np.where(e_src, w_rec, w_inh) * rng.uniform(0.9, 1.1, size=src.shape[0])
+    b.connect(src, dst, cv, mech, w, delay=3.0)
+    ext_dst = np.repeat(np.arange(n), n_ext)
+    ext_cv = np.where(ext_dst < n_exc, apical_tip, 0)
+    b.connect(SRC_POISSON, ext_dst, ext_cv, exc, w_ext, rate=ext_rate)
+    return b.build()
+
+
 def morphology_sweep(n_nets=64, cells_per_net=500, p=0.1, dt=0.2, seed=None,
                      w_syn=1e-3, drive_hz=10.0) -> Network:
     """Many independent networks built like the single-neuron workload: per network a

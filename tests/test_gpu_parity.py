@@ -452,3 +452,98 @@ def test_state_swap_into_a_new_model():
     gb, sb, _ = b.read_spikes()
     after = sa >= k_swap
     assert len(gb) > 0 and np.array_equal(ga[after], gb) and np.array_equal(sa[after], sb)
+
+
+def _diffusion_net(large_dend=False):
+    # D_p = 1 um2/ms and tau_p = 200 ms so that the field moves within the run
+    return W.recurrent_stc_morpho(n_exc=80, n_inh=20, d_p=1.0, tau_p=200.0, w_ext=0.02,
+                                  large_dend=large_dend)
+
+
+def _tag(net, seed=3):
+    """early-phase weights above theta_tag on a random half of the E->E synapses
+    (so that S exceeds theta_pro and PRP is synthesised)"""
+    rng = np.random.default_rng(seed)
+    h = np.zeros(net.n_conn)
+    stc = net.conn_mech == 4
+    h[stc] = 4.20075 + np.where(rng.random(stc.sum()) < 0.5, rng.uniform(0.9, 1.5, stc.sum()), 0.0)
+    return h
+
+
+@pytest.mark.parametrize("large_dend", [False, True])
+def test_prp_diffusion_fp64_bit_exact(large_dend):
+    """PRP diffusing over multi-compartment STC cells (31 / 48 CVs, branched at
+    the soma), closed loop: the PRP field per CV, tags, weights, voltages and
+    spikes bit-identical to the oracle."""
+    net = _diffusion_net(large_dend)
+    h = _tag(net)
+    o = O.Oracle(net)
+    o.set_syn(O.SYN_H, h)
+    o.run(2500)
+    m = E.Model(net, precision=E.PA_FP64)
+    m.write_state(E.FIELD_H, h)
+    for k in (700, 1900, 2500):
+        m.advance(k * net.dt)
+    m.sync()
+    check_state(o, m, E.PA_FP64, exact=True)
+    po, pg = o.prp(), m.read_state(E.FIELD_PRP_CV)
+    assert np.array_equal(po, pg)
+    exc = po.reshape(-1)[: 80 * net.morphs[0].n_cv].reshape(80, -1)
+    assert exc.max() > 0 and np.any(exc[:, 0] > 1.2 * exc[:, -1])   # a field, not a pool
+    assert np.all(po[80 * net.morphs[0].n_cv:] == 0)               # no field elsewhere
+
+
+def test_prp_diffusion_mixed_open_loop():
+    net = _diffusion_net()
+    h = _tag(net)
+    ref = O.Oracle(net)
+    ref.set_syn(O.SYN_H, h)
+    ref.run(2500)
+    gid, step, _ = ref.spikes()
+    o = O.Oracle(net)
+    o.set_syn(O.SYN_H, h)
+    o.set_replay(gid, step)
+    o.run(2500)
+    m = E.Model(net, precision=E.PA_MIXED)
+    m.write_state(E.FIELD_H, h)
+    m.set_replay(gid, step)
+    m.advance(2500 * net.dt)
+    m.sync()
+    check_state(o, m, E.PA_MIXED)
+    po, pg = o.prp(), m.read_state(E.FIELD_PRP_CV)
+    assert compare(po, pg) <= 1e-9 * max(1.0, po.max())
+
+
+def test_prp_diffusion_state_io_bins_and_refusals():
+    """The field written per CV or uniformly per cell, read back and continued
+    bit-identically to the oracle with the same writes; cells with a diffusing
+    PRP stay narrow under FLAG_WIDE_ALL (the others go wide); fast-forward is
+    refused."""
+    net = _diffusion_net()
+    ncv = net.n_cv
+    rng = np.random.default_rng(9)
+    field = rng.uniform(0.0, 3.0, ncv)
+    per_cell = rng.uniform(0.0, 3.0, net.n_cells)
+    o = O.Oracle(net)
+    o.set_syn(O.SYN_H, _tag(net))
+    o.set_prp(field)
+    o.run(300)
+    o.set_cell_p(per_cell)
+    o.run(300)
+    for flags in (0, E.FLAG_WIDE_ALL):
+        m = E.Model(net, precision=E.PA_FP64, flags=flags)
+        if flags:
+            assert m.info().n_wide == 20            # the inhibitory cells only
+        m.write_state(E.FIELD_H, _tag(net))
+        m.write_state(E.FIELD_PRP_CV, field)
+        got = m.read_state(E.FIELD_PRP_CV)
+        want = np.where(np.repeat(np.arange(net.n_cells) < 80, net.cell_ncv()), field, 0.0)
+        assert np.array_equal(got, want)
+        m.advance(300 * net.dt)
+        m.write_state(E.FIELD_PRP, per_cell)
+        m.advance(600 * net.dt)
+        m.sync()
+        check_state(o, m, E.PA_FP64, exact=True)
+        assert np.array_equal(o.prp(), m.read_state(E.FIELD_PRP_CV))
+        with pytest.raises(E.PaError):
+            m.fast_forward(1000.0, 10)
