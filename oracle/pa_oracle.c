@@ -338,7 +338,7 @@ struct orc_model {
   /* PRP diffusion (cells whose STC mechanism has D_p > 0): CV volume [um3],
      diffusive half-length (L/2)/(pi r^2) [1/um], PRP concentration, the
      constant backward-Euler matrix (diagonal, coupling to the parent), V/dt */
-  double *vol, *hx, *prp_cv, *prp_d, *prp_a, *prp_vdt, *vtot, *prp_src;
+  double *vol, *hx, *prp_cv, *prp_d, *prp_a, *prp_vdt, *vtot, *prp_src, *prp_gsum;
   int32_t* has_diff;
   double* istep;
   int64_t *k_on, *k_off;
@@ -430,7 +430,7 @@ void orc_free(orc_model* M) {
                   M->cell_syn_off, M->cell_syn, M->out_off, M->out_syn, M->poisson_syn,
                   M->spk_gid, M->spk_step, M->spk_time, M->probe_cv, M->probes, M->rep_gid,
                   M->rep_step, M->vol, M->hx, M->prp_cv, M->prp_d, M->prp_a, M->prp_vdt,
-                  M->vtot, M->prp_src, M->has_diff};
+                  M->vtot, M->prp_src, M->prp_gsum, M->has_diff};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
   if (M->q) {
     for (int64_t i = 0; i < M->R; ++i) free(M->q[i].v);
@@ -513,7 +513,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
   ALLOC(M->f, N); ALLOC(M->xp, N); ALLOC(M->xnew, N);
   ALLOC(M->vol, N); ALLOC(M->hx, N); ALLOC(M->prp_cv, N); ALLOC(M->prp_d, N);
   ALLOC(M->prp_a, N); ALLOC(M->prp_vdt, N); ALLOC(M->vtot, n_cells); ALLOC(M->has_diff, n_cells);
-  ALLOC(M->prp_src, n_cells);
+  ALLOC(M->prp_src, n_cells); ALLOC(M->prp_gsum, N);
   ALLOC(M->istep, n_cells); ALLOC(M->k_on, n_cells); ALLOC(M->k_off, n_cells);
   ALLOC(M->thresh, n_cells); ALLOC(M->p, n_cells); ALLOC(M->spiked_prev, n_cells);
   ALLOC(M->spk_flag, n_cells); ALLOC(M->spk_t, n_cells); ALLOC(M->cell_stc_mech, n_cells);
@@ -691,6 +691,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
     for (int64_t i = 0; i < n; ++i) {
       double v = M->vol[base + i];
       M->prp_vdt[base + i] = v / dt;
+      M->prp_gsum[base + i] = M->xnew[base + i];
       M->prp_d[base + i] = (v / dt) + M->xnew[base + i];
       vt = vt + v;
     }
@@ -794,6 +795,26 @@ static void queue_spike_events(orc_model* M, int32_t gid, int64_t k) {
   }
 }
 
+/* One step of the diffusing PRP field of cell c: the reaction as the
+   mechanism's explicit update, P* = P + rate (src - P) in every CV (rate =
+   step / tau_p; synthesis only at the soma, degradation everywhere), then the
+   diffusion by one backward-Euler solve with diagonal diag[] and right-hand
+   side vdt[] P* (vdt = V / step).  Uses the cell's solver scratch. */
+static void prp_field_step(orc_model* M, int32_t c, double qs, double rate, const double* diag,
+                           const double* vdt) {
+  int64_t base = M->cv_off[c], n = M->cv_off[c + 1] - base;
+  double *P = M->prp_cv + base, *d = M->d + base, *b = M->b + base, *x = M->xnew + base;
+  for (int64_t i = 0; i < n; ++i) {
+    double src = (i == 0) ? qs * M->prp_src[c] : 0.0;
+    double ps = P[i] + rate * (src - P[i]);
+    d[i] = diag[base + i];
+    b[i] = vdt[base + i] * ps;
+  }
+  hines(n, M->parent + base, d, M->prp_a + base, b, M->f + base, M->xp + base, x);
+  for (int64_t i = 0; i < n; ++i) P[i] = x[i];
+  M->p[c] = P[0];
+}
+
 /* steps 2-5 for one cell */
 static void cell_step(orc_model* M, int32_t c, int64_t k) {
   const double dt = M->dt;
@@ -890,19 +911,7 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
     const orc_mech* mc = &M->mech[M->cell_stc_mech[c]];
     double qs = (S > mc->p[14]) ? mc->p[15] : 0.0;
     if (M->has_diff[c]) {
-      /* the reaction as the mechanism's explicit update, P* = P + dt/tau_p
-         (src - P) in every CV (synthesis only at the soma, degradation
-         everywhere), then the diffusion by one backward-Euler solve */
-      double* P = M->prp_cv + base;
-      for (int64_t i = 0; i < n; ++i) {
-        double src = (i == 0) ? qs * M->prp_src[c] : 0.0;
-        double ps = P[i] + mc->rate_p * (src - P[i]);
-        d[i] = M->prp_d[base + i];
-        b[i] = M->prp_vdt[base + i] * ps;
-      }
-      hines(n, par, d, M->prp_a + base, b, M->f + base, M->xp + base, xnew);
-      for (int64_t i = 0; i < n; ++i) P[i] = xnew[i];
-      M->p[c] = P[0];
+      prp_field_step(M, c, qs, mc->rate_p, M->prp_d, M->prp_vdt);
     } else {
       M->p[c] = pk + mc->rate_p * (qs - pk);
     }
@@ -994,10 +1003,18 @@ int orc_run(orc_model* M, int64_t n_steps) {
  * through their closed form as the clock advances by K. */
 int orc_fast_forward(orc_model* M, int64_t K, int64_t n_long) {
   if (K < 0 || n_long < 1 || M->replay) return -1;
-  for (int32_t c = 0; c < M->n_cells; ++c)
-    if (M->has_diff[c]) return -1; /* a long step of the PRP field is not defined */
   const double T = (double)K * M->dt;
   const double dtl = T / (double)n_long;
+  /* a diffusing PRP field takes its long steps with the long step's matrix:
+     diagonal V/dtl + sum gD, right-hand side V/dtl P* */
+  double *dl = calloc((size_t)M->n_cv + 1, sizeof(double)), *vl = calloc((size_t)M->n_cv + 1, sizeof(double));
+  if (!dl || !vl) { free(dl); free(vl); return -1; }
+  for (int32_t c = 0; c < M->n_cells; ++c)
+    if (M->has_diff[c])
+      for (int64_t i = M->cv_off[c]; i < M->cv_off[c + 1]; ++i) {
+        vl[i] = M->vol[i] / dtl;
+        dl[i] = (M->vol[i] / dtl) + M->prp_gsum[i];
+      }
   for (int64_t s = 0; s < M->n_syn; ++s) {
     const orc_mech* mc = &M->mech[M->syn_mech[s]];
     M->g[s] = M->g[s] * exp(-T / mc->p[0]);
@@ -1019,8 +1036,9 @@ int orc_fast_forward(orc_model* M, int64_t K, int64_t n_long) {
         } else if (mc->kind == ORC_MECH_STC) {
           double h = M->hs[s], z = M->z[s], h0 = q[12];
           S = S + fabs(h - h0);
-          double T1 = ((h - h0) > q[13]) ? (pk * q[16]) * (1.0 - z) : 0.0;
-          double T2 = ((h0 - h) > q[13]) ? (pk * q[16]) * (z + 0.5) : 0.0;
+          double pz = M->has_diff[c] ? M->prp_cv[M->syn_cv[s]] : pk;
+          double T1 = ((h - h0) > q[13]) ? (pz * q[16]) * (1.0 - z) : 0.0;
+          double T2 = ((h0 - h) > q[13]) ? (pz * q[16]) * (z + 0.5) : 0.0;
           M->z[s] = z + (dtl / q[10]) * (T1 - T2);
           M->hs[s] = h + (dtl / q[9]) * (0.1 * (h0 - h));
         }
@@ -1028,10 +1046,13 @@ int orc_fast_forward(orc_model* M, int64_t K, int64_t n_long) {
       if (M->cell_stc_mech[c] >= 0) {
         const orc_mech* mc = &M->mech[M->cell_stc_mech[c]];
         double qs = (S > mc->p[14]) ? mc->p[15] : 0.0;
-        M->p[c] = pk + (dtl / mc->p[11]) * (qs - pk);
+        if (M->has_diff[c]) prp_field_step(M, c, qs, dtl / mc->p[11], dl, vl);
+        else M->p[c] = pk + (dtl / mc->p[11]) * (qs - pk);
       }
     }
   }
+  free(dl);
+  free(vl);
   M->step += K;
   return 0;
 }

@@ -121,7 +121,9 @@ uint32_t orc_poisson_u32(uint64_t seed, uint64_t stream, int64_t step);
 double orc_log(double x);
 double orc_cis2pi(double v, int which);
 double orc_normal(uint64_t seed, uint64_t id, int64_t step);
-/* Fast-forward K steps with n_long long steps of the slow plasticity variables. */
+/* Fast-forward K steps with n_long long steps of the slow plasticity variables
+ * (a diffusing PRP field: its explicit reaction and backward-Euler diffusion
+ * with the long step).  -1 on bad arguments or in replay. */
 int orc_fast_forward(orc_model* M, int64_t K, int64_t n_long);
 void orc_set_syn(orc_model* M, int32_t field, const double* in);
 void orc_set_v(orc_model* M, const double* in);

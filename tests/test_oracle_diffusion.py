@@ -167,10 +167,37 @@ def test_single_cv_matches_the_single_pool():
         assert np.allclose(oo[0].syn(O.SYN_Z), oo[1].syn(O.SYN_Z), rtol=1e-12)
 
 
-def test_fast_forward_refused_and_bad_diffusivity():
-    o = O.Oracle(_cell(_chain(4, 10.0, 2.0), 1.0))
-    with pytest.raises(ValueError):
-        o.fast_forward(100, 2)
+def test_fast_forward_long_steps_of_the_field():
+    """Fast-forward: the field takes backward-Euler diffusion steps of the long
+    step (chain modes divided by 1 + dtl rate) and the explicit degradation of
+    the long step; the amount follows the single pool's long-step recursion."""
+    n, L, D, dt, tau_p = 16, 10.0, 10.0, 0.2, 5000.0
+    o = O.Oracle(_cell(_chain(n, L, 2.0), D, tau_p=tau_p, syn_cv=(5,), dt=dt))
+    i = np.arange(n)
+    phi = np.cos(math.pi * 2 * (i + 0.5) / n)
+    o.set_prp(1.0 + 0.5 * phi)
+    K, n_long = 50_000, 40                          # 10 s in 40 steps of 250 ms
+    o.fast_forward(K, n_long)
+    dtl = K * dt / n_long
+    lam = (2 * D / L ** 2) * (1 - math.cos(math.pi * 2 / n))
+    r = dtl / tau_p
+    want = (1 - r) ** n_long + 0.5 * ((1 - r) / (1 + dtl * lam)) ** n_long * phi
+    assert np.allclose(o.prp(), want, rtol=0, atol=1e-12)
+    # with synthesis: the amount follows A' = (1 - r) A + r p_max V_tot
+    rng = np.random.default_rng(4)
+    morph = W.random_binary_tree(rng, 10)
+    o = O.Oracle(_cell(morph, 0.3, tau_p=tau_p, syn_cv=rng.integers(0, morph.n_cv, 12), dt=dt))
+    o.set_syn(O.SYN_H, np.full(12, H0 + 1.0))      # S = 12 > theta_pro, tagged, constant
+    o.fast_forward(K, n_long)
+    V = _volumes(morph)
+    A = 0.0
+    for _ in range(n_long):
+        A = (1 - r) * A + r * P_MAX * V.sum()
+    assert math.isclose(V @ o.prp(), A, rel_tol=1e-12)
+    assert o.step_count() == K
+
+
+def test_bad_diffusivity():
     net = _cell(_chain(4, 10.0, 2.0), 1.0)
     net.mech_params[1][-1] = -1.0
     with pytest.raises(ValueError):
