@@ -61,6 +61,9 @@ def parse():
                    help="skip the batched morphology-sweep measurement")
     p.add_argument("--serve-jobs", type=int, default=80,
                    help="serving measurement on this many jobs of the trace (0: skip)")
+    p.add_argument("--recall", action="store_true",
+                   help="time the 10s-recall and 8h-recall paradigms of the tagging-and-capture "
+                        "networks (ball-and-stick with a PRP pool; 48-CV cells with PRP diffusion)")
     p.add_argument("--shape", type=int, default=-1,
                    help="force this epoch-kernel shape instead of autotuning")
     return p.parse_args()
@@ -432,6 +435,112 @@ def busyring_bench(device, cells_list, depths, precision_name, extra_flags=0):
     return rows
 
 
+def _with_step(net, cells, i_nA, t_on, t_off):
+    """a copy of net whose cells `cells` receive a somatic current step"""
+    import copy
+    n2 = copy.copy(net)
+    n2.cell_istep = net.cell_istep.copy()
+    n2.cell_ton = net.cell_ton.copy()
+    n2.cell_toff = net.cell_toff.copy()
+    n2.cell_istep[cells] = i_nA
+    n2.cell_ton[cells] = t_on
+    n2.cell_toff[cells] = t_off
+    return n2
+
+
+def recall_bench(device, n_long_per_hour=3600, cpu=True):
+    """The '10s-recall' and '8h-recall' paradigms of the tagging-and-capture
+    network (Secs. on memory consolidation, Fig. 6 and Supplementary Fig. S13):
+    2000 cells (1600 E + 400 I), learning by a 0.1 s current step into a core
+    of 150 E cells, recall by a 0.1 s step into 75 of them, 10 s or 8 h later.
+    The recall stimulus lives in a second model into which the whole state is
+    swapped (the paradigm's state-saving mechanism); the 8 h wait is a
+    fast-forward of the slow plasticity variables in long steps
+    (n_long_per_hour per hour).  Networks: ball-and-stick cells (9 CVs) with
+    one PRP pool per cell, and the 48-CV morphological cells of Table 6 (small
+    cells, large dendrites) with PRP diffusing at 1e-11 m2/s.  FP64; wall
+    times of each phase (synchronised), as the paper's totals."""
+    import torch
+    from paper_2411_16445_b300 import engine as E
+    from paper_2411_16445_b300 import workloads as W
+    torch.cuda.set_device(device)
+    stream = E.C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    nets = {
+        "ball_and_stick_pool": W.recurrent_stc(n_exc=1600, n_inh=400),
+        "morpho48_diffusion": W.recurrent_stc_morpho(n_exc=1600, n_inh=400, d_p=1e-2,
+                                                     large_dend=True),
+    }
+    core = np.arange(150)
+    t_learn = (100.0, 200.0)
+    rows = []
+    for name, base in nets.items():
+        dt = base.dt
+        learn = _with_step(base, core, 1.0, *t_learn)
+        fields = [E.FIELD_V, E.FIELD_GATES, E.FIELD_PRP, E.FIELD_G, E.FIELD_C, E.FIELD_H,
+                  E.FIELD_Z]
+        for paradigm, wait_ms in (("10s-recall", 10_000.0), ("8h-recall", 8 * 3600e3)):
+            t_swap = t_learn[1] + wait_ms
+            recall = _with_step(base, core[:75], 1.0, t_swap, t_swap + 100.0)
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            a = E.Model(learn, precision=E.PA_FP64, device=device, stream=stream)
+            torch.cuda.synchronize(device)
+            t1 = time.perf_counter()
+            t_full = t_learn[1] + min(wait_ms, 10_000.0)      # full dynamics after learning
+            a.advance(t_full)
+            a.sync()
+            t2 = time.perf_counter()
+            n_long = 0
+            if wait_ms > 10_000.0:
+                n_long = int(round((t_swap - t_full) / 3600e3 * n_long_per_hour))
+                a.fast_forward(t_swap - t_full, n_long)
+                a.sync()
+            t3 = time.perf_counter()
+            fl = fields + ([E.FIELD_PRP_CV] if name.endswith("diffusion") else [])
+            saved = {f: a.read_state(f) for f in fl}
+            a.close()
+            b = E.Model(recall, precision=E.PA_FP64, device=device, stream=stream)
+            b.fast_forward(t_swap, 1)                          # the clock; state overwritten
+            for f in fl:
+                if f != E.FIELD_PRP or not name.endswith("diffusion"):
+                    b.write_state(f, saved[f])
+            b.sync()
+            t4 = time.perf_counter()
+            b.advance(t_swap + 300.0)
+            g, _, _ = b.read_spikes()
+            b.sync()
+            t5 = time.perf_counter()
+            info = b.info()
+            full_steps = int(round(t_full / dt)) + int(round(300.0 / dt))
+            rows.append({"network": name, "paradigm": paradigm, "n_cells": base.n_cells,
+                         "n_cv": int(info.n_cv), "dt_ms": dt, "full_steps": full_steps,
+                         "long_steps": n_long, "setup_s": round(t1 - t0, 3),
+                         "learn_and_wait_s": round(t2 - t1, 3), "fast_forward_s": round(t3 - t2, 4),
+                         "state_swap_s": round(t4 - t3, 3), "recall_s": round(t5 - t4, 3),
+                         "total_s": round(t5 - t0, 3),
+                         "cu_per_s_full": info.n_cv * full_steps / ((t2 - t1) + (t5 - t4)),
+                         "recall_spikes": int(len(g))})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    out = {"benchmark": "recall_paradigms", "precision": "fp64", "rows": rows}
+    if cpu:
+        # the oracle on the host cores: the full-dynamics part of the 10s-recall
+        # of each network, timed over a bounded sample of steps
+        import oracle as O
+        cores = os.cpu_count() or 1
+        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+        ref = {}
+        for name, base in nets.items():
+            o = O.Oracle(_with_step(base, core, 1.0, *t_learn))
+            t0 = time.perf_counter()
+            k = 5000
+            o.run(k)
+            t = time.perf_counter() - t0
+            ref[name] = {"cu_per_s": base.n_cv * k / t, "steps_timed": k,
+                         "est_10s_recall_full_s": t / k * (int(round(10_500.0 / base.dt)))}
+        out["cpu_oracle"] = {"cores": int(os.environ["OMP_NUM_THREADS"]), "networks": ref}
+    return out
+
+
 def reference_arm(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -479,6 +588,9 @@ def main():
                           "paper_hardware": "AMD Threadripper PRO 5995WX (64 cores), "
                                             "+ NVIDIA T1000 8GB for the cpu_gpu column"}),
               flush=True)
+        return
+    if args.recall:
+        print(json.dumps(recall_bench(0, cpu=not args.no_cpu)), flush=True)
         return
     import torch
     ws, rank, local = dist_setup()

@@ -72,7 +72,8 @@ extern "C" {
  * sum_j gD_ij (P_j' - P_i'), gD = D_p / ((L_i/2)/(pi r_i^2) + (L_j/2)/(pi r_j^2))
  * for adjacent CVs, solved by the same tree elimination as the cable equation.
  * PA_FIELD_PRP then reads the soma CV's concentration.  Such cells always run
- * in the narrow bin; pa_fast_forward refuses the model (PA_ERR_STATE). */
+ * in the narrow bin.  pa_fast_forward takes the same two steps with the long
+ * step (its own backward-Euler matrix). */
 /* Plasticity noise (Eqs. plasticity_noise_1-2): with the optional trailing
  * sigma_pl > 0, each step adds sigma_pl sqrt(n dt / tau) N(0,1) to w (GB,
  * tau = tau_w) or h (STC, tau = tau_h), n = number of the thresholds theta_p,
@@ -319,7 +320,8 @@ int pa_write_state(pa_model* m, int32_t field, const double* values, int64_t n);
  * canonical order) from h before the step, then per synapse z (Eq.
  * late_phase_weight with the cell's p), h (Eq. early_phase_weight: 0.1 (h0 - h)
  * / tau_h), GB w (Eq. weight_graupner_brunel: its cubic term), then p (Eq.
- * prp_single_comp).  STDP traces decay through their closed form.  All state
+ * prp_single_comp; a diffusing PRP field: its reaction and diffusion steps with
+ * the long step, z with the PRP at the synapse's CV).  STDP traces decay through their closed form.  All state
  * stays on the device.  Not in open-loop replay. */
 int pa_fast_forward(pa_model* m, double duration_ms, int64_t n_long);
 

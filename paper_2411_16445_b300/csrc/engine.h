@@ -241,6 +241,11 @@ struct FastForward {
   double decay_g[kMaxStreams], decay_c[kMaxStreams];
   double rate_w[kMaxStreams], rate_h[kMaxStreams], rate_z[kMaxStreams];
   double rate_p;  // dt_long / tau_p of the STC stream
+  // a diffusing PRP field: the long step's matrix diagonal V/dt_long + sum gD
+  // and V/dt_long per CV (narrow element layout); tree rows present
+  const double* prp_dg_long;
+  const double* prp_vdt_long;
+  bool tree;
 };
 int launch_fast_forward(const EpochArgs& a, const FastForward& f, bool mixed, void* stream);
 

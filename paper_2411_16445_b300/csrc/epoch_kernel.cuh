@@ -31,6 +31,7 @@
 
 #include "engine.h"
 #include "int_arith.cuh"
+#include "prp_field.cuh"
 #include "rng.cuh"
 
 namespace pa {
@@ -286,74 +287,6 @@ __device__ __forceinline__ void run_sum(TM* gs, TM* es, int32_t rb, int lane, in
     gs[ce] = accg;
     es[ce] = acce;
   }
-}
-
-// One step of a diffusing PRP field (Eq. diffusion on the cell's tree; the
-// lane's cell, rows n-1..0 then 0..n-1, in global memory): every CV takes the
-// explicit reaction step P* = P + dt/tau_p (src - P) (synthesis qs V_tot / V_0
-// at the soma only), then one backward-Euler diffusion solve with the constant
-// matrix (diagonal V/dt + sum gD, coupling -gD), eliminated like the cable
-// equation: children into parents from the highest row down (other children
-// first, the row below last), one correctly rounded reciprocal per row.  The
-// Hines scratch f, x' is free here (the voltage solve of the step is done).
-// Explicitly rounded operations: the same arithmetic in both precisions.
-// Returns the soma CV's new concentration.
-template <bool TREE>
-__device__ __noinline__ double prp_field_step(const EpochArgs& A, int32_t rb, int lane, int64_t L,
-                                              int n, double qs) {
-  const double rp = A.sp[A.stc_stream].rate_p;
-  double* __restrict__ P = A.prp_cv;
-  double* __restrict__ F = A.f;
-  double* __restrict__ XP = A.xp;
-  double cf = 0.0, ca = 0.0, cx = 0.0, x0 = 0.0;
-  bool carry = false;
-  for (int i = n - 1; i >= 0; --i) {
-    const uint32_t e = elem_of(rb, i, lane);
-    const double pv = P[e];
-    const double src = (i == 0) ? __dmul_rn(qs, A.prp_src[L]) : 0.0;
-    const double ps = __dadd_rn(pv, __dmul_rn(rp, __dsub_rn(src, pv)));
-    double d = A.prp_dg[e];
-    double b = __dmul_rn(A.prp_vdt[e], ps);
-    if (TREE) {
-      for (int ch = A.och_head[e]; ch >= 0;) {
-        const uint32_t ec = elem_of(rb, ch, lane);
-        const double ac = A.prp_a[ec];
-        d = __fma_rn(-F[ec], ac, d);
-        b = __fma_rn(-ac, XP[ec], b);
-        ch = A.och_next[ec];
-      }
-    }
-    if (carry) {
-      d = __fma_rn(-cf, ca, d);
-      b = __fma_rn(-ca, cx, b);
-    }
-    if (i > 0) {
-      const double ai = A.prp_a[e];
-      const double rr = rcp_rn_pos(d);
-      const double fi = __dmul_rn(ai, rr);
-      const double xi = __dmul_rn(b, rr);
-      F[e] = fi;
-      XP[e] = xi;
-      carry = !TREE || A.par[e] == i - 1;
-      cf = fi; ca = ai; cx = xi;
-    } else {
-      x0 = __dmul_rn(b, rcp_rn_pos(d));
-    }
-  }
-  if (n > 0) P[elem_of(rb, 0, lane)] = x0;
-  double prev = x0;
-  for (int i = 1; i < n; ++i) {
-    const uint32_t e = elem_of(rb, i, lane);
-    double pp = prev;
-    if (TREE) {
-      const int pi = A.par[e];
-      if (pi != i - 1) pp = P[elem_of(rb, pi, lane)];
-    }
-    const double xi = __fma_rn(-F[e], pp, XP[e]);
-    P[e] = xi;
-    prev = xi;
-  }
-  return x0;
 }
 
 template <class TM, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks>
@@ -685,7 +618,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       failed = true;
       break;
     }
-    if (A.prp_diff && has_stc) prp = prp_field_step<TREE>(A, rb, lane, L, n, qs_field);
+    if (A.prp_diff && has_stc)
+      prp = prp_field_step<TREE>(A, rb, lane, L, n, qs_field, A.sp[A.stc_stream].rate_p, A.prp_dg,
+                                 A.prp_vdt);
     if (n > 0) {
       for (int32_t q = pq0; q < pq1; ++q) {
         const int64_t smp = probe0 + (k - k_begin);

@@ -5,13 +5,16 @@
 // variables take n_long forward-Euler steps of T / n_long with the calcium
 // terms (and so the noise) off, in the order of a full step: per cell, S from
 // h before the update, then per synapse z (with the cell's p) and h
-// (relaxation to h0), GB w (its cubic drift), then p.  Everything stays in
+// (relaxation to h0), GB w (its cubic drift), then p -- or, for a diffusing
+// PRP field, its explicit reaction and backward-Euler diffusion with the long
+// step's matrix (z then captures the PRP at its own CV).  Everything stays in
 // HBM: no state leaves the device.  Built without contraction like the FP64
 // kernels.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "engine.h"
+#include "prp_field.cuh"
 
 namespace pa {
 namespace {
@@ -31,6 +34,7 @@ __global__ void ff_decay_kernel(StreamDev D, double decay_g, double decay_c, boo
 }
 
 // One thread per lane (cell): the long steps of its GB and STC synapses.
+template <bool TREE>
 __global__ void ff_slow_kernel(const EpochArgs A, const FastForward F) {
   const int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (L >= A.n_lanes) return;
@@ -38,6 +42,8 @@ __global__ void ff_slow_kernel(const EpochArgs A, const FastForward F) {
   const int64_t g = L >> 5, l = L & 31;
   const bool wide = g >= A.n_narrow;
   const bool has_stc = A.stc_stream >= 0 && A.has_stc[L];
+  const bool field = has_stc && A.prp_diff;  // never in the wide bin
+  const int32_t rb = A.row_base[g];
   double p = has_stc ? A.prp[L] : 0.0;
   for (int64_t it = 0; it < F.n_long; ++it) {
     double S = 0.0;
@@ -58,8 +64,10 @@ __global__ void ff_slow_kernel(const EpochArgs A, const FastForward F) {
         } else {
           const double h = D.w[e], z = D.z[e], h0 = P.h0;
           S = S + fabs(h - h0);
-          const double T1 = ((h - h0) > P.theta_tag) ? (pk * P.f_int) * (1.0 - z) : 0.0;
-          const double T2 = ((h0 - h) > P.theta_tag) ? (pk * P.f_int) * (z + 0.5) : 0.0;
+          const double pz =
+              field ? A.prp_cv[((uint32_t)(rb + (D.cvf[e] >> 3)) << 5) | (uint32_t)l] : pk;
+          const double T1 = ((h - h0) > P.theta_tag) ? (pz * P.f_int) * (1.0 - z) : 0.0;
+          const double T2 = ((h0 - h) > P.theta_tag) ? (pz * P.f_int) * (z + 0.5) : 0.0;
           D.z[e] = z + F.rate_z[s] * (T1 - T2);
           D.w[e] = h + F.rate_h[s] * (0.1 * (h0 - h));
         }
@@ -68,7 +76,11 @@ __global__ void ff_slow_kernel(const EpochArgs A, const FastForward F) {
     if (has_stc) {
       const StreamParams& P = A.sp[A.stc_stream];
       const double qs = (S > P.theta_pro) ? P.p_max : 0.0;
-      p = pk + F.rate_p * (qs - pk);
+      if (field)
+        p = prp_field_step<TREE>(A, rb, (int)l, L, A.ncv[L], qs, F.rate_p, F.prp_dg_long,
+                                 F.prp_vdt_long);
+      else
+        p = pk + F.rate_p * (qs - pk);
     }
   }
   if (has_stc) A.prp[L] = p;
@@ -85,8 +97,11 @@ int launch_fast_forward(const EpochArgs& a, const FastForward& f, bool mixed, vo
     if (blocks > 148 * 16) blocks = 148 * 16;
     ff_decay_kernel<<<blocks, 256, 0, st>>>(a.sd[s], f.decay_g[s], f.decay_c[s], mixed);
   }
-  if (a.n_lanes > 0)
-    ff_slow_kernel<<<(int)((a.n_lanes + 127) / 128), 128, 0, st>>>(a, f);
+  if (a.n_lanes > 0) {
+    const int blocks = (int)((a.n_lanes + 127) / 128);
+    if (f.tree) ff_slow_kernel<true><<<blocks, 128, 0, st>>>(a, f);
+    else ff_slow_kernel<false><<<blocks, 128, 0, st>>>(a, f);
+  }
   return (int)cudaGetLastError();
 }
 

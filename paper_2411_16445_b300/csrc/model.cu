@@ -111,6 +111,10 @@ struct pa_model {
   std::vector<double> conn_h0;
   bool prp_diff = false;                  // the STC mechanism's PRP diffuses (D_p > 0)
   std::vector<uint8_t> cell_diff;         // per gid: the cell's PRP is a field over its CVs
+  std::vector<double> prp_vol, prp_gsum;  // per element: CV volume, summed gD (fast-forward)
+  std::vector<double> ff_dg, ff_vdt;      // the long step's matrix, staged for upload
+  double* d_ff_dg = nullptr;              // device copies of the long step's matrix
+  double* d_ff_vdt = nullptr;
   size_t elem_bytes_m = 8;
   int n_streams = 0;
   pa::StreamParams sp[pa::kMaxStreams];
@@ -516,6 +520,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     h_pa.assign(n_elem, 0.0);
     h_pvdt.assign(n_elem, 0.0);
     h_psrc.assign(n_lanes, 0.0);
+    M->prp_vol.assign(n_elem, 0.0);
+    M->prp_gsum.assign(n_elem, 0.0);
   }
   for (int64_t L = 0; L < n_lanes; ++L) {
     if (lane_gid[L] < 0) continue;
@@ -601,6 +607,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         const int64_t e = elem(L, i);
         h_pvdt[e] = vol[i] / dt;
         h_pdg[e] = (vol[i] / dt) + gdx[i];
+        M->prp_vol[e] = vol[i];
+        M->prp_gsum[e] = gdx[i];
         vt = vt + vol[i];
       }
       h_psrc[L] = vt / vol[0];  // synthesis at the soma: p_max V_tot / (V_0 tau_p)
@@ -903,10 +911,11 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_wbr_e = R(sizeof(int32_t) * std::max<size_t>(h_wbr_e.size(), 1));
   const size_t o_wlvl = R(sizeof(int32_t) * std::max<size_t>(h_wlvl.size(), 1));
   const size_t o_clock = R(sizeof(EpochClock));
-  size_t o_pcv = 0, o_pdg = 0, o_pa = 0, o_pvdt = 0, o_psrc = 0;
+  size_t o_pcv = 0, o_pdg = 0, o_pa = 0, o_pvdt = 0, o_psrc = 0, o_ffdg = 0, o_ffvdt = 0;
   if (M->prp_diff) {
     o_pcv = R(8 * n_elem); o_pdg = R(8 * n_elem); o_pa = R(8 * n_elem);
     o_pvdt = R(8 * n_elem); o_psrc = R(8 * n_lanes);
+    o_ffdg = R(8 * n_elem); o_ffvdt = R(8 * n_elem);
   }
 
   const size_t total = ar.used;
@@ -1008,6 +1017,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     A.prp_a = (const double*)P8(o_pa);
     A.prp_vdt = (const double*)P8(o_pvdt);
     A.prp_src = (const double*)P8(o_psrc);
+    M->d_ff_dg = (double*)P8(o_ffdg);
+    M->d_ff_vdt = (double*)P8(o_ffvdt);
   }
   A.n_lanes = n_lanes;
   A.n_streams = n_streams;
@@ -1674,8 +1685,6 @@ int pa_fast_forward(pa_model* M, double duration_ms, int64_t n_long) {
   using namespace pa;
   if (!M) return set_err(PA_ERR_ARG, "model is NULL");
   if (M->replay) return set_err(PA_ERR_STATE, "pa_fast_forward does not run in open-loop replay");
-  if (M->prp_diff)
-    return set_err(PA_ERR_STATE, "pa_fast_forward: a diffusing PRP field has no long-step scheme");
   const double ks = duration_ms / M->dt;
   const int64_t K = std::llround(ks);
   if (!std::isfinite(ks) || K < 0 || std::fabs(ks - (double)K) > 1e-6 * std::max(1.0, std::fabs(ks)))
@@ -1698,6 +1707,22 @@ int pa_fast_forward(pa_model* M, double duration_ms, int64_t n_long) {
       F.rate_z[s] = dtl / p[10];
       F.rate_p = dtl / p[11];
     }
+  }
+  F.tree = M->tree;
+  if (M->prp_diff) {
+    // the diffusing PRP field's matrix for the long step
+    const int64_t ne = M->total_rows * kLanes;
+    M->ff_dg.assign(ne, 1.0);
+    M->ff_vdt.assign(ne, 0.0);
+    for (int64_t e = 0; e < ne; ++e)
+      if (M->prp_vol[e] > 0.0) {
+        M->ff_vdt[e] = M->prp_vol[e] / dtl;
+        M->ff_dg[e] = (M->prp_vol[e] / dtl) + M->prp_gsum[e];
+      }
+    CUDA_TRY(cudaMemcpyAsync(M->d_ff_dg, M->ff_dg.data(), 8 * ne, cudaMemcpyHostToDevice, M->stream));
+    CUDA_TRY(cudaMemcpyAsync(M->d_ff_vdt, M->ff_vdt.data(), 8 * ne, cudaMemcpyHostToDevice, M->stream));
+    F.prp_dg_long = M->d_ff_dg;
+    F.prp_vdt_long = M->d_ff_vdt;
   }
   int rc = launch_fast_forward(M->ea, F, M->precision == PA_MIXED, M->stream);
   if (rc) return set_err(PA_ERR_CUDA, "fast forward: %s", cudaGetErrorString((cudaError_t)rc));

@@ -514,11 +514,11 @@ def test_prp_diffusion_mixed_open_loop():
     assert compare(po, pg) <= 1e-9 * max(1.0, po.max())
 
 
-def test_prp_diffusion_state_io_bins_and_refusals():
-    """The field written per CV or uniformly per cell, read back and continued
-    bit-identically to the oracle with the same writes; cells with a diffusing
-    PRP stay narrow under FLAG_WIDE_ALL (the others go wide); fast-forward is
-    refused."""
+def test_prp_diffusion_state_io_bins_and_fast_forward():
+    """The field written per CV or uniformly per cell, read back, fast-forwarded
+    (long reaction and diffusion steps) and continued bit-identically to the
+    oracle with the same writes; cells with a diffusing PRP stay narrow under
+    FLAG_WIDE_ALL (the others go wide)."""
     net = _diffusion_net()
     ncv = net.n_cv
     rng = np.random.default_rng(9)
@@ -530,6 +530,9 @@ def test_prp_diffusion_state_io_bins_and_refusals():
     o.run(300)
     o.set_cell_p(per_cell)
     o.run(300)
+    o.fast_forward(int(round(2000.0 / net.dt)), 8)
+    o.run(300)
+    k_end = 600 + int(round(2000.0 / net.dt)) + 300
     for flags in (0, E.FLAG_WIDE_ALL):
         m = E.Model(net, precision=E.PA_FP64, flags=flags)
         if flags:
@@ -542,8 +545,8 @@ def test_prp_diffusion_state_io_bins_and_refusals():
         m.advance(300 * net.dt)
         m.write_state(E.FIELD_PRP, per_cell)
         m.advance(600 * net.dt)
+        m.fast_forward(2000.0, 8)
+        m.advance(k_end * net.dt)
         m.sync()
         check_state(o, m, E.PA_FP64, exact=True)
         assert np.array_equal(o.prp(), m.read_state(E.FIELD_PRP_CV))
-        with pytest.raises(E.PaError):
-            m.fast_forward(1000.0, 10)
