@@ -36,11 +36,16 @@ namespace pa {
 //   1/d = (2/M) 2^(1022-ex) and 2/M = Q 2^-52.
 // The seed's error may reach about 2^-19 before Q0 can miss by more than 1;
 // rcp.approx.f32 errs by at most about 2^-23.
+// The IEEE division for the inputs outside rcp_rn_pos's domain, behind a call so
+// that the compiler cannot turn the rare branch into predicated FP64 work on
+// every row.
+static __device__ __noinline__ double rcp_ieee(double d) { return 1.0 / d; }
+
 __device__ __forceinline__ double rcp_rn_pos(double d) {
   const uint64_t x = (uint64_t)__double_as_longlong(d);
   const uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
   const uint32_t ex = hi >> 20;          // includes the sign bit: d < 0 -> ex >= 2048
-  if (ex - 1u >= 2044u) return 1.0 / d;  // zero, subnormal, huge, negative, inf, nan
+  if (ex - 1u >= 2044u) return rcp_ieee(d);  // zero, subnormal, huge, negative, inf, nan
   const uint64_t m = (x & 0x000fffffffffffffULL) | 0x0010000000000000ULL;
   const float mh = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
   float y0;
@@ -64,16 +69,22 @@ __device__ __forceinline__ double rcp_rn_pos(double d) {
 }
 
 // Exact widening of a float to double by moving its fields (sign; exponent
-// rebiased from 127 to 1023; fraction shifted from 23 to 52 bits).  The
-// hardware conversion issues on the FP64-rate pipe of this GPU.  Subnormal,
-// infinite and NaN inputs take the hardware conversion.
+// rebiased from 127 to 1023; fraction shifted from 23 to 52 bits), without a
+// branch: the hardware conversion issues on the FP64-rate pipe of this GPU,
+// and a rarely taken branch to it may be turned into a predicated conversion
+// on every call.  A subnormal is first scaled by 2^24 in FP32 (exact) and
+// rebiased 24 lower; infinities and NaNs keep exponent 2047 and their
+// fraction; zeros keep their sign.
 __device__ __forceinline__ double widen_f32(float v) {
   const uint32_t u = __float_as_uint(v);
-  const uint32_t a = u & 0x7fffffffu;
-  if (a - 0x00800000u >= 0x7f000000u && a != 0u) return (double)v;
-  const uint32_t hi = a ? (u & 0x80000000u) | ((a >> 3) + ((1023u - 127u) << 20)) : u;
-  const uint32_t lo = a << 29;
-  return __hiloint2double((int)hi, (int)lo);
+  const uint32_t s = u & 0x80000000u, a0 = u & 0x7fffffffu;
+  const bool sub = a0 < 0x00800000u;
+  const uint32_t as = __float_as_uint(__fmul_rn(__uint_as_float(a0), 16777216.0f));
+  const uint32_t a = sub ? as : a0;
+  uint32_t hi = (a >> 3) + ((sub ? (1023u - 127u - 24u) : (1023u - 127u)) << 20);
+  hi = a0 >= 0x7f800000u ? ((a0 >> 3) | 0x7ff00000u) : hi;
+  hi = a0 == 0u ? 0u : hi;
+  return __hiloint2double((int)(hi | s), (int)(a << 29));
 }
 __device__ __forceinline__ double widen_f32(double v) { return v; }
 
