@@ -38,6 +38,11 @@ HBM_PEAK_GBS = 6470.8          # measured copy bandwidth of this machine's B300 (ST
 N_SM = 148
 DFMA_PER_SM_CLK = 2            # FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal @ 2.03 GHz)
 RCP64_DFMA_EQ = 465.0 / 71.0   # measured: FP64 FMA 465 G/s vs FP64 reciprocal 71 G/s on B300
+# DRAM bytes per compartment-update of the current epoch kernel (mixed, shape 0),
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
+# 65,536-cell launch of the same generator (89.87 GB for 735.3 M CU); traffic
+# grows in proportion to the CUs of a launch, so the full launch is scaled.
+TRAFFIC_B_PER_CU = {"mixed": 122.2}
 
 
 def parse():
@@ -631,8 +636,13 @@ def main():
         peak_tflops = N_SM * DFMA_PER_SM_CLK * 2 * clk * 1e6 / 1e12
         ach_tflops = 2 * fpc * cu_launch / t_launch / 1e12
         ach_gbs = bpc * cu_launch / t_launch / 1e9
+        tb = TRAFFIC_B_PER_CU.get("mixed" if mixed else "fp64")
         return {"bound": "alu", "achieved": ach_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": ach_tflops / peak_tflops, "traffic": None,
+                "frac": ach_tflops / peak_tflops,
+                "traffic": tb * cu_launch if tb else None,
+                "traffic_note": ("DRAM bytes per launch, scaled from one ncu capture of a "
+                                 "65,536-cell launch (122.2 B/CU)") if tb else
+                                "not captured for this precision",
                 "kernel": "epoch_kernel", "fp64_ops_per_cu": fpc,
                 "peak_note": f"FP64: {N_SM} SMs x {DFMA_PER_SM_CLK} FMA/clk x 2 flop at the median "
                              f"SM clock under load ({clk:.0f} MHz); HH divisions count "
