@@ -14,6 +14,10 @@
 
 namespace pa {
 
+// Fork flags of a tree row (EpochArgs::tflag).
+constexpr uint8_t kForkPop = 1;   // exactly one non-first child: its values are popped here
+constexpr uint8_t kForkPush = 2;  // the one non-first child of its parent: pushed here
+
 constexpr int kLanes = 32;
 constexpr int kMaxStreams = 8;
 constexpr int kMaxProbeRowsPerLane = 1 << 15;
@@ -118,6 +122,11 @@ struct EpochArgs {
   const int16_t* par;        // tree: parent row (row 0: -1)
   const int16_t* och_head;   // tree: highest-index non-first child (-1: none)
   const int16_t* och_next;   // tree: next lower non-first sibling (-1: none)
+  // tree: per row, kForkPop if the row has exactly one non-first child, kForkPush
+  // if the row is the one non-first child of such a row; and the axial coupling
+  // of that one non-first child (rows with kForkPop)
+  const uint8_t* tflag;
+  const double* aoch;
   // soma / cell state (lane index)
   const uint8_t* is_hh;
   const double* hh_g;        // [3][n_lanes] gna, gk, gl [uS]

@@ -163,21 +163,29 @@ __device__ __forceinline__ void fence_async_shared() {
 template <class TM, bool TREE, int kRowsBack, int kRowsFwd>
 struct Stage {
   // bytes per row (32 lanes) of each staged array
-  static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(TM), kI = TREE ? 32 * 2 : 0;
+  static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(TM), kI = TREE ? 32 * 2 : 0,
+                       kA = TREE ? 32 * 8 : 0, kT = TREE ? 32 : 0;
   // backward pass: V, C/dt, axial coupling, the assembled diagonal and
   // right-hand-side terms (constant parts plus synaptic sums, FP64), tree rows
-  // (parent, first other child)
+  // (parent, first other child, the one other child's coupling, fork flags)
   static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oA = oCDT + kRowsBack * kD,
                        oGS = oA + kRowsBack * kD, oES = oGS + kRowsBack * kD,
-                       oPAR = oES + kRowsBack * kD, oOCH = oPAR + kRowsBack * kI,
-                       kBackBytes = oOCH + kRowsBack * kI;
-  static constexpr int kBackRow = 5 * kD + 2 * kI;
-  // forward pass: f, x', tree parent rows
+                       oAOCH = oES + kRowsBack * kD, oPAR = oAOCH + kRowsBack * kA,
+                       oOCH = oPAR + kRowsBack * kI, oTF = oOCH + kRowsBack * kI,
+                       kBackBytes = oTF + kRowsBack * kT;
+  static constexpr int kBackRow = 5 * kD + kA + 2 * kI + kT;
+  // forward pass: f, x', tree parent rows and fork flags
   static constexpr int fF = 0, fXP = fF + kRowsFwd * kD, fPAR = fXP + kRowsFwd * kD,
-                       kFwdBytes = fPAR + kRowsFwd * kI;
-  static constexpr int kFwdRow = 2 * kD + kI;
+                       fTF = fPAR + kRowsFwd * kI, kFwdBytes = fTF + kRowsFwd * kT;
+  static constexpr int kFwdRow = 2 * kD + kI + kT;
   static constexpr int kBytes = (kBackBytes > kFwdBytes ? kBackBytes : kFwdBytes);
-  static constexpr int kWarpBytes = kStages * kBytes + 64;  // + mbarriers
+  // fork stacks (trees): the backward pass keeps (f, x') of up to kStackB pending
+  // one-other-children per lane, the forward pass V of up to kStackF pending forks;
+  // deeper entries are read back from global memory
+  static constexpr int kStackB = 8, kStackF = 16;
+  static constexpr int kStackBytes = TREE ? 32 * kStackB * 16 : 0;
+  static_assert(32 * kStackF * 8 <= 32 * kStackB * 16, "forward stack fits the region");
+  static constexpr int kWarpBytes = kStages * kBytes + 64 + kStackBytes;  // + mbarriers
 };
 
 // One synapse's step (rows a1, a2, a4): this step's conductance event, the
@@ -298,6 +306,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
   if (g >= A.n_narrow) return;  // whole warps only
   char* wbuf = smem_raw + (threadIdx.x >> 5) * ST::kWarpBytes;
   uint64_t* bar = (uint64_t*)(wbuf + kStages * ST::kBytes);
+  // the fork stack region (trees): double2 entries (backward), double (forward)
+  double2* stack2 = (double2*)(wbuf + kStages * ST::kBytes + 64);
+  double* stack1 = (double*)stack2;
   if (lane == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
     mbar_init_fence();
@@ -466,8 +477,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kD, &bar[s]);
           if (TREE) {
+            bulk_load(st + ST::oAOCH, A.aoch + r0 * 32, cnt * ST::kA, &bar[s]);
             bulk_load(st + ST::oPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
             bulk_load(st + ST::oOCH, A.och_head + r0 * 32, cnt * ST::kI, &bar[s]);
+            bulk_load(st + ST::oTF, A.tflag + r0 * 32, cnt * ST::kT, &bar[s]);
           }
         }
       };
@@ -476,6 +489,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       for (int c = 0; c < kStages - 1 && c < nc; ++c) issue(c);
       double cf = 0.0, ca = 0.0, cx = 0.0;
       bool carry = false;
+      int depth = 0;  // fork-stack depth of this lane
       for (int c = 0; c < nc; ++c) {
         if (c + kStages - 1 < nc) {
           fence_async_shared();  // reads of the stage about to be refilled are done
@@ -527,14 +541,36 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
             d = gsv;
             b = fma(cdt, v, esv);
           }
+          uint8_t tf = 0;
           if (TREE) {
-            // other children, highest index first, from the scratch arrays
-            for (int ch = ((const int16_t*)(st + ST::oOCH))[r]; ch >= 0;) {
-              const uint32_t ec = elem_of(rb, ch, lane);
-              const double ac = AA[ec];
-              d = fma(-F[ec], ac, d);
-              b = fma(-ac, XP[ec], b);
-              ch = A.och_next[ec];
+            tf = ((const uint8_t*)(st + ST::oTF))[r];
+            const int och = ((const int16_t*)(st + ST::oOCH))[r];
+            if (tf & kForkPop) {
+              // the one other child: its f and x' from the top of the fork stack
+              // (eliminated earlier in this pass), its coupling staged here
+              --depth;
+              double fc, xc;
+              if (depth < ST::kStackB) {
+                const double2 t = stack2[depth * 32 + lane];
+                fc = t.x;
+                xc = t.y;
+              } else {
+                const uint32_t ec = elem_of(rb, och, lane);
+                fc = F[ec];
+                xc = XP[ec];
+              }
+              const double ac = ((const double*)(st + ST::oAOCH))[r];
+              d = fma(-fc, ac, d);
+              b = fma(-ac, xc, b);
+            } else {
+              // several other children, highest index first, from the scratch arrays
+              for (int ch = och; ch >= 0;) {
+                const uint32_t ec = elem_of(rb, ch, lane);
+                const double ac = AA[ec];
+                d = fma(-F[ec], ac, d);
+                b = fma(-ac, XP[ec], b);
+                ch = A.och_next[ec];
+              }
             }
           }
           if (carry) {
@@ -548,6 +584,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
             const double xi = b * rr;
             F[e] = fi;
             XP[e] = xi;
+            if (TREE && (tf & kForkPush)) {
+              if (depth < ST::kStackB) stack2[depth * 32 + lane] = make_double2(fi, xi);
+              ++depth;
+            }
             carry = !TREE || pi == i - 1;
             cf = fi; ca = ai; cx = xi;
           } else {
@@ -575,7 +615,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           mbar_expect_tx(&bar[s], cnt * ST::kFwdRow);
           bulk_load(st + ST::fF, F + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::fXP, XP + r0 * 32, cnt * ST::kD, &bar[s]);
-          if (TREE) bulk_load(st + ST::fPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
+          if (TREE) {
+            bulk_load(st + ST::fPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
+            bulk_load(st + ST::fTF, A.tflag + r0 * 32, cnt * ST::kT, &bar[s]);
+          }
         }
       };
       fence_async_shared();
@@ -583,6 +626,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       for (int c = 0; c < kStages - 1 && c < nc; ++c) issue(c);
       if (n > 0) Vg[elem_of(rb, 0, lane)] = v0_new;
       double vprev = v0_new;
+      int depth = 0;  // fork-stack depth of this lane
       for (int c = 0; c < nc; ++c) {
         if (c + kStages - 1 < nc) {
           fence_async_shared();
@@ -598,17 +642,33 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
         }
         const char* st = wbuf + s * ST::kBytes;
         const int lo = kRowsFwd * c, hi = lo + kRowsFwd < rows ? lo + kRowsFwd : rows;
+        if (TREE && c == 0 && n > 0 && (((const uint8_t*)(st + ST::fTF))[lane] & kForkPop)) {
+          stack1[lane] = v0_new;  // the root is a fork with one other child
+          depth = 1;
+        }
         for (int i = lo > 1 ? lo : 1; i < hi; ++i) {
           if (i >= n) break;
           const int r = (i - lo) * 32 + lane;
           double vp = vprev;
+          uint8_t tf = 0;
           if (TREE) {
+            tf = ((const uint8_t*)(st + ST::fTF))[r];
             const int pi = ((const int16_t*)(st + ST::fPAR))[r];
-            if (pi != i - 1) vp = Vg[elem_of(rb, pi, lane)];
+            if (tf & kForkPush) {
+              // the one other child of its parent: the parent's V from the stack
+              --depth;
+              vp = depth < ST::kStackF ? stack1[depth * 32 + lane] : Vg[elem_of(rb, pi, lane)];
+            } else if (pi != i - 1) {
+              vp = Vg[elem_of(rb, pi, lane)];
+            }
           }
           const double vi = fma(-((const double*)(st + ST::fF))[r], vp,
                                 ((const double*)(st + ST::fXP))[r]);
           Vg[elem_of(rb, i, lane)] = vi;
+          if (TREE && (tf & kForkPop)) {
+            if (depth < ST::kStackF) stack1[depth * 32 + lane] = vi;
+            ++depth;
+          }
           vprev = vi;
         }
       }

@@ -504,10 +504,14 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<double> h_cdt(n_elem, 0.0), h_dc(n_elem, 1.0), h_em(n_elem, 0.0),
       h_a(n_elem, 0.0), h_V(n_elem, 0.0);
   std::vector<int16_t> h_par, h_och, h_ocn;
+  std::vector<uint8_t> h_tf;
+  std::vector<double> h_aoch;
   if (M->tree) {
     h_par.assign(n_elem, -1);
     h_och.assign(n_elem, -1);
     h_ocn.assign(n_elem, -1);
+    h_tf.assign(n_elem, 0);
+    h_aoch.assign(n_elem, 0.0);
   }
   std::vector<uint8_t> h_is_hh(n_lanes, 0);
   std::vector<double> h_hhg(3 * n_lanes, 0.0), h_hhe(3 * n_lanes, 0.0);
@@ -581,6 +585,19 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         // children are visited in increasing i: push to the front -> descending list
         h_ocn[elem(L, i)] = h_och[elem(L, p)];
         h_och[elem(L, p)] = (int16_t)i;
+      }
+      // fork flags: a row with exactly one other child takes that child's values
+      // from the warp's fork stack (LIFO in both passes), the child pushes them
+      std::vector<int32_t> n_other(n, 0);
+      for (int i = 1; i < n; ++i)
+        if (i != g.parent[i] + 1) ++n_other[g.parent[i]];
+      for (int i = 0; i < n; ++i) {
+        const int64_t e = elem(L, i);
+        if (n_other[i] == 1) {
+          h_tf[e] |= kForkPop;
+          h_aoch[e] = h_a[elem(L, h_och[e])];
+        }
+        if (i > 0 && i != g.parent[i] + 1 && n_other[g.parent[i]] == 1) h_tf[e] |= kForkPush;
       }
     }
     if (M->cell_diff[lane_gid[L]]) {
@@ -874,11 +891,13 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_cdt = R(8 * n_elem),
                o_a = R(8 * n_elem), o_gs = R(8 * n_elem), o_es = R(8 * n_elem);
   const size_t o_f = R(8 * n_elem), o_xp = R(8 * n_elem);
-  size_t o_par = 0, o_och = 0, o_ocn = 0;
+  size_t o_par = 0, o_och = 0, o_ocn = 0, o_tf = 0, o_aoch = 0;
   if (M->tree) {
     o_par = R(2 * n_elem);
     o_och = R(2 * n_elem);
     o_ocn = R(2 * n_elem);
+    o_tf = R(n_elem);
+    o_aoch = R(8 * n_elem);
   }
   const size_t o_ishh = R(n_lanes), o_hhg = R(8 * 3 * n_lanes), o_hhe = R(8 * 3 * n_lanes),
                o_gate = R(8 * 3 * n_lanes), o_iinj = R(8 * n_lanes), o_kon = R(8 * n_lanes),
@@ -959,6 +978,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   putv(o_hhg, h_hhg); putv(o_hhe, h_hhe);
   if (M->tree) {
     putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn);
+    putv(o_tf, h_tf); putv(o_aoch, h_aoch);
   }
   putv(o_ishh, h_is_hh);
   putv(o_wcell, h_wcell); putv(o_wbr_s, h_wbr_s); putv(o_wbr_e, h_wbr_e); putv(o_wlvl, h_wlvl);
@@ -1013,6 +1033,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     A.par = (const int16_t*)P8(o_par);
     A.och_head = (const int16_t*)P8(o_och);
     A.och_next = (const int16_t*)P8(o_ocn);
+    A.tflag = (const uint8_t*)P8(o_tf);
+    A.aoch = (const double*)P8(o_aoch);
   }
   A.is_hh = (const uint8_t*)P8(o_ishh);
   A.hh_g = (const double*)P8(o_hhg); A.hh_e = (const double*)P8(o_hhe);
