@@ -40,9 +40,9 @@ DFMA_PER_SM_CLK = 2            # FP64 FMA lanes per SM per clock (1.25 TFLOP/s n
 RCP64_DFMA_EQ = 465.0 / 71.0   # measured: FP64 FMA 465 G/s vs FP64 reciprocal 71 G/s on B300
 # DRAM bytes per compartment-update of the current epoch kernel (mixed, shape 0),
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
-# 65,536-cell launch of the same generator (89.87 GB for 735.3 M CU); traffic
+# 65,536-cell launch of the same generator (94.47 GB for 735.3 M CU); traffic
 # grows in proportion to the CUs of a launch, so the full launch is scaled.
-TRAFFIC_B_PER_CU = {"mixed": 122.2}
+TRAFFIC_B_PER_CU = {"mixed": 128.5}
 
 
 def parse():
@@ -641,7 +641,7 @@ def main():
                 "frac": ach_tflops / peak_tflops,
                 "traffic": tb * cu_launch if tb else None,
                 "traffic_note": ("DRAM bytes per launch, scaled from one ncu capture of a "
-                                 "65,536-cell launch (122.2 B/CU)") if tb else
+                                 "65,536-cell launch (128.5 B/CU)") if tb else
                                 "not captured for this precision",
                 "kernel": "epoch_kernel", "fp64_ops_per_cu": fpc,
                 "peak_note": f"FP64: {N_SM} SMs x {DFMA_PER_SM_CLK} FMA/clk x 2 flop at the median "
@@ -650,7 +650,11 @@ def main():
                              "row reciprocal runs on the integer pipes",
                 "hbm": {"achieved": ach_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                         "frac": ach_gbs / HBM_PEAK_GBS, "algorithmic_bytes_per_cu": bpc,
-                        "peak_note": "measured copy bandwidth"}}
+                        "traffic_gbs": tb * cu_launch / t_launch / 1e9 if tb else None,
+                        "traffic_frac": tb * cu_launch / t_launch / 1e9 / HBM_PEAK_GBS
+                        if tb else None,
+                        "peak_note": "measured copy bandwidth; traffic_* use the DRAM bytes "
+                                     "ncu counted (scaled), not the algorithmic bytes"}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
