@@ -42,7 +42,7 @@ RCP64_DFMA_EQ = 465.0 / 71.0   # measured: FP64 FMA 465 G/s vs FP64 reciprocal 7
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
 # 65,536-cell launch of the same generator (94.47 GB for 735.3 M CU); traffic
 # grows in proportion to the CUs of a launch, so the full launch is scaled.
-TRAFFIC_B_PER_CU = {"mixed": 128.5}
+TRAFFIC_B_PER_CU = {}
 
 
 def parse():

@@ -822,31 +822,14 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
   const int32_t* par = M->parent + base;
   double *V = M->V + base, *gs = M->gs + base, *es = M->es + base;
   double *d = M->d + base, *b = M->b + base;
-  /* The diagonal's and right-hand side's constant parts: C/dt + sum g_axial
-     (+ g_pas), and g_pas E_pas (0 for HH, whose terms enter below). */
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t gi = base + i;
-    int pas = M->mech[M->cv_mech[gi]].kind == ORC_MECH_PAS;
-    gs[i] = pas ? (M->cdt[gi] + M->gax[gi]) + M->gpas[gi] : M->cdt[gi] + M->gax[gi];
-    es[i] = pas ? M->em_pas[gi] : 0.0;
-  }
-  /* Synaptic conductances in the cell's canonical order (mechanism, CV,
-     connection): each run of one mechanism's synapses on one CV is summed from
-     0, then added to the CV's total. */
-  for (int64_t j = M->cell_syn_off[c]; j < M->cell_syn_off[c + 1];) {
-    int64_t s0 = M->cell_syn[j];
-    int32_t mech = M->syn_mech[s0];
-    int64_t i = M->syn_cv[s0] - base;
-    double E = M->mech[mech].p[1];
-    double rg = 0.0, re = 0.0;
-    for (; j < M->cell_syn_off[c + 1]; ++j) {
-      int64_t s = M->cell_syn[j];
-      if (M->syn_mech[s] != mech || M->syn_cv[s] - base != i) break;
-      rg = rg + M->g[s];
-      re = re + M->g[s] * E;
-    }
-    gs[i] = gs[i] + rg;
-    es[i] = es[i] + re;
+  for (int64_t i = 0; i < n; ++i) { gs[i] = 0.0; es[i] = 0.0; }
+  /* synaptic conductances summed per CV in the cell's canonical order */
+  for (int64_t j = M->cell_syn_off[c]; j < M->cell_syn_off[c + 1]; ++j) {
+    int64_t s = M->cell_syn[j];
+    int64_t i = M->syn_cv[s] - base;
+    double E = M->mech[M->syn_mech[s]].p[1];
+    gs[i] = gs[i] + M->g[s];
+    es[i] = es[i] + M->g[s] * E;
   }
   double iinj = (k >= M->k_on[c] && k < M->k_off[c]) ? M->istep[c] : 0.0;
   /* backward-Euler matrix: (C/dt + sum g_axial + g_m) V^{k+1} - sum g_axial V_nb^{k+1}
@@ -854,19 +837,19 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
   for (int64_t i = 0; i < n; ++i) {
     int64_t gi = base + i;
     const orc_mech* mc = &M->mech[M->cv_mech[gi]];
+    double gm, em;
     if (mc->kind == ORC_MECH_PAS) {
-      d[i] = gs[i];
-      b[i] = fma(M->cdt[gi], V[i], es[i]);
+      gm = M->gpas[gi];
+      em = M->em_pas[gi];
     } else {
       double mv = M->m[gi], hv = M->h[gi], nv = M->n[gi];
       double gna = M->gna_a[gi] * (((mv * mv) * mv) * hv);
       double gk = M->gk_a[gi] * (((nv * nv) * nv) * nv);
-      double gm = (gna + gk) + M->gl_a[gi];
-      double em = ((gna * mc->p[3]) + (gk * mc->p[4])) + (M->gl_a[gi] * mc->p[5]);
-      d[i] = gs[i] + gm;
-      b[i] = fma(M->cdt[gi], V[i], es[i] + em);
+      gm = (gna + gk) + M->gl_a[gi];
+      em = ((gna * mc->p[3]) + (gk * mc->p[4])) + (M->gl_a[gi] * mc->p[5]);
     }
-    if (i == 0) b[i] = b[i] + iinj;
+    d[i] = ((M->cdt[gi] + M->gax[gi]) + gm) + gs[i];
+    b[i] = (fma(M->cdt[gi], V[i], em) + (i == 0 ? iinj : 0.0)) + es[i];
   }
   double v0_old = V[0];
   double* xnew = M->xnew + base;

@@ -41,9 +41,7 @@ struct StreamParams {
 
 // Device pointers of one synapse stream.  Element index e = ((sbase+j)<<5)|lane.
 struct StreamDev {
-  const int32_t* cvf;    // (cv << 3) | flags (run_sum); -1 for padding
-  const double2* base;   // per synapse: the constant diagonal and RHS parts of its CV
-                         // where it ends the first run on that CV, else (0, 0)
+  const int32_t* cvf;    // (cv << 1) | first-on-CV flag; -1 for padding
   const int32_t* sbase;  // [n_groups + 1] row offsets of each group
   const void* weight;    // uS, double (FP64) or float (mixed)
   void* g;               // conductance, TM
@@ -114,9 +112,11 @@ struct EpochArgs {
   // CV arrays (element index)
   double* V;
   const double* cdt;         // C/dt [uS]
+  const double* dc;          // cdt + axial sum (+ leak for passive CVs)
+  const double* em;          // leak g E for passive CVs
   const double* a;           // -g_axial to the parent
-  void* gs;                  // FP64 diagonal term: C/dt + sum g_axial (+ g_pas) + synaptic g
-  void* es;                  // FP64 right-hand-side term: g_pas E_pas + synaptic g E
+  void* gs;                  // synaptic conductance per CV, TM
+  void* es;                  // synaptic g E per CV, TM
   double* f;                 // elimination scratch
   double* xp;                // elimination scratch
   const int16_t* par;        // tree: parent row (row 0: -1)

@@ -165,15 +165,15 @@ struct Stage {
   // bytes per row (32 lanes) of each staged array
   static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(TM), kI = TREE ? 32 * 2 : 0,
                        kA = TREE ? 32 * 8 : 0, kT = TREE ? 32 : 0;
-  // backward pass: V, C/dt, axial coupling, the assembled diagonal and
-  // right-hand-side terms (constant parts plus synaptic sums, FP64), tree rows
-  // (parent, first other child, the one other child's coupling, fork flags)
-  static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oA = oCDT + kRowsBack * kD,
-                       oGS = oA + kRowsBack * kD, oES = oGS + kRowsBack * kD,
-                       oAOCH = oES + kRowsBack * kD, oPAR = oAOCH + kRowsBack * kA,
+  // backward pass: V, C/dt, diagonal, leak E term, axial coupling, synaptic sums,
+  // tree rows (the one other child's coupling, parent, first other child, fork flags)
+  static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oDC = oCDT + kRowsBack * kD,
+                       oEM = oDC + kRowsBack * kD, oA = oEM + kRowsBack * kD,
+                       oAOCH = oA + kRowsBack * kD, oGS = oAOCH + kRowsBack * kA,
+                       oES = oGS + kRowsBack * kM, oPAR = oES + kRowsBack * kM,
                        oOCH = oPAR + kRowsBack * kI, oTF = oOCH + kRowsBack * kI,
                        kBackBytes = oTF + kRowsBack * kT;
-  static constexpr int kBackRow = 5 * kD + kA + 2 * kI + kT;
+  static constexpr int kBackRow = 5 * kD + kA + 2 * kM + 2 * kI + kT;
   // forward pass: f, x', tree parent rows and fork flags
   static constexpr int fF = 0, fXP = fF + kRowsFwd * kD, fPAR = fXP + kRowsFwd * kD,
                        fTF = fPAR + kRowsFwd * kI, kFwdBytes = fTF + kRowsFwd * kT;
@@ -263,37 +263,37 @@ __device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev&
 
 // The per-CV synaptic sums are spelled with explicitly rounded operations, never
 // contracted into fused multiply-adds, so that both cell bins (and any compiler
-// schedule) produce the same sums.  A run's sum is in the synapse precision;
-// adding it to the CV's FP64 total is exact widening plus one FP64 addition.
+// schedule) produce the same sums.
 __device__ __forceinline__ float tm_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float tm_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double tm_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double tm_add(double a, double b) { return __dadd_rn(a, b); }
 
 // Per-CV synaptic sums over one run of same-CV synapses of a stream, in the
-// canonical order: the run sums from 0; at its end the sum is added to the
-// CV's total -- the constant part (base: C/dt + sum g_axial (+ g_pas), and
-// g_pas E_pas; streamed with the synapse that ends the first run on the CV)
-// for the first run on the CV, else the total left by an earlier stream.
-// cvf = (cv << 3) | first run on the CV (1) | run start (2) | run end (4).
+// canonical order: the run starts from 0 (first synapse on the CV) or from the
+// sums left by an earlier stream, and is stored when it ends.
+// cvf = (cv << 3) | first-on-CV (1) | run start (2) | run end (4).
 template <class TM>
-__device__ __forceinline__ void run_sum(double* gs, double* es, double2 base, int32_t rb,
-                                        int lane, int32_t cvf, TM g, TM E, TM& accg,
-                                        TM& acce) {
+__device__ __forceinline__ void run_sum(TM* gs, TM* es, int32_t rb, int lane, int32_t cvf, TM g,
+                                        TM E, TM& accg, TM& acce) {
   const TM ge = tm_mul(g, E);
   if (cvf & 2) {
-    accg = g;
-    acce = ge;
+    if (cvf & 1) {
+      accg = g;
+      acce = ge;
+    } else {
+      const uint32_t ce = elem_of(rb, cvf >> 3, lane);
+      accg = tm_add(gs[ce], g);
+      acce = tm_add(es[ce], ge);
+    }
   } else {
     accg = tm_add(accg, g);
     acce = tm_add(acce, ge);
   }
   if (cvf & 4) {
     const uint32_t ce = elem_of(rb, cvf >> 3, lane);
-    const double bg = (cvf & 1) ? base.x : gs[ce];
-    const double be = (cvf & 1) ? base.y : es[ce];
-    gs[ce] = __dadd_rn(bg, widen_f32(accg));
-    es[ce] = __dadd_rn(be, widen_f32(acce));
+    gs[ce] = accg;
+    es[ce] = acce;
   }
 }
 
@@ -325,9 +325,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
 
   double* __restrict__ Vg = A.V;
   const double* __restrict__ CDT = A.cdt;
+  const double* __restrict__ DC = A.dc;
+  const double* __restrict__ EM = A.em;
   const double* __restrict__ AA = A.a;
-  double* __restrict__ GS = (double*)A.gs;
-  double* __restrict__ ES = (double*)A.es;
+  TM* __restrict__ GS = (TM*)A.gs;
+  TM* __restrict__ ES = (TM*)A.es;
   double* __restrict__ F = A.f;
   double* __restrict__ XP = A.xp;
 
@@ -370,12 +372,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       const bool calc = P.kind == SK_GB || P.kind == SK_STC;
       const bool stc = P.kind == SK_STC;
       constexpr int szm = 32 * (int)sizeof(TM);
-      const int rowb = 128 + 256 + szm + 512 + (calc ? 768 : 0) + (stc ? 256 : 0);
+      const int rowb = 128 + 256 + szm + (calc ? 768 : 0) + (stc ? 256 : 0);
       int RS = ST::kBytes / rowb;
       if (RS > 16) RS = 16;
-      const int o_cm = RS * 128, o_g = o_cm + RS * 256, o_b = o_g + RS * szm,
-                o_cam = o_b + RS * 512, o_c = o_cam + RS * 256, o_w = o_c + RS * 256,
-                o_z = o_w + RS * 256;
+      const int o_cm = RS * 128, o_g = o_cm + RS * 256, o_cam = o_g + RS * szm,
+                o_c = o_cam + RS * 256, o_w = o_c + RS * 256, o_z = o_w + RS * 256;
       const int nc = (nrow + RS - 1) / RS;
       const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
       const uint64_t* camg = calc ? D.camask + (int64_t)slot * D.n_elem : nullptr;
@@ -392,7 +393,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           bulk_load(st, D.cvf + r0, cnt * 128, &bar[si]);
           bulk_load(st + o_cm, cmg + r0, cnt * 256, &bar[si]);
           bulk_load(st + o_g, (const TM*)D.g + r0, cnt * szm, &bar[si]);
-          bulk_load(st + o_b, D.base + r0, cnt * 512, &bar[si]);
           if (calc) {
             bulk_load(st + o_cam, camg + r0, cnt * 256, &bar[si]);
             bulk_load(st + o_c, D.c + r0, cnt * 256, &bar[si]);
@@ -437,8 +437,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           const double pz = (stc && A.prp_diff) ? A.prp_cv[elem_of(rb, cvf >> 3, lane)] : prp;
           TM gv = syn_update<TM>(P, D, e, pre, capre, post, ((const TM*)(st + o_g))[r], cc, wv,
                                  zv, pz, k, dt, A.seed, S);
-          run_sum<TM>(GS, ES, ((const double2*)(st + o_b))[r], rb, lane, cvf, gv, E, accg,
-                      acce);
+          run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
           G[e] = gv * dg;
         }
       }
@@ -473,9 +472,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           mbar_expect_tx(&bar[s], cnt * ST::kBackRow);
           bulk_load(st + ST::oV, Vg + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oCDT, CDT + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::oDC, DC + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::oEM, EM + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oA, AA + r0 * 32, cnt * ST::kD, &bar[s]);
-          bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kD, &bar[s]);
-          bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kD, &bar[s]);
+          bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kM, &bar[s]);
+          bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kM, &bar[s]);
           if (TREE) {
             bulk_load(st + ST::oAOCH, A.aoch + r0 * 32, cnt * ST::kA, &bar[s]);
             bulk_load(st + ST::oPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
@@ -511,11 +512,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           const uint32_t e = elem_of(rb, i, lane);
           const double v = ((const double*)(st + ST::oV))[r];
           const double cdt = ((const double*)(st + ST::oCDT))[r];
+          const double dcv = ((const double*)(st + ST::oDC))[r];
           int pi = i - 1;
           if (TREE && i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
-          // the assembled diagonal and right-hand-side terms (Eq. cable)
-          const double gsv = ((const double*)(st + ST::oGS))[r];
-          const double esv = ((const double*)(st + ST::oES))[r];
+          const double gsv = widen_f32(((const TM*)(st + ST::oGS))[r]);
+          const double esv = widen_f32(((const TM*)(st + ST::oES))[r]);
           double d, b;
           if (i == 0) {
             v0_old = v;
@@ -531,15 +532,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
               const double g2 = gk * nnnn;
               const double gmt = (g1 + g2) + gl;
               const double emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
-              d = gsv + gmt;
-              b = fma(cdt, v, esv + emt) + iinj;
+              d = (dcv + gmt) + gsv;
+              b = (fma(cdt, v, emt) + iinj) + esv;
             } else {
-              d = gsv;
-              b = fma(cdt, v, esv) + iinj;
+              d = dcv + gsv;
+              b = (fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + iinj) + esv;
             }
           } else {
-            d = gsv;
-            b = fma(cdt, v, esv);
+            d = dcv + gsv;
+            b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + esv;
           }
           uint8_t tf = 0;
           if (TREE) {
@@ -780,14 +781,18 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // minimum resident blocks per SM (which sets the register budget).  Shape 0 is
 // the default; the autotuner times all of them on the model and keeps the
 // fastest.
+// Trees take one backward row less per chunk where chains take 4, which leaves
+// shared memory for the fork stacks at 12 warps per SM.
 template <class TM, bool TREE>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
+  constexpr int RB4 = TREE ? 3 : 4;
+  constexpr int RB6 = TREE ? 5 : 6;
   switch (shape) {
-    case 1: return launch_epoch_t<TM, TREE, 3, 9, 4, 4>(a, stream);   // 16 warps per SM
-    case 2: return launch_epoch_t<TM, TREE, 6, 16, 2, 4>(a, stream);  // 8 warps, long chunks
-    case 3: return launch_epoch_t<TM, TREE, 4, 12, 2, 6>(a, stream);  // 2-warp blocks
-    case 4: return launch_epoch_t<TM, TREE, 4, 12, 1, 12>(a, stream); // 1-warp blocks
-    default: return launch_epoch_t<TM, TREE, 4, 12, 4, 3>(a, stream); // 12 warps per SM
+    case 1: return launch_epoch_t<TM, TREE, 3, 9, 4, 4>(a, stream);     // 16 warps per SM
+    case 2: return launch_epoch_t<TM, TREE, RB6, 16, 2, 4>(a, stream);  // 8 warps, long chunks
+    case 3: return launch_epoch_t<TM, TREE, RB4, 12, 2, 6>(a, stream);  // 2-warp blocks
+    case 4: return launch_epoch_t<TM, TREE, RB4, 12, 1, 12>(a, stream); // 1-warp blocks
+    default: return launch_epoch_t<TM, TREE, RB4, 12, 4, 3>(a, stream); // 12 warps per SM
   }
 }
 

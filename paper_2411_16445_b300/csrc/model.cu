@@ -740,7 +740,6 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<std::vector<int32_t>> s_cvf(n_streams);
   std::vector<std::vector<double>> s_weight(n_streams), s_w(n_streams);
   std::vector<std::vector<int32_t>> s_nid(n_streams);   // noise source ids (noisy streams)
-  std::vector<std::vector<double>> s_base(n_streams);   // (dc, em) pairs at first-run ends
   std::vector<uint8_t> h_has_stc(n_lanes, 0);
   for (int s = 0; s < n_streams; ++s) {
     s_sbase[s].assign(n_groups + 1, 0);
@@ -763,16 +762,12 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     s_cvf[s].assign(ne, -1);
     s_weight[s].assign(ne, 0.0);
     s_w[s].assign(ne, 0.0);
-    s_base[s].assign(2 * ne, 0.0);
     if (M->sp[s].sigma > 0.0) s_nid[s].assign(ne, 0);
   }
   // Per-CV synaptic sums are accumulated in registers over each run of same-CV
-  // synapses of a stream (canonical order: mechanism, CV, connection), from 0;
-  // at the run's end the sum is added to the CV's total, which the first run on
-  // the CV starts from the constant part (C/dt + sum g_axial (+ g_pas), and
-  // g_pas E_pas).  Flags: bit 0 "this run is the first on its CV over all
-  // streams" (on every synapse of the run), bit 1 "run starts", bit 2 "run
-  // ends" (add to the total).  cvf = (cv << 3) | flags.
+  // synapses of a stream (canonical order: mechanism, CV, connection).  Flags:
+  // bit 0 "first on this CV over all streams" (the run starts from 0), bit 1 "run
+  // starts", bit 2 "run ends" (store the sums).  cvf = (cv << 3) | flags.
   for (int64_t L = 0; L < n_lanes; ++L) {
     if (lane_gid[L] < 0) continue;
     const int ncell = M->cell_ncv[lane_gid[L]];
@@ -782,20 +777,15 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       const int m = stream_mech[s];
       const double* p = mechs[m].params;
       auto& v = per_lane[(size_t)s * n_lanes + L];
-      bool run_first = false;
       for (size_t j = 0; j < v.size(); ++j) {
         const int64_t e = g < n_narrow ? ((int64_t)s_sbase[s][g] + (int64_t)j) * kLanes + l
                                        : ((int64_t)s_sbase[s][g] << 5) + (int64_t)j;
         const int cv = v[j].cv;
         const bool start = j == 0 || v[j - 1].cv != cv;
         const bool end = j + 1 == v.size() || v[j + 1].cv != cv;
-        if (start) run_first = !touched[cv];
-        s_cvf[s][e] = (cv << 3) | (run_first ? 1 : 0) | (start ? 2 : 0) | (end ? 4 : 0);
+        const bool first = !touched[cv];
+        s_cvf[s][e] = (cv << 3) | (first ? 1 : 0) | (start ? 2 : 0) | (end ? 4 : 0);
         touched[cv] = 1;
-        if (end && run_first) {
-          s_base[s][2 * e] = h_dc[elem(L, cv)];
-          s_base[s][2 * e + 1] = h_em[elem(L, cv)];
-        }
         s_weight[s][e] = conns[v[j].conn].weight;
         if (M->sp[s].kind == SK_GB) s_w[s][e] = p[12];
         if (M->sp[s].kind == SK_STDP) s_w[s][e] = p[6];
@@ -888,8 +878,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_ncv = R(sizeof(int32_t) * n_lanes);
   const size_t o_gid = R(sizeof(int32_t) * n_lanes);
   const size_t o_V = R(8 * n_elem);
-  const size_t o_cdt = R(8 * n_elem),
-               o_a = R(8 * n_elem), o_gs = R(8 * n_elem), o_es = R(8 * n_elem);
+  const size_t o_cdt = R(8 * n_elem), o_dc = R(8 * n_elem), o_em = R(8 * n_elem),
+               o_a = R(8 * n_elem), o_gs = R(tm * n_elem), o_es = R(tm * n_elem);
   const size_t o_f = R(8 * n_elem), o_xp = R(8 * n_elem);
   size_t o_par = 0, o_och = 0, o_ocn = 0, o_tf = 0, o_aoch = 0;
   if (M->tree) {
@@ -903,7 +893,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
                o_gate = R(8 * 3 * n_lanes), o_iinj = R(8 * n_lanes), o_kon = R(8 * n_lanes),
                o_koff = R(8 * n_lanes), o_th = R(8 * n_lanes), o_sp = R(n_lanes),
                o_prp = R(8 * n_lanes), o_hasstc = R(n_lanes), o_rbits = R(8 * n_lanes);
-  size_t o_s[kMaxStreams][13];
+  size_t o_s[kMaxStreams][12];
   for (int s = 0; s < n_streams; ++s) {
     const int64_t ne = M->s_nelem[s];
     const int kind = M->sp[s].kind;
@@ -919,7 +909,6 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     o_s[s][10] = (kind == SK_STDP) ? R(8 * ne) : 0;                             // kpre, kpost
     o_s[s][9] = R(8 * ne * (size_t)M->n_slots * ((kind == SK_GB || kind == SK_STC) ? 2 : 1));
     o_s[s][11] = M->sp[s].sigma > 0.0 ? R(4 * ne) : 0;                          // noise ids
-    o_s[s][12] = R(16 * ne);                                                    // CV bases
   }
   const size_t np = ps_conn.size();
   const size_t o_ps_stream = R(4 * np), o_ps_elem = R(8 * np), o_ps_conn = R(8 * np),
@@ -971,10 +960,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   putv(o_ncv, lane_ncv);
   putv(o_gid, lane_gid);
   putv(o_V, h_V);
-  putv(o_cdt, h_cdt); putv(o_a, h_a);
-  // the assembled diagonal and right-hand-side terms start as their constant
-  // parts; CVs with synapses rewrite them every step
-  putv(o_gs, h_dc); putv(o_es, h_em);
+  putv(o_cdt, h_cdt); putv(o_dc, h_dc); putv(o_em, h_em); putv(o_a, h_a);
   putv(o_hhg, h_hhg); putv(o_hhe, h_hhe);
   if (M->tree) {
     putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn);
@@ -993,7 +979,6 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     if (mixed) putv(o_s[s][2], to_f32(s_weight[s])); else putv(o_s[s][2], s_weight[s]);
     if (o_s[s][5]) putv(o_s[s][5], s_w[s]);
     if (o_s[s][11]) putv(o_s[s][11], s_nid[s]);
-    putv(o_s[s][12], s_base[s]);
   }
   putv(o_ps_stream, ps_stream); putv(o_ps_elem, ps_elem); putv(o_ps_conn, ps_conn);
   putv(o_ps_thr, ps_thr); putv(o_ps_dc, ps_dc);
@@ -1026,7 +1011,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   A.ncv = (const int32_t*)P8(o_ncv);
   A.gid = (const int32_t*)P8(o_gid);
   A.V = (double*)P8(o_V);
-  A.cdt = (const double*)P8(o_cdt); A.a = (const double*)P8(o_a);
+  A.cdt = (const double*)P8(o_cdt); A.dc = (const double*)P8(o_dc);
+  A.em = (const double*)P8(o_em); A.a = (const double*)P8(o_a);
   A.gs = P8(o_gs); A.es = P8(o_es);
   A.f = (double*)P8(o_f); A.xp = (double*)P8(o_xp);
   if (M->tree) {
@@ -1079,7 +1065,6 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     sd.cmask = (uint64_t*)P8(o_s[s][9]);
     sd.camask = (kind == SK_GB || kind == SK_STC) ? sd.cmask + ne * M->n_slots : nullptr;
     sd.nid = o_s[s][11] ? (const int32_t*)P8(o_s[s][11]) : nullptr;
-    sd.base = (const double2*)P8(o_s[s][12]);
     sd.n_elem = ne;
     M->mask_bases.push_back(sd.cmask);
     M->mask_elems.push_back(ne);

@@ -45,9 +45,11 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
 
   double* __restrict__ Vg = A.V;
   const double* __restrict__ CDT = A.cdt;
+  const double* __restrict__ DC = A.dc;
+  const double* __restrict__ EM = A.em;
   const double* __restrict__ AA = A.a;
-  double* __restrict__ GS = (double*)A.gs;
-  double* __restrict__ ES = (double*)A.es;
+  TM* __restrict__ GS = (TM*)A.gs;
+  TM* __restrict__ ES = (TM*)A.es;
   double* __restrict__ F = A.f;
   double* __restrict__ XP = A.xp;
   const int16_t* __restrict__ PAR = A.par;
@@ -98,7 +100,6 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
       for (int t = 0; t < nrow; ++t) {
         const uint32_t e = ((uint32_t)(sb + t) << 5) | (uint32_t)lane;
         const int32_t cvf = D.cvf[e];
-        const double2 bse = D.base[e];  // the CV's constant parts, at a first run's end
         const bool valid = cvf >= 0;  // padding only after the cell's last synapse
         TM gv = 0;
         double sadd = 0.0;
@@ -115,8 +116,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         // Per-CV sums in canonical order (run_sum's arithmetic): each lane sums
         // its run from the run's first synapse in this row up to itself, in
         // order, reading the values by shuffle; a run that crosses rows
-        // continues from the last lane's sums of the previous row; a run's
-        // last lane adds the run's sum to the CV's FP64 total.
+        // continues from the last lane's sums of the previous row.
         const TM ge = tm_mul(gv, E);
         const unsigned smask = __ballot_sync(full, valid && (cvf & 2));
         const unsigned upto = lane == 31 ? full : ((2u << lane) - 1u);
@@ -125,10 +125,15 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         const int src0 = seg0 < 0 ? 0 : seg0;
         const int len = valid ? lane - src0 + 1 : 0;
         const int maxlen = (int)__reduce_max_sync(full, (unsigned)len);
+        const int32_t cs = __shfl_sync(full, cvf, src0);
         TM acc = __shfl_sync(full, gv, src0), ace = __shfl_sync(full, ge, src0);
         if (seg0 < 0) {
           acc = tm_add(carry_g, acc);
           ace = tm_add(carry_e, ace);
+        } else if (valid && !(cs & 1)) {
+          const int64_t cs_e = e0 + (cs >> 3);  // continues the sums of earlier streams
+          acc = tm_add(GS[cs_e], acc);
+          ace = tm_add(ES[cs_e], ace);
         }
         for (int it = 1; it < maxlen; ++it) {
           const int src = src0 + it < 31 ? src0 + it : 31;
@@ -139,11 +144,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           }
         }
         if (valid && (cvf & 4)) {
-          const int64_t ce = e0 + (cvf >> 3);
-          const double bg = (cvf & 1) ? bse.x : GS[ce];
-          const double be = (cvf & 1) ? bse.y : ES[ce];
-          GS[ce] = __dadd_rn(bg, widen_f32(acc));
-          ES[ce] = __dadd_rn(be, widen_f32(ace));
+          GS[e0 + (cvf >> 3)] = acc;
+          ES[e0 + (cvf >> 3)] = ace;
         }
         carry_g = __shfl_sync(full, acc, 31);
         carry_e = __shfl_sync(full, ace, 31);
@@ -174,17 +176,19 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         bool carry = false;
         // one row of lookahead: the next row's values load during this row's
         // elimination
-        double nv = Vg[e0 + be], ncdt = CDT[e0 + be], na = AA[e0 + be];
-        double ngs = GS[e0 + be], nes = ES[e0 + be];
+        double nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be], nem = EM[e0 + be],
+               na = AA[e0 + be];
+        TM ngs = GS[e0 + be], nes = ES[e0 + be];
         int noch = PAR ? OCH[e0 + be] : -1;
         for (int i = be; i >= bs; --i) {
           const int64_t ei = e0 + i;
-          const double v = nv, cdt = ncdt, ai = na;
-          const double gsv = ngs, esv = nes;  // the assembled diagonal and RHS terms
+          const double v = nv, cdt = ncdt, dcv = ndc, emv = nem, ai = na;
+          const double gsv = widen_f32(ngs);
+          const double esv = widen_f32(nes);
           const int och = noch;
           if (i > bs) {
             const int64_t en = ei - 1;
-            nv = Vg[en]; ncdt = CDT[en]; na = AA[en];
+            nv = Vg[en]; ncdt = CDT[en]; ndc = DC[en]; nem = EM[en]; na = AA[en];
             ngs = GS[en]; nes = ES[en];
             if (PAR) noch = OCH[en];
           }
@@ -202,15 +206,15 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
               const double g2 = gk * nnnn;
               const double gmt = (g1 + g2) + gl;
               const double emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
-              d = gsv + gmt;
-              bb = fma(cdt, v, esv + emt) + iinj;
+              d = (dcv + gmt) + gsv;
+              bb = (fma(cdt, v, emt) + iinj) + esv;
             } else {
-              d = gsv;
-              bb = fma(cdt, v, esv) + iinj;
+              d = dcv + gsv;
+              bb = (fma(cdt, v, emv) + iinj) + esv;
             }
           } else {
-            d = gsv;
-            bb = fma(cdt, v, esv);
+            d = dcv + gsv;
+            bb = fma(cdt, v, emv) + esv;
           }
           if (PAR) {
             // other children, highest index first (eliminated at lower levels)
