@@ -182,7 +182,10 @@ struct Stage {
   // fork stacks (trees): the backward pass keeps (f, x') of up to kStackB pending
   // one-other-children per lane, the forward pass V of up to kStackF pending forks;
   // deeper entries are read back from global memory
-  static constexpr int kStackB = 8, kStackF = 16;
+  // (6 entries where the mixed kernel stages 4 backward rows, so that 12 warps
+  // fit per SM)
+  static constexpr int kStackB = (sizeof(TM) == 4 && kRowsBack >= 4) ? 6 : 8,
+                       kStackF = 2 * kStackB;
   static constexpr int kStackBytes = TREE ? 32 * kStackB * 16 : 0;
   static_assert(32 * kStackF * 8 <= 32 * kStackB * 16, "forward stack fits the region");
   static constexpr int kWarpBytes = kStages * kBytes + 64 + kStackBytes;  // + mbarriers
@@ -781,12 +784,14 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // minimum resident blocks per SM (which sets the register budget).  Shape 0 is
 // the default; the autotuner times all of them on the model and keeps the
 // fastest.
-// Trees take one backward row less per chunk where chains take 4, which leaves
-// shared memory for the fork stacks at 12 warps per SM.
+// FP64 trees take one backward row less per chunk where chains take 4, which
+// leaves shared memory for the fork stacks at 12 warps per SM (mixed trees keep
+// 4 rows and a shallower backward stack).
 template <class TM, bool TREE>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
-  constexpr int RB4 = TREE ? 3 : 4;
-  constexpr int RB6 = TREE ? 5 : 6;
+  constexpr bool f64tree = TREE && sizeof(TM) == 8;
+  constexpr int RB4 = f64tree ? 3 : 4;
+  constexpr int RB6 = f64tree ? 5 : 6;
   switch (shape) {
     case 1: return launch_epoch_t<TM, TREE, 3, 9, 4, 4>(a, stream);     // 16 warps per SM
     case 2: return launch_epoch_t<TM, TREE, RB6, 16, 2, 4>(a, stream);  // 8 warps, long chunks
