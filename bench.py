@@ -40,9 +40,9 @@ DFMA_PER_SM_CLK = 2            # FP64 FMA lanes per SM per clock (1.25 TFLOP/s n
 RCP64_DFMA_EQ = 465.0 / 71.0   # measured: FP64 FMA 465 G/s vs FP64 reciprocal 71 G/s on B300
 # DRAM bytes per compartment-update of the current epoch kernel (mixed, shape 0),
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
-# 65,536-cell launch of the same generator (94.47 GB for 735.3 M CU); traffic
+# 65,536-cell launch of the same generator (90.37 GB for 735.3 M CU); traffic
 # grows in proportion to the CUs of a launch, so the full launch is scaled.
-TRAFFIC_B_PER_CU = {}
+TRAFFIC_B_PER_CU = {"mixed": 122.9}
 
 
 def parse():
@@ -641,7 +641,7 @@ def main():
                 "frac": ach_tflops / peak_tflops,
                 "traffic": tb * cu_launch if tb else None,
                 "traffic_note": ("DRAM bytes per launch, scaled from one ncu capture of a "
-                                 "65,536-cell launch (128.5 B/CU)") if tb else
+                                 "65,536-cell launch (122.9 B/CU)") if tb else
                                 "not captured for this precision",
                 "kernel": "epoch_kernel", "fp64_ops_per_cu": fpc,
                 "peak_note": f"FP64: {N_SM} SMs x {DFMA_PER_SM_CLK} FMA/clk x 2 flop at the median "
