@@ -192,7 +192,7 @@ typedef struct {
 #define PA_FLAG_AUTOTUNE 2
 /* pa_options.flags: force epoch-kernel shape s (0 <= s < PA_N_SHAPES) */
 #define PA_FLAG_SHAPE(s) ((((s) + 1) & 0xF) << 8)
-#define PA_N_SHAPES 5
+#define PA_N_SHAPES 6
 /* pa_options.flags: launch every kernel directly.  By default pa_advance runs
  * each run of whole min-delay epochs as CUDA-graph launches (the epoch's Poisson,
  * time-step, routing and record kernels captured once, replayed per epoch; 8

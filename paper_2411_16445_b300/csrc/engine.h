@@ -212,7 +212,7 @@ struct RouteArgs {
 };
 
 // kernel launchers (defined in the .cu files)
-constexpr int kNumShapes = 5;  // kernel shapes (see launch_epoch_shape)
+constexpr int kNumShapes = 6;  // kernel shapes (see launch_epoch_shape)
 // The narrow kernel over groups [0, n_narrow) and the wide kernel.  With
 // `side` (a second stream and two events) and both bins in use, the wide
 // kernel runs on the side stream concurrently with the narrow one (fork and

@@ -160,11 +160,13 @@ __device__ __forceinline__ void fence_async_shared() {
 }
 
 // Shared-memory layout of one warp's stages for a given precision / tree flag.
-template <class TM, bool TREE, int kRowsBack, int kRowsFwd>
+template <class TM, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth>
 struct Stage {
   // bytes per row (32 lanes) of each staged array
   static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(TM), kI = TREE ? 32 * 2 : 0,
-                       kA = TREE ? 32 * 8 : 0, kT = TREE ? 32 : 0;
+                       kA = (TREE && kStackDepth > 0) ? 32 * 8 : 0,
+                       kT = (TREE && kStackDepth > 0) ? 32 : 0;
+  static constexpr bool kStacks = TREE && kStackDepth > 0;  // fork stacks in use
   // backward pass: V, C/dt, diagonal, leak E term, axial coupling, synaptic sums,
   // tree rows (the one other child's coupling, parent, first other child, fork flags)
   static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oDC = oCDT + kRowsBack * kD,
@@ -182,11 +184,10 @@ struct Stage {
   // fork stacks (trees): the backward pass keeps (f, x') of up to kStackB pending
   // one-other-children per lane, the forward pass V of up to kStackF pending forks;
   // deeper entries are read back from global memory
-  // (6 entries where the mixed kernel stages 4 backward rows, so that 12 warps
-  // fit per SM)
-  static constexpr int kStackB = (sizeof(TM) == 4 && kRowsBack >= 4) ? 6 : 8,
-                       kStackF = 2 * kStackB;
-  static constexpr int kStackBytes = TREE ? 32 * kStackB * 16 : 0;
+  // (the depth is part of the kernel shape: deep stacks where many forks nest,
+  // shallow ones where longer backward chunks take the shared memory)
+  static constexpr int kStackB = kStackDepth, kStackF = 2 * kStackDepth;
+  static constexpr int kStackBytes = kStacks ? 32 * kStackB * 16 : 0;
   static_assert(32 * kStackF * 8 <= 32 * kStackB * 16, "forward stack fits the region");
   static constexpr int kWarpBytes = kStages * kBytes + 64 + kStackBytes;  // + mbarriers
 };
@@ -300,9 +301,10 @@ __device__ __forceinline__ void run_sum(TM* gs, TM* es, int32_t rb, int lane, in
   }
 }
 
-template <class TM, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks>
+template <class TM, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
+          int kStackDepth>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const EpochArgs A) {
-  using ST = Stage<TM, TREE, kRowsBack, kRowsFwd>;
+  using ST = Stage<TM, TREE, kRowsBack, kRowsFwd, kStackDepth>;
   extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -481,9 +483,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kM, &bar[s]);
           bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kM, &bar[s]);
           if (TREE) {
-            bulk_load(st + ST::oAOCH, A.aoch + r0 * 32, cnt * ST::kA, &bar[s]);
             bulk_load(st + ST::oPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
             bulk_load(st + ST::oOCH, A.och_head + r0 * 32, cnt * ST::kI, &bar[s]);
+          }
+          if (ST::kStacks) {
+            bulk_load(st + ST::oAOCH, A.aoch + r0 * 32, cnt * ST::kA, &bar[s]);
             bulk_load(st + ST::oTF, A.tflag + r0 * 32, cnt * ST::kT, &bar[s]);
           }
         }
@@ -547,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           }
           uint8_t tf = 0;
           if (TREE) {
-            tf = ((const uint8_t*)(st + ST::oTF))[r];
+            if (ST::kStacks) tf = ((const uint8_t*)(st + ST::oTF))[r];
             const int och = ((const int16_t*)(st + ST::oOCH))[r];
             if (tf & kForkPop) {
               // the one other child: its f and x' from the top of the fork stack
@@ -619,10 +623,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           mbar_expect_tx(&bar[s], cnt * ST::kFwdRow);
           bulk_load(st + ST::fF, F + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::fXP, XP + r0 * 32, cnt * ST::kD, &bar[s]);
-          if (TREE) {
-            bulk_load(st + ST::fPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
-            bulk_load(st + ST::fTF, A.tflag + r0 * 32, cnt * ST::kT, &bar[s]);
-          }
+          if (TREE) bulk_load(st + ST::fPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
+          if (ST::kStacks) bulk_load(st + ST::fTF, A.tflag + r0 * 32, cnt * ST::kT, &bar[s]);
         }
       };
       fence_async_shared();
@@ -646,7 +648,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
         }
         const char* st = wbuf + s * ST::kBytes;
         const int lo = kRowsFwd * c, hi = lo + kRowsFwd < rows ? lo + kRowsFwd : rows;
-        if (TREE && c == 0 && n > 0 && (((const uint8_t*)(st + ST::fTF))[lane] & kForkPop)) {
+        if (ST::kStacks && c == 0 && n > 0 &&
+            (((const uint8_t*)(st + ST::fTF))[lane] & kForkPop)) {
           stack1[lane] = v0_new;  // the root is a fork with one other child
           depth = 1;
         }
@@ -656,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           double vp = vprev;
           uint8_t tf = 0;
           if (TREE) {
-            tf = ((const uint8_t*)(st + ST::fTF))[r];
+            if (ST::kStacks) tf = ((const uint8_t*)(st + ST::fTF))[r];
             const int pi = ((const int16_t*)(st + ST::fPAR))[r];
             if (tf & kForkPush) {
               // the one other child of its parent: the parent's V from the stack
@@ -758,25 +761,26 @@ int launch_init_gates_impl(const double* v, void* gate, int64_t n_lanes, const u
   return (int)cudaGetLastError();
 }
 
-template <class TM, bool TREE, int RB, int RF, int WPB, int MB>
+template <class TM, bool TREE, int RB, int RF, int WPB, int MB, int SB>
 int launch_epoch_t(const EpochArgs& a, void* stream) {
   constexpr int warps_per_block = WPB;
   const int threads = 32 * warps_per_block;
   const int64_t warps = a.n_narrow;
   const int blocks = (int)((warps * 32 + threads - 1) / threads);
   if (blocks == 0) return 0;
-  const int smem = warps_per_block * Stage<TM, TREE, RB, RF>::kWarpBytes;
+  const int smem = warps_per_block * Stage<TM, TREE, RB, RF, SB>::kWarpBytes;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
   static bool attr_set[64] = {false};  // per device; setting it twice is harmless
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(epoch_kernel<TM, TREE, RB, RF, 32 * WPB, MB>,
+    e = cudaFuncSetAttribute(epoch_kernel<TM, TREE, RB, RF, 32 * WPB, MB, SB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  epoch_kernel<TM, TREE, RB, RF, 32 * WPB, MB><<<blocks, threads, smem, (cudaStream_t)stream>>>(a);
+  epoch_kernel<TM, TREE, RB, RF, 32 * WPB, MB, SB>
+      <<<blocks, threads, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -784,20 +788,23 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // minimum resident blocks per SM (which sets the register budget).  Shape 0 is
 // the default; the autotuner times all of them on the model and keeps the
 // fastest.
-// FP64 trees take one backward row less per chunk where chains take 4, which
-// leaves shared memory for the fork stacks at 12 warps per SM (mixed trees keep
-// 4 rows and a shallower backward stack).
+// Trees also choose the fork stacks' depth: FP64 shape 0 takes 3 backward rows
+// per chunk and 8 entries (many nested forks), FP64 shapes 3 and 4 take 4 rows
+// and 2 entries, the mixed shapes 4 rows and 6 entries; shape 5 has no stacks
+// (trees with long branches and few forks); 12 warps per SM fit in each case.
 template <class TM, bool TREE>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   constexpr bool f64tree = TREE && sizeof(TM) == 8;
-  constexpr int RB4 = f64tree ? 3 : 4;
+  constexpr int RB0 = f64tree ? 3 : 4, SB0 = f64tree ? 8 : 6;
   constexpr int RB6 = f64tree ? 5 : 6;
+  constexpr int SB4 = f64tree ? 2 : 6;
   switch (shape) {
-    case 1: return launch_epoch_t<TM, TREE, 3, 9, 4, 4>(a, stream);     // 16 warps per SM
-    case 2: return launch_epoch_t<TM, TREE, RB6, 16, 2, 4>(a, stream);  // 8 warps, long chunks
-    case 3: return launch_epoch_t<TM, TREE, RB4, 12, 2, 6>(a, stream);  // 2-warp blocks
-    case 4: return launch_epoch_t<TM, TREE, RB4, 12, 1, 12>(a, stream); // 1-warp blocks
-    default: return launch_epoch_t<TM, TREE, RB4, 12, 4, 3>(a, stream); // 12 warps per SM
+    case 1: return launch_epoch_t<TM, TREE, 3, 9, 4, 4, 8>(a, stream);    // 16 warps per SM
+    case 2: return launch_epoch_t<TM, TREE, RB6, 16, 2, 4, 8>(a, stream); // 8 warps, long chunks
+    case 3: return launch_epoch_t<TM, TREE, 4, 12, 2, 6, SB4>(a, stream); // 2-warp blocks
+    case 4: return launch_epoch_t<TM, TREE, 4, 12, 1, 12, SB4>(a, stream);// 1-warp blocks
+    case 5: return launch_epoch_t<TM, TREE, 4, 12, 4, 3, 0>(a, stream);   // trees: no stacks
+    default: return launch_epoch_t<TM, TREE, RB0, 12, 4, 3, SB0>(a, stream);  // 12 warps per SM
   }
 }
 

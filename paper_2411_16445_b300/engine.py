@@ -62,7 +62,7 @@ FLAG_AUTOTUNE = 2
 FLAG_NO_GRAPHS = 8
 FLAG_NARROW_ONLY = 16
 FLAG_WIDE_ALL = 32
-N_SHAPES = 5
+N_SHAPES = 6
 
 
 def flag_shape(s: int) -> int:
