@@ -265,7 +265,7 @@ def time_e2e(net, precision, steps, device):
             "note": "includes pa_build_model (host descriptors -> HBM) and per-epoch spike read-back"}
 
 
-def oracle_sample(n_cells, n_shapes, budget_s=15.0, max_steps=4000, warm=2):
+def oracle_sample(n_cells, n_shapes, budget_s=12.0, max_steps=40000, warm=2):
     """The FP64 CPU oracle on a bounded sample of the workload: the same generator
     at n_cells cells, timed over whole steps until the CPU budget is spent."""
     cores = os.cpu_count() or 1
