@@ -71,9 +71,10 @@ extern "C" {
  * field takes one backward-Euler diffusion step, V_i (P_i' - P_i)/dt =
  * sum_j gD_ij (P_j' - P_i'), gD = D_p / ((L_i/2)/(pi r_i^2) + (L_j/2)/(pi r_j^2))
  * for adjacent CVs, solved by the same tree elimination as the cable equation.
- * PA_FIELD_PRP then reads the soma CV's concentration.  Such cells always run
- * in the narrow bin.  pa_fast_forward takes the same two steps with the long
- * step (its own backward-Euler matrix). */
+ * PA_FIELD_PRP then reads the soma CV's concentration.  Both cell bins solve
+ * the field (the wide bin by the same branch levels as the voltage).
+ * pa_fast_forward takes the same two steps with the long step (its own
+ * backward-Euler matrix). */
 /* Plasticity noise (Eqs. plasticity_noise_1-2): with the optional trailing
  * sigma_pl > 0, each step adds sigma_pl sqrt(n dt / tau) N(0,1) to w (GB,
  * tau = tau_w) or h (STC, tau = tau_h), n = number of the thresholds theta_p,
@@ -206,8 +207,7 @@ typedef struct {
  * cells with at least 128 CVs in at least 8 branches and at most 2 synapses
  * per CV are wide; below 1 warp per SM, every cell with at least 128 CVs plus
  * synapses is.  Both bins give identical results.  NARROW_ONLY / WIDE_ALL
- * force every cell into one bin, except that a cell whose PRP diffuses is
- * always narrow. */
+ * force every cell into one bin. */
 #define PA_FLAG_NARROW_ONLY 16
 #define PA_FLAG_WIDE_ALL 32
 

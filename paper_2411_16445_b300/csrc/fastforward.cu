@@ -42,7 +42,7 @@ __global__ void ff_slow_kernel(const EpochArgs A, const FastForward F) {
   const int64_t g = L >> 5, l = L & 31;
   const bool wide = g >= A.n_narrow;
   const bool has_stc = A.stc_stream >= 0 && A.has_stc[L];
-  const bool field = has_stc && A.prp_diff;  // never in the wide bin
+  const bool field = has_stc && A.prp_diff;
   const int32_t rb = A.row_base[g];
   double p = has_stc ? A.prp[L] : 0.0;
   for (int64_t it = 0; it < F.n_long; ++it) {
@@ -64,8 +64,10 @@ __global__ void ff_slow_kernel(const EpochArgs A, const FastForward F) {
         } else {
           const double h = D.w[e], z = D.z[e], h0 = P.h0;
           S = S + fabs(h - h0);
+          const uint32_t cv = (uint32_t)(D.cvf[e] >> 3);
           const double pz =
-              field ? A.prp_cv[((uint32_t)(rb + (D.cvf[e] >> 3)) << 5) | (uint32_t)l] : pk;
+              field ? A.prp_cv[wide ? ((uint32_t)rb << 5) + cv : ((uint32_t)(rb + cv) << 5) | (uint32_t)l]
+                    : pk;
           const double T1 = ((h - h0) > P.theta_tag) ? (pz * P.f_int) * (1.0 - z) : 0.0;
           const double T2 = ((h0 - h) > P.theta_tag) ? (pz * P.f_int) * (z + 0.5) : 0.0;
           D.z[e] = z + F.rate_z[s] * (T1 - T2);
@@ -76,7 +78,10 @@ __global__ void ff_slow_kernel(const EpochArgs A, const FastForward F) {
     if (has_stc) {
       const StreamParams& P = A.sp[A.stc_stream];
       const double qs = (S > P.theta_pro) ? P.p_max : 0.0;
-      if (field)
+      if (field && wide)
+        p = prp_field_step<TREE, true>(A, rb, 0, L, A.ncv[L], qs, F.rate_p, F.prp_dg_long,
+                                       F.prp_vdt_long);
+      else if (field)
         p = prp_field_step<TREE>(A, rb, (int)l, L, A.ncv[L], qs, F.rate_p, F.prp_dg_long,
                                  F.prp_vdt_long);
       else

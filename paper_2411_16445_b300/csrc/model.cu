@@ -448,10 +448,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
                             morph_branches[cells[c].morph] >= kWideMinBranches &&
                             cell_syn[c] <= (int64_t)kWideMaxSynPerCV * M->cell_ncv[c];
       const bool heavy = M->cell_ncv[c] + cell_syn[c] >= kWideMinWork;
-      // a diffusing PRP field is solved by the thread-per-cell bin only
-      wide[c] = !M->cell_diff[c] &&
-                ((opt->flags & PA_FLAG_WIDE_ALL) ||
-                 (!(opt->flags & PA_FLAG_NARROW_ONLY) && ((few && branched) || (idle && heavy))));
+      wide[c] = (opt->flags & PA_FLAG_WIDE_ALL) ||
+                (!(opt->flags & PA_FLAG_NARROW_ONLY) && ((few && branched) || (idle && heavy)));
     }
   }
   // narrow cells sorted by CV count (descending) and dealt into groups of 32
@@ -1556,7 +1554,9 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
       const int64_t L = M->lane_of_gid[c], g = L / kLanes;
       for (int i = 0; i < M->cell_ncv[c]; ++i)
         out[M->cell_cv_off[c] + i] =
-            M->cell_diff[c] ? tmp[((int64_t)M->row_base[g] + i) * kLanes + L % kLanes] : 0.0;
+            M->cell_diff[c] ? tmp[g < M->n_narrow ? ((int64_t)M->row_base[g] + i) * kLanes + L % kLanes
+                                                  : ((int64_t)M->row_base[g] << 5) + i]
+                            : 0.0;
     }
     return PA_OK;
   }
@@ -1800,7 +1800,8 @@ int pa_write_state(pa_model* M, int32_t field, const double* in, int64_t n) {
           if (!M->cell_diff[c]) continue;
           const int64_t L = M->lane_of_gid[c], g = L / kLanes;
           for (int i = 0; i < M->cell_ncv[c]; ++i)
-            v[((int64_t)M->row_base[g] + i) * kLanes + L % kLanes] =
+            v[g < M->n_narrow ? ((int64_t)M->row_base[g] + i) * kLanes + L % kLanes
+                              : ((int64_t)M->row_base[g] << 5) + i] =
                 per_cv ? in[M->cell_cv_off[c] + i] : in[c];
         }
       });

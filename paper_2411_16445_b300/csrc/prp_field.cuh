@@ -21,14 +21,18 @@ namespace pa {
 // row.  The Hines scratch f, x' must be free (the voltage solve of the step is
 // done).  Explicitly rounded operations: the same arithmetic in every build.
 // Returns the soma CV's new concentration.
-template <bool TREE>
+// WIDE: the cell's rows are contiguous (element (rb << 5) + row, the wide bin's
+// layout) instead of lane-interleaved.
+template <bool TREE, bool WIDE = false>
 __device__ __noinline__ double prp_field_step(const EpochArgs& A, int32_t rb, int lane, int64_t L,
                                               int n, double qs, double rate, const double* dg,
                                               const double* vdt) {
   double* __restrict__ P = A.prp_cv;
   double* __restrict__ F = A.f;
   double* __restrict__ XP = A.xp;
-  auto el = [&](int row) -> uint32_t { return ((uint32_t)(rb + row) << 5) | (uint32_t)lane; };
+  auto el = [&](int row) -> uint32_t {
+    return WIDE ? ((uint32_t)rb << 5) + (uint32_t)row : ((uint32_t)(rb + row) << 5) | (uint32_t)lane;
+  };
   double cf = 0.0, ca = 0.0, cx = 0.0, x0 = 0.0;
   bool carry = false;
   for (int i = n - 1; i >= 0; --i) {

@@ -23,7 +23,10 @@
 //      branch of the top level and runs on lane 0;
 //   c. forward pass by levels from the root down; a branch starts from its
 //      parent's new voltage (written one level earlier);
-//   d. soma on lane 0: HH gates, detection, spike record.
+//   d. a diffusing PRP field (Eq. diffusion): its reaction and backward-Euler
+//      diffusion step by the same branch levels and in the same order as the
+//      voltage (prp_field.cuh gives the arithmetic);
+//   e. soma on lane 0: HH gates, detection, spike record.
 #pragma once
 #include "epoch_kernel.cuh"
 
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
     const int kk = (int)(k - k0);
     const bool post = spiked_prev;
     // ---- a. synapse streams ---------------------------------------------------
-    double S = 0.0;
+    double S = 0.0, qs_field = 0.0;
     for (int s = 0; s < A.n_streams; ++s) {
       const StreamParams& P = A.sp[s];
       const StreamDev& D = A.sd[s];
@@ -109,7 +112,9 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           const double cc = calc ? D.c[e] : 0.0;
           const double wv = calc ? D.w[e] : 0.0;
           const double zv = stc ? D.z[e] : 0.0;
-          gv = syn_update<TM>(P, D, e, pre, capre, post, G[e], cc, wv, zv, prp, k, dt, A.seed,
+          // Eq. late_phase_weight with the cell's PRP, or that of the synapse's CV
+          const double pz = (stc && A.prp_diff) ? A.prp_cv[e0 + (cvf >> 3)] : prp;
+          gv = syn_update<TM>(P, D, e, pre, capre, post, G[e], cc, wv, zv, pz, k, dt, A.seed,
                               sadd);
           G[e] = gv * dg;
         }
@@ -161,7 +166,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
       __syncwarp();  // this stream's sums are visible to later streams and the solve
       if (s == A.stc_stream && has_stc) {
         const double qs = (S > P.theta_pro) ? P.p_max : 0.0;
-        prp = prp + P.rate_p * (qs - prp);
+        if (A.prp_diff) qs_field = qs;  // the field takes its step after the voltage solve
+        else prp = prp + P.rate_p * (qs - prp);
       }
     }
 
@@ -278,6 +284,79 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
       }
       __syncwarp();
     }
+    // ---- d. a diffusing PRP field, by the same levels ----------------------------
+    if (A.prp_diff && has_stc) {
+      const double rate = A.sp[A.stc_stream].rate_p;
+      double x0 = 0.0;
+      for (int lv = 0; lv < wc.n_lvl; ++lv) {
+        const int b0 = A.wlvl[wc.lvl0 + lv], b1 = A.wlvl[wc.lvl0 + lv + 1];
+        for (int b = b0 + lane; b < b1; b += 32) {
+          const int bs = A.wbr_s[wc.br0 + b], be = A.wbr_e[wc.br0 + b];
+          double cf = 0.0, ca = 0.0, cx = 0.0;
+          bool carry = false;
+          for (int i = be; i >= bs; --i) {
+            const int64_t ei = e0 + i;
+            const double pv = A.prp_cv[ei];
+            const double src = (i == 0) ? __dmul_rn(qs_field, A.prp_src[L]) : 0.0;
+            const double ps = __dadd_rn(pv, __dmul_rn(rate, __dsub_rn(src, pv)));
+            double d = A.prp_dg[ei];
+            double bb = __dmul_rn(A.prp_vdt[ei], ps);
+            if (PAR) {
+              for (int ch = OCH[ei]; ch >= 0; ch = OCN[e0 + ch]) {
+                const int64_t ec = e0 + ch;
+                const double ac = A.prp_a[ec];
+                d = __fma_rn(-F[ec], ac, d);
+                bb = __fma_rn(-ac, XP[ec], bb);
+              }
+            }
+            if (carry) {
+              d = __fma_rn(-cf, ca, d);
+              bb = __fma_rn(-ca, cx, bb);
+            } else if (i == be && PAR && i + 1 < n && PAR[ei + 1] == i) {
+              const double ac = A.prp_a[ei + 1];
+              d = __fma_rn(-F[ei + 1], ac, d);
+              bb = __fma_rn(-ac, XP[ei + 1], bb);
+            }
+            if (i > 0) {
+              const double ai = A.prp_a[ei];
+              const double rr = rcp_rn_pos(d);
+              const double fi = __dmul_rn(ai, rr);
+              const double xi = __dmul_rn(bb, rr);
+              F[ei] = fi;
+              XP[ei] = xi;
+              carry = true;
+              cf = fi; ca = ai; cx = xi;
+            } else {
+              x0 = __dmul_rn(bb, rcp_rn_pos(d));
+            }
+          }
+        }
+        __syncwarp();
+      }
+      for (int lv = wc.n_lvl - 1; lv >= 0; --lv) {
+        const int b0 = A.wlvl[wc.lvl0 + lv], b1 = A.wlvl[wc.lvl0 + lv + 1];
+        for (int b = b0 + lane; b < b1; b += 32) {
+          const int bs = A.wbr_s[wc.br0 + b], be = A.wbr_e[wc.br0 + b];
+          double pp;
+          int i = bs;
+          if (bs == 0) {
+            A.prp_cv[e0] = x0;
+            pp = x0;
+            i = 1;
+          } else {
+            pp = A.prp_cv[e0 + PAR[e0 + bs]];
+          }
+          for (; i <= be; ++i) {
+            const int64_t ei = e0 + i;
+            const double xi = __fma_rn(-F[ei], pp, XP[ei]);
+            A.prp_cv[ei] = xi;
+            pp = xi;
+          }
+        }
+        __syncwarp();
+      }
+      prp = __shfl_sync(full, x0, 0);  // the root branch runs on lane 0
+    }
     for (int32_t q = pq0 + lane; q < pq1; q += 32) {
       const int64_t smp = probe0 + (k - k_begin);
       if (smp < A.probe_cap) {
@@ -286,7 +365,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         atomicOr(A.err_flags, 1);
       }
     }
-    // ---- d. soma gates, detection (lane 0) -------------------------------------------
+    // ---- e. soma gates, detection (lane 0) -------------------------------------------
     bool spk = false;
     if (lane == 0) {
       if (hh) {

@@ -145,6 +145,47 @@ def caterpillar_net(n_trunk=40, dt=0.025, seed=13):
     return b.build()
 
 
+def fork_net(dt=0.025, seed=21):
+    """Trees for the fork stacks: a caterpillar numbered trunk-first (39 forks
+    pending at once, far beyond the stacks' depth), a star (a soma with five
+    dendrites, and one dendrite node with three children: forks with several
+    other children) and random binary trees (many short branches)."""
+    b = W._Builder(dt, seed, "forks")
+    rng = np.random.default_rng(seed)
+    hh = b.mech(W.HH, W.hh_params())
+    pas = b.mech(W.PAS, W.pas_params())
+    syn = b.mech(W.EXPSYN, W.expsyn_params(3.0, 0.0))
+    n_trunk = 40
+    n = 1 + 2 * n_trunk
+    par = np.empty(n, np.int32)
+    par[0] = -1
+    par[1:n_trunk + 1] = np.arange(0, n_trunk)
+    par[n_trunk + 1:] = np.arange(n_trunk, 0, -1)
+    cat = W.Morphology(par, np.full(n, 12.0), np.r_[18.0, np.full(n - 1, 1.5)],
+                       np.r_[0, np.ones(n - 1)].astype(np.int32))
+    # star: soma 0; dendrites start at 1, 6, 11, 16, 21 (5 CVs each); node 13 has
+    # children 14 (first), 26 and 27 (two other children)
+    spar = [-1]
+    for d in range(5):
+        start = len(spar)
+        spar += [0] + list(range(start, start + 4))
+    spar += [13, 13]
+    spar = np.asarray(spar, np.int32)
+    star = W.Morphology(spar, np.full(len(spar), 10.0), np.r_[16.0, np.full(len(spar) - 1, 1.2)],
+                        np.r_[0, np.ones(len(spar) - 1)].astype(np.int32))
+    m_cat, m_star = b.morph(cat), b.morph(star)
+    b.cells_add(9, m_cat, hh, pas, istep=0.3)
+    b.cells_add(9, m_star, hh, pas, istep=0.25)
+    for _ in range(30):
+        m = b.morph(W.random_binary_tree(rng, int(rng.integers(20, 120))))
+        b.cells_add(1, m, hh, pas, istep=0.2)
+    ncv = b.build().cell_ncv()
+    dst = np.repeat(np.arange(len(ncv)), 3)
+    cv = (rng.random(len(dst)) * ncv[dst]).astype(int)
+    b.connect(W.SRC_POISSON, dst, cv, syn, 3e-3, rate=50.0)
+    return b.build()
+
+
 def compare(a, b):
     a, b = np.asarray(a), np.asarray(b)
     assert a.shape == b.shape, (a.shape, b.shape)

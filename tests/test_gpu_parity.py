@@ -13,7 +13,8 @@ import oracle as O
 from paper_2411_16445_b300 import engine as E
 from paper_2411_16445_b300 import workloads as W
 
-from _nets import caterpillar_net, compare, edge_net, extract, map_spikes, tiny_tree_net
+from _nets import (caterpillar_net, compare, edge_net, extract, fork_net, map_spikes,
+                   tiny_tree_net)
 
 pytestmark = pytest.mark.gpu
 
@@ -517,8 +518,8 @@ def test_prp_diffusion_mixed_open_loop():
 def test_prp_diffusion_state_io_bins_and_fast_forward():
     """The field written per CV or uniformly per cell, read back, fast-forwarded
     (long reaction and diffusion steps) and continued bit-identically to the
-    oracle with the same writes; cells with a diffusing PRP stay narrow under
-    FLAG_WIDE_ALL (the others go wide)."""
+    oracle with the same writes, in the thread-per-cell bin and with every
+    cell in the warp-per-cell bin."""
     net = _diffusion_net()
     ncv = net.n_cv
     rng = np.random.default_rng(9)
@@ -536,7 +537,7 @@ def test_prp_diffusion_state_io_bins_and_fast_forward():
     for flags in (0, E.FLAG_WIDE_ALL):
         m = E.Model(net, precision=E.PA_FP64, flags=flags)
         if flags:
-            assert m.info().n_wide == 20            # the inhibitory cells only
+            assert m.info().n_wide == net.n_cells
         m.write_state(E.FIELD_H, _tag(net))
         m.write_state(E.FIELD_PRP_CV, field)
         got = m.read_state(E.FIELD_PRP_CV)
@@ -550,3 +551,27 @@ def test_prp_diffusion_state_io_bins_and_fast_forward():
         m.sync()
         check_state(o, m, E.PA_FP64, exact=True)
         assert np.array_equal(o.prp(), m.read_state(E.FIELD_PRP_CV))
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_fork_stacks_every_shape(precision):
+    """Fork stacks of every depth (and the shape without them) on trees whose
+    forks nest far beyond the stacks, forks with several other children and
+    random binary trees: FP64 bit-identical to the oracle in every shape,
+    mixed identical across shapes."""
+    net = fork_net()
+    steps = 1200
+    o = O.Oracle(net)
+    o.run(steps) if precision == E.PA_FP64 else None
+    ref = None
+    for s in range(E.N_SHAPES):
+        m = E.Model(net, precision=precision, flags=E.flag_shape(s) | E.FLAG_NARROW_ONLY)
+        assert m.info().tree == 1 and m.info().n_wide == 0
+        m.advance(steps * net.dt)
+        m.sync()
+        v = m.read_state(E.FIELD_V)
+        if precision == E.PA_FP64:
+            check_state(o, m, precision, exact=True)
+        if ref is None:
+            ref = v
+        assert np.array_equal(v, ref), f"shape {s} differs"
