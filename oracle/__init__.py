@@ -37,6 +37,8 @@ def lib():
         L.orc_get_syn.argtypes = [P, C.c_int32, P]
         L.orc_get_cell_p.argtypes = [P, P]
         L.orc_get_prp.argtypes = [P, P]
+        L.orc_get_ca.argtypes = [P, P]
+        L.orc_set_ca.argtypes = [P, P]
         L.orc_set_prp.argtypes = [P, P]
         L.orc_has_diffusion.restype = C.c_int32
         L.orc_has_diffusion.argtypes = [P, C.c_int32]
@@ -194,6 +196,18 @@ class Oracle:
         a = np.ascontiguousarray(values, np.float64)
         assert a.shape == (lib().orc_n_cv(self._h),)
         lib().orc_set_prp(self._h, _p(a))
+
+    def ca(self):
+        """Heterosynaptic calcium per CV (cell-major) of cells with HCA synapses
+        [umol/l]; 0 on every other CV."""
+        out = np.zeros(lib().orc_n_cv(self._h))
+        lib().orc_get_ca(self._h, _p(out))
+        return out
+
+    def set_ca(self, values):
+        a = np.ascontiguousarray(values, np.float64)
+        assert a.shape == (lib().orc_n_cv(self._h),)
+        lib().orc_set_ca(self._h, _p(a))
 
     def has_diffusion(self, cell: int) -> bool:
         return bool(lib().orc_has_diffusion(self._h, int(cell)))

@@ -320,6 +320,9 @@ typedef struct {
   double diff_d;  /* STC: PRP diffusivity D_p [um2/ms] (0: one pool per cell) */
   double amp[3];  /* Euler-Maruyama noise amplitude with n of the two thresholds crossed:
                      sigma_pl sqrt(n dt / tau) for tau = tau_w (GB) or tau_h (STC) */
+  /* HCA: calcium inflow per pA of injection current, gamma 1e6 / (2 F)
+     [umol/l um3 / (ms pA)]; dt gamma_p, dt gamma_d per step; dt / tau_C */
+  double kq, rate_gp, rate_gd, rate_ca;
 } orc_mech;
 
 struct orc_model {
@@ -340,6 +343,10 @@ struct orc_model {
      constant backward-Euler matrix (diagonal, coupling to the parent), V/dt */
   double *vol, *hx, *prp_cv, *prp_d, *prp_a, *prp_vdt, *vtot, *prp_src, *prp_gsum;
   int32_t* has_diff;
+  /* heterosynaptic calcium (cells with HCA synapses): concentration per CV
+     [umol/l], its backward-Euler matrix, V/dt, the step's inflow per CV */
+  double *ca_cv, *ca_d, *ca_a, *ca_vdt, *ca_src;
+  int32_t *has_ca, *cell_hca_mech;
   double* istep;
   int64_t *k_on, *k_off;
   double *thresh, *p;
@@ -376,7 +383,8 @@ struct orc_model {
 };
 
 static int is_point(int32_t k) {
-  return k == ORC_MECH_EXPSYN || k == ORC_MECH_GB || k == ORC_MECH_STC || k == ORC_MECH_STDP;
+  return k == ORC_MECH_EXPSYN || k == ORC_MECH_GB || k == ORC_MECH_STC || k == ORC_MECH_STDP ||
+         k == ORC_MECH_HCA;
 }
 static int n_params_of(int32_t k) {
   switch (k) {
@@ -386,6 +394,7 @@ static int n_params_of(int32_t k) {
     case ORC_MECH_GB: return 13;
     case ORC_MECH_STC: return 18;
     case ORC_MECH_STDP: return 8;
+    case ORC_MECH_HCA: return 10;
   }
   return -1;
 }
@@ -430,7 +439,8 @@ void orc_free(orc_model* M) {
                   M->cell_syn_off, M->cell_syn, M->out_off, M->out_syn, M->poisson_syn,
                   M->spk_gid, M->spk_step, M->spk_time, M->probe_cv, M->probes, M->rep_gid,
                   M->rep_step, M->vol, M->hx, M->prp_cv, M->prp_d, M->prp_a, M->prp_vdt,
-                  M->vtot, M->prp_src, M->prp_gsum, M->has_diff};
+                  M->vtot, M->prp_src, M->prp_gsum, M->has_diff, M->ca_cv, M->ca_d,
+                  M->ca_a, M->ca_vdt, M->ca_src, M->has_ca, M->cell_hca_mech};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
   if (M->q) {
     for (int64_t i = 0; i < M->R; ++i) free(M->q[i].v);
@@ -481,7 +491,21 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
       mc->amp[n] = (given > np) ? mc->sigma * sqrt(((double)n * dt) / mc->p[9]) : 0.0;
     /* per-dt constants: exact exponential decay of the linear ODEs
        (g' = -g/tau, c' = -c/tau_c, a' = -a/tau) and forward-Euler rates */
-    if (is_point(mc->kind)) mc->decay_g = exp(-dt / mc->p[0]);
+    if (is_point(mc->kind) && mc->kind != ORC_MECH_HCA) mc->decay_g = exp(-dt / mc->p[0]);
+    if (mc->kind == ORC_MECH_HCA) {
+      /* Eq. ca_injection_current_spine decays with tau_I; the current's
+         calcium (valence 2, Faraday constant 96485.33212 C/mol) in
+         umol/l um3 per ms and pA; rates of Eq. heterosyn_weight per second */
+      mc->decay_g = 1.0;
+      mc->decay_c = exp(-dt / mc->p[1]);
+      mc->kq = (mc->p[2] * 1e6) / (2.0 * 96485.33212);
+      mc->rate_gp = (dt * mc->p[3]) * 1e-3;
+      mc->rate_gd = (dt * mc->p[4]) * 1e-3;
+      mc->rate_ca = dt / mc->p[8];
+      if (!(mc->p[1] > 0) || !(mc->p[8] > 0) || !(mc->p[9] >= 0)) {
+        orc_free(M); return fail(-1, "mechanism %d: tau_I, tau_C > 0 and D >= 0 required", j);
+      }
+    }
     if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STC) {
       mc->decay_c = exp(-dt / mc->p[2]);
       double tcd = mc->kind == ORC_MECH_GB ? mc->p[11] : mc->p[17];
@@ -514,6 +538,8 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
   ALLOC(M->vol, N); ALLOC(M->hx, N); ALLOC(M->prp_cv, N); ALLOC(M->prp_d, N);
   ALLOC(M->prp_a, N); ALLOC(M->prp_vdt, N); ALLOC(M->vtot, n_cells); ALLOC(M->has_diff, n_cells);
   ALLOC(M->prp_src, n_cells); ALLOC(M->prp_gsum, N);
+  ALLOC(M->ca_cv, N); ALLOC(M->ca_d, N); ALLOC(M->ca_a, N); ALLOC(M->ca_vdt, N);
+  ALLOC(M->ca_src, N); ALLOC(M->has_ca, n_cells); ALLOC(M->cell_hca_mech, n_cells);
   ALLOC(M->istep, n_cells); ALLOC(M->k_on, n_cells); ALLOC(M->k_off, n_cells);
   ALLOC(M->thresh, n_cells); ALLOC(M->p, n_cells); ALLOC(M->spiked_prev, n_cells);
   ALLOC(M->spk_flag, n_cells); ALLOC(M->spk_t, n_cells); ALLOC(M->cell_stc_mech, n_cells);
@@ -586,6 +612,7 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
     M->k_off[c] = cell_toff[c] > 1e15 ? INT64_MAX : llround(cell_toff[c] / dt);
     M->thresh[c] = cell_thresh[c];
     M->cell_stc_mech[c] = -1;
+    M->cell_hca_mech[c] = -1;
   }
   free(rhalf);
   /* synapses, one per connection, in connection order */
@@ -638,6 +665,13 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
       M->cell_stc_mech[dst] = mj;
     }
     if (mc->kind == ORC_MECH_STDP) M->w[s] = mc->p[6];
+    if (mc->kind == ORC_MECH_HCA) {
+      M->w[s] = mc->p[7];
+      if (M->cell_hca_mech[dst] >= 0 && M->cell_hca_mech[dst] != mj) {
+        orc_free(M); return fail(-1, "cell %d: HCA synapses must share one mechanism", dst);
+      }
+      M->cell_hca_mech[dst] = mj;
+    }
   }
   for (int32_t c = 0; c < n_cells; ++c) M->out_off[c + 1] += M->out_off[c];
   ALLOC(M->out_syn, M->out_off[n_cells]);
@@ -702,6 +736,28 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
     M->prp_src[c] = vt / M->vol[base];
     M->has_diff[c] = 1;
   }
+  /* heterosynaptic calcium: the same backward-Euler diffusion on the cell's
+     tree (Eq. ca_diffusion_dendrite), with the mechanism's D */
+  for (int32_t c = 0; c < n_cells; ++c) {
+    int32_t mj = M->cell_hca_mech[c];
+    if (mj < 0) continue;
+    const double D = M->mech[mj].p[9];
+    int64_t base = M->cv_off[c], n = M->cv_off[c + 1] - base;
+    for (int64_t i = 0; i < n; ++i) M->xnew[base + i] = 0.0;
+    for (int64_t i = 1; i < n; ++i) {
+      int64_t p = base + M->parent[base + i];
+      double gd = D / (M->hx[base + i] + M->hx[p]);
+      M->ca_a[base + i] = -gd;
+      M->xnew[base + i] += gd;
+      M->xnew[p] += gd;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      double v = M->vol[base + i];
+      M->ca_vdt[base + i] = v / dt;
+      M->ca_d[base + i] = (v / dt) + M->xnew[base + i];
+    }
+    M->has_ca[c] = 1;
+  }
   M->n_probe = n_probe;
   ALLOC(M->probe_cv, n_probe);
   for (int32_t i = 0; i < n_probe; ++i) {
@@ -754,6 +810,10 @@ static void pre_event(orc_model* M, int64_t s, int64_t k) {
       M->g[s] += M->syn_weight[s] * ((M->hs[s] + h0 * M->z[s]) / h0);
       break;
     }
+    case ORC_MECH_HCA:
+      /* Eq. ca_injection_current_spine: the current jumps by I0 */
+      M->c[s] += mc->p[0];
+      break;
     case ORC_MECH_STDP: {
       double wc = M->w[s];
       if (wc < 0.0) wc = 0.0;
@@ -815,6 +875,26 @@ static void prp_field_step(orc_model* M, int32_t c, double qs, double rate, cons
   M->p[c] = P[0];
 }
 
+/* One step of the heterosynaptic calcium field of cell c (Eq.
+   ca_diffusion_dendrite): the reaction explicitly, C* = C + dt/tau_C (q - C)
+   with q = tau_C src / V the inflow's steady concentration in each CV (src
+   from this step's injection currents, 0 in CVs without synapses); then the
+   diffusion by one backward-Euler solve on the cell's tree. */
+static void ca_field_step(orc_model* M, int32_t c) {
+  int64_t base = M->cv_off[c], n = M->cv_off[c + 1] - base;
+  const orc_mech* mc = &M->mech[M->cell_hca_mech[c]];
+  const double tau_c = mc->p[8], r = mc->rate_ca;
+  double *C = M->ca_cv + base, *d = M->d + base, *b = M->b + base, *x = M->xnew + base;
+  for (int64_t i = 0; i < n; ++i) {
+    double q = (tau_c * M->ca_src[base + i]) / M->vol[base + i];
+    double cs = C[i] + r * (q - C[i]);
+    d[i] = M->ca_d[base + i];
+    b[i] = M->ca_vdt[base + i] * cs;
+  }
+  hines(n, M->parent + base, d, M->ca_a + base, b, M->f + base, M->xp + base, x);
+  for (int64_t i = 0; i < n; ++i) C[i] = x[i];
+}
+
 /* steps 2-5 for one cell */
 static void cell_step(orc_model* M, int32_t c, int64_t k) {
   const double dt = M->dt;
@@ -823,6 +903,8 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
   double *V = M->V + base, *gs = M->gs + base, *es = M->es + base;
   double *d = M->d + base, *b = M->b + base;
   for (int64_t i = 0; i < n; ++i) { gs[i] = 0.0; es[i] = 0.0; }
+  if (M->has_ca[c])
+    for (int64_t i = 0; i < n; ++i) M->ca_src[base + i] = 0.0;
   /* synaptic conductances summed per CV in the cell's canonical order */
   for (int64_t j = M->cell_syn_off[c]; j < M->cell_syn_off[c + 1]; ++j) {
     int64_t s = M->cell_syn[j];
@@ -903,6 +985,19 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
       if (mc->sigma > 0.0 && nth > 0) hn = hn + mc->amp[nth] * orc_normal(M->seed, (uint64_t)s, k);
       M->hs[s] = hn;
       M->c[s] = cc * mc->decay_c;
+    } else if (mc->kind == ORC_MECH_HCA) {
+      /* the injection current after this step's events (Eq.
+         ca_injection_current_spine) brings w gamma I / (2 F) of calcium into the
+         synapse's CV (the source of Eq. ca_diffusion_dendrite), summed per CV in
+         canonical order; Eq. heterosyn_weight by forward Euler with the CV's
+         calcium before this step's update; then the current decays */
+      int64_t ci = M->syn_cv[s] - base;
+      double I = M->c[s], w = M->w[s], cl = M->ca_cv[M->syn_cv[s]];
+      M->ca_src[base + ci] = M->ca_src[base + ci] + w * (mc->kq * I);
+      double P = (cl > q[5]) ? mc->rate_gp * (1.0 - w) : 0.0;
+      double D = (cl > q[6]) ? mc->rate_gd * w : 0.0;
+      M->w[s] = w + (P - D);
+      M->c[s] = I * mc->decay_c;
     }
   }
   if (M->cell_stc_mech[c] >= 0) {
@@ -916,6 +1011,7 @@ static void cell_step(orc_model* M, int32_t c, int64_t k) {
       M->p[c] = pk + mc->rate_p * (qs - pk);
     }
   }
+  if (M->has_ca[c]) ca_field_step(M, c);
   /* threshold detection at the soma CV with linear interpolation of the time */
   double th = M->thresh[c];
   M->spk_flag[c] = 0;
@@ -1003,6 +1099,8 @@ int orc_run(orc_model* M, int64_t n_steps) {
  * through their closed form as the clock advances by K. */
 int orc_fast_forward(orc_model* M, int64_t K, int64_t n_long) {
   if (K < 0 || n_long < 1 || M->replay) return -1;
+  for (int32_t c = 0; c < M->n_cells; ++c)
+    if (M->has_ca[c]) return -1; /* calcium dynamics have no long-step scheme */
   const double T = (double)K * M->dt;
   const double dtl = T / (double)n_long;
   /* a diffusing PRP field takes its long steps with the long step's matrix:
@@ -1084,6 +1182,16 @@ void orc_set_prp(orc_model* M, const double* in) {
   }
 }
 int32_t orc_has_diffusion(const orc_model* M, int32_t c) { return M->has_diff[c]; }
+/* heterosynaptic calcium per CV of cells with HCA synapses (other CVs: 0) */
+void orc_get_ca(const orc_model* M, double* out) {
+  memcpy(out, M->ca_cv, sizeof(double) * (size_t)M->n_cv);
+}
+void orc_set_ca(orc_model* M, const double* in) {
+  for (int32_t c = 0; c < M->n_cells; ++c) {
+    if (!M->has_ca[c]) continue;
+    for (int64_t i = M->cv_off[c]; i < M->cv_off[c + 1]; ++i) M->ca_cv[i] = in[i];
+  }
+}
 /* per cell; the field of a cell whose PRP diffuses is set uniform */
 void orc_set_cell_p(orc_model* M, const double* in) {
   memcpy(M->p, in, sizeof(double) * (size_t)M->n_cells);
@@ -1134,7 +1242,8 @@ void orc_get_syn(const orc_model* M, int32_t field, double* out) {
         break;
       case ORC_SYN_WEIGHT_TOTAL:
         if (mc->kind == ORC_MECH_STC) v = M->hs[s] + mc->p[12] * M->z[s];
-        else if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STDP) v = M->w[s];
+        else if (mc->kind == ORC_MECH_GB || mc->kind == ORC_MECH_STDP || mc->kind == ORC_MECH_HCA)
+          v = M->w[s];
         else v = M->syn_weight[s];
         break;
     }

@@ -41,7 +41,12 @@ enum {
                           theta_tag [mV], theta_pro [mV], p_max, f_int, t_c_delay
                           [, sigma_pl [, D_p [um2/ms]]]; D_p > 0: the cell's PRP is
                           a concentration per CV that diffuses (Eq. diffusion)      */
-  ORC_MECH_STDP = 13   /* params: tau, e, tau_pre, tau_post, A_pre, A_post, w0, w_max */
+  ORC_MECH_STDP = 13,  /* params: tau, e, tau_pre, tau_post, A_pre, A_post, w0, w_max */
+  ORC_MECH_HCA = 14    /* heterosynaptic calcium (Eqs. ca_injection_current_spine,
+                          ca_diffusion_dendrite, heterosyn_weight); params: I0 [pA],
+                          tau_I [ms], gamma (Ca2+ fraction of the current), gamma_p,
+                          gamma_d [1/s], theta_p, theta_d [umol/l], w0, tau_C [ms],
+                          D [um2/ms]; no conductance */
 };
 
 /* per-connection synapse state fields readable with orc_get_syn (STDP traces:
@@ -100,6 +105,8 @@ void orc_get_probes(const orc_model* m, double* out);      /* [sample][probe] */
 void orc_get_syn(const orc_model* m, int32_t field, double* out); /* connection order */
 void orc_get_cell_p(const orc_model* m, double* out);      /* PRP per cell */
 void orc_get_prp(const orc_model* m, double* out);  /* PRP per CV of diffusing cells, else 0 */
+void orc_get_ca(const orc_model* m, double* out);   /* calcium per CV of HCA cells, else 0 */
+void orc_set_ca(orc_model* m, const double* in);    /* per CV; other cells untouched */
 void orc_set_prp(orc_model* m, const double* in);   /* per CV; cells without diffusion untouched */
 int32_t orc_has_diffusion(const orc_model* m, int32_t cell);
 void orc_get_gates(const orc_model* m, double* out);       /* m,h,n of each cell's CV 0 */

@@ -18,7 +18,7 @@ from typing import List, Optional
 import numpy as np
 
 # Mechanism kinds (descriptor format shared by the engine's C-ABI and the oracle).
-PAS, HH, EXPSYN, GB, STC, STDP = 1, 2, 10, 11, 12, 13
+PAS, HH, EXPSYN, GB, STC, STDP, HCA = 1, 2, 10, 11, 12, 13, 14
 SRC_POISSON = -1
 NEVER = 1e300  # t_off meaning "never switched off"
 
@@ -71,6 +71,15 @@ def stc_params(tau=5.0, e=0.0, tau_c=48.8, c_pre=0.6, c_post=0.1655, theta_p=3.0
     if d_p > 0.0:
         p.append(d_p)
     return np.array(p)
+
+
+def hca_params(i0=4.0, tau_i=1.0, gamma=0.11, gamma_p=90.0, gamma_d=0.01, theta_p=0.11,
+               theta_d=0.05, w0=0.5, tau_c=100.0, d=0.22):
+    """Heterosynaptic calcium rule (Eqs. ca_injection_current_spine,
+    ca_diffusion_dendrite, heterosyn_weight; Table 4, Arbor's I0 = 4 pA):
+    I0 [pA], tau_I [ms], gamma, gamma_p, gamma_d [1/s], theta_p, theta_d
+    [umol/l], w0 (not in Table 4), tau_C [ms], D [um2/ms] (2.2e-10 m2/s)."""
+    return np.array([i0, tau_i, gamma, gamma_p, gamma_d, theta_p, theta_d, w0, tau_c, d])
 
 
 def stdp_params(tau=5.0, e=0.0, tau_pre=16.8, tau_post=33.7, a_pre=0.01, a_post=-0.012,
@@ -412,6 +421,39 @@ def recurrent_stc_morpho(n_exc=160, n_inh=40, p=0.1, dt=0.2, seed=None, d_p=1e-2
     ext_cv = np.where(ext_dst < n_exc, apical_tip, 0)
     b.connect(SRC_POISSON, ext_dst, ext_cv, exc, w_ext, rate=ext_rate)
     return b.build()
+
+
+def heterosyn_dendrite(dt=0.025, seed=None, n_spikes=10, isi_ms=10.0, t0_ms=10.0,
+                       active=(0, 2), **hca):
+    """Heterosynaptic calcium plasticity on a dendritic branch (Sec. on
+    heterosynaptic calcium-based plasticity, Table 4, Fig. 8): an 80 um
+    dendrite of 1 um CVs (radius 1 um) spanning x = -40..40 um, CV 0 its root,
+    with four spine heads (1 um long, radius 1 um) on the CVs holding x = -1,
+    0, 1 and 3 um; an HCA synapse on each head.  The active spines (1 and 3 by
+    default) receive a regular train (n_spikes every isi_ms from t0_ms) from a
+    source cell whose spikes are replayed; the others get a silent Poisson
+    source.  The membrane is passive: the calcium is decoupled from the cable.
+    Returns the network and the replay list (gid, step)."""
+    name = "heterosyn_dendrite"
+    b = _Builder(dt, config_seed(name) if seed is None else seed, name)
+    pas = b.mech(PAS, pas_params())
+    m_hca = b.mech(HCA, hca_params(**hca))
+    n_d = 80
+    heads = [39, 40, 41, 43]                       # CVs holding x = -1, 0, 1, 3 um
+    parent = np.r_[-1, np.arange(n_d - 1), heads].astype(np.int32)
+    n = parent.shape[0]
+    morph = Morphology(parent, np.ones(n), np.full(n, 2.0), np.r_[0, np.ones(n - 1)].astype(np.int32))
+    m_d = b.morph(morph)
+    m_s = b.morph(soma_only(10.0))
+    b.cells_add(1, m_d, pas, pas)
+    b.cells_add(1, m_s, pas, pas)                  # the replayed source, gid 1
+    for k in range(4):
+        if k in active:
+            b.connect(1, 0, n_d + k, m_hca, 1.0, delay=dt)
+        else:
+            b.connect(SRC_POISSON, 0, n_d + k, m_hca, 1.0, rate=0.0)
+    steps = np.array([int(round((t0_ms + j * isi_ms) / dt)) for j in range(n_spikes)], np.int64)
+    return b.build(), (np.ones(n_spikes, np.int32), steps)
 
 
 def morphology_sweep(n_nets=64, cells_per_net=500, p=0.1, dt=0.2, seed=None,
