@@ -86,6 +86,18 @@ extern "C" {
 #define PA_MECH_STDP 13   /* point, expsyn + pair STDP; params: tau, e, tau_pre, tau_post
                              [ms], A_pre, A_post, w0, w_max (w dimensionless, conductance
                              jump = weight * clip(w, 0, w_max)) */
+#define PA_MECH_HCA 14    /* point, heterosynaptic calcium (Eqs. ca_injection_current_spine,
+                             ca_diffusion_dendrite, heterosyn_weight); params: I0 [pA],
+                             tau_I [ms], gamma, gamma_p, gamma_d [1/s], theta_p, theta_d
+                             [umol/l], w0, tau_C [ms], D [um2/ms].  No conductance: an
+                             event adds I0 to the synapse's injection current I (decay
+                             tau_I), whose calcium w gamma I / (2 F) enters the synapse's
+                             CV each step; the cell's calcium per CV decays with tau_C and
+                             diffuses with D (the explicit reaction, then one backward-
+                             Euler diffusion step on the tree, as for the PRP); w follows
+                             Eq. heterosyn_weight by forward Euler with its CV's calcium.
+                             At most one HCA mechanism per model; its cells run in the
+                             narrow bin; pa_fast_forward refuses the model. */
 
 /* arithmetic of the loop */
 #define PA_FP64 0   /* everything in FP64 */
@@ -110,6 +122,9 @@ extern "C" {
 #define PA_FIELD_GATES 18  /* HH gates m, h, n of each cell's soma CV: 3 values per cell */
 #define PA_FIELD_PRP_CV 19 /* PRP concentration per CV (cell-major) of cells whose PRP
                               diffuses (STC with D_p > 0); 0 on every other CV */
+#define PA_FIELD_CA_CV 20  /* heterosynaptic calcium per CV (cell-major) of cells with HCA
+                              synapses [umol/l]; 0 on every other CV.  PA_FIELD_C reads an
+                              HCA synapse's injection current I [pA], PA_FIELD_W its w */
 
 typedef struct pa_model pa_model;
 

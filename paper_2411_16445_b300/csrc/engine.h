@@ -22,7 +22,7 @@ constexpr int kLanes = 32;
 constexpr int kMaxStreams = 8;
 constexpr int kMaxProbeRowsPerLane = 1 << 15;
 
-enum StreamKind : int32_t { SK_EXPSYN = 0, SK_GB = 1, SK_STC = 2, SK_STDP = 3 };
+enum StreamKind : int32_t { SK_EXPSYN = 0, SK_GB = 1, SK_STC = 2, SK_STDP = 3, SK_HCA = 4 };
 
 // Constants of one synapse stream (one point mechanism), derived for the dt.
 struct StreamParams {
@@ -37,6 +37,9 @@ struct StreamParams {
   double a_pre, a_post, tau_pre, tau_post, w_max;                         // STDP
   double sigma;          // GB, STC: plasticity noise sigma_pl (0: none)
   double amp[3];         // sigma_pl sqrt(n dt / tau) with n thresholds crossed
+  // HCA (c_pre = I0 [pA], decay_c = exp(-dt/tau_I), theta_p/theta_d [umol/l]):
+  // calcium inflow per pA gamma 1e6 / (2 F), dt gamma_p, dt gamma_d per step
+  double hca_kq, hca_gpr, hca_gdr;
 };
 
 // Device pointers of one synapse stream.  Element index e = ((sbase+j)<<5)|lane.
@@ -151,6 +154,18 @@ struct EpochArgs {
   const double* prp_a;
   const double* prp_vdt;
   const double* prp_src;
+  // heterosynaptic calcium (an HCA stream; its cells in the narrow bin): the
+  // calcium per CV [umol/l], its backward-Euler matrix (diagonal, coupling),
+  // V/dt and V per CV, the step's inflow per CV (summed by the synapse phase)
+  int32_t ca_stream;         // index of the HCA stream or -1
+  double ca_tau, ca_rate;    // tau_C, dt / tau_C
+  double* ca_cv;
+  double* ca_src;
+  const double* ca_dg;
+  const double* ca_a;
+  const double* ca_vdt;
+  const double* ca_vol;
+  const uint8_t* has_ca;     // per lane
   int64_t n_lanes;
   // synapse streams
   int32_t n_streams;

@@ -199,11 +199,26 @@ struct Stage {
 // plastic state and returns the conductance entering this step's per-CV sums.
 // cc, wv, zv are the synapse's calcium, weight (h for STC) and z as loaded by
 // the caller (only those its kind uses); S accumulates |h - h0| (STC).
+// HCA (heterosynaptic calcium): cc is the injection current, wv the weight,
+// prp the calcium of the synapse's CV; qv receives the calcium inflow.
 template <class TM>
 __device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev& D, uint32_t e,
                                          bool pre, bool capre, bool post, TM gv, double cc,
                                          double wv, double zv, double prp, int64_t k, double dt,
-                                         uint64_t seed, double& S) {
+                                         uint64_t seed, double& S, double& qv) {
+  if (P.kind == SK_HCA) {
+    // Eq. ca_injection_current_spine: I jumps by I0; its calcium w gamma I / (2 F)
+    // enters the CV (Eq. ca_diffusion_dendrite); Eq. heterosyn_weight by forward
+    // Euler with the CV's calcium before this step's update; then I decays
+    if (pre) cc = __dadd_rn(cc, P.c_pre);
+    const double w = wv, cl = prp;
+    qv = __dmul_rn(w, __dmul_rn(P.hca_kq, cc));
+    const double Pw = (cl > P.theta_p) ? __dmul_rn(P.hca_gpr, __dsub_rn(1.0, w)) : 0.0;
+    const double Dw = (cl > P.theta_d) ? __dmul_rn(P.hca_gdr, w) : 0.0;
+    D.w[e] = __dadd_rn(w, __dsub_rn(Pw, Dw));
+    D.c[e] = __dmul_rn(cc, P.decay_c);
+    return gv;
+  }
   if (P.kind == SK_EXPSYN) {
     if (pre) gv = gv + ((const TM*)D.weight)[e];
   } else if (P.kind == SK_GB) {
@@ -376,12 +391,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       const int32_t sb = D.sbase[g], nrow = D.sbase[g + 1] - sb;
       const bool calc = P.kind == SK_GB || P.kind == SK_STC;
       const bool stc = P.kind == SK_STC;
+      const bool hca = P.kind == SK_HCA;
+      const bool cw = calc || hca;  // calcium (or injection current) and weight rows
       constexpr int szm = 32 * (int)sizeof(TM);
-      const int rowb = 128 + 256 + szm + (calc ? 768 : 0) + (stc ? 256 : 0);
+      const int rowb = 128 + 256 + szm + (calc ? 256 : 0) + (cw ? 512 : 0) + (stc ? 256 : 0);
       int RS = ST::kBytes / rowb;
       if (RS > 16) RS = 16;
       const int o_cm = RS * 128, o_g = o_cm + RS * 256, o_cam = o_g + RS * szm,
-                o_c = o_cam + RS * 256, o_w = o_c + RS * 256, o_z = o_w + RS * 256;
+                o_c = o_cam + (calc ? RS * 256 : 0), o_w = o_c + RS * 256, o_z = o_w + RS * 256;
       const int nc = (nrow + RS - 1) / RS;
       const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
       const uint64_t* camg = calc ? D.camask + (int64_t)slot * D.n_elem : nullptr;
@@ -398,8 +415,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           bulk_load(st, D.cvf + r0, cnt * 128, &bar[si]);
           bulk_load(st + o_cm, cmg + r0, cnt * 256, &bar[si]);
           bulk_load(st + o_g, (const TM*)D.g + r0, cnt * szm, &bar[si]);
-          if (calc) {
-            bulk_load(st + o_cam, camg + r0, cnt * 256, &bar[si]);
+          if (calc) bulk_load(st + o_cam, camg + r0, cnt * 256, &bar[si]);
+          if (cw) {
             bulk_load(st + o_c, D.c + r0, cnt * 256, &bar[si]);
             bulk_load(st + o_w, D.w + r0, cnt * 256, &bar[si]);
           }
@@ -412,6 +429,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
         issue(0);
       }
       TM accg = 0, acce = 0;
+      double accq = 0.0;  // a run's calcium inflow (HCA)
       for (int c = 0; c < nc; ++c) {
         if (c + 1 < nc) {
           fence_async_shared();
@@ -434,14 +452,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           const uint32_t e = ((uint32_t)(sb + lo + jj) << 5) | (uint32_t)lane;
           const bool pre = (((const uint64_t*)(st + o_cm))[r] >> kk) & 1ull;
           const bool capre = calc && ((((const uint64_t*)(st + o_cam))[r] >> kk) & 1ull);
-          const double cc = calc ? ((const double*)(st + o_c))[r] : 0.0;
-          const double wv = calc ? ((const double*)(st + o_w))[r] : 0.0;
+          const double cc = cw ? ((const double*)(st + o_c))[r] : 0.0;
+          const double wv = cw ? ((const double*)(st + o_w))[r] : 0.0;
           const double zv = stc ? ((const double*)(st + o_z))[r] : 0.0;
           // Eq. late_phase_weight captures the cell's PRP, or that of the
           // synapse's own CV when the PRP diffuses
-          const double pz = (stc && A.prp_diff) ? A.prp_cv[elem_of(rb, cvf >> 3, lane)] : prp;
+          // (an HCA synapse takes its CV's calcium instead)
+          const double pz = hca ? A.ca_cv[elem_of(rb, cvf >> 3, lane)]
+                                : (stc && A.prp_diff) ? A.prp_cv[elem_of(rb, cvf >> 3, lane)] : prp;
+          double qv = 0.0;
           TM gv = syn_update<TM>(P, D, e, pre, capre, post, ((const TM*)(st + o_g))[r], cc, wv,
-                                 zv, pz, k, dt, A.seed, S);
+                                 zv, pz, k, dt, A.seed, S, qv);
+          if (hca) {
+            // the calcium inflow per CV, summed over the run in canonical order
+            accq = (cvf & 2) ? qv : __dadd_rn(accq, qv);
+            if (cvf & 4) A.ca_src[elem_of(rb, cvf >> 3, lane)] = accq;
+          }
           run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
           G[e] = gv * dg;
         }
@@ -687,6 +713,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
     if (A.prp_diff && has_stc)
       prp = prp_field_step<TREE>(A, rb, lane, L, n, qs_field, A.sp[A.stc_stream].rate_p, A.prp_dg,
                                  A.prp_vdt);
+    if (A.ca_stream >= 0 && n > 0 && A.has_ca[L]) ca_field_step<TREE>(A, rb, lane, n);
     if (n > 0) {
       for (int32_t q = pq0; q < pq1; ++q) {
         const int64_t smp = probe0 + (k - k_begin);

@@ -49,6 +49,7 @@ int n_params_of(int kind) {
     case PA_MECH_GB: return 13;
     case PA_MECH_STC: return 18;
     case PA_MECH_STDP: return 8;
+    case PA_MECH_HCA: return 10;
   }
   return -1;
 }
@@ -62,7 +63,7 @@ void set_noise(pa::StreamParams& P, const pa_mechanism& m, int np, double tau, d
 }
 bool is_point(int kind) {
   return kind == PA_MECH_EXPSYN || kind == PA_MECH_GB || kind == PA_MECH_STC ||
-         kind == PA_MECH_STDP;
+         kind == PA_MECH_STDP || kind == PA_MECH_HCA;
 }
 
 // A bump allocator over one cudaMalloc: every array of a model lives in it.
@@ -110,6 +111,7 @@ struct pa_model {
   std::vector<double> conn_weight;
   std::vector<double> conn_h0;
   bool prp_diff = false;                  // the STC mechanism's PRP diffuses (D_p > 0)
+  std::vector<uint8_t> cell_ca;           // per gid: the cell has HCA synapses
   std::vector<uint8_t> cell_diff;         // per gid: the cell's PRP is a field over its CVs
   std::vector<double> prp_vol, prp_gsum;  // per element: CV volume, summed gD (fast-forward)
   std::vector<double> ff_dg, ff_vdt;      // the long step's matrix, staged for upload
@@ -328,7 +330,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   }
   CUDA_TRY(cudaSetDevice(M->device));
 
-  int n_streams = 0, stc_stream = -1;
+  int n_streams = 0, stc_stream = -1, ca_stream = -1;
+  double ca_tau = 0.0, ca_d = 0.0;  // the HCA mechanism's tau_C and D
   double diff_d = 0.0;  // PRP diffusivity [um2/ms]
   int stream_mech[kMaxStreams];
   for (int64_t m = 0; m < n_mech; ++m) {
@@ -374,6 +377,25 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         P.tau_pre = p[2];
         P.tau_post = p[3];
         P.a_pre = p[4]; P.a_post = p[5]; P.w_max = p[7];
+        break;
+      case PA_MECH_HCA:
+        // no conductance: g stays 0 (e = 0, decay 1); the injection current in c
+        if (!(p[1] > 0) || !(p[8] > 0) || !(p[9] >= 0))
+          return set_err(PA_ERR_ARG, "mechanism %lld: tau_I, tau_C > 0 and D >= 0 required",
+                         (long long)m);
+        if (ca_stream >= 0) return set_err(PA_ERR_ARG, "at most one HCA mechanism per model");
+        P.kind = SK_HCA;
+        ca_stream = s;
+        P.e = 0.0;
+        P.decay_g = 1.0;
+        P.decay_c = std::exp(-dt / p[1]);
+        P.c_pre = p[0];
+        P.theta_p = p[5]; P.theta_d = p[6];
+        P.hca_kq = (p[2] * 1e6) / (2.0 * 96485.33212);
+        P.hca_gpr = (dt * p[3]) * 1e-3;
+        P.hca_gdr = (dt * p[4]) * 1e-3;
+        ca_tau = p[8];
+        ca_d = p[9];
         break;
     }
     if ((P.kind == SK_GB || P.kind == SK_STC) && P.dc_steps < 0)
@@ -427,6 +449,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     return set_err(PA_ERR_ARG, "PA_FLAG_NARROW_ONLY and PA_FLAG_WIDE_ALL exclude each other");
   std::vector<char> wide(n_cells, 0);
   M->cell_diff.assign(n_cells, 0);
+  std::vector<uint8_t> cell_ca(n_cells, 0);  // cells with HCA synapses (narrow bin)
   {
     std::vector<int64_t> cell_syn(n_cells, 0);
     for (int64_t c = 0; c < n_conn; ++c)
@@ -434,6 +457,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         ++cell_syn[conns[c].dst_gid];
         if (M->prp_diff && mechs[conns[c].mech].kind == PA_MECH_STC)
           M->cell_diff[conns[c].dst_gid] = 1;
+        if (mechs[conns[c].mech].kind == PA_MECH_HCA) cell_ca[conns[c].dst_gid] = 1;
       }
     std::vector<int32_t> morph_branches(n_morph, 0);
     for (int64_t j = 0; j < n_morph; ++j)
@@ -448,8 +472,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
                             morph_branches[cells[c].morph] >= kWideMinBranches &&
                             cell_syn[c] <= (int64_t)kWideMaxSynPerCV * M->cell_ncv[c];
       const bool heavy = M->cell_ncv[c] + cell_syn[c] >= kWideMinWork;
-      wide[c] = (opt->flags & PA_FLAG_WIDE_ALL) ||
-                (!(opt->flags & PA_FLAG_NARROW_ONLY) && ((few && branched) || (idle && heavy)));
+      // the heterosynaptic calcium field is solved by the thread-per-cell bin only
+      wide[c] = !cell_ca[c] &&
+                ((opt->flags & PA_FLAG_WIDE_ALL) ||
+                 (!(opt->flags & PA_FLAG_NARROW_ONLY) && ((few && branched) || (idle && heavy))));
     }
   }
   // narrow cells sorted by CV count (descending) and dealt into groups of 32
@@ -517,6 +543,13 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<int64_t> h_kon(n_lanes, 0), h_koff(n_lanes, 0);
   std::vector<double> rhalf, gi_v, gax, cdt_v, dcc;
   std::vector<double> h_pcv, h_pdg, h_pa, h_pvdt, h_psrc, vol, hx, gdx;
+  std::vector<double> h_cadg, h_caa, h_cavdt, h_cavol;
+  if (ca_stream >= 0) {
+    h_cadg.assign(n_elem, 1.0);
+    h_caa.assign(n_elem, 0.0);
+    h_cavdt.assign(n_elem, 0.0);
+    h_cavol.assign(n_elem, 1.0);
+  }
   if (M->prp_diff) {
     h_pdg.assign(n_elem, 1.0);
     h_pa.assign(n_elem, 0.0);
@@ -597,6 +630,30 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         }
         if (i > 0 && i != g.parent[i] + 1 && n_other[g.parent[i]] == 1) h_tf[e] |= kForkPush;
       }
+      // The stacks need the pushes and pops to nest (LIFO) in both sweeps, as in
+      // depth-first numberings; a numbering that interleaves subtrees (side
+      // branches numbered after the trunk, in trunk order) keeps the linked lists.
+      bool nested = true;
+      std::vector<int> stk;
+      for (int i = n - 1; i >= 0 && nested; --i) {
+        const uint8_t f = h_tf[elem(L, i)];
+        if (f & kForkPop) {
+          if (stk.empty() || stk.back() != h_och[elem(L, i)]) nested = false;
+          else stk.pop_back();
+        }
+        if (f & kForkPush) stk.push_back(i);
+      }
+      stk.clear();
+      for (int i = 0; i < n && nested; ++i) {
+        const uint8_t f = h_tf[elem(L, i)];
+        if (f & kForkPush) {
+          if (stk.empty() || stk.back() != g.parent[i]) nested = false;
+          else stk.pop_back();
+        }
+        if (f & kForkPop) stk.push_back(i);
+      }
+      if (!nested)
+        for (int i = 0; i < n; ++i) h_tf[elem(L, i)] = 0;
     }
     if (M->cell_diff[lane_gid[L]]) {
       // PRP diffusion (Eq. diffusion on the cable's tree): CV volume, the
@@ -627,6 +684,29 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         vt = vt + vol[i];
       }
       h_psrc[L] = vt / vol[0];  // synthesis at the soma: p_max V_tot / (V_0 tau_p)
+    }
+    if (cell_ca[lane_gid[L]]) {
+      // heterosynaptic calcium (Eq. ca_diffusion_dendrite): the same tree
+      // discretisation as the PRP field, with the HCA mechanism's D
+      std::vector<double> cvol(n), chx(n), cg(n, 0.0);
+      for (int i = 0; i < n; ++i) {
+        const double Lc = g.length_um[i], r = 0.5 * g.diam_um[i];
+        cvol[i] = (kPi * (r * r)) * Lc;
+        chx[i] = (0.5 * Lc) / (kPi * (r * r));
+      }
+      for (int i = 1; i < n; ++i) {
+        const int p = g.parent[i];
+        const double gd = ca_d / (chx[i] + chx[p]);
+        h_caa[elem(L, i)] = -gd;
+        cg[i] += gd;
+        cg[p] += gd;
+      }
+      for (int i = 0; i < n; ++i) {
+        const int64_t e = elem(L, i);
+        h_cavdt[e] = cvol[i] / dt;
+        h_cadg[e] = (cvol[i] / dt) + cg[i];
+        h_cavol[e] = cvol[i];
+      }
     }
     h_iinj[L] = cl.i_step;
     h_kon[L] = std::llround(cl.t_on / dt);
@@ -738,7 +818,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<std::vector<int32_t>> s_cvf(n_streams);
   std::vector<std::vector<double>> s_weight(n_streams), s_w(n_streams);
   std::vector<std::vector<int32_t>> s_nid(n_streams);   // noise source ids (noisy streams)
-  std::vector<uint8_t> h_has_stc(n_lanes, 0);
+  std::vector<uint8_t> h_has_stc(n_lanes, 0), h_has_ca(n_lanes, 0);
   for (int s = 0; s < n_streams; ++s) {
     s_sbase[s].assign(n_groups + 1, 0);
     for (int64_t g = 0; g < n_groups; ++g) {
@@ -787,6 +867,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         s_weight[s][e] = conns[v[j].conn].weight;
         if (M->sp[s].kind == SK_GB) s_w[s][e] = p[12];
         if (M->sp[s].kind == SK_STDP) s_w[s][e] = p[6];
+        if (M->sp[s].kind == SK_HCA) {
+          s_w[s][e] = p[7];
+          h_has_ca[L] = 1;
+        }
         if (M->sp[s].kind == SK_STC) {
           s_w[s][e] = p[12];
           h_has_stc[L] = 1;
@@ -899,7 +983,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     o_s[s][1] = R(4 * ne);                    // cvf
     o_s[s][2] = R(tm * ne);                   // weight
     o_s[s][3] = R(tm * ne);                   // g
-    o_s[s][4] = (kind == SK_GB || kind == SK_STC) ? R(8 * ne) : 0;              // c
+    o_s[s][4] = (kind == SK_GB || kind == SK_STC || kind == SK_HCA) ? R(8 * ne) : 0;  // c / I
     o_s[s][5] = (kind != SK_EXPSYN) ? R(8 * ne) : 0;                            // w / h
     o_s[s][6] = (kind == SK_STC) ? R(8 * ne) : 0;                               // z
     o_s[s][7] = (kind == SK_STDP) ? R(tm * ne) : 0;                             // apre
@@ -928,6 +1012,12 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_wbr_e = R(sizeof(int32_t) * std::max<size_t>(h_wbr_e.size(), 1));
   const size_t o_wlvl = R(sizeof(int32_t) * std::max<size_t>(h_wlvl.size(), 1));
   const size_t o_clock = R(sizeof(EpochClock));
+  size_t o_cacv = 0, o_casrc = 0, o_cadg = 0, o_caa = 0, o_cavdt = 0, o_cavol = 0, o_hasca = 0;
+  if (ca_stream >= 0) {
+    o_cacv = R(8 * n_elem); o_casrc = R(8 * n_elem); o_cadg = R(8 * n_elem);
+    o_caa = R(8 * n_elem); o_cavdt = R(8 * n_elem); o_cavol = R(8 * n_elem);
+    o_hasca = R(n_lanes);
+  }
   size_t o_pcv = 0, o_pdg = 0, o_pa = 0, o_pvdt = 0, o_psrc = 0, o_ffdg = 0, o_ffvdt = 0;
   if (M->prp_diff) {
     o_pcv = R(8 * n_elem); o_pdg = R(8 * n_elem); o_pa = R(8 * n_elem);
@@ -968,6 +1058,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   putv(o_wcell, h_wcell); putv(o_wbr_s, h_wbr_s); putv(o_wbr_e, h_wbr_e); putv(o_wlvl, h_wlvl);
   putv(o_iinj, h_iinj); putv(o_kon, h_kon); putv(o_koff, h_koff); putv(o_th, h_thresh);
   putv(o_hasstc, h_has_stc);
+  if (ca_stream >= 0) {
+    putv(o_cadg, h_cadg); putv(o_caa, h_caa); putv(o_cavdt, h_cavdt); putv(o_cavol, h_cavol);
+    putv(o_hasca, h_has_ca);
+  }
   if (M->prp_diff) {
     putv(o_pdg, h_pdg); putv(o_pa, h_pa); putv(o_pvdt, h_pvdt); putv(o_psrc, h_psrc);
   }
@@ -1030,6 +1124,19 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   A.prp = (double*)P8(o_prp);
   A.has_stc = (const uint8_t*)P8(o_hasstc);
   A.stc_stream = stc_stream;
+  A.ca_stream = ca_stream;
+  if (ca_stream >= 0) {
+    A.ca_tau = ca_tau;
+    A.ca_rate = dt / ca_tau;
+    A.ca_cv = (double*)P8(o_cacv);
+    A.ca_src = (double*)P8(o_casrc);
+    A.ca_dg = (const double*)P8(o_cadg);
+    A.ca_a = (const double*)P8(o_caa);
+    A.ca_vdt = (const double*)P8(o_cavdt);
+    A.ca_vol = (const double*)P8(o_cavol);
+    A.has_ca = (const uint8_t*)P8(o_hasca);
+    M->cell_ca = cell_ca;
+  }
   if (M->prp_diff) {
     A.prp_diff = 1;
     A.prp_cv = (double*)P8(o_pcv);
@@ -1544,6 +1651,21 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
     }
     return PA_OK;
   }
+  if (field == PA_FIELD_CA_CV) {
+    *n_out = M->n_cv;
+    if (cap == 0) return PA_OK;
+    if (!out || cap < M->n_cv) return set_err(PA_ERR_ARG, "output too small");
+    const bool has = M->ea.ca_stream >= 0;
+    int rc = fetch(M->ea.ca_cv, has ? M->total_rows * kLanes : 0, 8, tmp);
+    if (rc) return rc;
+    for (int64_t c = 0; c < M->n_cells; ++c) {
+      const int64_t L = M->lane_of_gid[c], g = L / kLanes;
+      for (int i = 0; i < M->cell_ncv[c]; ++i)
+        out[M->cell_cv_off[c] + i] =
+            (has && M->cell_ca[c]) ? tmp[((int64_t)M->row_base[g] + i) * kLanes + L % kLanes] : 0.0;
+    }
+    return PA_OK;
+  }
   if (field == PA_FIELD_PRP_CV) {
     *n_out = M->n_cv;
     if (cap == 0) return PA_OK;
@@ -1585,7 +1707,10 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
     switch (field) {
       case PA_FIELD_G: src = D.g; break;
       case PA_FIELD_C: src = D.c; esz = 8; break;
-      case PA_FIELD_W: src = (kind == SK_GB || kind == SK_STDP) ? D.w : nullptr; esz = 8; break;
+      case PA_FIELD_W:
+        src = (kind == SK_GB || kind == SK_STDP || kind == SK_HCA) ? D.w : nullptr;
+        esz = 8;
+        break;
       case PA_FIELD_H: src = kind == SK_STC ? D.w : nullptr; esz = 8; break;
       case PA_FIELD_Z: src = D.z; esz = 8; break;
       case PA_FIELD_APRE: src = D.apre; break;
@@ -1634,7 +1759,8 @@ int pa_read_weights(pa_model* M, double* out, int64_t cap, int64_t* n_out) {
   for (int64_t c = 0; c < M->n_conn; ++c) {
     switch (M->conn_kind[c]) {
       case PA_MECH_GB:
-      case PA_MECH_STDP: out[c] = w[c]; break;
+      case PA_MECH_STDP:
+      case PA_MECH_HCA: out[c] = w[c]; break;
       case PA_MECH_STC: out[c] = h[c] + M->conn_h0[c] * z[c]; break;
       default: out[c] = M->conn_weight[c];
     }
@@ -1707,6 +1833,8 @@ int pa_fast_forward(pa_model* M, double duration_ms, int64_t n_long) {
   using namespace pa;
   if (!M) return set_err(PA_ERR_ARG, "model is NULL");
   if (M->replay) return set_err(PA_ERR_STATE, "pa_fast_forward does not run in open-loop replay");
+  if (M->ea.ca_stream >= 0)
+    return set_err(PA_ERR_STATE, "pa_fast_forward: heterosynaptic calcium has no long-step scheme");
   const double ks = duration_ms / M->dt;
   const int64_t K = std::llround(ks);
   if (!std::isfinite(ks) || K < 0 || std::fabs(ks - (double)K) > 1e-6 * std::max(1.0, std::fabs(ks)))
@@ -1787,6 +1915,19 @@ int pa_write_state(pa_model* M, int32_t field, const double* in, int64_t n) {
       }
     });
   }
+  if (field == PA_FIELD_CA_CV) {
+    if (n != M->n_cv) return set_err(PA_ERR_ARG, "expected %lld values", (long long)M->n_cv);
+    if (M->ea.ca_stream < 0) return PA_OK;
+    return rmw(M->ea.ca_cv, M->total_rows * kLanes, 8, [&](char* raw) {
+      double* v = (double*)raw;
+      for (int64_t c = 0; c < M->n_cells; ++c) {
+        if (!M->cell_ca[c]) continue;
+        const int64_t L = M->lane_of_gid[c], g = L / kLanes;
+        for (int i = 0; i < M->cell_ncv[c]; ++i)
+          v[((int64_t)M->row_base[g] + i) * kLanes + L % kLanes] = in[M->cell_cv_off[c] + i];
+      }
+    });
+  }
   if (field == PA_FIELD_PRP_CV || (field == PA_FIELD_PRP && M->prp_diff)) {
     // the field of each diffusing cell (PA_FIELD_PRP: uniform at the cell's
     // value) and the soma value that PA_FIELD_PRP reads back
@@ -1835,7 +1976,7 @@ int pa_write_state(pa_model* M, int32_t field, const double* in, int64_t n) {
     switch (field) {
       case PA_FIELD_G: dst = D.g; tm32 = mixed; break;
       case PA_FIELD_C: dst = D.c; break;
-      case PA_FIELD_W: dst = (kind == SK_GB || kind == SK_STDP) ? D.w : nullptr; break;
+      case PA_FIELD_W: dst = (kind == SK_GB || kind == SK_STDP || kind == SK_HCA) ? D.w : nullptr; break;
       case PA_FIELD_H: dst = kind == SK_STC ? D.w : nullptr; break;
       case PA_FIELD_Z: dst = D.z; break;
       case PA_FIELD_APRE: dst = D.apre; tm32 = mixed; break;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libplasticarbor.so")
 PA_FP64, PA_MIXED = 0, 1
 PA_SRC_POISSON = -1
 FIELD_G, FIELD_C, FIELD_W, FIELD_H, FIELD_Z, FIELD_APRE, FIELD_APOST = range(7)
-FIELD_V, FIELD_PRP, FIELD_GATES, FIELD_PRP_CV = 16, 17, 18, 19
+FIELD_V, FIELD_PRP, FIELD_GATES, FIELD_PRP_CV, FIELD_CA_CV = 16, 17, 18, 19, 20
 ERRORS = {-1: "PA_ERR_ARG", -2: "PA_ERR_OOM", -3: "PA_ERR_CUDA", -4: "PA_ERR_TIMEOUT",
           -5: "PA_ERR_CAPACITY", -6: "PA_ERR_STATE"}
 

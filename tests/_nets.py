@@ -147,9 +147,10 @@ def caterpillar_net(n_trunk=40, dt=0.025, seed=13):
 
 def fork_net(dt=0.025, seed=21):
     """Trees for the fork stacks: a caterpillar numbered trunk-first (39 forks
-    pending at once, far beyond the stacks' depth), a star (a soma with five
-    dendrites, and one dendrite node with three children: forks with several
-    other children) and random binary trees (many short branches)."""
+    pending at once, far beyond the stacks' depth), the same with its side CVs
+    in trunk order (not nested), a star (a soma with five dendrites, and one
+    dendrite node with three children: forks with several other children) and
+    random binary trees (many short branches)."""
     b = W._Builder(dt, seed, "forks")
     rng = np.random.default_rng(seed)
     hh = b.mech(W.HH, W.hh_params())
@@ -173,9 +174,16 @@ def fork_net(dt=0.025, seed=21):
     spar = np.asarray(spar, np.int32)
     star = W.Morphology(spar, np.full(len(spar), 10.0), np.r_[16.0, np.full(len(spar) - 1, 1.2)],
                         np.r_[0, np.ones(len(spar) - 1)].astype(np.int32))
-    m_cat, m_star = b.morph(cat), b.morph(star)
+    # the same caterpillar with its side CVs numbered in trunk order: the pushes
+    # and pops of the fork stacks would not nest (the kernel keeps the lists)
+    par2 = par.copy()
+    par2[n_trunk + 1:] = np.arange(1, n_trunk + 1)
+    cat2 = W.Morphology(par2, np.full(n, 12.0), np.r_[18.0, np.full(n - 1, 1.5)],
+                        np.r_[0, np.ones(n - 1)].astype(np.int32))
+    m_cat, m_star, m_cat2 = b.morph(cat), b.morph(star), b.morph(cat2)
     b.cells_add(9, m_cat, hh, pas, istep=0.3)
     b.cells_add(9, m_star, hh, pas, istep=0.25)
+    b.cells_add(5, m_cat2, hh, pas, istep=0.3)
     for _ in range(30):
         m = b.morph(W.random_binary_tree(rng, int(rng.integers(20, 120))))
         b.cells_add(1, m, hh, pas, istep=0.2)

@@ -575,3 +575,62 @@ def test_fork_stacks_every_shape(precision):
         if ref is None:
             ref = v
         assert np.array_equal(v, ref), f"shape {s} differs"
+
+
+def _hca_check(o, m, exact):
+    pairs = [(o.v(), m.read_state(E.FIELD_V)), (o.ca(), m.read_state(E.FIELD_CA_CV)),
+             (o.syn(O.SYN_C), m.read_state(E.FIELD_C)), (o.syn(O.SYN_W), m.read_state(E.FIELD_W))]
+    for a, b in pairs:
+        if exact:
+            assert np.array_equal(a, b)
+        else:
+            assert compare(a, b) <= 1e-9 * max(1.0, np.abs(a).max())
+
+
+@pytest.mark.parametrize("precision", [E.PA_FP64, E.PA_MIXED])
+def test_heterosynaptic_calcium_dendrite(precision):
+    """The Table 4 dendrite with four spines, two of them driven by a regular
+    100 Hz train (replayed): injection currents, the calcium field per CV and
+    the weights, FP64 bit-identical to the oracle."""
+    net, (gid, step) = W.heterosyn_dendrite(n_spikes=10)
+    o = O.Oracle(net)
+    o.set_replay(gid, step)
+    m = E.Model(net, precision=precision)
+    m.set_replay(gid, step)
+    for t in (60.0, 150.0, 400.0):
+        k = int(round(t / net.dt))
+        o.run(k - o.step_count())
+        m.advance(k * net.dt)
+        m.sync()
+        _hca_check(o, m, exact=precision == E.PA_FP64)
+    ca = o.ca()
+    assert ca[80] > 0 and ca[82] > 0 and np.all(o.syn(O.SYN_W) != 0.5)
+
+
+def test_heterosynaptic_calcium_trees_closed_loop():
+    """HCA synapses on random trees of a small recurrent network (Poisson and
+    network events), closed loop: FP64 bit-identical, and the model refuses a
+    fast-forward."""
+    dt = 0.025
+    b = W._Builder(dt, 31, "hca_trees")
+    rng = np.random.default_rng(31)
+    hh = b.mech(W.HH, W.hh_params())
+    pas = b.mech(W.PAS, W.pas_params())
+    drive = b.mech(W.EXPSYN, W.expsyn_params(2.0, 0.0))
+    hca = b.mech(W.HCA, W.hca_params(d=0.5, tau_c=40.0, i0=6.0))
+    sizes = rng.integers(8, 50, 40)
+    for c in range(40):
+        b.cells_add(1, b.morph(W.random_binary_tree(rng, int(sizes[c]))), hh, pas)
+    b.connect(W.SRC_POISSON, np.arange(40), 0, drive, 0.08, rate=40.0)
+    src = rng.integers(0, 40, 300)
+    dst = rng.integers(0, 40, 300)
+    cv = (rng.random(300) * (sizes[dst] + 1)).astype(int)
+    b.connect(src, dst, cv, hca, 1.0, delay=1.0)
+    b.connect(W.SRC_POISSON, dst[:60], cv[:60], hca, 1.0, rate=30.0)
+    net = b.build()
+    o, m = run_both(net, 3000, E.PA_FP64, chunks=2)
+    check_state(o, m, E.PA_FP64, exact=True)
+    _hca_check(o, m, exact=True)
+    assert o.ca().max() > 0
+    with pytest.raises(E.PaError):
+        m.fast_forward(100.0, 2)
