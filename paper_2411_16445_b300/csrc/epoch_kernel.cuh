@@ -199,26 +199,11 @@ struct Stage {
 // plastic state and returns the conductance entering this step's per-CV sums.
 // cc, wv, zv are the synapse's calcium, weight (h for STC) and z as loaded by
 // the caller (only those its kind uses); S accumulates |h - h0| (STC).
-// HCA (heterosynaptic calcium): cc is the injection current, wv the weight,
-// prp the calcium of the synapse's CV; qv receives the calcium inflow.
 template <class TM>
 __device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev& D, uint32_t e,
                                          bool pre, bool capre, bool post, TM gv, double cc,
                                          double wv, double zv, double prp, int64_t k, double dt,
-                                         uint64_t seed, double& S, double& qv) {
-  if (P.kind == SK_HCA) {
-    // Eq. ca_injection_current_spine: I jumps by I0; its calcium w gamma I / (2 F)
-    // enters the CV (Eq. ca_diffusion_dendrite); Eq. heterosyn_weight by forward
-    // Euler with the CV's calcium before this step's update; then I decays
-    if (pre) cc = __dadd_rn(cc, P.c_pre);
-    const double w = wv, cl = prp;
-    qv = __dmul_rn(w, __dmul_rn(P.hca_kq, cc));
-    const double Pw = (cl > P.theta_p) ? __dmul_rn(P.hca_gpr, __dsub_rn(1.0, w)) : 0.0;
-    const double Dw = (cl > P.theta_d) ? __dmul_rn(P.hca_gdr, w) : 0.0;
-    D.w[e] = __dadd_rn(w, __dsub_rn(Pw, Dw));
-    D.c[e] = __dmul_rn(cc, P.decay_c);
-    return gv;
-  }
+                                         uint64_t seed, double& S) {
   if (P.kind == SK_EXPSYN) {
     if (pre) gv = gv + ((const TM*)D.weight)[e];
   } else if (P.kind == SK_GB) {
@@ -316,6 +301,53 @@ __device__ __forceinline__ void run_sum(TM* gs, TM* es, int32_t rb, int lane, in
   }
 }
 
+// One step of the lane's synapses of the heterosynaptic calcium stream (HCA),
+// apart from the TMA-staged loop of the other kinds so that theirs stays as
+// small as it is (HCA models are small; plain loads suffice).  Per synapse, in
+// canonical order: Eq. ca_injection_current_spine (I jumps by I0 at an event),
+// its calcium w gamma I / (2 F) summed per CV over each run into ca_src (the
+// source of Eq. ca_diffusion_dendrite), Eq. heterosyn_weight by forward Euler
+// with the CV's calcium before this step's field update, then I decays.  The
+// synapses carry no conductance: where an HCA run is the first on its CV, the
+// per-CV conductance sums start at zero there, as the loop of the other kinds
+// would make them.
+template <class TM>
+__device__ __noinline__ void hca_stream(const EpochArgs& A, int s, int g, int lane, int32_t rb,
+                                        int kk, int32_t slot) {
+  const StreamParams& P = A.sp[s];
+  const StreamDev& D = A.sd[s];
+  const int32_t sb = D.sbase[g], nrow = D.sbase[g + 1] - sb;
+  const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
+  TM* GS = (TM*)A.gs;
+  TM* ES = (TM*)A.es;
+  double accq = 0.0;
+  bool zero = false;
+  for (int j = 0; j < nrow; ++j) {
+    const uint32_t e = ((uint32_t)(sb + j) << 5) | (uint32_t)lane;
+    const int32_t cvf = D.cvf[e];
+    if (cvf < 0) continue;
+    const uint32_t ce = elem_of(rb, cvf >> 3, lane);
+    const bool pre = (cmg[e] >> kk) & 1ull;
+    double cc = D.c[e];
+    const double w = D.w[e], cl = A.ca_cv[ce];
+    if (pre) cc = __dadd_rn(cc, P.c_pre);
+    const double qv = __dmul_rn(w, __dmul_rn(P.hca_kq, cc));
+    const double Pw = (cl > P.theta_p) ? __dmul_rn(P.hca_gpr, __dsub_rn(1.0, w)) : 0.0;
+    const double Dw = (cl > P.theta_d) ? __dmul_rn(P.hca_gdr, w) : 0.0;
+    D.w[e] = __dadd_rn(w, __dsub_rn(Pw, Dw));
+    D.c[e] = __dmul_rn(cc, P.decay_c);
+    if (cvf & 2) zero = cvf & 1;  // the run is the first on its CV this step
+    accq = (cvf & 2) ? qv : __dadd_rn(accq, qv);
+    if (cvf & 4) {
+      A.ca_src[ce] = accq;
+      if (zero) {
+        GS[ce] = (TM)0;
+        ES[ce] = (TM)0;
+      }
+    }
+  }
+}
+
 template <class TM, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
           int kStackDepth>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const EpochArgs A) {
@@ -386,19 +418,21 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
     __syncwarp();
     double S = 0.0, qs_field = 0.0;
     for (int s = 0; s < A.n_streams && !failed; ++s) {
+      if (s == A.ca_stream) {
+        hca_stream<TM>(A, s, g, lane, rb, kk, slot);
+        continue;
+      }
       const StreamParams& P = A.sp[s];
       const StreamDev& D = A.sd[s];
       const int32_t sb = D.sbase[g], nrow = D.sbase[g + 1] - sb;
       const bool calc = P.kind == SK_GB || P.kind == SK_STC;
       const bool stc = P.kind == SK_STC;
-      const bool hca = P.kind == SK_HCA;
-      const bool cw = calc || hca;  // calcium (or injection current) and weight rows
       constexpr int szm = 32 * (int)sizeof(TM);
-      const int rowb = 128 + 256 + szm + (calc ? 256 : 0) + (cw ? 512 : 0) + (stc ? 256 : 0);
+      const int rowb = 128 + 256 + szm + (calc ? 768 : 0) + (stc ? 256 : 0);
       int RS = ST::kBytes / rowb;
       if (RS > 16) RS = 16;
       const int o_cm = RS * 128, o_g = o_cm + RS * 256, o_cam = o_g + RS * szm,
-                o_c = o_cam + (calc ? RS * 256 : 0), o_w = o_c + RS * 256, o_z = o_w + RS * 256;
+                o_c = o_cam + RS * 256, o_w = o_c + RS * 256, o_z = o_w + RS * 256;
       const int nc = (nrow + RS - 1) / RS;
       const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
       const uint64_t* camg = calc ? D.camask + (int64_t)slot * D.n_elem : nullptr;
@@ -415,8 +449,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           bulk_load(st, D.cvf + r0, cnt * 128, &bar[si]);
           bulk_load(st + o_cm, cmg + r0, cnt * 256, &bar[si]);
           bulk_load(st + o_g, (const TM*)D.g + r0, cnt * szm, &bar[si]);
-          if (calc) bulk_load(st + o_cam, camg + r0, cnt * 256, &bar[si]);
-          if (cw) {
+          if (calc) {
+            bulk_load(st + o_cam, camg + r0, cnt * 256, &bar[si]);
             bulk_load(st + o_c, D.c + r0, cnt * 256, &bar[si]);
             bulk_load(st + o_w, D.w + r0, cnt * 256, &bar[si]);
           }
@@ -429,7 +463,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
         issue(0);
       }
       TM accg = 0, acce = 0;
-      double accq = 0.0;  // a run's calcium inflow (HCA)
       for (int c = 0; c < nc; ++c) {
         if (c + 1 < nc) {
           fence_async_shared();
@@ -452,22 +485,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           const uint32_t e = ((uint32_t)(sb + lo + jj) << 5) | (uint32_t)lane;
           const bool pre = (((const uint64_t*)(st + o_cm))[r] >> kk) & 1ull;
           const bool capre = calc && ((((const uint64_t*)(st + o_cam))[r] >> kk) & 1ull);
-          const double cc = cw ? ((const double*)(st + o_c))[r] : 0.0;
-          const double wv = cw ? ((const double*)(st + o_w))[r] : 0.0;
+          const double cc = calc ? ((const double*)(st + o_c))[r] : 0.0;
+          const double wv = calc ? ((const double*)(st + o_w))[r] : 0.0;
           const double zv = stc ? ((const double*)(st + o_z))[r] : 0.0;
           // Eq. late_phase_weight captures the cell's PRP, or that of the
           // synapse's own CV when the PRP diffuses
-          // (an HCA synapse takes its CV's calcium instead)
-          const double pz = hca ? A.ca_cv[elem_of(rb, cvf >> 3, lane)]
-                                : (stc && A.prp_diff) ? A.prp_cv[elem_of(rb, cvf >> 3, lane)] : prp;
-          double qv = 0.0;
+          const double pz = (stc && A.prp_diff) ? A.prp_cv[elem_of(rb, cvf >> 3, lane)] : prp;
           TM gv = syn_update<TM>(P, D, e, pre, capre, post, ((const TM*)(st + o_g))[r], cc, wv,
-                                 zv, pz, k, dt, A.seed, S, qv);
-          if (hca) {
-            // the calcium inflow per CV, summed over the run in canonical order
-            accq = (cvf & 2) ? qv : __dadd_rn(accq, qv);
-            if (cvf & 4) A.ca_src[elem_of(rb, cvf >> 3, lane)] = accq;
-          }
+                                 zv, pz, k, dt, A.seed, S);
           run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
           G[e] = gv * dg;
         }

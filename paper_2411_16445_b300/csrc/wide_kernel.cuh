@@ -114,9 +114,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           const double zv = stc ? D.z[e] : 0.0;
           // Eq. late_phase_weight with the cell's PRP, or that of the synapse's CV
           const double pz = (stc && A.prp_diff) ? A.prp_cv[e0 + (cvf >> 3)] : prp;
-          double qv = 0.0;  // (HCA synapses are never in the wide bin)
           gv = syn_update<TM>(P, D, e, pre, capre, post, G[e], cc, wv, zv, pz, k, dt, A.seed,
-                              sadd, qv);
+                              sadd);
           G[e] = gv * dg;
         }
         // Per-CV sums in canonical order (run_sum's arithmetic): each lane sums
