@@ -13,7 +13,10 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
+
+#include <sched.h>
 
 #include "../../include/plastic_arbor.h"
 #include "engine.h"
@@ -172,6 +175,33 @@ struct SynRec {
   int64_t conn;
   int32_t cv;
 };
+
+// Runs fn(begin, end) over contiguous pieces of [0, n) on the host cores this
+// process may use (at most 64 threads).  The model builder's per-group loops
+// write disjoint elements, so the result does not depend on the thread count.
+// A thread that cannot be started has its piece run on the calling thread.
+template <class F>
+void parallel_ranges(int64_t n, F&& fn) {
+  cpu_set_t cs;
+  int64_t hw = sched_getaffinity(0, sizeof cs, &cs) == 0 ? CPU_COUNT(&cs) : 1;
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({hw, 64, n}));
+  if (nt <= 1) {
+    fn((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int64_t t = 1; t < nt; ++t) {
+    const int64_t b = n * t / nt, e = n * (t + 1) / nt;
+    try {
+      th.emplace_back([&fn, b, e] { fn(b, e); });
+    } catch (...) {
+      fn(b, e);
+    }
+  }
+  fn((int64_t)0, n / nt);
+  for (auto& x : th) x.join();
+}
 
 template <class T>
 std::vector<float> to_f32(const std::vector<T>& v) {
@@ -541,8 +571,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<double> h_hhg(3 * n_lanes, 0.0), h_hhe(3 * n_lanes, 0.0);
   std::vector<double> h_iinj(n_lanes, 0.0), h_thresh(n_lanes, 0.0);
   std::vector<int64_t> h_kon(n_lanes, 0), h_koff(n_lanes, 0);
-  std::vector<double> rhalf, gi_v, gax, cdt_v, dcc;
-  std::vector<double> h_pcv, h_pdg, h_pa, h_pvdt, h_psrc, vol, hx, gdx;
+  std::vector<double> h_pcv, h_pdg, h_pa, h_pvdt, h_psrc;
   std::vector<double> h_cadg, h_caa, h_cavdt, h_cavol;
   if (ca_stream >= 0) {
     h_cadg.assign(n_elem, 1.0);
@@ -558,13 +587,15 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     M->prp_vol.assign(n_elem, 0.0);
     M->prp_gsum.assign(n_elem, 0.0);
   }
-  for (int64_t L = 0; L < n_lanes; ++L) {
+  // cells are independent: groups of lanes in parallel
+  parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
+  std::vector<double> rhalf, gax, vol, hx, gdx;
+  for (int64_t L = g0 * kLanes; L < g1 * kLanes; ++L) {
     if (lane_gid[L] < 0) continue;
     const pa_cell& cl = cells[lane_gid[L]];
     const pa_morphology& g = morphs[cl.morph];
     const int n = g.n_cv;
     rhalf.assign(n, 0.0);
-    gi_v.assign(n, 0.0);
     gax.assign(n, 0.0);
     for (int i = 0; i < n; ++i) {
       const double Lc = g.length_um[i], dia = g.diam_um[i];
@@ -713,6 +744,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     h_koff[L] = cl.t_off > 1e15 ? INT64_MAX : std::llround(cl.t_off / dt);
     h_thresh[L] = cl.threshold;
   }
+  });
 
   // ---- branch tables of the wide cells ------------------------------------------
   // A branch is a run of rows i whose parent is i - 1 (rows are contiguous),
@@ -772,7 +804,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   M->conn_kind.assign(n_conn, 0);
   M->conn_weight.assign(n_conn, 0.0);
   M->conn_h0.assign(n_conn, 0.0);
-  std::vector<std::vector<SynRec>> per_lane(n_lanes * (size_t)std::max(n_streams, 1));
+  // the synapses of each (stream, lane) pair, by a counting sort: sl_ptr[q] ..
+  // sl_ptr[q + 1] in syn_rec, q = stream * n_lanes + lane
+  const size_t n_sl = (size_t)n_lanes * (size_t)std::max(n_streams, 1);
+  std::vector<int64_t> sl_ptr(n_sl + 1, 0);
   int64_t max_delay = 1, min_delay = INT64_MAX;
   int32_t max_dc = 0;
   std::vector<int64_t> n_out(n_cells + 1, 0);
@@ -803,11 +838,32 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     }
     if (P.dc_steps > max_dc) max_dc = P.dc_steps;
     const int64_t L = M->lane_of_gid[k.dst_gid];
-    per_lane[(size_t)s * n_lanes + L].push_back({c, k.dst_cv});
+    sl_ptr[(size_t)s * n_lanes + L + 1]++;
     M->conn_kind[c] = mechs[k.mech].kind;
     M->conn_weight[c] = k.weight;
     if (mechs[k.mech].kind == PA_MECH_STC) M->conn_h0[c] = mechs[k.mech].params[12];
   }
+  for (size_t q = 0; q < n_sl; ++q) sl_ptr[q + 1] += sl_ptr[q];
+  std::vector<SynRec> syn_rec(n_conn);
+  {
+    std::vector<int64_t> fill(sl_ptr.begin(), sl_ptr.end() - 1);
+    for (int64_t c = 0; c < n_conn; ++c) {
+      const size_t q = (size_t)mech_stream[conns[c].mech] * n_lanes +
+                       M->lane_of_gid[conns[c].dst_gid];
+      syn_rec[fill[q]++] = {c, conns[c].dst_cv};
+    }
+  }
+  // canonical order per lane: (CV, connection); groups in parallel
+  parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
+    for (int s = 0; s < n_streams; ++s)
+      for (int64_t L = g0 * kLanes; L < g1 * kLanes; ++L) {
+        const size_t q = (size_t)s * n_lanes + L;
+        std::sort(syn_rec.begin() + sl_ptr[q], syn_rec.begin() + sl_ptr[q + 1],
+                  [](const SynRec& x, const SynRec& y) {
+                    return x.cv != y.cv ? x.cv < y.cv : x.conn < y.conn;
+                  });
+      }
+  });
   int E = (int)std::min<int64_t>(min_delay == INT64_MAX ? max_e : min_delay, max_e);
   if (E < 1) E = 1;
   M->E = E;
@@ -824,11 +880,8 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     for (int64_t g = 0; g < n_groups; ++g) {
       size_t mx = 0;
       for (int l = 0; l < kLanes; ++l) {
-        auto& v = per_lane[(size_t)s * n_lanes + g * kLanes + l];
-        std::sort(v.begin(), v.end(), [](const SynRec& x, const SynRec& y) {
-          return x.cv != y.cv ? x.cv < y.cv : x.conn < y.conn;
-        });
-        mx = std::max(mx, v.size());
+        const size_t q = (size_t)s * n_lanes + g * kLanes + l;
+        mx = std::max(mx, (size_t)(sl_ptr[q + 1] - sl_ptr[q]));
       }
       const int64_t rows = g < n_narrow ? (int64_t)mx : ((int64_t)mx + kLanes - 1) / kLanes;
       if ((int64_t)s_sbase[s][g] + rows > (1LL << 26))
@@ -846,7 +899,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // synapses of a stream (canonical order: mechanism, CV, connection).  Flags:
   // bit 0 "first on this CV over all streams" (the run starts from 0), bit 1 "run
   // starts", bit 2 "run ends" (store the sums).  cvf = (cv << 3) | flags.
-  for (int64_t L = 0; L < n_lanes; ++L) {
+  // lanes write disjoint elements and connections: groups in parallel
+  std::vector<int64_t> n_static(n_groups, 0);
+  parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
+  for (int64_t L = g0 * kLanes; L < g1 * kLanes; ++L) {
     if (lane_gid[L] < 0) continue;
     const int ncell = M->cell_ncv[lane_gid[L]];
     std::vector<char> touched(ncell, 0);
@@ -854,13 +910,15 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     for (int s = 0; s < n_streams; ++s) {
       const int m = stream_mech[s];
       const double* p = mechs[m].params;
-      auto& v = per_lane[(size_t)s * n_lanes + L];
-      for (size_t j = 0; j < v.size(); ++j) {
+      const size_t q = (size_t)s * n_lanes + L;
+      const SynRec* v = syn_rec.data() + sl_ptr[q];
+      const size_t nv = (size_t)(sl_ptr[q + 1] - sl_ptr[q]);
+      for (size_t j = 0; j < nv; ++j) {
         const int64_t e = g < n_narrow ? ((int64_t)s_sbase[s][g] + (int64_t)j) * kLanes + l
                                        : ((int64_t)s_sbase[s][g] << 5) + (int64_t)j;
         const int cv = v[j].cv;
         const bool start = j == 0 || v[j - 1].cv != cv;
-        const bool end = j + 1 == v.size() || v[j + 1].cv != cv;
+        const bool end = j + 1 == nv || v[j + 1].cv != cv;
         const bool first = !touched[cv];
         s_cvf[s][e] = (cv << 3) | (first ? 1 : 0) | (start ? 2 : 0) | (end ? 4 : 0);
         touched[cv] = 1;
@@ -888,10 +946,12 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     for (int i = 0; i < ncell; ++i) dyn[i] = touched[i] || i == 0;
     for (int i = ncell - 1; i >= 1; --i)
       if (dyn[i]) dyn[gm.parent[i]] = 1;
-    for (int i = 1; i < ncell; ++i) M->n_static_cv += dyn[i] ? 0 : 1;
+    for (int i = 1; i < ncell; ++i) n_static[g] += dyn[i] ? 0 : 1;
   }
-  per_lane.clear();
-  per_lane.shrink_to_fit();
+  });
+  for (int64_t g = 0; g < n_groups; ++g) M->n_static_cv += n_static[g];
+  syn_rec.clear();
+  syn_rec.shrink_to_fit();
 
   // Poisson drives
   std::vector<int32_t> ps_stream, ps_dc;
