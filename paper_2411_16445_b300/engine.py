@@ -39,6 +39,36 @@ class Morph(C.Structure):
                 ("diam_um", C.c_void_p), ("region", C.c_void_p)]
 
 
+# the same layout as Morph, for building the whole table with numpy
+MORPH_DTYPE = np.dtype({"names": [f[0] for f in Morph._fields_],
+                        "formats": ["<i4", "<u8", "<u8", "<u8", "<u8"],
+                        "offsets": [getattr(Morph, f[0]).offset for f in Morph._fields_],
+                        "itemsize": C.sizeof(Morph)})
+
+
+def _morph_table(morphs, keep):
+    """pa_morphology descriptors of every morphology, pointing into four
+    concatenated arrays (appended to keep, which must outlive the call)."""
+    tab = np.zeros(max(len(morphs), 1), MORPH_DTYPE)
+    if not morphs:
+        return tab
+    k = len(morphs)
+    off = np.zeros(k, np.int64)
+    for f, src, dt in (("parent", "parent", np.int32), ("length_um", "length", np.float64),
+                       ("diam_um", "diam", np.float64), ("region", "region", np.int32)):
+        parts = [getattr(m, src) for m in morphs]
+        n = np.fromiter(map(len, parts), np.int64, k)
+        if f == "parent":
+            tab["n_cv"] = n
+            np.cumsum(n[:-1], out=off[1:])
+        elif not np.array_equal(n, tab["n_cv"]):
+            raise ValueError(f"morphology {src} arrays must have n_cv entries")
+        a = np.concatenate(parts + [np.zeros(1, dt)], dtype=dt)
+        keep.append(a)
+        tab[f] = a.ctypes.data + a.itemsize * off
+    return tab
+
+
 class Mech(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_params", C.c_int32), ("params", C.c_void_p)]
 
@@ -165,14 +195,7 @@ class Model:
                        ("t_on", net.cell_ton), ("t_off", net.cell_toff),
                        ("v_init", net.cell_vinit), ("threshold", net.cell_thresh)):
             cells[f] = src
-        morphs = (Morph * max(len(net.morphs), 1))()
-        for i, m in enumerate(net.morphs):
-            arrs = (np.ascontiguousarray(m.parent, np.int32),
-                    np.ascontiguousarray(m.length, np.float64),
-                    np.ascontiguousarray(m.diam, np.float64),
-                    np.ascontiguousarray(m.region, np.int32))
-            keep.append(arrs)
-            morphs[i] = Morph(m.n_cv, *[a.ctypes.data for a in arrs])
+        morphs = _morph_table(net.morphs, keep)
         mechs = (Mech * max(len(net.mech_params), 1))()
         for i, (k, p) in enumerate(zip(net.mech_kind, net.mech_params)):
             pa = np.ascontiguousarray(p, np.float64)
@@ -195,7 +218,7 @@ class Model:
                       probe_capacity=probe_capacity, spike_capacity=spike_capacity,
                       max_epoch_steps=max_epoch_steps, flags=flags)
         h = C.c_void_p()
-        _check(L.pa_build_model(_ptr(cells), net.n_cells, C.cast(morphs, C.c_void_p),
+        _check(L.pa_build_model(_ptr(cells), net.n_cells, _ptr(morphs),
                                 len(net.morphs), C.cast(mechs, C.c_void_p),
                                 len(net.mech_params), _ptr(conns), net.n_conn,
                                 C.byref(opt), C.byref(h)))
