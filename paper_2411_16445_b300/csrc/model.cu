@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -177,14 +178,22 @@ struct SynRec {
 };
 
 // Runs fn(begin, end) over contiguous pieces of [0, n) on the host cores this
-// process may use (at most 64 threads).  The model builder's per-group loops
-// write disjoint elements, so the result does not depend on the thread count.
-// A thread that cannot be started has its piece run on the calling thread.
+// process may use (at most 64 threads), shared among the builds that run at
+// the same time (a server builds several models at once).  The model builder's
+// per-group loops write disjoint elements, so the result does not depend on the
+// thread count.  A thread that cannot be started has its piece run on the
+// calling thread.
+std::atomic<int> g_parallel_regions{0};
+
 template <class F>
 void parallel_ranges(int64_t n, F&& fn) {
   cpu_set_t cs;
-  int64_t hw = sched_getaffinity(0, sizeof cs, &cs) == 0 ? CPU_COUNT(&cs) : 1;
-  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({hw, 64, n}));
+  const int64_t hw = sched_getaffinity(0, sizeof cs, &cs) == 0 ? CPU_COUNT(&cs) : 1;
+  const int64_t active = g_parallel_regions.fetch_add(1) + 1;
+  struct Leave {
+    ~Leave() { g_parallel_regions.fetch_sub(1); }
+  } leave;
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({hw / active, 64, n}));
   if (nt <= 1) {
     fn((int64_t)0, n);
     return;
