@@ -12,9 +12,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include <sched.h>
@@ -212,8 +214,32 @@ void parallel_ranges(int64_t n, F&& fn) {
   for (auto& x : th) x.join();
 }
 
+// An allocator whose value-less construct leaves elements default-initialised
+// (uninitialised for arithmetic types): large host arrays are then first
+// touched, and filled, by the builder threads that own their ranges.
 template <class T>
-std::vector<float> to_f32(const std::vector<T>& v) {
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new ((void*)p) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new ((void*)p) U(std::forward<Args>(args)...);
+  }
+};
+template <class T>
+using HostVec = std::vector<T, NoInitAlloc<T>>;
+
+template <class V>
+std::vector<float> to_f32(const V& v) {
   std::vector<float> o(v.size());
   for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
   return o;
@@ -564,17 +590,17 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   };
 
   // ---- CV discretisation (a CV is a cylinder; Eq. cable) -----------------------
-  std::vector<double> h_cdt(n_elem, 0.0), h_dc(n_elem, 1.0), h_em(n_elem, 0.0),
-      h_a(n_elem, 0.0), h_V(n_elem, 0.0);
-  std::vector<int16_t> h_par, h_och, h_ocn;
-  std::vector<uint8_t> h_tf;
-  std::vector<double> h_aoch;
+  // (filled group by group in the parallel loop below)
+  HostVec<double> h_cdt(n_elem), h_dc(n_elem), h_em(n_elem), h_a(n_elem), h_V(n_elem);
+  HostVec<int16_t> h_par, h_och, h_ocn;
+  HostVec<uint8_t> h_tf;
+  HostVec<double> h_aoch;
   if (M->tree) {
-    h_par.assign(n_elem, -1);
-    h_och.assign(n_elem, -1);
-    h_ocn.assign(n_elem, -1);
-    h_tf.assign(n_elem, 0);
-    h_aoch.assign(n_elem, 0.0);
+    h_par.resize(n_elem);
+    h_och.resize(n_elem);
+    h_ocn.resize(n_elem);
+    h_tf.resize(n_elem);
+    h_aoch.resize(n_elem);
   }
   std::vector<uint8_t> h_is_hh(n_lanes, 0);
   std::vector<double> h_hhg(3 * n_lanes, 0.0), h_hhe(3 * n_lanes, 0.0);
@@ -599,7 +625,25 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // cells are independent: groups of lanes in parallel
   parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
   std::vector<double> rhalf, gax, vol, hx, gdx;
-  for (int64_t L = g0 * kLanes; L < g1 * kLanes; ++L) {
+  for (int64_t gi = g0; gi < g1; ++gi) {
+  {
+    // the group's elements (one contiguous range) take their initial values
+    const int64_t e0 = (int64_t)M->row_base[gi] * kLanes;
+    const int64_t e1 = (int64_t)M->row_base[gi + 1] * kLanes;
+    std::fill(h_cdt.begin() + e0, h_cdt.begin() + e1, 0.0);
+    std::fill(h_dc.begin() + e0, h_dc.begin() + e1, 1.0);
+    std::fill(h_em.begin() + e0, h_em.begin() + e1, 0.0);
+    std::fill(h_a.begin() + e0, h_a.begin() + e1, 0.0);
+    std::fill(h_V.begin() + e0, h_V.begin() + e1, 0.0);
+    if (M->tree) {
+      std::fill(h_par.begin() + e0, h_par.begin() + e1, (int16_t)-1);
+      std::fill(h_och.begin() + e0, h_och.begin() + e1, (int16_t)-1);
+      std::fill(h_ocn.begin() + e0, h_ocn.begin() + e1, (int16_t)-1);
+      std::fill(h_tf.begin() + e0, h_tf.begin() + e1, (uint8_t)0);
+      std::fill(h_aoch.begin() + e0, h_aoch.begin() + e1, 0.0);
+    }
+  }
+  for (int64_t L = gi * kLanes; L < (gi + 1) * kLanes; ++L) {
     if (lane_gid[L] < 0) continue;
     const pa_cell& cl = cells[lane_gid[L]];
     const pa_morphology& g = morphs[cl.morph];
@@ -753,6 +797,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     h_koff[L] = cl.t_off > 1e15 ? INT64_MAX : std::llround(cl.t_off / dt);
     h_thresh[L] = cl.threshold;
   }
+  }
   });
 
   // ---- branch tables of the wide cells ------------------------------------------
@@ -821,46 +866,97 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   int32_t max_dc = 0;
   std::vector<int64_t> n_out(n_cells + 1, 0);
   std::vector<int32_t> conn_D(n_conn, 0);
-  for (int64_t c = 0; c < n_conn; ++c) {
-    const pa_connection& k = conns[c];
-    if (k.dst_gid < 0 || k.dst_gid >= n_cells)
-      return set_err(PA_ERR_ARG, "connection %lld: bad dst_gid", (long long)c);
-    if (k.dst_cv < 0 || k.dst_cv >= M->cell_ncv[k.dst_gid])
-      return set_err(PA_ERR_ARG, "connection %lld: bad dst_cv", (long long)c);
-    if (!std::isfinite(k.weight)) return set_err(PA_ERR_ARG, "connection %lld: bad weight", (long long)c);
-    const int s = mech_stream[k.mech];
-    const StreamParams& P = M->sp[s];
-    if (k.src_gid == PA_SRC_POISSON) {
-      const double x = ((k.rate_hz * dt) * 1e-3) * 4294967296.0;
-      if (!(x >= 0) || x >= 4294967296.0)
-        return set_err(PA_ERR_ARG, "connection %lld: rate_hz * dt out of range", (long long)c);
-    } else {
-      if (k.src_gid < 0 || k.src_gid >= n_cells)
-        return set_err(PA_ERR_ARG, "connection %lld: bad src_gid", (long long)c);
-      const int64_t D = std::llround(k.delay_ms / dt);
-      if (!(D >= 1) || D > (1 << 30))
-        return set_err(PA_ERR_ARG, "connection %lld: delay must be at least one step", (long long)c);
-      conn_D[c] = (int32_t)D;
-      max_delay = std::max(max_delay, D);
-      min_delay = std::min(min_delay, D);
-      n_out[k.src_gid + 1]++;
+  // validation and the per-connection tables over fixed pieces of the
+  // connection list, in parallel; the lowest bad connection is reported
+  {
+    constexpr int64_t kPieces = 64;
+    static const char* const kWhy[] = {"", "bad dst_gid", "bad dst_cv", "bad weight",
+                                       "rate_hz * dt out of range", "bad src_gid",
+                                       "delay must be at least one step"};
+    struct PieceOut {
+      int64_t bad = -1, max_d = 1, min_d = INT64_MAX;
+      int why = 0;
+      int32_t max_dc = 0;
+    };
+    std::vector<PieceOut> po(kPieces);
+    parallel_ranges(kPieces, [&](int64_t p0, int64_t p1) {
+      for (int64_t p = p0; p < p1; ++p) {
+        PieceOut& o = po[p];
+        for (int64_t c = n_conn * p / kPieces; c < n_conn * (p + 1) / kPieces; ++c) {
+          const pa_connection& k = conns[c];
+          int why = 0;
+          if (k.dst_gid < 0 || k.dst_gid >= n_cells) why = 1;
+          else if (k.dst_cv < 0 || k.dst_cv >= M->cell_ncv[k.dst_gid]) why = 2;
+          else if (!std::isfinite(k.weight)) why = 3;
+          else if (k.src_gid == PA_SRC_POISSON) {
+            const double x = ((k.rate_hz * dt) * 1e-3) * 4294967296.0;
+            if (!(x >= 0) || x >= 4294967296.0) why = 4;
+          } else if (k.src_gid < 0 || k.src_gid >= n_cells) {
+            why = 5;
+          } else {
+            const int64_t D = std::llround(k.delay_ms / dt);
+            if (!(D >= 1) || D > (1 << 30)) {
+              why = 6;
+            } else {
+              conn_D[c] = (int32_t)D;
+              o.max_d = std::max(o.max_d, D);
+              o.min_d = std::min(o.min_d, D);
+            }
+          }
+          if (why) {
+            o.bad = c;
+            o.why = why;
+            break;
+          }
+          const int s = mech_stream[k.mech];
+          if (M->sp[s].dc_steps > o.max_dc) o.max_dc = M->sp[s].dc_steps;
+          M->conn_kind[c] = mechs[k.mech].kind;
+          M->conn_weight[c] = k.weight;
+          if (mechs[k.mech].kind == PA_MECH_STC) M->conn_h0[c] = mechs[k.mech].params[12];
+        }
+      }
+    });
+    for (const PieceOut& o : po)
+      if (o.bad >= 0) return set_err(PA_ERR_ARG, "connection %lld: %s", (long long)o.bad, kWhy[o.why]);
+    for (const PieceOut& o : po) {
+      max_delay = std::max(max_delay, o.max_d);
+      min_delay = std::min(min_delay, o.min_d);
+      max_dc = std::max(max_dc, o.max_dc);
     }
-    if (P.dc_steps > max_dc) max_dc = P.dc_steps;
-    const int64_t L = M->lane_of_gid[k.dst_gid];
-    sl_ptr[(size_t)s * n_lanes + L + 1]++;
-    M->conn_kind[c] = mechs[k.mech].kind;
-    M->conn_weight[c] = k.weight;
-    if (mechs[k.mech].kind == PA_MECH_STC) M->conn_h0[c] = mechs[k.mech].params[12];
   }
-  for (size_t q = 0; q < n_sl; ++q) sl_ptr[q + 1] += sl_ptr[q];
+  for (int64_t c = 0; c < n_conn; ++c)
+    if (conns[c].src_gid != PA_SRC_POISSON) n_out[conns[c].src_gid + 1]++;
+  // counting sort of the connections by (stream, lane): per piece of the
+  // connection list a count per bucket, then each piece fills its own slots
+  // (within a bucket, connections stay in list order)
   std::vector<SynRec> syn_rec(n_conn);
   {
-    std::vector<int64_t> fill(sl_ptr.begin(), sl_ptr.end() - 1);
-    for (int64_t c = 0; c < n_conn; ++c) {
-      const size_t q = (size_t)mech_stream[conns[c].mech] * n_lanes +
-                       M->lane_of_gid[conns[c].dst_gid];
-      syn_rec[fill[q]++] = {c, conns[c].dst_cv};
+    int64_t np = 16;
+    while (np > 1 && (double)np * (double)n_sl * 8.0 > 512.0 * 1024 * 1024) np /= 2;
+    std::vector<int64_t> start((size_t)np * n_sl, 0);
+    auto bucket = [&](int64_t c) {
+      return (size_t)mech_stream[conns[c].mech] * n_lanes + M->lane_of_gid[conns[c].dst_gid];
+    };
+    parallel_ranges(np, [&](int64_t p0, int64_t p1) {
+      for (int64_t p = p0; p < p1; ++p)
+        for (int64_t c = n_conn * p / np; c < n_conn * (p + 1) / np; ++c)
+          start[(size_t)p * n_sl + bucket(c)]++;
+    });
+    int64_t run = 0;
+    for (size_t q = 0; q < n_sl; ++q) {
+      sl_ptr[q] = run;
+      for (int64_t p = 0; p < np; ++p) {
+        const int64_t k = start[(size_t)p * n_sl + q];
+        start[(size_t)p * n_sl + q] = run;
+        run += k;
+      }
     }
+    sl_ptr[n_sl] = run;
+    parallel_ranges(np, [&](int64_t p0, int64_t p1) {
+      for (int64_t p = p0; p < p1; ++p)
+        for (int64_t c = n_conn * p / np; c < n_conn * (p + 1) / np; ++c)
+          syn_rec[start[(size_t)p * n_sl + bucket(c)]++] = {c, conns[c].dst_cv};
+    });
   }
   // canonical order per lane: (CV, connection); groups in parallel
   parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
@@ -880,9 +976,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
 
   // per stream: canonical order (CV, connection) per lane, padded rows per group
   std::vector<std::vector<int32_t>> s_sbase(n_streams);
-  std::vector<std::vector<int32_t>> s_cvf(n_streams);
-  std::vector<std::vector<double>> s_weight(n_streams), s_w(n_streams);
-  std::vector<std::vector<int32_t>> s_nid(n_streams);   // noise source ids (noisy streams)
+  // (filled group by group in the parallel loop below)
+  std::vector<HostVec<int32_t>> s_cvf(n_streams);
+  std::vector<HostVec<double>> s_weight(n_streams), s_w(n_streams);
+  std::vector<HostVec<int32_t>> s_nid(n_streams);   // noise source ids (noisy streams)
   std::vector<uint8_t> h_has_stc(n_lanes, 0), h_has_ca(n_lanes, 0);
   for (int s = 0; s < n_streams; ++s) {
     s_sbase[s].assign(n_groups + 1, 0);
@@ -899,10 +996,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     }
     const int64_t ne = (int64_t)s_sbase[s][n_groups] * kLanes;
     M->s_nelem[s] = ne;
-    s_cvf[s].assign(ne, -1);
-    s_weight[s].assign(ne, 0.0);
-    s_w[s].assign(ne, 0.0);
-    if (M->sp[s].sigma > 0.0) s_nid[s].assign(ne, 0);
+    s_cvf[s].resize(ne);
+    s_weight[s].resize(ne);
+    s_w[s].resize(ne);
+    if (M->sp[s].sigma > 0.0) s_nid[s].resize(ne);
   }
   // Per-CV synaptic sums are accumulated in registers over each run of same-CV
   // synapses of a stream (canonical order: mechanism, CV, connection).  Flags:
@@ -911,7 +1008,16 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // lanes write disjoint elements and connections: groups in parallel
   std::vector<int64_t> n_static(n_groups, 0);
   parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
-  for (int64_t L = g0 * kLanes; L < g1 * kLanes; ++L) {
+  for (int64_t gi = g0; gi < g1; ++gi) {
+  for (int s = 0; s < n_streams; ++s) {
+    // the group's synapse slots (one contiguous range) take their initial values
+    const int64_t e0 = (int64_t)s_sbase[s][gi] * kLanes, e1 = (int64_t)s_sbase[s][gi + 1] * kLanes;
+    std::fill(s_cvf[s].begin() + e0, s_cvf[s].begin() + e1, -1);
+    std::fill(s_weight[s].begin() + e0, s_weight[s].begin() + e1, 0.0);
+    std::fill(s_w[s].begin() + e0, s_w[s].begin() + e1, 0.0);
+    if (!s_nid[s].empty()) std::fill(s_nid[s].begin() + e0, s_nid[s].begin() + e1, 0);
+  }
+  for (int64_t L = gi * kLanes; L < (gi + 1) * kLanes; ++L) {
     if (lane_gid[L] < 0) continue;
     const int ncell = M->cell_ncv[lane_gid[L]];
     std::vector<char> touched(ncell, 0);
@@ -956,6 +1062,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     for (int i = ncell - 1; i >= 1; --i)
       if (dyn[i]) dyn[gm.parent[i]] = 1;
     for (int i = 1; i < ncell; ++i) n_static[g] += dyn[i] ? 0 : 1;
+  }
   }
   });
   for (int64_t g = 0; g < n_groups; ++g) M->n_static_cv += n_static[g];
