@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+from concurrent.futures import ThreadPoolExecutor
 from typing import Optional, Sequence, Tuple
 
 import numpy as np
@@ -67,6 +68,26 @@ def _morph_table(morphs, keep):
         keep.append(a)
         tab[f] = a.ctypes.data + a.itemsize * off
     return tab
+
+
+def _pack(dtype, n: int, columns: dict) -> np.ndarray:
+    """A structured array of n records from per-field columns.  Large tables are
+    filled in row chunks on a few threads (numpy copies release the GIL)."""
+    out = np.empty(n, dtype)
+    chunk = 1 << 20
+    if n <= 2 * chunk:
+        for f, col in columns.items():
+            out[f] = col
+        return out
+
+    def fill(i):
+        sl = slice(i, min(i + chunk, n))
+        for f, col in columns.items():
+            out[f][sl] = np.asarray(col)[sl]
+
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        list(ex.map(fill, range(0, n, chunk)))
+    return out
 
 
 class Mech(C.Structure):
@@ -201,12 +222,10 @@ class Model:
             pa = np.ascontiguousarray(p, np.float64)
             keep.append(pa)
             mechs[i] = Mech(int(k), len(pa), pa.ctypes.data)
-        conns = np.zeros(net.n_conn, CONN_DTYPE)
-        conns["src_gid"], conns["dst_gid"], conns["dst_cv"], conns["mech"] = (
-            net.conn_src, net.conn_dst, net.conn_cv, net.conn_mech)
-        conns["weight"], conns["delay_ms"], conns["rate_hz"] = (
-            net.conn_weight, net.conn_delay, net.conn_rate)
-        conns["poisson_id"] = net.conn_pid
+        conns = _pack(CONN_DTYPE, net.n_conn, {
+            "src_gid": net.conn_src, "dst_gid": net.conn_dst, "dst_cv": net.conn_cv,
+            "mech": net.conn_mech, "weight": net.conn_weight, "delay_ms": net.conn_delay,
+            "rate_hz": net.conn_rate, "poisson_id": net.conn_pid})
         pg = np.ascontiguousarray([p[0] for p in probes], np.int32)
         pc = np.ascontiguousarray([p[1] for p in probes], np.int32)
         if stream is None:
