@@ -225,6 +225,12 @@ typedef struct {
  * force every cell into one bin. */
 #define PA_FLAG_NARROW_ONLY 16
 #define PA_FLAG_WIDE_ALL 32
+/* pa_options.flags: at most n host threads (1 <= n <= 63) for this model's
+ * build; 0 (the default): the cores the process may use, up to 64, shared
+ * among builds running at the same time.  A server that builds models while
+ * it launches other models' work keeps cores free this way.  The model does
+ * not depend on the thread count. */
+#define PA_FLAG_BUILD_THREADS(n) (((n) & 0x3F) << 12)
 
 typedef struct {
   int64_t epoch_launches;   /* epoch (time-step) kernel launches since the last reset */
@@ -251,7 +257,11 @@ typedef struct {
  * area pi d L, C = c_m A, axial conductance of two half-cylinders in series,
  * Eq. cable), lays the state out on the device and uploads it.  On success
  * *out receives the model.  Errors: PA_ERR_ARG (message names the offending
- * element), PA_ERR_OOM, PA_ERR_CUDA. */
+ * element; of several bad connections, the lowest-indexed), PA_ERR_OOM,
+ * PA_ERR_CUDA.  The host layout runs on the cores the calling process may use
+ * (at most 64 threads, shared among builds that run at the same time); the
+ * model does not depend on the thread count.  The descriptor arrays are only
+ * read, and only during the call. */
 int pa_build_model(const pa_cell* cells, int64_t n_cells, const pa_morphology* morphs,
                    int64_t n_morph, const pa_mechanism* mechs, int64_t n_mech,
                    const pa_connection* conns, int64_t n_conn, const pa_options* opt,

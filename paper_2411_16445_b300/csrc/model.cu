@@ -186,6 +186,7 @@ struct SynRec {
 // thread count.  A thread that cannot be started has its piece run on the
 // calling thread.
 std::atomic<int> g_parallel_regions{0};
+thread_local int64_t tl_build_threads = 0;  // the calling build's cap (0: none)
 
 template <class F>
 void parallel_ranges(int64_t n, F&& fn) {
@@ -195,7 +196,8 @@ void parallel_ranges(int64_t n, F&& fn) {
   struct Leave {
     ~Leave() { g_parallel_regions.fetch_sub(1); }
   } leave;
-  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({hw / active, 64, n}));
+  const int64_t cap = tl_build_threads > 0 ? tl_build_threads : 64;
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({hw / active, cap, n}));
   if (nt <= 1) {
     fn((int64_t)0, n);
     return;
@@ -328,6 +330,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   if (opt->precision != PA_FP64 && opt->precision != PA_MIXED)
     return set_err(PA_ERR_ARG, "precision must be PA_FP64 or PA_MIXED");
   const bool mixed = opt->precision == PA_MIXED;
+  tl_build_threads = (opt->flags >> 12) & 0x3F;
   int max_e = opt->max_epoch_steps > 0 ? opt->max_epoch_steps : 64;
   if (max_e > 64) return set_err(PA_ERR_ARG, "max_epoch_steps must be <= 64");
 

@@ -113,6 +113,11 @@ FLAG_AUTOTUNE = 2
 FLAG_NO_GRAPHS = 8
 FLAG_NARROW_ONLY = 16
 FLAG_WIDE_ALL = 32
+
+
+def FLAG_BUILD_THREADS(n: int) -> int:
+    """at most n host threads for the model's build (0: automatic)"""
+    return (int(n) & 0x3F) << 12
 N_SHAPES = 6
 
 

@@ -90,7 +90,7 @@ class _Resident:
 class Server:
     def __init__(self, hbm_budget_bytes: int = 64 << 30, quantum_cu: float = 1e6,
                  precision: int = E.PA_MIXED, device: int = 0, builders: int = 4,
-                 max_resident: int = 512):
+                 max_resident: int = 512, build_threads: int = 1):
         import torch
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
@@ -98,6 +98,9 @@ class Server:
         self.precision = precision
         self.device = device
         self.max_resident = max_resident
+        # host threads per model build (0: automatic); the builds overlap with
+        # the scheduling loop that keeps the resident jobs' work launched
+        self.build_threads = build_threads
         self.pool = ThreadPoolExecutor(max_workers=builders)
         torch.cuda.set_device(device)
 
@@ -108,7 +111,8 @@ class Server:
                             spec["dend_diam_um"], spec["seed"], dt=spec["dt"])
         stream = torch.cuda.Stream(device=self.device)
         m = E.Model(net, precision=self.precision, device=self.device,
-                    stream=E.C.c_void_p(stream.cuda_stream))
+                    stream=E.C.c_void_p(stream.cuda_stream),
+                    flags=E.FLAG_BUILD_THREADS(self.build_threads))
         return net, m, stream
 
     def run(self, trace: List[dict], time_scale: float = 1.0) -> Dict:
