@@ -31,8 +31,9 @@
  *
  * Readings where the paper is silent are listed in the repository's design
  * notes; the ones that fix arithmetic are repeated next to the code.
- * Parity: the HH channel kinetics are "parity unpinned" beyond the textbook
- * resting potential and firing-rate checks of the test-suite; every other
+ * Parity: the HH channel kinetics are "parity unpinned" beyond the published
+ * resting gate values, the textbook resting potential and the firing-rate
+ * checks of the test-suite; every other
  * function here is pinned by a closed form, a brute-force or library solve, or
  * an invariant (tests/test_oracle_pins.py).
  */

@@ -192,6 +192,24 @@ def test_hh_rest_and_textbook_firing():
     assert len(o.spikes()[0]) <= 1
 
 
+def test_hh_resting_gates_match_the_published_values():
+    """A cell initialised at -65 mV starts its HH gates at their steady states;
+    they equal the published resting values of the textbook model
+    (tests/golden/hh_resting_gates.txt) to the printed digits.  The three values
+    involve all six rate functions at rest, so a dropped term, a wrong sign or a
+    wrong constant in any of them fails here."""
+    want = {}
+    for line in open(os.path.join(GOLDEN, "hh_resting_gates.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            want[k] = float(v)
+    net = hh_point_net(0.0)
+    net.cell_vinit[:] = -65.0
+    g = O.Oracle(net).gates()[0]
+    for i, k in enumerate("mhn"):
+        assert abs(g[i] - want[k]) < 5e-7, (k, g[i], want[k])
+
+
 def test_vtrap_removable_singularity():
     am, _, _, _, an, _ = O.hh_rates(-40.0)
     assert am == 1.0
