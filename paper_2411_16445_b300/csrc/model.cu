@@ -12,7 +12,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -184,7 +186,8 @@ struct SynRec {
 // the same time (a server builds several models at once).  The model builder's
 // per-group loops write disjoint elements, so the result does not depend on the
 // thread count.  A thread that cannot be started has its piece run on the
-// calling thread.
+// calling thread.  An exception in any piece (an allocation failure) is
+// rethrown on the calling thread once every thread has joined.
 std::atomic<int> g_parallel_regions{0};
 thread_local int64_t tl_build_threads = 0;  // the calling build's cap (0: none)
 
@@ -202,18 +205,29 @@ void parallel_ranges(int64_t n, F&& fn) {
     fn((int64_t)0, n);
     return;
   }
+  std::exception_ptr err;
+  std::mutex mu;
+  auto run = [&](int64_t b, int64_t e) {
+    try {
+      fn(b, e);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!err) err = std::current_exception();
+    }
+  };
   std::vector<std::thread> th;
   th.reserve(nt);
   for (int64_t t = 1; t < nt; ++t) {
     const int64_t b = n * t / nt, e = n * (t + 1) / nt;
     try {
-      th.emplace_back([&fn, b, e] { fn(b, e); });
+      th.emplace_back([&run, b, e] { run(b, e); });
     } catch (...) {
-      fn(b, e);
+      run(b, e);
     }
   }
-  fn((int64_t)0, n / nt);
+  run((int64_t)0, n / nt);
   for (auto& x : th) x.join();
+  if (err) std::rethrow_exception(err);
 }
 
 // An allocator whose value-less construct leaves elements default-initialised
