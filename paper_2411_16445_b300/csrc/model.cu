@@ -230,6 +230,47 @@ void parallel_ranges(int64_t n, F&& fn) {
   if (err) std::rethrow_exception(err);
 }
 
+// Stable counting sort of items 0 .. n-1 into n_buckets buckets: bucket(i)
+// gives an item's bucket, or a negative value to leave it out.  ptr receives
+// the n_buckets + 1 bucket starts, ready(total) is called with the number of
+// kept items, and place(i, slot) is then called once per kept item, the slots
+// of a bucket following the item order.  Fixed pieces of the
+// items are counted and placed in parallel, so the result does not depend on
+// the thread count.
+template <class B, class R, class P>
+void bucket_scatter(int64_t n, int64_t n_buckets, B&& bucket, std::vector<int64_t>& ptr,
+                    R&& ready, P&& place) {
+  int64_t np = n < (1 << 16) ? 1 : 16;
+  while (np > 1 && (double)np * (double)n_buckets * 8.0 > 512.0 * 1024 * 1024) np /= 2;
+  std::vector<int64_t> start((size_t)np * (size_t)n_buckets, 0);
+  parallel_ranges(np, [&](int64_t p0, int64_t p1) {
+    for (int64_t p = p0; p < p1; ++p)
+      for (int64_t i = n * p / np; i < n * (p + 1) / np; ++i) {
+        const int64_t q = bucket(i);
+        if (q >= 0) start[(size_t)p * n_buckets + q]++;
+      }
+  });
+  ptr.assign((size_t)n_buckets + 1, 0);
+  int64_t run = 0;
+  for (int64_t q = 0; q < n_buckets; ++q) {
+    ptr[q] = run;
+    for (int64_t p = 0; p < np; ++p) {
+      const int64_t k = start[(size_t)p * n_buckets + q];
+      start[(size_t)p * n_buckets + q] = run;
+      run += k;
+    }
+  }
+  ptr[n_buckets] = run;
+  ready(run);
+  parallel_ranges(np, [&](int64_t p0, int64_t p1) {
+    for (int64_t p = p0; p < p1; ++p)
+      for (int64_t i = n * p / np; i < n * (p + 1) / np; ++i) {
+        const int64_t q = bucket(i);
+        if (q >= 0) place(i, start[(size_t)p * n_buckets + q]++);
+      }
+  });
+}
+
 // An allocator whose value-less construct leaves elements default-initialised
 // (uninitialised for arithmetic types): large host arrays are then first
 // touched, and filled, by the builder threads that own their ranges.
@@ -486,43 +527,94 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   M->n_streams = n_streams;
 
   // ---- morphologies and cells -------------------------------------------------
-  for (int64_t mo = 0; mo < n_morph; ++mo) {
-    const pa_morphology& g = morphs[mo];
-    if (g.n_cv < 1 || g.n_cv > 32767)
-      return set_err(PA_ERR_ARG, "morphology %lld: n_cv must be in [1, 32767]", (long long)mo);
-    if (!g.parent || !g.length_um || !g.diam_um || !g.region)
-      return set_err(PA_ERR_ARG, "morphology %lld: NULL array", (long long)mo);
-    for (int i = 0; i < g.n_cv; ++i) {
-      int p = g.parent[i];
-      if ((i == 0 && p != -1) || (i > 0 && (p < 0 || p >= i)))
-        return set_err(PA_ERR_ARG, "morphology %lld: parent[%d] = %d invalid", (long long)mo, i, p);
-      if (!(g.length_um[i] > 0) || !(g.diam_um[i] > 0) || !std::isfinite(g.length_um[i]) ||
-          !std::isfinite(g.diam_um[i]))
-        return set_err(PA_ERR_ARG, "morphology %lld: CV %d has non-positive length/diameter", (long long)mo, i);
-      if (i > 0 && p != i - 1) M->tree = true;
-    }
-  }
-  M->cell_ncv.resize(n_cells);
-  M->cell_cv_off.resize(n_cells + 1, 0);
-  for (int64_t c = 0; c < n_cells; ++c) {
-    const pa_cell& cl = cells[c];
-    if (cl.morph < 0 || cl.morph >= n_morph)
-      return set_err(PA_ERR_ARG, "cell %lld: bad morphology index", (long long)c);
-    for (int which = 0; which < 2; ++which) {
-      int m = which == 0 ? cl.soma_mech : cl.dend_mech;
-      if (m < 0 || m >= n_mech || (mechs[m].kind != PA_MECH_PAS && mechs[m].kind != PA_MECH_HH))
-        return set_err(PA_ERR_ARG, "cell %lld: soma/dendrite mechanism must be pas or hh", (long long)c);
-    }
-    const pa_morphology& g = morphs[cl.morph];
-    for (int i = 0; i < g.n_cv; ++i) {
-      int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
-      if (mechs[m].kind == PA_MECH_HH && i != 0)
-        return set_err(PA_ERR_ARG, "cell %lld: HH is supported on the soma CV (CV 0) only", (long long)c);
-    }
-    if (!(cl.cm > 0) || !(cl.ra > 0))
-      return set_err(PA_ERR_ARG, "cell %lld: cm and ra must be positive", (long long)c);
-    M->cell_ncv[c] = g.n_cv;
-    M->cell_cv_off[c + 1] = M->cell_cv_off[c] + g.n_cv;
+  // validated over fixed pieces in parallel; the lowest bad index is reported
+  {
+    constexpr int64_t kPieces = 64;
+    struct PieceErr {
+      int64_t bad = -1;
+      char msg[192];
+    };
+    std::vector<PieceErr> pe(kPieces);
+    std::vector<char> branched(kPieces, 0);
+    parallel_ranges(kPieces, [&](int64_t p0, int64_t p1) {
+      for (int64_t pc = p0; pc < p1; ++pc) {
+        PieceErr& o = pe[pc];
+        for (int64_t mo = n_morph * pc / kPieces; mo < n_morph * (pc + 1) / kPieces && o.bad < 0;
+             ++mo) {
+          const pa_morphology& g = morphs[mo];
+          if (g.n_cv < 1 || g.n_cv > 32767) {
+            o.bad = mo;
+            snprintf(o.msg, sizeof o.msg, "morphology %lld: n_cv must be in [1, 32767]",
+                     (long long)mo);
+            break;
+          }
+          if (!g.parent || !g.length_um || !g.diam_um || !g.region) {
+            o.bad = mo;
+            snprintf(o.msg, sizeof o.msg, "morphology %lld: NULL array", (long long)mo);
+            break;
+          }
+          for (int i = 0; i < g.n_cv; ++i) {
+            int p = g.parent[i];
+            if ((i == 0 && p != -1) || (i > 0 && (p < 0 || p >= i))) {
+              o.bad = mo;
+              snprintf(o.msg, sizeof o.msg, "morphology %lld: parent[%d] = %d invalid",
+                       (long long)mo, i, p);
+              break;
+            }
+            if (!(g.length_um[i] > 0) || !(g.diam_um[i] > 0) || !std::isfinite(g.length_um[i]) ||
+                !std::isfinite(g.diam_um[i])) {
+              o.bad = mo;
+              snprintf(o.msg, sizeof o.msg,
+                       "morphology %lld: CV %d has non-positive length/diameter", (long long)mo, i);
+              break;
+            }
+            if (i > 0 && p != i - 1) branched[pc] = 1;
+          }
+        }
+      }
+    });
+    for (const PieceErr& o : pe)
+      if (o.bad >= 0) return set_err(PA_ERR_ARG, "%s", o.msg);
+    for (char b : branched)
+      if (b) M->tree = true;
+    M->cell_ncv.resize(n_cells);
+    M->cell_cv_off.resize(n_cells + 1, 0);
+    parallel_ranges(kPieces, [&](int64_t p0, int64_t p1) {
+      for (int64_t pc = p0; pc < p1; ++pc) {
+        PieceErr& o = pe[pc];
+        for (int64_t c = n_cells * pc / kPieces; c < n_cells * (pc + 1) / kPieces && o.bad < 0;
+             ++c) {
+          const pa_cell& cl = cells[c];
+          const char* why = nullptr;
+          if (cl.morph < 0 || cl.morph >= n_morph) why = "bad morphology index";
+          for (int which = 0; which < 2 && !why; ++which) {
+            int m = which == 0 ? cl.soma_mech : cl.dend_mech;
+            if (m < 0 || m >= n_mech ||
+                (mechs[m].kind != PA_MECH_PAS && mechs[m].kind != PA_MECH_HH))
+              why = "soma/dendrite mechanism must be pas or hh";
+          }
+          if (!why) {
+            const pa_morphology& g = morphs[cl.morph];
+            for (int i = 0; i < g.n_cv && !why; ++i) {
+              int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
+              if (mechs[m].kind == PA_MECH_HH && i != 0)
+                why = "HH is supported on the soma CV (CV 0) only";
+            }
+          }
+          if (!why && (!(cl.cm > 0) || !(cl.ra > 0))) why = "cm and ra must be positive";
+          if (why) {
+            o.bad = c;
+            snprintf(o.msg, sizeof o.msg, "cell %lld: %s", (long long)c, why);
+            break;
+          }
+          M->cell_ncv[c] = morphs[cl.morph].n_cv;
+        }
+      }
+    });
+    for (const PieceErr& o : pe)
+      if (o.bad >= 0) return set_err(PA_ERR_ARG, "%s", o.msg);
+    for (int64_t c = 0; c < n_cells; ++c)
+      M->cell_cv_off[c + 1] = M->cell_cv_off[c] + M->cell_ncv[c];
   }
   M->n_cv = M->cell_cv_off[n_cells];
 
@@ -941,8 +1033,6 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       max_dc = std::max(max_dc, o.max_dc);
     }
   }
-  for (int64_t c = 0; c < n_conn; ++c)
-    if (conns[c].src_gid != PA_SRC_POISSON) n_out[conns[c].src_gid + 1]++;
   // counting sort of the connections by (stream, lane): per piece of the
   // connection list a count per bucket, then each piece fills its own slots
   // (within a bucket, connections stay in list order)
@@ -1086,38 +1176,54 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   syn_rec.clear();
   syn_rec.shrink_to_fit();
 
-  // Poisson drives
+  // Poisson drives, in connection order
   std::vector<int32_t> ps_stream, ps_dc;
   std::vector<int64_t> ps_conn;
   std::vector<int64_t> ps_elem;
   std::vector<uint32_t> ps_thr;
-  for (int64_t c = 0; c < n_conn; ++c) {
-    if (conns[c].src_gid != PA_SRC_POISSON) continue;
-    const int s = M->conn_stream[c];
-    const double x = ((conns[c].rate_hz * dt) * 1e-3) * 4294967296.0;
-    ps_stream.push_back(s);
-    ps_elem.push_back(M->conn_elem[c]);
-    ps_conn.push_back(conns[c].poisson_id >= 0 ? conns[c].poisson_id : c);
-    ps_thr.push_back((uint32_t)std::floor(x));
-    ps_dc.push_back(M->sp[s].dc_steps);
+  {
+    std::vector<int64_t> ps_ptr;
+    bucket_scatter(
+        n_conn, 1, [&](int64_t c) -> int64_t { return conns[c].src_gid == PA_SRC_POISSON ? 0 : -1; },
+        ps_ptr,
+        [&](int64_t total) {
+          ps_stream.resize(total);
+          ps_dc.resize(total);
+          ps_conn.resize(total);
+          ps_elem.resize(total);
+          ps_thr.resize(total);
+        },
+        [&](int64_t c, int64_t q) {
+          const int s = M->conn_stream[c];
+          const double x = ((conns[c].rate_hz * dt) * 1e-3) * 4294967296.0;
+          ps_stream[q] = s;
+          ps_elem[q] = M->conn_elem[c];
+          ps_conn[q] = conns[c].poisson_id >= 0 ? conns[c].poisson_id : c;
+          ps_thr[q] = (uint32_t)std::floor(x);
+          ps_dc[q] = M->sp[s].dc_steps;
+        });
   }
   // CSR of recurrent connections by source gid (connection order within a row)
-  for (int64_t c = 0; c < n_cells; ++c) n_out[c + 1] += n_out[c];
+  std::vector<uint8_t> out_stream;
+  std::vector<int64_t> out_elem;
+  std::vector<int32_t> out_delay;
+  bucket_scatter(
+      n_conn, n_cells,
+      [&](int64_t c) -> int64_t {
+        return conns[c].src_gid == PA_SRC_POISSON ? -1 : (int64_t)conns[c].src_gid;
+      },
+      n_out,
+      [&](int64_t total) {
+        out_stream.resize(total);
+        out_elem.resize(total);
+        out_delay.resize(total);
+      },
+      [&](int64_t c, int64_t q) {
+        out_stream[q] = (uint8_t)M->conn_stream[c];
+        out_elem[q] = M->conn_elem[c];
+        out_delay[q] = conn_D[c];
+      });
   const int64_t n_edges = n_out[n_cells];
-  std::vector<uint8_t> out_stream(n_edges);
-  std::vector<int64_t> out_elem(n_edges);
-  std::vector<int32_t> out_delay(n_edges);
-  {
-    std::vector<int64_t> fill(n_out.begin(), n_out.end() - 1);
-    for (int64_t c = 0; c < n_conn; ++c) {
-      const int src = conns[c].src_gid;
-      if (src == PA_SRC_POISSON) continue;
-      const int64_t q = fill[src]++;
-      out_stream[q] = (uint8_t)M->conn_stream[c];
-      out_elem[q] = M->conn_elem[c];
-      out_delay[q] = conn_D[c];
-    }
-  }
   // probes
   M->n_probe = opt->n_probe;
   if (opt->n_probe < 0 || (opt->n_probe > 0 && (!opt->probe_gid || !opt->probe_cv)))
