@@ -96,6 +96,36 @@ def test_isopotential_soma_decays_by_backward_euler_factor():
         assert np.max(np.abs(v - cont)) < 10.6 * dt / tau
 
 
+@pytest.mark.parametrize("theta", [-55.0, -50.5, -64.9])
+def test_threshold_crossing_step_and_interpolated_time(theta):
+    """A leak-only isopotential soma under a step current rises as
+    V^n = V_inf + (V^0 - V_inf)(1 + dt/tau)^-n, V_inf = E + I/g_L (backward
+    Euler, closed form).  Detection: one spike, in the step k with
+    V^k < theta <= V^{k+1}, at k dt + dt (theta - V^k) / (V^{k+1} - V^k), the
+    linear interpolation of the two samples; V never falls back below."""
+    g, e, diam, dt, cm = 3e-4, -65.0, 20.0, 0.025, 1.0
+    area = math.pi * diam * diam                      # um2 (cylinder side, L = diam)
+    g_tot = g * area * 1e-2                           # uS
+    i_nA = g_tot * 15.0                               # V_inf = -50 mV
+    b = W._Builder(dt, 1, "crossing")
+    pas = b.mech(W.PAS, W.pas_params(g, e))
+    m = b.morph(W.soma_only(diam))
+    b.cells_add(1, m, pas, pas, cm=cm, istep=i_nA, vinit=e, thresh=theta)
+    o = O.Oracle(b.build())
+    n_steps = 2000
+    o.run(n_steps)
+    tau = cm / g * 1e-3                               # ms
+    v_inf = e + i_nA / g_tot
+    n = np.arange(n_steps + 1, dtype=float)
+    v = v_inf + (e - v_inf) * (1.0 + dt / tau) ** (-n)
+    k = int(np.nonzero((v[:-1] < theta) & (v[1:] >= theta))[0][0])
+    t_want = k * dt + dt * (theta - v[k]) / (v[k + 1] - v[k])
+    gid, step, t = o.spikes()
+    assert len(gid) == 1 and gid[0] == 0 and step[0] == k
+    assert abs(t[0] - t_want) < 1e-9
+    assert k * dt <= t[0] <= (k + 1) * dt
+
+
 def cable_morph(n, L=1000.0, d=1.0):
     parent = np.arange(-1, n - 1, dtype=np.int32)
     region = np.ones(n, np.int32)
