@@ -286,6 +286,38 @@ def test_expsyn_conductance_closed_form():
         assert abs(o.syn(O.SYN_G)[0] - expect) <= 1e-15 + 1e-13 * expect
 
 
+@pytest.mark.parametrize("e_syn", [0.0, -80.0])
+def test_constant_synaptic_conductance_on_a_soma(e_syn):
+    """A synapse whose conductance does not decay (tau -> infinity) holds g = w
+    after its event; an isopotential leak-only soma at rest E_L then follows the
+    backward-Euler closed form V^n = V_inf + (E_L - V_inf)(1 + dt (g_L + w)/C)^-(n - k_ev),
+    V_inf = (g_L E_L + w E_syn) / (g_L + w): the conductance enters the diagonal
+    and w E_syn the right-hand side, at the synapse's CV, from the event's step."""
+    dt, D, w, g, e_l, diam, cm = 0.1, 10, 2e-3, 3e-4, -65.0, 20.0, 1.0
+    b = W._Builder(dt, 3, "gsyn")
+    pas = b.mech(W.PAS, W.pas_params(g, e_l))
+    syn = b.mech(W.EXPSYN, W.expsyn_params(1e300, e_syn))
+    m = b.morph(W.soma_only(diam))
+    b.cells_add(2, m, pas, pas, vinit=e_l)
+    b.connect(0, 1, 0, syn, w, delay=D * dt)
+    net = b.build()
+    o = O.Oracle(net, probes=[(1, 0)])
+    k_pre, N = 5, 3000
+    o.set_replay([0], [k_pre])
+    o.run(N)
+    v = o.probes()[:, 0]                        # V^1 .. V^N of cell 1
+    area = math.pi * diam * diam
+    g_l = g * area * 1e-2                       # uS
+    c = cm * area * 1e-5                        # nF
+    k_ev = k_pre + D
+    v_inf = (g_l * e_l + w * e_syn) / (g_l + w)
+    n = np.arange(1, N + 1)
+    expect = np.where(n <= k_ev, e_l,
+                      v_inf + (e_l - v_inf) * (1.0 + dt * (g_l + w) / c) ** (-(n - float(k_ev))))
+    assert np.allclose(v, expect, rtol=0, atol=1e-9)
+    assert abs(v[-1] - v_inf) < 1e-6 * abs(e_l - v_inf)
+
+
 def test_gb_calcium_pair_closed_form_and_no_depression_from_zero():
     """Eq. ca_model_graupner_brunel for one pre and one post spike is a sum of two
     sampled exponentials; with w0 = 0 every depression term -gamma_d w is zero, so
