@@ -397,6 +397,30 @@ def test_stdp_single_pair_window(lag):
     assert abs(dw - expect) < 1e-15 + 1e-13 * abs(expect)
 
 
+def test_stdp_spike_trains_sum_the_pair_window():
+    """Eqs. stdp_ode_1-3 have additive traces, so for trains of pre and post
+    events the total change is the pair window summed over every (pre, post)
+    pair: A_pre e^{-(q - p) dt / tau_pre} for each post event q at or after a
+    pre event p, A_post e^{-(p - q) dt / tau_post} for each pre event after a
+    post event."""
+    dt, D = 0.1, 5
+    tp, tq, ap, aq = 16.8, 33.7, 0.01, -0.012
+    p = W.stdp_params(tau_pre=tp, tau_post=tq, a_pre=ap, a_post=aq, w0=0.5)
+    net = pair_net(W.STDP, p, delay=D * dt, dt=dt)
+    pre = [100, 140, 300, 305]
+    post = [120, 150, 180, 300, 420]
+    o = run_replay(net, [(0, k - D) for k in pre] + [(1, k - 1) for k in post], 600)
+    expect = 0.0
+    for kp in pre:
+        for kq in post:
+            if kq >= kp:
+                expect += ap * math.exp(-(kq - kp) * dt / tp)
+            else:
+                expect += aq * math.exp(-(kp - kq) * dt / tq)
+    dw = o.syn(O.SYN_W)[0] - 0.5
+    assert abs(dw - expect) < 1e-13
+
+
 def test_stc_early_phase_relaxation_and_prp_closed_forms():
     """Eq. early_phase_weight without calcium: h - h0 shrinks by (1 - 0.1 dt/tau_h) per
     step.  Eq. prp_single_comp with theta_pro < 0 (synthesis always on) from p = 0:
