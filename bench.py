@@ -34,15 +34,32 @@ sys.path.insert(0, ROOT)
 
 METRIC = "compartment-updates/s, mixed vs FP64 plain, same GPU; serving p50/p99 latency"
 UNIT = "CU/s"
-HBM_PEAK_GBS = 6470.8          # measured copy bandwidth of this machine's B300 (STREAM-style)
 N_SM = 148
-DFMA_PER_SM_CLK = 2            # FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal @ 2.03 GHz)
+DFMA_PER_SM_CLK = 2            # nominal FP64 FMA lanes per SM and clock (context only)
 RCP64_DFMA_EQ = 465.0 / 71.0   # measured: FP64 FMA 465 G/s vs FP64 reciprocal 71 G/s on B300
-# DRAM bytes per compartment-update of the current epoch kernel (mixed, shape 0),
-# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
-# 65,536-cell launch of the same generator (90.37 GB for 735.3 M CU); traffic
-# grows in proportion to the CUs of a launch, so the full launch is scaled.
-TRAFFIC_B_PER_CU = {"mixed": 122.9}
+FALLBACK_HBM_GBS = 6400.0      # the profiling recipe's fallback when no measured peak exists
+# The survey's algorithmic bytes per compartment-update for the large STDP
+# network (hot-path scope table, measurement row): FP64 about 60 B/CU (V read
+# and write 16, axial coefficient 8, parent 4, C/dt 8, leak 8 per CV; HH gates
+# per soma; synapse state amortised at about 0.36 synapses per CV), mixed about
+# 45 B/CU (FP32 mechanism state and FP32-stored geometry).
+SURVEY_BYTES_PER_CU = {"fp64": 60.0, "mixed": 45.0, "fp32": 45.0}
+# DRAM bytes per compartment-update of the epoch kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of a 65,536-cell launch of the
+# same generator, scaled to a full launch by the CUs it processes); None once
+# the kernel has changed since the counters were taken.
+TRAFFIC_B_PER_CU = {}
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json (written by the pool's driver): HBM copy bandwidth."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "of fallback (no MEASURED_PEAKS.json)"
 
 
 def parse():
@@ -55,7 +72,8 @@ def parse():
     p.add_argument("--shapes", type=int, default=4096)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    p.add_argument("--precision", default="all", choices=["all", "both", "mixed", "fp64", "fp32"],
+                   help="all: mixed (the headline), fp64 and fp32; both: mixed and fp64")
     p.add_argument("--busyring", action="store_true",
                    help="run the paper's busyring table instead (setup and propagation)")
     p.add_argument("--busyring-cells", default="1024,16384,32768")
@@ -101,28 +119,30 @@ def net_stats(net):
     }
 
 
-def per_cu_model(st, mixed):
-    """Algorithmic work of one compartment-update, amortising soma and synapse work.
+def per_cu_model(st, prec):
+    """Work of one compartment-update of this engine's layout, amortising soma and
+    synapse work (prec: "fp64", "mixed" or "fp32").
     Bytes: state that must stream every step (V read+write, four FP64 cable
     coefficients: C/dt, diagonal, leak E term, axial coupling; 2-byte parent
-    index on trees) plus per-synapse state read+write (conductance; the STDP
+    index on trees) plus per-synapse state read+write (the conductance: 8 B in
+    FP64 and in mixed, where it is a float-float pair; 4 B in FP32; the STDP
     traces are touched only at events), CV index and event word.
     FP64 ops (FMA, multiply or add; the FP64 pipe's work): per row the diagonal
     and right-hand-side assembly (3: d + g_syn, C/dt V + E-term, + gE_syn), the
     f and x' products (2) and the back substitution (1); two FMAs per child
     eliminated into its parent (carried first child or other child); HH per
-    soma; on the FP64 path the synapse ops (decay, two sums, g E).  The row
-    reciprocal runs on the integer pipes (correctly rounded, about forty
-    integer ops) and is not counted."""
-    ts = 4 if mixed else 8
+    soma; the synapse ops: 4 per synapse in FP64 (decay, two sums, g E), 2 in
+    mixed (the run's float-float sum to FP64 and its product with E; the rest
+    runs on the FP32 pipes), 0 in FP32.  The row reciprocal runs on the integer
+    pipes (correctly rounded, about forty integer ops) and is not counted."""
+    gb = 4 if prec == "fp32" else 8
     cv_bytes = 16 + 32 + (2 if st["tree"] else 0)
-    stdp_bytes = 2 * ts + 4 + 8
-    exp_bytes = 2 * ts + 4 + 8
-    syn_bytes = st["n_stdp"] * stdp_bytes + st["n_expsyn"] * exp_bytes
+    syn_b = 2 * gb + 4 + 8
+    syn_bytes = (st["n_stdp"] + st["n_expsyn"]) * syn_b
     bytes_per_cu = cv_bytes + syn_bytes / st["n_cv"]
     solve = 6 * st["n_cv"] + 2 * (st["n_first"] + st["n_other"])
     hh = 153 + 6 * RCP64_DFMA_EQ + 20                  # 9 model exps, 6 divisions, currents
-    syn = 0 if mixed else 4 * (st["n_stdp"] + st["n_expsyn"])
+    syn = {"fp64": 4, "mixed": 2, "fp32": 0}[prec] * (st["n_stdp"] + st["n_expsyn"])
     fp64_per_cu = (solve + hh * st["n_cells"] + syn) / st["n_cv"]
     return bytes_per_cu, fp64_per_cu
 
@@ -402,7 +422,7 @@ def busyring_bench(device, cells_list, depths, precision_name, extra_flags=0):
     from paper_2411_16445_b300 import workloads as W
     torch.cuda.set_device(device)
     stream = torch.cuda.current_stream(device)
-    prec = E.PA_MIXED if precision_name == "mixed" else E.PA_FP64
+    prec = {"mixed": E.PA_MIXED, "fp32": E.PA_FP32}.get(precision_name, E.PA_FP64)
     rows = []
     for n in cells_list:
         for d in depths:
@@ -594,7 +614,7 @@ def main():
     if args.busyring:
         cells = [int(x) for x in args.busyring_cells.split(",")]
         rows = busyring_bench(0, cells, [int(x) for x in args.busyring_depths.split(",")],
-                              args.precision if args.precision != "both" else "fp64",
+                              args.precision if args.precision not in ("all", "both") else "fp64",
                               args.busyring_flags)
         print(json.dumps({"benchmark": "busyring", "unit": UNIT, "simulated_ms": 200.0,
                           "dt_ms": 0.025, "rows": rows,
@@ -621,8 +641,9 @@ def main():
     net = workload(args.cells, args.shapes, seed_offset=rank)
     st = net_stats(net)
     runs = {}
-    precs = {"mixed": 1, "fp64": 0}
-    order = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    precs = {"mixed": 1, "fp64": 0, "fp32": 2}
+    order = {"all": ["mixed", "fp64", "fp32"], "both": ["mixed", "fp64"]}.get(
+        args.precision, [args.precision])
     for name in order:
         runs[name] = time_gpu(net, precs[name], args.steps, args.warmup, device, barrier,
                               model_flags(args))
@@ -636,39 +657,50 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    def roofline(run, mixed):
-        bpc, fpc = per_cu_model(st, mixed)
+    hbm_peak, hbm_note = measured_peaks()
+    from paper_2411_16445_b300 import engine as E
+    fma_rate = E.measure_fp64(device)["fma_per_s"]       # FP64 FMA/s, measured here
+
+    def roofline(run, prec):
+        """Top level: the epoch kernel against the HBM roof on the survey's algorithmic
+        bytes; beside it the FP64 pipe, the engine's own layout bytes and the DRAM
+        traffic ncu counted."""
+        bpc, fpc = per_cu_model(st, prec)
+        sbpc = SURVEY_BYTES_PER_CU[prec]
         cu_launch = run["n_cv"] * run["epoch_steps"]
         t_launch = run["epoch_kernel_ms"] / max(run["epoch_launches"], 1) * 1e-3
+        ach_gbs = sbpc * cu_launch / t_launch / 1e9
         clk = (run["clocks"] or {}).get("sm_mhz") or 2032.0
-        peak_tflops = N_SM * DFMA_PER_SM_CLK * 2 * clk * 1e6 / 1e12
-        ach_tflops = 2 * fpc * cu_launch / t_launch / 1e12
-        ach_gbs = bpc * cu_launch / t_launch / 1e9
-        tb = TRAFFIC_B_PER_CU.get("mixed" if mixed else "fp64")
-        return {"bound": "alu", "achieved": ach_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": ach_tflops / peak_tflops,
-                "traffic": tb * cu_launch if tb else None,
-                "traffic_note": ("DRAM bytes per launch, scaled from one ncu capture of a "
-                                 "65,536-cell launch (122.9 B/CU)") if tb else
-                                "not captured for this precision",
-                "kernel": "epoch_kernel", "fp64_ops_per_cu": fpc,
-                "peak_note": f"FP64: {N_SM} SMs x {DFMA_PER_SM_CLK} FMA/clk x 2 flop at the median "
-                             f"SM clock under load ({clk:.0f} MHz); HH divisions count "
-                             f"{RCP64_DFMA_EQ:.2f} FMA-equivalents (measured); the solver's "
-                             "row reciprocal runs on the integer pipes",
-                "hbm": {"achieved": ach_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                        "frac": ach_gbs / HBM_PEAK_GBS, "algorithmic_bytes_per_cu": bpc,
-                        "traffic_gbs": tb * cu_launch / t_launch / 1e9 if tb else None,
-                        "traffic_frac": tb * cu_launch / t_launch / 1e9 / HBM_PEAK_GBS
-                        if tb else None,
-                        "peak_note": "measured copy bandwidth; traffic_* use the DRAM bytes "
-                                     "ncu counted (scaled), not the algorithmic bytes"}}
+        fp64_peak = 2 * fma_rate / 1e12
+        fp64_ach = 2 * fpc * cu_launch / t_launch / 1e12
+        tb = TRAFFIC_B_PER_CU.get(prec)
+        return {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach_gbs / hbm_peak, "traffic": tb * cu_launch if tb else None,
+                "kernel": "epoch_kernel", "peak_note": hbm_note,
+                "algorithmic_bytes_per_cu": sbpc,
+                "algorithmic_note": "the survey's per-CU bytes for this network "
+                                    "(hot-path scope table, measurement row) x CVs x steps of "
+                                    "one launch / the launch's mean device time (CUDA events)",
+                "traffic_note": None if tb else "kernel changed since the last ncu capture",
+                "layout": {"bytes_per_cu": bpc, "achieved_gbs": bpc * cu_launch / t_launch / 1e9,
+                           "frac": bpc * cu_launch / t_launch / 1e9 / hbm_peak,
+                           "note": "bytes this engine's layout streams per CU (cable rows, "
+                                   "conductances, CV index, event word; no scratch)"},
+                "fp64_pipe": {"achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": fp64_ach / fp64_peak, "fp64_ops_per_cu": fpc,
+                              "peak_note": "of measured: pa_measure_fp64 (FP64 FMA chains, CUDA "
+                                           "events) x 2 flop, this run",
+                              "nominal_tflops": N_SM * DFMA_PER_SM_CLK * 2 * clk * 1e6 / 1e12,
+                              "note": "HH divisions count "
+                                      f"{RCP64_DFMA_EQ:.2f} FMA-equivalents (measured); the "
+                                      "solver's row reciprocal runs on the integer pipes"}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 solve + f32 synapses" if head == "mixed" else "f64",
+        "dtype": {"mixed": "f64 solve and sums + f32x2 conductances",
+                  "fp32": "f64 solve + f32 synapses", "fp64": "f64"}[head],
         "data": "synthetic",
         "config": {"workload": "large_stdp", "n_cells": st["n_cells"], "n_cv": st["n_cv"],
                    "n_synapses": st["n_syn"], "dt_ms": net.dt,
@@ -676,7 +708,7 @@ def main():
                    "precision": head, "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (working set "
                          f"{r['device_bytes'] / 1e9:.1f} GB vs 126 MB L2)"},
-        "roofline": roofline(r, head == "mixed"),
+        "roofline": roofline(r, head),
         "gpu_launches": r["kernel_launches"],
         "clocks": r["clocks"],
         "setup_s": r["setup_s"],
@@ -688,9 +720,11 @@ def main():
                       "event_kernels_ms_per_step": run["event_kernels_ms"] / max(run["epoch_launches"], 1),
                       "spikes": run["spikes"], "kernel_shape": run["shape"],
                       "shape_trial_ms": run["shape_trial_ms"],
-                      "roofline": roofline(run, name == "mixed")}
+                      "roofline": roofline(run, name)}
     if "mixed" in runs and "fp64" in runs:
         line["mixed_over_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
+    if "fp32" in runs and "fp64" in runs:
+        line["fp32_over_fp64"] = line["fp32"]["value"] / line["fp64"]["value"]
     if not args.no_e2e:
         line["e2e"] = time_e2e(net, precs[head], args.steps, device)
     if not args.no_batched:

@@ -100,11 +100,19 @@ extern "C" {
                              narrow bin; pa_fast_forward refuses the model. */
 
 /* arithmetic of the loop */
-#define PA_FP64 0   /* everything in FP64 */
-#define PA_MIXED 1  /* synaptic conductances and STDP traces (exponential integration)
-                       and the per-CV synaptic sums in FP32; voltage, cable coefficients,
-                       assembly, Hines solve, HH, calcium and the slow plasticity state
-                       (GB w, STC h/z/p, STDP w) in FP64 */
+#define PA_FP64 0   /* everything in FP64: the plain definition, operation for operation */
+#define PA_MIXED 1  /* synaptic conductances (exponential decay, event jumps, the per-CV
+                       sums of each run of same-CV synapses) on the FP32 pipes in
+                       float-float form (hi + lo, about 48 significand bits); event
+                       weights and STDP traces in FP32; the per-CV synaptic sums handed
+                       to the assembly, the voltage, cable coefficients, assembly, Hines
+                       solve, HH, calcium and the slow plasticity state (GB w, STC h/z/p,
+                       STDP w) in FP64.  Meets the oracle within 1e-5 V and 1e-3 ms. */
+#define PA_FP32 2   /* as PA_MIXED but conductances and the per-CV synaptic sums in plain
+                       FP32: each step re-rounds every conductance (2^-24), and the
+                       accumulated rounding can move spike times by several microseconds
+                       on networks (its measured error against the oracle is documented
+                       with the engine). */
 
 /* connection source meaning "an independent Poisson train of rate rate_hz" */
 #define PA_SRC_POISSON (-1)
@@ -185,7 +193,7 @@ typedef struct {
 typedef struct {
   double dt;                /* ms, fixed for the model's lifetime */
   uint64_t seed;            /* keys the Poisson trains (Threefry-4x64-12) */
-  int32_t precision;        /* PA_FP64 or PA_MIXED */
+  int32_t precision;        /* PA_FP64, PA_MIXED or PA_FP32 */
   int32_t device;           /* CUDA device ordinal */
   void* stream;             /* cudaStream_t to run on; NULL = the legacy default stream */
   int32_t n_probe;          /* membrane-potential probes recorded after every step */
@@ -280,17 +288,19 @@ int pa_advance(pa_model* m, double t_end_ms, double dt_ms);
  * allocation could stall or fail.  The paper has no counterpart; this is an
  * interface convenience.
  *
- * It advances the model exactly like pa_advance (same kernels, same results;
- * the FP64 path is bit-identical), but the Hines elimination scratch of the
- * epoch kernel comes from one array of 32 MiB that the library reserves in
- * device memory on every GPU it is used on, held until the process exits.
- * The call itself allocates nothing: no cudaMalloc, no cudaFree, no kernel
- * timing events (PA_FLAG_TIME_KERNELS is ignored here).
+ * It advances the model exactly like pa_advance (the same kernels, so the same
+ * results bit for bit in every precision), but the Hines elimination scratch
+ * of the epoch kernels comes from one array of 32 MiB that the library
+ * reserves in device memory on every GPU it is used on, held until the process
+ * exits.  The call allocates nothing: no cudaMalloc, no cudaFree, no kernel
+ * timing events (PA_FLAG_TIME_KERNELS is ignored here), no CUDA graphs.
  *   - Limit: models of at most 2,097,152 padded CVs (pa_info.n_padded_cv);
  *     larger models get PA_ERR_ARG.  Open-loop replay is not supported
  *     (PA_ERR_STATE).
  *   - The first call on a GPU looks the array's device address up (a one-time
- *     set-up, per device): make that first call before any stream capture.
+ *     set-up, per device; with CUDA's lazy module loading the driver reserves
+ *     the array at that moment).  Make that first call before any stream
+ *     capture and outside any region that must not allocate.
  *   - All calls share the one array.  Calls whose GPU work overlaps (two models
  *     advanced concurrently on different streams) race on it; serialise them.
  *   - Nothing in the array needs clearing: each step writes the values before
@@ -299,6 +309,17 @@ int pa_advance_noalloc(pa_model* m, double t_end_ms, double dt_ms);
 
 /* Waits for the model's stream and reports device-side errors. */
 int pa_sync(pa_model* m);
+
+/* Poll limit of the epoch kernel's bounded waits for its staged rows (the
+ * paper has no counterpart; failure detection of this engine).  polls = 0
+ * restores the default (4,194,304 polls, milliseconds).  A wait that runs out
+ * makes the kernel stop stepping, let every copy it issued land, and return;
+ * the next pa_sync / pa_read_* reports PA_ERR_TIMEOUT and the model's state is
+ * then invalid (the CUDA context stays usable).  A limit of a few polls makes
+ * waits run out on purpose, which is how the failure path is tested.
+ * Synchronises the model's stream and drops its captured CUDA graphs (they are
+ * captured again at the next whole-epoch advance). */
+int pa_set_wait_limit(pa_model* m, uint32_t polls);
 
 /* Copies the probe samples recorded since the last call into out
  * ([sample][probe], double, cap values) and clears the record.  cap = 0 only
@@ -371,6 +392,15 @@ void pa_free_model(pa_model* m);
  * out[2] = cases checked, out[3] = bits of the first mismatching reciprocal
  * input (0 if none).  Synchronous; allocates 32 bytes of device memory. */
 int pa_check_arith(int32_t device, uint64_t seed, int64_t n_random, int64_t* out);
+
+/* Measures the GPU's FP64 fused multiply-add throughput (no model needed; the
+ * paper has no counterpart; the roofline denominator of the FP64 pipe).  Runs
+ * 8 x SMs blocks of 256 threads, each thread 8 independent chains of 16,384
+ * FMAs, timed with CUDA events on the legacy default stream, best of five
+ * after one warm-up.  out[0] = FMA operations per second (one FMA = 2 flop),
+ * out[1] = the best run's milliseconds.  Synchronous; allocates 8 bytes of
+ * device memory. */
+int pa_measure_fp64(int32_t device, double* out);
 
 const char* pa_last_error(void);
 

@@ -3,7 +3,8 @@
 Every translation unit is compiled for sm_103a only.  The FP64 kernels and the
 host builder are compiled without multiply-add contraction (--fmad=false,
 -ffp-contract=off): the FP64 path is specified operation by operation.  The
-mixed-precision kernels keep contraction on.
+mixed-precision and FP32-synapse kernels keep contraction on (their float-float
+operations are written with explicitly rounded intrinsics).
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ NOFMA = ["--fmad=false", "-Xcompiler", "-ffp-contract=off"]
 UNITS = {
     "step_fp64.cu": NOFMA,
     "step_mixed.cu": [],
+    "step_fp32.cu": [],
     "events.cu": [],
     "model.cu": NOFMA,
     "epoch_noalloc.cu": NOFMA,

@@ -86,7 +86,31 @@ __global__ void widen_all(unsigned long long* out) {
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&out[2], (unsigned long long)total);
 }
 
+// FP64 FMA throughput: eight independent FMA chains per thread (enough to
+// cover the dependent latency at full occupancy), values kept bounded
+// (x <- x a + b with 0 < a < 1); the result is stored only if it hits an
+// impossible value, so the chains cannot be removed.
+__global__ void __launch_bounds__(256) fma_rate_kernel(int iters, double a, double b,
+                                                       double* sink) {
+  double x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 1e-3 * (threadIdx.x + 1) + j;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (s == -1.0) sink[0] = s;
+}
+
 }  // namespace
+
+int launch_fma_rate(int blocks, int iters, double* sink, void* stream) {
+  fma_rate_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(iters, 0.9999999, 1e-7, sink);
+  return (int)cudaGetLastError();
+}
 
 int launch_arith_check(uint64_t seed, int64_t n_random, unsigned long long* d_out, int n_sm,
                        void* stream) {

@@ -46,13 +46,13 @@ struct StreamParams {
 struct StreamDev {
   const int32_t* cvf;    // (cv << 1) | first-on-CV flag; -1 for padding
   const int32_t* sbase;  // [n_groups + 1] row offsets of each group
-  const void* weight;    // uS, double (FP64) or float (mixed)
-  void* g;               // conductance, TM
+  const void* weight;    // uS: double (PA_FP64) or float (PA_MIXED, PA_FP32)
+  void* g;               // conductance [uS]: double, float2 hi + lo (PA_MIXED) or float
   double* c;             // calcium (GB, STC)
   double* w;             // GB w, STDP w, STC h
   double* z;             // STC z
-  void* apre;            // TM (STDP): trace value right after its last jump
-  void* apost;           // TM (STDP)
+  void* apre;            // STDP: trace value right after its last jump, as the weight
+  void* apost;           // STDP, as the weight
   int32_t* kpre;         // step of the last jump of apre (STDP)
   int32_t* kpost;        // step of the last jump of apost (STDP)
   uint64_t* cmask;       // [n_slots][n_elem]: bit (k mod E) = conductance event in step k
@@ -118,8 +118,8 @@ struct EpochArgs {
   const double* dc;          // cdt + axial sum (+ leak for passive CVs)
   const double* em;          // leak g E for passive CVs
   const double* a;           // -g_axial to the parent
-  void* gs;                  // synaptic conductance per CV, TM
-  void* es;                  // synaptic g E per CV, TM
+  void* gs;                  // synaptic conductance per CV: double (float in PA_FP32)
+  void* es;                  // synaptic g E per CV: double (float in PA_FP32)
   double* f;                 // elimination scratch
   double* xp;                // elimination scratch
   const int16_t* par;        // tree: parent row (row 0: -1)
@@ -190,6 +190,7 @@ struct EpochArgs {
   int32_t n_probe;
   int32_t* err_flags;        // bit 0: probe overflow, bit 1: spike record full,
                              // bit 2: a bounded wait expired
+  uint32_t wait_limit;       // polls of a bounded staging wait (0: the default)
 };
 
 struct PoissonArgs {
@@ -242,10 +243,17 @@ int launch_epoch_fp64(const EpochArgs& a, bool tree, int shape, void* stream,
                       const SideLaunch* side = nullptr);
 int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream,
                        const SideLaunch* side = nullptr);
-int launch_init_gates_fp64(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
-                           void* stream);
-int launch_init_gates_mixed(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
-                            void* stream);
+int launch_epoch_fp32(const EpochArgs& a, bool tree, int shape, void* stream,
+                      const SideLaunch* side = nullptr);
+// the launcher of precision `prec` (PA_FP64, PA_MIXED, PA_FP32)
+inline int launch_epoch(int prec, const EpochArgs& a, bool tree, int shape, void* stream,
+                        const SideLaunch* side = nullptr) {
+  return prec == 1   ? launch_epoch_mixed(a, tree, shape, stream, side)
+         : prec == 2 ? launch_epoch_fp32(a, tree, shape, stream, side)
+                     : launch_epoch_fp64(a, tree, shape, stream, side);
+}
+int launch_init_gates(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
+                      void* stream);
 // Graph launches: zero the mask slot of the clock's epoch in every mask array,
 // then advance the clock by one epoch (events.cu).
 struct SlotClear {
@@ -271,9 +279,9 @@ struct FastForward {
   const double* prp_vdt_long;
   bool tree;
 };
-int launch_fast_forward(const EpochArgs& a, const FastForward& f, bool mixed, void* stream);
+int launch_fast_forward(const EpochArgs& a, const FastForward& f, int prec, void* stream);
 
-int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, bool mixed,
+int launch_epoch_noalloc(const EpochArgs& a, int64_t n_padded_cv, bool tree, int prec,
                          int shape, void* stream);
 int64_t noalloc_max_padded_cv();
 
@@ -282,6 +290,9 @@ int64_t noalloc_max_padded_cv();
 // [3] the first mismatching reciprocal input (bits).
 int launch_arith_check(uint64_t seed, int64_t n_random, unsigned long long* d_out, int n_sm,
                        void* stream);
+// FP64 FMA throughput microbenchmark (arith_check.cu): blocks x 256 threads,
+// each running 8 independent chains of `iters` FMAs.
+int launch_fma_rate(int blocks, int iters, double* sink, void* stream);
 int launch_poisson(const PoissonArgs& a, int64_t k_from, int64_t k_to, void* stream);
 int launch_route(const RouteArgs& a, int32_t max_spikes, void* stream);
 int launch_log_append(const int32_t* spk_count, const int32_t* gid, const int32_t* step,

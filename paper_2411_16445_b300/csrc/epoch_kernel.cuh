@@ -31,6 +31,7 @@
 
 #include "engine.h"
 #include "int_arith.cuh"
+#include "precision.cuh"
 #include "prp_field.cuh"
 #include "rng.cuh"
 
@@ -137,9 +138,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false if the phase did not complete within kSpinLimit polls
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+// non-blocking test of the phase
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false if the phase did not complete within `limit` polls (the
+// first a non-blocking test, the others potentially blocking try_waits)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint32_t limit = kSpinLimit) {
+  if (mbar_test(bar, parity)) return true;
+  for (uint32_t it = 1; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -160,10 +176,10 @@ __device__ __forceinline__ void fence_async_shared() {
 }
 
 // Shared-memory layout of one warp's stages for a given precision / tree flag.
-template <class TM, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth>
+template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth>
 struct Stage {
   // bytes per row (32 lanes) of each staged array
-  static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(TM), kI = TREE ? 32 * 2 : 0,
+  static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(typename PR::S), kI = TREE ? 32 * 2 : 0,
                        kA = (TREE && kStackDepth > 0) ? 32 * 8 : 0,
                        kT = (TREE && kStackDepth > 0) ? 32 : 0;
   static constexpr bool kStacks = TREE && kStackDepth > 0;  // fork stacks in use
@@ -199,15 +215,17 @@ struct Stage {
 // plastic state and returns the conductance entering this step's per-CV sums.
 // cc, wv, zv are the synapse's calcium, weight (h for STC) and z as loaded by
 // the caller (only those its kind uses); S accumulates |h - h0| (STC).
-template <class TM>
-__device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev& D, uint32_t e,
-                                         bool pre, bool capre, bool post, TM gv, double cc,
-                                         double wv, double zv, double prp, int64_t k, double dt,
-                                         uint64_t seed, double& S) {
+template <class PR>
+__device__ __forceinline__ typename PR::G syn_update(const StreamParams& P, const StreamDev& D,
+                                                     uint32_t e, bool pre, bool capre, bool post,
+                                                     typename PR::G gv, double cc, double wv,
+                                                     double zv, double prp, int64_t k, double dt,
+                                                     uint64_t seed, double& S) {
+  using TW = typename PR::W;
   if (P.kind == SK_EXPSYN) {
-    if (pre) gv = gv + ((const TM*)D.weight)[e];
+    if (pre) gv = PR::add_w(gv, ((const TW*)D.weight)[e]);
   } else if (P.kind == SK_GB) {
-    if (pre) gv = gv + ((const TM*)D.weight)[e];
+    if (pre) gv = PR::add_w(gv, ((const TW*)D.weight)[e]);
     if (capre) cc = cc + P.c_pre;
     if (post) cc = cc + P.c_post;
     const double w = wv;
@@ -224,7 +242,7 @@ __device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev&
   } else if (P.kind == SK_STC) {
     const double h = wv, z = zv;
     const double h0 = P.h0;
-    if (pre) gv = gv + (TM)((double)((const TM*)D.weight)[e] * ((h + h0 * z) / h0));
+    if (pre) gv = PR::add_d(gv, (double)((const TW*)D.weight)[e] * ((h + h0 * z) / h0));
     if (capre) cc = cc + P.c_pre;
     if (post) cc = cc + P.c_post;
     S = S + fabs(h - h0);
@@ -241,64 +259,29 @@ __device__ __forceinline__ TM syn_update(const StreamParams& P, const StreamDev&
     D.w[e] = hn;
     D.c[e] = cc * P.decay_c;
   } else if (pre || post) {  // SK_STDP: traces evaluated in closed form at events only
-    TM* AP = (TM*)D.apre;
-    TM* AQ = (TM*)D.apost;
+    using TT = typename PR::T;
+    TT* AP = (TT*)D.apre;
+    TT* AQ = (TT*)D.apost;
     double w = D.w[e];
     double ap = (double)AP[e] * model_exp(-((double)(k - D.kpre[e]) * dt) / P.tau_pre);
     double aq = (double)AQ[e] * model_exp(-((double)(k - D.kpost[e]) * dt) / P.tau_post);
     if (pre) {
       const double wc = w < 0.0 ? 0.0 : (w > P.w_max ? P.w_max : w);
-      gv = gv + (TM)((double)((const TM*)D.weight)[e] * wc);
+      gv = PR::add_d(gv, (double)((const TW*)D.weight)[e] * wc);
       ap = ap + P.a_pre;
       w = w + aq;
-      AP[e] = (TM)ap;
+      AP[e] = (TT)ap;
       D.kpre[e] = (int32_t)k;
     }
     if (post) {
       aq = aq + P.a_post;
       w = w + ap;
-      AQ[e] = (TM)aq;
+      AQ[e] = (TT)aq;
       D.kpost[e] = (int32_t)k;
     }
     D.w[e] = w;
   }
   return gv;
-}
-
-// The per-CV synaptic sums are spelled with explicitly rounded operations, never
-// contracted into fused multiply-adds, so that both cell bins (and any compiler
-// schedule) produce the same sums.
-__device__ __forceinline__ float tm_mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float tm_add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double tm_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double tm_add(double a, double b) { return __dadd_rn(a, b); }
-
-// Per-CV synaptic sums over one run of same-CV synapses of a stream, in the
-// canonical order: the run starts from 0 (first synapse on the CV) or from the
-// sums left by an earlier stream, and is stored when it ends.
-// cvf = (cv << 3) | first-on-CV (1) | run start (2) | run end (4).
-template <class TM>
-__device__ __forceinline__ void run_sum(TM* gs, TM* es, int32_t rb, int lane, int32_t cvf, TM g,
-                                        TM E, TM& accg, TM& acce) {
-  const TM ge = tm_mul(g, E);
-  if (cvf & 2) {
-    if (cvf & 1) {
-      accg = g;
-      acce = ge;
-    } else {
-      const uint32_t ce = elem_of(rb, cvf >> 3, lane);
-      accg = tm_add(gs[ce], g);
-      acce = tm_add(es[ce], ge);
-    }
-  } else {
-    accg = tm_add(accg, g);
-    acce = tm_add(acce, ge);
-  }
-  if (cvf & 4) {
-    const uint32_t ce = elem_of(rb, cvf >> 3, lane);
-    gs[ce] = accg;
-    es[ce] = acce;
-  }
 }
 
 // One step of the lane's synapses of the heterosynaptic calcium stream (HCA),
@@ -311,15 +294,16 @@ __device__ __forceinline__ void run_sum(TM* gs, TM* es, int32_t rb, int lane, in
 // synapses carry no conductance: where an HCA run is the first on its CV, the
 // per-CV conductance sums start at zero there, as the loop of the other kinds
 // would make them.
-template <class TM>
+template <class PR>
 __device__ __noinline__ void hca_stream(const EpochArgs& A, int s, int g, int lane, int32_t rb,
                                         int kk, int32_t slot) {
   const StreamParams& P = A.sp[s];
   const StreamDev& D = A.sd[s];
   const int32_t sb = D.sbase[g], nrow = D.sbase[g + 1] - sb;
   const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
-  TM* GS = (TM*)A.gs;
-  TM* ES = (TM*)A.es;
+  using TS = typename PR::S;
+  TS* GS = (TS*)A.gs;
+  TS* ES = (TS*)A.es;
   double accq = 0.0;
   bool zero = false;
   for (int j = 0; j < nrow; ++j) {
@@ -341,17 +325,19 @@ __device__ __noinline__ void hca_stream(const EpochArgs& A, int s, int g, int la
     if (cvf & 4) {
       A.ca_src[ce] = accq;
       if (zero) {
-        GS[ce] = (TM)0;
-        ES[ce] = (TM)0;
+        GS[ce] = (TS)0;
+        ES[ce] = (TS)0;
       }
     }
   }
 }
 
-template <class TM, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
+template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
           int kStackDepth>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const EpochArgs A) {
-  using ST = Stage<TM, TREE, kRowsBack, kRowsFwd, kStackDepth>;
+  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
+  using TS = typename PR::S;
+  using TG = typename PR::G;
   extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -366,8 +352,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
     mbar_init_fence();
   }
   __syncwarp();
-  uint32_t phase = 0;  // expected parity of each stage's barrier
+  uint32_t phase = 0;    // expected parity of each stage's barrier
+  uint32_t pending = 0;  // stages with a copy issued and not yet waited for
   bool failed = false;
+  const uint32_t wait_limit = A.wait_limit ? A.wait_limit : kSpinLimit;
   using HH = HH64;
   const int64_t L = (int64_t)g * 32 + lane;
   const int n = A.ncv[L];
@@ -380,8 +368,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
   const double* __restrict__ DC = A.dc;
   const double* __restrict__ EM = A.em;
   const double* __restrict__ AA = A.a;
-  TM* __restrict__ GS = (TM*)A.gs;
-  TM* __restrict__ ES = (TM*)A.es;
+  TS* __restrict__ GS = (TS*)A.gs;
+  TS* __restrict__ ES = (TS*)A.es;
   double* __restrict__ F = A.f;
   double* __restrict__ XP = A.xp;
 
@@ -419,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
     double S = 0.0, qs_field = 0.0;
     for (int s = 0; s < A.n_streams && !failed; ++s) {
       if (s == A.ca_stream) {
-        hca_stream<TM>(A, s, g, lane, rb, kk, slot);
+        hca_stream<PR>(A, s, g, lane, rb, kk, slot);
         continue;
       }
       const StreamParams& P = A.sp[s];
@@ -427,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       const int32_t sb = D.sbase[g], nrow = D.sbase[g + 1] - sb;
       const bool calc = P.kind == SK_GB || P.kind == SK_STC;
       const bool stc = P.kind == SK_STC;
-      constexpr int szm = 32 * (int)sizeof(TM);
+      constexpr int szm = 32 * (int)sizeof(TG);
       const int rowb = 128 + 256 + szm + (calc ? 768 : 0) + (stc ? 256 : 0);
       int RS = ST::kBytes / rowb;
       if (RS > 16) RS = 16;
@@ -436,19 +424,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       const int nc = (nrow + RS - 1) / RS;
       const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
       const uint64_t* camg = calc ? D.camask + (int64_t)slot * D.n_elem : nullptr;
-      TM* G = (TM*)D.g;
-      const TM E = (TM)P.e;
-      const TM dg = (TM)P.decay_g;
+      TG* G = (TG*)D.g;
+      const typename PR::Ec E = PR::e_const(P.e);
+      const typename PR::Dc dg = PR::d_const(P.decay_g);
       auto issue = [&](int c) {
         const int si = c % kStages;
         const int lo = c * RS, cnt = nrow - lo < RS ? nrow - lo : RS;
+        pending |= 1u << si;
         if (lane == 0) {
           char* st = wbuf + si * ST::kBytes;
           const size_t r0 = (size_t)(sb + lo) * 32;
           mbar_expect_tx(&bar[si], (uint32_t)(cnt * rowb));
           bulk_load(st, D.cvf + r0, cnt * 128, &bar[si]);
           bulk_load(st + o_cm, cmg + r0, cnt * 256, &bar[si]);
-          bulk_load(st + o_g, (const TM*)D.g + r0, cnt * szm, &bar[si]);
+          bulk_load(st + o_g, (const TG*)D.g + r0, cnt * szm, &bar[si]);
           if (calc) {
             bulk_load(st + o_cam, camg + r0, cnt * 256, &bar[si]);
             bulk_load(st + o_c, D.c + r0, cnt * 256, &bar[si]);
@@ -462,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
         __syncwarp();
         issue(0);
       }
-      TM accg = 0, acce = 0;
+      typename PR::Acc acc;
       for (int c = 0; c < nc; ++c) {
         if (c + 1 < nc) {
           fence_async_shared();
@@ -470,8 +459,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           issue(c + 1);
         }
         const int si = c % kStages;
-        if (!mbar_wait(&bar[si], (phase >> si) & 1u)) failed = true;
-        phase ^= 1u << si;
+        if (mbar_wait(&bar[si], (phase >> si) & 1u, wait_limit)) {
+          phase ^= 1u << si;
+          pending &= ~(1u << si);
+        } else {
+          failed = true;
+        }
         if (__any_sync(0xffffffffu, failed)) {
           failed = true;
           break;
@@ -491,10 +484,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           // Eq. late_phase_weight captures the cell's PRP, or that of the
           // synapse's own CV when the PRP diffuses
           const double pz = (stc && A.prp_diff) ? A.prp_cv[elem_of(rb, cvf >> 3, lane)] : prp;
-          TM gv = syn_update<TM>(P, D, e, pre, capre, post, ((const TM*)(st + o_g))[r], cc, wv,
+          TG gv = syn_update<PR>(P, D, e, pre, capre, post, ((const TG*)(st + o_g))[r], cc, wv,
                                  zv, pz, k, dt, A.seed, S);
-          run_sum<TM>(GS, ES, rb, lane, cvf, gv, E, accg, acce);
-          G[e] = gv * dg;
+          // per-CV sums over the run of same-CV synapses, in canonical order
+          // (cvf = (cv << 3) | first-on-CV (1) | run start (2) | run end (4))
+          const uint32_t ce = elem_of(rb, cvf >> 3, lane);
+          if (cvf & 2) acc.start(gv, E, (cvf & 1) != 0, GS, ES, ce);
+          else acc.add(gv, E);
+          if (cvf & 4) acc.store(GS, ES, ce, E);
+          G[e] = PR::decay(gv, dg);
         }
       }
       if (s == A.stc_stream && has_stc) {
@@ -522,6 +520,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
         const int s = c % kStages;
         const int hi = rows - kRowsBack * c, lo = hi > kRowsBack ? hi - kRowsBack : 0;
         const uint32_t cnt = (uint32_t)(hi - lo);
+        pending |= 1u << s;
         if (lane == 0) {
           char* st = wbuf + s * ST::kBytes;
           const size_t r0 = (size_t)(rb + lo);
@@ -556,8 +555,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           issue(c + kStages - 1);
         }
         const int s = c % kStages;
-        if (!mbar_wait(&bar[s], (phase >> s) & 1u)) failed = true;
-        phase ^= 1u << s;
+        if (mbar_wait(&bar[s], (phase >> s) & 1u, wait_limit)) {
+          phase ^= 1u << s;
+          pending &= ~(1u << s);
+        } else {
+          failed = true;
+        }
         if (__any_sync(0xffffffffu, failed)) {
           failed = true;
           break;
@@ -573,8 +576,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           const double dcv = ((const double*)(st + ST::oDC))[r];
           int pi = i - 1;
           if (TREE && i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
-          const double gsv = widen_f32(((const TM*)(st + ST::oGS))[r]);
-          const double esv = widen_f32(((const TM*)(st + ST::oES))[r]);
+          const double gsv = widen_f32(((const TS*)(st + ST::oGS))[r]);
+          const double esv = widen_f32(((const TS*)(st + ST::oES))[r]);
           double d, b;
           if (i == 0) {
             v0_old = v;
@@ -668,6 +671,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
         const int s = c % kStages;
         const int lo = kRowsFwd * c, hi = lo + kRowsFwd < rows ? lo + kRowsFwd : rows;
         const uint32_t cnt = (uint32_t)(hi - lo);
+        pending |= 1u << s;
         if (lane == 0) {
           char* st = wbuf + s * ST::kBytes;
           const size_t r0 = (size_t)(rb + lo);
@@ -691,8 +695,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           issue(c + kStages - 1);
         }
         const int s = c % kStages;
-        if (!mbar_wait(&bar[s], (phase >> s) & 1u)) failed = true;
-        phase ^= 1u << s;
+        if (mbar_wait(&bar[s], (phase >> s) & 1u, wait_limit)) {
+          phase ^= 1u << s;
+          pending &= ~(1u << s);
+        } else {
+          failed = true;
+        }
         if (__any_sync(0xffffffffu, failed)) {
           failed = true;
           break;
@@ -775,9 +783,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
     spiked_prev = A.replay ? (((rbits >> (k - k_begin)) & 1ull) != 0) : spk;
   }
   if (failed) {
-    // a stage never arrived: report it and drain every copy still in flight
+    // a stage did not arrive within the poll limit: report it, then let every
+    // copy this warp issued land (bounded by the full limit) before the warp
+    // leaves, so that no bulk copy still writes into its shared memory.  A
+    // stage's expected parity is unchanged until its wait succeeds.
     if (lane == 0) atomicOr(A.err_flags, 4);
-    for (int s = 0; s < kStages; ++s) mbar_wait(&bar[s], (phase >> s) & 1u);
+    for (int s = 0; s < kStages; ++s)
+      if ((pending >> s) & 1u) mbar_wait(&bar[s], (phase >> s) & 1u, kSpinLimit);
+    __syncwarp();
     return;
   }
   if (n > 0) {
@@ -789,49 +802,25 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
   }
 }
 
-// Steady-state HH gates x_inf = alpha / (alpha + beta) at each soma's v_init.
-template <class TM>
-__global__ void init_gates_kernel(const double* v, double* gate, int64_t n_lanes,
-                                  const uint8_t* is_hh) {
-  const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (L >= n_lanes || !is_hh[L]) return;
-  double am, bm, ah, bh, an, bn;
-  HH64::rates(v[L], am, bm, ah, bh, an, bn);
-  gate[L] = am / (am + bm);
-  gate[n_lanes + L] = ah / (ah + bh);
-  gate[2 * n_lanes + L] = an / (an + bn);
-}
-
-template <class TM>
-int launch_init_gates_impl(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
-                           void* stream) {
-  if (n_lanes == 0) return 0;
-  const int threads = 128;
-  const int blocks = (int)((n_lanes + threads - 1) / threads);
-  init_gates_kernel<TM><<<blocks, threads, 0, (cudaStream_t)stream>>>(v, (double*)gate, n_lanes,
-                                                                      is_hh);
-  return (int)cudaGetLastError();
-}
-
-template <class TM, bool TREE, int RB, int RF, int WPB, int MB, int SB>
+template <class PR, bool TREE, int RB, int RF, int WPB, int MB, int SB>
 int launch_epoch_t(const EpochArgs& a, void* stream) {
   constexpr int warps_per_block = WPB;
   const int threads = 32 * warps_per_block;
   const int64_t warps = a.n_narrow;
   const int blocks = (int)((warps * 32 + threads - 1) / threads);
   if (blocks == 0) return 0;
-  const int smem = warps_per_block * Stage<TM, TREE, RB, RF, SB>::kWarpBytes;
+  const int smem = warps_per_block * Stage<PR, TREE, RB, RF, SB>::kWarpBytes;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
   static bool attr_set[64] = {false};  // per device; setting it twice is harmless
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(epoch_kernel<TM, TREE, RB, RF, 32 * WPB, MB, SB>,
+    e = cudaFuncSetAttribute(epoch_kernel<PR, TREE, RB, RF, 32 * WPB, MB, SB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  epoch_kernel<TM, TREE, RB, RF, 32 * WPB, MB, SB>
+  epoch_kernel<PR, TREE, RB, RF, 32 * WPB, MB, SB>
       <<<blocks, threads, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
@@ -844,26 +833,26 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // per chunk and 8 entries (many nested forks), FP64 shapes 3 and 4 take 4 rows
 // and 2 entries, the mixed shapes 4 rows and 6 entries; shape 5 has no stacks
 // (trees with long branches and few forks); 12 warps per SM fit in each case.
-template <class TM, bool TREE>
+template <class PR, bool TREE>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
-  constexpr bool f64tree = TREE && sizeof(TM) == 8;
+  constexpr bool f64tree = TREE && sizeof(typename PR::S) == 8;
   constexpr int RB0 = f64tree ? 3 : 4, SB0 = f64tree ? 8 : 6;
   constexpr int RB6 = f64tree ? 5 : 6;
   constexpr int SB4 = f64tree ? 2 : 6;
   switch (shape) {
-    case 1: return launch_epoch_t<TM, TREE, 3, 9, 4, 4, 8>(a, stream);    // 16 warps per SM
-    case 2: return launch_epoch_t<TM, TREE, RB6, 16, 2, 4, 8>(a, stream); // 8 warps, long chunks
-    case 3: return launch_epoch_t<TM, TREE, 4, 12, 2, 6, SB4>(a, stream); // 2-warp blocks
-    case 4: return launch_epoch_t<TM, TREE, 4, 12, 1, 12, SB4>(a, stream);// 1-warp blocks
-    case 5: return launch_epoch_t<TM, TREE, 4, 12, 4, 3, 0>(a, stream);   // trees: no stacks
-    default: return launch_epoch_t<TM, TREE, RB0, 12, 4, 3, SB0>(a, stream);  // 12 warps per SM
+    case 1: return launch_epoch_t<PR, TREE, 3, 9, 4, 4, 8>(a, stream);    // 16 warps per SM
+    case 2: return launch_epoch_t<PR, TREE, RB6, 16, 2, 4, 8>(a, stream); // 8 warps, long chunks
+    case 3: return launch_epoch_t<PR, TREE, 4, 12, 2, 6, SB4>(a, stream); // 2-warp blocks
+    case 4: return launch_epoch_t<PR, TREE, 4, 12, 1, 12, SB4>(a, stream);// 1-warp blocks
+    case 5: return launch_epoch_t<PR, TREE, 4, 12, 4, 3, 0>(a, stream);   // trees: no stacks
+    default: return launch_epoch_t<PR, TREE, RB0, 12, 4, 3, SB0>(a, stream);  // 12 warps per SM
   }
 }
 
-template <class TM>
+template <class PR>
 int launch_epoch_impl(const EpochArgs& a, bool tree, int shape, void* stream) {
-  return tree ? launch_epoch_shape<TM, true>(a, shape, stream)
-              : launch_epoch_shape<TM, false>(a, shape, stream);
+  return tree ? launch_epoch_shape<PR, true>(a, shape, stream)
+              : launch_epoch_shape<PR, false>(a, shape, stream);
 }
 
 }  // namespace pa

@@ -19,12 +19,18 @@
 namespace pa {
 namespace {
 
-__global__ void ff_decay_kernel(StreamDev D, double decay_g, double decay_c, bool mixed) {
+// prec: 0 = FP64 conductances, 1 = float-float (hi, lo), 2 = FP32
+__global__ void ff_decay_kernel(StreamDev D, double decay_g, double decay_c, int prec) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < D.n_elem;
        e += (int64_t)gridDim.x * blockDim.x) {
-    if (mixed) {
+    if (prec == 2) {
       float* g = (float*)D.g;
       g[e] = (float)((double)g[e] * decay_g);
+    } else if (prec == 1) {
+      float2* g = (float2*)D.g;
+      const double v = ((double)g[e].x + (double)g[e].y) * decay_g;
+      const float hi = (float)v;
+      g[e] = make_float2(hi, (float)(v - (double)hi));
     } else {
       double* g = (double*)D.g;
       g[e] = g[e] * decay_g;
@@ -93,14 +99,14 @@ __global__ void ff_slow_kernel(const EpochArgs A, const FastForward F) {
 
 }  // namespace
 
-int launch_fast_forward(const EpochArgs& a, const FastForward& f, bool mixed, void* stream) {
+int launch_fast_forward(const EpochArgs& a, const FastForward& f, int prec, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   for (int s = 0; s < a.n_streams; ++s) {
     const int64_t ne = a.sd[s].n_elem;
     if (ne == 0) continue;
     int blocks = (int)((ne + 255) / 256);
     if (blocks > 148 * 16) blocks = 148 * 16;
-    ff_decay_kernel<<<blocks, 256, 0, st>>>(a.sd[s], f.decay_g[s], f.decay_c[s], mixed);
+    ff_decay_kernel<<<blocks, 256, 0, st>>>(a.sd[s], f.decay_g[s], f.decay_c[s], prec);
   }
   if (a.n_lanes > 0) {
     const int blocks = (int)((a.n_lanes + 127) / 128);

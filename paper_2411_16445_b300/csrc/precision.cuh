@@ -1,0 +1,216 @@
+// precision.cuh -- the arithmetic policies of the time-step kernels.
+//
+// A policy fixes how the synaptic conductances g (the exponential synapse's
+// state, decayed every step by the exact factor exp(-dt/tau)), the event
+// weights, the STDP traces and the per-CV synaptic sums (the synapses' share
+// of the backward-Euler row of Eq. cable) are stored and computed.  The cable
+// coefficients, the assembly, the Hines solve, the voltage, HH, calcium and
+// the slow plasticity state (GB w, STC h/z/p, STDP w) are FP64 in every
+// policy.
+//
+//   PrecF64  (PA_FP64)  everything FP64, operation for operation the plain
+//                       definition (bit-identical to the FP64 oracle);
+//   PrecMix  (PA_MIXED) g is an unevaluated sum of two floats (float-float,
+//                       about 48 significand bits) decayed and summed on the
+//                       FP32 pipes; STDP traces FP32; event weights FP64 (read
+//                       at events only); each run of same-CV synapses is summed
+//                       in float-float and turned into the FP64 per-CV sums by
+//                       one FP64 addition, g E by one FP64 product;
+//   PrecF32  (PA_FP32)  g, weights, traces and the per-CV sums plain FP32.
+//
+// Why the conductance path needs more than FP32 in PA_MIXED (measured with a
+// CPU emulation of each variant against the FP64 oracle, recurrent tagging-
+// and-capture network at dt = 0.2 ms, open loop): a stored FP32 conductance
+// is re-rounded every step, and those errors random-walk over the hundreds of
+// steps a conductance lives; on an HH soma near threshold the resulting
+// voltage noise moves interpolated crossings by up to 7e-3 ms.  Even a single
+// static rounding of every event weight to FP32 moves them by 2e-3 ms, and
+// per-CV sums rounded to FP32 each step by up to 1e-3 ms.  Float-float keeps
+// the per-step rounding near 2^-47 while the work stays off the FP64 pipe,
+// which issues 1/64 of the FP32 rate on this GPU.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "int_arith.cuh"
+
+namespace pa {
+
+// ---------------------------------------------------------------------------
+// Float-float arithmetic.  Error-free transformations: TwoSum (Knuth), Fast2Sum
+// (Dekker; needs |a| >= |b| or a = 0) and the FMA-based exact product.  Spelled
+// with explicitly rounded intrinsics so that no contraction alters them.
+__device__ __forceinline__ float2 ff_fast2sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_twosum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, err);
+}
+// a + b of two normalised float-float values
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float2 s = ff_twosum(a.x, b.x);
+  return ff_fast2sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+// a + b without the final normalisation (a running sum over a short run of
+// synapses: lo collects the exact rounding errors of the hi additions and the
+// lo parts; it is normalised once, when the run is turned into FP64)
+__device__ __forceinline__ float2 ff_add_acc(float2 a, float2 b) {
+  const float2 s = ff_twosum(a.x, b.x);
+  return make_float2(s.x, __fadd_rn(a.y, __fadd_rn(b.y, s.y)));
+}
+// a * c with the constant c = ch + cl given as two floats
+__device__ __forceinline__ float2 ff_mul(float2 a, float ch, float cl) {
+  const float p = __fmul_rn(a.x, ch);
+  float e = __fmaf_rn(a.x, ch, -p);
+  e = __fmaf_rn(a.x, cl, e);
+  e = __fmaf_rn(a.y, ch, e);
+  return ff_fast2sum(p, e);
+}
+// a double split into the nearest float and the float nearest the remainder
+__device__ __forceinline__ float2 ff_from_d(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(__dsub_rn(x, (double)h)));
+}
+// hi + lo in FP64: exact widening of both parts on the integer pipes, one FP64
+// addition (exact while the parts' exponents differ by at most 29)
+__device__ __forceinline__ double ff_to_d(float2 a) {
+  return __dadd_rn(widen_f32(a.x), widen_f32(a.y));
+}
+
+// Sums of plain numbers, never contracted: both cell bins (and any compiler
+// schedule) produce the same values.
+__device__ __forceinline__ float tm_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float tm_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double tm_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double tm_add(double a, double b) { return __dadd_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// Per-CV sum accumulators over one run of same-CV synapses of a stream, in the
+// canonical synapse order.  start() opens the run with its first synapse (from
+// zero on the CV's first run of the step, else continuing the sums an earlier
+// stream left); add() takes the next synapse; store() writes the CV's sums.
+template <class T>
+struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
+  T g, e;
+  __device__ __forceinline__ void start(T gv, T E, bool first, const T* gs, const T* es,
+                                        uint32_t ce) {
+    const T ge = tm_mul(gv, E);
+    if (first) {
+      g = gv;
+      e = ge;
+    } else {
+      g = tm_add(gs[ce], gv);
+      e = tm_add(es[ce], ge);
+    }
+  }
+  __device__ __forceinline__ void add(T gv, T E) {
+    const T ge = tm_mul(gv, E);
+    g = tm_add(g, gv);
+    e = tm_add(e, ge);
+  }
+  __device__ __forceinline__ void store(T* gs, T* es, uint32_t ce, T) const {
+    gs[ce] = g;
+    es[ce] = e;
+  }
+  __device__ __forceinline__ AccPlain shfl(int src) const {
+    AccPlain r;
+    r.g = __shfl_sync(0xffffffffu, g, src);
+    r.e = __shfl_sync(0xffffffffu, e, src);
+    return r;
+  }
+};
+
+struct AccFF {  // mixed: the run's conductance in float-float, FP64 at its end
+  float2 g;
+  bool first;
+  __device__ __forceinline__ void start(float2 gv, double, bool first_on_cv, const double*,
+                                        const double*, uint32_t) {
+    g = gv;
+    first = first_on_cv;
+  }
+  __device__ __forceinline__ void add(float2 gv, double) { g = ff_add_acc(g, gv); }
+  __device__ __forceinline__ void store(double* gs, double* es, uint32_t ce, double E) const {
+    const double s = ff_to_d(g);
+    const double se = __dmul_rn(s, E);
+    if (first) {
+      gs[ce] = s;
+      es[ce] = se;
+    } else {
+      gs[ce] = __dadd_rn(gs[ce], s);
+      es[ce] = __dadd_rn(es[ce], se);
+    }
+  }
+  __device__ __forceinline__ AccFF shfl(int src) const {
+    AccFF r;
+    r.g.x = __shfl_sync(0xffffffffu, g.x, src);
+    r.g.y = __shfl_sync(0xffffffffu, g.y, src);
+    r.first = __shfl_sync(0xffffffffu, (int)first, src) != 0;
+    return r;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The policies.  G: conductance element; W: event weight element; T: STDP
+// trace element; S: per-CV sum element; Ec / Dc: the stream's reversal
+// potential and decay factor as the policy uses them.
+struct PrecF64 {
+  using G = double;
+  using W = double;
+  using T = double;
+  using S = double;
+  using Ec = double;
+  using Dc = double;
+  using Acc = AccPlain<double>;
+  static constexpr int kId = 0;
+  __device__ static __forceinline__ Ec e_const(double e) { return e; }
+  __device__ static __forceinline__ Dc d_const(double d) { return d; }
+  __device__ static __forceinline__ G add_w(G g, W w) { return g + w; }
+  __device__ static __forceinline__ G add_d(G g, double x) { return g + x; }
+  __device__ static __forceinline__ G decay(G g, Dc d) { return g * d; }
+  __device__ static __forceinline__ G zero() { return 0.0; }
+  __device__ static __forceinline__ G shfl(G g, int src) { return __shfl_sync(0xffffffffu, g, src); }
+};
+
+struct PrecMix {
+  using G = float2;
+  using W = double;
+  using T = float;
+  using S = double;
+  using Ec = double;
+  using Dc = float2;  // exp(-dt/tau) as hi + lo
+  using Acc = AccFF;
+  static constexpr int kId = 1;
+  __device__ static __forceinline__ Ec e_const(double e) { return e; }
+  __device__ static __forceinline__ Dc d_const(double d) { return ff_from_d(d); }
+  __device__ static __forceinline__ G add_w(G g, W w) { return ff_add(g, ff_from_d(w)); }
+  __device__ static __forceinline__ G add_d(G g, double x) { return ff_add(g, ff_from_d(x)); }
+  __device__ static __forceinline__ G decay(G g, Dc d) { return ff_mul(g, d.x, d.y); }
+  __device__ static __forceinline__ G zero() { return make_float2(0.0f, 0.0f); }
+  __device__ static __forceinline__ G shfl(G g, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, g.x, src), __shfl_sync(0xffffffffu, g.y, src));
+  }
+};
+
+struct PrecF32 {
+  using G = float;
+  using W = float;
+  using T = float;
+  using S = float;
+  using Ec = float;
+  using Dc = float;
+  using Acc = AccPlain<float>;
+  static constexpr int kId = 2;
+  __device__ static __forceinline__ Ec e_const(double e) { return (float)e; }
+  __device__ static __forceinline__ Dc d_const(double d) { return (float)d; }
+  __device__ static __forceinline__ G add_w(G g, W w) { return __fadd_rn(g, w); }
+  __device__ static __forceinline__ G add_d(G g, double x) { return __fadd_rn(g, (float)x); }
+  __device__ static __forceinline__ G decay(G g, Dc d) { return __fmul_rn(g, d); }
+  __device__ static __forceinline__ G zero() { return 0.0f; }
+  __device__ static __forceinline__ G shfl(G g, int src) { return __shfl_sync(0xffffffffu, g, src); }
+};
+
+}  // namespace pa

@@ -1,0 +1,11 @@
+// step_fp32.cu -- the FP32-synapse instantiation of the epoch kernels
+// (PA_FP32): synaptic conductances, event weights, STDP traces and the per-CV
+// synaptic sums in plain FP32; everything else as in PA_MIXED.
+#include "epoch_kernel.cuh"
+#include "wide_kernel.cuh"
+
+namespace pa {
+int launch_epoch_fp32(const EpochArgs& a, bool tree, int shape, void* stream, const SideLaunch* side) {
+  return launch_bins<PrecF32>(a, tree, shape, stream, side);
+}
+}  // namespace pa

@@ -32,8 +32,10 @@
 
 namespace pa {
 
-template <class TM>
+template <class PR>
 __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
+  using TS = typename PR::S;
+  using TG = typename PR::G;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -51,8 +53,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   const double* __restrict__ DC = A.dc;
   const double* __restrict__ EM = A.em;
   const double* __restrict__ AA = A.a;
-  TM* __restrict__ GS = (TM*)A.gs;
-  TM* __restrict__ ES = (TM*)A.es;
+  TS* __restrict__ GS = (TS*)A.gs;
+  TS* __restrict__ ES = (TS*)A.es;
   double* __restrict__ F = A.f;
   double* __restrict__ XP = A.xp;
   const int16_t* __restrict__ PAR = A.par;
@@ -96,15 +98,15 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
       const bool stc = P.kind == SK_STC;
       const uint64_t* cmg = D.cmask + (int64_t)slot * D.n_elem;
       const uint64_t* camg = calc ? D.camask + (int64_t)slot * D.n_elem : nullptr;
-      TM* G = (TM*)D.g;
-      const TM E = (TM)P.e;
-      const TM dg = (TM)P.decay_g;
-      TM carry_g = 0, carry_e = 0;  // sums of the run crossing into the next row
+      TG* G = (TG*)D.g;
+      const typename PR::Ec E = PR::e_const(P.e);
+      const typename PR::Dc dg = PR::d_const(P.decay_g);
+      typename PR::Acc carry;  // sums of the run crossing into the next row
       for (int t = 0; t < nrow; ++t) {
         const uint32_t e = ((uint32_t)(sb + t) << 5) | (uint32_t)lane;
         const int32_t cvf = D.cvf[e];
         const bool valid = cvf >= 0;  // padding only after the cell's last synapse
-        TM gv = 0;
+        TG gv = PR::zero();
         double sadd = 0.0;
         if (valid) {
           const bool pre = (cmg[e] >> kk) & 1ull;
@@ -114,15 +116,15 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           const double zv = stc ? D.z[e] : 0.0;
           // Eq. late_phase_weight with the cell's PRP, or that of the synapse's CV
           const double pz = (stc && A.prp_diff) ? A.prp_cv[e0 + (cvf >> 3)] : prp;
-          gv = syn_update<TM>(P, D, e, pre, capre, post, G[e], cc, wv, zv, pz, k, dt, A.seed,
+          gv = syn_update<PR>(P, D, e, pre, capre, post, G[e], cc, wv, zv, pz, k, dt, A.seed,
                               sadd);
-          G[e] = gv * dg;
+          G[e] = PR::decay(gv, dg);
         }
-        // Per-CV sums in canonical order (run_sum's arithmetic): each lane sums
-        // its run from the run's first synapse in this row up to itself, in
-        // order, reading the values by shuffle; a run that crosses rows
-        // continues from the last lane's sums of the previous row.
-        const TM ge = tm_mul(gv, E);
+        // Per-CV sums in canonical order (the narrow kernel's accumulator
+        // arithmetic): each lane sums its run from the run's first synapse in
+        // this row up to itself, in order, reading the values by shuffle; a run
+        // that crosses rows continues from the last lane's sums of the previous
+        // row.
         const unsigned smask = __ballot_sync(full, valid && (cvf & 2));
         const unsigned upto = lane == 31 ? full : ((2u << lane) - 1u);
         const unsigned mm = smask & upto;
@@ -131,29 +133,22 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         const int len = valid ? lane - src0 + 1 : 0;
         const int maxlen = (int)__reduce_max_sync(full, (unsigned)len);
         const int32_t cs = __shfl_sync(full, cvf, src0);
-        TM acc = __shfl_sync(full, gv, src0), ace = __shfl_sync(full, ge, src0);
+        const TG g0 = PR::shfl(gv, src0);
+        typename PR::Acc acc;
         if (seg0 < 0) {
-          acc = tm_add(carry_g, acc);
-          ace = tm_add(carry_e, ace);
-        } else if (valid && !(cs & 1)) {
-          const int64_t cs_e = e0 + (cs >> 3);  // continues the sums of earlier streams
-          acc = tm_add(GS[cs_e], acc);
-          ace = tm_add(ES[cs_e], ace);
+          acc = carry;
+          acc.add(g0, E);
+        } else {
+          // continues the sums of earlier streams unless first on its CV
+          acc.start(g0, E, !valid || (cs & 1), GS, ES, (uint32_t)(e0 + (cs >> 3)));
         }
         for (int it = 1; it < maxlen; ++it) {
           const int src = src0 + it < 31 ? src0 + it : 31;
-          const TM gi = __shfl_sync(full, gv, src), ei = __shfl_sync(full, ge, src);
-          if (it < len) {
-            acc = tm_add(acc, gi);
-            ace = tm_add(ace, ei);
-          }
+          const TG gi = PR::shfl(gv, src);
+          if (it < len) acc.add(gi, E);
         }
-        if (valid && (cvf & 4)) {
-          GS[e0 + (cvf >> 3)] = acc;
-          ES[e0 + (cvf >> 3)] = ace;
-        }
-        carry_g = __shfl_sync(full, acc, 31);
-        carry_e = __shfl_sync(full, ace, 31);
+        if (valid && (cvf & 4)) acc.store(GS, ES, (uint32_t)(e0 + (cvf >> 3)), E);
+        carry = acc.shfl(31);
         if (stc) {
           // the cell's S = sum |h - h0| over its STC synapses, in order
 #pragma unroll 1
@@ -184,7 +179,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         // elimination
         double nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be], nem = EM[e0 + be],
                na = AA[e0 + be];
-        TM ngs = GS[e0 + be], nes = ES[e0 + be];
+        TS ngs = GS[e0 + be], nes = ES[e0 + be];
         int noch = PAR ? OCH[e0 + be] : -1;
         for (int i = be; i >= bs; --i) {
           const int64_t ei = e0 + i;
@@ -397,31 +392,31 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   }
 }
 
-template <class TM>
+template <class PR>
 int launch_wide_impl(const EpochArgs& a, void* stream) {
   if (a.n_wide <= 0) return 0;
   const int threads = 128;
   const int blocks = (int)(((int64_t)a.n_wide * 32 + threads - 1) / threads);
-  wide_kernel<TM><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
+  wide_kernel<PR><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 
 // Both cell bins of one epoch (see SideLaunch).
-template <class TM>
+template <class PR>
 int launch_bins(const EpochArgs& a, bool tree, int shape, void* stream, const SideLaunch* side) {
   if (side && a.n_narrow > 0 && a.n_wide > 0) {
     cudaStream_t s0 = (cudaStream_t)stream, s1 = (cudaStream_t)side->stream;
     cudaError_t e = cudaEventRecord((cudaEvent_t)side->fork, s0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, (cudaEvent_t)side->fork, 0);
     if (e != cudaSuccess) return (int)e;
-    int rc = launch_epoch_impl<TM>(a, tree, shape, stream);
-    if (rc == 0) rc = launch_wide_impl<TM>(a, side->stream);
+    int rc = launch_epoch_impl<PR>(a, tree, shape, stream);
+    if (rc == 0) rc = launch_wide_impl<PR>(a, side->stream);
     e = cudaEventRecord((cudaEvent_t)side->join, s1);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, (cudaEvent_t)side->join, 0);
     return rc ? rc : (int)e;
   }
-  const int rc = launch_epoch_impl<TM>(a, tree, shape, stream);
-  return rc ? rc : launch_wide_impl<TM>(a, stream);
+  const int rc = launch_epoch_impl<PR>(a, tree, shape, stream);
+  return rc ? rc : launch_wide_impl<PR>(a, stream);
 }
 
 }  // namespace pa

@@ -16,17 +16,19 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libplasticarbor.so")
 
-PA_FP64, PA_MIXED = 0, 1
+PA_FP64, PA_MIXED, PA_FP32 = 0, 1, 2
 PA_SRC_POISSON = -1
 FIELD_G, FIELD_C, FIELD_W, FIELD_H, FIELD_Z, FIELD_APRE, FIELD_APOST = range(7)
 FIELD_V, FIELD_PRP, FIELD_GATES, FIELD_PRP_CV, FIELD_CA_CV = 16, 17, 18, 19, 20
 ERRORS = {-1: "PA_ERR_ARG", -2: "PA_ERR_OOM", -3: "PA_ERR_CUDA", -4: "PA_ERR_TIMEOUT",
           -5: "PA_ERR_CAPACITY", -6: "PA_ERR_STATE"}
 
-EXPORTED = ("pa_build_model", "pa_advance", "pa_advance_noalloc", "pa_sync", "pa_read_probes", "pa_read_spikes",
+EXPORTED = ("pa_build_model", "pa_advance", "pa_advance_noalloc", "pa_sync", "pa_set_wait_limit",
+            "pa_read_probes", "pa_read_spikes",
             "pa_read_weights", "pa_read_state", "pa_set_replay", "pa_model_info",
             "pa_get_kernel_stats", "pa_reset_kernel_stats", "pa_get_tuning", "pa_free_model",
-            "pa_check_arith", "pa_write_state", "pa_fast_forward", "pa_last_error")
+            "pa_check_arith", "pa_measure_fp64", "pa_write_state", "pa_fast_forward",
+            "pa_last_error")
 
 
 class PaError(RuntimeError):
@@ -158,6 +160,7 @@ def lib():
         L.pa_advance.argtypes = [P, C.c_double, C.c_double]
         L.pa_advance_noalloc.argtypes = [P, C.c_double, C.c_double]
         L.pa_sync.argtypes = [P]
+        L.pa_set_wait_limit.argtypes = [P, C.c_uint32]
         L.pa_read_probes.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.pa_read_spikes.argtypes = [P, P, P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.pa_read_weights.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
@@ -168,6 +171,7 @@ def lib():
         L.pa_reset_kernel_stats.argtypes = [P]
         L.pa_get_tuning.argtypes = [P, C.POINTER(C.c_int32), P, C.c_int32]
         L.pa_check_arith.argtypes = [C.c_int32, C.c_uint64, C.c_int64, P]
+        L.pa_measure_fp64.argtypes = [C.c_int32, P]
         L.pa_write_state.argtypes = [P, C.c_int32, P, C.c_int64]
         L.pa_fast_forward.argtypes = [P, C.c_double, C.c_int64]
         L.pa_free_model.argtypes = [P]
@@ -193,6 +197,13 @@ def check_arith(device: int = 0, seed: int = 1, n_random: int = 1 << 30) -> dict
     _check(lib().pa_check_arith(device, seed, n_random, _ptr(out)))
     return {"rcp_mismatch": int(out[0]), "widen_mismatch": int(out[1]),
             "checked": int(out[2]), "first_bad_rcp_bits": int(out[3])}
+
+
+def measure_fp64(device: int = 0) -> dict:
+    """pa_measure_fp64: the GPU's FP64 FMA throughput (FMA/s) and the best run's ms."""
+    out = np.zeros(2)
+    _check(lib().pa_measure_fp64(device, _ptr(out)))
+    return {"fma_per_s": float(out[0]), "ms": float(out[1])}
 
 
 def current_stream_handle(device: int = 0):
@@ -279,6 +290,10 @@ class Model:
 
     def sync(self):
         _check(lib().pa_sync(self._h))
+
+    def set_wait_limit(self, polls: int):
+        """pa_set_wait_limit: polls of the bounded row-staging waits (0: default)."""
+        _check(lib().pa_set_wait_limit(self._h, int(polls)))
 
     def read_probes(self, n_probe: int) -> np.ndarray:
         n = C.c_int64()

@@ -200,3 +200,26 @@ def compare(a, b):
     if a.size == 0:
         return 0.0
     return float(np.max(np.abs(a - b)))
+
+
+def hca_tree_net():
+    """HCA synapses on random trees of a small recurrent network (40 HH cells of
+    8-50 dendritic CVs, 300 network and 60 Poisson HCA synapses, somatic Poisson
+    drive)."""
+    dt = 0.025
+    b = W._Builder(dt, 31, "hca_trees")
+    rng = np.random.default_rng(31)
+    hh = b.mech(W.HH, W.hh_params())
+    pas = b.mech(W.PAS, W.pas_params())
+    drive = b.mech(W.EXPSYN, W.expsyn_params(2.0, 0.0))
+    hca = b.mech(W.HCA, W.hca_params(d=0.5, tau_c=40.0, i0=6.0))
+    sizes = rng.integers(8, 50, 40)
+    for c in range(40):
+        b.cells_add(1, b.morph(W.random_binary_tree(rng, int(sizes[c]))), hh, pas)
+    b.connect(W.SRC_POISSON, np.arange(40), 0, drive, 0.08, rate=40.0)
+    src = rng.integers(0, 40, 300)
+    dst = rng.integers(0, 40, 300)
+    cv = (rng.random(300) * (sizes[dst] + 1)).astype(int)
+    b.connect(src, dst, cv, hca, 1.0, delay=1.0)
+    b.connect(W.SRC_POISSON, dst[:60], cv[:60], hca, 1.0, rate=30.0)
+    return b.build()
