@@ -345,6 +345,19 @@ int pa_read_state(pa_model* m, int32_t field, double* out, int64_t cap, int64_t*
  * still detected and recorded. */
 int pa_set_replay(pa_model* m, int64_t n, const int32_t* gid, const int64_t* step);
 
+/* Spikes of cells simulated elsewhere -- the exchange step of a network
+ * sharded over several GPUs (one model per GPU, each holding its own cells
+ * plus passive stand-ins for remote presynaptic cells; the paper runs Arbor
+ * with one MPI rank per GPU, Sec. "Runtime and memory benchmarking with
+ * large-scale networks").  Cell gid[i] of this model is taken to have spiked in
+ * step step[i], which must lie in the last epoch, [current step - E, current
+ * step) with E = pa_info.epoch_steps: every connection's delay is at least E,
+ * so each of its events is still due.  The events are routed through the
+ * model's connection table exactly as for a spike detected here (the delayed
+ * calcium targets included); POST_EVENT is not triggered.  Not in open-loop
+ * replay.  Synchronises the model's stream. */
+int pa_inject_spikes(pa_model* m, int64_t n, const int32_t* gid, const int64_t* step);
+
 int pa_model_info(const pa_model* m, pa_info* info);
 
 /* Writes a state field (the inverse of pa_read_state, same layout and count):

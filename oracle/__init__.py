@@ -28,6 +28,7 @@ def lib():
                                 + [C.c_double, C.c_uint64, C.c_int32, P, P, P])
         L.orc_run.argtypes = [P, C.c_int64]
         L.orc_set_replay.argtypes = [P, C.c_int64, P, P]
+        L.orc_inject_spikes.argtypes = [P, C.c_int64, P, P]
         for fn in ("orc_n_spikes", "orc_n_cv", "orc_n_probe_samples", "orc_step_count"):
             getattr(L, fn).restype = C.c_int64
             getattr(L, fn).argtypes = [P]
@@ -119,6 +120,13 @@ class Oracle:
         gid = np.ascontiguousarray(gid, dtype=np.int32)
         step = np.ascontiguousarray(step, dtype=np.int64)
         if lib().orc_set_replay(self._h, len(gid), _p(gid), _p(step)) != 0:
+            raise ValueError(lib().orc_last_error().decode())
+
+    def inject_spikes(self, gid, step):
+        """Spikes of cells simulated elsewhere (past steps; their events still due)."""
+        gid = np.ascontiguousarray(gid, dtype=np.int32)
+        step = np.ascontiguousarray(step, dtype=np.int64)
+        if lib().orc_inject_spikes(self._h, len(gid), _p(gid), _p(step)) != 0:
             raise ValueError(lib().orc_last_error().decode())
 
     def run(self, n_steps: int):

@@ -790,6 +790,23 @@ int orc_set_replay(orc_model* M, int64_t n, const int32_t* gid, const int64_t* s
   return 0;
 }
 
+/* Spikes of cells simulated elsewhere (a shard's stubs for remote presynaptic
+   cells): cell gid[i] spiked in step step[i], a past step of the last epoch,
+   so that every event it sends is still due (step + delay >= the current
+   step).  The events are queued exactly as for a spike detected here. */
+static void queue_spike_events(orc_model* M, int32_t gid, int64_t k);
+int orc_inject_spikes(orc_model* M, int64_t n, const int32_t* gid, const int64_t* step) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (gid[i] < 0 || gid[i] >= M->n_cells) return fail(-1, "inject: gid %d out of range", gid[i]);
+    if (step[i] >= M->step) return fail(-1, "inject: spike step %lld is not in the past", (long long)step[i]);
+    for (int64_t e = M->out_off[gid[i]]; e < M->out_off[gid[i] + 1]; ++e)
+      if (step[i] + M->syn_D[M->out_syn[e]] < M->step)
+        return fail(-1, "inject: an event of the spike in step %lld is already overdue", (long long)step[i]);
+  }
+  for (int64_t i = 0; i < n; ++i) queue_spike_events(M, gid[i], step[i]);
+  return 0;
+}
+
 /* STDP trace value at step k: exact decay since its last jump (Eqs. stdp_ode_1-2
    without spikes in between) */
 static double trace_at(double a, int64_t k_last, int64_t k, double dt, double tau) {

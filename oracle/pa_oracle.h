@@ -93,6 +93,8 @@ int orc_build(int32_t n_cells, const int32_t* cell_morph, const int32_t* cell_so
  * POST_EVENT notifications (open-loop replay): gid[i] spiked in step step[i].
  * The cells still detect and record their own spikes. */
 int orc_set_replay(orc_model* m, int64_t n, const int32_t* gid, const int64_t* step);
+/* spikes of cells simulated elsewhere, in past steps whose events are still due */
+int orc_inject_spikes(orc_model* m, int64_t n, const int32_t* gid, const int64_t* step);
 
 int orc_run(orc_model* m, int64_t n_steps);
 int64_t orc_step_count(const orc_model* m);

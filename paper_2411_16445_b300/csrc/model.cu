@@ -2100,6 +2100,46 @@ int pa_set_replay(pa_model* M, int64_t n, const int32_t* gid, const int64_t* ste
   return PA_OK;
 }
 
+int pa_inject_spikes(pa_model* M, int64_t n, const int32_t* gid, const int64_t* step) {
+  using namespace pa;
+  if (!M || n < 0 || (n > 0 && (!gid || !step))) return set_err(PA_ERR_ARG, "bad spike arguments");
+  if (M->replay) return set_err(PA_ERR_STATE, "pa_inject_spikes does not run in open-loop replay");
+  for (int64_t i = 0; i < n; ++i) {
+    if (gid[i] < 0 || gid[i] >= M->n_cells)
+      return set_err(PA_ERR_ARG, "spike %lld: gid %d out of range", (long long)i, gid[i]);
+    if (step[i] >= M->step || step[i] < M->step - M->E)
+      return set_err(PA_ERR_ARG, "spike %lld: step %lld outside the last epoch [%lld, %lld)",
+                     (long long)i, (long long)step[i], (long long)(M->step - M->E),
+                     (long long)M->step);
+  }
+  if (n == 0) return PA_OK;
+  CUDA_TRY(cudaSetDevice(M->device));
+  // through the replay spike buffers, max_spikes at a time, routed like the
+  // model's own spikes (every connection's delay is at least one epoch, so
+  // each event lands at or after the current step)
+  RouteArgs RA = M->ra;
+  RA.spk_count = M->rep_spk_count;
+  RA.spk_gid = M->rep_spk_gid;
+  RA.spk_step = M->rep_spk_step;
+  std::vector<int32_t> g32, s32;
+  for (int64_t off = 0; off < n; off += M->max_spikes) {
+    const int32_t cnt = (int32_t)std::min<int64_t>(n - off, M->max_spikes);
+    g32.assign(gid + off, gid + off + cnt);
+    s32.resize(cnt);
+    for (int32_t j = 0; j < cnt; ++j) s32[j] = (int32_t)step[off + j];
+    CUDA_TRY(cudaMemcpyAsync(M->rep_spk_gid, g32.data(), 4 * (size_t)cnt, cudaMemcpyHostToDevice, M->stream));
+    CUDA_TRY(cudaMemcpyAsync(M->rep_spk_step, s32.data(), 4 * (size_t)cnt, cudaMemcpyHostToDevice, M->stream));
+    CUDA_TRY(cudaMemcpyAsync(M->rep_spk_count, &cnt, 4, cudaMemcpyHostToDevice, M->stream));
+    int rc = launch_route(RA, cnt, M->stream);
+    if (rc) return set_err(PA_ERR_CUDA, "route launch: %s", cudaGetErrorString((cudaError_t)rc));
+    M->n_kernel_launches++;
+    // the host buffers are reused: wait for the copies (and the routing) to finish
+    CUDA_TRY(cudaStreamSynchronize(M->stream));
+  }
+  CUDA_TRY(cudaMemsetAsync(M->rep_spk_count, 0, 4, M->stream));
+  return PA_OK;
+}
+
 int pa_model_info(const pa_model* M, pa_info* info) {
   if (!M || !info) return set_err(PA_ERR_ARG, "NULL argument");
   info->n_cells = M->n_cells;

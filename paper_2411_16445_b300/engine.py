@@ -28,6 +28,7 @@ EXPORTED = ("pa_build_model", "pa_advance", "pa_advance_noalloc", "pa_sync", "pa
             "pa_read_weights", "pa_read_state", "pa_set_replay", "pa_model_info",
             "pa_get_kernel_stats", "pa_reset_kernel_stats", "pa_get_tuning", "pa_free_model",
             "pa_check_arith", "pa_measure_fp64", "pa_write_state", "pa_fast_forward",
+            "pa_inject_spikes",
             "pa_last_error")
 
 
@@ -166,6 +167,7 @@ def lib():
         L.pa_read_weights.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.pa_read_state.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         L.pa_set_replay.argtypes = [P, C.c_int64, P, P]
+        L.pa_inject_spikes.argtypes = [P, C.c_int64, P, P]
         L.pa_model_info.argtypes = [P, C.POINTER(Info)]
         L.pa_get_kernel_stats.argtypes = [P, C.POINTER(KernelStats)]
         L.pa_reset_kernel_stats.argtypes = [P]
@@ -351,6 +353,12 @@ class Model:
 
     def reset_kernel_stats(self):
         _check(lib().pa_reset_kernel_stats(self._h))
+
+    def inject_spikes(self, gid, step):
+        """pa_inject_spikes: spikes of cells simulated elsewhere, in the last epoch."""
+        gid = np.ascontiguousarray(gid, np.int32)
+        step = np.ascontiguousarray(step, np.int64)
+        _check(lib().pa_inject_spikes(self._h, len(gid), _ptr(gid), _ptr(step)))
 
     def set_replay(self, gid, step):
         gid = np.ascontiguousarray(gid, np.int32)

@@ -50,14 +50,14 @@ def test_noalloc_after_other_models_dirtied_the_array():
     """Models with wide cells, a diffusing PRP field, heterosynaptic calcium and
     overflowing fork stacks leave their values in the shared array; a different
     model advanced next must still equal pa_advance bit for bit."""
-    dirty = [W.recurrent_stc_morpho(n_exc=64, n_inh=16, d_p=1.0),
-             hca_tree_net(),
-             tiny_tree_net(n_cells=70)]
-    for net in dirty:
-        m = E.Model(net)
+    dirty = [(W.recurrent_stc_morpho(n_exc=64, n_inh=16, d_p=1.0), E.FLAG_WIDE_ALL),
+             (hca_tree_net(), 0),
+             (tiny_tree_net(n_cells=70), 0)]
+    for net, flags in dirty:
+        m = E.Model(net, flags=flags)
         m.advance_noalloc(300 * net.dt)
         m.sync()
-    assert E.Model(dirty[0]).info().n_wide > 0
+    assert E.Model(dirty[0][0], flags=E.FLAG_WIDE_ALL).info().n_wide > 0
     for precision in (E.PA_FP64, E.PA_MIXED):
         net = tiny_tree_net(n_cells=45, seed=11)
         ref = E.Model(net, precision=precision)
