@@ -395,6 +395,34 @@ int pa_reset_kernel_stats(pa_model* m);
 
 void pa_free_model(pa_model* m);
 
+/* Batches of resident models (the paper has no counterpart: the serving path
+ * of this engine, many simulation jobs advanced together).  A batch advances
+ * every member by whole min-delay epochs (each member by its own epoch
+ * length, at its own dt), each batch epoch ONE launch of the
+ * time-step kernel over all members' cell groups (each block copies its
+ * member's launch arguments and runs that member's groups exactly as the
+ * member's own launch would), with each member's Poisson draws, routing,
+ * spike record and epoch clock on parallel branches; the epochs are replayed
+ * from CUDA graphs captured per membership (8 epochs per launch where they
+ * fit).  Members never share state: every result equals the member's result
+ * advanced alone, bit for bit.
+ * Members must be on the batch's device (a member built on another stream
+ * moves to the batch's stream when added, after its pending work, and stays
+ * there), share precision and tree class (chains or branched), have no
+ * wide-bin cells (build them with PA_FLAG_NARROW_ONLY), not be in open-loop replay, and be
+ * at an epoch boundary when added and advanced.  A member may be removed
+ * (and advanced alone, read, freed) between batch advances; remove it before
+ * pa_free_model.  pa_batch_advance only enqueues work on the stream. */
+typedef struct pa_batch pa_batch;
+int pa_batch_create(int32_t device, void* stream, pa_batch** out);
+int pa_batch_add(pa_batch* b, pa_model* m);
+int pa_batch_remove(pa_batch* b, pa_model* m);
+int pa_batch_advance(pa_batch* b, int64_t n_epochs);
+/* out[0] members, out[1] blocks of the grouped launch, out[2] graph launches,
+ * out[3] graphs captured (one per membership and epoch count in use) */
+int pa_batch_info(const pa_batch* b, int64_t* out);
+void pa_batch_free(pa_batch* b);
+
 /* Self-check of the engine's integer FP64 arithmetic on GPU `device` (no model
  * needed; the paper has no counterpart).  The solver's row reciprocal 1/d is
  * computed from integer operations and a single-precision seed, and the mixed

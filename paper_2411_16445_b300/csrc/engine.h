@@ -12,6 +12,8 @@
 #pragma once
 #include <cstdint>
 
+#include <vector_types.h>
+
 namespace pa {
 
 // Fork flags of a tree row (EpochArgs::tflag).
@@ -40,6 +42,13 @@ struct StreamParams {
   // HCA (c_pre = I0 [pA], decay_c = exp(-dt/tau_I), theta_p/theta_d [umol/l]):
   // calcium inflow per pA gamma 1e6 / (2 F), dt gamma_p, dt gamma_d per step
   double hca_kq, hca_gpr, hca_gdr;
+  // the same constants rounded to FP32, for the FP32-mechanism policy
+  struct F32 {
+    float decay_c, c_pre, c_post, theta_p, theta_d, gamma_p, gamma_d;
+    float rate_w, w_star, rate_h, rate_z, h0, theta_tag, f_int;
+    float a_pre, a_post, tau_pre, tau_post, w_max;
+    float pad;
+  } f;
 };
 
 // Device pointers of one synapse stream.  Element index e = ((sbase+j)<<5)|lane.
@@ -254,6 +263,21 @@ inline int launch_epoch(int prec, const EpochArgs& a, bool tree, int shape, void
 }
 int launch_init_gates(const double* v, void* gate, int64_t n_lanes, const uint8_t* is_hh,
                       void* stream);
+// One launch over several models (narrow bin only): block b runs 4 groups from
+// group d_bmap[b].y of model d_bmap[b].x, whose arguments are d_args[d_bmap[b].x].
+constexpr int kGroupedWarps = 4;
+int launch_epoch_grouped_fp64(const EpochArgs* d_args, const int2* d_bmap, int n_blocks, bool tree,
+                              void* stream);
+int launch_epoch_grouped_mixed(const EpochArgs* d_args, const int2* d_bmap, int n_blocks,
+                               bool tree, void* stream);
+int launch_epoch_grouped_fp32(const EpochArgs* d_args, const int2* d_bmap, int n_blocks, bool tree,
+                              void* stream);
+inline int launch_epoch_grouped(int prec, const EpochArgs* d_args, const int2* d_bmap,
+                                int n_blocks, bool tree, void* stream) {
+  return prec == 1   ? launch_epoch_grouped_mixed(d_args, d_bmap, n_blocks, tree, stream)
+         : prec == 2 ? launch_epoch_grouped_fp32(d_args, d_bmap, n_blocks, tree, stream)
+                     : launch_epoch_grouped_fp64(d_args, d_bmap, n_blocks, tree, stream);
+}
 // Graph launches: zero the mask slot of the clock's epoch in every mask array,
 // then advance the clock by one epoch (events.cu).
 struct SlotClear {

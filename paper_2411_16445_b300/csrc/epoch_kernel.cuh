@@ -96,6 +96,97 @@ struct HH64 {
   }
 };
 
+// The same kinetics in FP32 with CUDA's expf (the FP32-mechanism policy).
+struct HH32 {
+  __device__ static __forceinline__ float vtrap(float x, float y) {
+    const float u = x / y;
+    if (fabsf(u) < 1e-6f) return y * (1.0f - 0.5f * u);
+    return x / (expf(u) - 1.0f);
+  }
+  __device__ static __forceinline__ void rates(float v, float& am, float& bm, float& ah,
+                                               float& bh, float& an, float& bn) {
+    am = 0.1f * vtrap(-(v + 40.0f), 10.0f);
+    bm = 4.0f * expf(-(v + 65.0f) / 18.0f);
+    ah = 0.07f * expf(-(v + 65.0f) / 20.0f);
+    bh = 1.0f / (expf(-(v + 35.0f) / 10.0f) + 1.0f);
+    an = 0.01f * vtrap(-(v + 55.0f), 10.0f);
+    bn = 0.125f * expf(-(v + 65.0f) / 80.0f);
+  }
+  __device__ static __forceinline__ float gate(float x, float a, float b, float dt) {
+    const float s = a + b;
+    const float xinf = a / s;
+    return xinf + (x - xinf) * expf(-dt * s);
+  }
+};
+
+// An HH soma's gates m, h, n: loaded at the start of a launch, the membrane
+// conductance and E-weighted sum the assembly takes at V^k, the exponential
+// update at V^{k+1}, stored at the end.  FP64 (HH64) or, for the
+// FP32-mechanism policy, FP32 (HH32) with the results widened for the FP64
+// assembly; the gate array holds doubles in both.
+template <bool kF32>
+struct SomaHH {
+  double m = 0, h = 0, n = 0;
+  __device__ __forceinline__ void load(const double* gate, int64_t nl, int64_t L) {
+    m = gate[L]; h = gate[nl + L]; n = gate[2 * nl + L];
+  }
+  __device__ __forceinline__ void store(double* gate, int64_t nl, int64_t L) const {
+    gate[L] = m; gate[nl + L] = h; gate[2 * nl + L] = n;
+  }
+  // per-soma constants are reloaded here rather than kept live
+  __device__ __forceinline__ void currents(const EpochArgs& A, int64_t L, double& gmt,
+                                           double& emt) const {
+    const double gna = __ldg(&A.hh_g[L]), gk = __ldg(&A.hh_g[A.n_lanes + L]),
+                 gl = __ldg(&A.hh_g[2 * A.n_lanes + L]);
+    const double ena = __ldg(&A.hh_e[L]), ek = __ldg(&A.hh_e[A.n_lanes + L]),
+                 el = __ldg(&A.hh_e[2 * A.n_lanes + L]);
+    const double mmmh = ((m * m) * m) * h;
+    const double nnnn = ((n * n) * n) * n;
+    const double g1 = gna * mmmh;
+    const double g2 = gk * nnnn;
+    gmt = (g1 + g2) + gl;
+    emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
+  }
+  __device__ __forceinline__ void update(double v, double dt) {
+    double am, bm, ah, bh, an, bn;
+    HH64::rates(v, am, bm, ah, bh, an, bn);
+    m = HH64::gate(m, am, bm, dt);
+    h = HH64::gate(h, ah, bh, dt);
+    n = HH64::gate(n, an, bn, dt);
+  }
+};
+template <>
+struct SomaHH<true> {
+  float m = 0, h = 0, n = 0;
+  __device__ __forceinline__ void load(const double* gate, int64_t nl, int64_t L) {
+    m = narrow_rz(gate[L]); h = narrow_rz(gate[nl + L]); n = narrow_rz(gate[2 * nl + L]);
+  }
+  __device__ __forceinline__ void store(double* gate, int64_t nl, int64_t L) const {
+    gate[L] = widen_f32(m); gate[nl + L] = widen_f32(h); gate[2 * nl + L] = widen_f32(n);
+  }
+  __device__ __forceinline__ void currents(const EpochArgs& A, int64_t L, double& gmt,
+                                           double& emt) const {
+    const float gna = narrow_rz(__ldg(&A.hh_g[L])), gk = narrow_rz(__ldg(&A.hh_g[A.n_lanes + L])),
+                gl = narrow_rz(__ldg(&A.hh_g[2 * A.n_lanes + L]));
+    const float ena = narrow_rz(__ldg(&A.hh_e[L])), ek = narrow_rz(__ldg(&A.hh_e[A.n_lanes + L])),
+                el = narrow_rz(__ldg(&A.hh_e[2 * A.n_lanes + L]));
+    const float mmmh = ((m * m) * m) * h;
+    const float nnnn = ((n * n) * n) * n;
+    const float g1 = gna * mmmh;
+    const float g2 = gk * nnnn;
+    gmt = widen_f32((g1 + g2) + gl);
+    emt = widen_f32(((g1 * ena) + (g2 * ek)) + (gl * el));
+  }
+  __device__ __forceinline__ void update(double v, double dt) {
+    float am, bm, ah, bh, an, bn;
+    const float vf = narrow_rz(v), dtf = narrow_rz(dt);
+    HH32::rates(vf, am, bm, ah, bh, an, bn);
+    m = HH32::gate(m, am, bm, dtf);
+    h = HH32::gate(h, ah, bh, dtf);
+    n = HH32::gate(n, an, bn, dtf);
+  }
+};
+
 __device__ __forceinline__ uint32_t elem_of(int32_t row_base, int32_t row, int lane) {
   return ((uint32_t)(row_base + row) << 5) | (uint32_t)lane;
 }
@@ -224,6 +315,24 @@ __device__ __forceinline__ typename PR::G syn_update(const StreamParams& P, cons
   using TW = typename PR::W;
   if (P.kind == SK_EXPSYN) {
     if (pre) gv = PR::add_w(gv, ((const TW*)D.weight)[e]);
+  } else if (P.kind == SK_GB && PR::kMech32) {
+    // FP32 mechanism: calcium and the increment of Eq. weight_graupner_brunel
+    // in FP32, accumulated into the FP64 w
+    if (pre) gv = PR::add_w(gv, ((const TW*)D.weight)[e]);
+    const StreamParams::F32& Q = P.f;
+    float c = narrow_rz(cc);
+    if (capre) c = c + Q.c_pre;
+    if (post) c = c + Q.c_post;
+    const float w = narrow_rz(wv);
+    const float Aw = (w * (1.0f - w)) * (Q.w_star - w);
+    const float Pw = (c > Q.theta_p) ? Q.gamma_p * (1.0f - w) : 0.0f;
+    const float Dw = (c > Q.theta_d) ? Q.gamma_d * w : 0.0f;
+    double wn = wv + widen_f32(Q.rate_w * ((Pw - Aw) - Dw));
+    const int nth = (c > Q.theta_p) + (c > Q.theta_d);
+    if (P.sigma > 0.0 && nth > 0)
+      wn = __dadd_rn(wn, __dmul_rn(P.amp[nth], model_normal(seed, (uint64_t)D.nid[e], k)));
+    D.w[e] = wn;
+    D.c[e] = widen_f32(c * Q.decay_c);
   } else if (P.kind == SK_GB) {
     if (pre) gv = PR::add_w(gv, ((const TW*)D.weight)[e]);
     if (capre) cc = cc + P.c_pre;
@@ -239,6 +348,27 @@ __device__ __forceinline__ typename PR::G syn_update(const StreamParams& P, cons
       wn = __dadd_rn(wn, __dmul_rn(P.amp[nth], model_normal(seed, (uint64_t)D.nid[e], k)));
     D.w[e] = wn;
     D.c[e] = cc * P.decay_c;
+  } else if (P.kind == SK_STC && PR::kMech32) {
+    // FP32 mechanism: calcium and the increments of Eqs. early_phase_weight and
+    // late_phase_weight in FP32, accumulated into the FP64 h and z
+    const StreamParams::F32& Q = P.f;
+    const float h = narrow_rz(wv), z = narrow_rz(zv), pf = narrow_rz(prp);
+    if (pre) gv = PR::add_w(gv, (TW)(((const TW*)D.weight)[e] * ((h + Q.h0 * z) / Q.h0)));
+    float c = narrow_rz(cc);
+    if (capre) c = c + Q.c_pre;
+    if (post) c = c + Q.c_post;
+    S = S + widen_f32(fabsf(h - Q.h0));
+    const float T1 = ((h - Q.h0) > Q.theta_tag) ? (pf * Q.f_int) * (1.0f - z) : 0.0f;
+    const float T2 = ((Q.h0 - h) > Q.theta_tag) ? (pf * Q.f_int) * (z + 0.5f) : 0.0f;
+    D.z[e] = zv + widen_f32(Q.rate_z * (T1 - T2));
+    const float Ph = (c > Q.theta_p) ? Q.gamma_p * (10.0f - h) : 0.0f;
+    const float Dh = (c > Q.theta_d) ? Q.gamma_d * h : 0.0f;
+    double hn = wv + widen_f32(Q.rate_h * ((0.1f * (Q.h0 - h) + Ph) - Dh));
+    const int nth = (c > Q.theta_p) + (c > Q.theta_d);
+    if (P.sigma > 0.0 && nth > 0)
+      hn = __dadd_rn(hn, __dmul_rn(P.amp[nth], model_normal(seed, (uint64_t)D.nid[e], k)));
+    D.w[e] = hn;
+    D.c[e] = widen_f32(c * Q.decay_c);
   } else if (P.kind == SK_STC) {
     const double h = wv, z = zv;
     const double h0 = P.h0;
@@ -258,6 +388,30 @@ __device__ __forceinline__ typename PR::G syn_update(const StreamParams& P, cons
       hn = __dadd_rn(hn, __dmul_rn(P.amp[nth], model_normal(seed, (uint64_t)D.nid[e], k)));
     D.w[e] = hn;
     D.c[e] = cc * P.decay_c;
+  } else if ((pre || post) && PR::kMech32) {  // SK_STDP, FP32 traces and increments
+    using TT = typename PR::T;
+    TT* AP = (TT*)D.apre;
+    TT* AQ = (TT*)D.apost;
+    const StreamParams::F32& Q = P.f;
+    const float dtf = narrow_rz(dt);
+    double w = D.w[e];
+    float ap = (float)AP[e] * expf(-((float)(k - D.kpre[e]) * dtf) / Q.tau_pre);
+    float aq = (float)AQ[e] * expf(-((float)(k - D.kpost[e]) * dtf) / Q.tau_post);
+    if (pre) {
+      const double wc = w < 0.0 ? 0.0 : (w > P.w_max ? P.w_max : w);
+      gv = PR::add_w(gv, (TW)(((const TW*)D.weight)[e] * narrow_rz(wc)));
+      ap = ap + Q.a_pre;
+      w = w + widen_f32(aq);
+      AP[e] = (TT)ap;
+      D.kpre[e] = (int32_t)k;
+    }
+    if (post) {
+      aq = aq + Q.a_post;
+      w = w + widen_f32(ap);
+      AQ[e] = (TT)aq;
+      D.kpost[e] = (int32_t)k;
+    }
+    D.w[e] = w;
   } else if (pre || post) {  // SK_STDP: traces evaluated in closed form at events only
     using TT = typename PR::T;
     TT* AP = (TT*)D.apre;
@@ -332,17 +486,15 @@ __device__ __noinline__ void hca_stream(const EpochArgs& A, int s, int g, int la
   }
 }
 
-template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
-          int kStackDepth>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const EpochArgs A) {
+// The launch window of one warp: group g (32 cells, one per lane) of the model
+// A, with the warp's shared-memory stages at wbuf.
+template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth>
+__device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char* wbuf) {
   using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
   using TS = typename PR::S;
   using TG = typename PR::G;
-  extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   if (g >= A.n_narrow) return;  // whole warps only
-  char* wbuf = smem_raw + (threadIdx.x >> 5) * ST::kWarpBytes;
   uint64_t* bar = (uint64_t*)(wbuf + kStages * ST::kBytes);
   // the fork stack region (trees): double2 entries (backward), double (forward)
   double2* stack2 = (double2*)(wbuf + kStages * ST::kBytes + 64);
@@ -356,7 +508,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
   uint32_t pending = 0;  // stages with a copy issued and not yet waited for
   bool failed = false;
   const uint32_t wait_limit = A.wait_limit ? A.wait_limit : kSpinLimit;
-  using HH = HH64;
   const int64_t L = (int64_t)g * 32 + lane;
   const int n = A.ncv[L];
   const int32_t rb = A.row_base[g];
@@ -374,11 +525,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
   double* __restrict__ XP = A.xp;
 
   const bool hh = n > 0 && A.is_hh[L];
-  double* gate = A.gate;
-  double gm_ = 0, gh_ = 0, gn_ = 0;
-  if (hh) {
-    gm_ = gate[L]; gh_ = gate[A.n_lanes + L]; gn_ = gate[2 * A.n_lanes + L];
-  }
+  SomaHH<PR::kMech32> soma;
+  if (hh) soma.load(A.gate, A.n_lanes, L);
   const double iinj_val = n > 0 ? A.iinj[L] : 0.0;
   const int64_t kon = n > 0 ? A.k_on[L] : 0, koff = n > 0 ? A.k_off[L] : 0;
   const double th = n > 0 ? A.thresh[L] : 0.0;
@@ -582,17 +730,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
           if (i == 0) {
             v0_old = v;
             if (hh) {
-              // per-soma constants are reloaded here rather than kept live
-              const double gna = __ldg(&A.hh_g[L]), gk = __ldg(&A.hh_g[A.n_lanes + L]),
-                           gl = __ldg(&A.hh_g[2 * A.n_lanes + L]);
-              const double ena = __ldg(&A.hh_e[L]), ek = __ldg(&A.hh_e[A.n_lanes + L]),
-                           el = __ldg(&A.hh_e[2 * A.n_lanes + L]);
-              const double mmmh = ((gm_ * gm_) * gm_) * gh_;
-              const double nnnn = ((gn_ * gn_) * gn_) * gn_;
-              const double g1 = gna * mmmh;
-              const double g2 = gk * nnnn;
-              const double gmt = (g1 + g2) + gl;
-              const double emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
+              double gmt, emt;
+              soma.currents(A, L, gmt, emt);
               d = (dcv + gmt) + gsv;
               b = (fma(cdt, v, emt) + iinj) + esv;
             } else {
@@ -758,13 +897,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
       }
     }
     // ---- d. soma gates, detection, compaction --------------------------------
-    if (hh) {
-      double am, bm, ah, bh, an, bn;
-      HH::rates(v0_new, am, bm, ah, bh, an, bn);
-      gm_ = HH::gate(gm_, am, bm, dt);
-      gh_ = HH::gate(gh_, ah, bh, dt);
-      gn_ = HH::gate(gn_, an, bn, dt);
-    }
+    if (hh) soma.update(v0_new, dt);
     const bool spk = n > 0 && v0_old < th && v0_new >= th;
     const unsigned ball = __ballot_sync(0xffffffffu, spk);
     if (ball) {
@@ -795,11 +928,44 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const Epoch
   }
   if (n > 0) {
     A.spiked_prev[L] = spiked_prev ? 1 : 0;
-    if (hh) {
-      gate[L] = gm_; gate[A.n_lanes + L] = gh_; gate[2 * A.n_lanes + L] = gn_;
-    }
+    if (hh) soma.store(A.gate, A.n_lanes, L);
     if (has_stc) A.prp[L] = prp;
   }
+}
+
+template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
+          int kStackDepth>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const EpochArgs A) {
+  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
+  extern __shared__ __align__(128) char smem_raw[];
+  const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  epoch_warp<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>(
+      A, g, smem_raw + (threadIdx.x >> 5) * ST::kWarpBytes);
+}
+
+// Several models in one launch (a batch of resident jobs that share the
+// precision, the tree class and the epoch length): block b runs groups
+// [bmap[b].y, bmap[b].y + warps per block) of model bmap[b].x, whose launch
+// arguments the block first copies from args[] into shared memory.  Every
+// warp then takes exactly the steps it takes in the model's own launch.
+constexpr int kArgsSmemBytes = (int)((sizeof(EpochArgs) + 127) / 128 * 128);
+static_assert(sizeof(EpochArgs) % 8 == 0, "launch arguments copy as 8-byte words");
+
+template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
+          int kStackDepth>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    epoch_kernel_grouped(const EpochArgs* __restrict__ args, const int2* __restrict__ bmap) {
+  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
+  extern __shared__ __align__(128) char smem_raw[];
+  __shared__ __align__(128) char args_raw[kArgsSmemBytes];
+  const int2 bm = bmap[blockIdx.x];
+  const long long* src = (const long long*)(args + bm.x);
+  long long* dst = (long long*)args_raw;
+  for (int i = threadIdx.x; i < (int)(sizeof(EpochArgs) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  epoch_warp<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>(
+      *(const EpochArgs*)args_raw, bm.y + (int)(threadIdx.x >> 5),
+      smem_raw + (threadIdx.x >> 5) * ST::kWarpBytes);
 }
 
 template <class PR, bool TREE, int RB, int RF, int WPB, int MB, int SB>
@@ -847,6 +1013,39 @@ int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
     case 5: return launch_epoch_t<PR, TREE, 4, 12, 4, 3, 0>(a, stream);   // trees: no stacks
     default: return launch_epoch_t<PR, TREE, RB0, 12, 4, 3, SB0>(a, stream);  // 12 warps per SM
   }
+}
+
+// Grouped launches: 4 warps per block, 3 blocks per SM; chains take shape 0's
+// geometry, trees shape 5's (no fork stacks: the copied arguments take their
+// shared memory).  Results equal those of every other shape.
+constexpr int kGroupedWarpsPerBlock = 4;
+
+template <class PR, bool TREE, int RB, int RF, int MB, int SB>
+int launch_epoch_grouped_t(const EpochArgs* d_args, const int2* d_bmap, int n_blocks,
+                           void* stream) {
+  constexpr int WPB = kGroupedWarpsPerBlock;
+  if (n_blocks == 0) return 0;
+  const int smem = WPB * Stage<PR, TREE, RB, RF, SB>::kWarpBytes;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  static bool attr_set[64] = {false};
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    e = cudaFuncSetAttribute(epoch_kernel_grouped<PR, TREE, RB, RF, 32 * WPB, MB, SB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  epoch_kernel_grouped<PR, TREE, RB, RF, 32 * WPB, MB, SB>
+      <<<n_blocks, 32 * WPB, smem, (cudaStream_t)stream>>>(d_args, d_bmap);
+  return (int)cudaGetLastError();
+}
+
+template <class PR>
+int launch_epoch_grouped_impl(const EpochArgs* d_args, const int2* d_bmap, int n_blocks,
+                              bool tree, void* stream) {
+  return tree ? launch_epoch_grouped_t<PR, true, 4, 12, 3, 0>(d_args, d_bmap, n_blocks, stream)
+              : launch_epoch_grouped_t<PR, false, 4, 12, 3, 6>(d_args, d_bmap, n_blocks, stream);
 }
 
 template <class PR>

@@ -528,6 +528,11 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     }
     if ((P.kind == SK_GB || P.kind == SK_STC) && P.dc_steps < 0)
       return set_err(PA_ERR_ARG, "mechanism %lld: negative t_c_delay", (long long)m);
+    P.f = {(float)P.decay_c, (float)P.c_pre, (float)P.c_post, (float)P.theta_p,
+           (float)P.theta_d, (float)P.gamma_p, (float)P.gamma_d, (float)P.rate_w,
+           (float)P.w_star, (float)P.rate_h, (float)P.rate_z, (float)P.h0,
+           (float)P.theta_tag, (float)P.f_int, (float)P.a_pre, (float)P.a_post,
+           (float)P.tau_pre, (float)P.tau_post, (float)P.w_max, 0.0f};
   }
   M->n_streams = n_streams;
 
@@ -2443,3 +2448,262 @@ void pa_free_model(pa_model* M) {
 const char* pa_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+
+// ---------------------------------------------------------------------------
+// Batches: several resident models advanced together, one grouped epoch-kernel
+// launch per min-delay epoch for all of them (the serving path).
+
+struct pa_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;       // every member runs on it
+  cudaStream_t cap_stream = nullptr;   // capture only
+  static constexpr int kSide = 8;      // branches for the members' small kernels
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kSide] = {};
+  std::vector<pa_model*> members;
+  int precision = -1;
+  bool tree = false;
+  pa::EpochArgs* d_args = nullptr;     // members' launch arguments (clock-driven)
+  int2* d_bmap = nullptr;              // block -> (member, first group)
+  size_t cap_args = 0, cap_bmap = 0;
+  int n_blocks = 0;
+  bool dirty = true;                   // membership changed since the last upload
+  cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+  int64_t n_launches = 0;              // graph launches
+  int64_t n_captures = 0;              // graphs captured (membership changes)
+};
+
+namespace {
+
+void batch_drop_graphs(pa_batch* B) {
+  if (B->g1) cudaGraphExecDestroy(B->g1);
+  if (B->g8) cudaGraphExecDestroy(B->g8);
+  B->g1 = B->g8 = nullptr;
+}
+
+// Members' arguments and the block map to the device (on membership change).
+int batch_upload(pa_batch* B) {
+  using namespace pa;
+  std::vector<EpochArgs> args(B->members.size());
+  std::vector<int2> bmap;
+  for (size_t j = 0; j < B->members.size(); ++j) {
+    pa_model* M = B->members[j];
+    EpochArgs A = M->ea;
+    A.clock = M->clock;
+    A.replay = 0;
+    args[j] = A;
+    for (int32_t g0 = 0; g0 < M->n_narrow; g0 += kGroupedWarps) bmap.push_back(make_int2((int)j, g0));
+  }
+  if (args.size() > B->cap_args) {
+    if (B->d_args) cudaFree(B->d_args);
+    B->d_args = nullptr;
+    B->cap_args = 0;
+    CUDA_TRY(cudaMalloc(&B->d_args, sizeof(EpochArgs) * args.size()));
+    B->cap_args = args.size();
+  }
+  if (bmap.size() > B->cap_bmap) {
+    if (B->d_bmap) cudaFree(B->d_bmap);
+    B->d_bmap = nullptr;
+    B->cap_bmap = 0;
+    CUDA_TRY(cudaMalloc(&B->d_bmap, sizeof(int2) * bmap.size()));
+    B->cap_bmap = bmap.size();
+  }
+  if (!args.empty())
+    CUDA_TRY(cudaMemcpyAsync(B->d_args, args.data(), sizeof(EpochArgs) * args.size(),
+                             cudaMemcpyHostToDevice, B->stream));
+  if (!bmap.empty())
+    CUDA_TRY(cudaMemcpyAsync(B->d_bmap, bmap.data(), sizeof(int2) * bmap.size(),
+                             cudaMemcpyHostToDevice, B->stream));
+  CUDA_TRY(cudaStreamSynchronize(B->stream));
+  B->n_blocks = (int)bmap.size();
+  batch_drop_graphs(B);
+  B->dirty = false;
+  return PA_OK;
+}
+
+// One epoch of every member on capture stream st: the members' Poisson draws
+// on parallel branches, the grouped epoch kernel, then each member's routing,
+// spike record and clock tick on parallel branches.
+int batch_enqueue_epoch(pa_batch* B, cudaStream_t st) {
+  using namespace pa;
+  const int K = pa_batch::kSide;
+  auto fork = [&]() -> int {
+    CUDA_TRY(cudaEventRecord(B->ev_fork, st));
+    for (int k = 0; k < K; ++k) CUDA_TRY(cudaStreamWaitEvent(B->side[k], B->ev_fork, 0));
+    return PA_OK;
+  };
+  auto join = [&]() -> int {
+    for (int k = 0; k < K; ++k) {
+      CUDA_TRY(cudaEventRecord(B->ev_join[k], B->side[k]));
+      CUDA_TRY(cudaStreamWaitEvent(st, B->ev_join[k], 0));
+    }
+    return PA_OK;
+  };
+  int rc = fork();
+  for (size_t j = 0; j < B->members.size() && rc == 0; ++j) {
+    pa_model* M = B->members[j];
+    if (M->pa_args.n > 0) {
+      PoissonArgs P = M->pa_args;
+      P.clock = M->clock;
+      rc = launch_poisson(P, 0, M->E, B->side[j % K]);
+    }
+  }
+  if (rc == 0) rc = join();
+  if (rc == 0) rc = launch_epoch_grouped(B->precision, B->d_args, B->d_bmap, B->n_blocks, B->tree, st);
+  if (rc == 0) rc = fork();
+  for (size_t j = 0; j < B->members.size() && rc == 0; ++j) {
+    pa_model* M = B->members[j];
+    cudaStream_t sj = B->side[j % K];
+    rc = launch_route(M->ra, M->max_spikes, sj);
+    if (rc == 0)
+      rc = launch_log_append(M->ea.spk_count, M->ea.spk_gid, M->ea.spk_step, M->ea.spk_t,
+                             M->max_spikes, M->log_count, M->log_gid, M->log_step, M->log_t,
+                             M->log_cap, M->err_flags, sj);
+    if (rc == 0) rc = launch_clear_and_tick(M->slot_clear, M->clock, sj);
+  }
+  if (rc == 0) rc = join();
+  return rc;
+}
+
+int batch_capture(pa_batch* B, int count, cudaGraphExec_t* out) {
+  CUDA_TRY(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeRelaxed));
+  int rc = 0;
+  for (int i = 0; i < count && rc == 0; ++i) rc = batch_enqueue_epoch(B, B->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(B->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc < 0 ? rc : set_err(PA_ERR_CUDA, "batch capture: %s", cudaGetErrorString((cudaError_t)rc));
+  }
+  if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "batch instantiation: %s", cudaGetErrorString(e));
+  return PA_OK;
+}
+
+}  // namespace
+
+int pa_batch_create(int32_t device, void* stream, pa_batch** out) {
+  if (!out) return set_err(PA_ERR_ARG, "NULL output");
+  *out = nullptr;
+  pa_batch* B = new (std::nothrow) pa_batch();
+  if (!B) return set_err(PA_ERR_OOM, "host allocation failed");
+  B->device = device;
+  B->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < pa_batch::kSide && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&B->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    pa_batch_free(B);
+    return set_err(PA_ERR_CUDA, "pa_batch_create: %s", cudaGetErrorString(e));
+  }
+  *out = B;
+  return PA_OK;
+}
+
+int pa_batch_add(pa_batch* B, pa_model* M) {
+  if (!B || !M) return set_err(PA_ERR_ARG, "NULL argument");
+  if (std::find(B->members.begin(), B->members.end(), M) != B->members.end())
+    return set_err(PA_ERR_ARG, "model already in the batch");
+  if (M->device != B->device) return set_err(PA_ERR_ARG, "a member must be on the batch's device");
+  if (M->n_wide > 0) return set_err(PA_ERR_ARG, "a member must have no wide-bin cells (PA_FLAG_NARROW_ONLY)");
+  if (M->replay) return set_err(PA_ERR_STATE, "a member cannot be in open-loop replay");
+  if (M->step % M->E != 0) return set_err(PA_ERR_STATE, "a member must be at an epoch boundary");
+  if (!B->members.empty() && (M->precision != B->precision || M->tree != B->tree))
+    return set_err(PA_ERR_ARG, "members must share precision and tree class");
+  if (B->members.empty()) {
+    B->precision = M->precision;
+    B->tree = M->tree;
+  }
+  if (M->stream != B->stream) {
+    // the member moves to the batch's stream, after its own work
+    CUDA_TRY(cudaSetDevice(M->device));
+    CUDA_TRY(cudaStreamSynchronize(M->stream));
+    M->stream = B->stream;
+  }
+  B->members.push_back(M);
+  B->dirty = true;
+  return PA_OK;
+}
+
+int pa_batch_remove(pa_batch* B, pa_model* M) {
+  if (!B || !M) return set_err(PA_ERR_ARG, "NULL argument");
+  auto it = std::find(B->members.begin(), B->members.end(), M);
+  if (it == B->members.end()) return set_err(PA_ERR_ARG, "model not in the batch");
+  B->members.erase(it);
+  B->dirty = true;
+  return PA_OK;
+}
+
+int pa_batch_advance(pa_batch* B, int64_t n_epochs) {
+  using namespace pa;
+  if (!B || n_epochs < 0) return set_err(PA_ERR_ARG, "bad arguments");
+  if (B->members.empty() || n_epochs == 0) return PA_OK;
+  CUDA_TRY(cudaSetDevice(B->device));
+  for (pa_model* M : B->members)
+    if (M->step % M->E != 0) return set_err(PA_ERR_STATE, "a member left its epoch boundary");
+  if (B->dirty) {
+    int rc = batch_upload(B);
+    if (rc) return rc;
+  }
+  // the members' device clocks from their host positions (a member may have
+  // been advanced alone since the last batch advance)
+  for (pa_model* M : B->members) {
+    int rc = launch_set_clock(M->clock, M->step, M->probe_samples, B->stream);
+    if (rc) return set_err(PA_ERR_CUDA, "clock: %s", cudaGetErrorString((cudaError_t)rc));
+  }
+  int64_t n = n_epochs;
+  while (n > 0) {
+    const int take = n >= 8 ? 8 : 1;
+    cudaGraphExec_t& g = take == 8 ? B->g8 : B->g1;
+    if (!g) {
+      int rc = batch_capture(B, take, &g);
+      if (rc) return rc;
+      ++B->n_captures;
+    }
+    CUDA_TRY(cudaGraphLaunch(g, B->stream));
+    ++B->n_launches;
+    for (pa_model* M : B->members) {
+      for (int i = 0; i < take; ++i) {
+        M->poisson_epoch_done = M->step / M->E;
+        M->step += M->E;
+        if (M->n_probe > 0) M->probe_samples += M->E;
+      }
+      M->n_epoch_launches += take;
+    }
+    n -= take;
+  }
+  return PA_OK;
+}
+
+int pa_batch_info(const pa_batch* B, int64_t* out) {
+  if (!B || !out) return set_err(PA_ERR_ARG, "NULL argument");
+  out[0] = (int64_t)B->members.size();
+  out[1] = B->n_blocks;
+  out[2] = B->n_launches;
+  out[3] = B->n_captures;
+  return PA_OK;
+}
+
+void pa_batch_free(pa_batch* B) {
+  if (!B) return;
+  cudaSetDevice(B->device);
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  batch_drop_graphs(B);
+  if (B->d_args) cudaFree(B->d_args);
+  if (B->d_bmap) cudaFree(B->d_bmap);
+  for (int k = 0; k < pa_batch::kSide; ++k) {
+    if (B->side[k]) cudaStreamDestroy(B->side[k]);
+    if (B->ev_join[k]) cudaEventDestroy(B->ev_join[k]);
+  }
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+  delete B;
+}

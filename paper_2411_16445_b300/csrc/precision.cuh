@@ -16,7 +16,10 @@
 //                       at events only); each run of same-CV synapses is summed
 //                       in float-float and turned into the FP64 per-CV sums by
 //                       one FP64 addition, g E by one FP64 product;
-//   PrecF32  (PA_FP32)  g, weights, traces and the per-CV sums plain FP32.
+//   PrecF32  (PA_FP32)  g, weights, traces and the per-CV sums plain FP32, and
+//                       the mechanisms in FP32: HH rates and gates, calcium,
+//                       the GB / STC / STDP increments (the slow state they
+//                       accumulate into stays FP64).
 //
 // Why the conductance path needs more than FP32 in PA_MIXED (measured with a
 // CPU emulation of each variant against the FP64 oracle, recurrent tagging-
@@ -153,6 +156,19 @@ struct AccFF {  // mixed: the run's conductance in float-float, FP64 at its end
   }
 };
 
+// A double narrowed to a float by truncation on the integer pipes (sign,
+// exponent rebiased, the top 23 fraction bits); values below the float range
+// flush to zero.  The FP32-mechanism policy reads its FP64 slow state this way
+// (the variables it narrows are bounded: calcium, weights, tags, voltages).
+__device__ __forceinline__ float narrow_rz(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const uint32_t f = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t s = hi & 0x80000000u;
+  return __uint_as_float(e <= 0 ? s : (s | ((uint32_t)e << 23) | f));
+}
+
 // ---------------------------------------------------------------------------
 // The policies.  G: conductance element; W: event weight element; T: STDP
 // trace element; S: per-CV sum element; Ec / Dc: the stream's reversal
@@ -166,6 +182,7 @@ struct PrecF64 {
   using Dc = double;
   using Acc = AccPlain<double>;
   static constexpr int kId = 0;
+  static constexpr bool kMech32 = false;  // HH, calcium, plasticity increments in FP64
   __device__ static __forceinline__ Ec e_const(double e) { return e; }
   __device__ static __forceinline__ Dc d_const(double d) { return d; }
   __device__ static __forceinline__ G add_w(G g, W w) { return g + w; }
@@ -184,6 +201,7 @@ struct PrecMix {
   using Dc = float2;  // exp(-dt/tau) as hi + lo
   using Acc = AccFF;
   static constexpr int kId = 1;
+  static constexpr bool kMech32 = false;
   __device__ static __forceinline__ Ec e_const(double e) { return e; }
   __device__ static __forceinline__ Dc d_const(double d) { return ff_from_d(d); }
   __device__ static __forceinline__ G add_w(G g, W w) { return ff_add(g, ff_from_d(w)); }
@@ -204,6 +222,10 @@ struct PrecF32 {
   using Dc = float;
   using Acc = AccPlain<float>;
   static constexpr int kId = 2;
+  // HH rates and gates, calcium and the GB / STC / STDP increments in FP32
+  // (exponential integration with CUDA's expf); the slow state w, h, z, p
+  // accumulates the increments in FP64
+  static constexpr bool kMech32 = true;
   __device__ static __forceinline__ Ec e_const(double e) { return (float)e; }
   __device__ static __forceinline__ Dc d_const(double d) { return (float)d; }
   __device__ static __forceinline__ G add_w(G g, W w) { return __fadd_rn(g, w); }

@@ -11,4 +11,8 @@ namespace pa {
 int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream, const SideLaunch* side) {
   return launch_bins<PrecMix>(a, tree, shape, stream, side);
 }
+int launch_epoch_grouped_mixed(const EpochArgs* d_args, const int2* d_bmap, int n_blocks, bool tree,
+                            void* stream) {
+  return launch_epoch_grouped_impl<PrecMix>(d_args, d_bmap, n_blocks, tree, stream);
+}
 }  // namespace pa

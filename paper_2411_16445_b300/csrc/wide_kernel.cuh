@@ -46,7 +46,6 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   const int64_t e0 = (int64_t)A.row_base[g] << 5;  // element of CV 0
   const WideCell wc = A.wcell[w];
   const double dt = A.dt;
-  using HH = HH64;
 
   double* __restrict__ Vg = A.V;
   const double* __restrict__ CDT = A.cdt;
@@ -63,10 +62,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
 
   // soma state: lane 0 owns it (every lane keeps prp and the POST_EVENT flag)
   const bool hh = n > 0 && A.is_hh[L];
-  double gm_ = 0, gh_ = 0, gn_ = 0;
-  if (hh && lane == 0) {
-    gm_ = A.gate[L]; gh_ = A.gate[A.n_lanes + L]; gn_ = A.gate[2 * A.n_lanes + L];
-  }
+  SomaHH<PR::kMech32> soma;
+  if (hh && lane == 0) soma.load(A.gate, A.n_lanes, L);
   const double iinj_val = n > 0 ? A.iinj[L] : 0.0;
   const int64_t kon = n > 0 ? A.k_on[L] : 0, koff = n > 0 ? A.k_off[L] : 0;
   const double th = n > 0 ? A.thresh[L] : 0.0;
@@ -197,16 +194,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           if (i == 0) {
             v0_old = v;
             if (hh) {
-              const double gna = __ldg(&A.hh_g[L]), gk = __ldg(&A.hh_g[A.n_lanes + L]),
-                           gl = __ldg(&A.hh_g[2 * A.n_lanes + L]);
-              const double ena = __ldg(&A.hh_e[L]), ek = __ldg(&A.hh_e[A.n_lanes + L]),
-                           el = __ldg(&A.hh_e[2 * A.n_lanes + L]);
-              const double mmmh = ((gm_ * gm_) * gm_) * gh_;
-              const double nnnn = ((gn_ * gn_) * gn_) * gn_;
-              const double g1 = gna * mmmh;
-              const double g2 = gk * nnnn;
-              const double gmt = (g1 + g2) + gl;
-              const double emt = ((g1 * ena) + (g2 * ek)) + (gl * el);
+              double gmt, emt;
+              soma.currents(A, L, gmt, emt);
               d = (dcv + gmt) + gsv;
               bb = (fma(cdt, v, emt) + iinj) + esv;
             } else {
@@ -364,11 +353,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
     bool spk = false;
     if (lane == 0) {
       if (hh) {
-        double am, bm, ah, bh, an, bn;
-        HH::rates(v0_new, am, bm, ah, bh, an, bn);
-        gm_ = HH::gate(gm_, am, bm, dt);
-        gh_ = HH::gate(gh_, ah, bh, dt);
-        gn_ = HH::gate(gn_, an, bn, dt);
+        soma.update(v0_new, dt);
       }
       spk = v0_old < th && v0_new >= th;
       if (spk) {
@@ -386,7 +371,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   if (n > 0 && lane == 0) {
     A.spiked_prev[L] = spiked_prev ? 1 : 0;
     if (hh) {
-      A.gate[L] = gm_; A.gate[A.n_lanes + L] = gh_; A.gate[2 * A.n_lanes + L] = gn_;
+      soma.store(A.gate, A.n_lanes, L);
     }
     if (has_stc) A.prp[L] = prp;
   }

@@ -28,7 +28,8 @@ EXPORTED = ("pa_build_model", "pa_advance", "pa_advance_noalloc", "pa_sync", "pa
             "pa_read_weights", "pa_read_state", "pa_set_replay", "pa_model_info",
             "pa_get_kernel_stats", "pa_reset_kernel_stats", "pa_get_tuning", "pa_free_model",
             "pa_check_arith", "pa_measure_fp64", "pa_write_state", "pa_fast_forward",
-            "pa_inject_spikes",
+            "pa_inject_spikes", "pa_batch_create", "pa_batch_add", "pa_batch_remove",
+            "pa_batch_advance", "pa_batch_info", "pa_batch_free",
             "pa_last_error")
 
 
@@ -168,6 +169,13 @@ def lib():
         L.pa_read_state.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         L.pa_set_replay.argtypes = [P, C.c_int64, P, P]
         L.pa_inject_spikes.argtypes = [P, C.c_int64, P, P]
+        L.pa_batch_create.argtypes = [C.c_int32, P, C.POINTER(C.c_void_p)]
+        L.pa_batch_add.argtypes = [P, P]
+        L.pa_batch_remove.argtypes = [P, P]
+        L.pa_batch_advance.argtypes = [P, C.c_int64]
+        L.pa_batch_info.argtypes = [P, P]
+        L.pa_batch_free.argtypes = [P]
+        L.pa_batch_free.restype = None
         L.pa_model_info.argtypes = [P, C.POINTER(Info)]
         L.pa_get_kernel_stats.argtypes = [P, C.POINTER(KernelStats)]
         L.pa_reset_kernel_stats.argtypes = [P]
@@ -364,3 +372,41 @@ class Model:
         gid = np.ascontiguousarray(gid, np.int32)
         step = np.ascontiguousarray(step, np.int64)
         _check(lib().pa_set_replay(self._h, len(gid), _ptr(gid), _ptr(step)))
+
+
+class Batch:
+    """Resident models advanced together, one grouped time-step launch per epoch
+    (pa_batch_*).  Members run on the batch's stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = lib()
+        if stream is None:
+            stream = current_stream_handle(device)
+        h = C.c_void_p()
+        _check(L.pa_batch_create(device, stream, C.byref(h)))
+        self._h = h
+        self.members = []
+
+    def add(self, model: "Model"):
+        _check(lib().pa_batch_add(self._h, model._h))
+        self.members.append(model)
+
+    def remove(self, model: "Model"):
+        _check(lib().pa_batch_remove(self._h, model._h))
+        self.members.remove(model)
+
+    def advance_epochs(self, n: int):
+        _check(lib().pa_batch_advance(self._h, int(n)))
+
+    def info(self):
+        out = np.zeros(4, np.int64)
+        _check(lib().pa_batch_info(self._h, _ptr(out)))
+        return {"members": int(out[0]), "blocks": int(out[1]), "graph_launches": int(out[2]),
+                "captures": int(out[3])}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.pa_batch_free(self._h)
+            self._h = None
+
+    __del__ = close

@@ -18,14 +18,16 @@ from _nets import (caterpillar_net, compare, edge_net, extract, fork_net, hca_tr
 
 pytestmark = pytest.mark.gpu
 
-V_TOL = {E.PA_FP64: 1e-6, E.PA_MIXED: 1e-2, E.PA_FP32: 1e-2}   # mV
-W_RTOL = 1e-6
+V_TOL = {E.PA_FP64: 1e-6, E.PA_MIXED: 1e-2, E.PA_FP32: 0.5}   # mV
+W_RTOL = {E.PA_FP64: 1e-6, E.PA_MIXED: 1e-6, E.PA_FP32: 1e-3}
 T_TOL = 1e-3                                     # ms
-# PA_FP32 (plain FP32 conductances, the opt-in form) does not meet T_TOL on
-# networks: every step re-rounds each conductance, and the HH upstroke
-# amplifies that random walk into crossing-time errors of a few microseconds at
-# dt = 0.2 ms.  Its tests hold spike times to dt / 10 and report the error.
-T_TOL_FP32_FRAC_DT = 0.1
+# PA_FP32 (the opt-in form: conductances, calcium, HH and the plasticity
+# increments in FP32) does not meet the engine's tolerances on networks; its
+# measured errors against the oracle on these networks are up to 0.12 mV,
+# 0.09 ms (at dt 0.2 ms) and 1e-4 relative on the early-phase weight, with
+# identical spike counts.  Its tests hold it to a few times those: V within
+# 0.5 mV, spike times within dt / 2, weights within 1e-3 relative.
+T_TOL_FP32_FRAC_DT = 0.5
 PRECISIONS = [E.PA_FP64, E.PA_MIXED, E.PA_FP32]
 
 FIELDS = [(O.SYN_G, E.FIELD_G), (O.SYN_C, E.FIELD_C), (O.SYN_W, E.FIELD_W),
@@ -96,7 +98,7 @@ def check_state(o, m, precision, exact=False):
               f"max spike-time error {worst:.3e} ms")
     wo = o.syn(O.SYN_WEIGHT_TOTAL)
     wg = m.read_weights()
-    assert np.all(np.abs(wo - wg) <= W_RTOL * np.maximum(np.abs(wo), 1e-12) + 1e-15)
+    assert np.all(np.abs(wo - wg) <= W_RTOL[precision] * np.maximum(np.abs(wo), 1e-12) + 1e-15)
     if precision == E.PA_FP64:
         for fo, fg in FIELDS:
             a, b = o.syn(fo), m.read_state(fg)
@@ -179,7 +181,7 @@ def test_morphology_sweep_small_mixed_open_loop():
     check_state(o, m, E.PA_MIXED)
     for fo, fg in ((O.SYN_C, E.FIELD_C), (O.SYN_W, E.FIELD_W)):
         a, b = o.syn(fo), m.read_state(fg)
-        assert np.all(np.abs(a - b) <= W_RTOL * np.abs(a) + 1e-12), fg
+        assert np.all(np.abs(a - b) <= W_RTOL[E.PA_MIXED] * np.abs(a) + 1e-12), fg
 
 
 def _large_stdp_small():
@@ -214,7 +216,7 @@ def test_large_stdp_generator_mixed_open_loop():
     for fo, fg in ((O.SYN_W, E.FIELD_W), (O.SYN_APRE, E.FIELD_APRE),
                    (O.SYN_APOST, E.FIELD_APOST)):
         a, b = o.syn(fo), m.read_state(fg)
-        assert np.all(np.abs(a - b) <= W_RTOL * np.abs(a) + 1e-12), fg
+        assert np.all(np.abs(a - b) <= W_RTOL[E.PA_MIXED] * np.abs(a) + 1e-12), fg
 
 
 def test_short_epochs_equal_long_epochs():
@@ -245,7 +247,7 @@ def test_open_loop_replay_stc(precision):
     dv = compare(o.v(), m.read_state(E.FIELD_V))
     assert dv <= V_TOL[precision]
     wo, wg = o.syn(O.SYN_WEIGHT_TOTAL), m.read_weights()
-    assert np.all(np.abs(wo - wg) <= W_RTOL * np.abs(wo) + 1e-15)
+    assert np.all(np.abs(wo - wg) <= W_RTOL[precision] * np.abs(wo) + 1e-15)
 
 
 def test_poisson_train_ids_shared():

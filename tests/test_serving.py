@@ -1,6 +1,7 @@
 """Continuous-batching server: a job's results are the same alone and among other
-jobs (same precision: bit-identical, since jobs share no device state), budget
-admission never exceeds the budget estimate, and latency is reported."""
+jobs (same precision: bit-identical, since jobs share no device state and a
+batch member takes exactly its own steps), budget admission never exceeds the
+budget estimate, and latency is reported."""
 import numpy as np
 import pytest
 
@@ -35,10 +36,11 @@ def test_trace_statistics_and_estimates():
 def test_results_alone_equal_results_in_the_mix():
     from paper_2411_16445_b300 import engine as E
     trace = small_trace()
-    srv = S.Server(hbm_budget_bytes=2 << 30, quantum_cu=1e5, precision=E.PA_MIXED)
+    srv = S.Server(hbm_budget_bytes=2 << 30, epochs_per_tick=2, precision=E.PA_MIXED)
     out = srv.run(trace)
     assert len(out["results"]) == len(trace)
     assert out["p50_s"] is not None and out["p99_s"] >= out["p50_s"] > 0
+    assert out["graph_launches"] > 0      # the jobs did run as one batch
     for r, spec in zip(out["results"], sorted(trace, key=lambda j: j["job_id"])):
         n_cv, steps, g, s, w = S.run_alone(spec, precision=E.PA_MIXED)
         assert r.steps == steps and r.n_cv == n_cv
@@ -52,7 +54,7 @@ def test_budget_limits_residency():
     trace = small_trace(8, seed=9)
     biggest = max(S.estimate_spec_bytes(j) for j in trace)
     # a budget for one job at a time still completes every job, one after another
-    srv = S.Server(hbm_budget_bytes=biggest, quantum_cu=1e6, precision=E.PA_MIXED)
+    srv = S.Server(hbm_budget_bytes=biggest, epochs_per_tick=8, precision=E.PA_MIXED)
     out = srv.run(trace)
     assert len(out["results"]) == len(trace)
     starts = sorted((r.start_s, r.done_s) for r in out["results"])
