@@ -271,7 +271,7 @@ def time_e2e(net, precision, steps, device):
     from paper_2411_16445_b300 import engine as E
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
-    m = E.Model(net, precision=precision, device=device, flags=E.FLAG_AUTOTUNE)
+    m = E.Model(net, precision=precision, device=device)   # the default call: no autotuning
     info = m.info()
     h2d = info.device_bytes
     spikes = 0
@@ -287,7 +287,8 @@ def time_e2e(net, precision, steps, device):
     d2h = spikes * (4 + 8 + 8) + w.nbytes
     return {"value": cu / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d / steps),
             "d2h_bytes_per_step": int(d2h / steps), "wall_s": t,
-            "note": "includes pa_build_model (host descriptors -> HBM) and per-epoch spike read-back"}
+            "note": "includes pa_build_model with default flags (host descriptors -> HBM, "
+                    "no autotuning) and per-epoch spike read-back"}
 
 
 def oracle_sample(n_cells, n_shapes, budget_s=12.0, max_steps=40000, warm=2):

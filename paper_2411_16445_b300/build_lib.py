@@ -50,29 +50,41 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+# the bounds-checked build (-DPA_CHECKED): every kernel index checked against
+# its array, violations reported instead of performed; for the small parity
+# cases, never for timing
+CHECKED_LIB = os.path.join(HERE, "libplasticarbor_checked.so")
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False,
+          checked: bool = False) -> str:
+    if not checked:
+        build(force, verbose, ptxas_v, checked=True)
+    build_dir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib_path = CHECKED_LIB if checked else LIB
+    extra = ["-DPA_CHECKED"] if checked else []
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "plastic_arbor.h"))
     objs = []
     for unit, flags in UNITS.items():
         src = os.path.join(CSRC, unit)
-        obj = os.path.join(BUILD, unit + ".o")
+        obj = os.path.join(build_dir, unit + ".o")
         objs.append(obj)
         if force or _stale(obj, [src, *headers, __file__]):
-            cmd = [nvcc(), *ARCH, *COMMON, *flags, "-c", src, "-o", obj]
+            cmd = [nvcc(), *ARCH, *COMMON, *flags, *extra, "-c", src, "-o", obj]
             if ptxas_v:
                 cmd[1:1] = ["-Xptxas", "-v"]
             if verbose:
                 print(" ".join(cmd))
             subprocess.check_call(cmd)
-    if force or _stale(LIB, objs):
-        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs]
+    if force or _stale(lib_path, objs):
+        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", lib_path + ".tmp", *objs]
         if verbose:
             print(" ".join(cmd))
         subprocess.check_call(cmd)
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib_path + ".tmp", lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -200,6 +200,7 @@ struct EpochArgs {
   int32_t* err_flags;        // bit 0: probe overflow, bit 1: spike record full,
                              // bit 2: a bounded wait expired
   uint32_t wait_limit;       // polls of a bounded staging wait (0: the default)
+  int64_t n_row_elems;       // elements of the CV-row arrays (bounds of the checked build)
 };
 
 struct PoissonArgs {

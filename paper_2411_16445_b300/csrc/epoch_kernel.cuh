@@ -187,6 +187,21 @@ struct SomaHH<true> {
   }
 };
 
+// Bounds checks of the checked build (compiled with -DPA_CHECKED, for the
+// small parity cases): an index outside its array sets bit 3 of the model's
+// error word (reported by the next pa_sync) and the access is skipped.  In the
+// normal build PA_IN is the constant true.
+#ifdef PA_CHECKED
+__device__ __forceinline__ bool pa_in_range(int32_t* flags, int64_t i, int64_t n) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(flags, 8);
+  return false;
+}
+#define PA_IN(A, i, n) pa_in_range((A).err_flags, (int64_t)(i), (int64_t)(n))
+#else
+#define PA_IN(A, i, n) true
+#endif
+
 __device__ __forceinline__ uint32_t elem_of(int32_t row_base, int32_t row, int lane) {
   return ((uint32_t)(row_base + row) << 5) | (uint32_t)lane;
 }
@@ -582,6 +597,10 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
         if (lane == 0) {
           char* st = wbuf + si * ST::kBytes;
           const size_t r0 = (size_t)(sb + lo) * 32;
+          if (!PA_IN(A, r0 + (size_t)cnt * 32 - 1, D.n_elem)) {
+            mbar_expect_tx(&bar[si], 0u);  // nothing copied: the phase completes at once
+            return;
+          }
           mbar_expect_tx(&bar[si], (uint32_t)(cnt * rowb));
           bulk_load(st, D.cvf + r0, cnt * 128, &bar[si]);
           bulk_load(st + o_cm, cmg + r0, cnt * 256, &bar[si]);
@@ -624,6 +643,8 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           const int32_t cvf = ((const int32_t*)st)[r];
           if (cvf < 0) continue;
           const uint32_t e = ((uint32_t)(sb + lo + jj) << 5) | (uint32_t)lane;
+          if (!PA_IN(A, e, D.n_elem) || !PA_IN(A, elem_of(rb, cvf >> 3, lane), A.n_row_elems))
+            continue;
           const bool pre = (((const uint64_t*)(st + o_cm))[r] >> kk) & 1ull;
           const bool capre = calc && ((((const uint64_t*)(st + o_cam))[r] >> kk) & 1ull);
           const double cc = calc ? ((const double*)(st + o_c))[r] : 0.0;
@@ -672,6 +693,10 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
         if (lane == 0) {
           char* st = wbuf + s * ST::kBytes;
           const size_t r0 = (size_t)(rb + lo);
+          if (!PA_IN(A, (r0 + cnt) * 32 - 1, A.n_row_elems)) {
+            mbar_expect_tx(&bar[s], 0u);
+            return;
+          }
           mbar_expect_tx(&bar[s], cnt * ST::kBackRow);
           bulk_load(st + ST::oV, Vg + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oCDT, CDT + r0 * 32, cnt * ST::kD, &bar[s]);
@@ -719,6 +744,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           if (i >= n) continue;
           const int r = (i - lo) * 32 + lane;
           const uint32_t e = elem_of(rb, i, lane);
+          if (!PA_IN(A, e, A.n_row_elems)) continue;
           const double v = ((const double*)(st + ST::oV))[r];
           const double cdt = ((const double*)(st + ST::oCDT))[r];
           const double dcv = ((const double*)(st + ST::oDC))[r];
@@ -757,8 +783,8 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
                 xc = t.y;
               } else {
                 const uint32_t ec = elem_of(rb, och, lane);
-                fc = F[ec];
-                xc = XP[ec];
+                fc = PA_IN(A, ec, A.n_row_elems) ? F[ec] : 0.0;
+                xc = PA_IN(A, ec, A.n_row_elems) ? XP[ec] : 0.0;
               }
               const double ac = ((const double*)(st + ST::oAOCH))[r];
               d = fma(-fc, ac, d);
@@ -767,6 +793,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
               // several other children, highest index first, from the scratch arrays
               for (int ch = och; ch >= 0;) {
                 const uint32_t ec = elem_of(rb, ch, lane);
+                if (!PA_IN(A, ec, A.n_row_elems)) break;
                 const double ac = AA[ec];
                 d = fma(-F[ec], ac, d);
                 b = fma(-ac, XP[ec], b);
@@ -814,6 +841,10 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
         if (lane == 0) {
           char* st = wbuf + s * ST::kBytes;
           const size_t r0 = (size_t)(rb + lo);
+          if (!PA_IN(A, (r0 + cnt) * 32 - 1, A.n_row_elems)) {
+            mbar_expect_tx(&bar[s], 0u);
+            return;
+          }
           mbar_expect_tx(&bar[s], cnt * ST::kFwdRow);
           bulk_load(st + ST::fF, F + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::fXP, XP + r0 * 32, cnt * ST::kD, &bar[s]);
@@ -864,12 +895,12 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
               --depth;
               vp = depth < ST::kStackF ? stack1[depth * 32 + lane] : Vg[elem_of(rb, pi, lane)];
             } else if (pi != i - 1) {
-              vp = Vg[elem_of(rb, pi, lane)];
+              vp = PA_IN(A, elem_of(rb, pi, lane), A.n_row_elems) ? Vg[elem_of(rb, pi, lane)] : 0.0;
             }
           }
           const double vi = fma(-((const double*)(st + ST::fF))[r], vp,
                                 ((const double*)(st + ST::fXP))[r]);
-          Vg[elem_of(rb, i, lane)] = vi;
+          if (PA_IN(A, elem_of(rb, i, lane), A.n_row_elems)) Vg[elem_of(rb, i, lane)] = vi;
           if (TREE && (tf & kForkPop)) {
             if (depth < ST::kStackF) stack1[depth * 32 + lane] = vi;
             ++depth;

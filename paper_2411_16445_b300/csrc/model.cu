@@ -1457,6 +1457,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     M->d_ff_vdt = (double*)P8(o_ffvdt);
   }
   A.n_lanes = n_lanes;
+  A.n_row_elems = n_elem;
   A.n_streams = n_streams;
   M->mask_bases.clear();
   M->mask_elems.clear();
@@ -1596,6 +1597,9 @@ int check_device_errors(pa_model* M) {
   CUDA_TRY(cudaStreamSynchronize(M->stream));
   if (flags) {
     CUDA_TRY(cudaMemsetAsync(M->err_flags, 0, 4, M->stream));
+    if (flags & 8)
+      return set_err(PA_ERR_CUDA, "an index outside its array was caught by the bounds-checked "
+                                  "build and its access skipped; results invalid");
     if (flags & 4)
       return set_err(PA_ERR_TIMEOUT, "a bounded device wait expired (row staging); results invalid");
     return set_err(PA_ERR_CAPACITY, "%s%s",

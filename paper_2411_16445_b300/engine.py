@@ -14,7 +14,9 @@ from typing import Optional, Sequence, Tuple
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libplasticarbor.so")
+# PA_LIBRARY selects another build of the library (the bounds-checked one in
+# its tests); by default the in-tree libplasticarbor.so
+LIB_PATH = os.environ.get("PA_LIBRARY") or os.path.join(HERE, "libplasticarbor.so")
 
 PA_FP64, PA_MIXED, PA_FP32 = 0, 1, 2
 PA_SRC_POISSON = -1
