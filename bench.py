@@ -46,9 +46,11 @@ FALLBACK_HBM_GBS = 6400.0      # the profiling recipe's fallback when no measure
 SURVEY_BYTES_PER_CU = {"fp64": 60.0, "mixed": 45.0, "fp32": 45.0}
 # DRAM bytes per compartment-update of the epoch kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of a 65,536-cell launch of the
-# same generator, scaled to a full launch by the CUs it processes); None once
-# the kernel has changed since the counters were taken.
-TRAFFIC_B_PER_CU = {}
+# same generator, shape 0: 104.36 GB (mixed) and 104.29 GB (FP64) for 735.3 M
+# CU), scaled to a full launch by the CUs it processes, since traffic grows in
+# proportion to them; absent once the kernel has changed since the counters
+# were taken (and for the FP32-mechanism kernel, not captured).
+TRAFFIC_B_PER_CU = {"mixed": 141.9, "fp64": 141.8}
 
 
 def measured_peaks():
@@ -718,7 +720,9 @@ def main():
                 "algorithmic_note": "the survey's per-CU bytes for this network "
                                     "(hot-path scope table, measurement row) x CVs x steps of "
                                     "one launch / the launch's mean device time (CUDA events)",
-                "traffic_note": None if tb else "kernel changed since the last ncu capture",
+                "traffic_note": ("DRAM bytes per launch, scaled from one ncu capture of a "
+                                 f"65,536-cell launch ({tb} B/CU)") if tb else
+                                "not captured for this kernel",
                 "layout": {"bytes_per_cu": bpc, "achieved_gbs": bpc * cu_launch / t_launch / 1e9,
                            "frac": bpc * cu_launch / t_launch / 1e9 / hbm_peak,
                            "note": "bytes this engine's layout streams per CU (cable rows, "
