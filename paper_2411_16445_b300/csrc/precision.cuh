@@ -96,8 +96,31 @@ __device__ __forceinline__ double tm_add(double a, double b) { return __dadd_rn(
 // canonical synapse order.  start() opens the run with its first synapse (from
 // zero on the CV's first run of the step, else continuing the sums an earlier
 // stream left); add() takes the next synapse; store() writes the CV's sums.
+// A synapse's contribution C is formed once, on its own lane (contrib); the
+// wide kernel hands contributions to other lanes by shuffle (shfl_c).
 template <class T>
 struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
+  struct C {
+    T g, ge;
+  };
+  __device__ static __forceinline__ C contrib(T gv, T E) { return C{gv, tm_mul(gv, E)}; }
+  __device__ static __forceinline__ C shfl_c(C c, int src) {
+    return C{__shfl_sync(0xffffffffu, c.g, src), __shfl_sync(0xffffffffu, c.ge, src)};
+  }
+  __device__ __forceinline__ void start_c(C c, bool first, const T* gs, const T* es,
+                                          uint32_t ce) {
+    if (first) {
+      g = c.g;
+      e = c.ge;
+    } else {
+      g = tm_add(gs[ce], c.g);
+      e = tm_add(es[ce], c.ge);
+    }
+  }
+  __device__ __forceinline__ void add_c(C c) {
+    g = tm_add(g, c.g);
+    e = tm_add(e, c.ge);
+  }
   T g, e;
   __device__ __forceinline__ void start(T gv, T E, bool first, const T* gs, const T* es,
                                         uint32_t ce) {
@@ -128,6 +151,17 @@ struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
 };
 
 struct AccFF {  // mixed: the run's conductance in float-float, FP64 at its end
+  using C = float2;
+  __device__ static __forceinline__ C contrib(float2 gv, double) { return gv; }
+  __device__ static __forceinline__ C shfl_c(C c, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, c.x, src), __shfl_sync(0xffffffffu, c.y, src));
+  }
+  __device__ __forceinline__ void start_c(C c, bool first_on_cv, const double*, const double*,
+                                          uint32_t) {
+    g = c;
+    first = first_on_cv;
+  }
+  __device__ __forceinline__ void add_c(C c) { g = ff_add_acc(g, c); }
   float2 g;
   bool first;
   __device__ __forceinline__ void start(float2 gv, double, bool first_on_cv, const double*,

@@ -130,19 +130,21 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         const int len = valid ? lane - src0 + 1 : 0;
         const int maxlen = (int)__reduce_max_sync(full, (unsigned)len);
         const int32_t cs = __shfl_sync(full, cvf, src0);
-        const TG g0 = PR::shfl(gv, src0);
-        typename PR::Acc acc;
+        using Acc = typename PR::Acc;
+        const typename Acc::C cv = Acc::contrib(gv, E);  // formed once, on its own lane
+        const typename Acc::C c0 = Acc::shfl_c(cv, src0);
+        Acc acc;
         if (seg0 < 0) {
           acc = carry;
-          acc.add(g0, E);
+          acc.add_c(c0);
         } else {
           // continues the sums of earlier streams unless first on its CV
-          acc.start(g0, E, !valid || (cs & 1), GS, ES, (uint32_t)(e0 + (cs >> 3)));
+          acc.start_c(c0, !valid || (cs & 1), GS, ES, (uint32_t)(e0 + (cs >> 3)));
         }
         for (int it = 1; it < maxlen; ++it) {
           const int src = src0 + it < 31 ? src0 + it : 31;
-          const TG gi = PR::shfl(gv, src);
-          if (it < len) acc.add(gi, E);
+          const typename Acc::C ci = Acc::shfl_c(cv, src);
+          if (it < len) acc.add_c(ci);
         }
         if (valid && (cvf & 4)) acc.store(GS, ES, (uint32_t)(e0 + (cvf >> 3)), E);
         carry = acc.shfl(31);
