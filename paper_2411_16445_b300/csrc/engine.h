@@ -167,6 +167,9 @@ struct EpochArgs {
   // calcium per CV [umol/l], its backward-Euler matrix (diagonal, coupling),
   // V/dt and V per CV, the step's inflow per CV (summed by the synapse phase)
   int32_t ca_stream;         // index of the HCA stream or -1
+  // every stream's reversal potential is exactly +0: g E is the zero of g's
+  // sign, so the per-CV g E sums are signed zeros (kernels specialise on this)
+  int32_t es_zero;
   double ca_tau, ca_rate;    // tau_C, dt / tau_C
   double* ca_cv;
   double* ca_src;
@@ -267,17 +270,18 @@ int launch_init_gates(const double* v, void* gate, int64_t n_lanes, const uint8_
 // One launch over several models (narrow bin only): block b runs 4 groups from
 // group d_bmap[b].y of model d_bmap[b].x, whose arguments are d_args[d_bmap[b].x].
 constexpr int kGroupedWarps = 4;
+// (ez: every member model has es_zero set)
 int launch_epoch_grouped_fp64(const EpochArgs* d_args, const int2* d_bmap, int n_blocks, bool tree,
-                              void* stream);
+                              bool ez, void* stream);
 int launch_epoch_grouped_mixed(const EpochArgs* d_args, const int2* d_bmap, int n_blocks,
-                               bool tree, void* stream);
+                               bool tree, bool ez, void* stream);
 int launch_epoch_grouped_fp32(const EpochArgs* d_args, const int2* d_bmap, int n_blocks, bool tree,
-                              void* stream);
+                              bool ez, void* stream);
 inline int launch_epoch_grouped(int prec, const EpochArgs* d_args, const int2* d_bmap,
-                                int n_blocks, bool tree, void* stream) {
-  return prec == 1   ? launch_epoch_grouped_mixed(d_args, d_bmap, n_blocks, tree, stream)
-         : prec == 2 ? launch_epoch_grouped_fp32(d_args, d_bmap, n_blocks, tree, stream)
-                     : launch_epoch_grouped_fp64(d_args, d_bmap, n_blocks, tree, stream);
+                                int n_blocks, bool tree, bool ez, void* stream) {
+  return prec == 1   ? launch_epoch_grouped_mixed(d_args, d_bmap, n_blocks, tree, ez, stream)
+         : prec == 2 ? launch_epoch_grouped_fp32(d_args, d_bmap, n_blocks, tree, ez, stream)
+                     : launch_epoch_grouped_fp64(d_args, d_bmap, n_blocks, tree, ez, stream);
 }
 // Graph launches: zero the mask slot of the clock's epoch in every mask array,
 // then advance the clock by one epoch (events.cu).

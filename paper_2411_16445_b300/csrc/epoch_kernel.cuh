@@ -314,6 +314,18 @@ struct Stage {
   static constexpr int kWarpBytes = kStages * kBytes + 64 + kStackBytes;  // + mbarriers
 };
 
+// b + es for a CV whose g E sum es is a signed zero (every stream's E is +0):
+// b itself unless b is -0, when the stored es decides (a call, so that the
+// compiler cannot turn the rare branch into FP64 work on every row).
+template <class TS>
+__device__ __noinline__ double ez_fix(double b, const TS* es, uint32_t e) {
+  return b + widen_f32(es[e]);
+}
+template <class TS>
+__device__ __forceinline__ double ez_add(double b, const TS* es, uint32_t e) {
+  return __double_as_longlong(b) == (long long)0x8000000000000000ull ? ez_fix(b, es, e) : b;
+}
+
 // One synapse's step (rows a1, a2, a4): this step's conductance event, the
 // delayed calcium event and the POST_EVENT of the cell's spike in the previous
 // step, then the plasticity update of its kind (Eqs. weight_graupner_brunel,
@@ -503,7 +515,7 @@ __device__ __noinline__ void hca_stream(const EpochArgs& A, int s, int g, int la
 
 // The launch window of one warp: group g (32 cells, one per lane) of the model
 // A, with the warp's shared-memory stages at wbuf.
-template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth>
+template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth, bool EZ>
 __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char* wbuf) {
   using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
   using TS = typename PR::S;
@@ -658,9 +670,9 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           // per-CV sums over the run of same-CV synapses, in canonical order
           // (cvf = (cv << 3) | first-on-CV (1) | run start (2) | run end (4))
           const uint32_t ce = elem_of(rb, cvf >> 3, lane);
-          if (cvf & 2) acc.start(gv, E, (cvf & 1) != 0, GS, ES, ce);
-          else acc.add(gv, E);
-          if (cvf & 4) acc.store(GS, ES, ce, E);
+          if (cvf & 2) acc.template start<EZ>(gv, E, (cvf & 1) != 0, GS, ES, ce);
+          else acc.template add<EZ>(gv, E);
+          if (cvf & 4) acc.template store<EZ>(GS, ES, ce, E);
           G[e] = PR::decay(gv, dg);
         }
       }
@@ -697,14 +709,15 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
             mbar_expect_tx(&bar[s], 0u);
             return;
           }
-          mbar_expect_tx(&bar[s], cnt * ST::kBackRow);
+          // with EZ the g E sums are signed zeros: not staged (see ez_add)
+          mbar_expect_tx(&bar[s], cnt * (ST::kBackRow - (EZ ? ST::kM : 0)));
           bulk_load(st + ST::oV, Vg + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oCDT, CDT + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oDC, DC + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oEM, EM + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oA, AA + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kM, &bar[s]);
-          bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kM, &bar[s]);
+          if (!EZ) bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kM, &bar[s]);
           if (TREE) {
             bulk_load(st + ST::oPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
             bulk_load(st + ST::oOCH, A.och_head + r0 * 32, cnt * ST::kI, &bar[s]);
@@ -751,7 +764,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           int pi = i - 1;
           if (TREE && i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
           const double gsv = widen_f32(((const TS*)(st + ST::oGS))[r]);
-          const double esv = widen_f32(((const TS*)(st + ST::oES))[r]);
+          const double esv = EZ ? 0.0 : widen_f32(((const TS*)(st + ST::oES))[r]);
           double d, b;
           if (i == 0) {
             v0_old = v;
@@ -759,15 +772,16 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
               double gmt, emt;
               soma.currents(A, L, gmt, emt);
               d = (dcv + gmt) + gsv;
-              b = (fma(cdt, v, emt) + iinj) + esv;
+              b = fma(cdt, v, emt) + iinj;
             } else {
               d = dcv + gsv;
-              b = (fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + iinj) + esv;
+              b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + iinj;
             }
           } else {
             d = dcv + gsv;
-            b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + esv;
+            b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]);
           }
+          b = EZ ? ez_add(b, (const TS*)ES, e) : b + esv;
           uint8_t tf = 0;
           if (TREE) {
             if (ST::kStacks) tf = ((const uint8_t*)(st + ST::oTF))[r];
@@ -965,12 +979,12 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
 }
 
 template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
-          int kStackDepth>
+          int kStackDepth, bool EZ>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const EpochArgs A) {
   using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
   extern __shared__ __align__(128) char smem_raw[];
   const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  epoch_warp<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>(
+  epoch_warp<PR, TREE, kRowsBack, kRowsFwd, kStackDepth, EZ>(
       A, g, smem_raw + (threadIdx.x >> 5) * ST::kWarpBytes);
 }
 
@@ -983,7 +997,7 @@ constexpr int kArgsSmemBytes = (int)((sizeof(EpochArgs) + 127) / 128 * 128);
 static_assert(sizeof(EpochArgs) % 8 == 0, "launch arguments copy as 8-byte words");
 
 template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
-          int kStackDepth>
+          int kStackDepth, bool EZ>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     epoch_kernel_grouped(const EpochArgs* __restrict__ args, const int2* __restrict__ bmap) {
   using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
@@ -994,12 +1008,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   long long* dst = (long long*)args_raw;
   for (int i = threadIdx.x; i < (int)(sizeof(EpochArgs) / 8); i += blockDim.x) dst[i] = src[i];
   __syncthreads();
-  epoch_warp<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>(
+  epoch_warp<PR, TREE, kRowsBack, kRowsFwd, kStackDepth, EZ>(
       *(const EpochArgs*)args_raw, bm.y + (int)(threadIdx.x >> 5),
       smem_raw + (threadIdx.x >> 5) * ST::kWarpBytes);
 }
 
-template <class PR, bool TREE, int RB, int RF, int WPB, int MB, int SB>
+template <class PR, bool TREE, int RB, int RF, int WPB, int MB, int SB, bool EZ>
 int launch_epoch_t(const EpochArgs& a, void* stream) {
   constexpr int warps_per_block = WPB;
   const int threads = 32 * warps_per_block;
@@ -1012,12 +1026,12 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
   if (e != cudaSuccess) return (int)e;
   static bool attr_set[64] = {false};  // per device; setting it twice is harmless
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(epoch_kernel<PR, TREE, RB, RF, 32 * WPB, MB, SB>,
+    e = cudaFuncSetAttribute(epoch_kernel<PR, TREE, RB, RF, 32 * WPB, MB, SB, EZ>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  epoch_kernel<PR, TREE, RB, RF, 32 * WPB, MB, SB>
+  epoch_kernel<PR, TREE, RB, RF, 32 * WPB, MB, SB, EZ>
       <<<blocks, threads, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
@@ -1030,19 +1044,19 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // per chunk and 8 entries (many nested forks), FP64 shapes 3 and 4 take 4 rows
 // and 2 entries, the mixed shapes 4 rows and 6 entries; shape 5 has no stacks
 // (trees with long branches and few forks); 12 warps per SM fit in each case.
-template <class PR, bool TREE>
+template <class PR, bool TREE, bool EZ>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   constexpr bool f64tree = TREE && sizeof(typename PR::S) == 8;
   constexpr int RB0 = f64tree ? 3 : 4, SB0 = f64tree ? 8 : 6;
   constexpr int RB6 = f64tree ? 5 : 6;
   constexpr int SB4 = f64tree ? 2 : 6;
   switch (shape) {
-    case 1: return launch_epoch_t<PR, TREE, 3, 9, 4, 4, 8>(a, stream);    // 16 warps per SM
-    case 2: return launch_epoch_t<PR, TREE, RB6, 16, 2, 4, 8>(a, stream); // 8 warps, long chunks
-    case 3: return launch_epoch_t<PR, TREE, 4, 12, 2, 6, SB4>(a, stream); // 2-warp blocks
-    case 4: return launch_epoch_t<PR, TREE, 4, 12, 1, 12, SB4>(a, stream);// 1-warp blocks
-    case 5: return launch_epoch_t<PR, TREE, 4, 12, 4, 3, 0>(a, stream);   // trees: no stacks
-    default: return launch_epoch_t<PR, TREE, RB0, 12, 4, 3, SB0>(a, stream);  // 12 warps per SM
+    case 1: return launch_epoch_t<PR, TREE, 3, 9, 4, 4, 8, EZ>(a, stream);    // 16 warps per SM
+    case 2: return launch_epoch_t<PR, TREE, RB6, 16, 2, 4, 8, EZ>(a, stream); // 8 warps, long chunks
+    case 3: return launch_epoch_t<PR, TREE, 4, 12, 2, 6, SB4, EZ>(a, stream); // 2-warp blocks
+    case 4: return launch_epoch_t<PR, TREE, 4, 12, 1, 12, SB4, EZ>(a, stream);// 1-warp blocks
+    case 5: return launch_epoch_t<PR, TREE, 4, 12, 4, 3, 0, EZ>(a, stream);   // trees: no stacks
+    default: return launch_epoch_t<PR, TREE, RB0, 12, 4, 3, SB0, EZ>(a, stream);  // 12 warps per SM
   }
 }
 
@@ -1051,7 +1065,7 @@ int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
 // shared memory).  Results equal those of every other shape.
 constexpr int kGroupedWarpsPerBlock = 4;
 
-template <class PR, bool TREE, int RB, int RF, int MB, int SB>
+template <class PR, bool TREE, int RB, int RF, int MB, int SB, bool EZ>
 int launch_epoch_grouped_t(const EpochArgs* d_args, const int2* d_bmap, int n_blocks,
                            void* stream) {
   constexpr int WPB = kGroupedWarpsPerBlock;
@@ -1062,27 +1076,37 @@ int launch_epoch_grouped_t(const EpochArgs* d_args, const int2* d_bmap, int n_bl
   if (e != cudaSuccess) return (int)e;
   static bool attr_set[64] = {false};
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(epoch_kernel_grouped<PR, TREE, RB, RF, 32 * WPB, MB, SB>,
+    e = cudaFuncSetAttribute(epoch_kernel_grouped<PR, TREE, RB, RF, 32 * WPB, MB, SB, EZ>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  epoch_kernel_grouped<PR, TREE, RB, RF, 32 * WPB, MB, SB>
+  epoch_kernel_grouped<PR, TREE, RB, RF, 32 * WPB, MB, SB, EZ>
       <<<n_blocks, 32 * WPB, smem, (cudaStream_t)stream>>>(d_args, d_bmap);
   return (int)cudaGetLastError();
 }
 
 template <class PR>
 int launch_epoch_grouped_impl(const EpochArgs* d_args, const int2* d_bmap, int n_blocks,
-                              bool tree, void* stream) {
-  return tree ? launch_epoch_grouped_t<PR, true, 4, 12, 3, 0>(d_args, d_bmap, n_blocks, stream)
-              : launch_epoch_grouped_t<PR, false, 4, 12, 3, 6>(d_args, d_bmap, n_blocks, stream);
+                              bool tree, bool ez, void* stream) {
+  if (ez)
+    return tree ? launch_epoch_grouped_t<PR, true, 4, 12, 3, 0, true>(d_args, d_bmap, n_blocks,
+                                                                      stream)
+                : launch_epoch_grouped_t<PR, false, 4, 12, 3, 6, true>(d_args, d_bmap, n_blocks,
+                                                                       stream);
+  return tree ? launch_epoch_grouped_t<PR, true, 4, 12, 3, 0, false>(d_args, d_bmap, n_blocks,
+                                                                     stream)
+              : launch_epoch_grouped_t<PR, false, 4, 12, 3, 6, false>(d_args, d_bmap, n_blocks,
+                                                                      stream);
 }
 
 template <class PR>
 int launch_epoch_impl(const EpochArgs& a, bool tree, int shape, void* stream) {
-  return tree ? launch_epoch_shape<PR, true>(a, shape, stream)
-              : launch_epoch_shape<PR, false>(a, shape, stream);
+  if (a.es_zero)
+    return tree ? launch_epoch_shape<PR, true, true>(a, shape, stream)
+                : launch_epoch_shape<PR, false, true>(a, shape, stream);
+  return tree ? launch_epoch_shape<PR, true, false>(a, shape, stream)
+              : launch_epoch_shape<PR, false, false>(a, shape, stream);
 }
 
 }  // namespace pa

@@ -1459,6 +1459,13 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   A.n_lanes = n_lanes;
   A.n_row_elems = n_elem;
   A.n_streams = n_streams;
+  // every reversal potential exactly +0 (a bit test: -0 does not qualify)
+  A.es_zero = 1;
+  for (int s = 0; s < n_streams; ++s) {
+    uint64_t eb;
+    std::memcpy(&eb, &M->sp[s].e, sizeof eb);
+    if (eb != 0) A.es_zero = 0;
+  }
   M->mask_bases.clear();
   M->mask_elems.clear();
   for (int s = 0; s < n_streams; ++s) {
@@ -2555,7 +2562,10 @@ int batch_enqueue_epoch(pa_batch* B, cudaStream_t st) {
     }
   }
   if (rc == 0) rc = join();
-  if (rc == 0) rc = launch_epoch_grouped(B->precision, B->d_args, B->d_bmap, B->n_blocks, B->tree, st);
+  bool ez = true;  // the E = +0 kernels serve the batch only if they serve every member
+  for (const pa_model* M : B->members) ez = ez && M->ea.es_zero != 0;
+  if (rc == 0)
+    rc = launch_epoch_grouped(B->precision, B->d_args, B->d_bmap, B->n_blocks, B->tree, ez, st);
   if (rc == 0) rc = fork();
   for (size_t j = 0; j < B->members.size() && rc == 0; ++j) {
     pa_model* M = B->members[j];

@@ -92,21 +92,51 @@ __device__ __forceinline__ double tm_mul(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ double tm_add(double a, double b) { return __dadd_rn(a, b); }
 
 // ---------------------------------------------------------------------------
+// Reversal potentials of exactly +0 (EZ).  For a finite g, g (+0) is the zero
+// with g's sign, and a sum of signed zeros is -0 exactly when every term is
+// -0: the IEEE results follow from the sign bits alone, so a model whose every
+// stream has E = +0 forms its per-CV g E sums on the integer pipes.
+__device__ __forceinline__ double zero_of(double g) {
+  return __longlong_as_double(__double_as_longlong(g) & (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ float zero_of(float g) {
+  return __uint_as_float(__float_as_uint(g) & 0x80000000u);
+}
+// a + b for signed zeros a, b
+__device__ __forceinline__ double zsum(double a, double b) {
+  return __longlong_as_double(__double_as_longlong(a) & __double_as_longlong(b));
+}
+__device__ __forceinline__ float zsum(float a, float b) {
+  return __uint_as_float(__float_as_uint(a) & __float_as_uint(b));
+}
+
+// ---------------------------------------------------------------------------
 // Per-CV sum accumulators over one run of same-CV synapses of a stream, in the
 // canonical synapse order.  start() opens the run with its first synapse (from
 // zero on the CV's first run of the step, else continuing the sums an earlier
 // stream left); add() takes the next synapse; store() writes the CV's sums.
 // A synapse's contribution C is formed once, on its own lane (contrib); the
-// wide kernel hands contributions to other lanes by shuffle (shfl_c).
+// wide kernel hands contributions to other lanes by shuffle (shfl_c).  With
+// EZ (every stream's E is +0) the g E sums are signed zeros (zero_of, zsum).
 template <class T>
 struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
   struct C {
     T g, ge;
   };
-  __device__ static __forceinline__ C contrib(T gv, T E) { return C{gv, tm_mul(gv, E)}; }
+  template <bool EZ>
+  __device__ static __forceinline__ T ge_of(T gv, T E) {
+    return EZ ? zero_of(gv) : tm_mul(gv, E);
+  }
+  template <bool EZ>
+  __device__ static __forceinline__ T e_add(T a, T b) {
+    return EZ ? zsum(a, b) : tm_add(a, b);
+  }
+  template <bool EZ>
+  __device__ static __forceinline__ C contrib(T gv, T E) { return C{gv, ge_of<EZ>(gv, E)}; }
   __device__ static __forceinline__ C shfl_c(C c, int src) {
     return C{__shfl_sync(0xffffffffu, c.g, src), __shfl_sync(0xffffffffu, c.ge, src)};
   }
+  template <bool EZ>
   __device__ __forceinline__ void start_c(C c, bool first, const T* gs, const T* es,
                                           uint32_t ce) {
     if (first) {
@@ -114,30 +144,34 @@ struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
       e = c.ge;
     } else {
       g = tm_add(gs[ce], c.g);
-      e = tm_add(es[ce], c.ge);
+      e = e_add<EZ>(es[ce], c.ge);
     }
   }
+  template <bool EZ>
   __device__ __forceinline__ void add_c(C c) {
     g = tm_add(g, c.g);
-    e = tm_add(e, c.ge);
+    e = e_add<EZ>(e, c.ge);
   }
   T g, e;
+  template <bool EZ>
   __device__ __forceinline__ void start(T gv, T E, bool first, const T* gs, const T* es,
                                         uint32_t ce) {
-    const T ge = tm_mul(gv, E);
+    const T ge = ge_of<EZ>(gv, E);
     if (first) {
       g = gv;
       e = ge;
     } else {
       g = tm_add(gs[ce], gv);
-      e = tm_add(es[ce], ge);
+      e = e_add<EZ>(es[ce], ge);
     }
   }
+  template <bool EZ>
   __device__ __forceinline__ void add(T gv, T E) {
-    const T ge = tm_mul(gv, E);
+    const T ge = ge_of<EZ>(gv, E);
     g = tm_add(g, gv);
-    e = tm_add(e, ge);
+    e = e_add<EZ>(e, ge);
   }
+  template <bool EZ>
   __device__ __forceinline__ void store(T* gs, T* es, uint32_t ce, T) const {
     gs[ce] = g;
     es[ce] = e;
@@ -152,33 +186,39 @@ struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
 
 struct AccFF {  // mixed: the run's conductance in float-float, FP64 at its end
   using C = float2;
+  template <bool EZ>
   __device__ static __forceinline__ C contrib(float2 gv, double) { return gv; }
   __device__ static __forceinline__ C shfl_c(C c, int src) {
     return make_float2(__shfl_sync(0xffffffffu, c.x, src), __shfl_sync(0xffffffffu, c.y, src));
   }
+  template <bool EZ>
   __device__ __forceinline__ void start_c(C c, bool first_on_cv, const double*, const double*,
                                           uint32_t) {
     g = c;
     first = first_on_cv;
   }
+  template <bool EZ>
   __device__ __forceinline__ void add_c(C c) { g = ff_add_acc(g, c); }
   float2 g;
   bool first;
+  template <bool EZ>
   __device__ __forceinline__ void start(float2 gv, double, bool first_on_cv, const double*,
                                         const double*, uint32_t) {
     g = gv;
     first = first_on_cv;
   }
+  template <bool EZ>
   __device__ __forceinline__ void add(float2 gv, double) { g = ff_add_acc(g, gv); }
+  template <bool EZ>
   __device__ __forceinline__ void store(double* gs, double* es, uint32_t ce, double E) const {
     const double s = ff_to_d(g);
-    const double se = __dmul_rn(s, E);
+    const double se = EZ ? zero_of(s) : __dmul_rn(s, E);
     if (first) {
       gs[ce] = s;
       es[ce] = se;
     } else {
       gs[ce] = __dadd_rn(gs[ce], s);
-      es[ce] = __dadd_rn(es[ce], se);
+      es[ce] = EZ ? zsum(es[ce], se) : __dadd_rn(es[ce], se);
     }
   }
   __device__ __forceinline__ AccFF shfl(int src) const {

@@ -9,7 +9,7 @@ int launch_epoch_fp32(const EpochArgs& a, bool tree, int shape, void* stream, co
   return launch_bins<PrecF32>(a, tree, shape, stream, side);
 }
 int launch_epoch_grouped_fp32(const EpochArgs* d_args, const int2* d_bmap, int n_blocks, bool tree,
-                            void* stream) {
-  return launch_epoch_grouped_impl<PrecF32>(d_args, d_bmap, n_blocks, tree, stream);
+                            bool ez, void* stream) {
+  return launch_epoch_grouped_impl<PrecF32>(d_args, d_bmap, n_blocks, tree, ez, stream);
 }
 }  // namespace pa

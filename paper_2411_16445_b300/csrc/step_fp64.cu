@@ -10,8 +10,8 @@ int launch_epoch_fp64(const EpochArgs& a, bool tree, int shape, void* stream, co
   return launch_bins<PrecF64>(a, tree, shape, stream, side);
 }
 int launch_epoch_grouped_fp64(const EpochArgs* d_args, const int2* d_bmap, int n_blocks, bool tree,
-                            void* stream) {
-  return launch_epoch_grouped_impl<PrecF64>(d_args, d_bmap, n_blocks, tree, stream);
+                            bool ez, void* stream) {
+  return launch_epoch_grouped_impl<PrecF64>(d_args, d_bmap, n_blocks, tree, ez, stream);
 }
 // Steady-state HH gates x_inf = alpha / (alpha + beta) at each soma's v_init.
 __global__ void init_gates_kernel(const double* v, double* gate, int64_t n_lanes,

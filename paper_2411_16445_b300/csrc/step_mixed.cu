@@ -12,7 +12,7 @@ int launch_epoch_mixed(const EpochArgs& a, bool tree, int shape, void* stream, c
   return launch_bins<PrecMix>(a, tree, shape, stream, side);
 }
 int launch_epoch_grouped_mixed(const EpochArgs* d_args, const int2* d_bmap, int n_blocks, bool tree,
-                            void* stream) {
-  return launch_epoch_grouped_impl<PrecMix>(d_args, d_bmap, n_blocks, tree, stream);
+                            bool ez, void* stream) {
+  return launch_epoch_grouped_impl<PrecMix>(d_args, d_bmap, n_blocks, tree, ez, stream);
 }
 }  // namespace pa

@@ -32,7 +32,7 @@
 
 namespace pa {
 
-template <class PR>
+template <class PR, bool EZ>
 __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   using TS = typename PR::S;
   using TG = typename PR::G;
@@ -131,22 +131,22 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         const int maxlen = (int)__reduce_max_sync(full, (unsigned)len);
         const int32_t cs = __shfl_sync(full, cvf, src0);
         using Acc = typename PR::Acc;
-        const typename Acc::C cv = Acc::contrib(gv, E);  // formed once, on its own lane
+        const typename Acc::C cv = Acc::template contrib<EZ>(gv, E);  // once, on its own lane
         const typename Acc::C c0 = Acc::shfl_c(cv, src0);
         Acc acc;
         if (seg0 < 0) {
           acc = carry;
-          acc.add_c(c0);
+          acc.template add_c<EZ>(c0);
         } else {
           // continues the sums of earlier streams unless first on its CV
-          acc.start_c(c0, !valid || (cs & 1), GS, ES, (uint32_t)(e0 + (cs >> 3)));
+          acc.template start_c<EZ>(c0, !valid || (cs & 1), GS, ES, (uint32_t)(e0 + (cs >> 3)));
         }
         for (int it = 1; it < maxlen; ++it) {
           const int src = src0 + it < 31 ? src0 + it : 31;
           const typename Acc::C ci = Acc::shfl_c(cv, src);
-          if (it < len) acc.add_c(ci);
+          if (it < len) acc.template add_c<EZ>(ci);
         }
-        if (valid && (cvf & 4)) acc.store(GS, ES, (uint32_t)(e0 + (cvf >> 3)), E);
+        if (valid && (cvf & 4)) acc.template store<EZ>(GS, ES, (uint32_t)(e0 + (cvf >> 3)), E);
         carry = acc.shfl(31);
         if (stc) {
           // the cell's S = sum |h - h0| over its STC synapses, in order
@@ -178,18 +178,19 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         // elimination
         double nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be], nem = EM[e0 + be],
                na = AA[e0 + be];
-        TS ngs = GS[e0 + be], nes = ES[e0 + be];
+        TS ngs = GS[e0 + be], nes = EZ ? TS(0) : ES[e0 + be];
         int noch = PAR ? OCH[e0 + be] : -1;
         for (int i = be; i >= bs; --i) {
           const int64_t ei = e0 + i;
           const double v = nv, cdt = ncdt, dcv = ndc, emv = nem, ai = na;
           const double gsv = widen_f32(ngs);
-          const double esv = widen_f32(nes);
+          const double esv = widen_f32(nes);  // (EZ: unused, see ez_add)
           const int och = noch;
           if (i > bs) {
             const int64_t en = ei - 1;
             nv = Vg[en]; ncdt = CDT[en]; ndc = DC[en]; nem = EM[en]; na = AA[en];
-            ngs = GS[en]; nes = ES[en];
+            ngs = GS[en];
+            if (!EZ) nes = ES[en];
             if (PAR) noch = OCH[en];
           }
           double d, bb;
@@ -199,15 +200,16 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
               double gmt, emt;
               soma.currents(A, L, gmt, emt);
               d = (dcv + gmt) + gsv;
-              bb = (fma(cdt, v, emt) + iinj) + esv;
+              bb = fma(cdt, v, emt) + iinj;
             } else {
               d = dcv + gsv;
-              bb = (fma(cdt, v, emv) + iinj) + esv;
+              bb = fma(cdt, v, emv) + iinj;
             }
           } else {
             d = dcv + gsv;
-            bb = fma(cdt, v, emv) + esv;
+            bb = fma(cdt, v, emv);
           }
+          bb = EZ ? ez_add(bb, (const TS*)ES, (uint32_t)ei) : bb + esv;
           if (PAR) {
             // other children, highest index first (eliminated at lower levels)
             for (int ch = och; ch >= 0; ch = OCN[e0 + ch]) {
@@ -384,7 +386,10 @@ int launch_wide_impl(const EpochArgs& a, void* stream) {
   if (a.n_wide <= 0) return 0;
   const int threads = 128;
   const int blocks = (int)(((int64_t)a.n_wide * 32 + threads - 1) / threads);
-  wide_kernel<PR><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
+  if (a.es_zero)
+    wide_kernel<PR, true><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
+  else
+    wide_kernel<PR, false><<<blocks, threads, 0, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 
