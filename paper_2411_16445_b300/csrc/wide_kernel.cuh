@@ -32,6 +32,8 @@
 
 namespace pa {
 
+constexpr int kWideFwdChunk = 4;  // forward-pass rows whose f and x' load together
+
 template <class PR, bool EZ>
 __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   using TS = typename PR::S;
@@ -257,17 +259,25 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         } else {
           vp = Vg[e0 + PAR[e0 + bs]];
         }
-        double nf = i <= be ? F[e0 + i] : 0.0, nx = i <= be ? XP[e0 + i] : 0.0;
-        for (; i <= be; ++i) {
-          const int64_t ei = e0 + i;
-          const double fi = nf, xi = nx;
-          if (i < be) {
-            nf = F[ei + 1];
-            nx = XP[ei + 1];
+        // a chunk of the branch's f and x' is loaded at once (the chain has one
+        // FP64 operation per row, far shorter than a load's latency)
+        for (; i <= be; i += kWideFwdChunk) {
+          double fr[kWideFwdChunk], xr[kWideFwdChunk];
+#pragma unroll
+          for (int q = 0; q < kWideFwdChunk; ++q) {
+            if (i + q <= be) {
+              fr[q] = F[e0 + i + q];
+              xr[q] = XP[e0 + i + q];
+            }
           }
-          const double vi = fma(-fi, vp, xi);
-          Vg[ei] = vi;
-          vp = vi;
+#pragma unroll
+          for (int q = 0; q < kWideFwdChunk; ++q) {
+            if (i + q <= be) {
+              const double vi = fma(-fr[q], vp, xr[q]);
+              Vg[e0 + i + q] = vi;
+              vp = vi;
+            }
+          }
         }
       }
       __syncwarp();
