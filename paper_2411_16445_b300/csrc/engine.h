@@ -115,6 +115,9 @@ struct EpochArgs {
   const WideCell* wcell; // [n_wide]
   const int32_t* wbr_s;  // branch first row
   const int32_t* wbr_e;  // branch last row
+  const int32_t* wbr_p;  // parent row of the branch's first row (-1: the root branch)
+  const int32_t* wbr_c;  // first child of the branch's last row (-1: none)
+  const int32_t* wbr_o;  // highest other child of the branch's last row (-1: none)
   const int32_t* wlvl;   // level offsets
   double dt;
   // groups / lanes

@@ -927,6 +927,10 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // level.
   std::vector<WideCell> h_wcell(n_wide);
   std::vector<int32_t> h_wbr_s, h_wbr_e, h_wlvl;
+  // per branch: the parent row of its first row, and the first and the highest
+  // other child of its last row (-1: none), so that the kernel loads the
+  // children's values when it starts the branch
+  std::vector<int32_t> h_wbr_p, h_wbr_c, h_wbr_o;
   for (int64_t j = 0; j < n_wide; ++j) {
     const pa_morphology& gm = morphs[cells[order_w[j]].morph];
     const int n = gm.n_cv;
@@ -964,10 +968,17 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       while (b < nb && lvl[ordb[b]] < lv) ++b;
       h_wlvl.push_back(b);
     }
+    std::vector<int32_t> och(n, -1);  // highest non-first child
+    for (int i = 1; i < n; ++i)
+      if (i != gm.parent[i] + 1) och[gm.parent[i]] = std::max(och[gm.parent[i]], i);
     for (int q = 0; q < nb; ++q) {
       const int bb = ordb[q];
-      h_wbr_s.push_back(bstart[bb]);
-      h_wbr_e.push_back(bb + 1 < nb ? bstart[bb + 1] - 1 : n - 1);
+      const int bs = bstart[bb], be = bb + 1 < nb ? bstart[bb + 1] - 1 : n - 1;
+      h_wbr_s.push_back(bs);
+      h_wbr_e.push_back(be);
+      h_wbr_p.push_back(bs == 0 ? -1 : gm.parent[bs]);
+      h_wbr_c.push_back(be + 1 < n && gm.parent[be + 1] == be ? be + 1 : -1);
+      h_wbr_o.push_back(och[be]);
     }
   }
 
@@ -1319,6 +1330,9 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_wcell = R(sizeof(WideCell) * std::max<int64_t>(n_wide, 1));
   const size_t o_wbr_s = R(sizeof(int32_t) * std::max<size_t>(h_wbr_s.size(), 1));
   const size_t o_wbr_e = R(sizeof(int32_t) * std::max<size_t>(h_wbr_e.size(), 1));
+  const size_t o_wbr_p = R(sizeof(int32_t) * std::max<size_t>(h_wbr_p.size(), 1));
+  const size_t o_wbr_c = R(sizeof(int32_t) * std::max<size_t>(h_wbr_c.size(), 1));
+  const size_t o_wbr_o = R(sizeof(int32_t) * std::max<size_t>(h_wbr_o.size(), 1));
   const size_t o_wlvl = R(sizeof(int32_t) * std::max<size_t>(h_wlvl.size(), 1));
   const size_t o_clock = R(sizeof(EpochClock));
   size_t o_cacv = 0, o_casrc = 0, o_cadg = 0, o_caa = 0, o_cavdt = 0, o_cavol = 0, o_hasca = 0;
@@ -1365,6 +1379,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   }
   putv(o_ishh, h_is_hh);
   putv(o_wcell, h_wcell); putv(o_wbr_s, h_wbr_s); putv(o_wbr_e, h_wbr_e); putv(o_wlvl, h_wlvl);
+  putv(o_wbr_p, h_wbr_p); putv(o_wbr_c, h_wbr_c); putv(o_wbr_o, h_wbr_o);
   putv(o_iinj, h_iinj); putv(o_kon, h_kon); putv(o_koff, h_koff); putv(o_th, h_thresh);
   putv(o_hasstc, h_has_stc);
   if (ca_stream >= 0) {
@@ -1400,6 +1415,9 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   A.wcell = (const WideCell*)P8(o_wcell);
   A.wbr_s = (const int32_t*)P8(o_wbr_s);
   A.wbr_e = (const int32_t*)P8(o_wbr_e);
+  A.wbr_p = (const int32_t*)P8(o_wbr_p);
+  A.wbr_c = (const int32_t*)P8(o_wbr_c);
+  A.wbr_o = (const int32_t*)P8(o_wbr_o);
   A.wlvl = (const int32_t*)P8(o_wlvl);
   if (n_narrow > 0 && n_wide > 0) {
     CUDA_TRY(cudaStreamCreateWithFlags(&M->side_stream, cudaStreamNonBlocking));

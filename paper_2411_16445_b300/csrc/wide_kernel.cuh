@@ -174,26 +174,34 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
       const int b0 = A.wlvl[wc.lvl0 + lv], b1 = A.wlvl[wc.lvl0 + lv + 1];
       for (int b = b0 + lane; b < b1; b += 32) {
         const int bs = A.wbr_s[wc.br0 + b], be = A.wbr_e[wc.br0 + b];
+        // the children of the branch's last row (eliminated at lower levels): the
+        // first (be + 1) and the highest other one, loaded with the first row; a
+        // row inside a branch has exactly one child, the next row
+        const int c1 = A.wbr_c[wc.br0 + b], co = A.wbr_o[wc.br0 + b];
+        double f1 = 0.0, x1 = 0.0, a1 = 0.0, fo = 0.0, xo = 0.0, ao = 0.0;
+        int cn = -1;
+        if (c1 >= 0) {
+          f1 = F[e0 + c1]; x1 = XP[e0 + c1]; a1 = AA[e0 + c1];
+        }
+        if (co >= 0) {
+          fo = F[e0 + co]; xo = XP[e0 + co]; ao = AA[e0 + co]; cn = OCN[e0 + co];
+        }
         double cf = 0.0, ca = 0.0, cx = 0.0;
-        bool carry = false;
         // one row of lookahead: the next row's values load during this row's
         // elimination
         double nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be], nem = EM[e0 + be],
                na = AA[e0 + be];
         TS ngs = GS[e0 + be], nes = EZ ? TS(0) : ES[e0 + be];
-        int noch = PAR ? OCH[e0 + be] : -1;
         for (int i = be; i >= bs; --i) {
           const int64_t ei = e0 + i;
           const double v = nv, cdt = ncdt, dcv = ndc, emv = nem, ai = na;
           const double gsv = widen_f32(ngs);
           const double esv = widen_f32(nes);  // (EZ: unused, see ez_add)
-          const int och = noch;
           if (i > bs) {
             const int64_t en = ei - 1;
             nv = Vg[en]; ncdt = CDT[en]; ndc = DC[en]; nem = EM[en]; na = AA[en];
             ngs = GS[en];
             if (!EZ) nes = ES[en];
-            if (PAR) noch = OCH[en];
           }
           double d, bb;
           if (i == 0) {
@@ -212,23 +220,26 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
             bb = fma(cdt, v, emv);
           }
           bb = EZ ? ez_add(bb, (const TS*)ES, (uint32_t)ei) : bb + esv;
-          if (PAR) {
-            // other children, highest index first (eliminated at lower levels)
-            for (int ch = och; ch >= 0; ch = OCN[e0 + ch]) {
-              const int64_t ec = e0 + ch;
-              const double ac = AA[ec];
-              d = fma(-F[ec], ac, d);
-              bb = fma(-ac, XP[ec], bb);
+          if (i == be) {
+            // the other children, highest index first, then the first child
+            if (co >= 0) {
+              d = fma(-fo, ao, d);
+              bb = fma(-ao, xo, bb);
+              for (int ch = cn; ch >= 0; ch = OCN[e0 + ch]) {  // a third child and more
+                const int64_t ec = e0 + ch;
+                const double ac = AA[ec];
+                d = fma(-F[ec], ac, d);
+                bb = fma(-ac, XP[ec], bb);
+              }
             }
-          }
-          if (carry) {
+            if (c1 >= 0) {
+              d = fma(-f1, a1, d);
+              bb = fma(-a1, x1, bb);
+            }
+          } else {
+            // row i + 1 of this branch, eliminated just before
             d = fma(-cf, ca, d);
             bb = fma(-ca, cx, bb);
-          } else if (i == be && PAR && i + 1 < n && PAR[ei + 1] == i) {
-            // a fork: the first child starts a branch of a lower level
-            const double ac = AA[ei + 1];
-            d = fma(-F[ei + 1], ac, d);
-            bb = fma(-ac, XP[ei + 1], bb);
           }
           if (i > 0) {
             const double rr = rcp_rn_pos(d);
@@ -236,8 +247,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
             const double xi = bb * rr;
             F[ei] = fi;
             XP[ei] = xi;
-            carry = true;  // row i - 1 of this branch has i as its first child
-            cf = fi; ca = ai; cx = xi;
+            cf = fi; ca = ai; cx = xi;  // row i - 1 of this branch has i as its first child
           } else {
             v0_new = bb * rcp_rn_pos(d);
           }
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           vp = v0_new;
           i = 1;
         } else {
-          vp = Vg[e0 + PAR[e0 + bs]];
+          vp = Vg[e0 + A.wbr_p[wc.br0 + b]];
         }
         // a chunk of the branch's f and x' is loaded at once (the chain has one
         // FP64 operation per row, far shorter than a load's latency)
