@@ -46,11 +46,12 @@ FALLBACK_HBM_GBS = 6400.0      # the profiling recipe's fallback when no measure
 SURVEY_BYTES_PER_CU = {"fp64": 60.0, "mixed": 45.0, "fp32": 45.0}
 # DRAM bytes per compartment-update of the epoch kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of a 65,536-cell launch of the
-# same generator, shape 0: 104.36 GB (mixed) and 104.29 GB (FP64) for 735.3 M
-# CU), scaled to a full launch by the CUs it processes, since traffic grows in
-# proportion to them; absent once the kernel has changed since the counters
-# were taken (and for the FP32-mechanism kernel, not captured).
-TRAFFIC_B_PER_CU = {"mixed": 141.9, "fp64": 141.8}
+# same generator, shape 0, the kernels for reversal potentials of +0: 98.87 GB
+# (mixed) and 98.82 GB (FP64) for 735.3 M CU), scaled to a full launch by the
+# CUs it processes, since traffic grows in proportion to them; absent once the
+# kernel has changed since the counters were taken (and for the FP32-mechanism
+# kernel, not captured).
+TRAFFIC_B_PER_CU = {"mixed": 134.5, "fp64": 134.4}
 
 
 def measured_peaks():
@@ -123,6 +124,9 @@ def net_stats(net):
         "n_first": int(np.dot(per_cell, first)),
         "n_other": int(np.dot(per_cell, other)),
         "tree": any(not m.is_chain() for m in net.morphs),
+        # every synaptic reversal potential exactly +0 (the kernels' es_zero case)
+        "es_zero": all(np.float64(net.mech_params[m][1]).tobytes() == bytes(8)
+                       for m in np.unique(net.conn_mech) if net.mech_kind[m] in (10, 11, 12, 13)),
     }
 
 
@@ -140,16 +144,21 @@ def per_cu_model(st, prec):
     eliminated into its parent (carried first child or other child); HH per
     soma; the synapse ops: 4 per synapse in FP64 (decay, two sums, g E), 2 in
     mixed (the run's float-float sum to FP64 and its product with E; the rest
-    runs on the FP32 pipes), 0 in FP32.  The row reciprocal runs on the integer
-    pipes (correctly rounded, about forty integer ops) and is not counted."""
+    runs on the FP32 pipes), 0 in FP32.  When every reversal potential is +0
+    the g E terms are signed zeros handled on the integer pipes: one assembly
+    addition per row and the g E product and sum per synapse (the product in
+    mixed) drop out.  The row reciprocal runs on the integer pipes (correctly
+    rounded, about forty integer ops) and is not counted."""
     gb = 4 if prec == "fp32" else 8
     cv_bytes = 16 + 32 + (2 if st["tree"] else 0)
     syn_b = 2 * gb + 4 + 8
     syn_bytes = (st["n_stdp"] + st["n_expsyn"]) * syn_b
     bytes_per_cu = cv_bytes + syn_bytes / st["n_cv"]
-    solve = 6 * st["n_cv"] + 2 * (st["n_first"] + st["n_other"])
+    ez = st.get("es_zero", False)
+    solve = (5 if ez else 6) * st["n_cv"] + 2 * (st["n_first"] + st["n_other"])
     hh = 153 + 6 * RCP64_DFMA_EQ + 20                  # 9 model exps, 6 divisions, currents
-    syn = {"fp64": 4, "mixed": 2, "fp32": 0}[prec] * (st["n_stdp"] + st["n_expsyn"])
+    per_syn = {"fp64": 2 if ez else 4, "mixed": 1 if ez else 2, "fp32": 0}[prec]
+    syn = per_syn * (st["n_stdp"] + st["n_expsyn"])
     fp64_per_cu = (solve + hh * st["n_cells"] + syn) / st["n_cv"]
     return bytes_per_cu, fp64_per_cu
 
