@@ -142,13 +142,14 @@ def per_cu_model(st, prec):
     and right-hand-side assembly (3: d + g_syn, C/dt V + E-term, + gE_syn), the
     f and x' products (2) and the back substitution (1); two FMAs per child
     eliminated into its parent (carried first child or other child); HH per
-    soma; the synapse ops: 4 per synapse in FP64 (decay, two sums, g E), 2 in
-    mixed (the run's float-float sum to FP64 and its product with E; the rest
-    runs on the FP32 pipes), 0 in FP32.  When every reversal potential is +0
-    the g E terms are signed zeros handled on the integer pipes: one assembly
-    addition per row and the g E product and sum per synapse (the product in
-    mixed) drop out.  The row reciprocal runs on the integer pipes (correctly
-    rounded, about forty integer ops) and is not counted."""
+    soma; 4 per synapse in FP64 (decay, two sums, g E), 0 in FP32.  When every
+    reversal potential is +0 the g E terms are signed zeros handled on the
+    integer pipes: one assembly addition per row and the g E product and sum
+    per synapse drop out.  In mixed the conductances, per-CV sums and the row
+    itself (assembly, elimination, back substitution) are float-float on the
+    FP32 pipes: only HH remains on the FP64 pipe.  The FP64 row reciprocal runs
+    on the integer pipes (correctly rounded, about forty integer ops) and is
+    not counted."""
     gb = 4 if prec == "fp32" else 8
     cv_bytes = 16 + 32 + (2 if st["tree"] else 0)
     syn_b = 2 * gb + 4 + 8
@@ -156,8 +157,10 @@ def per_cu_model(st, prec):
     bytes_per_cu = cv_bytes + syn_bytes / st["n_cv"]
     ez = st.get("es_zero", False)
     solve = (5 if ez else 6) * st["n_cv"] + 2 * (st["n_first"] + st["n_other"])
+    if prec == "mixed":
+        solve = 0
     hh = 153 + 6 * RCP64_DFMA_EQ + 20                  # 9 model exps, 6 divisions, currents
-    per_syn = {"fp64": 2 if ez else 4, "mixed": 1 if ez else 2, "fp32": 0}[prec]
+    per_syn = {"fp64": 2 if ez else 4, "mixed": 0, "fp32": 0}[prec]
     syn = per_syn * (st["n_stdp"] + st["n_expsyn"])
     fp64_per_cu = (solve + hh * st["n_cells"] + syn) / st["n_cv"]
     return bytes_per_cu, fp64_per_cu
@@ -749,8 +752,9 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"mixed": "f64 solve and sums + f32x2 conductances",
-                  "fp32": "f64 solve + f32 synapses", "fp64": "f64"}[head],
+        "dtype": {"mixed": "f32x2 (float-float) solve, sums and conductances + f64 HH and "
+                           "plasticity",
+                  "fp32": "f64 solve + f32 synapses and mechanisms", "fp64": "f64"}[head],
         "data": "synthetic",
         "config": {"workload": "large_stdp", "n_cells": st["n_cells"], "n_cv": st["n_cv"],
                    "n_synapses": st["n_syn"], "dt_ms": net.dt,

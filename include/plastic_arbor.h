@@ -102,17 +102,20 @@ extern "C" {
 /* arithmetic of the loop */
 #define PA_FP64 0   /* everything in FP64: the plain definition, operation for operation */
 #define PA_MIXED 1  /* synaptic conductances (exponential decay, event jumps, the per-CV
-                       sums of each run of same-CV synapses) on the FP32 pipes in
-                       float-float form (hi + lo, about 48 significand bits); event
-                       weights and STDP traces in FP32; the per-CV synaptic sums handed
-                       to the assembly, the voltage, cable coefficients, assembly, Hines
-                       solve, HH, calcium and the slow plasticity state (GB w, STC h/z/p,
-                       STDP w) in FP64.  Meets the oracle within 1e-5 V and 1e-3 ms. */
-#define PA_FP32 2   /* as PA_MIXED but conductances and the per-CV synaptic sums in plain
-                       FP32: each step re-rounds every conductance (2^-24), and the
-                       accumulated rounding can move spike times by several microseconds
-                       on networks (its measured error against the oracle is documented
-                       with the engine). */
+                       sums of each run of same-CV synapses) and the cable solve (voltage,
+                       cable coefficients, per-CV sums, assembly, elimination, back
+                       substitution) on the FP32 pipes in float-float form (hi + lo, about
+                       48 significand bits); STDP traces in FP32; event weights, HH,
+                       calcium and the slow plasticity state (GB w, STC h/z/p, STDP w) in
+                       FP64.  Meets the oracle within 1e-5 V and 1e-3 ms. */
+#define PA_FP32 2   /* conductances, event weights, STDP traces and the per-CV synaptic
+                       sums in plain FP32, and the mechanisms in FP32 (HH rates and gates,
+                       calcium, the GB / STC / STDP increments, accumulated into the FP64
+                       slow state); the cable solve in FP64.  Each step re-rounds every
+                       conductance (2^-24): spike counts match the oracle on the test
+                       networks, spike times and voltages do not meet the PA_MIXED bounds
+                       (its measured error against the oracle is documented with the
+                       engine). */
 
 /* connection source meaning "an independent Poisson train of rate rate_hz" */
 #define PA_SRC_POISSON (-1)

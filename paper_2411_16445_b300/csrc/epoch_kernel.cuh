@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "engine.h"
 #include "int_arith.cuh"
 #include "precision.cuh"
@@ -506,8 +508,8 @@ __device__ __noinline__ void hca_stream(const EpochArgs& A, int s, int g, int la
     if (cvf & 4) {
       A.ca_src[ce] = accq;
       if (zero) {
-        GS[ce] = (TS)0;
-        ES[ce] = (TS)0;
+        GS[ce] = PR::s_zero();
+        ES[ce] = PR::s_zero();
       }
     }
   }
@@ -523,9 +525,12 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
   const int lane = threadIdx.x & 31;
   if (g >= A.n_narrow) return;  // whole warps only
   uint64_t* bar = (uint64_t*)(wbuf + kStages * ST::kBytes);
-  // the fork stack region (trees): double2 entries (backward), double (forward)
-  double2* stack2 = (double2*)(wbuf + kStages * ST::kBytes + 64);
-  double* stack1 = (double*)stack2;
+  // the fork stack region (trees): (f, x') pairs (backward), V (forward)
+  struct __align__(16) FX {
+    typename PR::Row::R f, x;
+  };
+  FX* stack2 = (FX*)(wbuf + kStages * ST::kBytes + 64);
+  typename PR::Row::R* stack1 = (typename PR::Row::R*)stack2;
   if (lane == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
     mbar_init_fence();
@@ -541,15 +546,19 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
   const int rows = A.row_base[g + 1] - rb;
   const double dt = A.dt;
 
-  double* __restrict__ Vg = A.V;
-  const double* __restrict__ CDT = A.cdt;
-  const double* __restrict__ DC = A.dc;
-  const double* __restrict__ EM = A.em;
-  const double* __restrict__ AA = A.a;
+  // the cable rows in the policy's row form (FP64, or float-float pairs in
+  // PA_MIXED; 8 bytes per value either way)
+  using RW = typename PR::Row;
+  using R = typename RW::R;
+  R* __restrict__ Vg = (R*)A.V;
+  const R* __restrict__ CDT = (const R*)A.cdt;
+  const R* __restrict__ DC = (const R*)A.dc;
+  const R* __restrict__ EM = (const R*)A.em;
+  const R* __restrict__ AA = (const R*)A.a;
   TS* __restrict__ GS = (TS*)A.gs;
   TS* __restrict__ ES = (TS*)A.es;
-  double* __restrict__ F = A.f;
-  double* __restrict__ XP = A.xp;
+  R* __restrict__ F = (R*)A.f;
+  R* __restrict__ XP = (R*)A.xp;
 
   const bool hh = n > 0 && A.is_hh[L];
   SomaHH<PR::kMech32> soma;
@@ -692,6 +701,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
     // takes the same operations (the lanes of a warp are different cells, so a
     // per-row shortcut would run both paths).
     double v0_old = 0.0, v0_new = 0.0;
+    R x0 = RW::zero();  // the soma's new V in the row form
     const double iinj = (k >= kon && k < koff) ? iinj_val : 0.0;
     fence_async_global();  // this step's synaptic sums, written by plain stores
     __syncwarp();
@@ -731,7 +741,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
       fence_async_shared();
       __syncwarp();
       for (int c = 0; c < kStages - 1 && c < nc; ++c) issue(c);
-      double cf = 0.0, ca = 0.0, cx = 0.0;
+      R cf = RW::zero(), ca = RW::zero(), cx = RW::zero();
       bool carry = false;
       int depth = 0;  // fork-stack depth of this lane
       for (int c = 0; c < nc; ++c) {
@@ -758,30 +768,33 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           const int r = (i - lo) * 32 + lane;
           const uint32_t e = elem_of(rb, i, lane);
           if (!PA_IN(A, e, A.n_row_elems)) continue;
-          const double v = ((const double*)(st + ST::oV))[r];
-          const double cdt = ((const double*)(st + ST::oCDT))[r];
-          const double dcv = ((const double*)(st + ST::oDC))[r];
+          const R v = ((const R*)(st + ST::oV))[r];
+          const R cdt = ((const R*)(st + ST::oCDT))[r];
+          const R dcv = ((const R*)(st + ST::oDC))[r];
           int pi = i - 1;
           if (TREE && i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
-          const double gsv = widen_f32(((const TS*)(st + ST::oGS))[r]);
-          const double esv = EZ ? 0.0 : widen_f32(((const TS*)(st + ST::oES))[r]);
-          double d, b;
+          const R gsv = PR::sum_r(((const TS*)(st + ST::oGS))[r]);
+          R d, b;
           if (i == 0) {
-            v0_old = v;
+            v0_old = RW::to_d(v);
             if (hh) {
               double gmt, emt;
               soma.currents(A, L, gmt, emt);
-              d = (dcv + gmt) + gsv;
-              b = fma(cdt, v, emt) + iinj;
+              d = RW::add(RW::add(dcv, RW::from_d(gmt)), gsv);
+              b = RW::add(RW::fma(cdt, v, RW::from_d(emt)), RW::from_d(iinj));
             } else {
-              d = dcv + gsv;
-              b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]) + iinj;
+              d = RW::add(dcv, gsv);
+              b = RW::add(RW::fma(cdt, v, ((const R*)(st + ST::oEM))[r]), RW::from_d(iinj));
             }
           } else {
-            d = dcv + gsv;
-            b = fma(cdt, v, ((const double*)(st + ST::oEM))[r]);
+            d = RW::add(dcv, gsv);
+            b = RW::fma(cdt, v, ((const R*)(st + ST::oEM))[r]);
           }
-          b = EZ ? ez_add(b, (const TS*)ES, e) : b + esv;
+          if constexpr (!EZ) {
+            b = RW::add(b, PR::sum_r(((const TS*)(st + ST::oES))[r]));
+          } else if constexpr (std::is_same<R, double>::value) {
+            b = ez_add(b, (const TS*)ES, e);  // (float-float: the signed zero is not added)
+          }
           uint8_t tf = 0;
           if (TREE) {
             if (ST::kStacks) tf = ((const uint8_t*)(st + ST::oTF))[r];
@@ -790,50 +803,51 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
               // the one other child: its f and x' from the top of the fork stack
               // (eliminated earlier in this pass), its coupling staged here
               --depth;
-              double fc, xc;
+              R fc, xc;
               if (depth < ST::kStackB) {
-                const double2 t = stack2[depth * 32 + lane];
-                fc = t.x;
-                xc = t.y;
+                const FX t = stack2[depth * 32 + lane];
+                fc = t.f;
+                xc = t.x;
               } else {
                 const uint32_t ec = elem_of(rb, och, lane);
-                fc = PA_IN(A, ec, A.n_row_elems) ? F[ec] : 0.0;
-                xc = PA_IN(A, ec, A.n_row_elems) ? XP[ec] : 0.0;
+                fc = PA_IN(A, ec, A.n_row_elems) ? F[ec] : RW::zero();
+                xc = PA_IN(A, ec, A.n_row_elems) ? XP[ec] : RW::zero();
               }
-              const double ac = ((const double*)(st + ST::oAOCH))[r];
-              d = fma(-fc, ac, d);
-              b = fma(-ac, xc, b);
+              const R ac = ((const R*)(st + ST::oAOCH))[r];
+              d = RW::fnma(fc, ac, d);
+              b = RW::fnma(ac, xc, b);
             } else {
               // several other children, highest index first, from the scratch arrays
               for (int ch = och; ch >= 0;) {
                 const uint32_t ec = elem_of(rb, ch, lane);
                 if (!PA_IN(A, ec, A.n_row_elems)) break;
-                const double ac = AA[ec];
-                d = fma(-F[ec], ac, d);
-                b = fma(-ac, XP[ec], b);
+                const R ac = AA[ec];
+                d = RW::fnma(F[ec], ac, d);
+                b = RW::fnma(ac, XP[ec], b);
                 ch = A.och_next[ec];
               }
             }
           }
           if (carry) {
-            d = fma(-cf, ca, d);
-            b = fma(-ca, cx, b);
+            d = RW::fnma(cf, ca, d);
+            b = RW::fnma(ca, cx, b);
           }
           if (i > 0) {
-            const double ai = ((const double*)(st + ST::oA))[r];
-            const double rr = rcp_rn_pos(d);
-            const double fi = ai * rr;
-            const double xi = b * rr;
+            const R ai = ((const R*)(st + ST::oA))[r];
+            const R rr = RW::rcp(d);
+            const R fi = RW::mul(ai, rr);
+            const R xi = RW::mul(b, rr);
             F[e] = fi;
             XP[e] = xi;
             if (TREE && (tf & kForkPush)) {
-              if (depth < ST::kStackB) stack2[depth * 32 + lane] = make_double2(fi, xi);
+              if (depth < ST::kStackB) stack2[depth * 32 + lane] = FX{fi, xi};
               ++depth;
             }
             carry = !TREE || pi == i - 1;
             cf = fi; ca = ai; cx = xi;
           } else {
-            v0_new = b * rcp_rn_pos(d);
+            x0 = RW::mul(b, RW::rcp(d));
+            v0_new = RW::to_d(x0);
           }
         }
       }
@@ -869,8 +883,8 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
       fence_async_shared();
       __syncwarp();
       for (int c = 0; c < kStages - 1 && c < nc; ++c) issue(c);
-      if (n > 0) Vg[elem_of(rb, 0, lane)] = v0_new;
-      double vprev = v0_new;
+      if (n > 0) Vg[elem_of(rb, 0, lane)] = x0;
+      R vprev = x0;
       int depth = 0;  // fork-stack depth of this lane
       for (int c = 0; c < nc; ++c) {
         if (c + kStages - 1 < nc) {
@@ -893,13 +907,13 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
         const int lo = kRowsFwd * c, hi = lo + kRowsFwd < rows ? lo + kRowsFwd : rows;
         if (ST::kStacks && c == 0 && n > 0 &&
             (((const uint8_t*)(st + ST::fTF))[lane] & kForkPop)) {
-          stack1[lane] = v0_new;  // the root is a fork with one other child
+          stack1[lane] = x0;  // the root is a fork with one other child
           depth = 1;
         }
         for (int i = lo > 1 ? lo : 1; i < hi; ++i) {
           if (i >= n) break;
           const int r = (i - lo) * 32 + lane;
-          double vp = vprev;
+          R vp = vprev;
           uint8_t tf = 0;
           if (TREE) {
             if (ST::kStacks) tf = ((const uint8_t*)(st + ST::fTF))[r];
@@ -909,11 +923,11 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
               --depth;
               vp = depth < ST::kStackF ? stack1[depth * 32 + lane] : Vg[elem_of(rb, pi, lane)];
             } else if (pi != i - 1) {
-              vp = PA_IN(A, elem_of(rb, pi, lane), A.n_row_elems) ? Vg[elem_of(rb, pi, lane)] : 0.0;
+              vp = PA_IN(A, elem_of(rb, pi, lane), A.n_row_elems) ? Vg[elem_of(rb, pi, lane)]
+                                                                   : RW::zero();
             }
           }
-          const double vi = fma(-((const double*)(st + ST::fF))[r], vp,
-                                ((const double*)(st + ST::fXP))[r]);
+          const R vi = RW::fnma(((const R*)(st + ST::fF))[r], vp, ((const R*)(st + ST::fXP))[r]);
           if (PA_IN(A, elem_of(rb, i, lane), A.n_row_elems)) Vg[elem_of(rb, i, lane)] = vi;
           if (TREE && (tf & kForkPop)) {
             if (depth < ST::kStackF) stack1[depth * 32 + lane] = vi;
@@ -935,7 +949,8 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
       for (int32_t q = pq0; q < pq1; ++q) {
         const int64_t smp = probe0 + (k - k_begin);
         if (smp < A.probe_cap) {
-          A.probe_buf[smp * A.n_probe + A.probe_id[q]] = Vg[elem_of(rb, A.probe_row[q], lane)];
+          A.probe_buf[smp * A.n_probe + A.probe_id[q]] =
+              RW::to_d(Vg[elem_of(rb, A.probe_row[q], lane)]);
         } else {
           atomicOr(A.err_flags, 1);
         }

@@ -1370,6 +1370,22 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   putv(o_rowbase, M->row_base);
   putv(o_ncv, lane_ncv);
   putv(o_gid, lane_gid);
+  // PA_MIXED keeps the cable rows (V, coefficients; the scratch and per-CV sums
+  // are written by the kernels) as float-float pairs: each double becomes the
+  // nearest float and the float nearest the remainder, in its own 8 bytes
+  if (M->precision == PA_MIXED) {
+    auto to_ff = [&](HostVec<double>& v) {
+      parallel_ranges((int64_t)v.size(), [&](int64_t a, int64_t b) {
+        for (int64_t i = a; i < b; ++i) {
+          const double x = v[i];
+          const float hl[2] = {(float)x, (float)(x - (double)(float)x)};
+          std::memcpy(&v[i], hl, sizeof hl);
+        }
+      });
+    };
+    to_ff(h_V); to_ff(h_cdt); to_ff(h_dc); to_ff(h_em); to_ff(h_a);
+    if (M->tree) to_ff(h_aoch);
+  }
   putv(o_V, h_V);
   putv(o_cdt, h_cdt); putv(o_dc, h_dc); putv(o_em, h_em); putv(o_a, h_a);
   putv(o_hhg, h_hhg); putv(o_hhe, h_hhe);
@@ -1993,7 +2009,7 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
     *n_out = M->n_cv;
     if (cap == 0) return PA_OK;
     if (!out || cap < M->n_cv) return set_err(PA_ERR_ARG, "output too small");
-    int rc = fetch(M->ea.V, M->total_rows * kLanes, 8, tmp);
+    int rc = fetch(M->ea.V, M->total_rows * kLanes, M->precision == PA_MIXED ? kFF : 8, tmp);
     if (rc) return rc;
     for (int64_t c = 0; c < M->n_cells; ++c) {
       const int64_t L = M->lane_of_gid[c], g = L / kLanes;
@@ -2297,13 +2313,21 @@ int pa_write_state(pa_model* M, int32_t field, const double* in, int64_t n) {
   };
   if (field == PA_FIELD_V) {
     if (n != M->n_cv) return set_err(PA_ERR_ARG, "expected %lld values", (long long)M->n_cv);
+    const bool ff = M->precision == PA_MIXED;  // V as float-float pairs
     return rmw(M->ea.V, M->total_rows * kLanes, 8, [&](char* raw) {
-      double* v = (double*)raw;
       for (int64_t c = 0; c < M->n_cells; ++c) {
         const int64_t L = M->lane_of_gid[c], g = L / kLanes;
-        for (int i = 0; i < M->cell_ncv[c]; ++i)
-          v[g < M->n_narrow ? ((int64_t)M->row_base[g] + i) * kLanes + L % kLanes
-                            : ((int64_t)M->row_base[g] << 5) + i] = in[M->cell_cv_off[c] + i];
+        for (int i = 0; i < M->cell_ncv[c]; ++i) {
+          const int64_t e = g < M->n_narrow ? ((int64_t)M->row_base[g] + i) * kLanes + L % kLanes
+                                            : ((int64_t)M->row_base[g] << 5) + i;
+          const double x = in[M->cell_cv_off[c] + i];
+          if (ff) {
+            const float hl[2] = {(float)x, (float)(x - (double)(float)x)};
+            std::memcpy(raw + 8 * e, hl, sizeof hl);
+          } else {
+            std::memcpy(raw + 8 * e, &x, sizeof x);
+          }
+        }
       }
     });
   }

@@ -2,24 +2,25 @@
 //
 // A policy fixes how the synaptic conductances g (the exponential synapse's
 // state, decayed every step by the exact factor exp(-dt/tau)), the event
-// weights, the STDP traces and the per-CV synaptic sums (the synapses' share
-// of the backward-Euler row of Eq. cable) are stored and computed.  The cable
-// coefficients, the assembly, the Hines solve, the voltage, HH, calcium and
-// the slow plasticity state (GB w, STC h/z/p, STDP w) are FP64 in every
-// policy.
+// weights, the STDP traces, the per-CV synaptic sums (the synapses' share of
+// the backward-Euler row of Eq. cable) and the cable solve itself are stored
+// and computed.  HH, calcium and the slow plasticity state (GB w, STC h/z/p,
+// STDP w) are FP64 in PA_FP64 and PA_MIXED.
 //
 //   PrecF64  (PA_FP64)  everything FP64, operation for operation the plain
 //                       definition (bit-identical to the FP64 oracle);
 //   PrecMix  (PA_MIXED) g is an unevaluated sum of two floats (float-float,
 //                       about 48 significand bits) decayed and summed on the
 //                       FP32 pipes; STDP traces FP32; event weights FP64 (read
-//                       at events only); each run of same-CV synapses is summed
-//                       in float-float and turned into the FP64 per-CV sums by
-//                       one FP64 addition, g E by one FP64 product;
+//                       at events only); the per-CV sums, V, the cable
+//                       coefficients and the elimination scratch are
+//                       float-float pairs too, and the row's assembly,
+//                       elimination and back substitution run in float-float
+//                       on the FP32 pipes (RowFF);
 //   PrecF32  (PA_FP32)  g, weights, traces and the per-CV sums plain FP32, and
 //                       the mechanisms in FP32: HH rates and gates, calcium,
 //                       the GB / STC / STDP increments (the slow state they
-//                       accumulate into stays FP64).
+//                       accumulate into stays FP64); the cable solve FP64.
 //
 // Why the conductance path needs more than FP32 in PA_MIXED (measured with a
 // CPU emulation of each variant against the FP64 oracle, recurrent tagging-
@@ -30,7 +31,8 @@
 // static rounding of every event weight to FP32 moves them by 2e-3 ms, and
 // per-CV sums rounded to FP32 each step by up to 1e-3 ms.  Float-float keeps
 // the per-step rounding near 2^-47 while the work stays off the FP64 pipe,
-// which issues 1/64 of the FP32 rate on this GPU.
+// where every warp instruction holds its scheduler's FP64 unit for 64 cycles
+// on this GPU (an FP32 addition chains at 4.5).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -90,6 +92,56 @@ __device__ __forceinline__ float tm_mul(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ float tm_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double tm_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double tm_add(double a, double b) { return __dadd_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// Row arithmetic of the cable solve (assembly, elimination, back
+// substitution).  RowD: FP64, the plain operations (PA_FP64, where they are the
+// oracle's operation for operation, and PA_FP32).  RowFF (PA_MIXED): values as
+// float-float pairs (hi + lo, about 48 significand bits) on the FP32 pipes:
+// additions by TwoSum, products by the FMA-exact product, the reciprocal by
+// one Newton step from the FP32 approximation (relative error about 2^-45).
+// Voltages, cable coefficients, per-CV sums and the elimination scratch are
+// stored in the row's own form, so the solve needs no conversion.
+struct RowD {
+  using R = double;
+  __device__ static __forceinline__ R add(R a, R b) { return a + b; }
+  __device__ static __forceinline__ R mul(R a, R b) { return a * b; }
+  __device__ static __forceinline__ R fma(R a, R b, R c) { return ::fma(a, b, c); }
+  // c - a b
+  __device__ static __forceinline__ R fnma(R a, R b, R c) { return ::fma(-a, b, c); }
+  __device__ static __forceinline__ R rcp(R d) { return rcp_rn_pos(d); }
+  __device__ static __forceinline__ double to_d(R a) { return a; }
+  __device__ static __forceinline__ R from_d(double x) { return x; }
+  __device__ static __forceinline__ R zero() { return 0.0; }
+};
+struct RowFF {
+  using R = float2;
+  __device__ static __forceinline__ R add(R a, R b) { return ff_add(a, b); }
+  __device__ static __forceinline__ R mul(R a, R b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return ff_fast2sum(p, e);
+  }
+  __device__ static __forceinline__ R fma(R a, R b, R c) { return ff_add(mul(a, b), c); }
+  __device__ static __forceinline__ R fnma(R a, R b, R c) {
+    const R p = mul(a, b);
+    return ff_add(c, make_float2(-p.x, -p.y));
+  }
+  // 1/d for d > 0: y0 = rcp.approx(hi), then y0 + y0 (1 - d y0) with the
+  // residual formed by FMAs
+  __device__ static __forceinline__ R rcp(R d) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d.x));
+    float e = __fmaf_rn(-d.x, y, 1.0f);
+    e = __fmaf_rn(-d.y, y, e);
+    return ff_fast2sum(y, __fmul_rn(y, e));
+  }
+  __device__ static __forceinline__ double to_d(R a) { return ff_to_d(a); }
+  __device__ static __forceinline__ R from_d(double x) { return ff_from_d(x); }
+  __device__ static __forceinline__ R zero() { return make_float2(0.0f, 0.0f); }
+};
 
 // ---------------------------------------------------------------------------
 // Reversal potentials of exactly +0 (EZ).  For a finite g, g (+0) is the zero
@@ -184,15 +236,15 @@ struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
   }
 };
 
-struct AccFF {  // mixed: the run's conductance in float-float, FP64 at its end
+struct AccFF {  // mixed: the run's conductance in float-float, stored as a normalised pair
   using C = float2;
   template <bool EZ>
-  __device__ static __forceinline__ C contrib(float2 gv, double) { return gv; }
+  __device__ static __forceinline__ C contrib(float2 gv, float2) { return gv; }
   __device__ static __forceinline__ C shfl_c(C c, int src) {
     return make_float2(__shfl_sync(0xffffffffu, c.x, src), __shfl_sync(0xffffffffu, c.y, src));
   }
   template <bool EZ>
-  __device__ __forceinline__ void start_c(C c, bool first_on_cv, const double*, const double*,
+  __device__ __forceinline__ void start_c(C c, bool first_on_cv, const float2*, const float2*,
                                           uint32_t) {
     g = c;
     first = first_on_cv;
@@ -202,23 +254,24 @@ struct AccFF {  // mixed: the run's conductance in float-float, FP64 at its end
   float2 g;
   bool first;
   template <bool EZ>
-  __device__ __forceinline__ void start(float2 gv, double, bool first_on_cv, const double*,
-                                        const double*, uint32_t) {
+  __device__ __forceinline__ void start(float2 gv, float2, bool first_on_cv, const float2*,
+                                        const float2*, uint32_t) {
     g = gv;
     first = first_on_cv;
   }
   template <bool EZ>
-  __device__ __forceinline__ void add(float2 gv, double) { g = ff_add_acc(g, gv); }
+  __device__ __forceinline__ void add(float2 gv, float2) { g = ff_add_acc(g, gv); }
   template <bool EZ>
-  __device__ __forceinline__ void store(double* gs, double* es, uint32_t ce, double E) const {
-    const double s = ff_to_d(g);
-    const double se = EZ ? zero_of(s) : __dmul_rn(s, E);
+  __device__ __forceinline__ void store(float2* gs, float2* es, uint32_t ce, float2 E) const {
+    const float2 s = ff_fast2sum(g.x, g.y);
+    // (EZ: the g E sums are zeros the row never reads; written as zeros)
+    const float2 se = EZ ? make_float2(zero_of(s.x), 0.0f) : ff_mul(s, E.x, E.y);
     if (first) {
       gs[ce] = s;
       es[ce] = se;
     } else {
-      gs[ce] = __dadd_rn(gs[ce], s);
-      es[ce] = EZ ? zsum(es[ce], se) : __dadd_rn(es[ce], se);
+      gs[ce] = ff_add(gs[ce], s);
+      es[ce] = EZ ? se : ff_add(es[ce], se);
     }
   }
   __device__ __forceinline__ AccFF shfl(int src) const {
@@ -255,6 +308,7 @@ struct PrecF64 {
   using Ec = double;
   using Dc = double;
   using Acc = AccPlain<double>;
+  using Row = RowD;
   static constexpr int kId = 0;
   static constexpr bool kMech32 = false;  // HH, calcium, plasticity increments in FP64
   __device__ static __forceinline__ Ec e_const(double e) { return e; }
@@ -264,19 +318,22 @@ struct PrecF64 {
   __device__ static __forceinline__ G decay(G g, Dc d) { return g * d; }
   __device__ static __forceinline__ G zero() { return 0.0; }
   __device__ static __forceinline__ G shfl(G g, int src) { return __shfl_sync(0xffffffffu, g, src); }
+  __device__ static __forceinline__ Row::R sum_r(S s) { return s; }
+  __device__ static __forceinline__ S s_zero() { return 0.0; }
 };
 
 struct PrecMix {
   using G = float2;
   using W = double;
   using T = float;
-  using S = double;
-  using Ec = double;
+  using S = float2;   // per-CV sums as float-float pairs
+  using Ec = float2;  // E as hi + lo
   using Dc = float2;  // exp(-dt/tau) as hi + lo
   using Acc = AccFF;
+  using Row = RowFF;
   static constexpr int kId = 1;
   static constexpr bool kMech32 = false;
-  __device__ static __forceinline__ Ec e_const(double e) { return e; }
+  __device__ static __forceinline__ Ec e_const(double e) { return ff_from_d(e); }
   __device__ static __forceinline__ Dc d_const(double d) { return ff_from_d(d); }
   __device__ static __forceinline__ G add_w(G g, W w) { return ff_add(g, ff_from_d(w)); }
   __device__ static __forceinline__ G add_d(G g, double x) { return ff_add(g, ff_from_d(x)); }
@@ -285,6 +342,8 @@ struct PrecMix {
   __device__ static __forceinline__ G shfl(G g, int src) {
     return make_float2(__shfl_sync(0xffffffffu, g.x, src), __shfl_sync(0xffffffffu, g.y, src));
   }
+  __device__ static __forceinline__ Row::R sum_r(S s) { return s; }
+  __device__ static __forceinline__ S s_zero() { return make_float2(0.0f, 0.0f); }
 };
 
 struct PrecF32 {
@@ -295,6 +354,7 @@ struct PrecF32 {
   using Ec = float;
   using Dc = float;
   using Acc = AccPlain<float>;
+  using Row = RowD;
   static constexpr int kId = 2;
   // HH rates and gates, calcium and the GB / STC / STDP increments in FP32
   // (exponential integration with CUDA's expf); the slow state w, h, z, p
@@ -307,6 +367,8 @@ struct PrecF32 {
   __device__ static __forceinline__ G decay(G g, Dc d) { return __fmul_rn(g, d); }
   __device__ static __forceinline__ G zero() { return 0.0f; }
   __device__ static __forceinline__ G shfl(G g, int src) { return __shfl_sync(0xffffffffu, g, src); }
+  __device__ static __forceinline__ Row::R sum_r(S s) { return widen_f32(s); }
+  __device__ static __forceinline__ S s_zero() { return 0.0f; }
 };
 
 }  // namespace pa

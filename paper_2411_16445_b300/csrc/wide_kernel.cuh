@@ -49,15 +49,21 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   const WideCell wc = A.wcell[w];
   const double dt = A.dt;
 
-  double* __restrict__ Vg = A.V;
-  const double* __restrict__ CDT = A.cdt;
-  const double* __restrict__ DC = A.dc;
-  const double* __restrict__ EM = A.em;
-  const double* __restrict__ AA = A.a;
+  // the cable rows in the policy's row form (FP64, or float-float pairs in
+  // PA_MIXED); the diffusing field uses the scratch as FP64
+  using RW = typename PR::Row;
+  using R = typename RW::R;
+  R* __restrict__ Vg = (R*)A.V;
+  const R* __restrict__ CDT = (const R*)A.cdt;
+  const R* __restrict__ DC = (const R*)A.dc;
+  const R* __restrict__ EM = (const R*)A.em;
+  const R* __restrict__ AA = (const R*)A.a;
   TS* __restrict__ GS = (TS*)A.gs;
   TS* __restrict__ ES = (TS*)A.es;
-  double* __restrict__ F = A.f;
-  double* __restrict__ XP = A.xp;
+  R* __restrict__ F = (R*)A.f;
+  R* __restrict__ XP = (R*)A.xp;
+  double* __restrict__ Fd = A.f;
+  double* __restrict__ XPd = A.xp;
   const int16_t* __restrict__ PAR = A.par;
   const int16_t* __restrict__ OCH = A.och_head;
   const int16_t* __restrict__ OCN = A.och_next;
@@ -169,6 +175,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
 
     // ---- b. backward pass by branch levels ---------------------------------------
     double v0_old = 0.0, v0_new = 0.0;
+    R x0r = RW::zero();  // the soma's new V in the row form
     const double iinj = (k >= kon && k < koff) ? iinj_val : 0.0;
     for (int lv = 0; lv < wc.n_lvl; ++lv) {
       const int b0 = A.wlvl[wc.lvl0 + lv], b1 = A.wlvl[wc.lvl0 + lv + 1];
@@ -178,7 +185,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         // first (be + 1) and the highest other one, loaded with the first row; a
         // row inside a branch has exactly one child, the next row
         const int c1 = A.wbr_c[wc.br0 + b], co = A.wbr_o[wc.br0 + b];
-        double f1 = 0.0, x1 = 0.0, a1 = 0.0, fo = 0.0, xo = 0.0, ao = 0.0;
+        R f1 = RW::zero(), x1 = RW::zero(), a1 = RW::zero(), fo = RW::zero(), xo = RW::zero(),
+          ao = RW::zero();
         int cn = -1;
         if (c1 >= 0) {
           f1 = F[e0 + c1]; x1 = XP[e0 + c1]; a1 = AA[e0 + c1];
@@ -186,70 +194,75 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         if (co >= 0) {
           fo = F[e0 + co]; xo = XP[e0 + co]; ao = AA[e0 + co]; cn = OCN[e0 + co];
         }
-        double cf = 0.0, ca = 0.0, cx = 0.0;
+        R cf = RW::zero(), ca = RW::zero(), cx = RW::zero();
         // one row of lookahead: the next row's values load during this row's
         // elimination
-        double nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be], nem = EM[e0 + be],
-               na = AA[e0 + be];
-        TS ngs = GS[e0 + be], nes = EZ ? TS(0) : ES[e0 + be];
+        R nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be], nem = EM[e0 + be],
+          na = AA[e0 + be];
+        TS ngs = GS[e0 + be], nes = EZ ? PR::s_zero() : ES[e0 + be];
         for (int i = be; i >= bs; --i) {
           const int64_t ei = e0 + i;
-          const double v = nv, cdt = ncdt, dcv = ndc, emv = nem, ai = na;
-          const double gsv = widen_f32(ngs);
-          const double esv = widen_f32(nes);  // (EZ: unused, see ez_add)
+          const R v = nv, cdt = ncdt, dcv = ndc, emv = nem, ai = na;
+          const R gsv = PR::sum_r(ngs);
+          const R esv = PR::sum_r(nes);  // (EZ: unused)
           if (i > bs) {
             const int64_t en = ei - 1;
             nv = Vg[en]; ncdt = CDT[en]; ndc = DC[en]; nem = EM[en]; na = AA[en];
             ngs = GS[en];
             if (!EZ) nes = ES[en];
           }
-          double d, bb;
+          R d, bb;
           if (i == 0) {
-            v0_old = v;
+            v0_old = RW::to_d(v);
             if (hh) {
               double gmt, emt;
               soma.currents(A, L, gmt, emt);
-              d = (dcv + gmt) + gsv;
-              bb = fma(cdt, v, emt) + iinj;
+              d = RW::add(RW::add(dcv, RW::from_d(gmt)), gsv);
+              bb = RW::add(RW::fma(cdt, v, RW::from_d(emt)), RW::from_d(iinj));
             } else {
-              d = dcv + gsv;
-              bb = fma(cdt, v, emv) + iinj;
+              d = RW::add(dcv, gsv);
+              bb = RW::add(RW::fma(cdt, v, emv), RW::from_d(iinj));
             }
           } else {
-            d = dcv + gsv;
-            bb = fma(cdt, v, emv);
+            d = RW::add(dcv, gsv);
+            bb = RW::fma(cdt, v, emv);
           }
-          bb = EZ ? ez_add(bb, (const TS*)ES, (uint32_t)ei) : bb + esv;
+          if constexpr (!EZ) {
+            bb = RW::add(bb, esv);
+          } else if constexpr (std::is_same<R, double>::value) {
+            bb = ez_add(bb, (const TS*)ES, (uint32_t)ei);  // (float-float: not added)
+          }
           if (i == be) {
             // the other children, highest index first, then the first child
             if (co >= 0) {
-              d = fma(-fo, ao, d);
-              bb = fma(-ao, xo, bb);
+              d = RW::fnma(fo, ao, d);
+              bb = RW::fnma(ao, xo, bb);
               for (int ch = cn; ch >= 0; ch = OCN[e0 + ch]) {  // a third child and more
                 const int64_t ec = e0 + ch;
-                const double ac = AA[ec];
-                d = fma(-F[ec], ac, d);
-                bb = fma(-ac, XP[ec], bb);
+                const R ac = AA[ec];
+                d = RW::fnma(F[ec], ac, d);
+                bb = RW::fnma(ac, XP[ec], bb);
               }
             }
             if (c1 >= 0) {
-              d = fma(-f1, a1, d);
-              bb = fma(-a1, x1, bb);
+              d = RW::fnma(f1, a1, d);
+              bb = RW::fnma(a1, x1, bb);
             }
           } else {
             // row i + 1 of this branch, eliminated just before
-            d = fma(-cf, ca, d);
-            bb = fma(-ca, cx, bb);
+            d = RW::fnma(cf, ca, d);
+            bb = RW::fnma(ca, cx, bb);
           }
           if (i > 0) {
-            const double rr = rcp_rn_pos(d);
-            const double fi = ai * rr;
-            const double xi = bb * rr;
+            const R rr = RW::rcp(d);
+            const R fi = RW::mul(ai, rr);
+            const R xi = RW::mul(bb, rr);
             F[ei] = fi;
             XP[ei] = xi;
             cf = fi; ca = ai; cx = xi;  // row i - 1 of this branch has i as its first child
           } else {
-            v0_new = bb * rcp_rn_pos(d);
+            x0r = RW::mul(bb, RW::rcp(d));
+            v0_new = RW::to_d(x0r);
           }
         }
       }
@@ -260,11 +273,11 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
       const int b0 = A.wlvl[wc.lvl0 + lv], b1 = A.wlvl[wc.lvl0 + lv + 1];
       for (int b = b0 + lane; b < b1; b += 32) {
         const int bs = A.wbr_s[wc.br0 + b], be = A.wbr_e[wc.br0 + b];
-        double vp;
+        R vp;
         int i = bs;
         if (bs == 0) {
-          Vg[e0] = v0_new;
-          vp = v0_new;
+          Vg[e0] = x0r;
+          vp = x0r;
           i = 1;
         } else {
           vp = Vg[e0 + A.wbr_p[wc.br0 + b]];
@@ -272,7 +285,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         // a chunk of the branch's f and x' is loaded at once (the chain has one
         // FP64 operation per row, far shorter than a load's latency)
         for (; i <= be; i += kWideFwdChunk) {
-          double fr[kWideFwdChunk], xr[kWideFwdChunk];
+          R fr[kWideFwdChunk], xr[kWideFwdChunk];
 #pragma unroll
           for (int q = 0; q < kWideFwdChunk; ++q) {
             if (i + q <= be) {
@@ -283,7 +296,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
 #pragma unroll
           for (int q = 0; q < kWideFwdChunk; ++q) {
             if (i + q <= be) {
-              const double vi = fma(-fr[q], vp, xr[q]);
+              const R vi = RW::fnma(fr[q], vp, xr[q]);
               Vg[e0 + i + q] = vi;
               vp = vi;
             }
@@ -313,8 +326,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
               for (int ch = OCH[ei]; ch >= 0; ch = OCN[e0 + ch]) {
                 const int64_t ec = e0 + ch;
                 const double ac = A.prp_a[ec];
-                d = __fma_rn(-F[ec], ac, d);
-                bb = __fma_rn(-ac, XP[ec], bb);
+                d = __fma_rn(-Fd[ec], ac, d);
+                bb = __fma_rn(-ac, XPd[ec], bb);
               }
             }
             if (carry) {
@@ -322,16 +335,16 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
               bb = __fma_rn(-ca, cx, bb);
             } else if (i == be && PAR && i + 1 < n && PAR[ei + 1] == i) {
               const double ac = A.prp_a[ei + 1];
-              d = __fma_rn(-F[ei + 1], ac, d);
-              bb = __fma_rn(-ac, XP[ei + 1], bb);
+              d = __fma_rn(-Fd[ei + 1], ac, d);
+              bb = __fma_rn(-ac, XPd[ei + 1], bb);
             }
             if (i > 0) {
               const double ai = A.prp_a[ei];
               const double rr = rcp_rn_pos(d);
               const double fi = __dmul_rn(ai, rr);
               const double xi = __dmul_rn(bb, rr);
-              F[ei] = fi;
-              XP[ei] = xi;
+              Fd[ei] = fi;
+              XPd[ei] = xi;
               carry = true;
               cf = fi; ca = ai; cx = xi;
             } else {
@@ -356,7 +369,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           }
           for (; i <= be; ++i) {
             const int64_t ei = e0 + i;
-            const double xi = __fma_rn(-F[ei], pp, XP[ei]);
+            const double xi = __fma_rn(-Fd[ei], pp, XPd[ei]);
             A.prp_cv[ei] = xi;
             pp = xi;
           }
@@ -368,7 +381,7 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
     for (int32_t q = pq0 + lane; q < pq1; q += 32) {
       const int64_t smp = probe0 + (k - k_begin);
       if (smp < A.probe_cap) {
-        A.probe_buf[smp * A.n_probe + A.probe_id[q]] = Vg[e0 + A.probe_row[q]];
+        A.probe_buf[smp * A.n_probe + A.probe_id[q]] = RW::to_d(Vg[e0 + A.probe_row[q]]);
       } else {
         atomicOr(A.err_flags, 1);
       }
