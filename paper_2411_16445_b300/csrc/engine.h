@@ -19,6 +19,8 @@ namespace pa {
 // Fork flags of a tree row (EpochArgs::tflag).
 constexpr uint8_t kForkPop = 1;   // exactly one non-first child: its values are popped here
 constexpr uint8_t kForkPush = 2;  // the one non-first child of its parent: pushed here
+constexpr uint8_t kParPrev = 4;   // the parent is the previous row (row i - 1)
+constexpr uint8_t kOtherList = 8; // non-first children taken through the linked list
 
 constexpr int kLanes = 32;
 constexpr int kMaxStreams = 8;
@@ -137,11 +139,11 @@ struct EpochArgs {
   const int16_t* par;        // tree: parent row (row 0: -1)
   const int16_t* och_head;   // tree: highest-index non-first child (-1: none)
   const int16_t* och_next;   // tree: next lower non-first sibling (-1: none)
-  // tree: per row, kForkPop if the row has exactly one non-first child, kForkPush
-  // if the row is the one non-first child of such a row; and the axial coupling
-  // of that one non-first child (rows with kForkPop)
+  // tree: per row, kForkPop if the row has exactly one non-first child (and its
+  // cell's forks nest), kForkPush if the row is the one non-first child of such
+  // a row, kParPrev if its parent is row i - 1, kOtherList if its non-first
+  // children go through the linked list
   const uint8_t* tflag;
-  const double* aoch;
   // soma / cell state (lane index)
   const uint8_t* is_hh;
   const double* hh_g;        // [3][n_lanes] gna, gk, gl [uS]

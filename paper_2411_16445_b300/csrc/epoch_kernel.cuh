@@ -286,33 +286,34 @@ __device__ __forceinline__ void fence_async_shared() {
 // Shared-memory layout of one warp's stages for a given precision / tree flag.
 template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth>
 struct Stage {
-  // bytes per row (32 lanes) of each staged array
-  static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(typename PR::S), kI = TREE ? 32 * 2 : 0,
-                       kA = (TREE && kStackDepth > 0) ? 32 * 8 : 0,
-                       kT = (TREE && kStackDepth > 0) ? 32 : 0;
+  // bytes per row (32 lanes) of each staged array.  With fork stacks a tree
+  // stages one flag byte per row (fork push / pop, parent = previous row,
+  // children through the list); without them, the parent and first-other-child
+  // rows.
   static constexpr bool kStacks = TREE && kStackDepth > 0;  // fork stacks in use
+  static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(typename PR::S),
+                       kI = (TREE && !kStacks) ? 32 * 2 : 0, kT = kStacks ? 32 : 0;
   // backward pass: V, C/dt, diagonal, leak E term, axial coupling, synaptic sums,
-  // tree rows (the one other child's coupling, parent, first other child, fork flags)
+  // tree rows
   static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oDC = oCDT + kRowsBack * kD,
                        oEM = oDC + kRowsBack * kD, oA = oEM + kRowsBack * kD,
-                       oAOCH = oA + kRowsBack * kD, oGS = oAOCH + kRowsBack * kA,
-                       oES = oGS + kRowsBack * kM, oPAR = oES + kRowsBack * kM,
-                       oOCH = oPAR + kRowsBack * kI, oTF = oOCH + kRowsBack * kI,
-                       kBackBytes = oTF + kRowsBack * kT;
-  static constexpr int kBackRow = 5 * kD + kA + 2 * kM + 2 * kI + kT;
-  // forward pass: f, x', tree parent rows and fork flags
+                       oGS = oA + kRowsBack * kD, oES = oGS + kRowsBack * kM,
+                       oPAR = oES + kRowsBack * kM, oOCH = oPAR + kRowsBack * kI,
+                       oTF = oOCH + kRowsBack * kI, kBackBytes = oTF + kRowsBack * kT;
+  static constexpr int kBackRow = 5 * kD + 2 * kM + 2 * kI + kT;
+  // forward pass: f, x', tree rows
   static constexpr int fF = 0, fXP = fF + kRowsFwd * kD, fPAR = fXP + kRowsFwd * kD,
                        fTF = fPAR + kRowsFwd * kI, kFwdBytes = fTF + kRowsFwd * kT;
   static constexpr int kFwdRow = 2 * kD + kI + kT;
   static constexpr int kBytes = (kBackBytes > kFwdBytes ? kBackBytes : kFwdBytes);
-  // fork stacks (trees): the backward pass keeps (f, x') of up to kStackB pending
-  // one-other-children per lane, the forward pass V of up to kStackF pending forks;
-  // deeper entries are read back from global memory
+  // fork stacks (trees): the backward pass keeps (f, x', coupling) of up to
+  // kStackB pending one-other-children per lane, the forward pass V of up to
+  // kStackF pending forks; deeper entries are read back from global memory
   // (the depth is part of the kernel shape: deep stacks where many forks nest,
   // shallow ones where longer backward chunks take the shared memory)
   static constexpr int kStackB = kStackDepth, kStackF = 2 * kStackDepth;
-  static constexpr int kStackBytes = kStacks ? 32 * kStackB * 16 : 0;
-  static_assert(32 * kStackF * 8 <= 32 * kStackB * 16, "forward stack fits the region");
+  static constexpr int kStackBytes = kStacks ? 32 * kStackB * 24 : 0;
+  static_assert(32 * kStackF * 8 <= 32 * kStackB * 24, "forward stack fits the region");
   static constexpr int kWarpBytes = kStages * kBytes + 64 + kStackBytes;  // + mbarriers
 };
 
@@ -525,9 +526,10 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
   const int lane = threadIdx.x & 31;
   if (g >= A.n_narrow) return;  // whole warps only
   uint64_t* bar = (uint64_t*)(wbuf + kStages * ST::kBytes);
-  // the fork stack region (trees): (f, x') pairs (backward), V (forward)
-  struct __align__(16) FX {
-    typename PR::Row::R f, x;
+  // the fork stack region (trees): (f, x', coupling) of the child (backward),
+  // V (forward)
+  struct FX {
+    typename PR::Row::R f, x, a;
   };
   FX* stack2 = (FX*)(wbuf + kStages * ST::kBytes + 64);
   typename PR::Row::R* stack1 = (typename PR::Row::R*)stack2;
@@ -728,14 +730,11 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           bulk_load(st + ST::oA, AA + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kM, &bar[s]);
           if (!EZ) bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kM, &bar[s]);
-          if (TREE) {
+          if (TREE && !ST::kStacks) {
             bulk_load(st + ST::oPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
             bulk_load(st + ST::oOCH, A.och_head + r0 * 32, cnt * ST::kI, &bar[s]);
           }
-          if (ST::kStacks) {
-            bulk_load(st + ST::oAOCH, A.aoch + r0 * 32, cnt * ST::kA, &bar[s]);
-            bulk_load(st + ST::oTF, A.tflag + r0 * 32, cnt * ST::kT, &bar[s]);
-          }
+          if (ST::kStacks) bulk_load(st + ST::oTF, A.tflag + r0 * 32, cnt * ST::kT, &bar[s]);
         }
       };
       fence_async_shared();
@@ -772,7 +771,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           const R cdt = ((const R*)(st + ST::oCDT))[r];
           const R dcv = ((const R*)(st + ST::oDC))[r];
           int pi = i - 1;
-          if (TREE && i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
+          if (TREE && !ST::kStacks && i > 0) pi = ((const int16_t*)(st + ST::oPAR))[r];
           const R gsv = PR::sum_r(((const TS*)(st + ST::oGS))[r]);
           R d, b;
           if (i == 0) {
@@ -798,26 +797,28 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           uint8_t tf = 0;
           if (TREE) {
             if (ST::kStacks) tf = ((const uint8_t*)(st + ST::oTF))[r];
-            const int och = ((const int16_t*)(st + ST::oOCH))[r];
             if (tf & kForkPop) {
-              // the one other child: its f and x' from the top of the fork stack
-              // (eliminated earlier in this pass), its coupling staged here
+              // the one other child: its f, x' and coupling from the top of the
+              // fork stack (eliminated earlier in this pass)
               --depth;
-              R fc, xc;
+              R fc, xc, ac;
               if (depth < ST::kStackB) {
                 const FX t = stack2[depth * 32 + lane];
                 fc = t.f;
                 xc = t.x;
+                ac = t.a;
               } else {
-                const uint32_t ec = elem_of(rb, och, lane);
-                fc = PA_IN(A, ec, A.n_row_elems) ? F[ec] : RW::zero();
-                xc = PA_IN(A, ec, A.n_row_elems) ? XP[ec] : RW::zero();
+                const uint32_t ec = elem_of(rb, A.och_head[e], lane);
+                const bool ok = PA_IN(A, ec, A.n_row_elems);
+                fc = ok ? F[ec] : RW::zero();
+                xc = ok ? XP[ec] : RW::zero();
+                ac = ok ? AA[ec] : RW::zero();
               }
-              const R ac = ((const R*)(st + ST::oAOCH))[r];
               d = RW::fnma(fc, ac, d);
               b = RW::fnma(ac, xc, b);
-            } else {
+            } else if (!ST::kStacks || (tf & kOtherList)) {
               // several other children, highest index first, from the scratch arrays
+              const int och = ST::kStacks ? A.och_head[e] : ((const int16_t*)(st + ST::oOCH))[r];
               for (int ch = och; ch >= 0;) {
                 const uint32_t ec = elem_of(rb, ch, lane);
                 if (!PA_IN(A, ec, A.n_row_elems)) break;
@@ -840,10 +841,10 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
             F[e] = fi;
             XP[e] = xi;
             if (TREE && (tf & kForkPush)) {
-              if (depth < ST::kStackB) stack2[depth * 32 + lane] = FX{fi, xi};
+              if (depth < ST::kStackB) stack2[depth * 32 + lane] = FX{fi, xi, ai};
               ++depth;
             }
-            carry = !TREE || pi == i - 1;
+            carry = !TREE || (ST::kStacks ? (tf & kParPrev) != 0 : pi == i - 1);
             cf = fi; ca = ai; cx = xi;
           } else {
             x0 = RW::mul(b, RW::rcp(d));
@@ -876,7 +877,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           mbar_expect_tx(&bar[s], cnt * ST::kFwdRow);
           bulk_load(st + ST::fF, F + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::fXP, XP + r0 * 32, cnt * ST::kD, &bar[s]);
-          if (TREE) bulk_load(st + ST::fPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
+          if (TREE && !ST::kStacks) bulk_load(st + ST::fPAR, A.par + r0 * 32, cnt * ST::kI, &bar[s]);
           if (ST::kStacks) bulk_load(st + ST::fTF, A.tflag + r0 * 32, cnt * ST::kT, &bar[s]);
         }
       };
@@ -916,15 +917,26 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
           R vp = vprev;
           uint8_t tf = 0;
           if (TREE) {
-            if (ST::kStacks) tf = ((const uint8_t*)(st + ST::fTF))[r];
-            const int pi = ((const int16_t*)(st + ST::fPAR))[r];
-            if (tf & kForkPush) {
-              // the one other child of its parent: the parent's V from the stack
-              --depth;
-              vp = depth < ST::kStackF ? stack1[depth * 32 + lane] : Vg[elem_of(rb, pi, lane)];
-            } else if (pi != i - 1) {
-              vp = PA_IN(A, elem_of(rb, pi, lane), A.n_row_elems) ? Vg[elem_of(rb, pi, lane)]
-                                                                   : RW::zero();
+            const uint32_t ei = elem_of(rb, i, lane);
+            if (ST::kStacks) {
+              // the parent row is read from memory only where it is not the
+              // previous row and not on the stack
+              tf = ((const uint8_t*)(st + ST::fTF))[r];
+              if (tf & kForkPush) {
+                // the one other child of its parent: the parent's V from the stack
+                --depth;
+                vp = depth < ST::kStackF ? stack1[depth * 32 + lane]
+                                         : Vg[elem_of(rb, A.par[ei], lane)];
+              } else if (!(tf & kParPrev)) {
+                const uint32_t ep = elem_of(rb, A.par[ei], lane);
+                vp = PA_IN(A, ep, A.n_row_elems) ? Vg[ep] : RW::zero();
+              }
+            } else {
+              const int pi = ((const int16_t*)(st + ST::fPAR))[r];
+              if (pi != i - 1) {
+                vp = PA_IN(A, elem_of(rb, pi, lane), A.n_row_elems) ? Vg[elem_of(rb, pi, lane)]
+                                                                     : RW::zero();
+              }
             }
           }
           const R vi = RW::fnma(((const R*)(st + ST::fF))[r], vp, ((const R*)(st + ST::fXP))[r]);
@@ -1055,14 +1067,15 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // minimum resident blocks per SM (which sets the register budget).  Shape 0 is
 // the default; the autotuner times all of them on the model and keeps the
 // fastest.
-// Trees also choose the fork stacks' depth: FP64 shape 0 takes 3 backward rows
-// per chunk and 8 entries (many nested forks), FP64 shapes 3 and 4 take 4 rows
-// and 2 entries, the mixed shapes 4 rows and 6 entries; shape 5 has no stacks
-// (trees with long branches and few forks); 12 warps per SM fit in each case.
+// Trees also choose the fork stacks' depth (24-byte entries): with 8-byte sums
+// (FP64, mixed) shape 0 takes 3 backward rows per chunk and 7 entries (many
+// nested forks), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
+// shape 0 takes 4 rows and 6 entries; shape 5 has no stacks (trees with long
+// branches and few forks); 12 warps per SM fit in each case.
 template <class PR, bool TREE, bool EZ>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   constexpr bool f64tree = TREE && sizeof(typename PR::S) == 8;
-  constexpr int RB0 = f64tree ? 3 : 4, SB0 = f64tree ? 8 : 6;
+  constexpr int RB0 = f64tree ? 3 : 4, SB0 = f64tree ? 7 : 6;
   constexpr int RB6 = f64tree ? 5 : 6;
   constexpr int SB4 = f64tree ? 2 : 6;
   switch (shape) {

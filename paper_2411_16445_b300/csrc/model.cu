@@ -713,13 +713,11 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   HostVec<double> h_cdt(n_elem), h_dc(n_elem), h_em(n_elem), h_a(n_elem), h_V(n_elem);
   HostVec<int16_t> h_par, h_och, h_ocn;
   HostVec<uint8_t> h_tf;
-  HostVec<double> h_aoch;
   if (M->tree) {
     h_par.resize(n_elem);
     h_och.resize(n_elem);
     h_ocn.resize(n_elem);
     h_tf.resize(n_elem);
-    h_aoch.resize(n_elem);
   }
   std::vector<uint8_t> h_is_hh(n_lanes, 0);
   std::vector<double> h_hhg(3 * n_lanes, 0.0), h_hhe(3 * n_lanes, 0.0);
@@ -759,7 +757,6 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       std::fill(h_och.begin() + e0, h_och.begin() + e1, (int16_t)-1);
       std::fill(h_ocn.begin() + e0, h_ocn.begin() + e1, (int16_t)-1);
       std::fill(h_tf.begin() + e0, h_tf.begin() + e1, (uint8_t)0);
-      std::fill(h_aoch.begin() + e0, h_aoch.begin() + e1, 0.0);
     }
   }
   for (int64_t L = gi * kLanes; L < (gi + 1) * kLanes; ++L) {
@@ -827,10 +824,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         if (i != g.parent[i] + 1) ++n_other[g.parent[i]];
       for (int i = 0; i < n; ++i) {
         const int64_t e = elem(L, i);
-        if (n_other[i] == 1) {
-          h_tf[e] |= kForkPop;
-          h_aoch[e] = h_a[elem(L, h_och[e])];
-        }
+        if (n_other[i] == 1) h_tf[e] |= kForkPop;
         if (i > 0 && i != g.parent[i] + 1 && n_other[g.parent[i]] == 1) h_tf[e] |= kForkPush;
       }
       // The stacks need the pushes and pops to nest (LIFO) in both sweeps, as in
@@ -857,6 +851,14 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       }
       if (!nested)
         for (int i = 0; i < n; ++i) h_tf[elem(L, i)] = 0;
+      // what the kernels with fork stacks read instead of the parent and
+      // child-list rows: whether the parent is the previous row (the carried
+      // first child), and whether the other children go through the list
+      for (int i = 0; i < n; ++i) {
+        const int64_t e = elem(L, i);
+        if (i > 0 && g.parent[i] == i - 1) h_tf[e] |= kParPrev;
+        if (n_other[i] > 0 && !(h_tf[e] & kForkPop)) h_tf[e] |= kOtherList;
+      }
     }
     if (M->cell_diff[lane_gid[L]]) {
       // PRP diffusion (Eq. diffusion on the cable's tree): CV volume, the
@@ -1283,13 +1285,12 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   const size_t o_cdt = R(8 * n_elem), o_dc = R(8 * n_elem), o_em = R(8 * n_elem),
                o_a = R(8 * n_elem), o_gs = R(tsum * n_elem), o_es = R(tsum * n_elem);
   const size_t o_f = R(8 * n_elem), o_xp = R(8 * n_elem);
-  size_t o_par = 0, o_och = 0, o_ocn = 0, o_tf = 0, o_aoch = 0;
+  size_t o_par = 0, o_och = 0, o_ocn = 0, o_tf = 0;
   if (M->tree) {
     o_par = R(2 * n_elem);
     o_och = R(2 * n_elem);
     o_ocn = R(2 * n_elem);
     o_tf = R(n_elem);
-    o_aoch = R(8 * n_elem);
   }
   const size_t o_ishh = R(n_lanes), o_hhg = R(8 * 3 * n_lanes), o_hhe = R(8 * 3 * n_lanes),
                o_gate = R(8 * 3 * n_lanes), o_iinj = R(8 * n_lanes), o_kon = R(8 * n_lanes),
@@ -1384,14 +1385,13 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       });
     };
     to_ff(h_V); to_ff(h_cdt); to_ff(h_dc); to_ff(h_em); to_ff(h_a);
-    if (M->tree) to_ff(h_aoch);
   }
   putv(o_V, h_V);
   putv(o_cdt, h_cdt); putv(o_dc, h_dc); putv(o_em, h_em); putv(o_a, h_a);
   putv(o_hhg, h_hhg); putv(o_hhe, h_hhe);
   if (M->tree) {
     putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn);
-    putv(o_tf, h_tf); putv(o_aoch, h_aoch);
+    putv(o_tf, h_tf);
   }
   putv(o_ishh, h_is_hh);
   putv(o_wcell, h_wcell); putv(o_wbr_s, h_wbr_s); putv(o_wbr_e, h_wbr_e); putv(o_wlvl, h_wlvl);
@@ -1455,7 +1455,6 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     A.och_head = (const int16_t*)P8(o_och);
     A.och_next = (const int16_t*)P8(o_ocn);
     A.tflag = (const uint8_t*)P8(o_tf);
-    A.aoch = (const double*)P8(o_aoch);
   }
   A.is_hh = (const uint8_t*)P8(o_ishh);
   A.hh_g = (const double*)P8(o_hhg); A.hh_e = (const double*)P8(o_hhe);
