@@ -150,6 +150,11 @@ struct EpochArgs {
   const double* hh_e;        // [3][n_lanes] ena, ek, el [mV]
   double* gate;              // [3][n_lanes] m, h, n
   const double* iinj;
+  // PA_MIXED, groups (either bin) with em_derived[g]: the leak E-term of a
+  // dendrite row is (C/dt) em_k[lane], the soma row's em_soma[lane]
+  const double* em_k;
+  const double* em_soma;
+  const uint8_t* em_derived;
   const int64_t* k_on;
   const int64_t* k_off;
   const double* thresh;

@@ -565,6 +565,9 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
   const bool hh = n > 0 && A.is_hh[L];
   SomaHH<PR::kMech32> soma;
   if (hh) soma.load(A.gate, A.n_lanes, L);
+  // the leak E-term formed from C/dt instead of staged (warp-uniform)
+  const bool em_der = PR::kDeriveEM && A.em_derived[g] != 0;
+  const R emk = em_der ? RW::from_d(A.em_k[L]) : RW::zero();
   const double iinj_val = n > 0 ? A.iinj[L] : 0.0;
   const int64_t kon = n > 0 ? A.k_on[L] : 0, koff = n > 0 ? A.k_off[L] : 0;
   const double th = n > 0 ? A.thresh[L] : 0.0;
@@ -722,11 +725,12 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
             return;
           }
           // with EZ the g E sums are signed zeros: not staged (see ez_add)
-          mbar_expect_tx(&bar[s], cnt * (ST::kBackRow - (EZ ? ST::kM : 0)));
+          mbar_expect_tx(&bar[s],
+                         cnt * (ST::kBackRow - (EZ ? ST::kM : 0) - (em_der ? ST::kD : 0)));
           bulk_load(st + ST::oV, Vg + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oCDT, CDT + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oDC, DC + r0 * 32, cnt * ST::kD, &bar[s]);
-          bulk_load(st + ST::oEM, EM + r0 * 32, cnt * ST::kD, &bar[s]);
+          if (!em_der) bulk_load(st + ST::oEM, EM + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oA, AA + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kM, &bar[s]);
           if (!EZ) bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kM, &bar[s]);
@@ -783,11 +787,13 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
               b = RW::add(RW::fma(cdt, v, RW::from_d(emt)), RW::from_d(iinj));
             } else {
               d = RW::add(dcv, gsv);
-              b = RW::add(RW::fma(cdt, v, ((const R*)(st + ST::oEM))[r]), RW::from_d(iinj));
+              const R emv = em_der ? RW::from_d(A.em_soma[L]) : ((const R*)(st + ST::oEM))[r];
+              b = RW::add(RW::fma(cdt, v, emv), RW::from_d(iinj));
             }
           } else {
             d = RW::add(dcv, gsv);
-            b = RW::fma(cdt, v, ((const R*)(st + ST::oEM))[r]);
+            const R emv = em_der ? RW::mul(cdt, emk) : ((const R*)(st + ST::oEM))[r];
+            b = RW::fma(cdt, v, emv);
           }
           if constexpr (!EZ) {
             b = RW::add(b, PR::sum_r(((const TS*)(st + ST::oES))[r]));

@@ -722,6 +722,12 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   std::vector<uint8_t> h_is_hh(n_lanes, 0);
   std::vector<double> h_hhg(3 * n_lanes, 0.0), h_hhe(3 * n_lanes, 0.0);
   std::vector<double> h_iinj(n_lanes, 0.0), h_thresh(n_lanes, 0.0);
+  // PA_MIXED forms a passive dendrite's leak E-term g E as (C/dt) k, with k
+  // one constant per cell, where every cell of a thread-per-cell group has its
+  // soma on row 0 only and one passive mechanism on every other row; the soma
+  // row's E-term is kept per lane (em_soma)
+  std::vector<double> h_emk(n_lanes, 0.0), h_em0(n_lanes, 0.0);
+  std::vector<uint8_t> h_emok(n_lanes, 1), h_emder(std::max<int64_t>(n_groups, 1), 0);
   std::vector<int64_t> h_kon(n_lanes, 0), h_koff(n_lanes, 0);
   std::vector<double> h_pcv, h_pdg, h_pa, h_pvdt, h_psrc;
   std::vector<double> h_cadg, h_caa, h_cavdt, h_cavol;
@@ -913,6 +919,18 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         h_cavol[e] = cvol[i];
       }
     }
+    {
+      bool ok = g.region[0] == 0;
+      for (int i = 1; i < n && ok; ++i)
+        ok = g.region[i] != 0 && mechs[cl.dend_mech].kind == PA_MECH_PAS;
+      h_emok[L] = ok ? 1 : 0;
+      h_em0[L] = h_em[elem(L, 0)];
+      if (ok && n > 1) {
+        const double* p = mechs[cl.dend_mech].params;
+        // (p0 A 1e-2) e / ((cm A 1e-5) / dt): the CV's area cancels
+        h_emk[L] = ((p[0] * 1e-2) * p[1]) * dt / (cl.cm * 1e-5);
+      }
+    }
     h_iinj[L] = cl.i_step;
     h_kon[L] = std::llround(cl.t_on / dt);
     h_koff[L] = cl.t_off > 1e15 ? INT64_MAX : std::llround(cl.t_off / dt);
@@ -920,6 +938,16 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   }
   }
   });
+
+  for (int64_t gi = 0; gi < n_groups; ++gi) {
+    uint8_t ok = M->precision == PA_MIXED ? 1 : 0;
+    if (gi < n_narrow) {
+      for (int64_t L = gi * kLanes; L < (gi + 1) * kLanes; ++L) ok &= h_emok[L];
+    } else {
+      ok &= h_emok[gi * kLanes];  // a wide cell: its lane slot
+    }
+    h_emder[gi] = ok;
+  }
 
   // ---- branch tables of the wide cells ------------------------------------------
   // A branch is a run of rows i whose parent is i - 1 (rows are contiguous),
@@ -1296,6 +1324,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
                o_gate = R(8 * 3 * n_lanes), o_iinj = R(8 * n_lanes), o_kon = R(8 * n_lanes),
                o_koff = R(8 * n_lanes), o_th = R(8 * n_lanes), o_sp = R(n_lanes),
                o_prp = R(8 * n_lanes), o_hasstc = R(n_lanes), o_rbits = R(8 * n_lanes);
+  const size_t o_emk = R(8 * n_lanes), o_em0 = R(8 * n_lanes), o_emder = R(h_emder.size());
   size_t o_s[kMaxStreams][12];
   for (int s = 0; s < n_streams; ++s) {
     const int64_t ne = M->s_nelem[s];
@@ -1397,6 +1426,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   putv(o_wcell, h_wcell); putv(o_wbr_s, h_wbr_s); putv(o_wbr_e, h_wbr_e); putv(o_wlvl, h_wlvl);
   putv(o_wbr_p, h_wbr_p); putv(o_wbr_c, h_wbr_c); putv(o_wbr_o, h_wbr_o);
   putv(o_iinj, h_iinj); putv(o_kon, h_kon); putv(o_koff, h_koff); putv(o_th, h_thresh);
+  putv(o_emk, h_emk); putv(o_em0, h_em0); putv(o_emder, h_emder);
   putv(o_hasstc, h_has_stc);
   if (ca_stream >= 0) {
     putv(o_cadg, h_cadg); putv(o_caa, h_caa); putv(o_cavdt, h_cavdt); putv(o_cavol, h_cavol);
@@ -1460,6 +1490,9 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   A.hh_g = (const double*)P8(o_hhg); A.hh_e = (const double*)P8(o_hhe);
   A.gate = (double*)P8(o_gate);
   A.iinj = (const double*)P8(o_iinj);
+  A.em_k = (const double*)P8(o_emk);
+  A.em_soma = (const double*)P8(o_em0);
+  A.em_derived = (const uint8_t*)P8(o_emder);
   A.k_on = (const int64_t*)P8(o_kon); A.k_off = (const int64_t*)P8(o_koff);
   A.thresh = (const double*)P8(o_th);
   A.spiked_prev = (uint8_t*)P8(o_sp);

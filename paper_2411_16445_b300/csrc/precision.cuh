@@ -309,6 +309,7 @@ struct PrecF64 {
   using Dc = double;
   using Acc = AccPlain<double>;
   using Row = RowD;
+  static constexpr bool kDeriveEM = false;  // the leak E-term row is read (the oracle's value)
   static constexpr int kId = 0;
   static constexpr bool kMech32 = false;  // HH, calcium, plasticity increments in FP64
   __device__ static __forceinline__ Ec e_const(double e) { return e; }
@@ -331,6 +332,9 @@ struct PrecMix {
   using Dc = float2;  // exp(-dt/tau) as hi + lo
   using Acc = AccFF;
   using Row = RowFF;
+  // a passive dendrite row's leak E-term formed as (C/dt) k where the model
+  // allows it (EpochArgs::em_derived), instead of read
+  static constexpr bool kDeriveEM = true;
   static constexpr int kId = 1;
   static constexpr bool kMech32 = false;
   __device__ static __forceinline__ Ec e_const(double e) { return ff_from_d(e); }
@@ -355,6 +359,7 @@ struct PrecF32 {
   using Dc = float;
   using Acc = AccPlain<float>;
   using Row = RowD;
+  static constexpr bool kDeriveEM = false;
   static constexpr int kId = 2;
   // HH rates and gates, calcium and the GB / STC / STDP increments in FP32
   // (exponential integration with CUDA's expf); the slow state w, h, z, p

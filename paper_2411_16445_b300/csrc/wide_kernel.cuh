@@ -68,6 +68,9 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   const int16_t* __restrict__ OCH = A.och_head;
   const int16_t* __restrict__ OCN = A.och_next;
 
+  // the leak E-term formed from C/dt instead of read, as in the narrow kernel
+  const bool em_der = PR::kDeriveEM && A.em_derived[g] != 0;
+  const R emk = em_der ? RW::from_d(A.em_k[L]) : RW::zero();
   // soma state: lane 0 owns it (every lane keeps prp and the POST_EVENT flag)
   const bool hh = n > 0 && A.is_hh[L];
   SomaHH<PR::kMech32> soma;
@@ -197,8 +200,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         R cf = RW::zero(), ca = RW::zero(), cx = RW::zero();
         // one row of lookahead: the next row's values load during this row's
         // elimination
-        R nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be], nem = EM[e0 + be],
-          na = AA[e0 + be];
+        R nv = Vg[e0 + be], ncdt = CDT[e0 + be], ndc = DC[e0 + be],
+          nem = em_der ? RW::zero() : EM[e0 + be], na = AA[e0 + be];
         TS ngs = GS[e0 + be], nes = EZ ? PR::s_zero() : ES[e0 + be];
         for (int i = be; i >= bs; --i) {
           const int64_t ei = e0 + i;
@@ -207,7 +210,8 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           const R esv = PR::sum_r(nes);  // (EZ: unused)
           if (i > bs) {
             const int64_t en = ei - 1;
-            nv = Vg[en]; ncdt = CDT[en]; ndc = DC[en]; nem = EM[en]; na = AA[en];
+            nv = Vg[en]; ncdt = CDT[en]; ndc = DC[en]; na = AA[en];
+            if (!em_der) nem = EM[en];
             ngs = GS[en];
             if (!EZ) nes = ES[en];
           }
@@ -221,11 +225,12 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
               bb = RW::add(RW::fma(cdt, v, RW::from_d(emt)), RW::from_d(iinj));
             } else {
               d = RW::add(dcv, gsv);
-              bb = RW::add(RW::fma(cdt, v, emv), RW::from_d(iinj));
+              const R em = em_der ? RW::from_d(A.em_soma[L]) : emv;
+              bb = RW::add(RW::fma(cdt, v, em), RW::from_d(iinj));
             }
           } else {
             d = RW::add(dcv, gsv);
-            bb = RW::fma(cdt, v, emv);
+            bb = RW::fma(cdt, v, em_der ? RW::mul(cdt, emk) : emv);
           }
           if constexpr (!EZ) {
             bb = RW::add(bb, esv);
