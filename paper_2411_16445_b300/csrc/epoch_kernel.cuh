@@ -1077,7 +1077,9 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // (FP64, mixed) shape 0 takes 3 backward rows per chunk and 7 entries (many
 // nested forks), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
 // shape 0 takes 4 rows and 6 entries; shape 5 has no stacks (trees with long
-// branches and few forks); 12 warps per SM fit in each case.
+// branches and few forks); 12 warps per SM fit in each case (4-entry stacks
+// that would let shape 1 keep 16 warps per SM on trees made it 33 % slower:
+// the random trees' forks nest deeper).
 template <class PR, bool TREE, bool EZ>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   constexpr bool f64tree = TREE && sizeof(typename PR::S) == 8;

@@ -124,10 +124,18 @@ struct RowFF {
     e = __fmaf_rn(a.y, b.x, e);
     return ff_fast2sum(p, e);
   }
-  __device__ static __forceinline__ R fma(R a, R b, R c) { return ff_add(mul(a, b), c); }
-  __device__ static __forceinline__ R fnma(R a, R b, R c) {
-    const R p = mul(a, b);
-    return ff_add(c, make_float2(-p.x, -p.y));
+  // a b + c and c - a b: the product (ph, pl) exact in ph and FMA-formed in pl,
+  // folded into c by TwoSum without normalising the product first (a shorter
+  // dependent chain than a product followed by an addition)
+  __device__ static __forceinline__ R fma(R a, R b, R c) { return fold(a, b, c, 1.0f); }
+  __device__ static __forceinline__ R fnma(R a, R b, R c) { return fold(a, b, c, -1.0f); }
+  __device__ static __forceinline__ R fold(R a, R b, R c, float sg) {
+    const float ph = __fmul_rn(a.x, b.x);
+    float pl = __fmaf_rn(a.x, b.x, -ph);
+    pl = __fmaf_rn(a.x, b.y, pl);
+    pl = __fmaf_rn(a.y, b.x, pl);
+    const float2 s = ff_twosum(c.x, sg * ph);  // (sg = +-1: exact)
+    return ff_fast2sum(s.x, __fadd_rn(s.y, __fmaf_rn(sg, pl, c.y)));
   }
   // 1/d for d > 0: y0 = rcp.approx(hi), then y0 + y0 (1 - d y0) with the
   // residual formed by FMAs
