@@ -88,6 +88,30 @@ struct Arena {
 
 }  // namespace
 
+// An allocator whose value-less construct leaves elements default-initialised
+// (uninitialised for arithmetic types): large host arrays are then first
+// touched, and filled, by the builder threads that own their ranges.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new ((void*)p) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new ((void*)p) U(std::forward<Args>(args)...);
+  }
+};
+template <class T>
+using HostVec = std::vector<T, NoInitAlloc<T>>;
+
 struct pa_model {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -113,11 +137,11 @@ struct pa_model {
   std::vector<int32_t> row_base;          // per group
   std::vector<int32_t> cell_ncv;          // per gid
   std::vector<int64_t> cell_cv_off;       // per gid, cell-major CV offsets
-  std::vector<int32_t> conn_stream;       // per connection
-  std::vector<int64_t> conn_elem;
-  std::vector<int32_t> conn_kind;         // PA_MECH_* of the connection
-  std::vector<double> conn_weight;
-  std::vector<double> conn_h0;
+  HostVec<int32_t> conn_stream;           // per connection
+  HostVec<int64_t> conn_elem;
+  HostVec<int32_t> conn_kind;             // PA_MECH_* of the connection
+  HostVec<double> conn_weight;
+  HostVec<double> conn_h0;
   bool prp_diff = false;                  // the STC mechanism's PRP diffuses (D_p > 0)
   std::vector<uint8_t> cell_ca;           // per gid: the cell has HCA synapses
   std::vector<uint8_t> cell_diff;         // per gid: the cell's PRP is a field over its CVs
@@ -274,29 +298,6 @@ void bucket_scatter(int64_t n, int64_t n_buckets, B&& bucket, std::vector<int64_
   });
 }
 
-// An allocator whose value-less construct leaves elements default-initialised
-// (uninitialised for arithmetic types): large host arrays are then first
-// touched, and filled, by the builder threads that own their ranges.
-template <class T>
-struct NoInitAlloc : std::allocator<T> {
-  template <class U>
-  struct rebind {
-    using other = NoInitAlloc<U>;
-  };
-  NoInitAlloc() = default;
-  template <class U>
-  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
-  template <class U>
-  void construct(U* p) noexcept {
-    ::new ((void*)p) U;
-  }
-  template <class U, class... Args>
-  void construct(U* p, Args&&... args) {
-    ::new ((void*)p) U(std::forward<Args>(args)...);
-  }
-};
-template <class T>
-using HostVec = std::vector<T, NoInitAlloc<T>>;
 
 template <class V>
 std::vector<float> to_f32(const V& v) {
@@ -414,13 +415,28 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // streams: one per point mechanism used by a connection, in table order
   std::vector<int> mech_stream(n_mech, -1);
   {
+    // over fixed pieces of the connection list; the lowest bad one is reported
+    constexpr int64_t kPieces = 64;
+    std::vector<std::vector<char>> used_p(kPieces, std::vector<char>(n_mech, 0));
+    std::vector<int64_t> bad_p(kPieces, -1);
+    parallel_ranges(kPieces, [&](int64_t p0, int64_t p1) {
+      for (int64_t p = p0; p < p1; ++p)
+        for (int64_t c = n_conn * p / kPieces; c < n_conn * (p + 1) / kPieces; ++c) {
+          const int m = conns[c].mech;
+          if (m < 0 || m >= n_mech || !is_point(mechs[m].kind)) {
+            bad_p[p] = c;
+            break;
+          }
+          used_p[p][m] = 1;
+        }
+    });
+    for (int64_t p = 0; p < kPieces; ++p)
+      if (bad_p[p] >= 0)
+        return set_err(PA_ERR_ARG, "connection %lld: mechanism must be a synapse",
+                       (long long)bad_p[p]);
     std::vector<char> used(n_mech, 0);
-    for (int64_t c = 0; c < n_conn; ++c) {
-      int m = conns[c].mech;
-      if (m < 0 || m >= n_mech || !is_point(mechs[m].kind))
-        return set_err(PA_ERR_ARG, "connection %lld: mechanism must be a synapse", (long long)c);
-      used[m] = 1;
-    }
+    for (int64_t p = 0; p < kPieces; ++p)
+      for (int64_t m = 0; m < n_mech; ++m) used[m] |= used_p[p][m];
     int ns = 0, n_stc = 0;
     for (int64_t m = 0; m < n_mech; ++m)
       if (used[m]) {
@@ -635,14 +651,37 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   M->cell_diff.assign(n_cells, 0);
   std::vector<uint8_t> cell_ca(n_cells, 0);  // cells with HCA synapses (narrow bin)
   {
+    // synapses per cell: per-piece counts in parallel, then summed per cell
     std::vector<int64_t> cell_syn(n_cells, 0);
-    for (int64_t c = 0; c < n_conn; ++c)
-      if (conns[c].dst_gid >= 0 && conns[c].dst_gid < n_cells) {
-        ++cell_syn[conns[c].dst_gid];
-        if (M->prp_diff && mechs[conns[c].mech].kind == PA_MECH_STC)
-          M->cell_diff[conns[c].dst_gid] = 1;
-        if (mechs[conns[c].mech].kind == PA_MECH_HCA) cell_ca[conns[c].dst_gid] = 1;
-      }
+    {
+      constexpr int64_t kPieces = 16;
+      std::vector<std::vector<int32_t>> part(kPieces);
+      parallel_ranges(kPieces, [&](int64_t p0, int64_t p1) {
+        for (int64_t p = p0; p < p1; ++p) {
+          part[p].assign(n_cells, 0);
+          for (int64_t c = n_conn * p / kPieces; c < n_conn * (p + 1) / kPieces; ++c)
+            if (conns[c].dst_gid >= 0 && conns[c].dst_gid < n_cells) ++part[p][conns[c].dst_gid];
+        }
+      });
+      parallel_ranges(n_cells, [&](int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c)
+          for (int64_t p = 0; p < kPieces; ++p) cell_syn[c] += part[p][c];
+      });
+    }
+    // cells with a diffusing PRP or heterosynaptic calcium (only where such a
+    // mechanism exists)
+    bool any_stc = false, any_hca = false;
+    for (int64_t m = 0; m < n_mech; ++m) {
+      any_stc = any_stc || mechs[m].kind == PA_MECH_STC;
+      any_hca = any_hca || mechs[m].kind == PA_MECH_HCA;
+    }
+    if ((M->prp_diff && any_stc) || any_hca)
+      for (int64_t c = 0; c < n_conn; ++c)
+        if (conns[c].dst_gid >= 0 && conns[c].dst_gid < n_cells) {
+          if (M->prp_diff && mechs[conns[c].mech].kind == PA_MECH_STC)
+            M->cell_diff[conns[c].dst_gid] = 1;
+          if (mechs[conns[c].mech].kind == PA_MECH_HCA) cell_ca[conns[c].dst_gid] = 1;
+        }
     std::vector<int32_t> morph_branches(n_morph, 0);
     for (int64_t j = 0; j < n_morph; ++j)
       for (int i = 0; i < morphs[j].n_cv; ++i)
@@ -1013,11 +1052,13 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   }
 
   // ---- synapses: one per connection, streams by mechanism -------------------------
-  M->conn_stream.assign(n_conn, -1);
-  M->conn_elem.assign(n_conn, -1);
-  M->conn_kind.assign(n_conn, 0);
-  M->conn_weight.assign(n_conn, 0.0);
-  M->conn_h0.assign(n_conn, 0.0);
+  // (every entry is written by the parallel loops below: the tables by the
+  // validation, stream and element by the synapse layout)
+  M->conn_stream.resize(n_conn);
+  M->conn_elem.resize(n_conn);
+  M->conn_kind.resize(n_conn);
+  M->conn_weight.resize(n_conn);
+  M->conn_h0.resize(n_conn);
   // the synapses of each (stream, lane) pair, by a counting sort: sl_ptr[q] ..
   // sl_ptr[q + 1] in syn_rec, q = stream * n_lanes + lane
   const size_t n_sl = (size_t)n_lanes * (size_t)std::max(n_streams, 1);
@@ -1025,7 +1066,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   int64_t max_delay = 1, min_delay = INT64_MAX;
   int32_t max_dc = 0;
   std::vector<int64_t> n_out(n_cells + 1, 0);
-  std::vector<int32_t> conn_D(n_conn, 0);
+  HostVec<int32_t> conn_D(n_conn);  // (recurrent connections only)
   // validation and the per-connection tables over fixed pieces of the
   // connection list, in parallel; the lowest bad connection is reported
   {
@@ -1072,7 +1113,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
           if (M->sp[s].dc_steps > o.max_dc) o.max_dc = M->sp[s].dc_steps;
           M->conn_kind[c] = mechs[k.mech].kind;
           M->conn_weight[c] = k.weight;
-          if (mechs[k.mech].kind == PA_MECH_STC) M->conn_h0[c] = mechs[k.mech].params[12];
+          M->conn_h0[c] = mechs[k.mech].kind == PA_MECH_STC ? mechs[k.mech].params[12] : 0.0;
         }
       }
     });
@@ -1087,7 +1128,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // counting sort of the connections by (stream, lane): per piece of the
   // connection list a count per bucket, then each piece fills its own slots
   // (within a bucket, connections stay in list order)
-  std::vector<SynRec> syn_rec(n_conn);
+  HostVec<SynRec> syn_rec(n_conn);
   {
     int64_t np = 16;
     while (np > 1 && (double)np * (double)n_sl * 8.0 > 512.0 * 1024 * 1024) np /= 2;
@@ -2030,10 +2071,12 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
     if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
     if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "read back: %s", cudaGetErrorString(e));
     const float* f = (const float*)raw.data();
-    for (int64_t i = 0; i < n; ++i)
-      dst[i] = code == 8    ? ((const double*)raw.data())[i]
-               : code == 4  ? (double)f[i]
-                            : (double)f[2 * i] + (double)f[2 * i + 1];
+    parallel_ranges(n, [&](int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i)
+        dst[i] = code == 8    ? ((const double*)raw.data())[i]
+                 : code == 4  ? (double)f[i]
+                              : (double)f[2 * i] + (double)f[2 * i + 1];
+    });
     return 0;
   };
   std::vector<double> tmp, tmp2;
@@ -2133,15 +2176,17 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
       kstep[s].assign(ks.begin(), ks.end());
     }
   }
-  for (int64_t c = 0; c < M->n_conn; ++c) {
-    const int s = M->conn_stream[c];
-    const auto& v = per_stream[s];
-    out[c] = v.empty() ? 0.0 : v[M->conn_elem[c]];
-    if (!kstep[s].empty()) {
-      const double tau = field == PA_FIELD_APRE ? M->sp[s].tau_pre : M->sp[s].tau_post;
-      out[c] *= std::exp(-((double)(M->step - (int64_t)kstep[s][M->conn_elem[c]]) * M->dt) / tau);
+  parallel_ranges(M->n_conn, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      const int s = M->conn_stream[c];
+      const auto& v = per_stream[s];
+      out[c] = v.empty() ? 0.0 : v[M->conn_elem[c]];
+      if (!kstep[s].empty()) {
+        const double tau = field == PA_FIELD_APRE ? M->sp[s].tau_pre : M->sp[s].tau_post;
+        out[c] *= std::exp(-((double)(M->step - (int64_t)kstep[s][M->conn_elem[c]]) * M->dt) / tau);
+      }
     }
-  }
+  });
   return PA_OK;
 }
 
@@ -2151,21 +2196,38 @@ int pa_read_weights(pa_model* M, double* out, int64_t cap, int64_t* n_out) {
   *n_out = M->n_conn;
   if (cap == 0) return PA_OK;
   if (!out || cap < M->n_conn) return set_err(PA_ERR_ARG, "output too small");
-  std::vector<double> w(M->n_conn), h(M->n_conn), z(M->n_conn);
-  int64_t n;
-  int rc = pa_read_state(M, PA_FIELD_W, w.data(), M->n_conn, &n);
-  if (!rc) rc = pa_read_state(M, PA_FIELD_H, h.data(), M->n_conn, &n);
-  if (!rc) rc = pa_read_state(M, PA_FIELD_Z, z.data(), M->n_conn, &n);
-  if (rc) return rc;
-  for (int64_t c = 0; c < M->n_conn; ++c) {
-    switch (M->conn_kind[c]) {
-      case PA_MECH_GB:
-      case PA_MECH_STDP:
-      case PA_MECH_HCA: out[c] = w[c]; break;
-      case PA_MECH_STC: out[c] = h[c] + M->conn_h0[c] * z[c]; break;
-      default: out[c] = M->conn_weight[c];
-    }
+  // only the fields the model's mechanisms have
+  bool need_w = false, need_hz = false;
+  for (int s = 0; s < M->n_streams; ++s) {
+    const int kind = M->sp[s].kind;
+    need_w = need_w || kind == SK_GB || kind == SK_STDP || kind == SK_HCA;
+    need_hz = need_hz || kind == SK_STC;
   }
+  std::vector<double> w, h, z;
+  int64_t n;
+  int rc = 0;
+  if (need_w) {
+    w.resize(M->n_conn);
+    rc = pa_read_state(M, PA_FIELD_W, w.data(), M->n_conn, &n);
+  }
+  if (!rc && need_hz) {
+    h.resize(M->n_conn);
+    z.resize(M->n_conn);
+    rc = pa_read_state(M, PA_FIELD_H, h.data(), M->n_conn, &n);
+    if (!rc) rc = pa_read_state(M, PA_FIELD_Z, z.data(), M->n_conn, &n);
+  }
+  if (rc) return rc;
+  parallel_ranges(M->n_conn, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      switch (M->conn_kind[c]) {
+        case PA_MECH_GB:
+        case PA_MECH_STDP:
+        case PA_MECH_HCA: out[c] = w[c]; break;
+        case PA_MECH_STC: out[c] = h[c] + M->conn_h0[c] * z[c]; break;
+        default: out[c] = M->conn_weight[c];
+      }
+    }
+  });
   return PA_OK;
 }
 
