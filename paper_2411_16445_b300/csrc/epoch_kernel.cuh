@@ -284,7 +284,7 @@ __device__ __forceinline__ void fence_async_shared() {
 }
 
 // Shared-memory layout of one warp's stages for a given precision / tree flag.
-template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth>
+template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth, bool EZ>
 struct Stage {
   // bytes per row (32 lanes) of each staged array.  With fork stacks a tree
   // stages one flag byte per row (fork push / pop, parent = previous row,
@@ -292,15 +292,16 @@ struct Stage {
   // rows.
   static constexpr bool kStacks = TREE && kStackDepth > 0;  // fork stacks in use
   static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(typename PR::S),
+                       kMES = EZ ? 0 : kM,  // the g E sums (not staged with every E = +0)
                        kI = (TREE && !kStacks) ? 32 * 2 : 0, kT = kStacks ? 32 : 0;
   // backward pass: V, C/dt, diagonal, leak E term, axial coupling, synaptic sums,
   // tree rows
   static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oDC = oCDT + kRowsBack * kD,
                        oEM = oDC + kRowsBack * kD, oA = oEM + kRowsBack * kD,
                        oGS = oA + kRowsBack * kD, oES = oGS + kRowsBack * kM,
-                       oPAR = oES + kRowsBack * kM, oOCH = oPAR + kRowsBack * kI,
+                       oPAR = oES + kRowsBack * kMES, oOCH = oPAR + kRowsBack * kI,
                        oTF = oOCH + kRowsBack * kI, kBackBytes = oTF + kRowsBack * kT;
-  static constexpr int kBackRow = 5 * kD + 2 * kM + 2 * kI + kT;
+  static constexpr int kBackRow = 5 * kD + kM + kMES + 2 * kI + kT;
   // forward pass: f, x', tree rows
   static constexpr int fF = 0, fXP = fF + kRowsFwd * kD, fPAR = fXP + kRowsFwd * kD,
                        fTF = fPAR + kRowsFwd * kI, kFwdBytes = fTF + kRowsFwd * kT;
@@ -520,7 +521,7 @@ __device__ __noinline__ void hca_stream(const EpochArgs& A, int s, int g, int la
 // A, with the warp's shared-memory stages at wbuf.
 template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kStackDepth, bool EZ>
 __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char* wbuf) {
-  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
+  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth, EZ>;
   using TS = typename PR::S;
   using TG = typename PR::G;
   const int lane = threadIdx.x & 31;
@@ -725,8 +726,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
             return;
           }
           // with EZ the g E sums are signed zeros: not staged (see ez_add)
-          mbar_expect_tx(&bar[s],
-                         cnt * (ST::kBackRow - (EZ ? ST::kM : 0) - (em_der ? ST::kD : 0)));
+          mbar_expect_tx(&bar[s], cnt * (ST::kBackRow - (em_der ? ST::kD : 0)));
           bulk_load(st + ST::oV, Vg + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oCDT, CDT + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oDC, DC + r0 * 32, cnt * ST::kD, &bar[s]);
@@ -1014,7 +1014,7 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
 template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kMinBlocks,
           int kStackDepth, bool EZ>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) epoch_kernel(const EpochArgs A) {
-  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
+  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth, EZ>;
   extern __shared__ __align__(128) char smem_raw[];
   const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   epoch_warp<PR, TREE, kRowsBack, kRowsFwd, kStackDepth, EZ>(
@@ -1033,7 +1033,7 @@ template <class PR, bool TREE, int kRowsBack, int kRowsFwd, int kThreads, int kM
           int kStackDepth, bool EZ>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     epoch_kernel_grouped(const EpochArgs* __restrict__ args, const int2* __restrict__ bmap) {
-  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth>;
+  using ST = Stage<PR, TREE, kRowsBack, kRowsFwd, kStackDepth, EZ>;
   extern __shared__ __align__(128) char smem_raw[];
   __shared__ __align__(128) char args_raw[kArgsSmemBytes];
   const int2 bm = bmap[blockIdx.x];
@@ -1053,7 +1053,7 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
   const int64_t warps = a.n_narrow;
   const int blocks = (int)((warps * 32 + threads - 1) / threads);
   if (blocks == 0) return 0;
-  const int smem = warps_per_block * Stage<PR, TREE, RB, RF, SB>::kWarpBytes;
+  const int smem = warps_per_block * Stage<PR, TREE, RB, RF, SB, EZ>::kWarpBytes;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
@@ -1078,8 +1078,8 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // and 8 entries (many nested forks), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
 // shape 0 takes 4 rows and 6 entries; shape 5 has no stacks (trees with long
 // branches and few forks); 12 warps per SM fit in each case (4-entry stacks
-// that would let shape 1 keep 16 warps per SM on trees made it 33 % slower:
-// the random trees' forks nest deeper).
+// that would let shape 1 keep 16 warps per SM on trees made it 33 % slower,
+// 6-entry stacks with 8 forward rows 19 %: the random trees' forks nest deeper).
 template <class PR, bool TREE, bool EZ>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   constexpr bool f64tree = TREE && sizeof(typename PR::S) == 8;
@@ -1106,7 +1106,7 @@ int launch_epoch_grouped_t(const EpochArgs* d_args, const int2* d_bmap, int n_bl
                            void* stream) {
   constexpr int WPB = kGroupedWarpsPerBlock;
   if (n_blocks == 0) return 0;
-  const int smem = WPB * Stage<PR, TREE, RB, RF, SB>::kWarpBytes;
+  const int smem = WPB * Stage<PR, TREE, RB, RF, SB, EZ>::kWarpBytes;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
