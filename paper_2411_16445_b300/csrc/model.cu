@@ -784,6 +784,132 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     M->prp_vol.assign(n_elem, 0.0);
     M->prp_gsum.assign(n_elem, 0.0);
   }
+  // One cell's discretisation (CV geometry, cable coefficients, tree tables,
+  // fork flags, the soma's HH conductances, the mixed form's leak E-term
+  // ratio) into arrays indexed by at(i) for CV i
+  struct HHOut {
+    uint8_t is_hh = 0;
+    double g[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
+  };
+  struct EmOut {
+    uint8_t ok = 0;
+    double k = 0.0, em0 = 0.0;
+  };
+  auto discretise = [&](const pa_cell& cl, auto at, double* cdt_, double* dc_, double* em_,
+                        double* a_, double* v_, int16_t* par_, int16_t* och_, int16_t* ocn_,
+                        uint8_t* tf_, HHOut& hh, EmOut& eo, std::vector<double>& rhalf,
+                        std::vector<double>& gax) {
+    const pa_morphology& g = morphs[cl.morph];
+    const int n = g.n_cv;
+    rhalf.assign(n, 0.0);
+    gax.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      const double Lc = g.length_um[i], dia = g.diam_um[i];
+      const double r = 0.5 * dia;
+      const double A = (kPi * dia) * Lc;               // um2
+      const double cap = (cl.cm * A) * 1e-5;            // nF
+      const int64_t e = at(i);
+      cdt_[e] = cap / dt;                              // uS
+      rhalf[i] = ((cl.ra * (0.5 * Lc)) / (kPi * (r * r))) * 1e-2;  // Mohm
+      const int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
+      const double* p = mechs[m].params;
+      if (mechs[m].kind == PA_MECH_PAS) {
+        const double gp = (p[0] * A) * 1e-2;            // S/cm2 * um2 -> uS
+        em_[e] = gp * p[1];
+        dc_[e] = gp;                                   // leak, folded in below
+      } else {
+        hh.is_hh = 1;
+        hh.g[0] = (p[0] * A) * 1e-2;
+        hh.g[1] = (p[1] * A) * 1e-2;
+        hh.g[2] = (p[2] * A) * 1e-2;
+        hh.e[0] = p[3];
+        hh.e[1] = p[4];
+        hh.e[2] = p[5];
+        dc_[e] = 0.0;                                  // gates enter per step
+        em_[e] = 0.0;
+      }
+      v_[e] = cl.v_init;
+    }
+    // axial conductance of two half-cylinders in series, summed in CV order
+    for (int i = 1; i < n; ++i) {
+      const int p = g.parent[i];
+      const double gi = 1.0 / (rhalf[i] + rhalf[p]);
+      a_[at(i)] = -gi;
+      gax[i] += gi;
+      gax[p] += gi;
+    }
+    for (int i = 0; i < n; ++i) {
+      const int64_t e = at(i);
+      const int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
+      const double base = cdt_[e] + gax[i];
+      dc_[e] = mechs[m].kind == PA_MECH_PAS ? base + dc_[e] : base;
+    }
+    if (M->tree) {
+      // other (non-first) children of each node, linked from the highest index down
+      for (int i = 1; i < n; ++i) par_[at(i)] = (int16_t)g.parent[i];
+      for (int i = 1; i < n; ++i) {
+        const int p = g.parent[i];
+        if (i == p + 1) continue;  // the first child is eliminated through registers
+        // children are visited in increasing i: push to the front -> descending list
+        ocn_[at(i)] = och_[at(p)];
+        och_[at(p)] = (int16_t)i;
+      }
+      // fork flags: a row with exactly one other child takes that child's values
+      // from the warp's fork stack (LIFO in both passes), the child pushes them
+      std::vector<int32_t> n_other(n, 0);
+      for (int i = 1; i < n; ++i)
+        if (i != g.parent[i] + 1) ++n_other[g.parent[i]];
+      for (int i = 0; i < n; ++i) {
+        const int64_t e = at(i);
+        if (n_other[i] == 1) tf_[e] |= kForkPop;
+        if (i > 0 && i != g.parent[i] + 1 && n_other[g.parent[i]] == 1) tf_[e] |= kForkPush;
+      }
+      // The stacks need the pushes and pops to nest (LIFO) in both sweeps, as in
+      // depth-first numberings; a numbering that interleaves subtrees (side
+      // branches numbered after the trunk, in trunk order) keeps the linked lists.
+      bool nested = true;
+      std::vector<int> stk;
+      for (int i = n - 1; i >= 0 && nested; --i) {
+        const uint8_t f = tf_[at(i)];
+        if (f & kForkPop) {
+          if (stk.empty() || stk.back() != och_[at(i)]) nested = false;
+          else stk.pop_back();
+        }
+        if (f & kForkPush) stk.push_back(i);
+      }
+      stk.clear();
+      for (int i = 0; i < n && nested; ++i) {
+        const uint8_t f = tf_[at(i)];
+        if (f & kForkPush) {
+          if (stk.empty() || stk.back() != g.parent[i]) nested = false;
+          else stk.pop_back();
+        }
+        if (f & kForkPop) stk.push_back(i);
+      }
+      if (!nested)
+        for (int i = 0; i < n; ++i) tf_[at(i)] = 0;
+      // what the kernels with fork stacks read instead of the parent and
+      // child-list rows: whether the parent is the previous row (the carried
+      // first child), and whether the other children go through the list
+      for (int i = 0; i < n; ++i) {
+        const int64_t e = at(i);
+        if (i > 0 && g.parent[i] == i - 1) tf_[e] |= kParPrev;
+        if (n_other[i] > 0 && !(tf_[e] & kForkPop)) tf_[e] |= kOtherList;
+      }
+    }
+    {
+      bool ok = g.region[0] == 0;
+      for (int i = 1; i < n && ok; ++i)
+        ok = g.region[i] != 0 && mechs[cl.dend_mech].kind == PA_MECH_PAS;
+      eo.ok = ok ? 1 : 0;
+      eo.em0 = em_[at(0)];
+      if (ok && n > 1) {
+        const double* p = mechs[cl.dend_mech].params;
+        // (p0 A 1e-2) e / ((cm A 1e-5) / dt): the CV's area cancels
+        eo.k = ((p[0] * 1e-2) * p[1]) * dt / (cl.cm * 1e-5);
+      }
+    }
+  };
   // cells are independent: groups of lanes in parallel
   parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
   std::vector<double> rhalf, gax, vol, hx, gdx;
@@ -809,102 +935,21 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     const pa_cell& cl = cells[lane_gid[L]];
     const pa_morphology& g = morphs[cl.morph];
     const int n = g.n_cv;
-    rhalf.assign(n, 0.0);
-    gax.assign(n, 0.0);
-    for (int i = 0; i < n; ++i) {
-      const double Lc = g.length_um[i], dia = g.diam_um[i];
-      const double r = 0.5 * dia;
-      const double A = (kPi * dia) * Lc;               // um2
-      const double cap = (cl.cm * A) * 1e-5;            // nF
-      const int64_t e = elem(L, i);
-      h_cdt[e] = cap / dt;                              // uS
-      rhalf[i] = ((cl.ra * (0.5 * Lc)) / (kPi * (r * r))) * 1e-2;  // Mohm
-      const int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
-      const double* p = mechs[m].params;
-      if (mechs[m].kind == PA_MECH_PAS) {
-        const double gp = (p[0] * A) * 1e-2;            // S/cm2 * um2 -> uS
-        h_em[e] = gp * p[1];
-        h_dc[e] = gp;                                   // leak, folded in below
-      } else {
-        h_is_hh[L] = 1;
-        h_hhg[L] = (p[0] * A) * 1e-2;
-        h_hhg[n_lanes + L] = (p[1] * A) * 1e-2;
-        h_hhg[2 * n_lanes + L] = (p[2] * A) * 1e-2;
-        h_hhe[L] = p[3];
-        h_hhe[n_lanes + L] = p[4];
-        h_hhe[2 * n_lanes + L] = p[5];
-        h_dc[e] = 0.0;                                  // gates enter per step
-        h_em[e] = 0.0;
-      }
-      h_V[e] = cl.v_init;
-    }
-    // axial conductance of two half-cylinders in series, summed in CV order
-    for (int i = 1; i < n; ++i) {
-      const int p = g.parent[i];
-      const double gi = 1.0 / (rhalf[i] + rhalf[p]);
-      h_a[elem(L, i)] = -gi;
-      gax[i] += gi;
-      gax[p] += gi;
-    }
-    for (int i = 0; i < n; ++i) {
-      const int64_t e = elem(L, i);
-      const int m = g.region[i] == 0 ? cl.soma_mech : cl.dend_mech;
-      const double base = h_cdt[e] + gax[i];
-      h_dc[e] = mechs[m].kind == PA_MECH_PAS ? base + h_dc[e] : base;
-    }
-    if (M->tree) {
-      // other (non-first) children of each node, linked from the highest index down
-      for (int i = 1; i < n; ++i) h_par[elem(L, i)] = (int16_t)g.parent[i];
-      for (int i = 1; i < n; ++i) {
-        const int p = g.parent[i];
-        if (i == p + 1) continue;  // the first child is eliminated through registers
-        // children are visited in increasing i: push to the front -> descending list
-        h_ocn[elem(L, i)] = h_och[elem(L, p)];
-        h_och[elem(L, p)] = (int16_t)i;
-      }
-      // fork flags: a row with exactly one other child takes that child's values
-      // from the warp's fork stack (LIFO in both passes), the child pushes them
-      std::vector<int32_t> n_other(n, 0);
-      for (int i = 1; i < n; ++i)
-        if (i != g.parent[i] + 1) ++n_other[g.parent[i]];
-      for (int i = 0; i < n; ++i) {
-        const int64_t e = elem(L, i);
-        if (n_other[i] == 1) h_tf[e] |= kForkPop;
-        if (i > 0 && i != g.parent[i] + 1 && n_other[g.parent[i]] == 1) h_tf[e] |= kForkPush;
-      }
-      // The stacks need the pushes and pops to nest (LIFO) in both sweeps, as in
-      // depth-first numberings; a numbering that interleaves subtrees (side
-      // branches numbered after the trunk, in trunk order) keeps the linked lists.
-      bool nested = true;
-      std::vector<int> stk;
-      for (int i = n - 1; i >= 0 && nested; --i) {
-        const uint8_t f = h_tf[elem(L, i)];
-        if (f & kForkPop) {
-          if (stk.empty() || stk.back() != h_och[elem(L, i)]) nested = false;
-          else stk.pop_back();
-        }
-        if (f & kForkPush) stk.push_back(i);
-      }
-      stk.clear();
-      for (int i = 0; i < n && nested; ++i) {
-        const uint8_t f = h_tf[elem(L, i)];
-        if (f & kForkPush) {
-          if (stk.empty() || stk.back() != g.parent[i]) nested = false;
-          else stk.pop_back();
-        }
-        if (f & kForkPop) stk.push_back(i);
-      }
-      if (!nested)
-        for (int i = 0; i < n; ++i) h_tf[elem(L, i)] = 0;
-      // what the kernels with fork stacks read instead of the parent and
-      // child-list rows: whether the parent is the previous row (the carried
-      // first child), and whether the other children go through the list
-      for (int i = 0; i < n; ++i) {
-        const int64_t e = elem(L, i);
-        if (i > 0 && g.parent[i] == i - 1) h_tf[e] |= kParPrev;
-        if (n_other[i] > 0 && !(h_tf[e] & kForkPop)) h_tf[e] |= kOtherList;
+    HHOut hh;
+    EmOut eo;
+    discretise(cl, [&](int i) { return elem(L, i); }, h_cdt.data(), h_dc.data(), h_em.data(),
+               h_a.data(), h_V.data(), h_par.data(), h_och.data(), h_ocn.data(), h_tf.data(), hh,
+               eo, rhalf, gax);
+    if (hh.is_hh) {
+      h_is_hh[L] = 1;
+      for (int j = 0; j < 3; ++j) {
+        h_hhg[j * n_lanes + L] = hh.g[j];
+        h_hhe[j * n_lanes + L] = hh.e[j];
       }
     }
+    h_emok[L] = eo.ok;
+    h_em0[L] = eo.em0;
+    h_emk[L] = eo.k;
     if (M->cell_diff[lane_gid[L]]) {
       // PRP diffusion (Eq. diffusion on the cable's tree): CV volume, the
       // diffusive conductance of two half-cylinders in series
@@ -956,18 +1001,6 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
         h_cavdt[e] = cvol[i] / dt;
         h_cadg[e] = (cvol[i] / dt) + cg[i];
         h_cavol[e] = cvol[i];
-      }
-    }
-    {
-      bool ok = g.region[0] == 0;
-      for (int i = 1; i < n && ok; ++i)
-        ok = g.region[i] != 0 && mechs[cl.dend_mech].kind == PA_MECH_PAS;
-      h_emok[L] = ok ? 1 : 0;
-      h_em0[L] = h_em[elem(L, 0)];
-      if (ok && n > 1) {
-        const double* p = mechs[cl.dend_mech].params;
-        // (p0 A 1e-2) e / ((cm A 1e-5) / dt): the CV's area cancels
-        h_emk[L] = ((p[0] * 1e-2) * p[1]) * dt / (cl.cm * 1e-5);
       }
     }
     h_iinj[L] = cl.i_step;
