@@ -18,6 +18,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -85,6 +86,76 @@ struct Arena {
     return off;
   }
 };
+
+// The cable rows of a model built by cell kind: per-kind tables (CV i of kind
+// q at off[q] + i) expanded into the lane-interleaved layout.  Element e is
+// row e / 32, lane e % 32 of its thread-per-cell group, or CV e - 32 row_base
+// of a wide group's cell (lane slot 0).  Rows past a cell's last CV and lanes
+// without a cell take the padding values (V, C/dt, leak E-term, coupling 0;
+// diagonal 1; no parent or children; no tree flags).  Mixed models keep V and
+// the coefficients as float-float pairs (the nearest float, then the float
+// nearest the remainder).
+struct RowKinds {
+  const double *cdt, *dc, *em, *a;
+  const int16_t *par, *och, *ocn;
+  const uint8_t* tf;
+  const int32_t* off;        // per kind, n_kind + 1
+  const int32_t* lane_kind;  // per lane, -1: no cell
+  const double* lane_v0;     // per lane: the cell's initial V
+  const int32_t* row_base;   // per group, n_groups + 1
+  int64_t n_groups, n_narrow, n_elem;
+  int mixed, tree;
+  double *V, *CDT, *DC, *EM, *A;
+  int16_t *PAR, *OCH, *OCN;
+  uint8_t* TF;
+};
+
+__device__ __forceinline__ void put_row(double* dst, int64_t e, double x, bool mixed) {
+  if (mixed) {
+    const float hi = __double2float_rn(x);
+    const float lo = __double2float_rn(x - (double)hi);
+    reinterpret_cast<float2*>(dst)[e] = make_float2(hi, lo);
+  } else {
+    dst[e] = x;
+  }
+}
+
+__global__ void expand_rows_kernel(RowKinds k) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k.n_elem; e += stride) {
+    const int32_t row = (int32_t)(e >> 5);
+    // the group: the last g with row_base[g] <= row
+    int64_t lo = 0, hi = k.n_groups;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (k.row_base[mid] <= row) lo = mid;
+      else hi = mid;
+    }
+    int64_t L, i;
+    if (lo < k.n_narrow) {
+      L = lo * 32 + (e & 31);
+      i = row - k.row_base[lo];
+    } else {
+      L = lo * 32;
+      i = e - ((int64_t)k.row_base[lo] << 5);
+    }
+    const int32_t q = k.lane_kind[L];
+    const int64_t o = q >= 0 ? (int64_t)k.off[q] + i : 0;
+    const bool in = q >= 0 && o < (int64_t)k.off[q + 1];
+    const bool mixed = k.mixed != 0;
+    put_row(k.V, e, in ? k.lane_v0[L] : 0.0, mixed);
+    put_row(k.CDT, e, in ? k.cdt[o] : 0.0, mixed);
+    put_row(k.DC, e, in ? k.dc[o] : 1.0, mixed);
+    put_row(k.EM, e, in ? k.em[o] : 0.0, mixed);
+    put_row(k.A, e, in ? k.a[o] : 0.0, mixed);
+    if (k.tree) {
+      k.PAR[e] = in ? k.par[o] : (int16_t)-1;
+      k.OCH[e] = in ? k.och[o] : (int16_t)-1;
+      k.OCN[e] = in ? k.ocn[o] : (int16_t)-1;
+      k.TF[e] = in ? k.tf[o] : (uint8_t)0;
+    }
+  }
+}
 
 }  // namespace
 
@@ -748,15 +819,76 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   };
 
   // ---- CV discretisation (a CV is a cylinder; Eq. cable) -----------------------
-  // (filled group by group in the parallel loop below)
-  HostVec<double> h_cdt(n_elem), h_dc(n_elem), h_em(n_elem), h_a(n_elem), h_V(n_elem);
+  // Without a diffusing PRP or heterosynaptic calcium (whose tables are built
+  // lane by lane below), cells that share their morphology, cm, ra and
+  // mechanisms have the same cable rows: each such kind is discretised once
+  // into per-kind tables and expand_rows_kernel writes the lane-interleaved
+  // rows on the device.  Otherwise the rows are filled here, group by group.
+  const bool by_kind = !M->prp_diff && ca_stream < 0;
+  const int64_t n_host_rows = by_kind ? 0 : n_elem;
+  HostVec<double> h_cdt(n_host_rows), h_dc(n_host_rows), h_em(n_host_rows), h_a(n_host_rows),
+      h_V(n_host_rows);
   HostVec<int16_t> h_par, h_och, h_ocn;
   HostVec<uint8_t> h_tf;
   if (M->tree) {
-    h_par.resize(n_elem);
-    h_och.resize(n_elem);
-    h_ocn.resize(n_elem);
-    h_tf.resize(n_elem);
+    h_par.resize(n_host_rows);
+    h_och.resize(n_host_rows);
+    h_ocn.resize(n_host_rows);
+    h_tf.resize(n_host_rows);
+  }
+  // the kinds: a representative cell each, the kind of every lane (-1: no
+  // cell) and every lane's initial V
+  std::vector<int32_t> kind_rep, lane_kind, kind_off(1, 0);
+  std::vector<double> lane_v0;
+  if (by_kind) {
+    struct KindKey {
+      int32_t morph, soma_mech, dend_mech;
+      uint64_t cm, ra;
+      bool operator==(const KindKey& o) const {
+        return morph == o.morph && soma_mech == o.soma_mech && dend_mech == o.dend_mech &&
+               cm == o.cm && ra == o.ra;
+      }
+    };
+    struct KindHash {
+      size_t operator()(const KindKey& k) const {
+        uint64_t h = (uint64_t)(uint32_t)k.morph * 0x9E3779B97F4A7C15ull;
+        h ^= ((uint64_t)(uint32_t)k.soma_mech << 32 | (uint32_t)k.dend_mech) + (h << 6) + (h >> 2);
+        h ^= k.cm + (h << 6) + (h >> 2);
+        h ^= k.ra + (h << 6) + (h >> 2);
+        return (size_t)h;
+      }
+    };
+    auto bits = [](double x) {
+      uint64_t u;
+      std::memcpy(&u, &x, 8);
+      return u;
+    };
+    std::unordered_map<KindKey, int32_t, KindHash> kinds;
+    lane_kind.assign(n_lanes, -1);
+    lane_v0.assign(n_lanes, 0.0);
+    for (int64_t L = 0; L < n_lanes; ++L) {
+      if (lane_gid[L] < 0) continue;
+      const pa_cell& cl = cells[lane_gid[L]];
+      const KindKey key{cl.morph, cl.soma_mech, cl.dend_mech, bits(cl.cm), bits(cl.ra)};
+      const auto it = kinds.emplace(key, (int32_t)kind_rep.size());
+      if (it.second) {
+        kind_rep.push_back(lane_gid[L]);
+        kind_off.push_back(kind_off.back() + morphs[cl.morph].n_cv);
+      }
+      lane_kind[L] = it.first->second;
+      lane_v0[L] = cl.v_init;
+    }
+  }
+  const int64_t n_kind = (int64_t)kind_rep.size(), n_kind_cv = kind_off.back();
+  std::vector<double> k_cdt(n_kind_cv, 0.0), k_dc(n_kind_cv, 1.0), k_em(n_kind_cv, 0.0),
+      k_a(n_kind_cv, 0.0), k_v(n_kind_cv, 0.0);
+  std::vector<int16_t> k_par, k_och, k_ocn;
+  std::vector<uint8_t> k_tf;
+  if (M->tree) {
+    k_par.assign(n_kind_cv, (int16_t)-1);
+    k_och.assign(n_kind_cv, (int16_t)-1);
+    k_ocn.assign(n_kind_cv, (int16_t)-1);
+    k_tf.assign(n_kind_cv, (uint8_t)0);
   }
   std::vector<uint8_t> h_is_hh(n_lanes, 0);
   std::vector<double> h_hhg(3 * n_lanes, 0.0), h_hhe(3 * n_lanes, 0.0);
@@ -910,8 +1042,44 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
       }
     }
   };
+  // the kinds' tables (kinds are independent), then each lane's per-cell values
+  std::vector<HHOut> kind_hh(n_kind);
+  std::vector<EmOut> kind_eo(n_kind);
+  parallel_ranges(n_kind, [&](int64_t q0, int64_t q1) {
+    std::vector<double> rhalf, gax;
+    for (int64_t q = q0; q < q1; ++q) {
+      const int64_t o = kind_off[q];
+      discretise(cells[kind_rep[q]], [o](int i) { return o + i; }, k_cdt.data(), k_dc.data(),
+                 k_em.data(), k_a.data(), k_v.data(), k_par.data(), k_och.data(), k_ocn.data(),
+                 k_tf.data(), kind_hh[q], kind_eo[q], rhalf, gax);
+    }
+  });
+  if (by_kind) {
+    parallel_ranges(n_lanes, [&](int64_t L0, int64_t L1) {
+      for (int64_t L = L0; L < L1; ++L) {
+        if (lane_gid[L] < 0) continue;
+        const pa_cell& cl = cells[lane_gid[L]];
+        const HHOut& hh = kind_hh[lane_kind[L]];
+        const EmOut& eo = kind_eo[lane_kind[L]];
+        if (hh.is_hh) {
+          h_is_hh[L] = 1;
+          for (int j = 0; j < 3; ++j) {
+            h_hhg[j * n_lanes + L] = hh.g[j];
+            h_hhe[j * n_lanes + L] = hh.e[j];
+          }
+        }
+        h_emok[L] = eo.ok;
+        h_em0[L] = eo.em0;
+        h_emk[L] = eo.k;
+        h_iinj[L] = cl.i_step;
+        h_kon[L] = std::llround(cl.t_on / dt);
+        h_koff[L] = cl.t_off > 1e15 ? INT64_MAX : std::llround(cl.t_off / dt);
+        h_thresh[L] = cl.threshold;
+      }
+    });
+  }
   // cells are independent: groups of lanes in parallel
-  parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
+  if (!by_kind) parallel_ranges(n_groups, [&](int64_t g0, int64_t g1) {
   std::vector<double> rhalf, gax, vol, hx, gdx;
   for (int64_t gi = g0; gi < g1; ++gi) {
   {
@@ -1399,6 +1567,18 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
                o_koff = R(8 * n_lanes), o_th = R(8 * n_lanes), o_sp = R(n_lanes),
                o_prp = R(8 * n_lanes), o_hasstc = R(n_lanes), o_rbits = R(8 * n_lanes);
   const size_t o_emk = R(8 * n_lanes), o_em0 = R(8 * n_lanes), o_emder = R(h_emder.size());
+  // per-kind row tables (models built by cell kind), read once by the expansion
+  size_t o_kcdt = 0, o_kdc = 0, o_kem = 0, o_ka = 0, o_kpar = 0, o_koch = 0, o_kocn = 0,
+         o_ktf = 0, o_kptr = 0, o_lkind = 0, o_lv0 = 0;
+  if (by_kind) {
+    o_kcdt = R(8 * n_kind_cv); o_kdc = R(8 * n_kind_cv); o_kem = R(8 * n_kind_cv);
+    o_ka = R(8 * n_kind_cv); o_kptr = R(4 * (n_kind + 1)); o_lkind = R(4 * n_lanes);
+    o_lv0 = R(8 * n_lanes);
+    if (M->tree) {
+      o_kpar = R(2 * n_kind_cv); o_koch = R(2 * n_kind_cv); o_kocn = R(2 * n_kind_cv);
+      o_ktf = R(n_kind_cv);
+    }
+  }
   size_t o_s[kMaxStreams][12];
   for (int s = 0; s < n_streams; ++s) {
     const int64_t ne = M->s_nelem[s];
@@ -1477,7 +1657,7 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   // PA_MIXED keeps the cable rows (V, coefficients; the scratch and per-CV sums
   // are written by the kernels) as float-float pairs: each double becomes the
   // nearest float and the float nearest the remainder, in its own 8 bytes
-  if (M->precision == PA_MIXED) {
+  if (M->precision == PA_MIXED && !by_kind) {
     auto to_ff = [&](HostVec<double>& v) {
       parallel_ranges((int64_t)v.size(), [&](int64_t a, int64_t b) {
         for (int64_t i = a; i < b; ++i) {
@@ -1489,13 +1669,21 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
     };
     to_ff(h_V); to_ff(h_cdt); to_ff(h_dc); to_ff(h_em); to_ff(h_a);
   }
-  putv(o_V, h_V);
-  putv(o_cdt, h_cdt); putv(o_dc, h_dc); putv(o_em, h_em); putv(o_a, h_a);
-  putv(o_hhg, h_hhg); putv(o_hhe, h_hhe);
-  if (M->tree) {
-    putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn);
-    putv(o_tf, h_tf);
+  if (!by_kind) {
+    putv(o_V, h_V);
+    putv(o_cdt, h_cdt); putv(o_dc, h_dc); putv(o_em, h_em); putv(o_a, h_a);
+    if (M->tree) {
+      putv(o_par, h_par); putv(o_och, h_och); putv(o_ocn, h_ocn);
+      putv(o_tf, h_tf);
+    }
+  } else {
+    putv(o_kcdt, k_cdt); putv(o_kdc, k_dc); putv(o_kem, k_em); putv(o_ka, k_a);
+    putv(o_kptr, kind_off); putv(o_lkind, lane_kind); putv(o_lv0, lane_v0);
+    if (M->tree) {
+      putv(o_kpar, k_par); putv(o_koch, k_och); putv(o_kocn, k_ocn); putv(o_ktf, k_tf);
+    }
   }
+  putv(o_hhg, h_hhg); putv(o_hhe, h_hhe);
   putv(o_ishh, h_is_hh);
   putv(o_wcell, h_wcell); putv(o_wbr_s, h_wbr_s); putv(o_wbr_e, h_wbr_e); putv(o_wlvl, h_wlvl);
   putv(o_wbr_p, h_wbr_p); putv(o_wbr_c, h_wbr_c); putv(o_wbr_o, h_wbr_o);
@@ -1522,6 +1710,25 @@ int build_impl(const pa_cell* cells, int64_t n_cells, const pa_morphology* morph
   putv(o_out_delay, out_delay);
   putv(o_pptr, probe_ptr); putv(o_prow, probe_row); putv(o_pid, probe_id);
   if (up_rc) return up_rc;
+  if (by_kind && n_elem > 0) {
+    char* D0 = M->dmem;
+    RowKinds rk;
+    rk.cdt = (const double*)(D0 + o_kcdt); rk.dc = (const double*)(D0 + o_kdc);
+    rk.em = (const double*)(D0 + o_kem); rk.a = (const double*)(D0 + o_ka);
+    rk.par = (const int16_t*)(D0 + o_kpar); rk.och = (const int16_t*)(D0 + o_koch);
+    rk.ocn = (const int16_t*)(D0 + o_kocn); rk.tf = (const uint8_t*)(D0 + o_ktf);
+    rk.off = (const int32_t*)(D0 + o_kptr); rk.lane_kind = (const int32_t*)(D0 + o_lkind);
+    rk.lane_v0 = (const double*)(D0 + o_lv0); rk.row_base = (const int32_t*)(D0 + o_rowbase);
+    rk.n_groups = n_groups; rk.n_narrow = n_narrow; rk.n_elem = n_elem;
+    rk.mixed = M->precision == PA_MIXED; rk.tree = M->tree;
+    rk.V = (double*)(D0 + o_V); rk.CDT = (double*)(D0 + o_cdt); rk.DC = (double*)(D0 + o_dc);
+    rk.EM = (double*)(D0 + o_em); rk.A = (double*)(D0 + o_a);
+    rk.PAR = (int16_t*)(D0 + o_par); rk.OCH = (int16_t*)(D0 + o_och);
+    rk.OCN = (int16_t*)(D0 + o_ocn); rk.TF = (uint8_t*)(D0 + o_tf);
+    const int64_t blocks = std::min<int64_t>((n_elem + 255) / 256, 148 * 16);
+    expand_rows_kernel<<<(unsigned)blocks, 256, 0, M->stream>>>(rk);
+    CUDA_TRY(cudaGetLastError());
+  }
   CUDA_TRY(cudaStreamSynchronize(M->stream));
 
   char* D = M->dmem;
