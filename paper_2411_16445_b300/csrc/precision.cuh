@@ -178,11 +178,37 @@ __device__ __forceinline__ float zsum(float a, float b) {
 // A synapse's contribution C is formed once, on its own lane (contrib); the
 // wide kernel hands contributions to other lanes by shuffle (shfl_c).  With
 // EZ (every stream's E is +0) the g E sums are signed zeros (zero_of, zsum).
+__device__ __forceinline__ bool is_zero_bits(double x) {
+  return (__double_as_longlong(x) << 1) == 0;
+}
+__device__ __forceinline__ bool is_zero_bits(float x) { return (__float_as_uint(x) << 1) == 0u; }
+__device__ __forceinline__ bool is_pos_zero_bits(double x) { return __double_as_longlong(x) == 0; }
+__device__ __forceinline__ bool is_pos_zero_bits(float x) { return __float_as_uint(x) == 0u; }
+// a + (a run of exact zeros, any_pos: one of them is +0): a nonzero a is
+// unchanged, a zero a becomes +0 when any term is +0 (the IEEE sum of zeros,
+// -0 only when every term is -0)
+__device__ __forceinline__ double zero_join(double a, bool any_pos) {
+  return (any_pos && is_zero_bits(a)) ? __longlong_as_double(0) : a;
+}
+__device__ __forceinline__ float zero_join(float a, bool any_pos) {
+  return (any_pos && is_zero_bits(a)) ? __uint_as_float(0u) : a;
+}
+
 template <class T>
 struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
   struct C {
     T g, ge;
   };
+  // a run of contributions that are all exact zeros folds on the integer
+  // pipes (add_zeros): the result of the in-order sum follows from the signs
+  static constexpr bool kZeroRuns = true;
+  __device__ static __forceinline__ bool zero_c(C c) { return is_zero_bits(c.g) && is_zero_bits(c.ge); }
+  __device__ static __forceinline__ bool pos_zero_g(C c) { return is_pos_zero_bits(c.g); }
+  __device__ static __forceinline__ bool pos_zero_e(C c) { return is_pos_zero_bits(c.ge); }
+  __device__ __forceinline__ void add_zeros(bool any_pos_g, bool any_pos_e) {
+    g = zero_join(g, any_pos_g);
+    e = zero_join(e, any_pos_e);
+  }
   template <bool EZ>
   __device__ static __forceinline__ T ge_of(T gv, T E) {
     return EZ ? zero_of(gv) : tm_mul(gv, E);
@@ -246,6 +272,7 @@ struct AccPlain {  // FP64 / FP32: gs = gs + g, es = es + g E per synapse
 
 struct AccFF {  // mixed: the run's conductance in float-float, stored as a normalised pair
   using C = float2;
+  static constexpr bool kZeroRuns = false;
   template <bool EZ>
   __device__ static __forceinline__ C contrib(float2 gv, float2) { return gv; }
   __device__ static __forceinline__ C shfl_c(C c, int src) {

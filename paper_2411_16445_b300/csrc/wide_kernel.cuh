@@ -152,10 +152,26 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           // continues the sums of earlier streams unless first on its CV
           acc.template start_c<EZ>(c0, !valid || (cs & 1), GS, ES, (uint32_t)(e0 + (cs >> 3)));
         }
-        for (int it = 1; it < maxlen; ++it) {
-          const int src = src0 + it < 31 ? src0 + it : 31;
-          const typename Acc::C ci = Acc::shfl_c(cv, src);
-          if (it < len) acc.template add_c<EZ>(ci);
+        bool zero_row = false;
+        if constexpr (Acc::kZeroRuns) {
+          // a row whose contributions are all exact zeros (zero-weight
+          // synapses): each lane's in-order sum over lanes src0 + 1 .. lane
+          // follows from the signs of the zeros (add_zeros), without the
+          // chain of dependent additions
+          zero_row = __ballot_sync(full, valid && !Acc::zero_c(cv)) == 0u;
+          if (zero_row) {
+            const unsigned pg = __ballot_sync(full, valid && Acc::pos_zero_g(cv));
+            const unsigned pe = __ballot_sync(full, valid && Acc::pos_zero_e(cv));
+            const unsigned rng = len > 1 ? (upto & ~((2u << src0) - 1u)) : 0u;
+            acc.add_zeros((pg & rng) != 0u, (pe & rng) != 0u);
+          }
+        }
+        if (!zero_row) {
+          for (int it = 1; it < maxlen; ++it) {
+            const int src = src0 + it < 31 ? src0 + it : 31;
+            const typename Acc::C ci = Acc::shfl_c(cv, src);
+            if (it < len) acc.template add_c<EZ>(ci);
+          }
         }
         if (valid && (cvf & 4)) acc.template store<EZ>(GS, ES, (uint32_t)(e0 + (cvf >> 3)), E);
         carry = acc.shfl(31);
