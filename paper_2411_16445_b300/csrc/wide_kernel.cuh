@@ -110,22 +110,42 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
       const typename PR::Ec E = PR::e_const(P.e);
       const typename PR::Dc dg = PR::d_const(P.decay_g);
       typename PR::Acc carry;  // sums of the run crossing into the next row
+      // one row of lookahead: the next row's synapse state loads while this
+      // row is updated and folded (rows are disjoint; padding elements exist)
+      int32_t n_cvf = -1;
+      uint64_t n_cm = 0, n_cam = 0;
+      TG n_g = PR::zero();
+      double n_c = 0.0, n_w = 0.0, n_z = 0.0;
+      auto fetch = [&](int t) {
+        const uint32_t e = ((uint32_t)(sb + t) << 5) | (uint32_t)lane;
+        n_cvf = D.cvf[e];
+        n_cm = cmg[e];
+        n_g = G[e];
+        if (calc) {
+          n_cam = camg[e];
+          n_c = D.c[e];
+          n_w = D.w[e];
+        }
+        if (stc) n_z = D.z[e];
+      };
+      if (nrow > 0) fetch(0);
       for (int t = 0; t < nrow; ++t) {
         const uint32_t e = ((uint32_t)(sb + t) << 5) | (uint32_t)lane;
-        const int32_t cvf = D.cvf[e];
+        const int32_t cvf = n_cvf;
+        const uint64_t cm = n_cm, cam = n_cam;
+        const TG g_old = n_g;
+        const double cc = n_c, wv = n_w, zv = n_z;
+        if (t + 1 < nrow) fetch(t + 1);
         const bool valid = cvf >= 0;  // padding only after the cell's last synapse
         TG gv = PR::zero();
         double sadd = 0.0;
         if (valid) {
-          const bool pre = (cmg[e] >> kk) & 1ull;
-          const bool capre = calc && ((camg[e] >> kk) & 1ull);
-          const double cc = calc ? D.c[e] : 0.0;
-          const double wv = calc ? D.w[e] : 0.0;
-          const double zv = stc ? D.z[e] : 0.0;
+          const bool pre = (cm >> kk) & 1ull;
+          const bool capre = calc && ((cam >> kk) & 1ull);
           // Eq. late_phase_weight with the cell's PRP, or that of the synapse's CV
           const double pz = (stc && A.prp_diff) ? A.prp_cv[e0 + (cvf >> 3)] : prp;
-          gv = syn_update<PR>(P, D, e, pre, capre, post, G[e], cc, wv, zv, pz, k, dt, A.seed,
-                              sadd);
+          gv = syn_update<PR>(P, D, e, pre, capre, post, g_old, calc ? cc : 0.0,
+                              calc ? wv : 0.0, stc ? zv : 0.0, pz, k, dt, A.seed, sadd);
           G[e] = PR::decay(gv, dg);
         }
         // Per-CV sums in canonical order (the narrow kernel's accumulator
