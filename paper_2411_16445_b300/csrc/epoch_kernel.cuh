@@ -1074,8 +1074,8 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // the default; the autotuner times all of them on the model and keeps the
 // fastest.
 // Trees also choose the fork stacks' depth (24-byte entries): with 8-byte sums
-// (FP64, mixed) shape 0 takes 3 backward rows and 11 forward rows per chunk
-// and 8 entries (many nested forks), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
+// (FP64, mixed) shape 0 takes 3 backward rows (4 where every E = +0) and 11
+// forward rows per chunk and 8 entries (many nested forks), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
 // shape 0 takes 4 rows and 6 entries; shape 5 has no stacks (trees with long
 // branches and few forks); 12 warps per SM fit in each case (4-entry stacks
 // that would let shape 1 keep 16 warps per SM on trees made it 33 % slower,
@@ -1083,7 +1083,9 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 template <class PR, bool TREE, bool EZ>
 int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   constexpr bool f64tree = TREE && sizeof(typename PR::S) == 8;
-  constexpr int RB0 = f64tree ? 3 : 4, SB0 = f64tree ? 8 : 6, RF0 = f64tree ? 11 : 12;
+  // (with every E = +0 the g E sums are not staged, which leaves room for a
+  // fourth backward row beside 11 forward rows and 8 stack entries)
+  constexpr int RB0 = (f64tree && !EZ) ? 3 : 4, SB0 = f64tree ? 8 : 6, RF0 = f64tree ? 11 : 12;
   constexpr int RB6 = f64tree ? 5 : 6;
   constexpr int SB4 = f64tree ? 2 : 6;
   switch (shape) {
