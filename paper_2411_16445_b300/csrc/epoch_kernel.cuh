@@ -291,17 +291,20 @@ struct Stage {
   // children through the list); without them, the parent and first-other-child
   // rows.
   static constexpr bool kStacks = TREE && kStackDepth > 0;  // fork stacks in use
-  static constexpr int kD = 32 * 8, kM = 32 * (int)sizeof(typename PR::S),
+  // kE: the leak E-term row, not staged by policies that form it from C/dt
+  // (their rare groups that cannot read it from memory)
+  static constexpr int kD = 32 * 8, kE = PR::kDeriveEM ? 0 : kD,
+                       kM = 32 * (int)sizeof(typename PR::S),
                        kMES = EZ ? 0 : kM,  // the g E sums (not staged with every E = +0)
                        kI = (TREE && !kStacks) ? 32 * 2 : 0, kT = kStacks ? 32 : 0;
   // backward pass: V, C/dt, diagonal, leak E term, axial coupling, synaptic sums,
   // tree rows
   static constexpr int oV = 0, oCDT = oV + kRowsBack * kD, oDC = oCDT + kRowsBack * kD,
-                       oEM = oDC + kRowsBack * kD, oA = oEM + kRowsBack * kD,
+                       oEM = oDC + kRowsBack * kD, oA = oEM + kRowsBack * kE,
                        oGS = oA + kRowsBack * kD, oES = oGS + kRowsBack * kM,
                        oPAR = oES + kRowsBack * kMES, oOCH = oPAR + kRowsBack * kI,
                        oTF = oOCH + kRowsBack * kI, kBackBytes = oTF + kRowsBack * kT;
-  static constexpr int kBackRow = 5 * kD + kM + kMES + 2 * kI + kT;
+  static constexpr int kBackRow = 4 * kD + kE + kM + kMES + 2 * kI + kT;
   // forward pass: f, x', tree rows
   static constexpr int fF = 0, fXP = fF + kRowsFwd * kD, fPAR = fXP + kRowsFwd * kD,
                        fTF = fPAR + kRowsFwd * kI, kFwdBytes = fTF + kRowsFwd * kT;
@@ -726,11 +729,11 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
             return;
           }
           // with EZ the g E sums are signed zeros: not staged (see ez_add)
-          mbar_expect_tx(&bar[s], cnt * (ST::kBackRow - (em_der ? ST::kD : 0)));
+          mbar_expect_tx(&bar[s], cnt * ST::kBackRow);
           bulk_load(st + ST::oV, Vg + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oCDT, CDT + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oDC, DC + r0 * 32, cnt * ST::kD, &bar[s]);
-          if (!em_der) bulk_load(st + ST::oEM, EM + r0 * 32, cnt * ST::kD, &bar[s]);
+          if (ST::kE) bulk_load(st + ST::oEM, EM + r0 * 32, cnt * ST::kE, &bar[s]);
           bulk_load(st + ST::oA, AA + r0 * 32, cnt * ST::kD, &bar[s]);
           bulk_load(st + ST::oGS, GS + r0 * 32, cnt * ST::kM, &bar[s]);
           if (!EZ) bulk_load(st + ST::oES, ES + r0 * 32, cnt * ST::kM, &bar[s]);
@@ -787,12 +790,16 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
               b = RW::add(RW::fma(cdt, v, RW::from_d(emt)), RW::from_d(iinj));
             } else {
               d = RW::add(dcv, gsv);
-              const R emv = em_der ? RW::from_d(A.em_soma[L]) : ((const R*)(st + ST::oEM))[r];
+              const R emv = em_der    ? RW::from_d(A.em_soma[L])
+                            : ST::kE    ? ((const R*)(st + ST::oEM))[r]
+                                        : EM[e];
               b = RW::add(RW::fma(cdt, v, emv), RW::from_d(iinj));
             }
           } else {
             d = RW::add(dcv, gsv);
-            const R emv = em_der ? RW::mul(cdt, emk) : ((const R*)(st + ST::oEM))[r];
+            const R emv = em_der ? RW::mul(cdt, emk)
+                          : ST::kE ? ((const R*)(st + ST::oEM))[r]
+                                   : EM[e];
             b = RW::fma(cdt, v, emv);
           }
           if constexpr (!EZ) {
@@ -1075,7 +1082,8 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // fastest.
 // Trees also choose the fork stacks' depth (24-byte entries): with 8-byte sums
 // (FP64, mixed) shape 0 takes 3 backward rows (4 where every E = +0) and 11
-// forward rows per chunk and 8 entries (many nested forks), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
+// forward rows per chunk and 8 entries (many nested forks; mixed with every
+// E = +0: 5 and 12 rows, 7 entries), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
 // shape 0 takes 4 rows and 6 entries; shape 5 has no stacks (trees with long
 // branches and few forks); 12 warps per SM fit in each case (4-entry stacks
 // that would let shape 1 keep 16 warps per SM on trees made it 33 % slower,
@@ -1085,7 +1093,12 @@ int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   constexpr bool f64tree = TREE && sizeof(typename PR::S) == 8;
   // (with every E = +0 the g E sums are not staged, which leaves room for a
   // fourth backward row beside 11 forward rows and 8 stack entries)
-  constexpr int RB0 = (f64tree && !EZ) ? 3 : 4, SB0 = f64tree ? 8 : 6, RF0 = f64tree ? 11 : 12;
+  // (mixed trees stage neither the g E sums nor the leak E-term: 5 backward
+  // and 12 forward rows with 7 stack entries fit, and were 0.7 % faster than
+  // 4 and 11 rows with 8 entries)
+  constexpr bool mx = PR::kDeriveEM && f64tree && EZ;
+  constexpr int RB0 = mx ? 5 : (f64tree && !EZ) ? 3 : 4, SB0 = mx ? 7 : f64tree ? 8 : 6,
+                RF0 = mx ? 12 : f64tree ? 11 : 12;
   constexpr int RB6 = f64tree ? 5 : 6;
   constexpr int SB4 = f64tree ? 2 : 6;
   switch (shape) {
