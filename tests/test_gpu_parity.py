@@ -167,6 +167,45 @@ def test_edge_cases(precision):
     check_state(o, m, precision, exact=precision == E.PA_FP64)
 
 
+def soma_over_two_cvs_net(dt=0.025, seed=21):
+    """Passive cells whose soma region covers CVs 0 and 1, beside HH cells of
+    the usual shape: the mixed kernels cannot form these groups' leak E-term
+    from C/dt and read it from memory instead."""
+    b = W._Builder(dt, seed, "soma_over_two_cvs")
+    rng = np.random.default_rng(seed)
+    hh = b.mech(W.HH, W.hh_params())
+    pas = b.mech(W.PAS, W.pas_params())
+    syn = b.mech(W.EXPSYN, W.expsyn_params(3.0, 0.0))
+    m2 = W.ball_and_stick(20.0, 200.0, 1.5, 8)
+    m2.region[1] = 0
+    two = b.morph(m2)
+    one = b.morph(W.ball_and_stick(20.0, 200.0, 1.5, 8))
+    b.cells_add(40, two, pas, pas, istep=0.05)
+    b.cells_add(8, one, hh, pas, istep=0.3)
+    n = b.n_cells
+    b.connect(W.SRC_POISSON, np.arange(n), rng.integers(0, 9, n), syn, 4e-3, rate=60.0)
+    return b.build()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_soma_over_two_cvs(precision):
+    """Groups without the formed leak E-term: the oracle (FP64 bit for bit, the
+    other forms within their bounds), and the two cell bins bit-identical."""
+    net = soma_over_two_cvs_net()
+    if precision == E.PA_FP64:
+        o, m = run_both(net, 2000, precision, chunks=3)
+    else:
+        o, m = run_replay_both(net, 2000, precision, chunks=3)
+    check_state(o, m, precision, exact=precision == E.PA_FP64)
+    m.close()
+    probes = [(0, 0), (0, 1), (net.n_cells - 1, 4)]
+    a, na = _bin_run(net, precision, E.FLAG_NARROW_ONLY, probes)
+    b, nb = _bin_run(net, precision, E.FLAG_WIDE_ALL, probes)
+    assert na == 0 and nb == net.n_cells
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
 def test_morphology_sweep_small_fp64():
     net = W.morphology_sweep(n_nets=3, cells_per_net=40)
     o, m = run_both(net, 600, E.PA_FP64, chunks=2)
