@@ -2302,24 +2302,28 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
   // element encodings: 8 = double, 4 = float, kFF = float-float pair (hi, lo)
   constexpr size_t kFF = 16;
   const size_t g_code = M->precision == PA_MIXED ? kFF : M->g_bytes;
-  auto fetch = [&](const void* dptr, int64_t n, size_t code, std::vector<double>& dst) -> int {
-    dst.assign(n, 0.0);
+  // (host arrays left uninitialised: every entry is written by the copy or
+  // the conversion)
+  auto fetch = [&](const void* dptr, int64_t n, size_t code, HostVec<double>& dst) -> int {
+    dst.clear();
     if (n == 0 || !dptr) return 0;
+    dst.resize(n);
     const size_t esz = code == kFF ? 8 : code;
-    std::vector<char> raw(n * esz);
-    cudaError_t e = cudaMemcpyAsync(raw.data(), dptr, n * esz, cudaMemcpyDeviceToHost, M->stream);
+    HostVec<char> raw;
+    if (code != 8) raw.resize(n * esz);
+    void* land = code == 8 ? (void*)dst.data() : (void*)raw.data();
+    cudaError_t e = cudaMemcpyAsync(land, dptr, n * esz, cudaMemcpyDeviceToHost, M->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
     if (e != cudaSuccess) return set_err(PA_ERR_CUDA, "read back: %s", cudaGetErrorString(e));
+    if (code == 8) return 0;
     const float* f = (const float*)raw.data();
     parallel_ranges(n, [&](int64_t i0, int64_t i1) {
       for (int64_t i = i0; i < i1; ++i)
-        dst[i] = code == 8    ? ((const double*)raw.data())[i]
-                 : code == 4  ? (double)f[i]
-                              : (double)f[2 * i] + (double)f[2 * i + 1];
+        dst[i] = code == 4 ? (double)f[i] : (double)f[2 * i] + (double)f[2 * i + 1];
     });
     return 0;
   };
-  std::vector<double> tmp, tmp2;
+  HostVec<double> tmp;
   if (field == PA_FIELD_V) {
     *n_out = M->n_cv;
     if (cap == 0) return PA_OK;
@@ -2382,7 +2386,7 @@ int pa_read_state(pa_model* M, int32_t field, double* out, int64_t cap, int64_t*
   *n_out = M->n_conn;
   if (cap == 0) return PA_OK;
   if (!out || cap < M->n_conn) return set_err(PA_ERR_ARG, "output too small");
-  std::vector<std::vector<double>> per_stream(M->n_streams);
+  std::vector<HostVec<double>> per_stream(M->n_streams);
   for (int s = 0; s < M->n_streams; ++s) {
     const StreamDev& D = M->ea.sd[s];
     const int kind = M->sp[s].kind;
@@ -2443,7 +2447,7 @@ int pa_read_weights(pa_model* M, double* out, int64_t cap, int64_t* n_out) {
     need_w = need_w || kind == SK_GB || kind == SK_STDP || kind == SK_HCA;
     need_hz = need_hz || kind == SK_STC;
   }
-  std::vector<double> w, h, z;
+  HostVec<double> w, h, z;  // (every entry is written by pa_read_state)
   int64_t n;
   int rc = 0;
   if (need_w) {
