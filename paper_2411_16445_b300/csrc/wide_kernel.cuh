@@ -8,9 +8,11 @@
 // Per step, in the same order and with the same operations as the narrow
 // kernel (epoch_kernel.cuh), so that both equal the plain definition:
 //   a. synapse streams: lanes update 32 synapses at a time in parallel
-//      (events, POST_EVENT, plasticity; syn_update); the per-CV sums and the
-//      cell's STC sum S are then folded in canonical synapse order, every lane
-//      reading the 32 values by shuffle, so the sums are the sequential ones;
+//      (events, POST_EVENT, plasticity; syn_update), the next row's state
+//      loading meanwhile; the per-CV sums and the cell's STC sum S are then
+//      folded in canonical synapse order, every lane reading the 32 values by
+//      shuffle, so the sums are the sequential ones (a row of exact zeros
+//      changes a sum only through the sign rule of zeros, taken from ballots);
 //   b. backward pass by branches: a branch is a run of rows i whose parent is
 //      i - 1 (contiguous in the numbering), cut after every fork; at a fork the
 //      first child's values come from memory like the other children's, applied
