@@ -36,6 +36,46 @@ namespace pa {
 
 constexpr int kWideFwdChunk = 4;  // forward-pass rows whose f and x' load together
 
+// The FP64 HH soma's gate update (HH64::rates, then HH64::gate for m, h, n) on
+// the lanes of the cell's warp, operation for operation the sequential one:
+// lanes 0-5 each form one rate (am, bm, ah, bh, an, bn) by one instruction
+// stream, every form's steps taken on every lane and the lane's own chosen
+// by selects; lanes 0-2 then update m, h, n.  Called by the whole warp; the
+// gates live on lane 0.
+template <bool kF32>
+__device__ __forceinline__ void hh64_update_warp(SomaHH<kF32>& soma, double v, double dt,
+                                                 int lane) {
+  static_assert(!kF32, "FP64 gates only");
+  const unsigned full = 0xffffffffu;
+  const int q = lane < 6 ? lane : 0;
+  // rate q: A vtrap(-(v + B), C) (am, an), A exp(-(v + B) / C) (bm, ah, bn),
+  // 1 / (exp(-(v + B) / C) + 1) (bh)
+  const double B = q == 0 ? 40.0 : q == 3 ? 35.0 : q == 4 ? 55.0 : 65.0;
+  const double Cq = q == 0 ? 10.0 : q == 1 ? 18.0 : q == 2 ? 20.0 : q == 3 ? 10.0
+                  : q == 4 ? 10.0 : 80.0;
+  const double Aq = q == 0 ? 0.1 : q == 1 ? 4.0 : q == 2 ? 0.07 : q == 4 ? 0.01 : 0.125;
+  const bool vt = q == 0 || q == 4, sig = q == 3;
+  const double x = -(v + B);
+  const double u = x / Cq;
+  const double e = model_exp(u);
+  const double d = (vt ? x : 1.0) / (vt ? e - 1.0 : e + 1.0);
+  double r = (vt || sig) ? d : e;
+  if (vt && fabs(u) < 1e-6) r = Cq * (1.0 - 0.5 * u);
+  const double rate = sig ? r : Aq * r;
+  // gate g on lane g: rates 2g and 2g + 1, the gate's value from lane 0
+  const int g = lane < 3 ? lane : 0;
+  const double a = __shfl_sync(full, rate, 2 * g), b = __shfl_sync(full, rate, 2 * g + 1);
+  const double m0 = __shfl_sync(full, soma.m, 0), h0 = __shfl_sync(full, soma.h, 0),
+               n0 = __shfl_sync(full, soma.n, 0);
+  const double x0 = g == 0 ? m0 : g == 1 ? h0 : n0;
+  const double sab = a + b;
+  const double xinf = a / sab;
+  const double xn = xinf + (x0 - xinf) * model_exp(-dt * sab);
+  soma.m = __shfl_sync(full, xn, 0);
+  soma.h = __shfl_sync(full, xn, 1);
+  soma.n = __shfl_sync(full, xn, 2);
+}
+
 template <class PR, bool EZ>
 __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
   using TS = typename PR::S;
@@ -431,9 +471,16 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
     }
     // ---- e. soma gates, detection (lane 0) -------------------------------------------
     bool spk = false;
+    // (FP64 policy: its unit is compiled without contraction, so the spread
+    // update is the sequential one bit for bit; the other policies keep the
+    // narrow kernel's code on lane 0)
+    constexpr bool kSpreadHH = PR::kId == PrecF64::kId;
+    if constexpr (kSpreadHH) {
+      if (hh) hh64_update_warp(soma, __shfl_sync(full, v0_new, 0), dt, lane);
+    }
     if (lane == 0) {
-      if (hh) {
-        soma.update(v0_new, dt);
+      if constexpr (!kSpreadHH) {
+        if (hh) soma.update(v0_new, dt);
       }
       spk = v0_old < th && v0_new >= th;
       if (spk) {
