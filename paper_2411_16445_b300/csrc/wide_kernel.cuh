@@ -238,11 +238,16 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
         if (valid && (cvf & 4)) acc.template store<EZ>(GS, ES, (uint32_t)(e0 + (cvf >> 3)), E);
         carry = acc.shfl(31);
         if (stc) {
-          // the cell's S = sum |h - h0| over its STC synapses, in order
+          // the cell's S = sum |h - h0| over its STC synapses, in order.  S
+          // starts at +0 and every term is >= +0, so a term of +0 (h = h0
+          // exactly) leaves S unchanged: only the nonzero terms are added,
+          // still in order
+          unsigned nz = __ballot_sync(full, valid && !is_zero_bits(sadd));
 #pragma unroll 1
-          for (int q = 0; q < 32; ++q) {
-            const double sq = __shfl_sync(full, sadd, q);
-            if (__shfl_sync(full, cvf, q) >= 0) S = S + sq;
+          while (nz) {
+            const int q = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            S = S + __shfl_sync(full, sadd, q);
           }
         }
       }
