@@ -214,21 +214,33 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           // continues the sums of earlier streams unless first on its CV
           acc.template start_c<EZ>(c0, !valid || (cs & 1), GS, ES, (uint32_t)(e0 + (cs >> 3)));
         }
-        bool zero_row = false;
+        bool sparse = false;
         if constexpr (Acc::kZeroRuns) {
-          // a row whose contributions are all exact zeros (zero-weight
-          // synapses): each lane's in-order sum over lanes src0 + 1 .. lane
-          // follows from the signs of the zeros (add_zeros), without the
-          // chain of dependent additions
-          zero_row = __ballot_sync(full, valid && !Acc::zero_c(cv)) == 0u;
-          if (zero_row) {
+          // Exact zeros in the in-order sums.  Adding a zero changes a partial
+          // sum only when that sum is itself a zero (IEEE: x + 0 = x for
+          // x != 0); a sum that has taken a nonzero term is never -0 again
+          // (exact cancellation gives +0), and a zero plus a nonzero t is t.
+          // So each lane's sum over lanes src0 + 1 .. lane equals the sum of
+          // its nonzero terms in order, followed by the sign rule of zeros
+          // (add_zeros: +0 if the range holds a +0 and the sum is a zero).
+          // Where the row has fewer nonzero terms than the dense fold has
+          // steps, only those are added (all-zero rows: none).
+          const unsigned nzm = __ballot_sync(full, valid && !Acc::zero_c(cv));
+          if (__popc(nzm) + 1 < maxlen) {
+            sparse = true;
             const unsigned pg = __ballot_sync(full, valid && Acc::pos_zero_g(cv));
             const unsigned pe = __ballot_sync(full, valid && Acc::pos_zero_e(cv));
             const unsigned rng = len > 1 ? (upto & ~((2u << src0) - 1u)) : 0u;
+#pragma unroll 1
+            for (unsigned mm = nzm; mm; mm &= mm - 1u) {
+              const int qn = __ffs(mm) - 1;
+              const typename Acc::C ci = Acc::shfl_c(cv, qn);
+              if ((rng >> qn) & 1u) acc.template add_c<EZ>(ci);
+            }
             acc.add_zeros((pg & rng) != 0u, (pe & rng) != 0u);
           }
         }
-        if (!zero_row) {
+        if (!sparse) {
           for (int it = 1; it < maxlen; ++it) {
             const int src = src0 + it < 31 ? src0 + it : 31;
             const typename Acc::C ci = Acc::shfl_c(cv, src);
