@@ -316,10 +316,27 @@ struct Stage {
   // (the depth is part of the kernel shape: deep stacks where many forks nest,
   // shallow ones where longer backward chunks take the shared memory)
   static constexpr int kStackB = kStackDepth, kStackF = 2 * kStackDepth;
-  static constexpr int kStackBytes = kStacks ? 32 * kStackB * 24 : 0;
-  static_assert(32 * kStackF * 8 <= 32 * kStackB * 24, "forward stack fits the region");
+  // a backward entry: (f, x', coupling), or the two products (16 bytes)
+  static constexpr int kSE = PR::Row::kProdStack ? 16 : 24;
+  static constexpr int kStackBytes = kStacks ? 32 * kStackB * kSE : 0;
+  static_assert(32 * kStackF * 8 <= 32 * kStackB * kSE, "forward stack fits the region");
   static constexpr int kWarpBytes = kStages * kBytes + 64 + kStackBytes;  // + mbarriers
 };
+
+// A non-first child entering its parent's row: d - f a, b - a x' (by fused
+// multiply-adds, or as subtracted products where the row form keeps them)
+template <class RW>
+__device__ __forceinline__ void other_child(typename RW::R a, typename RW::R f,
+                                            typename RW::R x, typename RW::R& d,
+                                            typename RW::R& b) {
+  if constexpr (RW::kProdStack) {
+    d = RW::sub(d, RW::mul(a, f));
+    b = RW::sub(b, RW::mul(a, x));
+  } else {
+    d = RW::fnma(f, a, d);
+    b = RW::fnma(a, x, b);
+  }
+}
 
 // b + es for a CV whose g E sum es is a signed zero (every stream's E is +0):
 // b itself unless b is -0, when the stored es decides (a call, so that the
@@ -535,7 +552,11 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
   struct FX {
     typename PR::Row::R f, x, a;
   };
-  FX* stack2 = (FX*)(wbuf + kStages * ST::kBytes + 64);
+  struct FP {  // (coupling f, coupling x') of the product form
+    typename PR::Row::R p, q;
+  };
+  using SE = typename std::conditional<PR::Row::kProdStack, FP, FX>::type;
+  SE* stack2 = (SE*)(wbuf + kStages * ST::kBytes + 64);
   typename PR::Row::R* stack1 = (typename PR::Row::R*)stack2;
   if (lane == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
@@ -814,30 +835,44 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
               // the one other child: its f, x' and coupling from the top of the
               // fork stack (eliminated earlier in this pass)
               --depth;
-              R fc, xc, ac;
-              if (depth < ST::kStackB) {
-                const FX t = stack2[depth * 32 + lane];
-                fc = t.f;
-                xc = t.x;
-                ac = t.a;
+              if constexpr (RW::kProdStack) {
+                R pc, qc;
+                if (depth < ST::kStackB) {
+                  const SE t = stack2[depth * 32 + lane];
+                  pc = t.p;
+                  qc = t.q;
+                } else {
+                  const uint32_t ec = elem_of(rb, A.och_head[e], lane);
+                  const bool ok = PA_IN(A, ec, A.n_row_elems);
+                  const R ac = ok ? AA[ec] : RW::zero();
+                  pc = RW::mul(ac, ok ? F[ec] : RW::zero());
+                  qc = RW::mul(ac, ok ? XP[ec] : RW::zero());
+                }
+                d = RW::sub(d, pc);
+                b = RW::sub(b, qc);
               } else {
-                const uint32_t ec = elem_of(rb, A.och_head[e], lane);
-                const bool ok = PA_IN(A, ec, A.n_row_elems);
-                fc = ok ? F[ec] : RW::zero();
-                xc = ok ? XP[ec] : RW::zero();
-                ac = ok ? AA[ec] : RW::zero();
+                R fc, xc, ac;
+                if (depth < ST::kStackB) {
+                  const SE t = stack2[depth * 32 + lane];
+                  fc = t.f;
+                  xc = t.x;
+                  ac = t.a;
+                } else {
+                  const uint32_t ec = elem_of(rb, A.och_head[e], lane);
+                  const bool ok = PA_IN(A, ec, A.n_row_elems);
+                  fc = ok ? F[ec] : RW::zero();
+                  xc = ok ? XP[ec] : RW::zero();
+                  ac = ok ? AA[ec] : RW::zero();
+                }
+                other_child<RW>(ac, fc, xc, d, b);
               }
-              d = RW::fnma(fc, ac, d);
-              b = RW::fnma(ac, xc, b);
             } else if (!ST::kStacks || (tf & kOtherList)) {
               // several other children, highest index first, from the scratch arrays
               const int och = ST::kStacks ? A.och_head[e] : ((const int16_t*)(st + ST::oOCH))[r];
               for (int ch = och; ch >= 0;) {
                 const uint32_t ec = elem_of(rb, ch, lane);
                 if (!PA_IN(A, ec, A.n_row_elems)) break;
-                const R ac = AA[ec];
-                d = RW::fnma(F[ec], ac, d);
-                b = RW::fnma(ac, XP[ec], b);
+                other_child<RW>(AA[ec], F[ec], XP[ec], d, b);
                 ch = A.och_next[ec];
               }
             }
@@ -854,7 +889,10 @@ __device__ __forceinline__ void epoch_warp(const EpochArgs& A, const int g, char
             F[e] = fi;
             XP[e] = xi;
             if (TREE && (tf & kForkPush)) {
-              if (depth < ST::kStackB) stack2[depth * 32 + lane] = FX{fi, xi, ai};
+              if (depth < ST::kStackB) {
+                if constexpr (RW::kProdStack) stack2[depth * 32 + lane] = SE{RW::mul(ai, fi), RW::mul(ai, xi)};
+                else stack2[depth * 32 + lane] = SE{fi, xi, ai};
+              }
               ++depth;
             }
             carry = !TREE || (ST::kStacks ? (tf & kParPrev) != 0 : pi == i - 1);
@@ -1083,7 +1121,7 @@ int launch_epoch_t(const EpochArgs& a, void* stream) {
 // Trees also choose the fork stacks' depth (24-byte entries): with 8-byte sums
 // (FP64, mixed) shape 0 takes 3 backward rows (4 where every E = +0) and 11
 // forward rows per chunk and 8 entries (many nested forks; mixed with every
-// E = +0: 5 and 12 rows, 7 entries), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
+// E = +0: 5 and 12 rows, 10 entries of 16 bytes), shapes 3 and 4 take 4 rows and 2 entries; with FP32 sums
 // shape 0 takes 4 rows (5 where every E = +0) and 6 entries; shape 5 has no stacks (trees with long
 // branches and few forks); 12 warps per SM fit in each case (4-entry stacks
 // that would let shape 1 keep 16 warps per SM on trees made it 33 % slower,
@@ -1093,15 +1131,16 @@ int launch_epoch_shape(const EpochArgs& a, int shape, void* stream) {
   constexpr bool f64tree = TREE && sizeof(typename PR::S) == 8;
   // (with every E = +0 the g E sums are not staged, which leaves room for a
   // fourth backward row beside 11 forward rows and 8 stack entries)
-  // (mixed trees stage neither the g E sums nor the leak E-term: 5 backward
-  // and 12 forward rows with 7 stack entries fit, and were 0.7 % faster than
-  // 4 and 11 rows with 8 entries)
+  // (mixed trees stage neither the g E sums nor the leak E-term and keep
+  // 16-byte stack entries: 5 backward and 12 forward rows with 10 entries
+  // fit; 0.7 % faster than 4 and 11 rows, then 1.4 % from the product-form
+  // entries, 10 of them against 7 of 24 bytes)
   // (FP32 sums with every E = +0 leave room for 5 backward rows as well:
   // 1.6 % faster than 4 on the large network)
   constexpr bool mx = PR::kDeriveEM && f64tree && EZ;
   constexpr bool f32ez = TREE && !f64tree && EZ;
-  constexpr int RB0 = (mx || f32ez) ? 5 : (f64tree && !EZ) ? 3 : 4, SB0 = mx ? 7 : f64tree ? 8 : 6,
-                RF0 = mx ? 12 : f64tree ? 11 : 12;
+  constexpr int RB0 = (mx || f32ez) ? 5 : (f64tree && !EZ) ? 3 : 4,
+                SB0 = mx ? 10 : f64tree ? 8 : 6, RF0 = mx ? 12 : f64tree ? 11 : 12;
   constexpr int RB6 = f64tree ? 5 : 6;
   constexpr int SB4 = f64tree ? 2 : 6;
   switch (shape) {

@@ -109,6 +109,9 @@ struct RowD {
   __device__ static __forceinline__ R fma(R a, R b, R c) { return ::fma(a, b, c); }
   // c - a b
   __device__ static __forceinline__ R fnma(R a, R b, R c) { return ::fma(-a, b, c); }
+  // a non-first child enters its parent's row by fused multiply-adds (the
+  // oracle's operations); its fork-stack entry holds (f, x', coupling)
+  static constexpr bool kProdStack = false;
   __device__ static __forceinline__ R rcp(R d) { return rcp_rn_pos(d); }
   __device__ static __forceinline__ double to_d(R a) { return a; }
   __device__ static __forceinline__ R from_d(double x) { return x; }
@@ -129,6 +132,13 @@ struct RowFF {
   // dependent chain than a product followed by an addition)
   __device__ static __forceinline__ R fma(R a, R b, R c) { return fold(a, b, c, 1.0f); }
   __device__ static __forceinline__ R fnma(R a, R b, R c) { return fold(a, b, c, -1.0f); }
+  // a non-first child enters its parent's row as the normalised products
+  // (coupling f, coupling x') subtracted, so that a fork-stack entry holds the
+  // two products (16 bytes) instead of f, x' and the coupling
+  static constexpr bool kProdStack = true;
+  __device__ static __forceinline__ R sub(R c, R p) {
+    return ff_add(c, make_float2(-p.x, -p.y));
+  }
   __device__ static __forceinline__ R fold(R a, R b, R c, float sg) {
     const float ph = __fmul_rn(a.x, b.x);
     float pl = __fmaf_rn(a.x, b.x, -ph);

@@ -335,13 +335,10 @@ __global__ void __launch_bounds__(128, 2) wide_kernel(const EpochArgs A) {
           if (i == be) {
             // the other children, highest index first, then the first child
             if (co >= 0) {
-              d = RW::fnma(fo, ao, d);
-              bb = RW::fnma(ao, xo, bb);
+              other_child<RW>(ao, fo, xo, d, bb);
               for (int ch = cn; ch >= 0; ch = OCN[e0 + ch]) {  // a third child and more
                 const int64_t ec = e0 + ch;
-                const R ac = AA[ec];
-                d = RW::fnma(F[ec], ac, d);
-                bb = RW::fnma(ac, XP[ec], bb);
+                other_child<RW>(AA[ec], F[ec], XP[ec], d, bb);
               }
             }
             if (c1 >= 0) {
