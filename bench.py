@@ -46,12 +46,12 @@ FALLBACK_HBM_GBS = 6400.0      # the profiling recipe's fallback when no measure
 SURVEY_BYTES_PER_CU = {"fp64": 60.0, "mixed": 45.0, "fp32": 45.0}
 # DRAM bytes per compartment-update of the epoch kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of a 65,536-cell launch of the
-# same generator, shape 0, the kernels for reversal potentials of +0: 82.39 GB
+# same generator, shape 0, the kernels for reversal potentials of +0: 82.47 GB
 # (mixed, float-float solve, leak E-term formed) and 88.42 GB (FP64) for
 # 735.3 M CU), scaled to a full launch by the CUs it processes, since traffic
 # grows in proportion to them; absent once the kernel has changed since the
 # counters were taken (and for the FP32-mechanism kernel, not captured).
-TRAFFIC_B_PER_CU = {"mixed": 112.1, "fp64": 120.2}
+TRAFFIC_B_PER_CU = {"mixed": 112.2, "fp64": 120.2}
 
 
 def measured_peaks():
